@@ -1,0 +1,205 @@
+"""FP64 CPU oracle of the explicit TE/TM scheme (Sec. 4.2, Eq. (23)).
+
+TEST INFRASTRUCTURE. Only the test suite, ``__graft_entry__.smoke()`` and the
+CPU-baseline leg of ``bench.py`` may import this package. It shares no code
+with the CUDA path (``paper_0901_1053_gb300``) and never imports it.
+
+The arithmetic lives in ``tetm_oracle.c`` (plain loops, one function per
+paper passage); this module only loads it with ctypes, marshals numpy arrays
+and offers the canonical FIT layout helpers.
+
+Component numbering: 0 ex, 1 ey, 2 ez, 3 hx, 4 hy, 5 hz. Every field array
+has the canonical FIT shape ``(nz+1, ny+1, nx+1)`` (x fastest), float64, in
+integral units (edge voltages [V], dual-edge currents [A]).
+
+Parity status: every function here is pinned by the ``-m "not gpu"`` tests
+(dense matrix form of Eq. (23), eigen-angles of Eq. (27), energy law (19),
+charge laws (34)/(35), exact z-shift at c*dt = dz, loss-factor identity).
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+import numpy as np
+
+from .build import build_oracle, library_path
+
+COMPONENTS = ("ex", "ey", "ez", "hx", "hy", "hz")
+C_LIGHT = 299792458.0
+EPS0 = 8.8541878128e-12
+MU0 = 1.0 / (EPS0 * C_LIGHT * C_LIGHT)
+
+_lib = None
+
+
+def _load():
+    global _lib
+    if _lib is not None:
+        return _lib
+    path = library_path()
+    if not os.path.exists(path):
+        build_oracle()
+    lib = ctypes.CDLL(path)
+    d, i, vp = ctypes.c_double, ctypes.c_int, ctypes.c_void_p
+    dp = ctypes.POINTER(ctypes.c_double)
+    lib.oracle_new.restype = vp
+    lib.oracle_new.argtypes = [i, i, i, d, d, d, d, vp, vp, vp]
+    lib.oracle_free.argtypes = [vp]
+    lib.oracle_stable.restype = i
+    lib.oracle_stable.argtypes = [d, d, d, d]
+    lib.oracle_set_bunch.restype = i
+    lib.oracle_set_bunch.argtypes = [vp, d, d, i, i]
+    lib.oracle_current.argtypes = [vp, ctypes.c_long, vp]
+    lib.oracle_step_j.argtypes = [vp, vp, vp, vp]
+    lib.oracle_step.argtypes = [vp, i]
+    lib.oracle_step_custom.argtypes = [vp, vp, vp, vp]
+    lib.oracle_wake.restype = i
+    lib.oracle_wake.argtypes = [vp, vp, i, ctypes.POINTER(i), dp, dp]
+    lib.oracle_energy.restype = d
+    lib.oracle_energy.argtypes = [vp]
+    lib.oracle_qbar_e.argtypes = [vp] + [vp] * 6
+    lib.oracle_qbar_h.argtypes = [vp] + [vp] * 6
+    lib.oracle_get.argtypes = [vp, i, vp]
+    lib.oracle_set.argtypes = [vp, i, vp]
+    lib.oracle_coef.argtypes = [vp, i, vp]
+    lib.oracle_step_count.restype = ctypes.c_long
+    lib.oracle_step_count.argtypes = [vp]
+    lib.oracle_dt.restype = d
+    lib.oracle_dt.argtypes = [vp]
+    lib.oracle_bunch_info.restype = i
+    lib.oracle_bunch_info.argtypes = [vp, ctypes.POINTER(i), ctypes.POINTER(i),
+                                      ctypes.POINTER(i), vp]
+    _lib = lib
+    return lib
+
+
+def _ptr(a):
+    return None if a is None else a.ctypes.data_as(ctypes.c_void_p)
+
+
+def stable(dx, dy, dz, cdt):
+    """Eq. (25): c*dt <= dz and c*dt <= (dx^-2 + dy^-2)^-1/2."""
+    return bool(_load().oracle_stable(dx, dy, dz, cdt))
+
+
+class Oracle:
+    """One FP64 solve on a closed PEC box (Sec. 2, Eq. (1)), cold start.
+
+    ``eps_r``, ``mu_r``: float64 per primary cell, shape (nz, ny, nx) or None
+    (vacuum); ``pec``: uint8 per cell, 1 = PEC, or None. ``cdt`` = c*dt in
+    metres, 0 means dz (the "magic" step of Sec. 4.5).
+    """
+
+    def __init__(self, nx, ny, nz, dx, dy, dz, cdt=0.0, eps_r=None, mu_r=None, pec=None):
+        self.lib = _load()
+        self.nx, self.ny, self.nz = int(nx), int(ny), int(nz)
+        self.dx, self.dy, self.dz = float(dx), float(dy), float(dz)
+        shape_c = (self.nz, self.ny, self.nx)
+        self._keep = []
+        args = []
+        for a, dt in ((eps_r, np.float64), (mu_r, np.float64), (pec, np.uint8)):
+            if a is None:
+                args.append(None)
+            else:
+                a = np.ascontiguousarray(a, dtype=dt).reshape(shape_c)
+                self._keep.append(a)
+                args.append(_ptr(a))
+        h = self.lib.oracle_new(self.nx, self.ny, self.nz, self.dx, self.dy, self.dz,
+                                float(cdt), *args)
+        if not h:
+            raise ValueError("oracle_new: invalid grid")
+        self.h = ctypes.c_void_p(h)
+        self.shape = (self.nz + 1, self.ny + 1, self.nx + 1)
+        self.dt = self.lib.oracle_dt(self.h)
+        self.alpha = 0.5 * self.dt
+
+    def __del__(self):
+        h = getattr(self, "h", None)
+        if h is not None and self.lib is not None:
+            self.lib.oracle_free(h)
+            self.h = None
+
+    # --- fields -----------------------------------------------------------
+    def get(self, comp):
+        out = np.empty(self.shape, dtype=np.float64)
+        self.lib.oracle_get(self.h, _comp(comp), _ptr(out))
+        return out
+
+    def set(self, comp, arr):
+        a = np.ascontiguousarray(arr, dtype=np.float64).reshape(self.shape)
+        self.lib.oracle_set(self.h, _comp(comp), _ptr(a))
+
+    def coef(self, comp):
+        out = np.empty(self.shape, dtype=np.float64)
+        self.lib.oracle_coef(self.h, _comp(comp), _ptr(out))
+        return out
+
+    def fields(self):
+        return {c: self.get(c) for c in COMPONENTS}
+
+    # --- bunch, stepping, wake ---------------------------------------------
+    def set_bunch(self, sigma, charge, i0, j0):
+        if self.lib.oracle_set_bunch(self.h, float(sigma), float(charge), int(i0), int(j0)) != 0:
+            raise ValueError("oracle_set_bunch: bad argument")
+
+    def current(self, n):
+        out = np.zeros(self.shape, dtype=np.float64)
+        self.lib.oracle_current(self.h, int(n), _ptr(out))
+        return out
+
+    def step(self, n=1):
+        self.lib.oracle_step(self.h, int(n))
+
+    def step_custom(self, jz=None, jx=None, jy=None):
+        arrs = [None if a is None else np.ascontiguousarray(a, dtype=np.float64).reshape(self.shape)
+                for a in (jz, jx, jy)]
+        self.lib.oracle_step_custom(self.h, *[_ptr(a) for a in arrs])
+
+    @property
+    def step_count(self):
+        return int(self.lib.oracle_step_count(self.h))
+
+    def wake(self):
+        n = ctypes.c_int()
+        s0 = ctypes.c_double()
+        ds = ctypes.c_double()
+        if self.lib.oracle_wake(self.h, None, 0, ctypes.byref(n), ctypes.byref(s0),
+                                ctypes.byref(ds)) != 0:
+            raise RuntimeError("no bunch set")
+        out = np.empty(n.value, dtype=np.float64)
+        self.lib.oracle_wake(self.h, _ptr(out), n.value, None, None, None)
+        return out, s0.value, ds.value
+
+    def bunch_info(self):
+        c0, mn, mx = ctypes.c_int(), ctypes.c_int(), ctypes.c_int()
+        if self.lib.oracle_bunch_info(self.h, ctypes.byref(c0), ctypes.byref(mn),
+                                      ctypes.byref(mx), None) != 0:
+            raise RuntimeError("no bunch set")
+        qcell = np.empty(2 * c0.value, dtype=np.float64)
+        self.lib.oracle_bunch_info(self.h, ctypes.byref(c0), ctypes.byref(mn), ctypes.byref(mx),
+                                   _ptr(qcell))
+        return {"c0": c0.value, "m_min": mn.value, "m_max": mx.value, "qcell": qcell}
+
+    # --- invariants -----------------------------------------------------------
+    def energy(self):
+        return float(self.lib.oracle_energy(self.h))
+
+    def qbar_e(self, ex1, ex0, ey1, ey0, ez):
+        arrs = [np.ascontiguousarray(a, dtype=np.float64).reshape(self.shape)
+                for a in (ex1, ex0, ey1, ey0, ez)]
+        q = np.empty(self.shape, dtype=np.float64)
+        self.lib.oracle_qbar_e(self.h, *[_ptr(a) for a in arrs], _ptr(q))
+        return q
+
+    def qbar_h(self, hx1, hx0, hy1, hy0, hz):
+        arrs = [np.ascontiguousarray(a, dtype=np.float64).reshape(self.shape)
+                for a in (hx1, hx0, hy1, hy0, hz)]
+        q = np.empty(self.shape, dtype=np.float64)
+        self.lib.oracle_qbar_h(self.h, *[_ptr(a) for a in arrs], _ptr(q))
+        return q
+
+
+def _comp(c):
+    if isinstance(c, str):
+        return COMPONENTS.index(c)
+    return int(c)

@@ -1,0 +1,523 @@
+"""Pins of the FP64 oracle against what the paper and the mathematics fix.
+
+Each test checks the oracle (oracle/tetm_oracle.c) against something other
+than itself: the dense two-level form (23) assembled from the operator
+definitions of Sec. 2 and Sec. 4.2, the closed-form dispersion relation (27),
+the energy law (19), the charge laws (34)/(35), Gauss's law for the bunch,
+the exact one-cell shift of a TEM pulse at c*dt = dz (Sec. 4.5), causality,
+and the loss-factor identity that ties the wake of Sec. 5 to the field energy.
+"""
+import math
+
+import numpy as np
+import pytest
+
+import oracle
+from oracle import Oracle, C_LIGHT, MU0, EPS0
+from dense23 import Dense23
+from paper_0901_1053_gb300 import workloads as wl
+
+MM = 1e-3
+DXY = math.sqrt(2.0) * MM
+
+
+def _random_state(o, seed, scale=1.0):
+    rng = np.random.default_rng(seed)
+    for c in oracle.COMPONENTS:
+        o.set(c, scale * rng.standard_normal(o.shape))
+
+
+def _coefs(o):
+    return [o.coef(c) for c in range(6)]
+
+
+# ---------------------------------------------------------------------------
+# Geometry (staircase reading of the material matrices)
+# ---------------------------------------------------------------------------
+
+def test_vacuum_box_active_counts_and_values():
+    nx, ny, nz = 3, 4, 5
+    o = Oracle(nx, ny, nz, 1.3 * MM, 1.7 * MM, 0.9 * MM)
+    dx, dy, dz = 1.3 * MM, 1.7 * MM, 0.9 * MM
+    counts = [int(np.count_nonzero(o.coef(c))) for c in range(6)]
+    assert counts == [nx * (ny - 1) * (nz - 1), (nx - 1) * ny * (nz - 1), (nx - 1) * (ny - 1) * nz,
+                      (nx - 1) * ny * nz, nx * (ny - 1) * nz, nx * ny * (nz - 1)]
+    expect = [dx / (EPS0 * dy * dz), dy / (EPS0 * dx * dz), dz / (EPS0 * dx * dy),
+              dx / (MU0 * dy * dz), dy / (MU0 * dx * dz), dz / (MU0 * dx * dy)]
+    for c in range(6):
+        v = o.coef(c)
+        np.testing.assert_allclose(v[v != 0], expect[c], rtol=1e-15)
+
+
+def test_pec_cell_deactivates_its_edges_and_faces():
+    nx = ny = nz = 4
+    pec = np.zeros((nz, ny, nx), np.uint8)
+    pec[1, 2, 1] = 1                    # cell (ci=1, cj=2, ck=1)
+    o0 = Oracle(nx, ny, nz, MM, MM, MM)
+    o1 = Oracle(nx, ny, nz, MM, MM, MM, pec=pec)
+    # brute force from the cell side: the 12 edges and 6 faces of the cell
+    ci, cj, ck = 1, 2, 1
+    edges = {0: [(ci, cj + b, ck + c) for b in (0, 1) for c in (0, 1)],
+             1: [(ci + a, cj, ck + c) for a in (0, 1) for c in (0, 1)],
+             2: [(ci + a, cj + b, ck) for a in (0, 1) for b in (0, 1)],
+             3: [(ci + a, cj, ck) for a in (0, 1)],
+             4: [(ci, cj + b, ck) for b in (0, 1)],
+             5: [(ci, cj, ck + c) for c in (0, 1)]}
+    for comp in range(6):
+        a0, a1 = o0.coef(comp) != 0, o1.coef(comp) != 0
+        lost = set(zip(*np.nonzero(a0 & ~a1)))
+        lost = {(int(i), int(j), int(k)) for (k, j, i) in lost}
+        expect = {e for e in edges[comp] if a0[e[2], e[1], e[0]]}
+        assert lost == expect, (comp, lost, expect)
+        assert not np.any(a1 & ~a0)
+
+
+def test_material_averaging():
+    nx = ny = nz = 3
+    eps = np.full((nz, ny, nx), 2.0)
+    eps[1, 1, 1] = 4.0
+    mu = np.full((nz, ny, nx), 1.0)
+    mu[1, 1, 1] = 3.0
+    o = Oracle(nx, ny, nz, MM, MM, MM, eps_r=eps, mu_r=mu)
+    # ez edge (1,1,k=1+1/2) touches cells (0..1, 0..1, 1): one of them eps 4
+    ez = o.coef(2)
+    assert ez[1, 1, 1] == pytest.approx(MM / (EPS0 * (2.0 + 2.0 + 2.0 + 4.0) / 4.0 * MM * MM), rel=1e-15)
+    # hx face x=1 between cells (0,1,1) and (1,1,1): 1/mu_bar = (1 + 1/3)/2
+    hx = o.coef(3)
+    assert hx[1, 1, 1] == pytest.approx(MM * ((1.0 + 1.0 / 3.0) / 2.0) / (MU0 * MM * MM), rel=1e-15)
+
+
+# ---------------------------------------------------------------------------
+# Brute force: ten detailed updates == dense two-level form (23)
+# ---------------------------------------------------------------------------
+
+@pytest.mark.parametrize("seed", [0, 1])
+def test_step_equals_dense_form_with_materials_and_currents(seed):
+    nx, ny, nz = 3, 3, 4
+    eps, mu, pec = wl.random_materials(nx, ny, nz, seed)
+    pec[:] = 0
+    pec[1, 1, 1] = 1
+    dx, dy, dz = 1.1 * DXY, DXY, MM
+    cdt = 0.9 * dz
+    o = Oracle(nx, ny, nz, dx, dy, dz, cdt=cdt, eps_r=eps, mu_r=mu, pec=pec)
+    d = Dense23(nx, ny, nz, _coefs(o), cdt)
+    assert d.skew_ok < 1e-9 * np.max(np.abs(d.l))
+    _random_state(o, 100 + seed)
+    rng = np.random.default_rng(200 + seed)
+    y = d.y_from_fields(o.fields())
+    for _ in range(3):
+        jz, jx, jy = (rng.standard_normal(o.shape) * 1e-3 for _ in range(3))
+        o.step_custom(jz, jx, jy)
+        y = d.step(y, d.f_vec(jz, jx, jy))
+        y_or = d.y_from_fields(o.fields())
+        assert np.max(np.abs(y_or - y)) <= 1e-12 * np.max(np.abs(y))
+
+
+def test_energy_formula_equals_dense_quadratic_form():
+    nx, ny, nz = 3, 4, 3
+    eps, mu, pec = wl.random_materials(nx, ny, nz, 5)
+    pec[:] = 0
+    o = Oracle(nx, ny, nz, DXY, 1.2 * DXY, MM, eps_r=eps, mu_r=mu, pec=pec)
+    d = Dense23(nx, ny, nz, _coefs(o), MM)
+    assert np.max(np.abs(d.qe - d.qe.T)) <= 1e-12 * np.max(np.abs(d.qe))   # Q^e = Q^e*
+    _random_state(o, 7)
+    y = d.y_from_fields(o.fields())
+    w_dense = d.energy(y)
+    assert o.energy() == pytest.approx(w_dense, rel=1e-12)
+
+
+# ---------------------------------------------------------------------------
+# Dispersion relation (27) and stability (25)
+# ---------------------------------------------------------------------------
+
+def _oracle_propagator(o, d):
+    """Columns = one oracle step applied to each unit vector of y."""
+    ny_ = d.be.shape[0]
+    g = np.empty((ny_, ny_))
+    for col in range(ny_):
+        y = np.zeros(ny_)
+        y[col] = 1.0
+        f = d.fields_from_y(y)
+        for c in range(6):
+            o.set(c, f[c].reshape(o.shape))
+        o.step_custom()
+        g[:, col] = d.y_from_fields(o.fields())
+    return g
+
+
+def _closed_form_angles(nx, ny, nz, dx, dy, dz, cdt):
+    """Eq. (27): sin^2 W / dtau^2 = sin^2 Kz/dz^2 + (sin^2 Kx/dx^2 + sin^2 Ky/dy^2)
+    (1 - dtau^2/dz^2 sin^2 Kz), K = p*pi/(2N) for the standing waves of a PEC box;
+    one step turns a mode by 2W. Multiplicity 2 if p, q, r >= 1, 1 if exactly one is 0."""
+    out = []
+    for p in range(nx):
+        for q in range(ny):
+            for r in range(nz):
+                zeros = (p == 0) + (q == 0) + (r == 0)
+                mult = {0: 2, 1: 1}.get(zeros, 0)
+                if not mult:
+                    continue
+                sx = math.sin(p * math.pi / (2 * nx)) ** 2 / dx ** 2
+                sy = math.sin(q * math.pi / (2 * ny)) ** 2 / dy ** 2
+                sz = math.sin(r * math.pi / (2 * nz)) ** 2 / dz ** 2
+                s2 = cdt ** 2 * (sz + (sx + sy) * (1.0 - cdt ** 2 * sz))
+                out += [2.0 * math.asin(math.sqrt(s2))] * mult
+    return np.sort(np.array(out))
+
+
+@pytest.mark.parametrize("dims,ratio", [((3, 4, 5), (DXY, DXY, MM)), ((4, 3, 4), (1.7 * MM, 1.5 * MM, MM))])
+def test_eigen_angles_match_dispersion_relation(dims, ratio):
+    nx, ny, nz = dims
+    dx, dy, dz = ratio
+    cdt = dz
+    assert oracle.stable(dx, dy, dz, cdt)
+    o = Oracle(nx, ny, nz, dx, dy, dz, cdt=cdt)
+    d = Dense23(nx, ny, nz, _coefs(o), cdt)
+    g = _oracle_propagator(o, d)
+    np.testing.assert_allclose(g, d.propagator(), atol=1e-12)
+    lam = np.linalg.eigvals(g)
+    assert np.max(np.abs(np.abs(lam) - 1.0)) < 1e-9
+    ang = np.angle(lam)
+    pos = np.sort(ang[ang > 1e-7])
+    expect = _closed_form_angles(nx, ny, nz, dx, dy, dz, cdt)
+    assert len(pos) == len(expect)
+    np.testing.assert_allclose(pos, expect, atol=1e-9)
+
+
+def test_cubic_mesh_at_magic_step_is_unstable():
+    """Eq. (25) is necessary (Sec. 4.5): dx = dy = dz with c*dt = dz grows."""
+    nx, ny, nz = 4, 4, 4
+    assert not oracle.stable(MM, MM, MM, MM)
+    o = Oracle(nx, ny, nz, MM, MM, MM, cdt=MM)
+    d = Dense23(nx, ny, nz, _coefs(o), MM)
+    lam = np.linalg.eigvals(_oracle_propagator(o, d))
+    assert np.max(np.abs(lam)) > 1.5
+    # and the amended mesh of the same box is not
+    o2 = Oracle(nx, ny, nz, DXY, DXY, MM, cdt=MM)
+    d2 = Dense23(nx, ny, nz, _coefs(o2), MM)
+    lam2 = np.linalg.eigvals(_oracle_propagator(o2, d2))
+    assert np.max(np.abs(lam2)) < 1.0 + 1e-9
+
+
+# ---------------------------------------------------------------------------
+# Energy law (19)
+# ---------------------------------------------------------------------------
+
+def test_energy_conserved_without_current():
+    o = Oracle(6, 5, 8, DXY, 1.1 * DXY, MM)
+    _random_state(o, 11)
+    w0 = o.energy()
+    for _ in range(20):
+        o.step(25)
+        assert o.energy() == pytest.approx(w0, rel=1e-13)
+
+
+def test_energy_law_with_current():
+    """W^{n+1} - W^n = -dt sum jj_z^n (ez^{n+1/2} + ez^{n-1/2})/2, Eq. (19)."""
+    o = Oracle(6, 6, 10, DXY, DXY, MM)
+    _random_state(o, 12)
+    rng = np.random.default_rng(13)
+    for _ in range(10):
+        w0 = o.energy()
+        ez0 = o.get("ez")
+        jz = rng.standard_normal(o.shape)
+        o.step_custom(jz)
+        ez1 = o.get("ez")
+        w1 = o.energy()
+        rhs = -o.dt * np.sum(jz * 0.5 * (ez0 + ez1) * (o.coef("ez") != 0))
+        assert w1 - w0 == pytest.approx(rhs, rel=1e-9, abs=1e-12 * abs(w0))
+
+
+# ---------------------------------------------------------------------------
+# Charge laws (34), (35) and Gauss's law for the bunch
+# ---------------------------------------------------------------------------
+
+def _interior_nodes(o):
+    """Nodes whose six incident edges are all non-PEC."""
+    ae = [o.coef(c) != 0 for c in range(3)]
+    m = np.zeros(o.shape, bool)
+    m[1:, 1:, 1:] = (ae[0][1:, 1:, 1:] & ae[0][1:, 1:, :-1] & ae[1][1:, 1:, 1:] &
+                     ae[1][1:, :-1, 1:] & ae[2][1:, 1:, 1:] & ae[2][:-1, 1:, 1:])
+    return m
+
+
+def _interior_cells(o):
+    """Cells (indexed by their lower node) whose six faces are all active."""
+    ah = [o.coef(c) != 0 for c in range(3, 6)]
+    m = np.zeros(o.shape, bool)
+    m[:-1, :-1, :-1] = (ah[0][:-1, :-1, :-1] & ah[0][:-1, :-1, 1:] & ah[1][:-1, :-1, :-1] &
+                        ah[1][:-1, 1:, :-1] & ah[2][:-1, :-1, :-1] & ah[2][1:, :-1, :-1])
+    return m
+
+
+def test_charge_laws_with_random_fields_and_currents():
+    nx, ny, nz = 5, 5, 6
+    pec = np.zeros((nz, ny, nx), np.uint8)
+    pec[2, 3, 3] = 1
+    o = Oracle(nx, ny, nz, DXY, DXY, MM, pec=pec)
+    _random_state(o, 21)
+    rng = np.random.default_rng(22)
+    jx = [rng.standard_normal(o.shape) for _ in range(3)]
+    jy = [rng.standard_normal(o.shape) for _ in range(3)]
+    jz = [rng.standard_normal(o.shape) for _ in range(3)]
+    hist = [o.fields()]
+    for n in range(3):
+        o.step_custom(jz[n], jx[n], jy[n])
+        hist.append(o.fields())
+    inode, icell = _interior_nodes(o), _interior_cells(o)
+    assert inode.sum() > 10 and icell.sum() > 10
+    # (35): qe^{n+1/2} - qe^{n-1/2} = dt (P_x^T jbar_x + P_y^T jbar_y + P_z^T jz^n)
+    for n in (1, 2):
+        qe1 = o.qbar_e(hist[n + 1]["ex"], hist[n]["ex"], hist[n + 1]["ey"], hist[n]["ey"], hist[n + 1]["ez"])
+        qe0 = o.qbar_e(hist[n]["ex"], hist[n - 1]["ex"], hist[n]["ey"], hist[n - 1]["ey"], hist[n]["ez"])
+        jbx = 0.5 * (jx[n] + jx[n - 1]) * (o.coef("ex") != 0)
+        jby = 0.5 * (jy[n] + jy[n - 1]) * (o.coef("ey") != 0)
+        jbz = jz[n] * (o.coef("ez") != 0)
+        div = np.zeros(o.shape)
+        # (P^T v)[node] = v[node - s] - v[node], written on the 3-D array
+        div += -jbx
+        div[:, :, 1:] += jbx[:, :, :-1]
+        div += -jby
+        div[:, 1:, :] += jby[:, :-1, :]
+        div += -jbz
+        div[1:, :, :] += jbz[:-1, :, :]
+        res = (qe1 - qe0) - o.dt * div
+        scale = np.max(np.abs(qe1[inode]))
+        assert np.max(np.abs(res[inode])) <= 1e-12 * scale
+    # (34): qh^n constant
+    qh = [o.qbar_h(hist[n + 1]["hx"], hist[n]["hx"], hist[n + 1]["hy"], hist[n]["hy"], hist[n]["hz"])
+          for n in range(3)]
+    scale = np.max(np.abs(qh[0][icell]))
+    for n in (1, 2):
+        assert np.max(np.abs(qh[n][icell] - qh[0][icell])) <= 1e-12 * scale
+
+
+def test_sign_of_the_r_term_in_the_charge():
+    """The printed (I + alpha^2 r_0) does not give a conserved charge; the
+    reading (I - alpha^2 r_0) does (previous test). Flip the correction and
+    the residual becomes O(1)."""
+    nx, ny, nz = 5, 5, 6
+    o = Oracle(nx, ny, nz, DXY, DXY, MM)
+    _random_state(o, 31)
+    h = [o.fields()]
+    for _ in range(2):
+        o.step_custom()
+        h.append(o.fields())
+    inode = _interior_nodes(o)
+
+    def qe_plus(n):
+        # the same charge but with the alpha^2 correction added instead of subtracted:
+        base = o.qbar_e(h[n + 1]["ex"], h[n]["ex"], h[n + 1]["ey"], h[n]["ey"], h[n + 1]["ez"])
+        ez = h[n + 1]["ez"]
+        zero = np.zeros_like(ez)
+        plain = o.qbar_e(zero, zero, zero, zero, ez)          # -P_z^T dz~ only
+        no_r = -_ptz(ez * _inv(o.coef("ez")))                 # -P_z^T M_eps ez
+        return base - 2.0 * (plain - no_r)
+
+    res_plus = qe_plus(1) - qe_plus(0)
+    scale = np.max(np.abs(qe_plus(0)[inode]))
+    assert np.max(np.abs(res_plus[inode])) > 1e-3 * scale
+
+
+def _inv(c):
+    out = np.zeros_like(c)
+    out[c != 0] = 1.0 / c[c != 0]
+    return out
+
+
+def _ptz(v):
+    out = -v.copy()
+    out[1:, :, :] += v[:-1, :, :]
+    return out
+
+
+def _node_charge_closed_form(q, sigma, dz, zc, k):
+    """Charge of the truncated Gaussian inside the dual cell [z_k - dz/2, z_k + dz/2]."""
+    a = max(k * dz - 0.5 * dz - zc, -5 * sigma)
+    b = min(k * dz + 0.5 * dz - zc, 5 * sigma)
+    if b <= a:
+        return 0.0
+    return q * 0.5 * (math.erf(b / (sigma * math.sqrt(2))) - math.erf(a / (sigma * math.sqrt(2))))
+
+
+def test_gauss_law_for_the_bunch():
+    """Cold start: qe^{n+1/2} equals the bunch charge in each node's dual cell
+    on the bunch line and vanishes at every other interior node (Eq. (35)
+    summed over the steps)."""
+    nx, ny, nz = 10, 10, 40
+    q = 1e-9
+    sigma = 2.5 * MM
+    o = Oracle(nx, ny, nz, DXY, DXY, MM)
+    o.set_bunch(sigma, q, 5, 5)
+    c0 = o.bunch_info()["c0"]
+    inode = _interior_nodes(o)
+    for n in (6, 13, 20, 29):
+        o2 = Oracle(nx, ny, nz, DXY, DXY, MM)
+        o2.set_bunch(sigma, q, 5, 5)
+        o2.step(n)
+        f0 = o2.fields()
+        o2.step(1)
+        f1 = o2.fields()
+        qe = o2.qbar_e(f1["ex"], f0["ex"], f1["ey"], f0["ey"], f1["ez"])
+        zc = (n + 0.5 - c0) * MM
+        expect = np.zeros(o.shape)
+        for k in range(nz + 1):
+            expect[k, 5, 5] = _node_charge_closed_form(q, sigma, MM, zc, k)
+        assert np.max(np.abs(qe[inode] - expect[inode])) <= 1e-12 * q
+        if n >= 13:
+            assert np.max(np.abs(expect[inode])) > 0.05 * q
+
+
+# ---------------------------------------------------------------------------
+# Zero dispersion along z (Sec. 4.5): exact one-cell shift of a TEM pulse
+# ---------------------------------------------------------------------------
+
+def _tem_potential(nx, ny, dx, dy, i0, j0):
+    """phi on the nodes of the cross-section: (dy/dx P_x^T P_x + dx/dy P_y^T P_y) phi
+    = delta(i0, j0) at interior nodes, phi = 0 on the PEC wall."""
+    idx = {}
+    for j in range(1, ny):
+        for i in range(1, nx):
+            idx[(i, j)] = len(idx)
+    a = np.zeros((len(idx), len(idx)))
+    wx, wy = dy / dx, dx / dy
+    for (i, j), r in idx.items():
+        a[r, r] = 2 * wx + 2 * wy
+        for (ii, jj), w in (((i + 1, j), wx), ((i - 1, j), wx), ((i, j + 1), wy), ((i, j - 1), wy)):
+            if (ii, jj) in idx:
+                a[r, idx[(ii, jj)]] -= w
+    b = np.zeros(len(idx))
+    b[idx[(i0, j0)]] = 1.0
+    x = np.linalg.solve(a, b)
+    phi = np.zeros((ny + 1, nx + 1))
+    for (i, j), r in idx.items():
+        phi[j, i] = x[r]
+    return phi
+
+
+def test_tem_pulse_shifts_one_cell_per_step():
+    nx, ny, nz = 6, 5, 40
+    dx, dy, dz = DXY, 1.2 * DXY, MM
+    i0, j0 = 3, 2
+    phi = _tem_potential(nx, ny, dx, dy, i0, j0)
+    pxp = np.zeros_like(phi)
+    pyp = np.zeros_like(phi)
+    pxp[:, :-1] = phi[:, 1:] - phi[:, :-1]
+    pyp[:-1, :] = phi[1:, :] - phi[:-1, :]
+    eta0 = MU0 * C_LIGHT
+    kk = np.arange(nz + 1)
+
+    def F(k):
+        k = np.asarray(k, dtype=float)
+        x = (k - 8.0) / 3.0
+        return np.where(np.abs(x) < 1.0, (1 - x * x) ** 3, 0.0)
+
+    o = Oracle(nx, ny, nz, dx, dy, dz)
+    sh = o.shape
+    f0 = F(kk)[:, None, None]
+    f1 = F(kk + 1)[:, None, None]
+    o.set("ex", -pxp[None] * f0 * np.ones(sh))
+    o.set("ey", -pyp[None] * f0 * np.ones(sh))
+    o.set("hx", (dx / dy) * pyp[None] * f1 / eta0 * np.ones(sh))
+    o.set("hy", -(dy / dx) * pxp[None] * f1 / eta0 * np.ones(sh))
+    nsteps = 20
+    for n in range(nsteps):
+        jz = np.zeros(sh)
+        jz[:nz, j0, i0] = 0.5 * (F(kk[:nz] + 1 - n) + F(kk[:nz] - n)) / eta0
+        o.step_custom(jz)
+    fN = F(kk - nsteps)[:, None, None]
+    fN1 = F(kk + 1 - nsteps)[:, None, None]
+    ex_exp = -pxp[None] * fN * (o.coef("ex") != 0)
+    ey_exp = -pyp[None] * fN * (o.coef("ey") != 0)
+    hx_exp = (dx / dy) * pyp[None] * fN1 / eta0 * (o.coef("hx") != 0)
+    hy_exp = -(dy / dx) * pxp[None] * fN1 / eta0 * (o.coef("hy") != 0)
+    escale = np.max(np.abs(ex_exp))
+    hscale = np.max(np.abs(hx_exp))
+    assert np.max(np.abs(o.get("ex") - ex_exp)) <= 1e-13 * escale
+    assert np.max(np.abs(o.get("ey") - ey_exp)) <= 1e-13 * escale
+    assert np.max(np.abs(o.get("hx") - hx_exp)) <= 1e-13 * hscale
+    assert np.max(np.abs(o.get("hy") - hy_exp)) <= 1e-13 * hscale
+    assert np.max(np.abs(o.get("ez"))) <= 1e-13 * escale
+    assert np.max(np.abs(o.get("hz"))) <= 1e-13 * hscale
+
+
+# ---------------------------------------------------------------------------
+# Bunch, causality and the wake
+# ---------------------------------------------------------------------------
+
+def test_bunch_profile_closed_form():
+    o = Oracle(8, 8, 30, DXY, DXY, MM)
+    sigma, q = 3.3 * MM, 2e-9
+    o.set_bunch(sigma, q, 4, 4)
+    info = o.bunch_info()
+    assert info["c0"] == math.ceil(5 * 3.3)
+    assert info["qcell"].sum() == pytest.approx(q * math.erf(5 / math.sqrt(2)), rel=1e-13)
+    # current of step n on edge k is c*Q_cell(k - n + c0)/dz
+    n = 7
+    jz = o.current(n)
+    c0 = info["c0"]
+    for k in range(30):
+        d = k - n + c0
+        qc = info["qcell"][d + c0] if -c0 <= d < c0 else 0.0
+        assert jz[k, 4, 4] == pytest.approx(C_LIGHT * qc / MM, rel=1e-15, abs=0)
+
+
+def test_no_field_ahead_of_the_bunch():
+    w = wl.plain_pipe(nz=60, n=10, steps=0)
+    o = Oracle(w.nx, w.ny, w.nz, w.dx, w.dy, w.dz, w.cdt)
+    o.set_bunch(w.sigma, w.charge, w.i0, w.j0)
+    for n in (10, 25, 40):
+        o.step(n - o.step_count)
+        for c in oracle.COMPONENTS:
+            f = o.get(c)
+            assert np.all(f[n + 1:] == 0.0), (c, n)
+            assert np.any(f[:n] != 0.0)
+    wk, s0, ds = o.wake()
+    info = o.bunch_info()
+    assert s0 == pytest.approx(info["m_min"] * MM)
+    # samples ahead of the head are exactly zero
+    c0 = info["c0"]
+    assert wk[0] == 0.0 and wk[1] == 0.0          # m = -c0-1 and m = -c0
+
+
+def test_loss_factor_identity():
+    """Energy law (19) summed over the whole passage: the field energy left
+    behind equals Q/2 * sum_d Q_cell(d) [W(-d) + W(-d-1)]."""
+    nx, ny, nz = 8, 8, 30
+    sigma = 2.0 * MM
+    o = Oracle(nx, ny, nz, DXY, DXY, MM)
+    q = 1e-9
+    o.set_bunch(sigma, q, 4, 4)
+    info = o.bunch_info()
+    c0 = info["c0"]
+    o.step(nz + 2 * c0 + info["m_max"])
+    wk, s0, ds = o.wake()
+    m_min = info["m_min"]
+    rhs = 0.0
+    for d in range(-c0, c0):
+        qc = info["qcell"][d + c0]
+        rhs += 0.5 * q * qc * (wk[-d - m_min] + wk[-d - 1 - m_min])
+    assert o.energy() == pytest.approx(rhs, rel=1e-12)
+    assert o.energy() > 0
+
+
+def test_wake_independent_of_charge_and_symmetric():
+    w = wl.plain_pipe(nz=40, n=8, steps=0)
+    res = []
+    for q in (1e-9, 3e-12):
+        o = Oracle(w.nx, w.ny, w.nz, w.dx, w.dy, w.dz)
+        o.set_bunch(3 * MM, q, 4, 4)
+        o.step(90)
+        res.append(o)
+    w1, w2 = res[0].wake()[0], res[1].wake()[0]
+    np.testing.assert_allclose(w1, w2, rtol=1e-12, atol=1e-12 * np.max(np.abs(w1)))
+    # square pipe, on-axis bunch: ex(i+1/2, j) = ey(j, i+1/2) (x <-> y mirror)
+    ex, ey = res[0].get("ex"), res[0].get("ey")
+    np.testing.assert_allclose(ex, np.swapaxes(ey, 1, 2), atol=1e-12 * np.max(np.abs(ex)))
+
+
+def test_as_written_cubic_config_fails_stability_check():
+    w = wl.plain_pipe_cubic()
+    assert not oracle.stable(w.dx, w.dy, w.dz, w.cdt)
+    w2 = wl.plain_pipe()
+    assert oracle.stable(w2.dx, w2.dy, w2.dz, w2.cdt)
