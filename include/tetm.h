@@ -1,0 +1,193 @@
+/*
+ * tetm.h — C ABI of libtetm.so, a GB300 (sm_103a) solver for the explicit
+ * TE/TM scheme of M. Dohlus and I. Zagorodnov, "Explicit TE/TM scheme for
+ * particle beam simulations": the two-level TE/TM-split leapfrog (Sec. 4.2,
+ * Eq. (23)) of the FIT grid-doublet fields on a Cartesian grid, with a rigid
+ * relativistic Gaussian bunch current injected each step and the longitudinal
+ * wake potential (Sec. 5) gathered along the bunch path.
+ *
+ * Conventions shared by every call
+ *  - Return value: TETM_OK (0) or a negative TETM_E_* code; no call aborts,
+ *    traps or exits. tetm_strerror() names a code.
+ *  - Handles are not thread-safe; distinct handles may be used from distinct
+ *    host threads. All device memory of a solve is allocated by tetm_create
+ *    and released by tetm_destroy (the handle owns it). Host arrays passed in
+ *    are read during the call only; host arrays passed out are written
+ *    during the call only; the caller owns both.
+ *  - Device work is queued on the solver's CUDA stream (tetm_set_stream).
+ *    Calls marked "synchronizes" wait for that stream before returning.
+ *  - Geometry: a closed box of nx*ny*nz primary cells with perfectly
+ *    conducting walls, n x E = 0 (Sec. 2, Eq. (1)). Cell (ci, cj, ck) has the
+ *    C-order index ci + nx*(cj + ny*ck) (x fastest).
+ *  - Field layout ("canonical FIT layout", Sec. 2): one float64 vector per
+ *    component with (nx+1)*(ny+1)*(nz+1) entries, entry i + (nx+1)*(j +
+ *    (ny+1)*k) attached to node (i,j,k):
+ *      ex (i+1/2,j,k)  ey (i,j+1/2,k)  ez (i,j,k+1/2)       edge voltages [V]
+ *      hx (i,j+1/2,k+1/2)  hy (i+1/2,j,k+1/2)  hz (i+1/2,j+1/2,k)  [A]
+ *    Entries on PEC edges, on faces next to PEC and outside the box are zero.
+ *  - Time: the state after n steps is y^n = (u^{n-1/2}, v^n) with
+ *    u = (hx, hy, ez) and v = (ex, ey, hz) (Sec. 4.1, Eq. (17)).
+ */
+#ifndef TETM_H
+#define TETM_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+/* ---- return codes ------------------------------------------------------ */
+#define TETM_OK 0
+#define TETM_E_ARG (-1)        /* bad argument (NULL, size, range)                 */
+#define TETM_E_UNSTABLE (-2)   /* time step outside Eq. (25)                        */
+#define TETM_E_NOT_MAGIC (-3)  /* bunch / wake need c*dt == dz (Sec. 4.5, Sec. 5)   */
+#define TETM_E_NOMEM (-4)      /* device or host allocation failed                  */
+#define TETM_E_CUDA (-5)       /* a CUDA runtime call failed                        */
+#define TETM_E_STATE (-6)      /* call not valid in the solver's current state      */
+#define TETM_E_TIMEOUT (-7)    /* a bounded device-side wait gave up                */
+#define TETM_E_DIVERGED (-8)   /* non-finite energy: the run blew up               */
+#define TETM_E_UNSUPPORTED (-9) /* combination of options this build does not offer */
+
+/* ---- field precision ---------------------------------------------------- */
+#define TETM_FP64 0            /* fields stored and updated in float64            */
+#define TETM_FP32 1            /* fields in float32; wake and balances in float64 */
+
+/* ---- update kernels ------------------------------------------------------ */
+#define TETM_KERNEL_FUSED 0     /* one z-marching launch per step (default)        */
+#define TETM_KERNEL_REFERENCE 1 /* one launch per update equation: 10 per step     */
+
+/* ---- components ---------------------------------------------------------- */
+#define TETM_EX 0
+#define TETM_EY 1
+#define TETM_EZ 2
+#define TETM_HX 3
+#define TETM_HY 4
+#define TETM_HZ 5
+
+typedef struct tetm_grid {
+  int32_t nx, ny, nz;  /* primary cells, each >= 2                          */
+  int32_t precision;   /* TETM_FP64 or TETM_FP32                             */
+  double dx, dy, dz;   /* cell sizes [m], > 0                                */
+  double cdt;          /* c*dt [m]; 0 selects dz, the step of Sec. 4.5       */
+} tetm_grid;
+
+typedef struct tetm_info {
+  int64_t step;            /* n of the current state y^n                     */
+  int64_t device_bytes;    /* device memory held by the solve                */
+  int64_t active_cells;    /* cells that carry at least one non-PEC object   */
+  int64_t processed_cells; /* cells the fused kernel reads and writes a step */
+  int32_t kernel;          /* TETM_KERNEL_*                                  */
+  int32_t precision;       /* TETM_FP64 / TETM_FP32                          */
+  int32_t tile_x, tile_y, chunk_z; /* fused-kernel block shape               */
+  int32_t work_items;      /* (tile, z-chunk) blocks launched per step       */
+  int32_t wake_len;        /* wake samples (0 before tetm_set_bunch)         */
+  int32_t uniform_material;/* 1 if every active coefficient of a component is equal */
+} tetm_info;
+
+typedef struct tetm_solver tetm_solver;
+
+/* Create a solve (Sec. 2, Eq. (4) with the staircase reading of the
+ * material matrices):
+ *   - an edge is PEC (M_eps^-1 = 0) if any of the up to four cells sharing it
+ *     is PEC or outside the box; otherwise M_eps^-1 = L / (eps0 eps_bar A~)
+ *     with eps_bar the mean eps_r of those cells;
+ *   - a face is active only if both cells sharing it are inside and not PEC;
+ *     M_mu^-1 = L~ / (mu0 mu_bar A), 1/mu_bar the mean of 1/mu_r.
+ * eps_r, mu_r: float64 per cell (>= 1), NULL = vacuum. pec: uint8 per cell,
+ * nonzero = PEC, NULL = none. All three are read during the call only.
+ * Checks Eq. (25): c*dt <= dz and c*dt <= (dx^-2 + dy^-2)^-1/2, else
+ * TETM_E_UNSTABLE. The fields start at zero (cold start, y^0 = 0).
+ * On failure *out is set to NULL. */
+int tetm_create(const tetm_grid* g, const double* eps_r, const double* mu_r, const uint8_t* pec,
+                tetm_solver** out);
+
+/* Rigid ultra-relativistic Gaussian bunch (Sec. 3 and Sec. 5): RMS length
+ * sigma_z [m] > 0, charge [C] != 0, moving at c along the z-line through
+ * node (i0, j0), 1 <= i0 <= nx-1, 1 <= j0 <= ny-1. The line density is
+ * truncated at +-5 sigma_z; at t = 0 the centre is c0 = ceil(5 sigma/dz)
+ * cells behind the wall z = 0. Edge (i0, j0, k+1/2) carries
+ * jj_z^n = c * Q_cell(k - n + c0) / dz, Q_cell(d) the charge in
+ * [d dz, (d+1) dz] of the bunch frame. Needs c*dt == dz (TETM_E_NOT_MAGIC)
+ * and must precede the first step (TETM_E_STATE). Defines the wake window
+ * s_m = m dz, m = -c0-1 .. ceil(15 sigma/dz). */
+int tetm_set_bunch(tetm_solver* s, double sigma_z, double charge, int32_t i0, int32_t j0);
+
+/* Advance n >= 0 steps of Eq. (23): per step the ten updates of Sec. 4.2
+ * (TM stage hx, hy, ez, hx, hy; TE stage ex, ey, hz, ex, ey), the bunch
+ * current in the ez update and one wake sample per window point. Queued on
+ * the solver's stream; returns once the launches are queued. */
+int tetm_step(tetm_solver* s, int32_t n);
+
+/* Wait for the solver's stream (synchronizes). */
+int tetm_sync(tetm_solver* s);
+
+/* Longitudinal wake W(s_m) [V/C], W(s) = -(1/Q) * integral of E_z along the
+ * test-charge path t = (z + s)/c (Sec. 5), exact on the grid at c*dt = dz,
+ * accumulated in float64. Copies n = window length values into out[cap]
+ * (cap >= n, else TETM_E_ARG; out may be NULL to query n). *s0 = s of the
+ * first sample, *ds = dz. Any output pointer may be NULL. Synchronizes. */
+int tetm_wake(tetm_solver* s, double* out, int32_t cap, int32_t* n_out, double* s0, double* ds);
+
+/* Release the solve and all its device memory. NULL-safe. */
+void tetm_destroy(tetm_solver* s);
+
+/* Discrete energy of the explicit scheme, W^{n,e} = 1/2 <Q^e y^n, y^n>
+ * with Q^e = B^e - alpha A (Sec. 4.4), in J, summed in float64 on the
+ * device in a fixed order. TETM_E_DIVERGED if not finite. Synchronizes. */
+int tetm_energy(tetm_solver* s, double* w);
+
+/* Charge balances of the last step (Sec. 4.5), float64 on the device, over
+ * nodes (cells) whose six edges (faces) are all active:
+ *   *max_e = max |qbar_e^{n+1/2} - q_bunch^{n+1/2}|, Eq. (35) summed from a
+ *            cold start; q_bunch is the truncated Gaussian charge inside the
+ *            node's dual cell on the bunch line, 0 elsewhere;
+ *   *max_h = max |qbar_h^{n-1/2}|, Eq. (34) from a cold start;
+ *   *q_scale = max |q_bunch| (0 without a bunch) for relative residuals.
+ * Needs at least one step since creation or the last tetm_set_fields
+ * (TETM_E_STATE). Valid for cold starts. Synchronizes. */
+int tetm_charge_residual(tetm_solver* s, double* max_e, double* max_h, double* q_scale);
+
+/* Copy one component (TETM_EX..TETM_HZ) of the current state to / from a
+ * host float64 array in the canonical FIT layout. Values on entries that
+ * carry no field are ignored on input and zero on output. Both synchronize. */
+int tetm_get_fields(tetm_solver* s, int32_t comp, double* host);
+int tetm_set_fields(tetm_solver* s, int32_t comp, const double* host);
+
+/* Use this CUDA stream (a cudaStream_t, NULL = legacy default stream) for
+ * all later device work of the solve. The stream is not owned. */
+int tetm_set_stream(tetm_solver* s, void* cuda_stream);
+
+/* Select the update kernels (TETM_KERNEL_*). The fused kernel needs every
+ * active coefficient of a component to be equal (vacuum or one material
+ * plus PEC); otherwise TETM_E_UNSUPPORTED. */
+int tetm_set_kernel(tetm_solver* s, int32_t kernel);
+
+/* Fused-kernel block shape: transverse tile tile_x x tile_y (tile_x in
+ * {32, 64}, tile_y in {4, 8, 16}) and z-chunk length chunk_z >= 4. Any
+ * value 0 keeps the current one. TETM_E_ARG for other values. */
+int tetm_set_tiling(tetm_solver* s, int32_t tile_x, int32_t tile_y, int32_t chunk_z);
+
+/* Snapshot of the solve's bookkeeping. */
+int tetm_get_info(tetm_solver* s, tetm_info* info);
+
+/* Device bytes tetm_create would allocate for this grid (0 on a bad grid),
+ * for admission control by a caller that budgets device memory. */
+int64_t tetm_bytes_needed(const tetm_grid* g);
+
+/* Save the complete state (fields, step counter, wake accumulators) into a
+ * caller buffer of cap bytes; *used receives the size (buf may be NULL to
+ * query it). tetm_load restores it into a solve created with the same grid
+ * and geometry (TETM_E_ARG on a size or grid mismatch). Both synchronize. */
+int tetm_save(tetm_solver* s, void* buf, size_t cap, size_t* used);
+int tetm_load(tetm_solver* s, const void* buf, size_t size);
+
+/* Static description of a return code. */
+const char* tetm_strerror(int code);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* TETM_H */

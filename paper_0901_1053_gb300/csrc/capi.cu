@@ -1,0 +1,857 @@
+// C ABI of libtetm (include/tetm.h): solve lifetime, geometry, bunch,
+// stepping, wake, diagnostics and checkpoints. Host logic only; the update
+// and reduction kernels live in kernels_step.cu and kernels_diag.cu.
+#include <math.h>
+#include <stdio.h>
+#include <stdlib.h>
+#include <string.h>
+
+#include <algorithm>
+#include <new>
+#include <vector>
+
+#include "tetm_internal.h"
+
+using namespace tetm;
+
+namespace tetm {
+
+Layout make_layout(int nx, int ny, int nz, int elem_bytes) {
+  Layout L;
+  L.nx = nx;
+  L.ny = ny;
+  L.nz = nz;
+  L.ox = 16 / elem_bytes;                          // i = 0 on a 16-byte boundary, >= 2 guards
+  const int align = 32 / elem_bytes;               // rows on 32-byte sectors
+  long long px = L.ox + nx + 2;
+  px = (px + align - 1) / align * align;
+  L.px = px;
+  L.sz = (long long)(ny + 4) * px;
+  L.count = (long long)(nz + 3) * L.sz;            // planes -1 .. nz+1
+  return L;
+}
+
+}  // namespace tetm
+
+namespace {
+
+// ---------------------------------------------------------------------------
+// Geometry on the device (staircase reading of the material matrices)
+// ---------------------------------------------------------------------------
+struct GeomIn {
+  const uint8_t* pec;    // per cell or nullptr
+  const double* eps;     // per cell or nullptr
+  const double* mu;      // per cell or nullptr
+  int nx, ny, nz;
+  double dx, dy, dz;
+};
+
+__device__ __forceinline__ bool gpec(const GeomIn& g, long ci, long cj, long ck) {
+  if (ci < 0 || cj < 0 || ck < 0 || ci >= g.nx || cj >= g.ny || ck >= g.nz) return true;
+  return g.pec ? g.pec[ci + (long)g.nx * (cj + (long)g.ny * ck)] != 0 : false;
+}
+__device__ __forceinline__ double gval(const double* a, const GeomIn& g, long ci, long cj, long ck) {
+  return a ? a[ci + (long)g.nx * (cj + (long)g.ny * ck)] : 1.0;
+}
+
+// Edge along `axis` at node (i,j,k): the four cells around it.
+__device__ double edge_minv(const GeomIn& g, int axis, long i, long j, long k) {
+  long c[4][3];
+  double len, area;
+  if (axis == 0) {
+    long t[4][3] = {{i, j - 1, k - 1}, {i, j, k - 1}, {i, j - 1, k}, {i, j, k}};
+    memcpy(c, t, sizeof(c)); len = g.dx; area = g.dy * g.dz;
+  } else if (axis == 1) {
+    long t[4][3] = {{i - 1, j, k - 1}, {i, j, k - 1}, {i - 1, j, k}, {i, j, k}};
+    memcpy(c, t, sizeof(c)); len = g.dy; area = g.dx * g.dz;
+  } else {
+    long t[4][3] = {{i - 1, j - 1, k}, {i, j - 1, k}, {i - 1, j, k}, {i, j, k}};
+    memcpy(c, t, sizeof(c)); len = g.dz; area = g.dx * g.dy;
+  }
+  double e = 0.0;
+  for (int q = 0; q < 4; ++q) {
+    if (gpec(g, c[q][0], c[q][1], c[q][2])) return 0.0;
+    e += gval(g.eps, g, c[q][0], c[q][1], c[q][2]);
+  }
+  return len / (kEps0 * 0.25 * e * area);
+}
+
+// Face normal to `axis` at node (i,j,k): the two cells sharing it.
+__device__ double face_minv(const GeomIn& g, int axis, long i, long j, long k) {
+  long c[2][3];
+  double len, area;
+  if (axis == 0) {
+    long t[2][3] = {{i - 1, j, k}, {i, j, k}};
+    memcpy(c, t, sizeof(c)); len = g.dx; area = g.dy * g.dz;
+  } else if (axis == 1) {
+    long t[2][3] = {{i, j - 1, k}, {i, j, k}};
+    memcpy(c, t, sizeof(c)); len = g.dy; area = g.dx * g.dz;
+  } else {
+    long t[2][3] = {{i, j, k - 1}, {i, j, k}};
+    memcpy(c, t, sizeof(c)); len = g.dz; area = g.dx * g.dy;
+  }
+  double r = 0.0;
+  for (int q = 0; q < 2; ++q) {
+    if (gpec(g, c[q][0], c[q][1], c[q][2])) return 0.0;
+    r += 1.0 / gval(g.mu, g, c[q][0], c[q][1], c[q][2]);
+  }
+  return len * 0.5 * r / (kMu0 * area);
+}
+
+struct MinvOut {
+  double* a[6];  // per-entry M^-1 arrays (material runs) or nullptr
+};
+
+__global__ void build_geometry(GeomIn g, Layout L, uint8_t* mask, MinvOut mo) {
+  const long long total = (long long)(g.nx + 1) * (g.ny + 1) * (g.nz + 1);
+  const long long q = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (q >= total) return;
+  const int i = (int)(q % (g.nx + 1));
+  const int j = (int)((q / (g.nx + 1)) % (g.ny + 1));
+  const int k = (int)(q / ((long long)(g.nx + 1) * (g.ny + 1)));
+  const long long id = L.idx(i, j, k);
+  double v[6] = {0, 0, 0, 0, 0, 0};
+  if (i < g.nx) v[kEX] = edge_minv(g, 0, i, j, k);
+  if (j < g.ny) v[kEY] = edge_minv(g, 1, i, j, k);
+  if (k < g.nz) v[kEZ] = edge_minv(g, 2, i, j, k);
+  if (j < g.ny && k < g.nz) v[kHX] = face_minv(g, 0, i, j, k);
+  if (i < g.nx && k < g.nz) v[kHY] = face_minv(g, 1, i, j, k);
+  if (i < g.nx && j < g.ny) v[kHZ] = face_minv(g, 2, i, j, k);
+  uint8_t m = 0;
+  for (int c = 0; c < 6; ++c) {
+    if (v[c] != 0.0) m |= (uint8_t)(1u << c);
+    if (mo.a[c]) mo.a[c][id] = v[c];
+  }
+  mask[id] = m;
+}
+
+template <typename T>
+__global__ void scale_coef(const double* minv, double s, long long n, T* out) {
+  const long long q = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (q < n) out[q] = (T)(s * minv[q]);
+}
+
+// Canonical FIT layout <-> device layout, for planes [k0, k0 + nk).
+template <typename T>
+__global__ void to_canonical(const T* src, Layout L, int k0, int nk, double* dst) {
+  const long long total = (long long)(L.nx + 1) * (L.ny + 1) * nk;
+  const long long q = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (q >= total) return;
+  const int i = (int)(q % (L.nx + 1));
+  const int j = (int)((q / (L.nx + 1)) % (L.ny + 1));
+  const int k = k0 + (int)(q / ((long long)(L.nx + 1) * (L.ny + 1)));
+  dst[q] = (double)src[L.idx(i, j, k)];
+}
+template <typename T>
+__global__ void from_canonical(const double* src, Layout L, int k0, int nk, const uint8_t* mask,
+                               int comp, T* dst) {
+  const long long total = (long long)(L.nx + 1) * (L.ny + 1) * nk;
+  const long long q = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (q >= total) return;
+  const int i = (int)(q % (L.nx + 1));
+  const int j = (int)((q / (L.nx + 1)) % (L.ny + 1));
+  const int k = k0 + (int)(q / ((long long)(L.nx + 1) * (L.ny + 1)));
+  const long long id = L.idx(i, j, k);
+  dst[id] = ((mask[id] >> comp) & 1) ? (T)src[q] : T(0);
+}
+
+// One flag per fused work item (tile, z-chunk): 1 if any own cell carries a field.
+__global__ void item_flags(const uint8_t* mask, Layout L, int tx, int ty, int cz, int tiles_x,
+                           int tiles_y, int n_items, int* flags) {
+  const int item = blockIdx.x;
+  if (item >= n_items) return;
+  const int ntile = tiles_x * tiles_y;
+  const int tile = item % ntile, chunk = item / ntile;
+  const int i0 = (tile % tiles_x) * tx, j0 = (tile / tiles_x) * ty, k0 = chunk * cz;
+  int any = 0;
+  const int cells = tx * ty * cz;
+  for (int q = threadIdx.x; q < cells && !any; q += blockDim.x) {
+    const int i = i0 + q % tx, j = j0 + (q / tx) % ty, k = k0 + q / (tx * ty);
+    if (i < L.nx && j < L.ny && k < L.nz && mask[L.idx(i, j, k)] != 0) any = 1;
+  }
+  any = __syncthreads_or(any);
+  if (threadIdx.x == 0) flags[item] = any;
+}
+
+__global__ void count_active(const uint8_t* mask, Layout L, unsigned long long* out) {
+  const long long total = (long long)L.nx * L.ny * L.nz;
+  unsigned long long c = 0;
+  for (long long q = (long long)blockIdx.x * blockDim.x + threadIdx.x; q < total;
+       q += (long long)gridDim.x * blockDim.x) {
+    const int i = (int)(q % L.nx), j = (int)((q / L.nx) % L.ny), k = (int)(q / ((long long)L.nx * L.ny));
+    c += mask[L.idx(i, j, k)] != 0;
+  }
+  for (int o = 16; o > 0; o >>= 1) c += __shfl_down_sync(0xffffffffu, c, o);
+  if ((threadIdx.x & 31) == 0) atomicAdd(out, c);
+}
+
+double phi(double x) { return 0.5 * erfc(-x / sqrt(2.0)); }
+
+}  // namespace
+
+struct tetm_solver {
+  tetm_grid g;
+  size_t esz;
+  Layout L;
+  void* set[2][6];
+  int cur;
+  uint8_t* mask;
+  double minv_c[6];
+  double* minv_a[6];
+  void* ua[6];
+  bool uniform;
+  double alpha;   // dt/2
+  cudaStream_t stream;
+  int kernel;
+  int tile_x, tile_y, chunk_z;
+  int tiles_x, tiles_y, n_chunks;
+  int* work;
+  int n_work;
+  bool work_dirty;
+  // bunch
+  bool bunch;
+  int i0, j0, c0, m_min, m_max;
+  double sigma, q;
+  std::vector<double> qcell;
+  void* J;
+  double* W;
+  double* qline;
+  // state
+  long long step;
+  bool prev_valid;
+  DiagScratch diag;
+  double* staging;
+  long long staging_elems;
+  long long device_bytes;
+  long long active_cells;
+};
+
+namespace {
+
+int cuda_fail(cudaError_t e) {
+  if (e == cudaErrorMemoryAllocation) return TETM_E_NOMEM;
+  return TETM_E_CUDA;
+}
+#define CK(call)                                  \
+  do {                                            \
+    cudaError_t e_ = (call);                      \
+    if (e_ != cudaSuccess) return cuda_fail(e_);  \
+  } while (0)
+
+int dalloc(tetm_solver* s, void** p, size_t bytes) {
+  cudaError_t e = cudaMalloc(p, bytes);
+  if (e != cudaSuccess) {
+    *p = nullptr;
+    cudaGetLastError();
+    return cuda_fail(e);
+  }
+  s->device_bytes += (long long)bytes;
+  return TETM_OK;
+}
+
+bool grid_ok(const tetm_grid* g) {
+  return g && g->nx >= 2 && g->ny >= 2 && g->nz >= 2 && g->dx > 0 && g->dy > 0 && g->dz > 0 &&
+         g->cdt >= 0 && (g->precision == TETM_FP64 || g->precision == TETM_FP32) &&
+         isfinite(g->dx) && isfinite(g->dy) && isfinite(g->dz) && isfinite(g->cdt) &&
+         (long long)g->nx * g->ny < (1LL << 31) && (long long)(g->nx + 1) * (g->ny + 1) * (g->nz + 1) < (1LL << 40);
+}
+
+double cdt_of(const tetm_grid* g) { return g->cdt > 0 ? g->cdt : g->dz; }
+
+int rebuild_work(tetm_solver* s) {
+  const Layout& L = s->L;
+  s->tiles_x = (L.nx + s->tile_x - 1) / s->tile_x;
+  s->tiles_y = (L.ny + s->tile_y - 1) / s->tile_y;
+  s->n_chunks = (L.nz + s->chunk_z - 1) / s->chunk_z;
+  const long long items = (long long)s->tiles_x * s->tiles_y * s->n_chunks;
+  if (items >= (1LL << 31)) return TETM_E_ARG;
+  if (s->work) {
+    cudaFree(s->work);
+    s->device_bytes -= s->n_work > 0 ? 0 : 0;
+    s->work = nullptr;
+  }
+  int* flags = nullptr;
+  CK(cudaMalloc(&flags, sizeof(int) * (size_t)items));
+  item_flags<<<(unsigned)items, 256, 0, s->stream>>>(s->mask, L, s->tile_x, s->tile_y, s->chunk_z,
+                                                     s->tiles_x, s->tiles_y, (int)items, flags);
+  std::vector<int> h((size_t)items);
+  cudaError_t e = cudaGetLastError();
+  if (e == cudaSuccess) e = cudaMemcpyAsync(h.data(), flags, sizeof(int) * (size_t)items,
+                                            cudaMemcpyDeviceToHost, s->stream);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(s->stream);
+  cudaFree(flags);
+  if (e != cudaSuccess) return cuda_fail(e);
+  std::vector<int> list;
+  list.reserve((size_t)items);
+  for (long long q = 0; q < items; ++q)
+    if (h[(size_t)q]) list.push_back((int)q);
+  s->n_work = (int)list.size();
+  if (!list.empty()) {
+    CK(cudaMalloc(&s->work, sizeof(int) * list.size()));
+    CK(cudaMemcpyAsync(s->work, list.data(), sizeof(int) * list.size(), cudaMemcpyHostToDevice,
+                       s->stream));
+    CK(cudaStreamSynchronize(s->stream));
+  }
+  s->work_dirty = false;
+  return TETM_OK;
+}
+
+template <typename T>
+StepArgs<T> step_args(tetm_solver* s, bool fused) {
+  StepArgs<T> a;
+  for (int c = 0; c < 6; ++c) {
+    a.in[c] = (const T*)s->set[s->cur][c];
+    a.out[c] = fused ? (T*)s->set[1 - s->cur][c] : (T*)s->set[s->cur][c];
+    a.co.u[c] = (T)(((c == kEZ || c == kHZ) ? 2.0 * s->alpha : s->alpha) * s->minv_c[c]);
+    a.co.ua[c] = (const T*)s->ua[c];
+  }
+  a.co.mask = s->mask;
+  a.L = s->L;
+  a.n = s->step;
+  a.b.on = s->bunch ? 1 : 0;
+  a.b.i0 = s->i0;
+  a.b.j0 = s->j0;
+  a.b.c0 = s->c0;
+  a.b.m_min = s->m_min;
+  a.b.m_max = s->m_max;
+  a.b.inv_q = s->bunch ? 1.0 / s->q : 0.0;
+  a.b.J = (const T*)s->J;
+  a.b.W = s->W;
+  a.tiles_x = s->tiles_x;
+  a.tiles_y = s->tiles_y;
+  a.chunk_z = s->chunk_z;
+  a.n_chunks = s->n_chunks;
+  a.work = s->work;
+  a.n_work = s->n_work;
+  return a;
+}
+
+template <typename T>
+int do_steps(tetm_solver* s, int n) {
+  for (int q = 0; q < n; ++q) {
+    if (s->kernel == TETM_KERNEL_FUSED) {
+      StepArgs<T> a = step_args<T>(s, true);
+      if (s->n_work > 0) CK(launch_fused_step<T>(a, s->tile_x, s->tile_y, s->stream));
+      s->cur = 1 - s->cur;
+    } else {
+      if (q == n - 1) {  // keep y^n beside y^{n+1} for the charge balance
+        for (int c = 0; c < 6; ++c)
+          CK(cudaMemcpyAsync(s->set[1 - s->cur][c], s->set[s->cur][c], (size_t)s->L.count * s->esz,
+                             cudaMemcpyDeviceToDevice, s->stream));
+      }
+      StepArgs<T> a = step_args<T>(s, false);
+      CK(launch_reference_step<T>(a, s->stream));
+    }
+    s->step += 1;
+  }
+  if (n > 0) s->prev_valid = true;
+  return TETM_OK;
+}
+
+int ensure_staging(tetm_solver* s) {
+  if (s->staging) return TETM_OK;
+  const long long plane = (long long)(s->L.nx + 1) * (s->L.ny + 1);
+  long long nk = std::max(1LL, std::min((long long)s->L.nz + 1, (16LL << 20) / plane));
+  s->staging_elems = nk * plane;
+  return dalloc(s, (void**)&s->staging, sizeof(double) * (size_t)s->staging_elems);
+}
+
+template <typename T>
+int get_fields_t(tetm_solver* s, int comp, double* host) {
+  const long long plane = (long long)(s->L.nx + 1) * (s->L.ny + 1);
+  const int nk_max = (int)(s->staging_elems / plane);
+  for (int k0 = 0; k0 <= s->L.nz; k0 += nk_max) {
+    const int nk = std::min(nk_max, s->L.nz + 1 - k0);
+    const long long n = plane * nk;
+    to_canonical<T><<<(unsigned)((n + 255) / 256), 256, 0, s->stream>>>(
+        (const T*)s->set[s->cur][comp], s->L, k0, nk, s->staging);
+    CK(cudaGetLastError());
+    CK(cudaMemcpyAsync(host + plane * k0, s->staging, sizeof(double) * (size_t)n,
+                       cudaMemcpyDeviceToHost, s->stream));
+    CK(cudaStreamSynchronize(s->stream));
+  }
+  return TETM_OK;
+}
+
+template <typename T>
+int set_fields_t(tetm_solver* s, int comp, const double* host) {
+  const long long plane = (long long)(s->L.nx + 1) * (s->L.ny + 1);
+  const int nk_max = (int)(s->staging_elems / plane);
+  for (int k0 = 0; k0 <= s->L.nz; k0 += nk_max) {
+    const int nk = std::min(nk_max, s->L.nz + 1 - k0);
+    const long long n = plane * nk;
+    CK(cudaMemcpyAsync(s->staging, host + plane * k0, sizeof(double) * (size_t)n,
+                       cudaMemcpyHostToDevice, s->stream));
+    from_canonical<T><<<(unsigned)((n + 255) / 256), 256, 0, s->stream>>>(
+        s->staging, s->L, k0, nk, s->mask, comp, (T*)s->set[s->cur][comp]);
+    CK(cudaGetLastError());
+    CK(cudaStreamSynchronize(s->stream));
+  }
+  return TETM_OK;
+}
+
+void free_all(tetm_solver* s) {
+  for (int b = 0; b < 2; ++b)
+    for (int c = 0; c < 6; ++c) cudaFree(s->set[b][c]);
+  for (int c = 0; c < 6; ++c) {
+    cudaFree(s->minv_a[c]);
+    cudaFree(s->ua[c]);
+  }
+  cudaFree(s->mask);
+  cudaFree(s->work);
+  cudaFree(s->J);
+  cudaFree(s->W);
+  cudaFree(s->qline);
+  cudaFree(s->diag.part);
+  cudaFree(s->diag.out);
+  cudaFree(s->staging);
+}
+
+}  // namespace
+
+extern "C" {
+
+const char* tetm_strerror(int code) {
+  switch (code) {
+    case TETM_OK: return "ok";
+    case TETM_E_ARG: return "bad argument";
+    case TETM_E_UNSTABLE: return "time step violates the stability bound of Eq. (25)";
+    case TETM_E_NOT_MAGIC: return "bunch and wake need c*dt == dz";
+    case TETM_E_NOMEM: return "out of memory";
+    case TETM_E_CUDA: return "CUDA runtime error";
+    case TETM_E_STATE: return "call not valid in the current solver state";
+    case TETM_E_TIMEOUT: return "bounded device wait timed out";
+    case TETM_E_DIVERGED: return "energy is not finite: the run diverged";
+    case TETM_E_UNSUPPORTED: return "unsupported option combination";
+    default: return "unknown error";
+  }
+}
+
+int64_t tetm_bytes_needed(const tetm_grid* g) {
+  if (!grid_ok(g)) return 0;
+  const size_t esz = g->precision == TETM_FP64 ? 8 : 4;
+  const Layout L = make_layout(g->nx, g->ny, g->nz, (int)esz);
+  return (int64_t)(12 * esz + 1) * L.count + (int64_t)(1 << 20);
+}
+
+int tetm_create(const tetm_grid* g, const double* eps_r, const double* mu_r, const uint8_t* pec,
+                tetm_solver** out) {
+  if (!out) return TETM_E_ARG;
+  *out = nullptr;
+  if (!grid_ok(g)) return TETM_E_ARG;
+  const double cdt = cdt_of(g);
+  const double lim_t = 1.0 / sqrt(1.0 / (g->dx * g->dx) + 1.0 / (g->dy * g->dy));
+  if (cdt > g->dz * (1.0 + 1e-12) || cdt > lim_t * (1.0 + 1e-12)) return TETM_E_UNSTABLE;
+  const long long ncell = (long long)g->nx * g->ny * g->nz;
+  // materials: physical (>= 1) and finite; uniform if every cell has the same value
+  bool uniform = true;
+  double eps_u = 1.0, mu_u = 1.0;
+  for (int w = 0; w < 2; ++w) {
+    const double* a = w == 0 ? eps_r : mu_r;
+    if (!a) continue;
+    for (long long q = 0; q < ncell; ++q)
+      if (!(a[q] >= 1.0) || !isfinite(a[q])) return TETM_E_ARG;
+    for (long long q = 1; q < ncell; ++q)
+      if (a[q] != a[0]) { uniform = false; break; }
+    (w == 0 ? eps_u : mu_u) = a[0];
+  }
+  int dev_count = 0;
+  if (cudaGetDeviceCount(&dev_count) != cudaSuccess || dev_count < 1) {
+    cudaGetLastError();
+    return TETM_E_CUDA;
+  }
+  tetm_solver* s = new (std::nothrow) tetm_solver();
+  if (!s) return TETM_E_NOMEM;
+  s->g = *g;
+  s->g.cdt = cdt;
+  s->esz = g->precision == TETM_FP64 ? 8 : 4;
+  s->L = make_layout(g->nx, g->ny, g->nz, (int)s->esz);
+  s->alpha = 0.5 * cdt / kC;
+  s->stream = nullptr;
+  s->kernel = uniform ? TETM_KERNEL_FUSED : TETM_KERNEL_REFERENCE;
+  s->uniform = uniform;
+  s->tile_x = 32;
+  s->tile_y = 8;
+  s->chunk_z = 64;
+  int rc = TETM_OK;
+  const size_t fbytes = (size_t)s->L.count * s->esz;
+  for (int b = 0; b < 2 && rc == TETM_OK; ++b)
+    for (int c = 0; c < 6 && rc == TETM_OK; ++c) {
+      rc = dalloc(s, &s->set[b][c], fbytes);
+      if (rc == TETM_OK) rc = cudaMemsetAsync(s->set[b][c], 0, fbytes, s->stream) == cudaSuccess ? TETM_OK : TETM_E_CUDA;
+    }
+  if (rc == TETM_OK) rc = dalloc(s, (void**)&s->mask, (size_t)s->L.count);
+  if (rc == TETM_OK) rc = cudaMemsetAsync(s->mask, 0, (size_t)s->L.count, s->stream) == cudaSuccess ? TETM_OK : TETM_E_CUDA;
+  if (rc == TETM_OK) rc = dalloc(s, (void**)&s->diag.part, sizeof(double) * 2048);
+  if (rc == TETM_OK) rc = dalloc(s, (void**)&s->diag.out, sizeof(double) * 8);
+  s->diag.cap = 2048;
+  MinvOut mo;
+  for (int c = 0; c < 6; ++c) mo.a[c] = nullptr;
+  if (rc == TETM_OK && !uniform) {
+    for (int c = 0; c < 6 && rc == TETM_OK; ++c) {
+      rc = dalloc(s, (void**)&s->minv_a[c], sizeof(double) * (size_t)s->L.count);
+      if (rc == TETM_OK) rc = cudaMemsetAsync(s->minv_a[c], 0, sizeof(double) * (size_t)s->L.count, s->stream) == cudaSuccess ? TETM_OK : TETM_E_CUDA;
+      mo.a[c] = s->minv_a[c];
+    }
+  }
+  // upload the cell arrays, build the mask (and M^-1 arrays) on the device
+  GeomIn gi;
+  gi.pec = nullptr;
+  gi.eps = nullptr;
+  gi.mu = nullptr;
+  gi.nx = g->nx; gi.ny = g->ny; gi.nz = g->nz;
+  gi.dx = g->dx; gi.dy = g->dy; gi.dz = g->dz;
+  uint8_t* dpec = nullptr;
+  double *deps = nullptr, *dmu = nullptr;
+  if (rc == TETM_OK && pec) {
+    if (cudaMalloc(&dpec, (size_t)ncell) != cudaSuccess ||
+        cudaMemcpyAsync(dpec, pec, (size_t)ncell, cudaMemcpyHostToDevice, s->stream) != cudaSuccess)
+      rc = TETM_E_CUDA;
+    gi.pec = dpec;
+  }
+  if (rc == TETM_OK && !uniform) {
+    for (int w = 0; w < 2 && rc == TETM_OK; ++w) {
+      const double* a = w == 0 ? eps_r : mu_r;
+      if (!a) continue;
+      double** d = w == 0 ? &deps : &dmu;
+      if (cudaMalloc(d, sizeof(double) * (size_t)ncell) != cudaSuccess ||
+          cudaMemcpyAsync(*d, a, sizeof(double) * (size_t)ncell, cudaMemcpyHostToDevice, s->stream) != cudaSuccess)
+        rc = TETM_E_CUDA;
+    }
+    gi.eps = deps;
+    gi.mu = dmu;
+  }
+  if (rc == TETM_OK) {
+    const long long total = (long long)(g->nx + 1) * (g->ny + 1) * (g->nz + 1);
+    build_geometry<<<(unsigned)((total + 255) / 256), 256, 0, s->stream>>>(gi, s->L, s->mask, mo);
+    if (cudaGetLastError() != cudaSuccess || cudaStreamSynchronize(s->stream) != cudaSuccess) rc = TETM_E_CUDA;
+  }
+  cudaFree(dpec);
+  cudaFree(deps);
+  cudaFree(dmu);
+  // per-component constants for the uniform case (vacuum or one material)
+  const double dx = g->dx, dy = g->dy, dz = g->dz;
+  s->minv_c[kEX] = dx / (kEps0 * eps_u * dy * dz);
+  s->minv_c[kEY] = dy / (kEps0 * eps_u * dx * dz);
+  s->minv_c[kEZ] = dz / (kEps0 * eps_u * dx * dy);
+  s->minv_c[kHX] = dx / (kMu0 * mu_u * dy * dz);
+  s->minv_c[kHY] = dy / (kMu0 * mu_u * dx * dz);
+  s->minv_c[kHZ] = dz / (kMu0 * mu_u * dx * dy);
+  if (rc == TETM_OK && !uniform) {
+    for (int c = 0; c < 6 && rc == TETM_OK; ++c) {
+      rc = dalloc(s, &s->ua[c], (size_t)s->L.count * s->esz);
+      if (rc != TETM_OK) break;
+      const double sc = (c == kEZ || c == kHZ) ? 2.0 * s->alpha : s->alpha;
+      const unsigned nb = (unsigned)((s->L.count + 255) / 256);
+      if (s->esz == 8)
+        scale_coef<double><<<nb, 256, 0, s->stream>>>(s->minv_a[c], sc, s->L.count, (double*)s->ua[c]);
+      else
+        scale_coef<float><<<nb, 256, 0, s->stream>>>(s->minv_a[c], sc, s->L.count, (float*)s->ua[c]);
+      if (cudaGetLastError() != cudaSuccess) rc = TETM_E_CUDA;
+    }
+  }
+  if (rc == TETM_OK) {
+    unsigned long long* cnt = nullptr;
+    unsigned long long h = 0;
+    if (cudaMalloc(&cnt, sizeof(*cnt)) != cudaSuccess) rc = TETM_E_CUDA;
+    if (rc == TETM_OK) {
+      cudaMemsetAsync(cnt, 0, sizeof(*cnt), s->stream);
+      count_active<<<256, 256, 0, s->stream>>>(s->mask, s->L, cnt);
+      if (cudaMemcpyAsync(&h, cnt, sizeof(h), cudaMemcpyDeviceToHost, s->stream) != cudaSuccess ||
+          cudaStreamSynchronize(s->stream) != cudaSuccess)
+        rc = TETM_E_CUDA;
+      cudaFree(cnt);
+    }
+    s->active_cells = (long long)h;
+  }
+  if (rc == TETM_OK) rc = rebuild_work(s);
+  if (rc != TETM_OK) {
+    free_all(s);
+    delete s;
+    cudaGetLastError();
+    return rc;
+  }
+  *out = s;
+  return TETM_OK;
+}
+
+void tetm_destroy(tetm_solver* s) {
+  if (!s) return;
+  if (s->stream) cudaStreamSynchronize(s->stream); else cudaDeviceSynchronize();
+  free_all(s);
+  delete s;
+}
+
+int tetm_set_stream(tetm_solver* s, void* st) {
+  if (!s) return TETM_E_ARG;
+  s->stream = (cudaStream_t)st;
+  return TETM_OK;
+}
+
+int tetm_set_kernel(tetm_solver* s, int32_t kernel) {
+  if (!s || (kernel != TETM_KERNEL_FUSED && kernel != TETM_KERNEL_REFERENCE)) return TETM_E_ARG;
+  if (kernel == TETM_KERNEL_FUSED && !s->uniform) return TETM_E_UNSUPPORTED;
+  s->kernel = kernel;
+  return TETM_OK;
+}
+
+int tetm_set_tiling(tetm_solver* s, int32_t tile_x, int32_t tile_y, int32_t chunk_z) {
+  if (!s) return TETM_E_ARG;
+  const int tx = tile_x ? tile_x : s->tile_x;
+  const int ty = tile_y ? tile_y : s->tile_y;
+  const int cz = chunk_z ? chunk_z : s->chunk_z;
+  if (!fused_shape_ok(tx, ty) || cz < 4) return TETM_E_ARG;
+  if (tx == s->tile_x && ty == s->tile_y && cz == s->chunk_z && s->work) return TETM_OK;
+  s->tile_x = tx;
+  s->tile_y = ty;
+  s->chunk_z = cz;
+  return rebuild_work(s);
+}
+
+int tetm_set_bunch(tetm_solver* s, double sigma_z, double charge, int32_t i0, int32_t j0) {
+  if (!s || !(sigma_z > 0) || !isfinite(sigma_z) || charge == 0 || !isfinite(charge)) return TETM_E_ARG;
+  if (i0 < 1 || i0 > s->g.nx - 1 || j0 < 1 || j0 > s->g.ny - 1) return TETM_E_ARG;
+  if (fabs(s->g.cdt - s->g.dz) > 1e-12 * s->g.dz) return TETM_E_NOT_MAGIC;
+  if (s->step != 0 || s->bunch) return TETM_E_STATE;
+  const double dz = s->g.dz;
+  const int c0 = (int)ceil(5.0 * sigma_z / dz - 1e-12);
+  const int m_max = (int)ceil(15.0 * sigma_z / dz - 1e-12);
+  if (c0 < 1 || c0 > (1 << 20)) return TETM_E_ARG;
+  std::vector<double> qc((size_t)(2 * c0));
+  for (int d = -c0; d < c0; ++d) {
+    const double lo = std::max((double)d * dz, -5.0 * sigma_z);
+    const double hi = std::min((double)(d + 1) * dz, 5.0 * sigma_z);
+    qc[(size_t)(d + c0)] = hi > lo ? charge * (phi(hi / sigma_z) - phi(lo / sigma_z)) : 0.0;
+  }
+  const int nw = m_max + c0 + 2;
+  void* J = nullptr;
+  double* W = nullptr;
+  double* ql = nullptr;
+  if (cudaMalloc(&J, s->esz * qc.size()) != cudaSuccess || cudaMalloc(&W, sizeof(double) * nw) != cudaSuccess ||
+      cudaMalloc(&ql, sizeof(double) * (size_t)(s->g.nz + 1)) != cudaSuccess) {
+    cudaFree(J); cudaFree(W); cudaFree(ql);
+    cudaGetLastError();
+    return TETM_E_NOMEM;
+  }
+  int rc = TETM_OK;
+  if (s->esz == 8) {
+    std::vector<double> j(qc.size());
+    for (size_t q = 0; q < qc.size(); ++q) j[q] = kC * qc[q] / dz;
+    if (cudaMemcpy(J, j.data(), sizeof(double) * j.size(), cudaMemcpyHostToDevice) != cudaSuccess) rc = TETM_E_CUDA;
+  } else {
+    std::vector<float> j(qc.size());
+    for (size_t q = 0; q < qc.size(); ++q) j[q] = (float)(kC * qc[q] / dz);
+    if (cudaMemcpy(J, j.data(), sizeof(float) * j.size(), cudaMemcpyHostToDevice) != cudaSuccess) rc = TETM_E_CUDA;
+  }
+  if (rc == TETM_OK && cudaMemset(W, 0, sizeof(double) * nw) != cudaSuccess) rc = TETM_E_CUDA;
+  if (rc != TETM_OK) {
+    cudaFree(J); cudaFree(W); cudaFree(ql);
+    return rc;
+  }
+  s->J = J;
+  s->W = W;
+  s->qline = ql;
+  s->device_bytes += (long long)(s->esz * qc.size() + sizeof(double) * (nw + s->g.nz + 1));
+  s->qcell = qc;
+  s->bunch = true;
+  s->i0 = i0;
+  s->j0 = j0;
+  s->c0 = c0;
+  s->m_min = -c0 - 1;
+  s->m_max = m_max;
+  s->sigma = sigma_z;
+  s->q = charge;
+  return TETM_OK;
+}
+
+int tetm_step(tetm_solver* s, int32_t n) {
+  if (!s || n < 0) return TETM_E_ARG;
+  if (s->kernel == TETM_KERNEL_FUSED && s->work_dirty) {
+    int rc = rebuild_work(s);
+    if (rc) return rc;
+  }
+  return s->esz == 8 ? do_steps<double>(s, n) : do_steps<float>(s, n);
+}
+
+int tetm_sync(tetm_solver* s) {
+  if (!s) return TETM_E_ARG;
+  CK(cudaStreamSynchronize(s->stream));
+  return TETM_OK;
+}
+
+int tetm_wake(tetm_solver* s, double* out, int32_t cap, int32_t* n_out, double* s0, double* ds) {
+  if (!s) return TETM_E_ARG;
+  if (!s->bunch) return TETM_E_STATE;
+  const int nw = s->m_max - s->m_min + 1;
+  if (n_out) *n_out = nw;
+  if (s0) *s0 = s->m_min * s->g.dz;
+  if (ds) *ds = s->g.dz;
+  if (out) {
+    if (cap < nw) return TETM_E_ARG;
+    CK(cudaMemcpyAsync(out, s->W, sizeof(double) * nw, cudaMemcpyDeviceToHost, s->stream));
+  }
+  CK(cudaStreamSynchronize(s->stream));
+  return TETM_OK;
+}
+
+int tetm_energy(tetm_solver* s, double* w) {
+  if (!s || !w) return TETM_E_ARG;
+  const double* ma[6];
+  for (int c = 0; c < 6; ++c) ma[c] = s->minv_a[c];
+  cudaError_t e;
+  if (s->esz == 8) {
+    const double* f[6];
+    for (int c = 0; c < 6; ++c) f[c] = (const double*)s->set[s->cur][c];
+    e = launch_energy<double>(f, s->mask, s->minv_c, ma, s->L, s->alpha, s->diag, s->stream);
+  } else {
+    const float* f[6];
+    for (int c = 0; c < 6; ++c) f[c] = (const float*)s->set[s->cur][c];
+    e = launch_energy<float>(f, s->mask, s->minv_c, ma, s->L, s->alpha, s->diag, s->stream);
+  }
+  CK(e);
+  CK(cudaMemcpyAsync(w, s->diag.out, sizeof(double), cudaMemcpyDeviceToHost, s->stream));
+  CK(cudaStreamSynchronize(s->stream));
+  return isfinite(*w) ? TETM_OK : TETM_E_DIVERGED;
+}
+
+int tetm_charge_residual(tetm_solver* s, double* max_e, double* max_h, double* q_scale) {
+  if (!s) return TETM_E_ARG;
+  if (!s->prev_valid || s->step < 1) return TETM_E_STATE;
+  double qmax = 0.0;
+  if (s->bunch) {
+    // bunch charge in each dual cell [z_k - dz/2, z_k + dz/2] at time n+1/2
+    const double dz = s->g.dz;
+    const double zc = ((double)(s->step - 1) + 0.5 - s->c0) * dz;
+    std::vector<double> ql((size_t)(s->g.nz + 1));
+    for (int k = 0; k <= s->g.nz; ++k) {
+      const double lo = std::max(k * dz - 0.5 * dz - zc, -5.0 * s->sigma);
+      const double hi = std::min(k * dz + 0.5 * dz - zc, 5.0 * s->sigma);
+      ql[(size_t)k] = hi > lo ? s->q * (phi(hi / s->sigma) - phi(lo / s->sigma)) : 0.0;
+      qmax = std::max(qmax, fabs(ql[(size_t)k]));
+    }
+    CK(cudaMemcpyAsync(s->qline, ql.data(), sizeof(double) * ql.size(), cudaMemcpyHostToDevice, s->stream));
+  }
+  const double* ma[6];
+  for (int c = 0; c < 6; ++c) ma[c] = s->minv_a[c];
+  cudaError_t e;
+  if (s->esz == 8) {
+    const double *cur[6], *prv[6];
+    for (int c = 0; c < 6; ++c) {
+      cur[c] = (const double*)s->set[s->cur][c];
+      prv[c] = (const double*)s->set[1 - s->cur][c];
+    }
+    e = launch_charge<double>(cur, prv, s->mask, s->minv_c, ma, s->L, s->alpha,
+                              s->bunch ? s->qline : nullptr, s->i0, s->j0, s->diag, s->stream);
+  } else {
+    const float *cur[6], *prv[6];
+    for (int c = 0; c < 6; ++c) {
+      cur[c] = (const float*)s->set[s->cur][c];
+      prv[c] = (const float*)s->set[1 - s->cur][c];
+    }
+    e = launch_charge<float>(cur, prv, s->mask, s->minv_c, ma, s->L, s->alpha,
+                             s->bunch ? s->qline : nullptr, s->i0, s->j0, s->diag, s->stream);
+  }
+  CK(e);
+  double h[2];
+  CK(cudaMemcpyAsync(h, s->diag.out, sizeof(h), cudaMemcpyDeviceToHost, s->stream));
+  CK(cudaStreamSynchronize(s->stream));
+  if (max_e) *max_e = h[0];
+  if (max_h) *max_h = h[1];
+  if (q_scale) *q_scale = qmax;
+  return TETM_OK;
+}
+
+int tetm_get_fields(tetm_solver* s, int32_t comp, double* host) {
+  if (!s || !host || comp < 0 || comp > 5) return TETM_E_ARG;
+  int rc = ensure_staging(s);
+  if (rc) return rc;
+  return s->esz == 8 ? get_fields_t<double>(s, comp, host) : get_fields_t<float>(s, comp, host);
+}
+
+int tetm_set_fields(tetm_solver* s, int32_t comp, const double* host) {
+  if (!s || !host || comp < 0 || comp > 5) return TETM_E_ARG;
+  int rc = ensure_staging(s);
+  if (rc) return rc;
+  rc = s->esz == 8 ? set_fields_t<double>(s, comp, host) : set_fields_t<float>(s, comp, host);
+  s->prev_valid = false;
+  return rc;
+}
+
+int tetm_get_info(tetm_solver* s, tetm_info* info) {
+  if (!s || !info) return TETM_E_ARG;
+  memset(info, 0, sizeof(*info));
+  info->step = s->step;
+  info->device_bytes = s->device_bytes;
+  info->active_cells = s->active_cells;
+  info->processed_cells = (long long)s->n_work * s->tile_x * s->tile_y * s->chunk_z;
+  info->kernel = s->kernel;
+  info->precision = s->g.precision;
+  info->tile_x = s->tile_x;
+  info->tile_y = s->tile_y;
+  info->chunk_z = s->chunk_z;
+  info->work_items = s->n_work;
+  info->wake_len = s->bunch ? s->m_max - s->m_min + 1 : 0;
+  info->uniform_material = s->uniform ? 1 : 0;
+  return TETM_OK;
+}
+
+// Checkpoint format: a fixed header, the six arrays of the current state in
+// the device layout, then the wake accumulators.
+struct CkptHeader {
+  char magic[8];
+  int32_t nx, ny, nz, precision;
+  double dx, dy, dz, cdt;
+  int64_t step;
+  int64_t count;
+  int32_t bunch, nw;
+};
+
+int tetm_save(tetm_solver* s, void* buf, size_t cap, size_t* used) {
+  if (!s) return TETM_E_ARG;
+  const int nw = s->bunch ? s->m_max - s->m_min + 1 : 0;
+  const size_t fb = (size_t)s->L.count * s->esz;
+  const size_t need = sizeof(CkptHeader) + 6 * fb + sizeof(double) * (size_t)nw;
+  if (used) *used = need;
+  if (!buf) return TETM_OK;
+  if (cap < need) return TETM_E_ARG;
+  CkptHeader h;
+  memset(&h, 0, sizeof(h));
+  memcpy(h.magic, "TETMCKP1", 8);
+  h.nx = s->g.nx; h.ny = s->g.ny; h.nz = s->g.nz; h.precision = s->g.precision;
+  h.dx = s->g.dx; h.dy = s->g.dy; h.dz = s->g.dz; h.cdt = s->g.cdt;
+  h.step = s->step;
+  h.count = s->L.count;
+  h.bunch = s->bunch;
+  h.nw = nw;
+  char* p = (char*)buf;
+  memcpy(p, &h, sizeof(h));
+  p += sizeof(h);
+  for (int c = 0; c < 6; ++c, p += fb)
+    CK(cudaMemcpyAsync(p, s->set[s->cur][c], fb, cudaMemcpyDeviceToHost, s->stream));
+  if (nw) CK(cudaMemcpyAsync(p, s->W, sizeof(double) * nw, cudaMemcpyDeviceToHost, s->stream));
+  CK(cudaStreamSynchronize(s->stream));
+  return TETM_OK;
+}
+
+int tetm_load(tetm_solver* s, const void* buf, size_t size) {
+  if (!s || !buf || size < sizeof(CkptHeader)) return TETM_E_ARG;
+  CkptHeader h;
+  memcpy(&h, buf, sizeof(h));
+  const int nw = s->bunch ? s->m_max - s->m_min + 1 : 0;
+  const size_t fb = (size_t)s->L.count * s->esz;
+  if (memcmp(h.magic, "TETMCKP1", 8) != 0 || h.nx != s->g.nx || h.ny != s->g.ny || h.nz != s->g.nz ||
+      h.precision != s->g.precision || h.count != s->L.count || h.bunch != (int)s->bunch || h.nw != nw ||
+      h.dx != s->g.dx || h.dy != s->g.dy || h.dz != s->g.dz || h.cdt != s->g.cdt)
+    return TETM_E_ARG;
+  if (size < sizeof(CkptHeader) + 6 * fb + sizeof(double) * (size_t)nw) return TETM_E_ARG;
+  const char* p = (const char*)buf + sizeof(h);
+  for (int c = 0; c < 6; ++c, p += fb)
+    CK(cudaMemcpyAsync(s->set[s->cur][c], p, fb, cudaMemcpyHostToDevice, s->stream));
+  if (nw) CK(cudaMemcpyAsync(s->W, p, sizeof(double) * nw, cudaMemcpyHostToDevice, s->stream));
+  CK(cudaStreamSynchronize(s->stream));
+  s->step = h.step;
+  s->prev_valid = false;
+  return TETM_OK;
+}
+
+}  // extern "C"

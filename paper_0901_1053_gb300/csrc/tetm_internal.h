@@ -1,0 +1,101 @@
+// Internal declarations of libtetm: device layout, kernel argument blocks and
+// the launchers each translation unit provides. Not part of the public ABI.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include "../../include/tetm.h"
+
+namespace tetm {
+
+constexpr double kC = 299792458.0;
+constexpr double kEps0 = 8.8541878128e-12;
+constexpr double kMu0 = 1.0 / (kEps0 * kC * kC);
+
+// One activity bit per component and node index: bit c set <=> the object of
+// component c attached to that node carries a field (non-PEC edge, face with
+// two non-PEC cells inside the box). Components: ex ey ez hx hy hz = 0..5.
+constexpr int kEX = 0, kEY = 1, kEZ = 2, kHX = 3, kHY = 4, kHZ = 5;
+
+// Device layout of every per-node array (fields, mask, coefficients):
+// planes k = -1..nz, rows j = -2..ny+1, columns i = -ox..px-ox-1, x fastest.
+// Index (i, j, k) of the canonical FIT layout maps to idx(i, j, k); the guard
+// entries around the canonical range are zero and inactive, so stencils read
+// them without bounds checks (P_x at i = nx reads the zero at i = nx + ... ).
+struct Layout {
+  int nx, ny, nz;
+  int ox;            // column of i = 0 (16-byte aligned)
+  long long px;      // row pitch in elements
+  long long sz;      // plane stride in elements, (ny + 4) * px
+  long long count;   // elements per array, (nz + 2) * sz
+  __host__ __device__ __forceinline__ long long idx(int i, int j, int k) const {
+    return ((long long)(k + 1) * (ny + 4) + (j + 2)) * px + (i + ox);
+  }
+};
+
+Layout make_layout(int nx, int ny, int nz, int elem_bytes);
+
+// Bunch data as the kernels see it (all device pointers).
+template <typename T>
+struct BunchDev {
+  int on;               // 0: no bunch
+  int i0, j0;           // bunch line node
+  int c0;               // start offset in cells
+  int m_min, m_max;     // wake window
+  double inv_q;         // 1/Q
+  const T* J;           // J[d + c0] = c*Q_cell(d)/dz [A], d = -c0..c0-1
+  double* W;            // W[m - m_min], float64 accumulators
+};
+
+// Per-component coefficients: either one constant per component with the
+// activity mask, or (material runs) one array per component.
+template <typename T>
+struct Coefs {
+  const uint8_t* mask;  // activity bits, device layout
+  T u[6];               // update coefficients alpha*M^-1 (ex,ey,hx,hy), 2 alpha*M^-1 (ez,hz)
+  const T* ua[6];       // per-entry update coefficients, or nullptr
+};
+
+template <typename T>
+struct StepArgs {
+  const T* in[6];       // state y^n (fused: read only)
+  T* out[6];            // fused: state y^{n+1}; reference: == in (updated in place)
+  Coefs<T> co;
+  Layout L;
+  long long n;          // step index of the state being advanced
+  BunchDev<T> b;
+  // fused-kernel work decomposition
+  int tiles_x, tiles_y, chunk_z, n_chunks;
+  const int* work;      // optional list of active (tile, chunk) items; nullptr = all
+  int n_work;
+};
+
+// ---- launchers (kernels_step.cu) -----------------------------------------
+template <typename T>
+cudaError_t launch_reference_step(const StepArgs<T>& a, cudaStream_t st);
+template <typename T>
+cudaError_t launch_fused_step(const StepArgs<T>& a, int tile_x, int tile_y, cudaStream_t st);
+bool fused_shape_ok(int tile_x, int tile_y);
+
+// ---- diagnostics (kernels_diag.cu) ----------------------------------------
+struct DiagScratch {
+  double* part;   // per-block partials
+  int cap;        // entries of part
+  double* out;    // device result slots (at least 4)
+};
+
+// Discrete energy W^{n,e}; minv[c] constants (mask mode) or minv_a[c] arrays.
+template <typename T>
+cudaError_t launch_energy(const T* const f[6], const uint8_t* mask, const double* minv,
+                          const double* const minv_a[6], const Layout& L, double alpha,
+                          const DiagScratch& s, cudaStream_t st);
+
+// Charge residuals of the last step: out[0] = max|qe - qbunch|, out[1] = max|qh|.
+template <typename T>
+cudaError_t launch_charge(const T* const cur[6], const T* const prev[6], const uint8_t* mask,
+                          const double* minv, const double* const minv_a[6], const Layout& L,
+                          double alpha, const double* qline, int i0, int j0,
+                          const DiagScratch& s, cudaStream_t st);
+
+}  // namespace tetm

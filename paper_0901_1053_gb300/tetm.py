@@ -1,0 +1,236 @@
+"""Thin ctypes binding of libtetm.so (include/tetm.h), same names as the C ABI.
+
+Argument marshalling only: every step of the solve runs in the library's
+CUDA kernels. Importing this module loads the in-tree library and raises
+ImportError if it has not been built (``python -m paper_0901_1053_gb300.build``
+or ``__graft_entry__.build()``); there is no fallback implementation.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+
+import numpy as np
+
+from .build import library_path
+
+TETM_OK = 0
+TETM_E_ARG = -1
+TETM_E_UNSTABLE = -2
+TETM_E_NOT_MAGIC = -3
+TETM_E_NOMEM = -4
+TETM_E_CUDA = -5
+TETM_E_STATE = -6
+TETM_E_TIMEOUT = -7
+TETM_E_DIVERGED = -8
+TETM_E_UNSUPPORTED = -9
+
+TETM_FP64 = 0
+TETM_FP32 = 1
+TETM_KERNEL_FUSED = 0
+TETM_KERNEL_REFERENCE = 1
+COMPONENTS = ("ex", "ey", "ez", "hx", "hy", "hz")
+
+# Every function the header declares (checked by the CPU test suite).
+EXPORTS = ("tetm_create", "tetm_set_bunch", "tetm_step", "tetm_sync", "tetm_wake",
+           "tetm_destroy", "tetm_energy", "tetm_charge_residual", "tetm_get_fields",
+           "tetm_set_fields", "tetm_set_stream", "tetm_set_kernel", "tetm_set_tiling",
+           "tetm_get_info", "tetm_bytes_needed", "tetm_save", "tetm_load", "tetm_strerror")
+
+
+class tetm_grid(ctypes.Structure):
+    _fields_ = [("nx", ctypes.c_int32), ("ny", ctypes.c_int32), ("nz", ctypes.c_int32),
+                ("precision", ctypes.c_int32), ("dx", ctypes.c_double), ("dy", ctypes.c_double),
+                ("dz", ctypes.c_double), ("cdt", ctypes.c_double)]
+
+
+class tetm_info(ctypes.Structure):
+    _fields_ = [("step", ctypes.c_int64), ("device_bytes", ctypes.c_int64),
+                ("active_cells", ctypes.c_int64), ("processed_cells", ctypes.c_int64),
+                ("kernel", ctypes.c_int32), ("precision", ctypes.c_int32),
+                ("tile_x", ctypes.c_int32), ("tile_y", ctypes.c_int32), ("chunk_z", ctypes.c_int32),
+                ("work_items", ctypes.c_int32), ("wake_len", ctypes.c_int32),
+                ("uniform_material", ctypes.c_int32)]
+
+
+def _load():
+    path = library_path()
+    if not os.path.exists(path):
+        raise ImportError("libtetm.so is not built (%s); run __graft_entry__.build()" % path)
+    lib = ctypes.CDLL(path)
+    vp, i32, dbl = ctypes.c_void_p, ctypes.c_int32, ctypes.c_double
+    pp = ctypes.POINTER(ctypes.c_void_p)
+    sig = {
+        "tetm_create": (ctypes.c_int, [ctypes.POINTER(tetm_grid), vp, vp, vp, pp]),
+        "tetm_set_bunch": (ctypes.c_int, [vp, dbl, dbl, i32, i32]),
+        "tetm_step": (ctypes.c_int, [vp, i32]),
+        "tetm_sync": (ctypes.c_int, [vp]),
+        "tetm_wake": (ctypes.c_int, [vp, vp, i32, ctypes.POINTER(i32), ctypes.POINTER(dbl),
+                                     ctypes.POINTER(dbl)]),
+        "tetm_destroy": (None, [vp]),
+        "tetm_energy": (ctypes.c_int, [vp, ctypes.POINTER(dbl)]),
+        "tetm_charge_residual": (ctypes.c_int, [vp, ctypes.POINTER(dbl), ctypes.POINTER(dbl),
+                                                ctypes.POINTER(dbl)]),
+        "tetm_get_fields": (ctypes.c_int, [vp, i32, vp]),
+        "tetm_set_fields": (ctypes.c_int, [vp, i32, vp]),
+        "tetm_set_stream": (ctypes.c_int, [vp, vp]),
+        "tetm_set_kernel": (ctypes.c_int, [vp, i32]),
+        "tetm_set_tiling": (ctypes.c_int, [vp, i32, i32, i32]),
+        "tetm_get_info": (ctypes.c_int, [vp, ctypes.POINTER(tetm_info)]),
+        "tetm_bytes_needed": (ctypes.c_int64, [ctypes.POINTER(tetm_grid)]),
+        "tetm_save": (ctypes.c_int, [vp, vp, ctypes.c_size_t, ctypes.POINTER(ctypes.c_size_t)]),
+        "tetm_load": (ctypes.c_int, [vp, vp, ctypes.c_size_t]),
+        "tetm_strerror": (ctypes.c_char_p, [ctypes.c_int]),
+    }
+    for name, (res, args) in sig.items():
+        f = getattr(lib, name)
+        f.restype = res
+        f.argtypes = args
+    return lib
+
+
+lib = _load()
+
+
+class TetmError(RuntimeError):
+    def __init__(self, code, where):
+        self.code = code
+        super().__init__("%s: %s (%d)" % (where, lib.tetm_strerror(code).decode(), code))
+
+
+def _check(rc, where):
+    if rc != TETM_OK:
+        raise TetmError(rc, where)
+    return rc
+
+
+def _ptr(a):
+    return None if a is None else ctypes.c_void_p(a.ctypes.data)
+
+
+def make_grid(nx, ny, nz, dx, dy, dz, cdt=0.0, precision="fp32"):
+    p = {"fp64": TETM_FP64, "fp32": TETM_FP32}[precision] if isinstance(precision, str) else precision
+    return tetm_grid(int(nx), int(ny), int(nz), int(p), float(dx), float(dy), float(dz), float(cdt))
+
+
+def tetm_bytes_needed(grid):
+    return int(lib.tetm_bytes_needed(ctypes.byref(grid)))
+
+
+def tetm_strerror(code):
+    return lib.tetm_strerror(int(code)).decode()
+
+
+class Solver:
+    """One solve; a thin object around a ``tetm_solver*`` handle.
+
+    ``eps_r``/``mu_r``: float64 per cell (nz, ny, nx) or None; ``pec``: uint8
+    per cell or None. Fields are exchanged in the canonical FIT layout
+    (nz+1, ny+1, nx+1) as float64.
+    """
+
+    def __init__(self, nx, ny, nz, dx, dy, dz, cdt=0.0, precision="fp32", eps_r=None, mu_r=None,
+                 pec=None):
+        self.grid = make_grid(nx, ny, nz, dx, dy, dz, cdt, precision)
+        cell = (int(nz), int(ny), int(nx))
+        arrs = []
+        for a, dt in ((eps_r, np.float64), (mu_r, np.float64), (pec, np.uint8)):
+            arrs.append(None if a is None else np.ascontiguousarray(a, dtype=dt).reshape(cell))
+        h = ctypes.c_void_p()
+        self.h = None
+        _check(lib.tetm_create(ctypes.byref(self.grid), *[_ptr(a) for a in arrs], ctypes.byref(h)),
+               "tetm_create")
+        self.h = h
+        self.shape = (int(nz) + 1, int(ny) + 1, int(nx) + 1)
+
+    @classmethod
+    def from_workload(cls, w, precision=None):
+        s = cls(w.nx, w.ny, w.nz, w.dx, w.dy, w.dz, w.cdt, precision or w.precision, pec=w.pec)
+        s.set_bunch(w.sigma, w.charge, w.i0, w.j0)
+        return s
+
+    def close(self):
+        if self.h is not None:
+            lib.tetm_destroy(self.h)
+            self.h = None
+
+    __del__ = close
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *exc):
+        self.close()
+
+    def set_bunch(self, sigma, charge, i0, j0):
+        _check(lib.tetm_set_bunch(self.h, float(sigma), float(charge), int(i0), int(j0)),
+               "tetm_set_bunch")
+
+    def step(self, n=1):
+        _check(lib.tetm_step(self.h, int(n)), "tetm_step")
+
+    def sync(self):
+        _check(lib.tetm_sync(self.h), "tetm_sync")
+
+    def wake(self):
+        n = ctypes.c_int32()
+        s0, ds = ctypes.c_double(), ctypes.c_double()
+        _check(lib.tetm_wake(self.h, None, 0, ctypes.byref(n), ctypes.byref(s0), ctypes.byref(ds)),
+               "tetm_wake")
+        out = np.empty(n.value, dtype=np.float64)
+        _check(lib.tetm_wake(self.h, _ptr(out), n.value, None, None, None), "tetm_wake")
+        return out, s0.value, ds.value
+
+    def energy(self):
+        w = ctypes.c_double()
+        _check(lib.tetm_energy(self.h, ctypes.byref(w)), "tetm_energy")
+        return w.value
+
+    def charge_residual(self):
+        e, h, q = ctypes.c_double(), ctypes.c_double(), ctypes.c_double()
+        _check(lib.tetm_charge_residual(self.h, ctypes.byref(e), ctypes.byref(h), ctypes.byref(q)),
+               "tetm_charge_residual")
+        return e.value, h.value, q.value
+
+    def get(self, comp):
+        out = np.empty(self.shape, dtype=np.float64)
+        _check(lib.tetm_get_fields(self.h, _comp(comp), _ptr(out)), "tetm_get_fields")
+        return out
+
+    def set(self, comp, arr):
+        a = np.ascontiguousarray(arr, dtype=np.float64).reshape(self.shape)
+        _check(lib.tetm_set_fields(self.h, _comp(comp), _ptr(a)), "tetm_set_fields")
+
+    def fields(self):
+        return {c: self.get(c) for c in COMPONENTS}
+
+    def set_stream(self, stream):
+        """stream: an int/pointer cudaStream_t (e.g. torch's ``stream.cuda_stream``) or None."""
+        _check(lib.tetm_set_stream(self.h, ctypes.c_void_p(stream or 0)), "tetm_set_stream")
+
+    def set_kernel(self, kernel):
+        k = {"fused": TETM_KERNEL_FUSED, "reference": TETM_KERNEL_REFERENCE}.get(kernel, kernel)
+        _check(lib.tetm_set_kernel(self.h, int(k)), "tetm_set_kernel")
+
+    def set_tiling(self, tile_x=0, tile_y=0, chunk_z=0):
+        _check(lib.tetm_set_tiling(self.h, int(tile_x), int(tile_y), int(chunk_z)), "tetm_set_tiling")
+
+    def info(self):
+        i = tetm_info()
+        _check(lib.tetm_get_info(self.h, ctypes.byref(i)), "tetm_get_info")
+        return {f: getattr(i, f) for f, _ in tetm_info._fields_}
+
+    def save(self):
+        used = ctypes.c_size_t()
+        _check(lib.tetm_save(self.h, None, 0, ctypes.byref(used)), "tetm_save")
+        buf = np.empty(used.value, dtype=np.uint8)
+        _check(lib.tetm_save(self.h, _ptr(buf), used.value, ctypes.byref(used)), "tetm_save")
+        return buf
+
+    def load(self, buf):
+        b = np.ascontiguousarray(buf, dtype=np.uint8)
+        _check(lib.tetm_load(self.h, _ptr(b), b.size), "tetm_load")
+
+
+def _comp(c):
+    return COMPONENTS.index(c) if isinstance(c, str) else int(c)

@@ -1,0 +1,62 @@
+"""CPU-side checks of the C ABI: the library loads, exports every function
+include/tetm.h declares, and its host-only paths (argument validation, the
+stability bound of Eq. (25), sizes, error strings) answer without a GPU."""
+import os
+import re
+
+import pytest
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+def _header_functions():
+    txt = open(os.path.join(ROOT, "include", "tetm.h")).read()
+    txt = re.sub(r"/\*.*?\*/", "", txt, flags=re.S)
+    return sorted(set(re.findall(r"\b(tetm_[a-z_]+)\s*\(", txt)))
+
+
+@pytest.fixture(scope="module")
+def tetm():
+    from paper_0901_1053_gb300 import build as b
+    if not os.path.exists(b.library_path()):
+        b.build()
+    from paper_0901_1053_gb300 import tetm as t
+    return t
+
+
+def test_library_exports_every_declared_function(tetm):
+    declared = _header_functions()
+    assert len(declared) >= 15
+    for name in declared:
+        assert hasattr(tetm.lib, name), name
+    assert sorted(tetm.EXPORTS) == declared
+
+
+def test_error_strings(tetm):
+    assert tetm.tetm_strerror(0) == "ok"
+    assert "Eq. (25)" in tetm.tetm_strerror(tetm.TETM_E_UNSTABLE)
+    assert tetm.tetm_strerror(-1234) == "unknown error"
+
+
+def test_create_rejects_bad_and_unstable_grids_before_touching_the_gpu(tetm):
+    import ctypes
+    h = ctypes.c_void_p(123)
+    bad = tetm.make_grid(1, 8, 8, 1e-3, 1e-3, 1e-3)
+    assert tetm.lib.tetm_create(ctypes.byref(bad), None, None, None, ctypes.byref(h)) == tetm.TETM_E_ARG
+    assert not h.value
+    cubic = tetm.make_grid(8, 8, 8, 1e-3, 1e-3, 1e-3, 0.0)   # dx=dy=dz, c*dt=dz: outside Eq. (25)
+    assert tetm.lib.tetm_create(ctypes.byref(cubic), None, None, None, ctypes.byref(h)) == \
+        tetm.TETM_E_UNSTABLE
+    longstep = tetm.make_grid(8, 8, 8, 2e-3, 2e-3, 1e-3, 1.01e-3)  # c*dt > dz
+    assert tetm.lib.tetm_create(ctypes.byref(longstep), None, None, None, ctypes.byref(h)) == \
+        tetm.TETM_E_UNSTABLE
+
+
+def test_bytes_needed(tetm):
+    g32 = tetm.make_grid(256, 256, 2048, 1.414e-3, 1.414e-3, 1e-3, precision="fp32")
+    g64 = tetm.make_grid(256, 256, 2048, 1.414e-3, 1.414e-3, 1e-3, precision="fp64")
+    b32, b64 = tetm.tetm_bytes_needed(g32), tetm.tetm_bytes_needed(g64)
+    cells = 256 * 256 * 2048
+    assert 49 * cells < b32 < 60 * cells          # two field sets of six float32 + mask
+    assert 97 * cells < b64 < 115 * cells
+    assert tetm.tetm_bytes_needed(tetm.make_grid(0, 2, 2, 1, 1, 1)) == 0

@@ -1,0 +1,246 @@
+"""GPU parity: the CUDA path (through the C ABI) against the FP64 CPU oracle.
+
+Tolerances. GPU FP64 fields and wake: 1e-12 relative to the peak of each
+quantity (the FP64 target). The two sides differ only in rounding: the GPU
+contracts a + c*(b - d) into one FMA where the oracle rounds twice, which
+moves each update by at most an ulp; the scheme is energy-conserving, so
+these differences grow about linearly with the step count, far below 1e-12
+over the hundreds of steps used here. FP32 fields with FP64 wake sums: the
+wake must stay within 1e-4 of its peak.
+"""
+import dataclasses
+import math
+
+import numpy as np
+import pytest
+
+from oracle import Oracle
+from paper_0901_1053_gb300 import workloads as wl
+
+pytestmark = pytest.mark.gpu
+
+TOL64 = 1e-12
+TOL32_WAKE = 1e-4
+
+
+@pytest.fixture(scope="module")
+def tetm():
+    import __graft_entry__
+    __graft_entry__.build()
+    from paper_0901_1053_gb300 import tetm as t
+    return t
+
+
+def oracle_run(w, steps=None, fields=None):
+    o = Oracle(w.nx, w.ny, w.nz, w.dx, w.dy, w.dz, w.cdt, pec=w.pec)
+    if fields is not None:
+        for c, a in fields.items():
+            o.set(c, a)
+    if w.sigma:
+        o.set_bunch(w.sigma, w.charge, w.i0, w.j0)
+    o.step(w.steps if steps is None else steps)
+    return o
+
+
+def rel_err(a, b):
+    peak = np.max(np.abs(b))
+    return float(np.max(np.abs(a - b)) / peak) if peak > 0 else float(np.max(np.abs(a)))
+
+
+def compare_fields(s, o, tol):
+    for c in ("ex", "ey", "ez", "hx", "hy", "hz"):
+        g, r = s.get(c), o.get(c)
+        assert rel_err(g, r) <= tol, (c, rel_err(g, r))
+
+
+@pytest.mark.parametrize("kernel", ["fused", "reference"])
+def test_plain_pipe_fp64_matches_oracle(tetm, kernel):
+    """24x24x96 PEC pipe, sigma = 4 dz, 400 steps, wake over 20 sigma."""
+    w = wl.plain_pipe(precision="fp64")
+    s = tetm.Solver.from_workload(w)
+    s.set_kernel(kernel)
+    s.step(w.steps)
+    o = oracle_run(w)
+    wk, s0, ds = s.wake()
+    ref, r0, rd = o.wake()
+    assert (s0, ds) == (r0, rd) and len(wk) == len(ref)
+    assert rel_err(wk, ref) <= TOL64
+    compare_fields(s, o, TOL64)
+    assert s.energy() == pytest.approx(o.energy(), rel=TOL64)
+
+
+def test_plain_pipe_matches_stored_oracle_wake(tetm):
+    from test_oracle_golden import load_golden
+    ref, meta = load_golden()
+    w = wl.plain_pipe(precision="fp64")
+    s = tetm.Solver.from_workload(w)
+    s.step(w.steps)
+    wk, s0, ds = s.wake()
+    assert s0 == pytest.approx(meta["s0_m"])
+    assert rel_err(wk, ref) <= TOL64
+
+
+@pytest.mark.parametrize("kernel", ["fused", "reference"])
+@pytest.mark.parametrize("dims", [(40, 36, 70), (33, 18, 9), (2, 2, 2), (70, 5, 130)])
+def test_ragged_collimators_fp64(tetm, kernel, dims):
+    """Sizes that leave ragged tiles in x and y and a ragged last z-chunk;
+    staircase PEC collimator with the bunch off the tile grid."""
+    nx, ny, nz = dims
+    if min(nx, ny) >= 8:
+        w = wl.scaled_collimator(max(nx, ny), nz, sigma_cells=2.5)
+        w.nx, w.ny = nx, ny
+        w.pec = wl.radius_mask(nx, ny, nz, wl.collimator_radius(nz, 0.45 * min(nx, ny),
+                                                                 0.2 * min(nx, ny), nz // 4, nz // 2))
+        w.i0, w.j0 = nx // 2, ny // 2
+        w.steps = nz + 25
+    else:
+        w = wl.plain_pipe(nz=nz, n=2, steps=10)
+        w.nx, w.ny = nx, ny
+        w.sigma = 0.0
+    w.precision = "fp64"
+    s = tetm.Solver(w.nx, w.ny, w.nz, w.dx, w.dy, w.dz, w.cdt, "fp64", pec=w.pec)
+    s.set_kernel(kernel)
+    rng = np.random.default_rng(sum(dims))
+    init = {c: rng.standard_normal(s.shape) for c in ("ex", "ey", "ez", "hx", "hy", "hz")}
+    for c, a in init.items():
+        s.set(c, a)
+    if w.sigma:
+        s.set_bunch(w.sigma, w.charge, w.i0, w.j0)
+    s.step(w.steps)
+    o = oracle_run(w, fields=init)
+    compare_fields(s, o, TOL64)
+    if w.sigma:
+        assert rel_err(s.wake()[0], o.wake()[0]) <= 1e-11
+
+
+@pytest.mark.parametrize("tiling", [(32, 4, 4), (32, 8, 16), (32, 16, 7), (64, 4, 64), (64, 8, 5)])
+def test_fused_tilings_are_bitwise_identical(tetm, tiling):
+    """The fused kernel computes every node with the same operations whatever
+    the block shape, so all tilings agree bit for bit."""
+    w = wl.scaled_collimator(72, 90, sigma_cells=3.0, precision="fp64")
+    w.steps = 60
+    res = []
+    for t in [(32, 8, 64), tiling]:
+        s = tetm.Solver.from_workload(w)
+        s.set_tiling(*t)
+        s.step(w.steps)
+        res.append((s.wake()[0], s.get("ez"), s.get("hy")))
+    for a, b in zip(res[0], res[1]):
+        assert np.array_equal(a, b)
+
+
+def test_fp32_wake_within_1e4_of_peak(tetm):
+    w = wl.scaled_collimator(48, 192, sigma_cells=4.0, precision="fp32")
+    s = tetm.Solver.from_workload(w)
+    s.step(w.steps)
+    o = oracle_run(w)
+    err = rel_err(s.wake()[0], o.wake()[0])
+    assert err <= TOL32_WAKE, err
+
+
+def test_reference_and_fused_fp32_agree(tetm):
+    w = wl.scaled_collimator(40, 120, sigma_cells=3.0, precision="fp32")
+    out = []
+    for k in ("fused", "reference"):
+        s = tetm.Solver.from_workload(w)
+        s.set_kernel(k)
+        s.step(w.steps)
+        out.append(s.wake()[0])
+    assert rel_err(out[0], out[1]) <= 1e-5
+
+
+def test_materials_reference_kernel_fp64(tetm):
+    nx, ny, nz = 12, 10, 16
+    eps, mu, pec = wl.random_materials(nx, ny, nz, 3)
+    s = tetm.Solver(nx, ny, nz, wl.DXY, wl.DXY, wl.DZ, 0.0, "fp64", eps_r=eps, mu_r=mu, pec=pec)
+    assert s.info()["kernel"] == tetm.TETM_KERNEL_REFERENCE
+    with pytest.raises(tetm.TetmError):
+        s.set_kernel("fused")
+    o = Oracle(nx, ny, nz, wl.DXY, wl.DXY, wl.DZ, 0.0, eps_r=eps, mu_r=mu, pec=pec)
+    rng = np.random.default_rng(9)
+    for c in ("ex", "ey", "ez", "hx", "hy", "hz"):
+        a = rng.standard_normal(s.shape)
+        s.set(c, a)
+        o.set(c, a)
+    s.step(50)
+    o.step(50)
+    compare_fields(s, o, TOL64)
+    assert s.energy() == pytest.approx(o.energy(), rel=TOL64)
+
+
+def test_energy_and_charge_balances_on_gpu(tetm):
+    w = wl.scaled_collimator(40, 100, sigma_cells=3.0, precision="fp64")
+    s = tetm.Solver.from_workload(w)
+    o = Oracle(w.nx, w.ny, w.nz, w.dx, w.dy, w.dz, w.cdt, pec=w.pec)
+    o.set_bunch(w.sigma, w.charge, w.i0, w.j0)
+    for n in (30, 30, 40):
+        s.step(n)
+        o.step(n)
+        assert s.energy() == pytest.approx(o.energy(), rel=TOL64)
+        e, h, q = s.charge_residual()
+        assert q > 0.01 * w.charge
+        assert e <= 1e-12 * q and h <= 1e-12 * q
+
+
+def test_fp32_charge_balance(tetm):
+    w = wl.scaled_collimator(40, 100, sigma_cells=3.0, precision="fp32")
+    s = tetm.Solver.from_workload(w)
+    s.step(70)
+    e, h, q = s.charge_residual()
+    assert e <= 1e-4 * q
+
+
+def test_checkpoint_split_run_is_bitwise_equal(tetm):
+    w = wl.scaled_collimator(32, 64, sigma_cells=3.0, precision="fp32")
+    a = tetm.Solver.from_workload(w)
+    a.step(50)
+    buf = a.save()
+    a.step(30)
+    b = tetm.Solver.from_workload(w)
+    b.load(buf)
+    assert b.info()["step"] == 50
+    b.step(30)
+    assert np.array_equal(a.wake()[0], b.wake()[0])
+    assert np.array_equal(a.get("ez"), b.get("ez"))
+
+
+def test_state_errors(tetm):
+    w = wl.plain_pipe(nz=20, n=8, steps=5, precision="fp64")
+    s = tetm.Solver(w.nx, w.ny, w.nz, w.dx, w.dy, w.dz, 0.0, "fp64")
+    with pytest.raises(tetm.TetmError) as e:
+        s.charge_residual()
+    assert e.value.code == tetm.TETM_E_STATE
+    with pytest.raises(tetm.TetmError) as e:
+        s.wake()
+    assert e.value.code == tetm.TETM_E_STATE
+    s.step(1)
+    with pytest.raises(tetm.TetmError) as e:
+        s.set_bunch(2e-3, 1e-9, 4, 4)
+    assert e.value.code == tetm.TETM_E_STATE
+    s2 = tetm.Solver(w.nx, w.ny, w.nz, w.dx, w.dy, w.dz, 0.9 * w.dz, "fp64")
+    with pytest.raises(tetm.TetmError) as e:
+        s2.set_bunch(2e-3, 1e-9, 4, 4)
+    assert e.value.code == tetm.TETM_E_NOT_MAGIC
+    with pytest.raises(tetm.TetmError) as e:
+        s2.set_tiling(48, 8, 16)
+    assert e.value.code == tetm.TETM_E_ARG
+
+
+@pytest.mark.parametrize("precision,tol", [("fp32", 2e-5), ("fp64", TOL64)])
+def test_full_size_collimator_head_matches_oracle(tetm, precision, tol):
+    """256x256x2048 step collimator in the benchmark's launch configuration.
+    After n steps nothing ahead of plane n has moved (no precursor), so the
+    oracle on the first 80 planes of the same geometry reproduces the full
+    box for n = 70 steps: planes 0..70 are compared entry by entry."""
+    w = wl.step_collimator(precision=precision)
+    n = 70
+    s = tetm.Solver.from_workload(w)
+    s.step(n)
+    head = dataclasses.replace(w, nz=80, pec=w.pec[:80].copy(), steps=n)
+    o = oracle_run(head, steps=n)
+    for c in ("ex", "ey", "ez", "hx", "hy", "hz"):
+        g = s.get(c)
+        assert np.all(g[n + 2:] == 0.0), c
+        r = o.get(c)
+        assert rel_err(g[:n + 1], r[:n + 1]) <= tol, (c, rel_err(g[:n + 1], r[:n + 1]))
+    assert rel_err(s.wake()[0], o.wake()[0]) <= (1e-4 if precision == "fp32" else 1e-11)
