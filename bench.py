@@ -1,0 +1,393 @@
+#!/usr/bin/env python3
+"""Throughput benchmark of the explicit TE/TM solver (Eq. (23)) on one GB300.
+
+Workload (default): the 256 x 256 x 2048 staircase step collimator, pipe
+radius 96 -> 32 -> 96 transverse cells, dz = 1 mm, dx = dy = sqrt(2) mm,
+c*dt = dz, Gaussian bunch sigma = 6 dz on the axis; float32 fields, float64
+wake and balances. One benchmark step is one time step of the whole path:
+the bunch current, the ten updates, one wake sample per window point, and
+every --balance-every steps the float64 energy and charge balances.
+
+value  = cells * steps / device time of the timed steps, Gcell-updates/s,
+         summed over ranks (each rank runs its own replica: weak scaling).
+e2e    = the same metric for one complete solve through the C ABI from host
+         buffers: tetm_create from a pinned host PEC array, tetm_set_bunch,
+         tetm_step(all steps), tetm_wake into host memory.
+roofline: the fused step kernel, algorithmic bytes = 12 field words + 1 mask
+         byte per processed cell (49 B in float32) per launch, over its mean
+         launch duration measured with CUDA events on its stream.
+
+--impl reference times the FP64 CPU oracle (test infrastructure) on the
+host, on a bounded sample of the same workload.
+"""
+from __future__ import annotations
+
+import argparse
+import hashlib
+import json
+import math
+import os
+import re
+import statistics
+import subprocess
+import sys
+import tempfile
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "Gcell-updates/s"
+UNIT = "Gcell-updates/s"
+
+
+def parse_args():
+    p = argparse.ArgumentParser()
+    p.add_argument("--gpus", type=int, default=1)
+    p.add_argument("--steps", type=int, default=2000)
+    p.add_argument("--warmup", type=int, default=20)
+    p.add_argument("--impl", default="tetm", choices=["tetm", "reference"])
+    p.add_argument("--workload", default="collimator", choices=["collimator", "plain_pipe"])
+    p.add_argument("--precision", default=None, choices=[None, "fp32", "fp64"])
+    p.add_argument("--balance-every", type=int, default=100)
+    p.add_argument("--tiling", default=None, help="tile_x,tile_y,chunk_z")
+    p.add_argument("--kernel", default="fused", choices=["fused", "reference"])
+    p.add_argument("--no-e2e", action="store_true")
+    p.add_argument("--no-cpu-baseline", action="store_true")
+    p.add_argument("--e2e-steps", type=int, default=0, help="0 = the workload's full step count")
+    return p.parse_args()
+
+
+def make_workload(args):
+    from paper_0901_1053_gb300 import workloads as wl
+    if args.workload == "plain_pipe":
+        w = wl.plain_pipe()
+    else:
+        w = wl.step_collimator()
+    if args.precision:
+        w.precision = args.precision
+    return w
+
+
+def dist_env():
+    rank = int(os.environ.get("RANK", "0"))
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return rank, world, local
+
+
+class Dist:
+    """Control plane only (barrier, max of timings): gloo on CPU tensors."""
+
+    def __init__(self, world):
+        self.world = world
+        if world > 1:
+            import torch.distributed as dist
+            os.environ.setdefault("MASTER_ADDR", "127.0.0.1")
+            dist.init_process_group("gloo")
+            self.d = dist
+
+    def barrier(self):
+        if self.world > 1:
+            self.d.barrier()
+
+    def max(self, x):
+        if self.world == 1:
+            return x
+        import torch
+        t = torch.tensor([float(x)], dtype=torch.float64)
+        self.d.all_reduce(t, op=self.d.ReduceOp.MAX)
+        return float(t.item())
+
+    def close(self):
+        if self.world > 1:
+            self.d.destroy_process_group()
+
+
+# ---------------------------------------------------------------------------
+# Clocks during the timed region
+# ---------------------------------------------------------------------------
+class ClockSampler:
+    FIELDS = ("index,uuid,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, uuid):
+        self.uuid = uuid
+        self.proc = None
+        self.path = None
+
+    def start(self):
+        try:
+            fd, self.path = tempfile.mkstemp(prefix="clocks_", suffix=".csv")
+            self.f = os.fdopen(fd, "w")
+            self.proc = subprocess.Popen(["nvidia-smi", "--query-gpu=" + self.FIELDS,
+                                          "--format=csv,noheader,nounits", "-lms", "200"],
+                                         stdout=self.f, stderr=subprocess.DEVNULL)
+        except (OSError, ValueError):
+            self.proc = None
+
+    def stop(self):
+        if self.proc is None:
+            return None
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except subprocess.TimeoutExpired:
+            self.proc.kill()
+        self.f.close()
+        rows = []
+        with open(self.path) as f:
+            for line in f:
+                t = [x.strip() for x in line.split(",")]
+                if len(t) < 10:
+                    continue
+                if self.uuid and self.uuid not in t[1]:
+                    continue
+                rows.append(t)
+        os.unlink(self.path)
+        if not rows:
+            return None
+        sm = [float(r[2]) for r in rows if _num(r[2])]
+        mx = [float(r[3]) for r in rows if _num(r[3])]
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        reasons = sorted({names[i] for r in rows for i in range(4) if r[6 + i].lower() == "active"})
+        return {"sm_mhz": statistics.median(sm) if sm else None,
+                "sm_max_mhz": max(mx) if mx else None, "reasons": reasons, "samples": len(rows),
+                "power_w_max": max((float(r[4]) for r in rows if _num(r[4])), default=None)}
+
+
+def _num(s):
+    try:
+        float(s)
+        return True
+    except ValueError:
+        return False
+
+
+# ---------------------------------------------------------------------------
+# Roofline bookkeeping
+# ---------------------------------------------------------------------------
+def measured_peak_hbm():
+    path = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(path):
+        with open(path) as f:
+            return float(json.load(f)["hbm_gbs"]), "measured"
+    return 6800.0, "fallback"
+
+
+def kernel_source_hash():
+    with open(os.path.join(ROOT, "paper_0901_1053_gb300", "csrc", "kernels_step.cu"), "rb") as f:
+        return hashlib.sha256(f.read()).hexdigest()[:16]
+
+
+def profiled_traffic(name):
+    """DRAM bytes per launch from the committed ncu summary for this kernel
+    and workload; None if absent or taken on a different kernel source."""
+    path = os.path.join(ROOT, "profiles", name)
+    if not os.path.exists(path):
+        return None
+    txt = open(path).read()
+    m = re.search(r"traffic_bytes_per_launch:\s*([0-9.eE+]+)", txt)
+    h = re.search(r"kernel_source_sha256_16:\s*([0-9a-f]+)", txt)
+    if not m or not h or h.group(1) != kernel_source_hash():
+        return None
+    return float(m.group(1))
+
+
+# ---------------------------------------------------------------------------
+# CPU oracle (test infrastructure) on a bounded sample
+# ---------------------------------------------------------------------------
+def oracle_sample(w, planes, steps):
+    import dataclasses
+    from oracle import Oracle
+    sub = dataclasses.replace(w, nz=planes, pec=None if w.pec is None else w.pec[:planes].copy())
+    o = Oracle(sub.nx, sub.ny, sub.nz, sub.dx, sub.dy, sub.dz, sub.cdt, pec=sub.pec)
+    o.set_bunch(sub.sigma, sub.charge, sub.i0, sub.j0)
+    t0 = time.perf_counter()
+    o.step(steps)
+    dt = time.perf_counter() - t0
+    cells = sub.nx * sub.ny * sub.nz
+    return cells * steps / dt / 1e9, dt, "first %d of %d planes of %s (same transverse grid and " \
+        "geometry), %d steps, FP64, 1 thread" % (planes, w.nz, w.name, steps)
+
+
+def cpu_baseline(w):
+    planes = min(w.nz, 256 if w.nx * w.ny >= 256 * 256 else w.nz)
+    steps = 20 if w.nx * w.ny >= 256 * 256 else 400
+    v, dt, desc = oracle_sample(w, planes, steps)
+    return {"value": v, "unit": UNIT, "cores": 1, "kind": "oracle", "sample": desc,
+            "seconds": round(dt, 2)}
+
+
+def run_reference(args):
+    rank, world, _ = dist_env()
+    if rank != 0:
+        return 0
+    w = make_workload(args)
+    # bounded sample: each benchmark step is one oracle time step on the first
+    # planes of the workload, sized so the whole run stays around two minutes
+    budget_cells = 2.0e7 * 120.0 / max(1, args.steps + args.warmup)
+    planes = int(max(2, min(w.nz, budget_cells // (w.nx * w.ny))))
+    import dataclasses
+    from oracle import Oracle
+    sub = dataclasses.replace(w, nz=planes, pec=None if w.pec is None else w.pec[:planes].copy())
+    o = Oracle(sub.nx, sub.ny, sub.nz, sub.dx, sub.dy, sub.dz, sub.cdt, pec=sub.pec)
+    o.set_bunch(sub.sigma, sub.charge, sub.i0, sub.j0)
+    o.step(args.warmup)
+    t0 = time.perf_counter()
+    o.step(args.steps)
+    dt = time.perf_counter() - t0
+    cells = sub.nx * sub.ny * sub.nz
+    v = cells * args.steps / dt / 1e9
+    desc = "first %d of %d planes of %s, %d timed steps after %d warm-up steps, FP64, 1 thread" % (
+        planes, w.nz, w.name, args.steps, args.warmup)
+    line = {"metric": METRIC, "value": v, "unit": UNIT, "impl": "reference", "n_gpus": world,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": dt * 1e3 / args.steps,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+            "data": "synthetic", "config": {"workload": w.name, "sample_planes": planes},
+            "cpu_baseline": {"value": v, "unit": UNIT, "cores": 1, "kind": "oracle", "sample": desc},
+            "e2e": {"value": v, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+            "gpu_launches": 0}
+    print(json.dumps(line), flush=True)
+    return 0
+
+
+# ---------------------------------------------------------------------------
+# GPU arm
+# ---------------------------------------------------------------------------
+def run_tetm(args):
+    rank, world, local = dist_env()
+    import numpy as np
+    import torch
+    torch.cuda.set_device(local)
+    dist = Dist(world)
+    from paper_0901_1053_gb300 import tetm
+    w = make_workload(args)
+    stream = torch.cuda.current_stream()
+    s = tetm.Solver.from_workload(w)
+    s.set_stream(stream.cuda_stream)
+    s.set_kernel(args.kernel)
+    if args.tiling:
+        s.set_tiling(*[int(x) for x in args.tiling.split(",")])
+    s.set_balance_every(args.balance_every)
+    info = s.info()
+    s.step(args.warmup)
+    s.sync()
+
+    try:
+        uuid = torch.cuda.get_device_properties(local).uuid
+        uuid = str(uuid)
+    except Exception:
+        uuid = None
+    clocks = ClockSampler(uuid)
+    clocks.start()
+    time.sleep(0.5)
+    K = args.steps
+    evs = [torch.cuda.Event(enable_timing=True) for _ in range(K + 1)]
+    dist.barrier()
+    torch.cuda.synchronize()
+    n0 = s.info()["step"]
+    for i in range(K):
+        evs[i].record(stream)
+        s.step(1)
+    evs[K].record(stream)
+    torch.cuda.synchronize()
+    dist.barrier()
+    clk = clocks.stop()
+    total_ms = evs[0].elapsed_time(evs[K])
+    per = [evs[i].elapsed_time(evs[i + 1]) for i in range(K)]
+    be = args.balance_every
+    bal_steps = [i for i in range(K) if be > 0 and (n0 + i + 1) % be == 0]
+    plain = [per[i] for i in range(K) if i not in set(bal_steps)]
+    kern_ms = statistics.mean(plain) if plain else total_ms / K
+    max_ms = dist.max(total_ms)
+
+    esz = 4 if w.precision == "fp32" else 8
+    bytes_per_cell = 12 * esz + 1
+    proc = info["processed_cells"] if args.kernel == "fused" else w.cells
+    achieved = bytes_per_cell * proc / (kern_ms * 1e-3) / 1e9
+    peak, peak_kind = measured_peak_hbm()
+    prof_name = "fused_step_%s_%s.md" % (w.precision, w.name)
+    traffic = profiled_traffic(prof_name) if args.kernel == "fused" else None
+    wake = s.wake()[0]
+    hist = s.balance_history()
+    s.close()
+
+    e2e = None
+    if not args.no_e2e:
+        steps_e2e = args.e2e_steps or w.steps
+        pinned = None
+        if w.pec is not None:
+            pinned = torch.empty(w.pec.shape, dtype=torch.uint8, pin_memory=True).numpy()
+            pinned[...] = w.pec
+        out = torch.empty(len(wake), dtype=torch.float64, pin_memory=True).numpy()
+        dist.barrier()
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        s2 = tetm.Solver(w.nx, w.ny, w.nz, w.dx, w.dy, w.dz, w.cdt, w.precision, pec=pinned)
+        s2.set_bunch(w.sigma, w.charge, w.i0, w.j0)
+        s2.set_kernel(args.kernel)
+        if args.tiling:
+            s2.set_tiling(*[int(x) for x in args.tiling.split(",")])
+        s2.step(steps_e2e)
+        wk2 = s2.wake()[0]
+        out[:] = wk2
+        t1 = time.perf_counter()
+        s2.close()
+        e2e_s = dist.max(t1 - t0)
+        e2e = {"value": world * w.cells * steps_e2e / e2e_s / 1e9, "unit": UNIT,
+               "h2d_bytes_per_step": int(pinned.nbytes if pinned is not None else 0),
+               "d2h_bytes_per_step": int(out.nbytes), "steps_per_call": steps_e2e,
+               "seconds": round(e2e_s, 3),
+               "call": "tetm_create(host pec) + tetm_set_bunch + tetm_step + tetm_wake(host)"}
+
+    cpu = None
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        cpu = cpu_baseline(w)
+
+    value = world * w.cells * K / (max_ms * 1e-3) / 1e9
+    n_bal = len(bal_steps)
+    line = {
+        "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": K,
+        "warmup": args.warmup, "ms_per_step": max_ms / K, "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "f32" if w.precision == "fp32" else "f64",
+        "data": "synthetic",
+        "config": {"workload": w.name, "nx": w.nx, "ny": w.ny, "nz": w.nz,
+                   "dx_mm": round(w.dx * 1e3, 4), "dz_mm": w.dz * 1e3, "cdt": "dz",
+                   "sigma_dz": round(w.sigma / w.dz, 3), "fields": w.precision,
+                   "wake_and_balances": "f64", "balance_every": be, "kernel": args.kernel,
+                   "tiling": [info["tile_x"], info["tile_y"], info["chunk_z"]],
+                   "work_items": info["work_items"], "cells": w.cells,
+                   "active_cells": info["active_cells"], "processed_cells": proc,
+                   "l2": "inputs larger than L2 (two field sets of %.1f GB each)"
+                         % (12 * esz * w.cells / 2 / 1e9),
+                   "parallelism": "replicas x%d" % world},
+        "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
+                     "frac": achieved / peak, "traffic": traffic, "peak_kind": peak_kind,
+                     "kernel": "fused_step", "kernel_ms": kern_ms,
+                     "bytes_per_cell": bytes_per_cell, "cells_per_launch": proc},
+        "cpu_baseline": cpu,
+        "e2e": e2e,
+        "gpu_launches": K + 6 * n_bal if args.kernel == "fused" else 10 * K + 6 * n_bal,
+        "clocks": clk,
+        "balances": {"records": int(hist.shape[0]),
+                     "max_charge_residual_rel": float(np.max(hist[:, 2] / np.maximum(hist[:, 4], 1e-300)))
+                     if hist.shape[0] else None,
+                     "energy_last_J": float(hist[-1, 1]) if hist.shape[0] else None},
+    }
+    if rank == 0:
+        print(json.dumps(line), flush=True)
+    dist.close()
+    return 0
+
+
+def main():
+    args = parse_args()
+    if args.impl == "reference":
+        return run_reference(args)
+    return run_tetm(args)
+
+
+if __name__ == "__main__":
+    sys.exit(main())

@@ -149,6 +149,19 @@ int tetm_energy(tetm_solver* s, double* w);
  * (TETM_E_STATE). Valid for cold starts. Synchronizes. */
 int tetm_charge_residual(tetm_solver* s, double* max_e, double* max_h, double* q_scale);
 
+/* Periodic FP64 balances inside tetm_step (0 = off, the default): after
+ * every `every`-th step the solver queues, on its stream and without host
+ * synchronisation, the energy of tetm_energy and the charge residuals of
+ * tetm_charge_residual for the state just reached, as one record
+ * {n, W^{n,e}, max_e, max_h, q_scale} in a device ring of 4096 records
+ * (the oldest is overwritten). */
+int tetm_set_balance_every(tetm_solver* s, int32_t every);
+
+/* Copy the recorded balances, oldest first, 5 float64 per record, into
+ * out[cap] (cap counts records; cap below the record count gives
+ * TETM_E_ARG; out may be NULL to query the count *n). Synchronizes. */
+int tetm_balance_history(tetm_solver* s, double* out, int32_t cap, int32_t* n);
+
 /* Copy one component (TETM_EX..TETM_HZ) of the current state to / from a
  * host float64 array in the canonical FIT layout. Values on entries that
  * carry no field are ignored on input and zero on output. Both synchronize. */

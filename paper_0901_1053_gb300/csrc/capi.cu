@@ -216,6 +216,11 @@ struct tetm_solver {
   void* J;
   double* W;
   double* qline;
+  // periodic balances: records {n, W, max_e, max_h, q_scale}
+  int bal_every;
+  double* hist;
+  int hist_cap;
+  long long hist_count;
   // state
   long long step;
   bool prev_valid;
@@ -326,15 +331,38 @@ StepArgs<T> step_args(tetm_solver* s, bool fused) {
   return a;
 }
 
+// Queue the FP64 balances of the step just taken into device slots:
+// rec[0] = n, rec[1] = W^{n,e}, rec[2] = max|qe - qbunch|, rec[3] = max|qh|,
+// rec[4] = max|qbunch|. No host synchronisation.
+template <typename T>
+int queue_balances(tetm_solver* s, double* rec) {
+  const double zc = ((double)(s->step - 1) + 0.5 - s->c0) * s->g.dz;
+  CK(launch_bunch_charge(s->bunch ? s->q : 0.0, s->bunch ? s->sigma : 1.0, s->g.dz, zc, s->g.nz,
+                         s->qline, rec + 4, (double)s->step, rec, s->stream));
+  const T *cur[6], *prv[6];
+  const double* ma[6];
+  for (int c = 0; c < 6; ++c) {
+    cur[c] = (const T*)s->set[s->cur][c];
+    prv[c] = (const T*)s->set[1 - s->cur][c];
+    ma[c] = s->minv_a[c];
+  }
+  CK(launch_energy<T>(cur, s->mask, s->minv_c, ma, s->L, s->alpha, s->diag, rec + 1, s->stream));
+  CK(launch_charge<T>(cur, prv, s->mask, s->minv_c, ma, s->L, s->alpha,
+                      s->bunch ? s->qline : nullptr, s->i0, s->j0, s->diag, rec + 2, rec + 3,
+                      s->stream));
+  return TETM_OK;
+}
+
 template <typename T>
 int do_steps(tetm_solver* s, int n) {
   for (int q = 0; q < n; ++q) {
+    const bool bal = s->bal_every > 0 && (s->step + 1) % s->bal_every == 0;
     if (s->kernel == TETM_KERNEL_FUSED) {
       StepArgs<T> a = step_args<T>(s, true);
       if (s->n_work > 0) CK(launch_fused_step<T>(a, s->tile_x, s->tile_y, s->stream));
       s->cur = 1 - s->cur;
     } else {
-      if (q == n - 1) {  // keep y^n beside y^{n+1} for the charge balance
+      if (q == n - 1 || bal) {  // keep y^n beside y^{n+1} for the charge balance
         for (int c = 0; c < 6; ++c)
           CK(cudaMemcpyAsync(s->set[1 - s->cur][c], s->set[s->cur][c], (size_t)s->L.count * s->esz,
                              cudaMemcpyDeviceToDevice, s->stream));
@@ -343,6 +371,12 @@ int do_steps(tetm_solver* s, int n) {
       CK(launch_reference_step<T>(a, s->stream));
     }
     s->step += 1;
+    if (bal) {
+      double* rec = s->hist + 5 * (s->hist_count % s->hist_cap);
+      int rc = queue_balances<T>(s, rec);
+      if (rc) return rc;
+      s->hist_count += 1;
+    }
   }
   if (n > 0) s->prev_valid = true;
   return TETM_OK;
@@ -404,6 +438,7 @@ void free_all(tetm_solver* s) {
   cudaFree(s->qline);
   cudaFree(s->diag.part);
   cudaFree(s->diag.out);
+  cudaFree(s->hist);
   cudaFree(s->staging);
 }
 
@@ -485,6 +520,9 @@ int tetm_create(const tetm_grid* g, const double* eps_r, const double* mu_r, con
   if (rc == TETM_OK) rc = dalloc(s, (void**)&s->diag.part, sizeof(double) * 2048);
   if (rc == TETM_OK) rc = dalloc(s, (void**)&s->diag.out, sizeof(double) * 8);
   s->diag.cap = 2048;
+  s->hist_cap = 4096;
+  if (rc == TETM_OK) rc = dalloc(s, (void**)&s->hist, sizeof(double) * 5 * (size_t)s->hist_cap);
+  if (rc == TETM_OK) rc = dalloc(s, (void**)&s->qline, sizeof(double) * (size_t)(g->nz + 1));
   MinvOut mo;
   for (int c = 0; c < 6; ++c) mo.a[c] = nullptr;
   if (rc == TETM_OK && !uniform) {
@@ -626,10 +664,8 @@ int tetm_set_bunch(tetm_solver* s, double sigma_z, double charge, int32_t i0, in
   const int nw = m_max + c0 + 2;
   void* J = nullptr;
   double* W = nullptr;
-  double* ql = nullptr;
-  if (cudaMalloc(&J, s->esz * qc.size()) != cudaSuccess || cudaMalloc(&W, sizeof(double) * nw) != cudaSuccess ||
-      cudaMalloc(&ql, sizeof(double) * (size_t)(s->g.nz + 1)) != cudaSuccess) {
-    cudaFree(J); cudaFree(W); cudaFree(ql);
+  if (cudaMalloc(&J, s->esz * qc.size()) != cudaSuccess || cudaMalloc(&W, sizeof(double) * nw) != cudaSuccess) {
+    cudaFree(J); cudaFree(W);
     cudaGetLastError();
     return TETM_E_NOMEM;
   }
@@ -645,13 +681,12 @@ int tetm_set_bunch(tetm_solver* s, double sigma_z, double charge, int32_t i0, in
   }
   if (rc == TETM_OK && cudaMemset(W, 0, sizeof(double) * nw) != cudaSuccess) rc = TETM_E_CUDA;
   if (rc != TETM_OK) {
-    cudaFree(J); cudaFree(W); cudaFree(ql);
+    cudaFree(J); cudaFree(W);
     return rc;
   }
   s->J = J;
   s->W = W;
-  s->qline = ql;
-  s->device_bytes += (long long)(s->esz * qc.size() + sizeof(double) * (nw + s->g.nz + 1));
+  s->device_bytes += (long long)(s->esz * qc.size() + sizeof(double) * nw);
   s->qcell = qc;
   s->bunch = true;
   s->i0 = i0;
@@ -702,11 +737,11 @@ int tetm_energy(tetm_solver* s, double* w) {
   if (s->esz == 8) {
     const double* f[6];
     for (int c = 0; c < 6; ++c) f[c] = (const double*)s->set[s->cur][c];
-    e = launch_energy<double>(f, s->mask, s->minv_c, ma, s->L, s->alpha, s->diag, s->stream);
+    e = launch_energy<double>(f, s->mask, s->minv_c, ma, s->L, s->alpha, s->diag, s->diag.out, s->stream);
   } else {
     const float* f[6];
     for (int c = 0; c < 6; ++c) f[c] = (const float*)s->set[s->cur][c];
-    e = launch_energy<float>(f, s->mask, s->minv_c, ma, s->L, s->alpha, s->diag, s->stream);
+    e = launch_energy<float>(f, s->mask, s->minv_c, ma, s->L, s->alpha, s->diag, s->diag.out, s->stream);
   }
   CK(e);
   CK(cudaMemcpyAsync(w, s->diag.out, sizeof(double), cudaMemcpyDeviceToHost, s->stream));
@@ -717,47 +752,40 @@ int tetm_energy(tetm_solver* s, double* w) {
 int tetm_charge_residual(tetm_solver* s, double* max_e, double* max_h, double* q_scale) {
   if (!s) return TETM_E_ARG;
   if (!s->prev_valid || s->step < 1) return TETM_E_STATE;
-  double qmax = 0.0;
-  if (s->bunch) {
-    // bunch charge in each dual cell [z_k - dz/2, z_k + dz/2] at time n+1/2
-    const double dz = s->g.dz;
-    const double zc = ((double)(s->step - 1) + 0.5 - s->c0) * dz;
-    std::vector<double> ql((size_t)(s->g.nz + 1));
-    for (int k = 0; k <= s->g.nz; ++k) {
-      const double lo = std::max(k * dz - 0.5 * dz - zc, -5.0 * s->sigma);
-      const double hi = std::min(k * dz + 0.5 * dz - zc, 5.0 * s->sigma);
-      ql[(size_t)k] = hi > lo ? s->q * (phi(hi / s->sigma) - phi(lo / s->sigma)) : 0.0;
-      qmax = std::max(qmax, fabs(ql[(size_t)k]));
-    }
-    CK(cudaMemcpyAsync(s->qline, ql.data(), sizeof(double) * ql.size(), cudaMemcpyHostToDevice, s->stream));
-  }
-  const double* ma[6];
-  for (int c = 0; c < 6; ++c) ma[c] = s->minv_a[c];
-  cudaError_t e;
-  if (s->esz == 8) {
-    const double *cur[6], *prv[6];
-    for (int c = 0; c < 6; ++c) {
-      cur[c] = (const double*)s->set[s->cur][c];
-      prv[c] = (const double*)s->set[1 - s->cur][c];
-    }
-    e = launch_charge<double>(cur, prv, s->mask, s->minv_c, ma, s->L, s->alpha,
-                              s->bunch ? s->qline : nullptr, s->i0, s->j0, s->diag, s->stream);
-  } else {
-    const float *cur[6], *prv[6];
-    for (int c = 0; c < 6; ++c) {
-      cur[c] = (const float*)s->set[s->cur][c];
-      prv[c] = (const float*)s->set[1 - s->cur][c];
-    }
-    e = launch_charge<float>(cur, prv, s->mask, s->minv_c, ma, s->L, s->alpha,
-                             s->bunch ? s->qline : nullptr, s->i0, s->j0, s->diag, s->stream);
-  }
-  CK(e);
-  double h[2];
+  int rc = s->esz == 8 ? queue_balances<double>(s, s->diag.out) : queue_balances<float>(s, s->diag.out);
+  if (rc) return rc;
+  double h[5];
   CK(cudaMemcpyAsync(h, s->diag.out, sizeof(h), cudaMemcpyDeviceToHost, s->stream));
   CK(cudaStreamSynchronize(s->stream));
-  if (max_e) *max_e = h[0];
-  if (max_h) *max_h = h[1];
-  if (q_scale) *q_scale = qmax;
+  if (max_e) *max_e = h[2];
+  if (max_h) *max_h = h[3];
+  if (q_scale) *q_scale = h[4];
+  return TETM_OK;
+}
+
+int tetm_set_balance_every(tetm_solver* s, int32_t every) {
+  if (!s || every < 0) return TETM_E_ARG;
+  s->bal_every = every;
+  return TETM_OK;
+}
+
+int tetm_balance_history(tetm_solver* s, double* out, int32_t cap, int32_t* n_out) {
+  if (!s) return TETM_E_ARG;
+  const long long n = std::min<long long>(s->hist_count, s->hist_cap);
+  if (n_out) *n_out = (int32_t)n;
+  if (out && n > 0) {
+    if (cap < n) return TETM_E_ARG;
+    std::vector<double> h((size_t)(5 * s->hist_cap));
+    CK(cudaMemcpyAsync(h.data(), s->hist, sizeof(double) * h.size(), cudaMemcpyDeviceToHost, s->stream));
+    CK(cudaStreamSynchronize(s->stream));
+    const long long first = s->hist_count - n;
+    for (long long r = 0; r < n; ++r) {
+      const long long slot = (first + r) % s->hist_cap;
+      memcpy(out + 5 * r, h.data() + 5 * slot, 5 * sizeof(double));
+    }
+  } else {
+    CK(cudaStreamSynchronize(s->stream));
+  }
   return TETM_OK;
 }
 

@@ -200,11 +200,11 @@ int blocks_for(long long total, int cap) {
 template <typename T>
 cudaError_t launch_energy(const T* const f[6], const uint8_t* mask, const double* minv,
                           const double* const minv_a[6], const Layout& L, double alpha,
-                          const DiagScratch& s, cudaStream_t st) {
+                          const DiagScratch& s, double* result, cudaStream_t st) {
   const int nb = blocks_for((long long)L.nx * L.ny * L.nz, s.cap);
   energy_pass1<T><<<nb, kBlock, 0, st>>>(f[0], f[1], f[2], f[3], f[4], f[5],
                                           make_view(mask, minv, minv_a), L, alpha, s.part);
-  reduce_pass2<false><<<1, 1024, 0, st>>>(s.part, nb, s.out);
+  reduce_pass2<false><<<1, 1024, 0, st>>>(s.part, nb, result);
   return cudaGetLastError();
 }
 
@@ -212,7 +212,7 @@ template <typename T>
 cudaError_t launch_charge(const T* const cur[6], const T* const prev[6], const uint8_t* mask,
                           const double* minv, const double* const minv_a[6], const Layout& L,
                           double alpha, const double* qline, int i0, int j0,
-                          const DiagScratch& s, cudaStream_t st) {
+                          const DiagScratch& s, double* res_e, double* res_h, cudaStream_t st) {
   const int nb = blocks_for((long long)(L.nx + 1) * (L.ny + 1) * (L.nz + 1), s.cap / 2);
   ChargeFields cf;
   for (int c = 0; c < 6; ++c) {
@@ -221,24 +221,53 @@ cudaError_t launch_charge(const T* const cur[6], const T* const prev[6], const u
   }
   charge_pass1<T><<<nb, kBlock, 0, st>>>(cf, make_view(mask, minv, minv_a), L, alpha, qline,
                                           i0, j0, s.part, s.part + nb);
-  reduce_pass2<true><<<1, 1024, 0, st>>>(s.part, nb, s.out);
-  reduce_pass2<true><<<1, 1024, 0, st>>>(s.part + nb, nb, s.out + 1);
+  reduce_pass2<true><<<1, 1024, 0, st>>>(s.part, nb, res_e);
+  reduce_pass2<true><<<1, 1024, 0, st>>>(s.part + nb, nb, res_h);
+  return cudaGetLastError();
+}
+
+namespace {
+// Charge of the +-5 sigma truncated Gaussian inside [zc + lo, zc + hi] per
+// node: the closed form the charge law (35) telescopes to from a cold start.
+__global__ void bunch_charge_kernel(double q, double sigma, double dz, double zc, int nz,
+                                    double* ql, double* qmax, double tag, double* tag_out) {
+  double m = 0.0;
+  const double r2 = 0.70710678118654752440;  // 1/sqrt(2)
+  for (int k = threadIdx.x; k <= nz; k += blockDim.x) {
+    const double lo = fmax(k * dz - 0.5 * dz - zc, -5.0 * sigma);
+    const double hi = fmin(k * dz + 0.5 * dz - zc, 5.0 * sigma);
+    double v = 0.0;
+    if (q != 0.0 && hi > lo) v = q * 0.5 * (erfc(-hi / sigma * r2) - erfc(-lo / sigma * r2));
+    ql[k] = v;
+    m = fmax(m, fabs(v));
+  }
+  m = block_reduce<true>(m);
+  if (threadIdx.x == 0) {
+    *qmax = m;
+    if (tag_out) *tag_out = tag;
+  }
+}
+}  // namespace
+
+cudaError_t launch_bunch_charge(double q, double sigma, double dz, double zc, int nz, double* ql,
+                                double* qmax, double tag, double* tag_out, cudaStream_t st) {
+  bunch_charge_kernel<<<1, 1024, 0, st>>>(q, sigma, dz, zc, nz, ql, qmax, tag, tag_out);
   return cudaGetLastError();
 }
 
 template cudaError_t launch_energy<float>(const float* const[6], const uint8_t*, const double*,
                                           const double* const[6], const Layout&, double,
-                                          const DiagScratch&, cudaStream_t);
+                                          const DiagScratch&, double*, cudaStream_t);
 template cudaError_t launch_energy<double>(const double* const[6], const uint8_t*, const double*,
                                            const double* const[6], const Layout&, double,
-                                           const DiagScratch&, cudaStream_t);
+                                           const DiagScratch&, double*, cudaStream_t);
 template cudaError_t launch_charge<float>(const float* const[6], const float* const[6],
                                           const uint8_t*, const double*, const double* const[6],
                                           const Layout&, double, const double*, int, int,
-                                          const DiagScratch&, cudaStream_t);
+                                          const DiagScratch&, double*, double*, cudaStream_t);
 template cudaError_t launch_charge<double>(const double* const[6], const double* const[6],
                                            const uint8_t*, const double*, const double* const[6],
                                            const Layout&, double, const double*, int, int,
-                                           const DiagScratch&, cudaStream_t);
+                                           const DiagScratch&, double*, double*, cudaStream_t);
 
 }  // namespace tetm

@@ -19,16 +19,17 @@ constexpr double kMu0 = 1.0 / (kEps0 * kC * kC);
 constexpr int kEX = 0, kEY = 1, kEZ = 2, kHX = 3, kHY = 4, kHZ = 5;
 
 // Device layout of every per-node array (fields, mask, coefficients):
-// planes k = -1..nz, rows j = -2..ny+1, columns i = -ox..px-ox-1, x fastest.
-// Index (i, j, k) of the canonical FIT layout maps to idx(i, j, k); the guard
-// entries around the canonical range are zero and inactive, so stencils read
-// them without bounds checks (P_x at i = nx reads the zero at i = nx + ... ).
+// planes k = -1..nz+1, rows j = -2..ny+1, columns i = -ox..px-ox-1, x fastest.
+// Index (i, j, k) of the canonical FIT layout maps to idx(i, j, k). All
+// entries outside the cells (index nx, ny or nz and the guard ring around)
+// hold zero and are inactive, so every stencil and prefetch reads them
+// without bounds checks.
 struct Layout {
   int nx, ny, nz;
   int ox;            // column of i = 0 (16-byte aligned)
   long long px;      // row pitch in elements
   long long sz;      // plane stride in elements, (ny + 4) * px
-  long long count;   // elements per array, (nz + 2) * sz
+  long long count;   // elements per array, (nz + 3) * sz
   __host__ __device__ __forceinline__ long long idx(int i, int j, int k) const {
     return ((long long)(k + 1) * (ny + 4) + (j + 2)) * px + (i + ox);
   }
@@ -85,17 +86,24 @@ struct DiagScratch {
   double* out;    // device result slots (at least 4)
 };
 
-// Discrete energy W^{n,e}; minv[c] constants (mask mode) or minv_a[c] arrays.
+// Discrete energy W^{n,e} into *result (device); minv[c] constants (mask
+// mode) or minv_a[c] arrays.
 template <typename T>
 cudaError_t launch_energy(const T* const f[6], const uint8_t* mask, const double* minv,
                           const double* const minv_a[6], const Layout& L, double alpha,
-                          const DiagScratch& s, cudaStream_t st);
+                          const DiagScratch& s, double* result, cudaStream_t st);
 
-// Charge residuals of the last step: out[0] = max|qe - qbunch|, out[1] = max|qh|.
+// Charge residuals of the last step into device slots: *res_e = max|qe - qbunch|,
+// *res_h = max|qh|.
 template <typename T>
 cudaError_t launch_charge(const T* const cur[6], const T* const prev[6], const uint8_t* mask,
                           const double* minv, const double* const minv_a[6], const Layout& L,
                           double alpha, const double* qline, int i0, int j0,
-                          const DiagScratch& s, cudaStream_t st);
+                          const DiagScratch& s, double* res_e, double* res_h, cudaStream_t st);
+
+// Truncated Gaussian bunch charge in the dual cell of each node k = 0..nz of
+// the bunch line at bunch-centre position zc; *qmax = max |ql[k]|; *tag = tag.
+cudaError_t launch_bunch_charge(double q, double sigma, double dz, double zc, int nz, double* ql,
+                                double* qmax, double tag, double* tag_out, cudaStream_t st);
 
 }  // namespace tetm

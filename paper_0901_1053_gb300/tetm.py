@@ -35,7 +35,8 @@ COMPONENTS = ("ex", "ey", "ez", "hx", "hy", "hz")
 EXPORTS = ("tetm_create", "tetm_set_bunch", "tetm_step", "tetm_sync", "tetm_wake",
            "tetm_destroy", "tetm_energy", "tetm_charge_residual", "tetm_get_fields",
            "tetm_set_fields", "tetm_set_stream", "tetm_set_kernel", "tetm_set_tiling",
-           "tetm_get_info", "tetm_bytes_needed", "tetm_save", "tetm_load", "tetm_strerror")
+           "tetm_get_info", "tetm_bytes_needed", "tetm_save", "tetm_load", "tetm_strerror",
+           "tetm_set_balance_every", "tetm_balance_history")
 
 
 class tetm_grid(ctypes.Structure):
@@ -81,6 +82,8 @@ def _load():
         "tetm_save": (ctypes.c_int, [vp, vp, ctypes.c_size_t, ctypes.POINTER(ctypes.c_size_t)]),
         "tetm_load": (ctypes.c_int, [vp, vp, ctypes.c_size_t]),
         "tetm_strerror": (ctypes.c_char_p, [ctypes.c_int]),
+        "tetm_set_balance_every": (ctypes.c_int, [vp, i32]),
+        "tetm_balance_history": (ctypes.c_int, [vp, vp, i32, ctypes.POINTER(i32)]),
     }
     for name, (res, args) in sig.items():
         f = getattr(lib, name)
@@ -191,6 +194,19 @@ class Solver:
         _check(lib.tetm_charge_residual(self.h, ctypes.byref(e), ctypes.byref(h), ctypes.byref(q)),
                "tetm_charge_residual")
         return e.value, h.value, q.value
+
+    def set_balance_every(self, every):
+        _check(lib.tetm_set_balance_every(self.h, int(every)), "tetm_set_balance_every")
+
+    def balance_history(self):
+        """Array (n, 5): step, energy, max_e, max_h, q_scale per record."""
+        n = ctypes.c_int32()
+        _check(lib.tetm_balance_history(self.h, None, 0, ctypes.byref(n)), "tetm_balance_history")
+        out = np.zeros((n.value, 5), dtype=np.float64)
+        if n.value:
+            _check(lib.tetm_balance_history(self.h, _ptr(out), n.value, ctypes.byref(n)),
+                   "tetm_balance_history")
+        return out
 
     def get(self, comp):
         out = np.empty(self.shape, dtype=np.float64)

@@ -48,9 +48,16 @@ def rel_err(a, b):
 
 
 def compare_fields(s, o, tol):
-    for c in ("ex", "ey", "ez", "hx", "hy", "hz"):
-        g, r = s.get(c), o.get(c)
-        assert rel_err(g, r) <= tol, (c, rel_err(g, r))
+    """Entry-wise comparison, scaled by the peak of the field family (E or H):
+    a component that vanishes by symmetry (hz for a centred bunch in a square
+    pipe) holds only rounding noise on both sides."""
+    g = {c: s.get(c) for c in ("ex", "ey", "ez", "hx", "hy", "hz")}
+    r = {c: o.get(c) for c in g}
+    for fam in (("ex", "ey", "ez"), ("hx", "hy", "hz")):
+        peak = max(np.max(np.abs(r[c])) for c in fam)
+        for c in fam:
+            err = float(np.max(np.abs(g[c] - r[c])) / peak)
+            assert err <= tol, (c, err)
 
 
 @pytest.mark.parametrize("kernel", ["fused", "reference"])
@@ -238,9 +245,12 @@ def test_full_size_collimator_head_matches_oracle(tetm, precision, tol):
     s.step(n)
     head = dataclasses.replace(w, nz=80, pec=w.pec[:80].copy(), steps=n)
     o = oracle_run(head, steps=n)
-    for c in ("ex", "ey", "ez", "hx", "hy", "hz"):
-        g = s.get(c)
-        assert np.all(g[n + 2:] == 0.0), c
-        r = o.get(c)
-        assert rel_err(g[:n + 1], r[:n + 1]) <= tol, (c, rel_err(g[:n + 1], r[:n + 1]))
+    g = {c: s.get(c) for c in ("ex", "ey", "ez", "hx", "hy", "hz")}
+    r = {c: o.get(c) for c in g}
+    for fam in (("ex", "ey", "ez"), ("hx", "hy", "hz")):
+        peak = max(np.max(np.abs(r[c][:n + 1])) for c in fam)
+        for c in fam:
+            assert np.all(g[c][n + 2:] == 0.0), c
+            err = float(np.max(np.abs(g[c][:n + 1] - r[c][:n + 1])) / peak)
+            assert err <= tol, (c, err)
     assert rel_err(s.wake()[0], o.wake()[0]) <= (1e-4 if precision == "fp32" else 1e-11)
