@@ -55,15 +55,17 @@ def parse_args():
     p.add_argument("--no-e2e", action="store_true")
     p.add_argument("--no-cpu-baseline", action="store_true")
     p.add_argument("--e2e-steps", type=int, default=0, help="0 = the workload's full step count")
+    p.add_argument("--nz", type=int, default=0,
+                   help="smaller case of the same workload (profiling): number of z cells")
     return p.parse_args()
 
 
 def make_workload(args):
     from paper_0901_1053_gb300 import workloads as wl
     if args.workload == "plain_pipe":
-        w = wl.plain_pipe()
+        w = wl.plain_pipe(nz=args.nz or 96)
     else:
-        w = wl.step_collimator()
+        w = wl.step_collimator(nz=args.nz or 2048)
     if args.precision:
         w.precision = args.precision
     return w
