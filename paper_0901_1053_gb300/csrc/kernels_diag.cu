@@ -11,7 +11,7 @@ namespace tetm {
 namespace {
 
 constexpr int kBlock = 256;
-constexpr int kMaxBlocks = 1024;
+constexpr int kMaxBlocks = 2048;
 
 __device__ __forceinline__ double warp_sum(double v) {
   for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(0xffffffffu, v, o);
@@ -39,11 +39,20 @@ __device__ double block_reduce(double v) {
 
 struct MinvView {
   const uint8_t* mask;
-  double c[6];
-  const double* a[6];
+  double c[6];          // M^-1 constants (uniform material)
+  double r[6];          // their reciprocals M = 1/M^-1
+  const double* a[6];   // per-entry M^-1 (material runs) or nullptr
   __device__ __forceinline__ double operator()(int comp, long long id) const {
     if (a[comp]) return a[comp][id];
     return ((mask[id] >> comp) & 1) ? c[comp] : 0.0;
+  }
+  // M = 1/M^-1 of an active entry (0 for inactive ones)
+  __device__ __forceinline__ double m(int comp, long long id) const {
+    if (a[comp]) {
+      const double v = a[comp][id];
+      return v != 0.0 ? 1.0 / v : 0.0;
+    }
+    return ((mask[id] >> comp) & 1) ? r[comp] : 0.0;
   }
 };
 
@@ -63,6 +72,7 @@ __global__ void energy_pass1(const T* __restrict__ ex, const T* __restrict__ ey,
     const int j = (int)((q / L.nx) % L.ny);
     const int k = (int)(q / ((long long)L.nx * L.ny));
     const long long id = L.idx(i, j, k);
+    if (mv.mask[id] == 0) continue;  // no field object here: every term is zero
     const T* f[6] = {ex, ey, ez, hx, hy, hz};
     double w = 0.0;
     double mi[6];
@@ -70,7 +80,7 @@ __global__ void energy_pass1(const T* __restrict__ ex, const T* __restrict__ ey,
       mi[c] = mv(c, id);
       if (mi[c] != 0.0) {
         const double v = (double)f[c][id];
-        w += 0.5 * v * v / mi[c];
+        w += 0.5 * v * v * mv.m(c, id);
       }
     }
     const double pyez = (double)ez[id + sy] - (double)ez[id];
@@ -100,8 +110,7 @@ __global__ void reduce_pass2(const double* part, int n, double* out) {
 template <typename T>
 __device__ __forceinline__ double dbar(const T* f1, const T* f0, const MinvView& mv, int comp,
                                        long long e) {
-  const double mi = mv(comp, e);
-  return mi != 0.0 ? 0.5 * ((double)f1[e] + (double)f0[e]) / mi : 0.0;
+  return 0.5 * ((double)f1[e] + (double)f0[e]) * mv.m(comp, e);
 }
 template <typename T>
 __device__ __forceinline__ double dz_tilde(const T* ez, const MinvView& mv, long long e,
@@ -111,13 +120,12 @@ __device__ __forceinline__ double dz_tilde(const T* ez, const MinvView& mv, long
   auto t1 = [&](long long f) { return mv(kHX, f) * ((double)ez[f + sy] - (double)ez[f]); };
   auto t2 = [&](long long f) { return mv(kHY, f) * ((double)ez[f + sx] - (double)ez[f]); };
   const double r = (t1(e - sy) - t1(e)) + (t2(e - sx) - t2(e));
-  return (double)ez[e] / mi - a2 * r;
+  return (double)ez[e] * mv.m(kEZ, e) - a2 * r;
 }
 template <typename T>
 __device__ __forceinline__ double bbar(const T* f1, const T* f0, const MinvView& mv, int comp,
                                        long long f) {
-  const double mi = mv(comp, f);
-  return mi != 0.0 ? 0.5 * ((double)f1[f] + (double)f0[f]) / mi : 0.0;
+  return 0.5 * ((double)f1[f] + (double)f0[f]) * mv.m(comp, f);
 }
 template <typename T>
 __device__ __forceinline__ double bz_tilde(const T* hz, const MinvView& mv, long long f,
@@ -127,7 +135,7 @@ __device__ __forceinline__ double bz_tilde(const T* hz, const MinvView& mv, long
   auto t3 = [&](long long e) { return mv(kEX, e) * ((double)hz[e - sy] - (double)hz[e]); };
   auto t4 = [&](long long e) { return mv(kEY, e) * ((double)hz[e - sx] - (double)hz[e]); };
   const double r = (t3(f + sy) - t3(f)) + (t4(f + sx) - t4(f));
-  return (double)hz[f] / mi - a2 * r;
+  return (double)hz[f] * mv.m(kHZ, f) - a2 * r;
 }
 
 struct ChargeFields {
@@ -150,8 +158,10 @@ __global__ void charge_pass1(ChargeFields cf, MinvView mv, Layout L, double alph
     const int j = (int)((q / (L.nx + 1)) % (L.ny + 1));
     const int k = (int)(q / ((long long)(L.nx + 1) * (L.ny + 1)));
     const long long n = L.idx(i, j, k);
+    const uint8_t m0 = mv.mask[n];
+    if (m0 == 0) continue;  // neither the node's edges nor the cell's faces start here
     // Eq. (35) at node n: six incident edges active
-    if (mv(kEX, n) != 0.0 && mv(kEX, n - sx) != 0.0 && mv(kEY, n) != 0.0 &&
+    if ((m0 & 7) == 7 && mv(kEX, n) != 0.0 && mv(kEX, n - sx) != 0.0 && mv(kEY, n) != 0.0 &&
         mv(kEY, n - sy) != 0.0 && mv(kEZ, n) != 0.0 && mv(kEZ, n - sz) != 0.0) {
       const double qe =
           -(dbar(cur[kEX], prv[kEX], mv, kEX, n - sx) - dbar(cur[kEX], prv[kEX], mv, kEX, n)) -
@@ -161,7 +171,7 @@ __global__ void charge_pass1(ChargeFields cf, MinvView mv, Layout L, double alph
       me = fmax(me, fabs(qe - qb));
     }
     // Eq. (34) at the cell whose lower node is n: six faces active
-    if (mv(kHX, n) != 0.0 && mv(kHX, n + sx) != 0.0 && mv(kHY, n) != 0.0 &&
+    if ((m0 & 56) == 56 && mv(kHX, n) != 0.0 && mv(kHX, n + sx) != 0.0 && mv(kHY, n) != 0.0 &&
         mv(kHY, n + sy) != 0.0 && mv(kHZ, n) != 0.0 && mv(kHZ, n + sz) != 0.0) {
       const double qh =
           (bbar(cur[kHX], prv[kHX], mv, kHX, n + sx) - bbar(cur[kHX], prv[kHX], mv, kHX, n)) +
@@ -183,6 +193,7 @@ MinvView make_view(const uint8_t* mask, const double* minv, const double* const 
   v.mask = mask;
   for (int c = 0; c < 6; ++c) {
     v.c[c] = minv ? minv[c] : 0.0;
+    v.r[c] = (minv && minv[c] != 0.0) ? 1.0 / minv[c] : 0.0;
     v.a[c] = minv_a ? minv_a[c] : nullptr;
   }
   return v;
