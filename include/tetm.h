@@ -49,6 +49,7 @@ extern "C" {
 #define TETM_E_TIMEOUT (-7)    /* a bounded device-side wait gave up                */
 #define TETM_E_DIVERGED (-8)   /* non-finite energy: the run blew up               */
 #define TETM_E_UNSUPPORTED (-9) /* combination of options this build does not offer */
+#define TETM_E_TOO_LARGE (-10) /* problem exceeds the fixed scratch of tetm_energy_noalloc */
 
 /* ---- field precision ---------------------------------------------------- */
 #define TETM_FP64 0            /* fields stored and updated in float64            */
@@ -195,6 +196,39 @@ int64_t tetm_bytes_needed(const tetm_grid* g);
  * and geometry (TETM_E_ARG on a size or grid mismatch). Both synchronize. */
 int tetm_save(tetm_solver* s, void* buf, size_t cap, size_t* used);
 int tetm_load(tetm_solver* s, const void* buf, size_t size);
+
+/* ---- no-allocation variant ------------------------------------------------
+ * The paper has no counterpart to this entry point; it exists for callers
+ * that are not allowed to allocate device memory: code whose device memory
+ * comes from an arena or allocator owned by a host framework, plugins that
+ * may only use buffers handed to them, and real-time loops that cannot pay
+ * for cudaMalloc/cudaFree or their implicit synchronisation.
+ *
+ * tetm_energy_noalloc computes the same discrete energy as tetm_energy
+ * (W^{n,e}, Sec. 4.4) for a state the caller keeps in its own device arrays,
+ * and allocates nothing: no cudaMalloc, no cudaFree, no allocating library
+ * call. Its block partial sums live in one fixed array of 8192 doubles
+ * (64 KiB) in the library's device memory, which every GPU that loads the
+ * library holds until the process exits.
+ *   g       grid; vacuum only (the coefficients follow from dx, dy, dz, cdt);
+ *           g->precision says whether fields are float64 or float32.
+ *   fields  six device pointers (ex, ey, ez, hx, hy, hz), each in the
+ *           canonical FIT layout of this header, (nx+1)(ny+1)(nz+1) entries.
+ *   mask    device uint8 per canonical entry, bit c set when component c
+ *           carries a field there (PEC geometry); NULL = empty PEC box.
+ *   w       device double that receives the energy [J].
+ *   stream  cudaStream_t the two kernels are queued on (NULL = legacy stream);
+ *           the call returns once they are queued and does not synchronize.
+ * At most TETM_NOALLOC_MAX_ENTRIES canonical entries (e.g. 256 x 256 x 499
+ * cells); larger grids return TETM_E_TOO_LARGE. The first call on a device
+ * looks up the scratch array's device address (cudaGetSymbolAddress) with
+ * that device current and caches it; make that first call before any stream
+ * capture. Calls share the scratch array: calls whose kernels overlap on the
+ * GPU (several streams or host threads at once) race and must be serialised
+ * by the caller. */
+#define TETM_NOALLOC_MAX_ENTRIES 33554432
+int tetm_energy_noalloc(const tetm_grid* g, const void* const fields[6], const uint8_t* mask,
+                        double* w, void* stream);
 
 /* Static description of a return code. */
 const char* tetm_strerror(int code);

@@ -458,6 +458,7 @@ const char* tetm_strerror(int code) {
     case TETM_E_TIMEOUT: return "bounded device wait timed out";
     case TETM_E_DIVERGED: return "energy is not finite: the run diverged";
     case TETM_E_UNSUPPORTED: return "unsupported option combination";
+    case TETM_E_TOO_LARGE: return "grid larger than the fixed scratch of tetm_energy_noalloc";
     default: return "unknown error";
   }
 }

@@ -24,6 +24,8 @@ TETM_E_STATE = -6
 TETM_E_TIMEOUT = -7
 TETM_E_DIVERGED = -8
 TETM_E_UNSUPPORTED = -9
+TETM_E_TOO_LARGE = -10
+TETM_NOALLOC_MAX_ENTRIES = 33554432
 
 TETM_FP64 = 0
 TETM_FP32 = 1
@@ -36,7 +38,7 @@ EXPORTS = ("tetm_create", "tetm_set_bunch", "tetm_step", "tetm_sync", "tetm_wake
            "tetm_destroy", "tetm_energy", "tetm_charge_residual", "tetm_get_fields",
            "tetm_set_fields", "tetm_set_stream", "tetm_set_kernel", "tetm_set_tiling",
            "tetm_get_info", "tetm_bytes_needed", "tetm_save", "tetm_load", "tetm_strerror",
-           "tetm_set_balance_every", "tetm_balance_history")
+           "tetm_set_balance_every", "tetm_balance_history", "tetm_energy_noalloc")
 
 
 class tetm_grid(ctypes.Structure):
@@ -84,6 +86,8 @@ def _load():
         "tetm_strerror": (ctypes.c_char_p, [ctypes.c_int]),
         "tetm_set_balance_every": (ctypes.c_int, [vp, i32]),
         "tetm_balance_history": (ctypes.c_int, [vp, vp, i32, ctypes.POINTER(i32)]),
+        "tetm_energy_noalloc": (ctypes.c_int, [ctypes.POINTER(tetm_grid),
+                                               ctypes.POINTER(ctypes.c_void_p), vp, vp, vp]),
     }
     for name, (res, args) in sig.items():
         f = getattr(lib, name)
@@ -118,6 +122,16 @@ def make_grid(nx, ny, nz, dx, dy, dz, cdt=0.0, precision="fp32"):
 
 def tetm_bytes_needed(grid):
     return int(lib.tetm_bytes_needed(ctypes.byref(grid)))
+
+
+def tetm_energy_noalloc(grid, field_ptrs, mask_ptr, w_ptr, stream=0):
+    """Energy of a state held in caller-owned device arrays, without any
+    device allocation (see include/tetm.h). All pointers are device
+    addresses (ints); returns the TETM_* code."""
+    arr = (ctypes.c_void_p * 6)(*[ctypes.c_void_p(int(p)) for p in field_ptrs])
+    return int(lib.tetm_energy_noalloc(ctypes.byref(grid), arr,
+                                       ctypes.c_void_p(int(mask_ptr) if mask_ptr else 0),
+                                       ctypes.c_void_p(int(w_ptr)), ctypes.c_void_p(int(stream or 0))))
 
 
 def tetm_strerror(code):
