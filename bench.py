@@ -57,13 +57,15 @@ def parse_args():
     p.add_argument("--e2e-steps", type=int, default=0, help="0 = the workload's full step count")
     p.add_argument("--nz", type=int, default=0,
                    help="smaller case of the same workload (profiling): number of z cells")
+    p.add_argument("--n", type=int, default=0,
+                   help="plain_pipe only: transverse cells (profiling a fully active box)")
     return p.parse_args()
 
 
 def make_workload(args):
     from paper_0901_1053_gb300 import workloads as wl
     if args.workload == "plain_pipe":
-        w = wl.plain_pipe(nz=args.nz or 96)
+        w = wl.plain_pipe(nz=args.nz or 96, n=args.n or 24)
     else:
         w = wl.step_collimator(nz=args.nz or 2048)
     if args.precision:
@@ -179,8 +181,12 @@ def measured_peak_hbm():
 
 
 def kernel_source_hash():
-    with open(os.path.join(ROOT, "paper_0901_1053_gb300", "csrc", "kernels_step.cu"), "rb") as f:
-        return hashlib.sha256(f.read()).hexdigest()[:16]
+    """Hash of the step-kernel sources (both tilings' translation units)."""
+    h = hashlib.sha256()
+    for name in ("kernels_step.cu", "kernels_warp.cu"):
+        with open(os.path.join(ROOT, "paper_0901_1053_gb300", "csrc", name), "rb") as f:
+            h.update(f.read())
+    return h.hexdigest()[:16]
 
 
 def profiled_traffic(name):
@@ -310,7 +316,8 @@ def run_tetm(args):
     proc = info["processed_cells"] if args.kernel == "fused" else w.cells
     achieved = bytes_per_cell * proc / (kern_ms * 1e-3) / 1e9
     peak, peak_kind = measured_peak_hbm()
-    prof_name = "fused_step_%s_%s.md" % (w.precision, w.name)
+    kname = "fused_step_warp" if info["tile_x"] == 28 else "fused_step"
+    prof_name = "%s_%s_%s.md" % (kname, w.precision, w.name)
     traffic = profiled_traffic(prof_name) if args.kernel == "fused" else None
     wake = s.wake()[0]
     hist = s.balance_history()
@@ -367,7 +374,7 @@ def run_tetm(args):
                    "parallelism": "replicas x%d" % world},
         "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
                      "frac": achieved / peak, "traffic": traffic, "peak_kind": peak_kind,
-                     "kernel": "fused_step", "kernel_ms": kern_ms,
+                     "kernel": kname, "kernel_ms": kern_ms,
                      "bytes_per_cell": bytes_per_cell, "cells_per_launch": proc},
         "cpu_baseline": cpu,
         "e2e": e2e,

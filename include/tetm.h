@@ -178,9 +178,12 @@ int tetm_set_stream(tetm_solver* s, void* cuda_stream);
  * plus PEC); otherwise TETM_E_UNSUPPORTED. */
 int tetm_set_kernel(tetm_solver* s, int32_t kernel);
 
-/* Fused-kernel block shape: transverse tile tile_x x tile_y (tile_x in
- * {32, 64}, tile_y in {4, 8, 16}) and z-chunk length chunk_z >= 4. Any
- * value 0 keeps the current one. TETM_E_ARG for other values. */
+/* Fused-kernel work shape: transverse tile tile_x x tile_y and z-chunk
+ * length chunk_z >= 4 of one work item. tile_x = 28 selects the warp-tiled
+ * kernel (one warp per item, tile_y in {4, 8, 12, 16, 20, 28}; the default
+ * is 28 x 20 x 32); tile_x = 32 (tile_y in {4, 8, 16}) or 64 (tile_y in
+ * {4, 8}) selects the block-tiled kernel. Any value 0 keeps the current one.
+ * TETM_E_ARG for other values. */
 int tetm_set_tiling(tetm_solver* s, int32_t tile_x, int32_t tile_y, int32_t chunk_z);
 
 /* Snapshot of the solve's bookkeeping. */

@@ -6,7 +6,7 @@ loads the library and fails loudly if it has not been built. ``workloads``
 holds the seeded synthetic inputs and imports nothing else from here.
 """
 
-__all__ = ["tetm", "workloads"]
+__all__ = ["tetm", "workloads", "sharding"]
 
 
 def __getattr__(name):

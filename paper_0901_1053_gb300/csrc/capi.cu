@@ -23,7 +23,8 @@ Layout make_layout(int nx, int ny, int nz, int elem_bytes) {
   L.nz = nz;
   L.ox = 16 / elem_bytes;                          // i = 0 on a 16-byte boundary, >= 2 guards
   const int align = 32 / elem_bytes;               // rows on 32-byte sectors
-  long long px = L.ox + nx + 2;
+  long long px = L.ox + nx + 3;                    // >= 2 zero columns past nx, plus one
+                                                   // so a column pair starting at nx + 1 stays in the row
   px = (px + align - 1) / align * align;
   L.px = px;
   L.sz = (long long)(ny + 4) * px;
@@ -359,7 +360,12 @@ int do_steps(tetm_solver* s, int n) {
     const bool bal = s->bal_every > 0 && (s->step + 1) % s->bal_every == 0;
     if (s->kernel == TETM_KERNEL_FUSED) {
       StepArgs<T> a = step_args<T>(s, true);
-      if (s->n_work > 0) CK(launch_fused_step<T>(a, s->tile_x, s->tile_y, s->stream));
+      if (s->n_work > 0) {
+        if (warp_shape_ok(s->tile_x, s->tile_y))
+          CK(launch_fused_warp_step<T>(a, s->tile_x, s->tile_y, s->stream));
+        else
+          CK(launch_fused_step<T>(a, s->tile_x, s->tile_y, s->stream));
+      }
       s->cur = 1 - s->cur;
     } else {
       if (q == n - 1 || bal) {  // keep y^n beside y^{n+1} for the charge balance
@@ -506,9 +512,9 @@ int tetm_create(const tetm_grid* g, const double* eps_r, const double* mu_r, con
   s->stream = nullptr;
   s->kernel = uniform ? TETM_KERNEL_FUSED : TETM_KERNEL_REFERENCE;
   s->uniform = uniform;
-  s->tile_x = 32;
-  s->tile_y = 8;
-  s->chunk_z = 64;
+  s->tile_x = 28;   // warp-tiled kernel (kernels_warp.cu)
+  s->tile_y = 20;
+  s->chunk_z = 32;
   int rc = TETM_OK;
   const size_t fbytes = (size_t)s->L.count * s->esz;
   for (int b = 0; b < 2 && rc == TETM_OK; ++b)
@@ -639,7 +645,7 @@ int tetm_set_tiling(tetm_solver* s, int32_t tile_x, int32_t tile_y, int32_t chun
   const int tx = tile_x ? tile_x : s->tile_x;
   const int ty = tile_y ? tile_y : s->tile_y;
   const int cz = chunk_z ? chunk_z : s->chunk_z;
-  if (!fused_shape_ok(tx, ty) || cz < 4) return TETM_E_ARG;
+  if ((!fused_shape_ok(tx, ty) && !warp_shape_ok(tx, ty)) || cz < 4) return TETM_E_ARG;
   if (tx == s->tile_x && ty == s->tile_y && cz == s->chunk_z && s->work) return TETM_OK;
   s->tile_x = tx;
   s->tile_y = ty;

@@ -78,6 +78,10 @@ cudaError_t launch_reference_step(const StepArgs<T>& a, cudaStream_t st);
 template <typename T>
 cudaError_t launch_fused_step(const StepArgs<T>& a, int tile_x, int tile_y, cudaStream_t st);
 bool fused_shape_ok(int tile_x, int tile_y);
+// ---- warp-tiled fused step (kernels_warp.cu): tile 28 x tile_y ----------
+template <typename T>
+cudaError_t launch_fused_warp_step(const StepArgs<T>& a, int tile_x, int tile_y, cudaStream_t st);
+bool warp_shape_ok(int tile_x, int tile_y);
 
 // ---- diagnostics (kernels_diag.cu) ----------------------------------------
 struct DiagScratch {

@@ -254,3 +254,92 @@ def test_full_size_collimator_head_matches_oracle(tetm, precision, tol):
             err = float(np.max(np.abs(g[c][:n + 1] - r[c][:n + 1])) / peak)
             assert err <= tol, (c, err)
     assert rel_err(s.wake()[0], o.wake()[0]) <= (1e-4 if precision == "fp32" else 1e-11)
+
+
+# ---------------------------------------------------------------------------
+# Warp-tiled fused kernel (tile 28 x TY, one warp per tile and z-chunk)
+# ---------------------------------------------------------------------------
+
+WARP_TILINGS = [(28, 4, 64), (28, 12, 5), (28, 20, 16), (28, 28, 64), (28, 12, 128)]
+
+
+@pytest.mark.parametrize("tiling", WARP_TILINGS)
+@pytest.mark.parametrize("dims", [(40, 36, 70), (33, 18, 9), (61, 23, 40)])
+def test_warp_kernel_matches_oracle(tetm, tiling, dims):
+    nx, ny, nz = dims
+    w = wl.scaled_collimator(max(nx, ny), nz, sigma_cells=2.5)
+    w.nx, w.ny = nx, ny
+    w.pec = wl.radius_mask(nx, ny, nz, wl.collimator_radius(nz, 0.45 * min(nx, ny),
+                                                             0.2 * min(nx, ny), nz // 4, nz // 2))
+    w.i0, w.j0 = nx // 2, ny // 2
+    w.steps = nz + 25
+    s = tetm.Solver(w.nx, w.ny, w.nz, w.dx, w.dy, w.dz, w.cdt, "fp64", pec=w.pec)
+    s.set_tiling(*tiling)
+    rng = np.random.default_rng(7 + sum(dims))
+    init = {c: rng.standard_normal(s.shape) for c in ("ex", "ey", "ez", "hx", "hy", "hz")}
+    for c, a in init.items():
+        s.set(c, a)
+    s.set_bunch(w.sigma, w.charge, w.i0, w.j0)
+    s.step(w.steps)
+    o = oracle_run(w, fields=init)
+    compare_fields(s, o, TOL64)
+    assert rel_err(s.wake()[0], o.wake()[0]) <= 1e-11
+
+
+def test_warp_tilings_are_bitwise_identical(tetm):
+    w = wl.scaled_collimator(72, 90, sigma_cells=3.0, precision="fp64")
+    w.steps = 60
+    res = []
+    for t in WARP_TILINGS:
+        s = tetm.Solver.from_workload(w)
+        s.set_tiling(*t)
+        s.step(w.steps)
+        res.append((s.wake()[0], s.get("ez"), s.get("hx"), s.get("ey")))
+    for other in res[1:]:
+        for a, b in zip(res[0], other):
+            assert np.array_equal(a, b)
+
+
+def test_warp_kernel_fp32_wake(tetm):
+    w = wl.scaled_collimator(48, 192, sigma_cells=4.0, precision="fp32")
+    s = tetm.Solver.from_workload(w)
+    s.set_tiling(28, 20, 32)
+    s.step(w.steps)
+    o = oracle_run(w)
+    assert rel_err(s.wake()[0], o.wake()[0]) <= TOL32_WAKE
+
+
+# ---------------------------------------------------------------------------
+# Register-ring variant of the warp kernel (float32; float64 for tile heights 8, 16)
+# ---------------------------------------------------------------------------
+
+@pytest.mark.parametrize("tiling", [(28, 8, 16), (28, 16, 7)])
+def test_register_ring_fp64_matches_oracle(tetm, tiling):
+    nx, ny, nz = 61, 37, 45
+    w = wl.scaled_collimator(nx, nz, sigma_cells=2.5)
+    w.nx, w.ny = nx, ny
+    w.pec = wl.radius_mask(nx, ny, nz, wl.collimator_radius(nz, 0.45 * ny, 0.2 * ny, nz // 4, nz // 2))
+    w.i0, w.j0 = nx // 2, ny // 2
+    w.steps = nz + 25
+    s = tetm.Solver(w.nx, w.ny, w.nz, w.dx, w.dy, w.dz, w.cdt, "fp64", pec=w.pec)
+    s.set_tiling(*tiling)
+    s.set_bunch(w.sigma, w.charge, w.i0, w.j0)
+    s.step(w.steps)
+    o = oracle_run(w)
+    compare_fields(s, o, TOL64)
+    assert rel_err(s.wake()[0], o.wake()[0]) <= 1e-11
+
+
+@pytest.mark.parametrize("tiling", [(28, 20, 32), (28, 8, 5), (28, 12, 64), (28, 4, 16)])
+def test_register_ring_fp32_matches_block_kernel(tetm, tiling):
+    w = wl.scaled_collimator(72, 90, sigma_cells=3.0, precision="fp32")
+    w.steps = 80
+    out = []
+    for t in [(32, 8, 64), tiling]:
+        s = tetm.Solver.from_workload(w)
+        s.set_tiling(*t)
+        s.step(w.steps)
+        out.append([s.get(c) for c in ("ex", "ey", "ez", "hx", "hy", "hz")] + [s.wake()[0]])
+    for a, b in zip(out[0], out[1]):
+        scale = np.max(np.abs(a)) or 1.0
+        assert np.max(np.abs(a - b)) <= 1e-6 * scale
