@@ -233,6 +233,41 @@ int tetm_load(tetm_solver* s, const void* buf, size_t size);
 int tetm_energy_noalloc(const tetm_grid* g, const void* const fields[6], const uint8_t* mask,
                         double* w, void* stream);
 
+/* ---- batches of solves ------------------------------------------------------
+ * A batch advances several solves together: every batch step is one launch
+ * of the warp-tiled kernel over the work items of all members, followed by a
+ * device-side advance of every member (field-set swap, step count,
+ * retirement at its step limit). Members keep their own grid, geometry,
+ * bunch, wake and step counter; the paper's scheme is applied to each member
+ * exactly as by tetm_step (the results are bit-identical to stepping each
+ * solve alone). */
+typedef struct tetm_batch tetm_batch;
+
+/* Group n distinct solves of one precision and one uniform material each.
+ * step_limits[i] >= 0: member i stops when its step counter reaches it
+ * (NULL or a negative entry: no limit). Members are switched to the
+ * warp-tiled kernel with the first member's tile height. graph_steps > 0:
+ * runs of that many steps are captured once as a CUDA graph and replayed;
+ * 0 launches every step directly. While in the batch a member rejects
+ * tetm_step, tetm_set_fields, tetm_set_kernel, tetm_set_tiling and tetm_load
+ * (TETM_E_STATE); read-only calls (tetm_wake, tetm_get_fields, tetm_energy,
+ * tetm_charge_residual) remain valid after tetm_batch_sync. Destroy the batch
+ * before destroying a member. */
+int tetm_batch_create(tetm_solver* const* solvers, const int64_t* step_limits, int32_t n,
+                      int32_t graph_steps, tetm_batch** out);
+
+/* Queue nsteps batch steps; each member advances min(nsteps, limit - step). */
+int tetm_batch_step(tetm_batch* b, int32_t nsteps);
+
+/* Wait for the batch's stream (synchronizes). */
+int tetm_batch_sync(tetm_batch* b);
+
+/* Members, members below their limit, and (member, item) work entries. */
+int tetm_batch_info(tetm_batch* b, int32_t* n_members, int32_t* n_active, int32_t* work_items);
+
+/* Release the batch (synchronizes); members become independent again. */
+void tetm_batch_destroy(tetm_batch* b);
+
 /* Static description of a return code. */
 const char* tetm_strerror(int code);
 

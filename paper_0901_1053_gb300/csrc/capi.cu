@@ -190,47 +190,6 @@ double phi(double x) { return 0.5 * erfc(-x / sqrt(2.0)); }
 
 }  // namespace
 
-struct tetm_solver {
-  tetm_grid g;
-  size_t esz;
-  Layout L;
-  void* set[2][6];
-  int cur;
-  uint8_t* mask;
-  double minv_c[6];
-  double* minv_a[6];
-  void* ua[6];
-  bool uniform;
-  double alpha;   // dt/2
-  cudaStream_t stream;
-  int kernel;
-  int tile_x, tile_y, chunk_z;
-  int tiles_x, tiles_y, n_chunks;
-  int* work;
-  int n_work;
-  bool work_dirty;
-  // bunch
-  bool bunch;
-  int i0, j0, c0, m_min, m_max;
-  double sigma, q;
-  std::vector<double> qcell;
-  void* J;
-  double* W;
-  double* qline;
-  // periodic balances: records {n, W, max_e, max_h, q_scale}
-  int bal_every;
-  double* hist;
-  int hist_cap;
-  long long hist_count;
-  // state
-  long long step;
-  bool prev_valid;
-  DiagScratch diag;
-  double* staging;
-  long long staging_elems;
-  long long device_bytes;
-  long long active_cells;
-};
 
 namespace {
 
@@ -264,7 +223,9 @@ bool grid_ok(const tetm_grid* g) {
 
 double cdt_of(const tetm_grid* g) { return g->cdt > 0 ? g->cdt : g->dz; }
 
-int rebuild_work(tetm_solver* s) {
+}  // namespace
+
+int tetm::rebuild_work(tetm_solver* s) {
   const Layout& L = s->L;
   s->tiles_x = (L.nx + s->tile_x - 1) / s->tile_x;
   s->tiles_y = (L.ny + s->tile_y - 1) / s->tile_y;
@@ -292,6 +253,7 @@ int rebuild_work(tetm_solver* s) {
   for (long long q = 0; q < items; ++q)
     if (h[(size_t)q]) list.push_back((int)q);
   s->n_work = (int)list.size();
+  s->work_host = list;
   if (!list.empty()) {
     CK(cudaMalloc(&s->work, sizeof(int) * list.size()));
     CK(cudaMemcpyAsync(s->work, list.data(), sizeof(int) * list.size(), cudaMemcpyHostToDevice,
@@ -302,8 +264,12 @@ int rebuild_work(tetm_solver* s) {
   return TETM_OK;
 }
 
+namespace {
+
+}  // namespace
+
 template <typename T>
-StepArgs<T> step_args(tetm_solver* s, bool fused) {
+StepArgs<T> tetm::step_args(tetm_solver* s, bool fused) {
   StepArgs<T> a;
   for (int c = 0; c < 6; ++c) {
     a.in[c] = (const T*)s->set[s->cur][c];
@@ -331,6 +297,10 @@ StepArgs<T> step_args(tetm_solver* s, bool fused) {
   a.n_work = s->n_work;
   return a;
 }
+template StepArgs<float> tetm::step_args<float>(tetm_solver*, bool);
+template StepArgs<double> tetm::step_args<double>(tetm_solver*, bool);
+
+namespace {
 
 // Queue the FP64 balances of the step just taken into device slots:
 // rec[0] = n, rec[1] = W^{n,e}, rec[2] = max|qe - qbunch|, rec[3] = max|qh|,
@@ -635,6 +605,7 @@ int tetm_set_stream(tetm_solver* s, void* st) {
 
 int tetm_set_kernel(tetm_solver* s, int32_t kernel) {
   if (!s || (kernel != TETM_KERNEL_FUSED && kernel != TETM_KERNEL_REFERENCE)) return TETM_E_ARG;
+  if (s->in_batch) return TETM_E_STATE;
   if (kernel == TETM_KERNEL_FUSED && !s->uniform) return TETM_E_UNSUPPORTED;
   s->kernel = kernel;
   return TETM_OK;
@@ -642,6 +613,7 @@ int tetm_set_kernel(tetm_solver* s, int32_t kernel) {
 
 int tetm_set_tiling(tetm_solver* s, int32_t tile_x, int32_t tile_y, int32_t chunk_z) {
   if (!s) return TETM_E_ARG;
+  if (s->in_batch) return TETM_E_STATE;
   const int tx = tile_x ? tile_x : s->tile_x;
   const int ty = tile_y ? tile_y : s->tile_y;
   const int cz = chunk_z ? chunk_z : s->chunk_z;
@@ -708,6 +680,7 @@ int tetm_set_bunch(tetm_solver* s, double sigma_z, double charge, int32_t i0, in
 
 int tetm_step(tetm_solver* s, int32_t n) {
   if (!s || n < 0) return TETM_E_ARG;
+  if (s->in_batch) return TETM_E_STATE;
   if (s->kernel == TETM_KERNEL_FUSED && s->work_dirty) {
     int rc = rebuild_work(s);
     if (rc) return rc;
@@ -805,6 +778,7 @@ int tetm_get_fields(tetm_solver* s, int32_t comp, double* host) {
 
 int tetm_set_fields(tetm_solver* s, int32_t comp, const double* host) {
   if (!s || !host || comp < 0 || comp > 5) return TETM_E_ARG;
+  if (s->in_batch) return TETM_E_STATE;
   int rc = ensure_staging(s);
   if (rc) return rc;
   rc = s->esz == 8 ? set_fields_t<double>(s, comp, host) : set_fields_t<float>(s, comp, host);
@@ -870,6 +844,7 @@ int tetm_save(tetm_solver* s, void* buf, size_t cap, size_t* used) {
 
 int tetm_load(tetm_solver* s, const void* buf, size_t size) {
   if (!s || !buf || size < sizeof(CkptHeader)) return TETM_E_ARG;
+  if (s->in_batch) return TETM_E_STATE;
   CkptHeader h;
   memcpy(&h, buf, sizeof(h));
   const int nw = s->bunch ? s->m_max - s->m_min + 1 : 0;

@@ -60,14 +60,14 @@ constexpr int kDepth = 8;   // rows of loads in flight ahead of the sweep
 constexpr int kArrs = 8;    // ez hx hy hz (plane k), ex ey (plane k), ex ey (plane k+1)
 
 template <typename T, int TY>
-__global__ void __launch_bounds__(64)
-fused_step_warp(const StepArgs<T> a) {
+__device__ __forceinline__ void fused_step_warp_item(const StepArgs<T>& a, int item,
+                                                unsigned char* smem_raw) {
+
   constexpr int RH = TY + 4;
   static_assert(RH % kDepth == 0, "rows per tile must be a multiple of the ring depth");
   // per warp: the load ring [kDepth][kArrs][32] and the per-row state carried
   // to the next plane (new hx, hy of this plane) [2][RH][32]; the activity
   // bytes of the ring rows stay in registers
-  extern __shared__ __align__(16) unsigned char smem_raw[];
   const int lane = threadIdx.x & 31;
   const int wib = threadIdx.x >> 5;
   T* wbase = reinterpret_cast<T*>(smem_raw) + (size_t)wib * (kDepth * kArrs + 2 * RH) * 32;
@@ -75,8 +75,6 @@ fused_step_warp(const StepArgs<T> a) {
   T* sHXP = wbase + kDepth * kArrs * 32;
   T* sHYP = sHXP + RH * 32;
 
-  const int nitems = a.work ? a.n_work : a.tiles_x * a.tiles_y * a.n_chunks;
-  const int nwarps = (int)((gridDim.x * blockDim.x) >> 5);
   const Layout L = a.L;
   const long long SZ = L.sz;
   const long long PX = L.px;
@@ -96,9 +94,6 @@ fused_step_warp(const StepArgs<T> a) {
   const T uEX = a.co.u[kEX], uEY = a.co.u[kEY], uEZ = a.co.u[kEZ];
   const T uHX = a.co.u[kHX], uHY = a.co.u[kHY], uHZ = a.co.u[kHZ];
 
-  for (int witem = (int)((blockIdx.x * blockDim.x + threadIdx.x) >> 5); witem < nitems;
-       witem += nwarps) {
-  const int item = a.work ? a.work[witem] : witem;
   const int ntile = a.tiles_x * a.tiles_y;
   const int tile = item % ntile, chunk = item / ntile;
   const int gi = (tile % a.tiles_x) * kWarpTileX - 2 + lane;
@@ -245,7 +240,34 @@ fused_step_warp(const StepArgs<T> a) {
     }
   }
   cp_async_wait<0>();  // the ring is reused by the next work item
-  }  // work items
+}
+
+template <typename T, int TY>
+__global__ void __launch_bounds__(64)
+fused_step_warp(const StepArgs<T> a) {
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  const int nitems = a.work ? a.n_work : a.tiles_x * a.tiles_y * a.n_chunks;
+  const int nwarps = (int)((gridDim.x * blockDim.x) >> 5);
+  for (int witem = (int)((blockIdx.x * blockDim.x + threadIdx.x) >> 5); witem < nitems;
+       witem += nwarps)
+    fused_step_warp_item<T, TY>(a, a.work ? a.work[witem] : witem, smem_raw);
+}
+
+// Batched form: one launch advances every active member of a batch by one
+// step; the work list holds (member, item) pairs of all members.
+template <typename T, int TY>
+__global__ void __launch_bounds__(64)
+fused_step_warp_batch(const BatchMember<T>* __restrict__ members,
+                            const int2* __restrict__ work, int n_work) {
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  const int nwarps = (int)((gridDim.x * blockDim.x) >> 5);
+  for (int witem = (int)((blockIdx.x * blockDim.x + threadIdx.x) >> 5); witem < n_work;
+       witem += nwarps) {
+    const int2 e = work[witem];
+    const BatchMember<T>& mb = members[e.x];
+    if (!mb.active) continue;
+    fused_step_warp_item<T, TY>(mb.a, e.y, smem_raw);
+  }
 }
 
 template <typename T, int TY>
@@ -313,13 +335,13 @@ struct RowIn {
 };
 
 template <typename T, int TY>
-__global__ void __launch_bounds__(128)
-fused_step_warp_reg(const StepArgs<T> a) {
+__device__ __forceinline__ void fused_step_warp_reg_item(const StepArgs<T>& a, int item,
+                                                unsigned char* smem_raw) {
+
   constexpr int RH = TY + 4;
   static_assert(RH % kRing == 0, "rows per tile must be a multiple of the ring depth");
   // per-row state carried from plane to plane, lane-private: old ex, ey of
   // the current plane and new hx, hy of the previous plane
-  extern __shared__ __align__(16) unsigned char smem_raw[];
   const int lane = threadIdx.x & 31;
   const int wib = threadIdx.x >> 5;
   T* st = reinterpret_cast<T*>(smem_raw) + (size_t)wib * 4 * RH * 32;
@@ -328,8 +350,6 @@ fused_step_warp_reg(const StepArgs<T> a) {
   T* sHXP = st + 2 * RH * 32;
   T* sHYP = st + 3 * RH * 32;
 
-  const int nitems = a.work ? a.n_work : a.tiles_x * a.tiles_y * a.n_chunks;
-  const int nwarps = (int)((gridDim.x * blockDim.x) >> 5);
   const Layout L = a.L;
   const long long SZ = L.sz;
   const long long PX = L.px;
@@ -349,9 +369,6 @@ fused_step_warp_reg(const StepArgs<T> a) {
   const T uEX = a.co.u[kEX], uEY = a.co.u[kEY], uEZ = a.co.u[kEZ];
   const T uHX = a.co.u[kHX], uHY = a.co.u[kHY], uHZ = a.co.u[kHZ];
 
-  for (int witem = (int)((blockIdx.x * blockDim.x + threadIdx.x) >> 5); witem < nitems;
-       witem += nwarps) {
-  const int item = a.work ? a.work[witem] : witem;
   const int ntile = a.tiles_x * a.tiles_y;
   const int tile = item % ntile, chunk = item / ntile;
   const int gi = (tile % a.tiles_x) * kWarpTileX - 2 + lane;
@@ -475,7 +492,34 @@ fused_step_warp_reg(const StepArgs<T> a) {
       }
     }
   }
-  }  // work items
+}
+
+template <typename T, int TY>
+__global__ void __launch_bounds__(128)
+fused_step_warp_reg(const StepArgs<T> a) {
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  const int nitems = a.work ? a.n_work : a.tiles_x * a.tiles_y * a.n_chunks;
+  const int nwarps = (int)((gridDim.x * blockDim.x) >> 5);
+  for (int witem = (int)((blockIdx.x * blockDim.x + threadIdx.x) >> 5); witem < nitems;
+       witem += nwarps)
+    fused_step_warp_reg_item<T, TY>(a, a.work ? a.work[witem] : witem, smem_raw);
+}
+
+// Batched form: one launch advances every active member of a batch by one
+// step; the work list holds (member, item) pairs of all members.
+template <typename T, int TY>
+__global__ void __launch_bounds__(128)
+fused_step_warp_reg_batch(const BatchMember<T>* __restrict__ members,
+                            const int2* __restrict__ work, int n_work) {
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  const int nwarps = (int)((gridDim.x * blockDim.x) >> 5);
+  for (int witem = (int)((blockIdx.x * blockDim.x + threadIdx.x) >> 5); witem < n_work;
+       witem += nwarps) {
+    const int2 e = work[witem];
+    const BatchMember<T>& mb = members[e.x];
+    if (!mb.active) continue;
+    fused_step_warp_reg_item<T, TY>(mb.a, e.y, smem_raw);
+  }
 }
 
 template <typename T, int TY>
@@ -505,6 +549,57 @@ cudaError_t launch_warp_reg_shape(const StepArgs<T>& a, cudaStream_t st) {
   return cudaGetLastError();
 }
 
+
+// After a batch step: every active member swaps its field sets, counts the
+// step and retires when it reaches its limit.
+template <typename T>
+__global__ void batch_advance(BatchMember<T>* members, int n) {
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= n || !members[i].active) return;
+  StepArgs<T>& a = members[i].a;
+  for (int c = 0; c < 6; ++c) {
+    T* t = a.out[c];
+    a.out[c] = const_cast<T*>(a.in[c]);
+    a.in[c] = t;
+  }
+  a.n += 1;
+  if (a.n >= members[i].limit) members[i].active = 0;
+}
+
+template <typename T, int TY, bool ASYNC, typename K>
+cudaError_t launch_batch_kernel(K kern, const BatchMember<T>* members, const int2* work, int n_work,
+                                cudaStream_t st) {
+  const int warps_per_block = ASYNC ? 2 : 4;
+  const size_t smem = ASYNC ? (size_t)warps_per_block * (kDepth * kArrs + 2 * (TY + 4)) * 32 * sizeof(T)
+                            : (size_t)warps_per_block * 4 * (TY + 4) * 32 * sizeof(T);
+  static int resident = 0;
+  if (!resident) {
+    if (smem > 48 * 1024) {
+      cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+      if (e != cudaSuccess) return e;
+    }
+    int dev = 0, sms = 0, per_sm = 0;
+    cudaError_t e = cudaGetDevice(&dev);
+    if (e == cudaSuccess) e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    if (e == cudaSuccess)
+      e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, 32 * warps_per_block, smem);
+    if (e != cudaSuccess) return e;
+    resident = std::max(1, sms * per_sm);
+  }
+  const int blocks = std::min(resident, (n_work + warps_per_block - 1) / warps_per_block);
+  if (blocks > 0) kern<<<blocks, 32 * warps_per_block, smem, st>>>(members, work, n_work);
+  return cudaGetLastError();
+}
+
+template <typename T, int TY, bool ASYNC>
+cudaError_t launch_batch_shape(const BatchMember<T>* members, const int2* work, int n_work,
+                               cudaStream_t st) {
+  if constexpr (ASYNC)
+    return launch_batch_kernel<T, TY, true>(fused_step_warp_batch<T, TY>, members, work, n_work, st);
+  else
+    return launch_batch_kernel<T, TY, false>(fused_step_warp_reg_batch<T, TY>, members, work, n_work, st);
+}
+
 }  // namespace
 
 bool warp_shape_ok(int tx, int ty) {
@@ -530,6 +625,37 @@ cudaError_t launch_fused_warp_step(const StepArgs<T>& a, int tx, int ty, cudaStr
   if (ty == 28) return launch_warp_reg_shape<T, 28>(a, st);
   return cudaErrorInvalidValue;
 }
+
+
+template <typename T>
+cudaError_t launch_fused_warp_batch(const BatchMember<T>* members, int n_members, const int2* work,
+                                    int n_work, int ty, cudaStream_t st) {
+  cudaError_t e = cudaErrorInvalidValue;
+  if constexpr (sizeof(T) == 8) {
+    if (ty == 4) e = launch_batch_shape<T, 4, true>(members, work, n_work, st);
+    else if (ty == 12) e = launch_batch_shape<T, 12, true>(members, work, n_work, st);
+    else if (ty == 20) e = launch_batch_shape<T, 20, true>(members, work, n_work, st);
+    else if (ty == 28) e = launch_batch_shape<T, 28, true>(members, work, n_work, st);
+    else if (ty == 8) e = launch_batch_shape<T, 8, false>(members, work, n_work, st);
+    else if (ty == 16) e = launch_batch_shape<T, 16, false>(members, work, n_work, st);
+  } else {
+    if (ty == 4) e = launch_batch_shape<T, 4, false>(members, work, n_work, st);
+    else if (ty == 8) e = launch_batch_shape<T, 8, false>(members, work, n_work, st);
+    else if (ty == 12) e = launch_batch_shape<T, 12, false>(members, work, n_work, st);
+    else if (ty == 16) e = launch_batch_shape<T, 16, false>(members, work, n_work, st);
+    else if (ty == 20) e = launch_batch_shape<T, 20, false>(members, work, n_work, st);
+    else if (ty == 28) e = launch_batch_shape<T, 28, false>(members, work, n_work, st);
+  }
+  if (e != cudaSuccess) return e;
+  batch_advance<T><<<(n_members + 127) / 128, 128, 0, st>>>(const_cast<BatchMember<T>*>(members),
+                                                            n_members);
+  return cudaGetLastError();
+}
+
+template cudaError_t launch_fused_warp_batch<float>(const BatchMember<float>*, int, const int2*, int,
+                                                    int, cudaStream_t);
+template cudaError_t launch_fused_warp_batch<double>(const BatchMember<double>*, int, const int2*,
+                                                     int, int, cudaStream_t);
 
 template cudaError_t launch_fused_warp_step<float>(const StepArgs<float>&, int, int, cudaStream_t);
 template cudaError_t launch_fused_warp_step<double>(const StepArgs<double>&, int, int, cudaStream_t);

@@ -5,6 +5,8 @@
 #include <cuda_runtime.h>
 #include <stdint.h>
 
+#include <vector>
+
 #include "../../include/tetm.h"
 
 namespace tetm {
@@ -72,6 +74,17 @@ struct StepArgs {
   int n_work;
 };
 
+// One member of a batch as the batched kernels see it: its step arguments
+// (advanced on the device: ping-pong pointers swapped and n incremented after
+// every batch step) and whether it still has steps to take.
+template <typename T>
+struct BatchMember {
+  StepArgs<T> a;
+  long long limit;  // last step index + 1 this member may reach
+  int active;       // 0 once a.n == limit
+  int pad;
+};
+
 // ---- launchers (kernels_step.cu) -----------------------------------------
 template <typename T>
 cudaError_t launch_reference_step(const StepArgs<T>& a, cudaStream_t st);
@@ -82,6 +95,11 @@ bool fused_shape_ok(int tile_x, int tile_y);
 template <typename T>
 cudaError_t launch_fused_warp_step(const StepArgs<T>& a, int tile_x, int tile_y, cudaStream_t st);
 bool warp_shape_ok(int tile_x, int tile_y);
+// one step of every active member of a batch (work = (member, item) pairs),
+// then the device-side advance of all members
+template <typename T>
+cudaError_t launch_fused_warp_batch(const BatchMember<T>* members, int n_members, const int2* work,
+                                    int n_work, int tile_y, cudaStream_t st);
 
 // ---- diagnostics (kernels_diag.cu) ----------------------------------------
 struct DiagScratch {
@@ -110,4 +128,57 @@ cudaError_t launch_charge(const T* const cur[6], const T* const prev[6], const u
 cudaError_t launch_bunch_charge(double q, double sigma, double dz, double zc, int nz, double* ql,
                                 double* qmax, double tag, double* tag_out, cudaStream_t st);
 
+}  // namespace tetm
+
+// The solve behind a tetm_solver* handle (host bookkeeping and device arrays).
+struct tetm_solver {
+  tetm_grid g;
+  size_t esz;
+  tetm::Layout L;
+  void* set[2][6];
+  int cur;
+  uint8_t* mask;
+  double minv_c[6];
+  double* minv_a[6];
+  void* ua[6];
+  bool uniform;
+  double alpha;   // dt/2
+  cudaStream_t stream;
+  int kernel;
+  int tile_x, tile_y, chunk_z;
+  int tiles_x, tiles_y, n_chunks;
+  int* work;
+  int n_work;
+  std::vector<int> work_host;  // host copy of the work list
+  bool in_batch;               // stepped by a tetm_batch
+  bool work_dirty;
+  // bunch
+  bool bunch;
+  int i0, j0, c0, m_min, m_max;
+  double sigma, q;
+  std::vector<double> qcell;
+  void* J;
+  double* W;
+  double* qline;
+  // periodic balances: records {n, W, max_e, max_h, q_scale}
+  int bal_every;
+  double* hist;
+  int hist_cap;
+  long long hist_count;
+  // state
+  long long step;
+  bool prev_valid;
+  tetm::DiagScratch diag;
+  double* staging;
+  long long staging_elems;
+  long long device_bytes;
+  long long active_cells;
+};
+
+namespace tetm {
+// step arguments of a solve for the fused (ping-pong) or reference kernel
+template <typename T>
+StepArgs<T> step_args(tetm_solver* s, bool fused);
+// (re)build the list of (tile, chunk) work items that own a field-carrying cell
+int rebuild_work(tetm_solver* s);
 }  // namespace tetm

@@ -38,7 +38,9 @@ EXPORTS = ("tetm_create", "tetm_set_bunch", "tetm_step", "tetm_sync", "tetm_wake
            "tetm_destroy", "tetm_energy", "tetm_charge_residual", "tetm_get_fields",
            "tetm_set_fields", "tetm_set_stream", "tetm_set_kernel", "tetm_set_tiling",
            "tetm_get_info", "tetm_bytes_needed", "tetm_save", "tetm_load", "tetm_strerror",
-           "tetm_set_balance_every", "tetm_balance_history", "tetm_energy_noalloc")
+           "tetm_set_balance_every", "tetm_balance_history", "tetm_energy_noalloc",
+           "tetm_batch_create", "tetm_batch_step", "tetm_batch_sync", "tetm_batch_info",
+           "tetm_batch_destroy")
 
 
 class tetm_grid(ctypes.Structure):
@@ -86,6 +88,13 @@ def _load():
         "tetm_strerror": (ctypes.c_char_p, [ctypes.c_int]),
         "tetm_set_balance_every": (ctypes.c_int, [vp, i32]),
         "tetm_balance_history": (ctypes.c_int, [vp, vp, i32, ctypes.POINTER(i32)]),
+        "tetm_batch_create": (ctypes.c_int, [ctypes.POINTER(ctypes.c_void_p), vp, i32, i32,
+                                             ctypes.POINTER(ctypes.c_void_p)]),
+        "tetm_batch_step": (ctypes.c_int, [vp, i32]),
+        "tetm_batch_sync": (ctypes.c_int, [vp]),
+        "tetm_batch_info": (ctypes.c_int, [vp, ctypes.POINTER(i32), ctypes.POINTER(i32),
+                                           ctypes.POINTER(i32)]),
+        "tetm_batch_destroy": (None, [vp]),
         "tetm_energy_noalloc": (ctypes.c_int, [ctypes.POINTER(tetm_grid),
                                                ctypes.POINTER(ctypes.c_void_p), vp, vp, vp]),
     }
@@ -264,3 +273,47 @@ class Solver:
 
 def _comp(c):
     return COMPONENTS.index(c) if isinstance(c, str) else int(c)
+
+
+class Batch:
+    """Solves advancing together (tetm_batch_*): one launch per step for all
+    members, optionally replayed from a captured CUDA graph."""
+
+    def __init__(self, solvers, step_limits=None, graph_steps=0):
+        self.solvers = list(solvers)
+        n = len(self.solvers)
+        hs = (ctypes.c_void_p * n)(*[s.h for s in self.solvers])
+        lim = None
+        if step_limits is not None:
+            self._lim = np.ascontiguousarray([int(x) for x in step_limits], dtype=np.int64)
+            lim = _ptr(self._lim)
+        h = ctypes.c_void_p()
+        self.h = None
+        _check(lib.tetm_batch_create(hs, lim, n, int(graph_steps), ctypes.byref(h)),
+               "tetm_batch_create")
+        self.h = h
+
+    def step(self, n):
+        _check(lib.tetm_batch_step(self.h, int(n)), "tetm_batch_step")
+
+    def sync(self):
+        _check(lib.tetm_batch_sync(self.h), "tetm_batch_sync")
+
+    def info(self):
+        a, b, c = ctypes.c_int32(), ctypes.c_int32(), ctypes.c_int32()
+        _check(lib.tetm_batch_info(self.h, ctypes.byref(a), ctypes.byref(b), ctypes.byref(c)),
+               "tetm_batch_info")
+        return {"members": a.value, "active": b.value, "work_items": c.value}
+
+    def close(self):
+        if self.h is not None:
+            lib.tetm_batch_destroy(self.h)
+            self.h = None
+
+    __del__ = close
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *exc):
+        self.close()
