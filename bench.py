@@ -47,7 +47,11 @@ def parse_args():
     p.add_argument("--steps", type=int, default=2000)
     p.add_argument("--warmup", type=int, default=20)
     p.add_argument("--impl", default="tetm", choices=["tetm", "reference"])
-    p.add_argument("--workload", default="collimator", choices=["collimator", "plain_pipe"])
+    p.add_argument("--workload", default="collimator",
+                   choices=["collimator", "plain_pipe", "batch", "serve"])
+    p.add_argument("--requests", type=int, default=2000, help="serve: requests in the stream")
+    p.add_argument("--rate", type=float, default=40.0, help="serve: mean arrivals per second")
+    p.add_argument("--solves", type=int, default=64, help="batch: number of solves")
     p.add_argument("--precision", default=None, choices=[None, "fp32", "fp64"])
     p.add_argument("--balance-every", type=int, default=100)
     p.add_argument("--tiling", default=None, help="tile_x,tile_y,chunk_z")
@@ -391,10 +395,107 @@ def run_tetm(args):
     return 0
 
 
+# ---------------------------------------------------------------------------
+# Batched and served workloads (independent solves)
+# ---------------------------------------------------------------------------
+def _rel(a, b):
+    import numpy as np
+    return float(np.max(np.abs(a - b)) / max(np.max(np.abs(b)), 1e-300))
+
+
+def run_batch_mode(args):
+    """64 seeded pipe/cavity solves N x N x 4N, N ~ U{32..192}, sigma ~ U[3,10] dz:
+    one FP32 batch (autotuned tile, CUDA-graph runs) against the single-solve
+    FP64 path, each solve alone in turn."""
+    from paper_0901_1053_gb300 import workloads as wl, sharding
+    from paper_0901_1053_gb300.autotune import Autotuner
+    from paper_0901_1053_gb300.batching import run_batch, run_sequential
+    rank, world, local = dist_env()
+    import torch
+    torch.cuda.set_device(local)
+    dist = Dist(world)
+    allw = wl.batch_solves(count=args.solves)
+    ws = sharding.shard_workloads(allw, world, rank)
+    big = max(ws, key=lambda w: w.cells)
+    tuner = Autotuner()
+    t32 = tuner.tune(big, "fp32")
+    t64 = tuner.tune(big, "fp64")
+    dist.barrier()
+    wakes32, t_step, t_total = run_batch(ws, "fp32", t32, graph_steps=32)
+    wakes64, t_seq64 = run_sequential(ws, "fp64", t64)
+    err = max(_rel(a, b) for a, b in zip(wakes32, wakes64))
+    cs = sum(w.cells * w.steps for w in ws)
+    t_step, t_total, t_seq64 = dist.max(t_step), dist.max(t_total), dist.max(t_seq64)
+    cs_all = sum(w.cells * w.steps for w in allw)
+    line = {"metric": METRIC, "value": cs_all / t_step / 1e9, "unit": UNIT, "n_gpus": world,
+            "steps": max(w.steps for w in allw), "warmup": 0, "higher_is_better": True,
+            "scaling": "strong", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+            "config": {"workload": "batch_%d_pipe_cavity_seed9011053" % len(allw),
+                       "n_range": [min(w.nx for w in allw), max(w.nx for w in allw)],
+                       "tiling_fp32": list(t32), "tiling_fp64": list(t64), "graph_steps": 32,
+                       "cell_steps": cs_all},
+            "solves_per_s": len(allw) / t_total,
+            "fp64_single_solve_path_solves_per_s": len(allw) / t_seq64,
+            "max_wake_err_vs_fp64_rel_peak": err,
+            "e2e": {"value": cs_all / t_total / 1e9, "unit": UNIT,
+                    "h2d_bytes_per_step": int(sum(w.pec.nbytes for w in allw)),
+                    "d2h_bytes_per_step": int(sum(8 * len(x) for x in wakes32)),
+                    "seconds": t_total},
+            "seconds": {"batch_steps": t_step, "batch_total": t_total, "fp64_sequential": t_seq64}}
+    if rank == 0:
+        print(json.dumps(line), flush=True)
+    dist.close()
+    return 0
+
+
+def run_serve_mode(args):
+    """Poisson stream of solve requests (N ~ U{48..256}, N x N x 4N, pipe /
+    cavity / collimator, sigma ~ U[3,10] dz) served with continuous batching
+    under a 150 GB device-memory budget."""
+    import numpy as np
+    from paper_0901_1053_gb300 import workloads as wl, tetm
+    from paper_0901_1053_gb300.serve import GpuBackend, Server, latency_stats
+    from paper_0901_1053_gb300.autotune import Autotuner
+    rank, world, local = dist_env()
+    if rank != 0:
+        return 0
+    reqs = wl.request_stream(count=args.requests, rate=args.rate)
+    probe = max(reqs[:32], key=lambda r: r.n).workload("fp32")
+    tiling = Autotuner().tune(probe, "fp32")
+    srv = Server(GpuBackend("fp32", tiling), hbm_budget=150e9, max_slots=64, round_steps=64)
+    res = srv.run_stream(reqs, lambda r: r.workload("fp32"))
+    st = latency_stats(res)
+    # accuracy of a sample of served wakes against the FP64 path
+    errs = []
+    for r in reqs[:6]:
+        w = r.workload("fp64")
+        s = tetm.Solver.from_workload(w)
+        s.step(w.steps)
+        errs.append(_rel(res[r.rid].wake, s.wake()[0]))
+        s.close()
+    line = {"metric": "served solves/s", "value": st.get("solves_per_s"), "unit": "solves/s",
+            "n_gpus": 1, "higher_is_better": True, "vs_baseline": None, "dtype": "f32",
+            "data": "synthetic",
+            "config": {"workload": "serve_poisson_%d_at_%g_per_s_seed9011054" % (args.requests, args.rate),
+                       "hbm_budget_gb": 150, "max_slots": 64, "round_steps": 64,
+                       "tiling": list(tiling)},
+            "latency": {"p50_s": st.get("p50_s"), "p99_s": st.get("p99_s"), "mean_s": st.get("mean_s")},
+            "gcell_updates_per_s": st.get("cell_steps", 0) / st["makespan_s"] / 1e9 if st.get("makespan_s") else None,
+            "max_active": srv.max_active, "rounds": srv.rounds, "gpu_busy_s": srv.busy_s,
+            "makespan_s": st.get("makespan_s"), "status_counts": {k: st[k] for k in ("ok", "rejected", "cancelled", "error")},
+            "max_wake_err_vs_fp64_rel_peak_sample6": max(errs) if errs else None}
+    print(json.dumps(line), flush=True)
+    return 0
+
+
 def main():
     args = parse_args()
     if args.impl == "reference":
         return run_reference(args)
+    if args.workload == "batch":
+        return run_batch_mode(args)
+    if args.workload == "serve":
+        return run_serve_mode(args)
     return run_tetm(args)
 
 

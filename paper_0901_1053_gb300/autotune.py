@@ -1,0 +1,105 @@
+"""Work-shape autotuner for the fused step kernels.
+
+For a grid and geometry it times candidate (tile_x, tile_y, chunk_z) shapes
+on a scratch solve with the same geometry (the cost of a step does not depend
+on the bunch or on the field values), keeps the fastest and caches it in a
+JSON file keyed by GPU name, precision, grid size and a digest of the PEC
+mask. Tuning runs solves through the C ABI only; nothing here computes fields.
+"""
+from __future__ import annotations
+
+import hashlib
+import json
+import os
+import time
+from typing import Dict, List, Optional, Sequence, Tuple
+
+Shape = Tuple[int, int, int]
+
+CANDIDATES_FP32: List[Shape] = [(28, 20, 32), (28, 20, 16), (28, 12, 32), (28, 12, 16),
+                                (28, 28, 32), (28, 8, 32), (28, 4, 32), (32, 8, 64)]
+CANDIDATES_FP64: List[Shape] = [(28, 20, 32), (28, 20, 16), (28, 12, 32), (28, 28, 32),
+                                (28, 4, 32), (32, 8, 64)]
+
+
+def default_cache_path() -> str:
+    return os.environ.get("TETM_AUTOTUNE_CACHE",
+                          os.path.join(os.path.expanduser("~"), ".cache", "tetm", "autotune.json"))
+
+
+def _gpu_name() -> str:
+    try:
+        import torch
+        if torch.cuda.is_available():
+            return torch.cuda.get_device_name(0)
+    except Exception:
+        pass
+    return "unknown-gpu"
+
+
+def geometry_digest(pec) -> str:
+    if pec is None:
+        return "box"
+    return hashlib.sha1(memoryview(pec).tobytes()).hexdigest()[:16]
+
+
+class Autotuner:
+    def __init__(self, cache_path: Optional[str] = None, steps: int = 6, warmup: int = 2):
+        self.path = cache_path or default_cache_path()
+        self.steps = steps
+        self.warmup = warmup
+        self.cache: Dict[str, list] = {}
+        if os.path.exists(self.path):
+            try:
+                with open(self.path) as f:
+                    self.cache = json.load(f)
+            except (OSError, ValueError):
+                self.cache = {}
+
+    def key(self, w, precision: str) -> str:
+        return "|".join([_gpu_name(), precision, "%dx%dx%d" % (w.nx, w.ny, w.nz),
+                         geometry_digest(w.pec)])
+
+    def _save(self):
+        try:
+            os.makedirs(os.path.dirname(self.path), exist_ok=True)
+            tmp = self.path + ".tmp%d" % os.getpid()
+            with open(tmp, "w") as f:
+                json.dump(self.cache, f, indent=1, sort_keys=True)
+            os.replace(tmp, self.path)
+        except OSError:
+            pass
+
+    def measure(self, w, precision: str, shapes: Sequence[Shape]) -> Dict[Shape, float]:
+        """Seconds per step of each shape on a scratch solve of w's geometry."""
+        from . import tetm
+        s = tetm.Solver(w.nx, w.ny, w.nz, w.dx, w.dy, w.dz, w.cdt, precision, pec=w.pec)
+        out = {}
+        try:
+            for shape in shapes:
+                try:
+                    s.set_tiling(*shape)
+                except tetm.TetmError:
+                    continue
+                s.step(self.warmup)
+                s.sync()
+                t0 = time.perf_counter()
+                s.step(self.steps)
+                s.sync()
+                out[tuple(shape)] = (time.perf_counter() - t0) / self.steps
+        finally:
+            s.close()
+        return out
+
+    def tune(self, w, precision: Optional[str] = None,
+             candidates: Optional[Sequence[Shape]] = None) -> Shape:
+        precision = precision or w.precision
+        k = self.key(w, precision)
+        if k in self.cache:
+            return tuple(self.cache[k])
+        cands = candidates or (CANDIDATES_FP32 if precision == "fp32" else CANDIDATES_FP64)
+        times = self.measure(w, precision, cands)
+        best = min(times, key=times.get)
+        self.cache[k] = list(best)
+        self._save()
+        return best

@@ -70,7 +70,9 @@ def radius_mask(nx: int, ny: int, nz: int, radius_of_k: Callable[[np.ndarray], n
     cj = np.arange(ny) + 0.5 - cy
     r = np.sqrt(ci[None, :] ** 2 + cj[:, None] ** 2)             # (ny, nx)
     rk = np.asarray(radius_of_k(np.arange(nz)), dtype=np.float64)  # (nz,)
-    return (r[None, :, :] > rk[:, None, None]).astype(np.uint8)
+    radii, which = np.unique(rk, return_inverse=True)
+    planes = np.stack([(r > rad).astype(np.uint8) for rad in radii])  # one mask per radius
+    return planes[which.reshape(-1)]
 
 
 def collimator_radius(nz: int, r_out: float, r_in: float, k1: int, k2: int):
