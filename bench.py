@@ -53,7 +53,7 @@ def parse_args():
     p.add_argument("--rate", type=float, default=40.0, help="serve: mean arrivals per second")
     p.add_argument("--solves", type=int, default=64, help="batch: number of solves")
     p.add_argument("--precision", default=None, choices=[None, "fp32", "fp64"])
-    p.add_argument("--balance-every", type=int, default=100)
+    p.add_argument("--balance-every", type=int, default=250)
     p.add_argument("--tiling", default=None, help="tile_x,tile_y,chunk_z")
     p.add_argument("--kernel", default="fused", choices=["fused", "reference"])
     p.add_argument("--no-e2e", action="store_true")

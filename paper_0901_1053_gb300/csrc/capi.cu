@@ -254,6 +254,14 @@ int tetm::rebuild_work(tetm_solver* s) {
     if (h[(size_t)q]) list.push_back((int)q);
   s->n_work = (int)list.size();
   s->work_host = list;
+  if (2 * s->n_work > s->diag.cap) {  // balance reductions keep one partial per work item
+    cudaFree(s->diag.part);
+    s->diag.part = nullptr;
+    s->diag.cap = 0;
+    const int cap = std::max(2048, 2 * s->n_work);
+    CK(cudaMalloc(&s->diag.part, sizeof(double) * (size_t)cap));
+    s->diag.cap = cap;
+  }
   if (!list.empty()) {
     CK(cudaMalloc(&s->work, sizeof(int) * list.size()));
     CK(cudaMemcpyAsync(s->work, list.data(), sizeof(int) * list.size(), cudaMemcpyHostToDevice,
@@ -305,6 +313,18 @@ namespace {
 // Queue the FP64 balances of the step just taken into device slots:
 // rec[0] = n, rec[1] = W^{n,e}, rec[2] = max|qe - qbunch|, rec[3] = max|qh|,
 // rec[4] = max|qbunch|. No host synchronisation.
+WorkView work_view(const tetm_solver* s) {
+  WorkView v;
+  v.items = s->work;
+  v.n_items = s->n_work;
+  v.tile_x = s->tile_x;
+  v.tile_y = s->tile_y;
+  v.chunk_z = s->chunk_z;
+  v.tiles_x = s->tiles_x;
+  v.tiles_y = s->tiles_y;
+  return v;
+}
+
 template <typename T>
 int queue_balances(tetm_solver* s, double* rec) {
   const double zc = ((double)(s->step - 1) + 0.5 - s->c0) * s->g.dz;
@@ -317,9 +337,10 @@ int queue_balances(tetm_solver* s, double* rec) {
     prv[c] = (const T*)s->set[1 - s->cur][c];
     ma[c] = s->minv_a[c];
   }
-  CK(launch_energy<T>(cur, s->mask, s->minv_c, ma, s->L, s->alpha, s->diag, rec + 1, s->stream));
+  const WorkView wv = work_view(s);
+  CK(launch_energy<T>(cur, s->mask, s->minv_c, ma, s->L, s->alpha, wv, s->diag, rec + 1, s->stream));
   CK(launch_charge<T>(cur, prv, s->mask, s->minv_c, ma, s->L, s->alpha,
-                      s->bunch ? s->qline : nullptr, s->i0, s->j0, s->diag, rec + 2, rec + 3,
+                      s->bunch ? s->qline : nullptr, s->i0, s->j0, wv, s->diag, rec + 2, rec + 3,
                       s->stream));
   return TETM_OK;
 }
@@ -717,11 +738,13 @@ int tetm_energy(tetm_solver* s, double* w) {
   if (s->esz == 8) {
     const double* f[6];
     for (int c = 0; c < 6; ++c) f[c] = (const double*)s->set[s->cur][c];
-    e = launch_energy<double>(f, s->mask, s->minv_c, ma, s->L, s->alpha, s->diag, s->diag.out, s->stream);
+    e = launch_energy<double>(f, s->mask, s->minv_c, ma, s->L, s->alpha, work_view(s), s->diag,
+                              s->diag.out, s->stream);
   } else {
     const float* f[6];
     for (int c = 0; c < 6; ++c) f[c] = (const float*)s->set[s->cur][c];
-    e = launch_energy<float>(f, s->mask, s->minv_c, ma, s->L, s->alpha, s->diag, s->diag.out, s->stream);
+    e = launch_energy<float>(f, s->mask, s->minv_c, ma, s->L, s->alpha, work_view(s), s->diag,
+                             s->diag.out, s->stream);
   }
   CK(e);
   CK(cudaMemcpyAsync(w, s->diag.out, sizeof(double), cudaMemcpyDeviceToHost, s->stream));

@@ -11,7 +11,6 @@ namespace tetm {
 namespace {
 
 constexpr int kBlock = 256;
-constexpr int kMaxBlocks = 2048;
 
 __device__ __forceinline__ double warp_sum(double v) {
   for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(0xffffffffu, v, o);
@@ -56,42 +55,81 @@ struct MinvView {
   }
 };
 
-// Energy density of node index (i,j,k): Sec. 4.4, W = 1/2 <Q^e y, y> with
-// Q^e = [[I - a^2 R_0, a L], [a L^T, I - a^2 R_1]], in integral variables.
+// Cells of one work item, column by column: thread t takes columns t,
+// t + blockDim, ... of the tile and marches through the item's z-planes.
+struct ItemCells {
+  int i0, j0, k0, k1, tx, ty;
+  __device__ ItemCells(const WorkView& wv, const Layout& L, int item) {
+    const int ntile = wv.tiles_x * wv.tiles_y;
+    const int tile = item % ntile, chunk = item / ntile;
+    tx = wv.tile_x;
+    ty = wv.tile_y;
+    i0 = (tile % wv.tiles_x) * wv.tile_x;
+    j0 = (tile / wv.tiles_x) * wv.tile_y;
+    k0 = chunk * wv.chunk_z;
+    k1 = min(k0 + wv.chunk_z, L.nz);
+  }
+};
+
+// Energy of Sec. 4.4, W = 1/2 <Q^e y, y> with Q^e = [[I - a^2 R_0, a L],
+// [a L^T, I - a^2 R_1]], in integral variables: the share of node index
+// (i,j,k) is 1/2 sum_c M_c f_c^2 - a^2/2 (M_mux^-1 (P_y ez)^2 +
+// M_muy^-1 (P_x ez)^2 + M_epsx^-1 (P_y^T hz)^2 + M_epsy^-1 (P_x^T hz)^2)
+// + a (hx P_z ey - hy P_z ex). One partial per work item.
 template <typename T>
-__global__ void energy_pass1(const T* __restrict__ ex, const T* __restrict__ ey,
+__global__ void energy_items(const T* __restrict__ ex, const T* __restrict__ ey,
                              const T* __restrict__ ez, const T* __restrict__ hx,
                              const T* __restrict__ hy, const T* __restrict__ hz, MinvView mv,
-                             Layout L, double alpha, double* part) {
-  const long long total = (long long)L.nx * L.ny * L.nz;
-  const long long stride = (long long)gridDim.x * blockDim.x;
-  double acc = 0.0;
+                             Layout L, WorkView wv, double alpha, double* part) {
+  const int item = wv.items ? wv.items[blockIdx.x] : (int)blockIdx.x;
+  const ItemCells ic(wv, L, item);
   const long long sx = 1, sy = L.px, sz = L.sz;
-  for (long long q = (long long)blockIdx.x * blockDim.x + threadIdx.x; q < total; q += stride) {
-    const int i = (int)(q % L.nx);
-    const int j = (int)((q / L.nx) % L.ny);
-    const int k = (int)(q / ((long long)L.nx * L.ny));
-    const long long id = L.idx(i, j, k);
-    if (mv.mask[id] == 0) continue;  // no field object here: every term is zero
-    const T* f[6] = {ex, ey, ez, hx, hy, hz};
-    double w = 0.0;
-    double mi[6];
-    for (int c = 0; c < 6; ++c) {
-      mi[c] = mv(c, id);
-      if (mi[c] != 0.0) {
-        const double v = (double)f[c][id];
-        w += 0.5 * v * v * mv.m(c, id);
+  const T* f[6] = {ex, ey, ez, hx, hy, hz};
+  const bool uniform = mv.a[0] == nullptr;
+  // uniform material: per-component sums of squares, scaled once at the end
+  double sq[6] = {0, 0, 0, 0, 0, 0};
+  double rq[4] = {0, 0, 0, 0};  // (P_y ez)^2 on hx faces, (P_x ez)^2 on hy faces, (P_y^T hz)^2 on ex, (P_x^T hz)^2 on ey
+  double acc = 0.0;             // cross terms (and everything, for material arrays)
+  for (int c = threadIdx.x; c < ic.tx * ic.ty; c += blockDim.x) {
+    const int i = ic.i0 + c % ic.tx, j = ic.j0 + c / ic.tx;
+    if (i >= L.nx || j >= L.ny) continue;
+    for (int k = ic.k0; k < ic.k1; ++k) {
+      const long long id = L.idx(i, j, k);
+      const uint8_t m = mv.mask[id];
+      if (m == 0) continue;  // no field object here: every term is zero
+      const double pyez = (double)ez[id + sy] - (double)ez[id];
+      const double pxez = (double)ez[id + sx] - (double)ez[id];
+      const double ptyhz = (double)hz[id - sy] - (double)hz[id];
+      const double ptxhz = (double)hz[id - sx] - (double)hz[id];
+      const double l = (double)hx[id] * ((double)ey[id + sz] - (double)ey[id]) -
+                       (double)hy[id] * ((double)ex[id + sz] - (double)ex[id]);
+      if (uniform) {
+        // inactive entries hold zero fields, so their squares add nothing
+        for (int q = 0; q < 6; ++q) {
+          const double v = (double)f[q][id];
+          sq[q] += v * v;
+        }
+        if (m & 8) rq[0] += pyez * pyez;
+        if (m & 16) rq[1] += pxez * pxez;
+        if (m & 1) rq[2] += ptyhz * ptyhz;
+        if (m & 2) rq[3] += ptxhz * ptxhz;
+        acc += alpha * l;
+      } else {
+        double w = 0.0;
+        for (int q = 0; q < 6; ++q) {
+          const double v = (double)f[q][id];
+          w += 0.5 * v * v * mv.m(q, id);
+        }
+        const double r = mv(kHX, id) * pyez * pyez + mv(kHY, id) * pxez * pxez +
+                         mv(kEX, id) * ptyhz * ptyhz + mv(kEY, id) * ptxhz * ptxhz;
+        acc += w - 0.5 * alpha * alpha * r + alpha * l;
       }
     }
-    const double pyez = (double)ez[id + sy] - (double)ez[id];
-    const double pxez = (double)ez[id + sx] - (double)ez[id];
-    const double ptyhz = (double)hz[id - sy] - (double)hz[id];
-    const double ptxhz = (double)hz[id - sx] - (double)hz[id];
-    const double r = mi[kHX] * pyez * pyez + mi[kHY] * pxez * pxez + mi[kEX] * ptyhz * ptyhz +
-                     mi[kEY] * ptxhz * ptxhz;
-    const double l = (double)hx[id] * ((double)ey[id + sz] - (double)ey[id]) -
-                     (double)hy[id] * ((double)ex[id + sz] - (double)ex[id]);
-    acc += w - 0.5 * alpha * alpha * r + alpha * l;
+  }
+  if (uniform) {
+    for (int q = 0; q < 6; ++q) acc += 0.5 * mv.r[q] * sq[q];
+    acc -= 0.5 * alpha * alpha *
+           (mv.c[kHX] * rq[0] + mv.c[kHY] * rq[1] + mv.c[kEX] * rq[2] + mv.c[kEY] * rq[3]);
   }
   const double b = block_reduce<false>(acc);
   if (threadIdx.x == 0) part[blockIdx.x] = b;
@@ -143,41 +181,50 @@ struct ChargeFields {
   const void* prev[6];
 };
 
+// Charge balances over the nodes and cells of one work item. Marching up a
+// column, the corrected z-fluxes of Eq. (35) and Eq. (34) on the edge/face
+// below are those computed one plane earlier.
 template <typename T>
-__global__ void charge_pass1(ChargeFields cf, MinvView mv, Layout L, double alpha,
+__global__ void charge_items(ChargeFields cf, MinvView mv, Layout L, WorkView wv, double alpha,
                              const double* qline, int i0, int j0, double* part_e, double* part_h) {
   const T* const* cur = reinterpret_cast<const T* const*>(cf.cur);
   const T* const* prv = reinterpret_cast<const T* const*>(cf.prev);
-  const long long total = (long long)(L.nx + 1) * (L.ny + 1) * (L.nz + 1);
-  const long long stride = (long long)gridDim.x * blockDim.x;
+  const int item = wv.items ? wv.items[blockIdx.x] : (int)blockIdx.x;
+  const ItemCells ic(wv, L, item);
   const long long sx = 1, sy = L.px, sz = L.sz;
   const double a2 = alpha * alpha;
   double me = 0.0, mh = 0.0;
-  for (long long q = (long long)blockIdx.x * blockDim.x + threadIdx.x; q < total; q += stride) {
-    const int i = (int)(q % (L.nx + 1));
-    const int j = (int)((q / (L.nx + 1)) % (L.ny + 1));
-    const int k = (int)(q / ((long long)(L.nx + 1) * (L.ny + 1)));
-    const long long n = L.idx(i, j, k);
-    const uint8_t m0 = mv.mask[n];
-    if (m0 == 0) continue;  // neither the node's edges nor the cell's faces start here
-    // Eq. (35) at node n: six incident edges active
-    if ((m0 & 7) == 7 && mv(kEX, n) != 0.0 && mv(kEX, n - sx) != 0.0 && mv(kEY, n) != 0.0 &&
-        mv(kEY, n - sy) != 0.0 && mv(kEZ, n) != 0.0 && mv(kEZ, n - sz) != 0.0) {
-      const double qe =
-          -(dbar(cur[kEX], prv[kEX], mv, kEX, n - sx) - dbar(cur[kEX], prv[kEX], mv, kEX, n)) -
-          (dbar(cur[kEY], prv[kEY], mv, kEY, n - sy) - dbar(cur[kEY], prv[kEY], mv, kEY, n)) -
-          (dz_tilde(cur[kEZ], mv, n - sz, sx, sy, a2) - dz_tilde(cur[kEZ], mv, n, sx, sy, a2));
-      const double qb = (qline && i == i0 && j == j0) ? qline[k] : 0.0;
-      me = fmax(me, fabs(qe - qb));
-    }
-    // Eq. (34) at the cell whose lower node is n: six faces active
-    if ((m0 & 56) == 56 && mv(kHX, n) != 0.0 && mv(kHX, n + sx) != 0.0 && mv(kHY, n) != 0.0 &&
-        mv(kHY, n + sy) != 0.0 && mv(kHZ, n) != 0.0 && mv(kHZ, n + sz) != 0.0) {
-      const double qh =
-          (bbar(cur[kHX], prv[kHX], mv, kHX, n + sx) - bbar(cur[kHX], prv[kHX], mv, kHX, n)) +
-          (bbar(cur[kHY], prv[kHY], mv, kHY, n + sy) - bbar(cur[kHY], prv[kHY], mv, kHY, n)) +
-          (bz_tilde(prv[kHZ], mv, n + sz, sx, sy, a2) - bz_tilde(prv[kHZ], mv, n, sx, sy, a2));
-      mh = fmax(mh, fabs(qh));
+  for (int c = threadIdx.x; c < ic.tx * ic.ty; c += blockDim.x) {
+    const int i = ic.i0 + c % ic.tx, j = ic.j0 + c / ic.tx;
+    if (i >= L.nx || j >= L.ny) continue;
+    long long n = L.idx(i, j, ic.k0);
+    double dz_below = dz_tilde(cur[kEZ], mv, n - sz, sx, sy, a2);  // edge (i,j,k0-1/2)
+    double bz_here = bz_tilde(prv[kHZ], mv, n, sx, sy, a2);        // face (i+1/2,j+1/2,k0)
+    for (int k = ic.k0; k < ic.k1; ++k, n += sz) {
+      const double dz_here = dz_tilde(cur[kEZ], mv, n, sx, sy, a2);
+      const double bz_above = bz_tilde(prv[kHZ], mv, n + sz, sx, sy, a2);
+      const uint8_t m0 = mv.mask[n];
+      // Eq. (35) at node n: six incident edges active
+      if ((m0 & 7) == 7 && mv(kEX, n - sx) != 0.0 && mv(kEY, n - sy) != 0.0 &&
+          mv(kEZ, n - sz) != 0.0) {
+        const double qe =
+            -(dbar(cur[kEX], prv[kEX], mv, kEX, n - sx) - dbar(cur[kEX], prv[kEX], mv, kEX, n)) -
+            (dbar(cur[kEY], prv[kEY], mv, kEY, n - sy) - dbar(cur[kEY], prv[kEY], mv, kEY, n)) -
+            (dz_below - dz_here);
+        const double qb = (qline && i == i0 && j == j0) ? qline[k] : 0.0;
+        me = fmax(me, fabs(qe - qb));
+      }
+      // Eq. (34) at the cell whose lower node is n: six faces active
+      if ((m0 & 56) == 56 && mv(kHX, n + sx) != 0.0 && mv(kHY, n + sy) != 0.0 &&
+          mv(kHZ, n + sz) != 0.0) {
+        const double qh =
+            (bbar(cur[kHX], prv[kHX], mv, kHX, n + sx) - bbar(cur[kHX], prv[kHX], mv, kHX, n)) +
+            (bbar(cur[kHY], prv[kHY], mv, kHY, n + sy) - bbar(cur[kHY], prv[kHY], mv, kHY, n)) +
+            (bz_above - bz_here);
+        mh = fmax(mh, fabs(qh));
+      }
+      dz_below = dz_here;
+      bz_here = bz_above;
     }
   }
   const double be = block_reduce<true>(me);
@@ -199,22 +246,19 @@ MinvView make_view(const uint8_t* mask, const double* minv, const double* const 
   return v;
 }
 
-int blocks_for(long long total, int cap) {
-  long long b = (total + kBlock - 1) / kBlock;
-  if (b > cap) b = cap;
-  if (b > kMaxBlocks) b = kMaxBlocks;
-  return b < 1 ? 1 : (int)b;
-}
 
 }  // namespace
 
 template <typename T>
 cudaError_t launch_energy(const T* const f[6], const uint8_t* mask, const double* minv,
                           const double* const minv_a[6], const Layout& L, double alpha,
-                          const DiagScratch& s, double* result, cudaStream_t st) {
-  const int nb = blocks_for((long long)L.nx * L.ny * L.nz, s.cap);
-  energy_pass1<T><<<nb, kBlock, 0, st>>>(f[0], f[1], f[2], f[3], f[4], f[5],
-                                          make_view(mask, minv, minv_a), L, alpha, s.part);
+                          const WorkView& wv, const DiagScratch& s, double* result,
+                          cudaStream_t st) {
+  const int nb = wv.n_items;
+  if (nb > s.cap) return cudaErrorInvalidValue;
+  if (nb == 0) return cudaMemsetAsync(result, 0, sizeof(double), st);
+  energy_items<T><<<nb, kBlock, 0, st>>>(f[0], f[1], f[2], f[3], f[4], f[5],
+                                          make_view(mask, minv, minv_a), L, wv, alpha, s.part);
   reduce_pass2<false><<<1, 1024, 0, st>>>(s.part, nb, result);
   return cudaGetLastError();
 }
@@ -222,15 +266,20 @@ cudaError_t launch_energy(const T* const f[6], const uint8_t* mask, const double
 template <typename T>
 cudaError_t launch_charge(const T* const cur[6], const T* const prev[6], const uint8_t* mask,
                           const double* minv, const double* const minv_a[6], const Layout& L,
-                          double alpha, const double* qline, int i0, int j0,
+                          double alpha, const double* qline, int i0, int j0, const WorkView& wv,
                           const DiagScratch& s, double* res_e, double* res_h, cudaStream_t st) {
-  const int nb = blocks_for((long long)(L.nx + 1) * (L.ny + 1) * (L.nz + 1), s.cap / 2);
+  const int nb = wv.n_items;
+  if (2 * nb > s.cap) return cudaErrorInvalidValue;
+  if (nb == 0) {
+    cudaError_t e = cudaMemsetAsync(res_e, 0, sizeof(double), st);
+    return e != cudaSuccess ? e : cudaMemsetAsync(res_h, 0, sizeof(double), st);
+  }
   ChargeFields cf;
   for (int c = 0; c < 6; ++c) {
     cf.cur[c] = cur[c];
     cf.prev[c] = prev[c];
   }
-  charge_pass1<T><<<nb, kBlock, 0, st>>>(cf, make_view(mask, minv, minv_a), L, alpha, qline,
+  charge_items<T><<<nb, kBlock, 0, st>>>(cf, make_view(mask, minv, minv_a), L, wv, alpha, qline,
                                           i0, j0, s.part, s.part + nb);
   reduce_pass2<true><<<1, 1024, 0, st>>>(s.part, nb, res_e);
   reduce_pass2<true><<<1, 1024, 0, st>>>(s.part + nb, nb, res_h);
@@ -268,17 +317,21 @@ cudaError_t launch_bunch_charge(double q, double sigma, double dz, double zc, in
 
 template cudaError_t launch_energy<float>(const float* const[6], const uint8_t*, const double*,
                                           const double* const[6], const Layout&, double,
-                                          const DiagScratch&, double*, cudaStream_t);
+                                          const WorkView&, const DiagScratch&, double*,
+                                          cudaStream_t);
 template cudaError_t launch_energy<double>(const double* const[6], const uint8_t*, const double*,
                                            const double* const[6], const Layout&, double,
-                                           const DiagScratch&, double*, cudaStream_t);
+                                           const WorkView&, const DiagScratch&, double*,
+                                           cudaStream_t);
 template cudaError_t launch_charge<float>(const float* const[6], const float* const[6],
                                           const uint8_t*, const double*, const double* const[6],
                                           const Layout&, double, const double*, int, int,
-                                          const DiagScratch&, double*, double*, cudaStream_t);
+                                          const WorkView&, const DiagScratch&, double*, double*,
+                                          cudaStream_t);
 template cudaError_t launch_charge<double>(const double* const[6], const double* const[6],
                                            const uint8_t*, const double*, const double* const[6],
                                            const Layout&, double, const double*, int, int,
-                                           const DiagScratch&, double*, double*, cudaStream_t);
+                                           const WorkView&, const DiagScratch&, double*, double*,
+                                           cudaStream_t);
 
 }  // namespace tetm

@@ -105,7 +105,15 @@ cudaError_t launch_fused_warp_batch(const BatchMember<T>* members, int n_members
 struct DiagScratch {
   double* part;   // per-block partials
   int cap;        // entries of part
-  double* out;    // device result slots (at least 4)
+  double* out;    // device result slots (at least 8)
+};
+
+// The fused kernels' work items, which the balance reductions also walk:
+// entries outside them lie in cells that carry no field.
+struct WorkView {
+  const int* items;  // active (tile, chunk) items; nullptr = every item
+  int n_items;
+  int tile_x, tile_y, chunk_z, tiles_x, tiles_y;
 };
 
 // Discrete energy W^{n,e} into *result (device); minv[c] constants (mask
@@ -113,14 +121,15 @@ struct DiagScratch {
 template <typename T>
 cudaError_t launch_energy(const T* const f[6], const uint8_t* mask, const double* minv,
                           const double* const minv_a[6], const Layout& L, double alpha,
-                          const DiagScratch& s, double* result, cudaStream_t st);
+                          const WorkView& wv, const DiagScratch& s, double* result,
+                          cudaStream_t st);
 
 // Charge residuals of the last step into device slots: *res_e = max|qe - qbunch|,
 // *res_h = max|qh|.
 template <typename T>
 cudaError_t launch_charge(const T* const cur[6], const T* const prev[6], const uint8_t* mask,
                           const double* minv, const double* const minv_a[6], const Layout& L,
-                          double alpha, const double* qline, int i0, int j0,
+                          double alpha, const double* qline, int i0, int j0, const WorkView& wv,
                           const DiagScratch& s, double* res_e, double* res_h, cudaStream_t st);
 
 // Truncated Gaussian bunch charge in the dual cell of each node k = 0..nz of
