@@ -54,7 +54,9 @@ def parse_args():
     p.add_argument("--solves", type=int, default=64, help="batch: number of solves")
     p.add_argument("--precision", default=None, choices=[None, "fp32", "fp64"])
     p.add_argument("--balance-every", type=int, default=250)
-    p.add_argument("--tiling", default=None, help="tile_x,tile_y,chunk_z")
+    p.add_argument("--tiling", default=None,
+                   help="tile_x,tile_y,chunk_z (default: chosen by the autotuner, untimed)")
+    p.add_argument("--no-autotune", action="store_true", help="keep the library's default shape")
     p.add_argument("--kernel", default="fused", choices=["fused", "reference"])
     p.add_argument("--no-e2e", action="store_true")
     p.add_argument("--no-cpu-baseline", action="store_true")
@@ -281,7 +283,14 @@ def run_tetm(args):
     s.set_stream(stream.cuda_stream)
     s.set_kernel(args.kernel)
     if args.tiling:
-        s.set_tiling(*[int(x) for x in args.tiling.split(",")])
+        args.tiling_used = tuple(int(x) for x in args.tiling.split(","))
+    elif args.kernel == "fused" and not args.no_autotune:
+        from paper_0901_1053_gb300.autotune import Autotuner
+        args.tiling_used = Autotuner().tune(w, w.precision)
+    else:
+        args.tiling_used = None
+    if args.tiling_used:
+        s.set_tiling(*args.tiling_used)
     s.set_balance_every(args.balance_every)
     info = s.info()
     s.step(args.warmup)
@@ -341,8 +350,8 @@ def run_tetm(args):
         s2 = tetm.Solver(w.nx, w.ny, w.nz, w.dx, w.dy, w.dz, w.cdt, w.precision, pec=pinned)
         s2.set_bunch(w.sigma, w.charge, w.i0, w.j0)
         s2.set_kernel(args.kernel)
-        if args.tiling:
-            s2.set_tiling(*[int(x) for x in args.tiling.split(",")])
+        if args.tiling_used:
+            s2.set_tiling(*args.tiling_used)
         s2.step(steps_e2e)
         wk2 = s2.wake()[0]
         out[:] = wk2

@@ -91,13 +91,46 @@ class Autotuner:
             s.close()
         return out
 
+    def wave_fitted(self, w, precision: str, tile_ys=(12, 20, 28), max_extra: int = 6):
+        """Shapes (28, ty, cz) whose work-item count fills whole waves of the
+        resident warps (16 per SM): for each tile height, the chunk lengths
+        around the one that gives one or two full waves."""
+        from . import tetm
+        try:
+            import torch
+            sms = torch.cuda.get_device_properties(0).multi_processor_count
+        except Exception:
+            sms = 152
+        slots = 16 * sms
+        s = tetm.Solver(w.nx, w.ny, w.nz, w.dx, w.dy, w.dz, w.cdt, precision, pec=w.pec)
+        out = []
+        try:
+            for ty in tile_ys:
+                s.set_tiling(28, ty, 32)
+                items32 = s.info()["work_items"]
+                for waves in (1, 2):
+                    cz = max(4, int(round(32 * items32 / (waves * slots))))
+                    best = None
+                    for c in range(max(4, cz - max_extra), cz + max_extra + 1):
+                        s.set_tiling(28, ty, c)
+                        n = s.info()["work_items"]
+                        eff = n / (slots * -(-n // slots))
+                        if best is None or eff > best[0] + 1e-9:
+                            best = (eff, c)
+                    out.append((28, ty, best[1]))
+        finally:
+            s.close()
+        return sorted(set(out))
+
     def tune(self, w, precision: Optional[str] = None,
              candidates: Optional[Sequence[Shape]] = None) -> Shape:
         precision = precision or w.precision
         k = self.key(w, precision)
         if k in self.cache:
             return tuple(self.cache[k])
-        cands = candidates or (CANDIDATES_FP32 if precision == "fp32" else CANDIDATES_FP64)
+        cands = list(candidates or (CANDIDATES_FP32 if precision == "fp32" else CANDIDATES_FP64))
+        if candidates is None:
+            cands += [c for c in self.wave_fitted(w, precision) if c not in cands]
         times = self.measure(w, precision, cands)
         best = min(times, key=times.get)
         self.cache[k] = list(best)

@@ -7,7 +7,7 @@
 
 #include <vector>
 
-#include "../../include/tetm.h"
+#include "tetm.h"
 
 namespace tetm {
 
