@@ -48,7 +48,7 @@ def parse_args():
     p.add_argument("--warmup", type=int, default=20)
     p.add_argument("--impl", default="tetm", choices=["tetm", "reference"])
     p.add_argument("--workload", default="collimator",
-                   choices=["collimator", "plain_pipe", "batch", "serve"])
+                   choices=["collimator", "plain_pipe", "batch", "serve", "dielectric"])
     p.add_argument("--requests", type=int, default=2000, help="serve: requests in the stream")
     p.add_argument("--rate", type=float, default=40.0, help="serve: mean arrivals per second")
     p.add_argument("--solves", type=int, default=64, help="batch: number of solves")
@@ -70,6 +70,12 @@ def parse_args():
 
 def make_workload(args):
     from paper_0901_1053_gb300 import workloads as wl
+    args.eps = None
+    if args.workload == "dielectric":
+        w, args.eps = wl.dielectric_collimator(n=256, nz=args.nz or 1024)
+        if args.precision:
+            w.precision = args.precision
+        return w
     if args.workload == "plain_pipe":
         w = wl.plain_pipe(nz=args.nz or 96, n=args.n or 24)
     else:
@@ -279,7 +285,9 @@ def run_tetm(args):
     from paper_0901_1053_gb300 import tetm
     w = make_workload(args)
     stream = torch.cuda.current_stream()
-    s = tetm.Solver.from_workload(w)
+    s = tetm.Solver(w.nx, w.ny, w.nz, w.dx, w.dy, w.dz, w.cdt, w.precision, eps_r=args.eps,
+                    pec=w.pec)
+    s.set_bunch(w.sigma, w.charge, w.i0, w.j0)
     s.set_stream(stream.cuda_stream)
     s.set_kernel(args.kernel)
     if args.tiling:
@@ -325,11 +333,15 @@ def run_tetm(args):
     max_ms = dist.max(total_ms)
 
     esz = 4 if w.precision == "fp32" else 8
-    bytes_per_cell = 12 * esz + 1
+    # 12 field words and either the activity byte or, with per-cell materials,
+    # the six coefficient words
+    bytes_per_cell = 12 * esz + 1 if args.eps is None else 18 * esz
     proc = info["processed_cells"] if args.kernel == "fused" else w.cells
     achieved = bytes_per_cell * proc / (kern_ms * 1e-3) / 1e9
     peak, peak_kind = measured_peak_hbm()
     kname = "fused_step_warp" if info["tile_x"] == 28 else "fused_step"
+    if args.eps is not None:
+        kname = "fused_step_warp_mat"
     prof_name = "%s_%s_%s.md" % (kname, w.precision, w.name)
     traffic = profiled_traffic(prof_name) if args.kernel == "fused" else None
     wake = s.wake()[0]
@@ -347,7 +359,8 @@ def run_tetm(args):
         dist.barrier()
         torch.cuda.synchronize()
         t0 = time.perf_counter()
-        s2 = tetm.Solver(w.nx, w.ny, w.nz, w.dx, w.dy, w.dz, w.cdt, w.precision, pec=pinned)
+        s2 = tetm.Solver(w.nx, w.ny, w.nz, w.dx, w.dy, w.dz, w.cdt, w.precision, eps_r=args.eps,
+                         pec=pinned)
         s2.set_bunch(w.sigma, w.charge, w.i0, w.j0)
         s2.set_kernel(args.kernel)
         if args.tiling_used:
@@ -391,7 +404,7 @@ def run_tetm(args):
                      "bytes_per_cell": bytes_per_cell, "cells_per_launch": proc},
         "cpu_baseline": cpu,
         "e2e": e2e,
-        "gpu_launches": K + 6 * n_bal if args.kernel == "fused" else 10 * K + 6 * n_bal,
+        "gpu_launches": (K if args.kernel == "fused" else 10 * K) + 7 * n_bal,
         "clocks": clk,
         "balances": {"records": int(hist.shape[0]),
                      "max_charge_residual_rel": float(np.max(hist[:, 2] / np.maximum(hist[:, 4], 1e-300)))

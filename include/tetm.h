@@ -173,9 +173,10 @@ int tetm_set_fields(tetm_solver* s, int32_t comp, const double* host);
  * all later device work of the solve. The stream is not owned. */
 int tetm_set_stream(tetm_solver* s, void* cuda_stream);
 
-/* Select the update kernels (TETM_KERNEL_*). The fused kernel needs every
- * active coefficient of a component to be equal (vacuum or one material
- * plus PEC); otherwise TETM_E_UNSUPPORTED. */
+/* Select the update kernels (TETM_KERNEL_*). With general materials (per-cell
+ * eps_r / mu_r that differ) the fused path streams per-entry coefficient
+ * arrays and needs the warp-tiled work shape (tile_x = 28, the default);
+ * the block-tiled shapes then give TETM_E_UNSUPPORTED. */
 int tetm_set_kernel(tetm_solver* s, int32_t kernel);
 
 /* Fused-kernel work shape: transverse tile tile_x x tile_y and z-chunk

@@ -501,7 +501,7 @@ int tetm_create(const tetm_grid* g, const double* eps_r, const double* mu_r, con
   s->L = make_layout(g->nx, g->ny, g->nz, (int)s->esz);
   s->alpha = 0.5 * cdt / kC;
   s->stream = nullptr;
-  s->kernel = uniform ? TETM_KERNEL_FUSED : TETM_KERNEL_REFERENCE;
+  s->kernel = TETM_KERNEL_FUSED;
   s->uniform = uniform;
   s->tile_x = 28;   // warp-tiled kernel (kernels_warp.cu)
   s->tile_y = 20;
@@ -627,7 +627,7 @@ int tetm_set_stream(tetm_solver* s, void* st) {
 int tetm_set_kernel(tetm_solver* s, int32_t kernel) {
   if (!s || (kernel != TETM_KERNEL_FUSED && kernel != TETM_KERNEL_REFERENCE)) return TETM_E_ARG;
   if (s->in_batch) return TETM_E_STATE;
-  if (kernel == TETM_KERNEL_FUSED && !s->uniform) return TETM_E_UNSUPPORTED;
+  if (kernel == TETM_KERNEL_FUSED && !s->uniform && s->tile_x != 28) return TETM_E_UNSUPPORTED;
   s->kernel = kernel;
   return TETM_OK;
 }
@@ -639,6 +639,8 @@ int tetm_set_tiling(tetm_solver* s, int32_t tile_x, int32_t tile_y, int32_t chun
   const int ty = tile_y ? tile_y : s->tile_y;
   const int cz = chunk_z ? chunk_z : s->chunk_z;
   if ((!fused_shape_ok(tx, ty) && !warp_shape_ok(tx, ty)) || cz < 4) return TETM_E_ARG;
+  // per-entry coefficients (general materials) run on the warp-tiled kernel only
+  if (!s->uniform && tx != 28 && s->kernel == TETM_KERNEL_FUSED) return TETM_E_UNSUPPORTED;
   if (tx == s->tile_x && ty == s->tile_y && cz == s->chunk_z && s->work) return TETM_OK;
   s->tile_x = tx;
   s->tile_y = ty;

@@ -600,6 +600,212 @@ cudaError_t launch_batch_shape(const BatchMember<T>* members, const int2* work, 
     return launch_batch_kernel<T, TY, false>(fused_step_warp_reg_batch<T, TY>, members, work, n_work, st);
 }
 
+
+// ---------------------------------------------------------------------------
+// General materials: the six update coefficients are per-entry arrays
+// (alpha M^-1 and 2 alpha M^-1 of each edge and face, zero on PEC and outside
+// the box) streamed through the asynchronous-copy ring with the fields, four
+// rows ahead. Each row's TE coefficients are carried to the TE lags of the
+// sweep. Same sweep and lags as fused_step_warp.
+// ---------------------------------------------------------------------------
+constexpr int kMatDepth = 4;
+constexpr int kMatArrs = 14;  // 8 field entries as in kArrs, then u_ex u_ey u_ez u_hx u_hy u_hz
+
+template <typename T, int TY>
+__device__ __forceinline__ void fused_step_warp_mat_item(const StepArgs<T>& a, int item,
+                                                         unsigned char* smem_raw) {
+  constexpr int RH = TY + 4;
+  static_assert(RH % kMatDepth == 0, "rows per tile must be a multiple of the ring depth");
+  const int lane = threadIdx.x & 31;
+  const int wib = threadIdx.x >> 5;
+  T* wbase = reinterpret_cast<T*>(smem_raw) + (size_t)wib * (kMatDepth * kMatArrs + 2 * RH) * 32;
+  T* ring = wbase;
+  T* sHXP = wbase + kMatDepth * kMatArrs * 32;
+  T* sHYP = sHXP + RH * 32;
+
+  const Layout L = a.L;
+  const long long SZ = L.sz;
+  const long long PX = L.px;
+  const T* __restrict__ iex = a.in[kEX];
+  const T* __restrict__ iey = a.in[kEY];
+  const T* __restrict__ iez = a.in[kEZ];
+  const T* __restrict__ ihx = a.in[kHX];
+  const T* __restrict__ ihy = a.in[kHY];
+  const T* __restrict__ ihz = a.in[kHZ];
+  T* __restrict__ oex = a.out[kEX];
+  T* __restrict__ oey = a.out[kEY];
+  T* __restrict__ oez = a.out[kEZ];
+  T* __restrict__ ohx = a.out[kHX];
+  T* __restrict__ ohy = a.out[kHY];
+  T* __restrict__ ohz = a.out[kHZ];
+
+  const int ntile = a.tiles_x * a.tiles_y;
+  const int tile = item % ntile, chunk = item / ntile;
+  const int gi = (tile % a.tiles_x) * kWarpTileX - 2 + lane;
+  const int jbase = (tile / a.tiles_x) * TY - 2;
+  const int ci = min(gi, L.nx + 1);
+  const bool own_x = lane >= 2 && lane < kWarpTileX + 2 && gi < L.nx;
+  const bool line_x = a.b.on && gi == a.b.i0;
+  const int line_r = a.b.j0 - jbase;
+  const int own_r_end = min(TY + 2, L.ny - jbase);
+  const int k0 = chunk * a.chunk_z;
+  const int k1 = min(k0 + a.chunk_z, L.nz);
+  const int kstart = k0 - 1;
+
+  auto index = [&](int k, int r) -> long long {
+    const int j = min(jbase + r, L.ny + 1);
+    return (long long)(k + 1) * SZ + (long long)(j + 2) * PX + (ci + L.ox);
+  };
+  auto issue_row = [&](int g) {
+    const int k = kstart + g / RH, r = g % RH;
+    const long long id = index(k, r);
+    T* sl = ring + (g % kMatDepth) * kMatArrs * 32 + lane;
+    const T* src[kMatArrs] = {iez + id, ihx + id, ihy + id, ihz + id, iex + id, iey + id,
+                              iex + id + SZ, iey + id + SZ,
+                              a.co.ua[kEX] + id, a.co.ua[kEY] + id, a.co.ua[kEZ] + id,
+                              a.co.ua[kHX] + id, a.co.ua[kHY] + id, a.co.ua[kHZ] + id};
+#pragma unroll
+    for (int q = 0; q < kMatArrs; ++q) {
+      if (sizeof(T) == 4) cp_async4(sl + q * 32, src[q]);
+      else cp_async8(sl + q * 32, src[q]);
+    }
+    cp_async_commit();
+  };
+
+  for (int r = 0; r < RH; ++r) {
+    sHXP[r * 32 + lane] = T(0);
+    sHYP[r * 32 + lane] = T(0);
+  }
+#pragma unroll
+  for (int q = 0; q < kMatDepth; ++q) issue_row(q);
+  int g = 0;
+
+  for (int k = kstart; k < k1; ++k) {
+    const bool te = k >= k0;
+    T hxa_p = T(0), dey_p = T(0), cHX_p = T(0), ezn_p = T(0);
+    T hyn_p = T(0), hyn_pp = T(0), hxn_pp = T(0);
+    T hz_p = T(0), hz_pp = T(0);
+    T cEX_p = T(0), cEY_p = T(0), cHZ_p = T(0);     // TE coefficients of row r-1
+    T cEX_pp = T(0), cEY_pp = T(0), cHZ_pp = T(0);  // ... and of row r-2
+    T ex0_p = T(0), ey0_p = T(0);
+    T exa_pp = T(0), eya_pp = T(0), hzn_ppp = T(0);
+#pragma unroll 1
+    for (int rg = 0; rg < RH; rg += kMatDepth) {
+#pragma unroll
+      for (int u = 0; u < kMatDepth; ++u) {
+        const int r = rg + u;
+        cp_async_wait<kMatDepth - 2>();  // rows g and g+1 have landed
+        const T* sl = ring + u * kMatArrs * 32 + lane;
+        const T ez = sl[0], hx = sl[32], hy = sl[64], hz = sl[96];
+        const T ex0r = sl[128], ey0r = sl[160], ex1 = sl[192], ey1 = sl[224];
+        const T cEX = sl[256], cEY = sl[288], cEZ = sl[320];
+        const T cHX = sl[352], cHY = sl[384], cHZ = sl[416];
+        const T ez_next = ring[((u + 1) % kMatDepth) * kMatArrs * 32 + lane];  // row r+1
+        issue_row(g + kMatDepth);
+        ++g;
+
+        const long long id = index(k, r);
+        const bool own_r = r >= 2 && r < own_r_end;
+        // ---------------- TM stage, row r ----------------
+        const T dey = ey1 - ey0r, dex = ex1 - ex0r;
+        const T hxa = hx + cHX * (dey - (ez_next - ez));                         // U1
+        const T hya = hy + cHY * (-dex + (shfl_dn(ez) - ez));                    // U2
+        T cur = (hxa_p - hxa) - (shfl_up1(hya) - hya);
+        const bool line = line_x && r == line_r;
+        if (line && k >= 0) {
+          const long long dd = (long long)k - a.n + a.b.c0;
+          if (dd >= -a.b.c0 && dd < a.b.c0) cur -= a.b.J[dd + a.b.c0];
+        }
+        const T ezn = ez + cEZ * cur;                                            // U3
+        const T hyn = hya + cHY * (-dex + (shfl_dn(ezn) - ezn));                 // U5
+        const T hxn_p = hxa_p + cHX_p * (dey_p - (ezn - ezn_p));                 // U4, row r-1
+        if (te && own_x) {
+          if (own_r) {
+            oez[id] = ezn;
+            ohy[id] = hyn;
+            if (line) {
+              const long long mm = a.n - k - a.b.c0;
+              if (mm >= a.b.m_min && mm <= a.b.m_max)
+                a.b.W[mm - a.b.m_min] -= (double)ezn * a.b.inv_q;
+            }
+          }
+          if (r - 1 >= 2 && r - 1 < own_r_end) ohx[id - PX] = hxn_p;
+        }
+        // ---------------- TE stage, rows q = r-1 and p = r-2 ----------------
+        const int q = r - 1, p = r - 2;
+        const T hxq_old = q >= 0 ? sHXP[q * 32 + lane] : T(0);
+        const T hyq_old = q >= 0 ? sHYP[q * 32 + lane] : T(0);
+        const T exa = ex0_p + cEX_p * ((hyq_old - hyn_p) - (hz_pp - hz_p));           // U6, row q
+        const T eya = ey0_p + cEY_p * (-(hxq_old - hxn_p) + (shfl_up1(hz_p) - hz_p));  // U7, row q
+        const T hzn = hz_pp + cHZ_pp * ((exa - exa_pp) - (shfl_dn(eya_pp) - eya_pp)); // U8, row p
+        const T hxp_old = p >= 0 ? sHXP[p * 32 + lane] : T(0);
+        const T hyp_old = p >= 0 ? sHYP[p * 32 + lane] : T(0);
+        const T exn = exa_pp + cEX_pp * ((hyp_old - hyn_pp) - (hzn_ppp - hzn));     // U9, row p
+        const T eyn = eya_pp + cEY_pp * (-(hxp_old - hxn_pp) + (shfl_up1(hzn) - hzn));  // U10, row p
+        if (te && own_x && p >= 2 && p < own_r_end) {
+          const long long idp = id - 2 * PX;
+          oex[idp] = exn;
+          oey[idp] = eyn;
+          ohz[idp] = hzn;
+        }
+        if (p >= 0) {
+          sHXP[p * 32 + lane] = hxn_pp;
+          sHYP[p * 32 + lane] = hyn_pp;
+        }
+        if (r == RH - 1) sHYP[q * 32 + lane] = hyn_p;
+        hxn_pp = hxn_p;
+        hyn_pp = hyn_p;
+        hyn_p = hyn;
+        hxa_p = hxa; dey_p = dey; cHX_p = cHX; ezn_p = ezn;
+        hz_pp = hz_p; hz_p = hz;
+        cEX_pp = cEX_p; cEY_pp = cEY_p; cHZ_pp = cHZ_p;
+        cEX_p = cEX; cEY_p = cEY; cHZ_p = cHZ;
+        ex0_p = ex0r; ey0_p = ey0r;
+        exa_pp = exa; eya_pp = eya; hzn_ppp = hzn;
+      }
+    }
+  }
+  cp_async_wait<0>();
+}
+
+template <typename T, int TY>
+__global__ void __launch_bounds__(64)
+fused_step_warp_mat(const StepArgs<T> a) {
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  const int nitems = a.work ? a.n_work : a.tiles_x * a.tiles_y * a.n_chunks;
+  const int nwarps = (int)((gridDim.x * blockDim.x) >> 5);
+  for (int witem = (int)((blockIdx.x * blockDim.x + threadIdx.x) >> 5); witem < nitems;
+       witem += nwarps)
+    fused_step_warp_mat_item<T, TY>(a, a.work ? a.work[witem] : witem, smem_raw);
+}
+
+template <typename T, int TY>
+cudaError_t launch_warp_mat_shape(const StepArgs<T>& a, cudaStream_t st) {
+  const int items = a.work ? a.n_work : a.tiles_x * a.tiles_y * a.n_chunks;
+  if (items <= 0) return cudaSuccess;
+  const int warps_per_block = 2;
+  const size_t smem = (size_t)warps_per_block * (kMatDepth * kMatArrs + 2 * (TY + 4)) * 32 * sizeof(T);
+  static int resident = 0;
+  if (!resident) {
+    if (smem > 48 * 1024) {
+      cudaError_t e = cudaFuncSetAttribute(fused_step_warp_mat<T, TY>,
+                                           cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+      if (e != cudaSuccess) return e;
+    }
+    int dev = 0, sms = 0, per_sm = 0;
+    cudaError_t e = cudaGetDevice(&dev);
+    if (e == cudaSuccess) e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    if (e == cudaSuccess)
+      e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, fused_step_warp_mat<T, TY>,
+                                                        32 * warps_per_block, smem);
+    if (e != cudaSuccess) return e;
+    resident = std::max(1, sms * per_sm);
+  }
+  const int blocks = std::min(resident, (items + warps_per_block - 1) / warps_per_block);
+  fused_step_warp_mat<T, TY><<<blocks, 32 * warps_per_block, smem, st>>>(a);
+  return cudaGetLastError();
+}
+
 }  // namespace
 
 bool warp_shape_ok(int tx, int ty) {
@@ -611,6 +817,15 @@ bool warp_shape_ok(int tx, int ty) {
 template <typename T>
 cudaError_t launch_fused_warp_step(const StepArgs<T>& a, int tx, int ty, cudaStream_t st) {
   if (tx != kWarpTileX) return cudaErrorInvalidValue;
+  if (a.co.ua[0]) {  // per-entry coefficient arrays (general materials)
+    if (ty == 4) return launch_warp_mat_shape<T, 4>(a, st);
+    if (ty == 8) return launch_warp_mat_shape<T, 8>(a, st);
+    if (ty == 12) return launch_warp_mat_shape<T, 12>(a, st);
+    if (ty == 16) return launch_warp_mat_shape<T, 16>(a, st);
+    if (ty == 20) return launch_warp_mat_shape<T, 20>(a, st);
+    if (ty == 28) return launch_warp_mat_shape<T, 28>(a, st);
+    return cudaErrorInvalidValue;
+  }
   if constexpr (sizeof(T) == 8) {
     if (ty == 4) return launch_warp_shape<T, 4>(a, st);
     if (ty == 12) return launch_warp_shape<T, 12>(a, st);

@@ -119,6 +119,22 @@ def scaled_collimator(n: int, nz: int, sigma_cells: float = 6.0, steps: Optional
     return w
 
 
+def dielectric_collimator(n: int = 256, nz: int = 1024, sigma_cells: float = 6.0,
+                          precision: str = "fp32", eps_liner: float = 3.0):
+    """The scaled step collimator with a dielectric liner: cells within 4
+    transverse cells inside the narrow section's wall have eps_r = eps_liner.
+    Returns (workload, eps_r per cell)."""
+    w = scaled_collimator(n, nz, sigma_cells=sigma_cells, precision=precision)
+    r_in = 0.125 * n
+    k1, k2 = nz // 4, (3 * nz) // 4
+    liner = radius_mask(n, n, nz, collimator_radius(nz, 1e9, r_in - 4.0, k1, k2))
+    eps = np.ones((nz, n, n))
+    eps[(liner == 1) & (w.pec == 0)] = eps_liner
+    w.name = "dielectric_collimator_%dx%dx%d" % (n, n, nz)
+    w.kind = "dielectric"
+    return w, eps
+
+
 def _solve_geometry(n: int, kind: str, rng: np.random.Generator):
     nz = 4 * n
     if kind == "pipe":

@@ -156,13 +156,18 @@ def test_reference_and_fused_fp32_agree(tetm):
     assert rel_err(out[0], out[1]) <= 1e-5
 
 
-def test_materials_reference_kernel_fp64(tetm):
-    nx, ny, nz = 12, 10, 16
+@pytest.mark.parametrize("kernel,tiling", [("reference", None), ("fused", (28, 8, 5)),
+                                           ("fused", (28, 20, 16)), ("fused", (28, 4, 64))])
+def test_materials_fp64_match_oracle(tetm, kernel, tiling):
+    """Per-cell eps_r, mu_r and PEC: the reference kernel and the fused kernel
+    with per-entry coefficient arrays against the oracle."""
+    nx, ny, nz = 33, 29, 21
     eps, mu, pec = wl.random_materials(nx, ny, nz, 3)
     s = tetm.Solver(nx, ny, nz, wl.DXY, wl.DXY, wl.DZ, 0.0, "fp64", eps_r=eps, mu_r=mu, pec=pec)
-    assert s.info()["kernel"] == tetm.TETM_KERNEL_REFERENCE
-    with pytest.raises(tetm.TetmError):
-        s.set_kernel("fused")
+    assert s.info()["uniform_material"] == 0
+    s.set_kernel(kernel)
+    if tiling:
+        s.set_tiling(*tiling)
     o = Oracle(nx, ny, nz, wl.DXY, wl.DXY, wl.DZ, 0.0, eps_r=eps, mu_r=mu, pec=pec)
     rng = np.random.default_rng(9)
     for c in ("ex", "ey", "ez", "hx", "hy", "hz"):
@@ -173,6 +178,28 @@ def test_materials_reference_kernel_fp64(tetm):
     o.step(50)
     compare_fields(s, o, TOL64)
     assert s.energy() == pytest.approx(o.energy(), rel=TOL64)
+
+
+def test_materials_block_tiles_unsupported(tetm):
+    nx, ny, nz = 12, 10, 16
+    eps, mu, pec = wl.random_materials(nx, ny, nz, 4)
+    s = tetm.Solver(nx, ny, nz, wl.DXY, wl.DXY, wl.DZ, 0.0, "fp32", eps_r=eps, mu_r=mu, pec=pec)
+    with pytest.raises(tetm.TetmError) as e:
+        s.set_tiling(32, 8, 16)
+    assert e.value.code == tetm.TETM_E_UNSUPPORTED
+
+
+def test_dielectric_collimator_fp32_wake(tetm):
+    """A collimator with a dielectric liner (eps_r = 3 over the narrow part),
+    FP32 fused kernel with coefficient arrays, against the FP64 oracle."""
+    w, eps = wl.dielectric_collimator(n=40, nz=120, sigma_cells=3.0, precision="fp32")
+    s = tetm.Solver(w.nx, w.ny, w.nz, w.dx, w.dy, w.dz, w.cdt, "fp32", eps_r=eps, pec=w.pec)
+    s.set_bunch(w.sigma, w.charge, w.i0, w.j0)
+    s.step(w.steps)
+    o = Oracle(w.nx, w.ny, w.nz, w.dx, w.dy, w.dz, w.cdt, eps_r=eps, pec=w.pec)
+    o.set_bunch(w.sigma, w.charge, w.i0, w.j0)
+    o.step(w.steps)
+    assert rel_err(s.wake()[0], o.wake()[0]) <= TOL32_WAKE
 
 
 def test_energy_and_charge_balances_on_gpu(tetm):
