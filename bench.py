@@ -404,7 +404,7 @@ def run_tetm(args):
                      "bytes_per_cell": bytes_per_cell, "cells_per_launch": proc},
         "cpu_baseline": cpu,
         "e2e": e2e,
-        "gpu_launches": (K if args.kernel == "fused" else 10 * K) + 7 * n_bal,
+        "gpu_launches": (K if args.kernel == "fused" else 10 * K) + 6 * n_bal,
         "clocks": clk,
         "balances": {"records": int(hist.shape[0]),
                      "max_charge_residual_rel": float(np.max(hist[:, 2] / np.maximum(hist[:, 4], 1e-300)))
