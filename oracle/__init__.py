@@ -1,4 +1,5 @@
-"""FP64 CPU oracle of the explicit TE/TM scheme (Sec. 4.2, Eq. (23)).
+"""FP64 CPU oracle of the explicit TE/TM scheme: the 3D scheme (Sec. 4.2,
+Eq. (23)) and the rotationally symmetric one (Sec. 4.3, Eq. (24)).
 
 TEST INFRASTRUCTURE. Only the test suite, ``__graft_entry__.smoke()`` and the
 CPU-baseline leg of ``bench.py`` may import this package. It shares no code
@@ -15,6 +16,10 @@ integral units (edge voltages [V], dual-edge currents [A]).
 Parity status: every function here is pinned by the ``-m "not gpu"`` tests
 (dense matrix form of Eq. (23), eigen-angles of Eq. (27), energy law (19),
 charge laws (34)/(35), exact z-shift at c*dt = dz, loss-factor identity).
+``RzOracle`` (tetm_rz_oracle.c) is pinned by its own tests: the dense form
+(24), stability at c*dt = min(dr, dz) for every mode, energy law (19),
+pillbox Bessel-zero frequencies, the coaxial TEM shift, Gauss's law and the
+loss-factor identity.
 """
 from __future__ import annotations
 
@@ -202,4 +207,141 @@ class Oracle:
 def _comp(c):
     if isinstance(c, str):
         return COMPONENTS.index(c)
+    return int(c)
+
+
+# ---------------------------------------------------------------------------
+# Rotationally symmetric scheme (Sec. 4.3, Eq. (24)), one azimuthal mode
+# ---------------------------------------------------------------------------
+
+RZ_COMPONENTS = ("er", "ephi", "ez", "hr", "hphi", "hz")
+
+
+def _load_rz():
+    lib = _load()
+    if getattr(lib, "_rz_ready", False):
+        return lib
+    d, i, vp = ctypes.c_double, ctypes.c_int, ctypes.c_void_p
+    dp = ctypes.POINTER(ctypes.c_double)
+    lib.rz_oracle_new.restype = vp
+    lib.rz_oracle_new.argtypes = [i, i, i, d, d, d, vp, vp, vp]
+    lib.rz_oracle_free.argtypes = [vp]
+    lib.rz_oracle_stable.restype = i
+    lib.rz_oracle_stable.argtypes = [d, d, d]
+    lib.rz_oracle_set_bunch.restype = i
+    lib.rz_oracle_set_bunch.argtypes = [vp, d, d, i]
+    lib.rz_oracle_current.argtypes = [vp, ctypes.c_long, vp]
+    lib.rz_oracle_step.argtypes = [vp, i]
+    lib.rz_oracle_step_custom.argtypes = [vp, vp]
+    lib.rz_oracle_wake.restype = i
+    lib.rz_oracle_wake.argtypes = [vp, vp, i, ctypes.POINTER(i), dp, dp]
+    lib.rz_oracle_energy.restype = d
+    lib.rz_oracle_energy.argtypes = [vp]
+    lib.rz_oracle_get.argtypes = [vp, i, vp]
+    lib.rz_oracle_set.argtypes = [vp, i, vp]
+    lib.rz_oracle_coef.argtypes = [vp, i, vp]
+    lib.rz_oracle_dt.restype = d
+    lib.rz_oracle_dt.argtypes = [vp]
+    lib.rz_oracle_step_count.restype = ctypes.c_long
+    lib.rz_oracle_step_count.argtypes = [vp]
+    lib._rz_ready = True
+    return lib
+
+
+def rz_stable(dr, dz, cdt):
+    """Sec. 4.4: c*dt <= min(dr, dz), for every azimuthal mode."""
+    return bool(_load_rz().rz_oracle_stable(dr, dz, cdt))
+
+
+class RzOracle:
+    """One FP64 solve of azimuthal mode ``m`` on an (r, z) grid of nr x nz
+    cells, axis at r = 0, PEC at r = nr*dr and at both z ends, cold start.
+
+    Field arrays have the canonical shape (nz+1, nr+1), r fastest, per-radian
+    integral units. ``eps_r``, ``mu_r`` per cell (nz, nr) or None; ``pec``
+    uint8 per cell or None. ``cdt`` = c*dt, 0 means min(dr, dz)."""
+
+    def __init__(self, nr, nz, m, dr, dz, cdt=0.0, eps_r=None, mu_r=None, pec=None):
+        self.lib = _load_rz()
+        self.nr, self.nz, self.m = int(nr), int(nz), int(m)
+        self.dr, self.dz = float(dr), float(dz)
+        shape_c = (self.nz, self.nr)
+        self._keep = []
+        args = []
+        for a, dt in ((eps_r, np.float64), (mu_r, np.float64), (pec, np.uint8)):
+            if a is None:
+                args.append(None)
+            else:
+                a = np.ascontiguousarray(a, dtype=dt).reshape(shape_c)
+                self._keep.append(a)
+                args.append(_ptr(a))
+        h = self.lib.rz_oracle_new(self.nr, self.nz, self.m, self.dr, self.dz, float(cdt), *args)
+        if not h:
+            raise ValueError("rz_oracle_new: invalid grid")
+        self.h = ctypes.c_void_p(h)
+        self.shape = (self.nz + 1, self.nr + 1)
+        self.dt = self.lib.rz_oracle_dt(self.h)
+        self.alpha = 0.5 * self.dt
+
+    def __del__(self):
+        h = getattr(self, "h", None)
+        if h is not None and self.lib is not None:
+            self.lib.rz_oracle_free(h)
+            self.h = None
+
+    def get(self, comp):
+        out = np.empty(self.shape, dtype=np.float64)
+        self.lib.rz_oracle_get(self.h, _rz_comp(comp), _ptr(out))
+        return out
+
+    def set(self, comp, arr):
+        a = np.ascontiguousarray(arr, dtype=np.float64).reshape(self.shape)
+        self.lib.rz_oracle_set(self.h, _rz_comp(comp), _ptr(a))
+
+    def coef(self, comp):
+        out = np.empty(self.shape, dtype=np.float64)
+        self.lib.rz_oracle_coef(self.h, _rz_comp(comp), _ptr(out))
+        return out
+
+    def fields(self):
+        return {c: self.get(c) for c in RZ_COMPONENTS}
+
+    def set_bunch(self, sigma, charge, i0=0):
+        if self.lib.rz_oracle_set_bunch(self.h, float(sigma), float(charge), int(i0)) != 0:
+            raise ValueError("rz_oracle_set_bunch: bad argument")
+
+    def current(self, n):
+        out = np.zeros(self.shape, dtype=np.float64)
+        self.lib.rz_oracle_current(self.h, int(n), _ptr(out))
+        return out
+
+    def step(self, n=1):
+        self.lib.rz_oracle_step(self.h, int(n))
+
+    def step_custom(self, jz=None):
+        a = None if jz is None else np.ascontiguousarray(jz, dtype=np.float64).reshape(self.shape)
+        self.lib.rz_oracle_step_custom(self.h, _ptr(a))
+
+    @property
+    def step_count(self):
+        return int(self.lib.rz_oracle_step_count(self.h))
+
+    def wake(self):
+        n = ctypes.c_int()
+        s0 = ctypes.c_double()
+        ds = ctypes.c_double()
+        if self.lib.rz_oracle_wake(self.h, None, 0, ctypes.byref(n), ctypes.byref(s0),
+                                   ctypes.byref(ds)) != 0:
+            raise RuntimeError("no bunch set")
+        out = np.empty(n.value, dtype=np.float64)
+        self.lib.rz_oracle_wake(self.h, _ptr(out), n.value, None, None, None)
+        return out, s0.value, ds.value
+
+    def energy(self):
+        return float(self.lib.rz_oracle_energy(self.h))
+
+
+def _rz_comp(c):
+    if isinstance(c, str):
+        return RZ_COMPONENTS.index(c)
     return int(c)

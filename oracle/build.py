@@ -11,7 +11,7 @@ import os
 import subprocess
 
 HERE = os.path.dirname(os.path.abspath(__file__))
-SRC = os.path.join(HERE, "tetm_oracle.c")
+SRCS = [os.path.join(HERE, "tetm_oracle.c"), os.path.join(HERE, "tetm_rz_oracle.c")]
 BUILD_DIR = os.path.join(HERE, "_build")
 
 
@@ -24,7 +24,7 @@ def build_oracle(verbose=False):
     out = library_path()
     tmp = out + ".tmp%d" % os.getpid()
     cmd = ["gcc", "-std=c11", "-O2", "-ffp-contract=off", "-fno-fast-math", "-fPIC", "-shared",
-           "-o", tmp, SRC, "-lm"]
+           "-o", tmp] + SRCS + ["-lm"]
     if verbose:
         print(" ".join(cmd))
     subprocess.check_call(cmd)
