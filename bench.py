@@ -48,7 +48,9 @@ def parse_args():
     p.add_argument("--warmup", type=int, default=20)
     p.add_argument("--impl", default="tetm", choices=["tetm", "reference"])
     p.add_argument("--workload", default="collimator",
-                   choices=["collimator", "plain_pipe", "batch", "serve", "dielectric"])
+                   choices=["collimator", "plain_pipe", "batch", "serve", "dielectric", "rz"])
+    p.add_argument("--rz-chunk", type=int, default=0,
+                   help="rz: planes per work item (0 = wave-fitted default)")
     p.add_argument("--requests", type=int, default=2000, help="serve: requests in the stream")
     p.add_argument("--rate", type=float, default=40.0, help="serve: mean arrivals per second")
     p.add_argument("--solves", type=int, default=64, help="batch: number of solves")
@@ -510,10 +512,179 @@ def run_serve_mode(args):
     return 0
 
 
+# ---------------------------------------------------------------------------
+# Rotationally symmetric scheme (Eq. (24)): nine-cell chain, modes 0..4
+# ---------------------------------------------------------------------------
+def rz_workload(args):
+    from paper_0901_1053_gb300 import workloads as wl
+    return wl.cavity_chain_rz(nz=args.nz or 16384, precision=args.precision or "fp32")
+
+
+def rz_oracle_sample(w, planes, steps):
+    import dataclasses
+    from oracle import RzOracle
+    sub = dataclasses.replace(w, nz=planes, pec=w.pec[:planes].copy())
+    os_ = []
+    for m in range(w.m_lo, w.m_hi + 1):
+        o = RzOracle(sub.nr, sub.nz, m, sub.dr, sub.dz, sub.cdt, pec=sub.pec)
+        o.set_bunch(sub.sigma, sub.charge, sub.i0)
+        os_.append(o)
+    t0 = time.perf_counter()
+    for o in os_:
+        o.step(steps)
+    dt = time.perf_counter() - t0
+    cells = w.n_modes * sub.nr * sub.nz
+    desc = ("modes %d..%d, first %d of %d planes of %s (same radial grid and geometry), "
+            "%d steps, FP64, 1 thread" % (w.m_lo, w.m_hi, planes, w.nz, w.name, steps))
+    return cells * steps / dt / 1e9, dt, desc
+
+
+def run_rz_mode(args):
+    rank, world, local = dist_env()
+    import numpy as np
+    import torch
+    torch.cuda.set_device(local)
+    dist = Dist(world)
+    from paper_0901_1053_gb300 import tetm
+    w = rz_workload(args)
+    stream = torch.cuda.Stream()
+    s = tetm.RzSolver(w.nr, w.nz, w.m_lo, w.m_hi, w.dr, w.dz, w.cdt, w.precision, pec=w.pec)
+    s.set_bunch(w.sigma, w.charge, w.i0)
+    s.set_stream(stream.cuda_stream)
+    if args.rz_chunk:
+        chunk = args.rz_chunk
+        s.set_tiling(chunk)
+    else:
+        chunk = s.wave_fitted_chunk()
+    info = s.info()
+    s.step(args.warmup)
+    s.sync()
+    try:
+        uuid = str(torch.cuda.get_device_properties(local).uuid)
+    except Exception:
+        uuid = None
+    clocks = ClockSampler(uuid)
+    clocks.start()
+    time.sleep(0.5)
+    K = args.steps
+    evs = [torch.cuda.Event(enable_timing=True) for _ in range(K + 1)]
+    dist.barrier()
+    torch.cuda.synchronize()
+    for i in range(K):
+        evs[i].record(stream)
+        s.step(1)
+    evs[K].record(stream)
+    torch.cuda.synchronize()
+    dist.barrier()
+    clk = clocks.stop()
+    total_ms = evs[0].elapsed_time(evs[K])
+    per = [evs[i].elapsed_time(evs[i + 1]) for i in range(K)]
+    kern_ms = statistics.mean(per)
+    max_ms = dist.max(total_ms)
+    esz = 4 if w.precision == "fp32" else 8
+    bytes_per_cell = 12 * esz + 1
+    proc = info["processed_cells"]
+    achieved = bytes_per_cell * proc / (kern_ms * 1e-3) / 1e9
+    peak, peak_kind = measured_peak_hbm()
+    traffic = profiled_traffic("rz_step_kernel_%s_%s.md" % (w.precision, w.name))
+    s.close()
+
+    e2e = None
+    if not args.no_e2e:
+        steps_e2e = args.e2e_steps or w.steps
+        pinned = torch.empty(w.pec.shape, dtype=torch.uint8, pin_memory=True).numpy()
+        pinned[...] = w.pec
+        dist.barrier()
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        s2 = tetm.RzSolver(w.nr, w.nz, w.m_lo, w.m_hi, w.dr, w.dz, w.cdt, w.precision, pec=pinned)
+        s2.set_bunch(w.sigma, w.charge, w.i0)
+        s2.set_tiling(chunk)
+        s2.step(steps_e2e)
+        wakes = [s2.wake(m)[0] for m in range(w.m_lo, w.m_hi + 1)]
+        t1 = time.perf_counter()
+        s2.close()
+        e2e_s = dist.max(t1 - t0)
+        e2e = {"value": world * w.cells * steps_e2e / e2e_s / 1e9, "unit": UNIT,
+               "h2d_bytes_per_step": int(pinned.nbytes),
+               "d2h_bytes_per_step": int(sum(x.nbytes for x in wakes)), "steps_per_call": steps_e2e,
+               "seconds": round(e2e_s, 3),
+               "call": "tetm_rz_create(host pec) + tetm_rz_set_bunch + tetm_rz_step + tetm_rz_wake(host)"}
+
+    cpu = None
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        v, dt, desc = rz_oracle_sample(w, min(w.nz, 1024), 60)
+        cpu = {"value": v, "unit": UNIT, "cores": 1, "kind": "oracle", "sample": desc,
+               "seconds": round(dt, 2)}
+    value = world * w.cells * K / (max_ms * 1e-3) / 1e9
+    line = {
+        "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": K,
+        "warmup": args.warmup, "ms_per_step": max_ms / K, "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "f32" if w.precision == "fp32" else "f64",
+        "data": "synthetic",
+        "config": {"workload": w.name, "nr": w.nr, "nz": w.nz, "modes": [w.m_lo, w.m_hi],
+                   "dr_mm": w.dr * 1e3, "dz_mm": w.dz * 1e3, "cdt": "dz",
+                   "sigma_dz": round(w.sigma / w.dz, 3), "bunch_ring_i0": w.i0,
+                   "fields": w.precision, "wake": "f64", "chunk_z": chunk,
+                   "work_items": info["work_items"], "cells": w.cells, "processed_cells": proc,
+                   "l2": "inputs larger than L2 (two field sets of %.1f GB each)"
+                         % (6 * esz * w.cells / 1e9),
+                   "parallelism": "replicas x%d" % world},
+        "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
+                     "frac": achieved / peak, "traffic": traffic, "peak_kind": peak_kind,
+                     "kernel": "rz_step_kernel", "kernel_ms": kern_ms,
+                     "bytes_per_cell": bytes_per_cell, "cells_per_launch": proc},
+        "cpu_baseline": cpu,
+        "e2e": e2e,
+        "gpu_launches": K,
+        "clocks": clk,
+    }
+    if rank == 0:
+        print(json.dumps(line), flush=True)
+    dist.close()
+    return 0
+
+
+def run_rz_reference(args):
+    rank, world, _ = dist_env()
+    if rank != 0:
+        return 0
+    w = rz_workload(args)
+    budget = 2.0e7 * 120.0 / max(1, args.steps + args.warmup)
+    planes = int(max(2, min(w.nz, budget // (w.n_modes * w.nr))))
+    import dataclasses
+    from oracle import RzOracle
+    sub = dataclasses.replace(w, nz=planes, pec=w.pec[:planes].copy())
+    os_ = []
+    for m in range(w.m_lo, w.m_hi + 1):
+        o = RzOracle(sub.nr, sub.nz, m, sub.dr, sub.dz, sub.cdt, pec=sub.pec)
+        o.set_bunch(sub.sigma, sub.charge, sub.i0)
+        o.step(args.warmup)
+        os_.append(o)
+    t0 = time.perf_counter()
+    for o in os_:
+        o.step(args.steps)
+    dt = time.perf_counter() - t0
+    v = w.n_modes * sub.nr * planes * args.steps / dt / 1e9
+    desc = "modes %d..%d, first %d of %d planes of %s, %d timed steps, FP64, 1 thread" % (
+        w.m_lo, w.m_hi, planes, w.nz, w.name, args.steps)
+    line = {"metric": METRIC, "value": v, "unit": UNIT, "impl": "reference", "n_gpus": world,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": dt * 1e3 / args.steps,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+            "data": "synthetic", "config": {"workload": w.name, "sample_planes": planes},
+            "cpu_baseline": {"value": v, "unit": UNIT, "cores": 1, "kind": "oracle", "sample": desc},
+            "e2e": {"value": v, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+            "gpu_launches": 0}
+    print(json.dumps(line), flush=True)
+    return 0
+
+
 def main():
     args = parse_args()
     if args.impl == "reference":
-        return run_reference(args)
+        return run_rz_reference(args) if args.workload == "rz" else run_reference(args)
+    if args.workload == "rz":
+        return run_rz_mode(args)
     if args.workload == "batch":
         return run_batch_mode(args)
     if args.workload == "serve":

@@ -1,0 +1,125 @@
+/*
+ * tetm_rz.h — C ABI of the rotationally symmetric solver in libtetm.so: the
+ * explicit TE/TM scheme for bodies of revolution (Sec. 4.3, Eq. (24)), one
+ * set of azimuthal modes m_lo..m_hi advanced together on one (r, z) grid,
+ * with a rigid relativistic Gaussian bunch on a ring and the longitudinal
+ * wake potential of every mode gathered along the bunch path (Sec. 5).
+ *
+ * Conventions are those of tetm.h (return codes, ownership, streams); in
+ * addition:
+ *  - Grid: nr x nz primary cells in (r, z); nodes r_i = i*dr (i = 0..nr, the
+ *    axis is i = 0), z_k = k*dz. Perfectly conducting wall at r = nr*dr and
+ *    at both z ends; cold start. Cell (ci, ck) has the index ci + nr*ck.
+ *  - Fields of mode m: e_r, e_z, h_phi ~ cos(m phi) and e_phi, h_r, h_z ~
+ *    sin(m phi), integral quantities per radian of azimuth. Canonical layout:
+ *    one float64 vector per component with (nr+1)*(nz+1) entries, entry
+ *    i + (nr+1)*k attached to node (i, k):
+ *      e_r (i+1/2, k)   e_phi (i, k)   e_z (i, k+1/2)
+ *      h_r (i, k+1/2)   h_phi (i+1/2, k+1/2)   h_z (i+1/2, k)
+ *    Entries on PEC edges, on faces next to PEC, e_phi and h_r on the axis
+ *    and e_z on the axis for m >= 1 are zero.
+ *  - Metric (per radian, staircase): the cylindrical FIT lengths and areas;
+ *    the axis e_z (m = 0) has the dual area dr^2/4, which keeps the bound of
+ *    Sec. 4.4 (c*dt <= min(dr, dz) for every m).
+ *  - Time: the state after n steps is y^n = (u^{n-1/2}, v^n) with
+ *    u = (h_phi, h_r, e_z), v = (e_phi, e_r, h_z).
+ */
+#ifndef TETM_RZ_H
+#define TETM_RZ_H
+
+#include "tetm.h"
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+#define TETM_RZ_ER 0
+#define TETM_RZ_EPHI 1
+#define TETM_RZ_EZ 2
+#define TETM_RZ_HR 3
+#define TETM_RZ_HPHI 4
+#define TETM_RZ_HZ 5
+
+#define TETM_RZ_MAX_MODES 64
+
+typedef struct tetm_rz_grid {
+  int32_t nr, nz;      /* primary cells, each >= 2                                 */
+  int32_t m_lo, m_hi;  /* azimuthal modes m_lo..m_hi, 0 <= m_lo <= m_hi,
+                          at most TETM_RZ_MAX_MODES of them                        */
+  int32_t precision;   /* TETM_FP64 or TETM_FP32                                    */
+  int32_t pad;
+  double dr, dz;       /* cell sizes [m], > 0                                       */
+  double cdt;          /* c*dt [m]; 0 selects min(dr, dz)                           */
+} tetm_rz_grid;
+
+typedef struct tetm_rz_info {
+  int64_t step;             /* n of the current state                          */
+  int64_t device_bytes;     /* device memory held by the solve                 */
+  int64_t processed_cells;  /* entries one step updates, summed over the modes */
+  int32_t n_modes;
+  int32_t chunk_z;          /* planes per work item                            */
+  int32_t work_items;       /* (mode, radial tile, z chunk) items per step      */
+  int32_t wake_len;         /* samples of each mode's wake, 0 without a bunch  */
+  int32_t resident_warps;   /* step-kernel warps resident on the device at once */
+  int32_t pad;
+} tetm_rz_info;
+
+typedef struct tetm_rz tetm_rz;
+
+/* Creates a solve (Sec. 4.3). pec: uint8 per cell (1 = PEC), nr*nz entries,
+ * or NULL for the empty pipe of radius nr*dr. eps_r, mu_r: reserved, must be
+ * NULL (vacuum), else TETM_E_UNSUPPORTED. Fails with TETM_E_UNSTABLE when
+ * c*dt > min(dr, dz) (Sec. 4.4). Synchronizes. */
+int tetm_rz_create(const tetm_rz_grid* g, const double* eps_r, const double* mu_r,
+                   const uint8_t* pec, tetm_rz** out);
+
+/* Rigid Gaussian bunch of RMS length sigma [m] and charge q [C] on the ring
+ * r = i0*dr (Sec. 5), truncated at +-5 sigma, head at z = 0 at t = 0, moving
+ * at c along +z. Mode m receives the share (2 - delta_m0)/(2 pi) per radian.
+ * i0 = 0 (the axis) only when m_hi = 0. Requires c*dt == dz
+ * (TETM_E_NOT_MAGIC) and step 0 (TETM_E_STATE). The wake window of every mode
+ * is s = m*dz, m = -c0-1 .. ceil(15 sigma/dz), c0 = ceil(5 sigma/dz). */
+int tetm_rz_set_bunch(tetm_rz* s, double sigma, double q, int32_t i0);
+
+/* Queues n steps of Eq. (24) for every mode (n >= 0). */
+int tetm_rz_step(tetm_rz* s, int64_t n);
+
+/* Waits for the solve's stream. */
+int tetm_rz_sync(tetm_rz* s);
+
+/* Wake potential of mode m_lo + mode [V/C], W(s) = -(1/q) * sum of e_z at the
+ * bunch ring over the passage, as float64 (cap entries at out). n_out, s0
+ * (first sample's s [m]) and ds may be NULL. out == NULL returns the length
+ * only. Synchronizes. */
+int tetm_rz_wake(tetm_rz* s, int32_t mode, double* out, int32_t cap, int32_t* n_out,
+                 double* s0, double* ds);
+
+/* Discrete energy per radian of mode m_lo + mode, 0.5 <Q^{e,r} y, y>
+ * (Sec. 4.4), reduced in float64 on the device. Synchronizes. */
+int tetm_rz_energy(tetm_rz* s, int32_t mode, double* w);
+
+/* Copy one component of one mode to / from a host float64 array in the
+ * canonical layout ((nr+1)*(nz+1) entries). Writes zero inactive entries.
+ * Synchronize. */
+int tetm_rz_get_fields(tetm_rz* s, int32_t mode, int32_t comp, double* out);
+int tetm_rz_set_fields(tetm_rz* s, int32_t mode, int32_t comp, const double* in);
+
+/* Planes per work item (>= 4); rebuilds the work list. */
+int tetm_rz_set_tiling(tetm_rz* s, int32_t chunk_z);
+
+/* Queue on this CUDA stream (NULL: the solve's own stream). */
+int tetm_rz_set_stream(tetm_rz* s, void* cuda_stream);
+
+int tetm_rz_get_info(tetm_rz* s, tetm_rz_info* info);
+
+/* Device bytes tetm_rz_create would allocate for g (0 for a bad grid). */
+int64_t tetm_rz_bytes_needed(const tetm_rz_grid* g);
+
+/* Frees every device and host resource of the solve. NULL is accepted. */
+int tetm_rz_destroy(tetm_rz* s);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif

@@ -1,4 +1,5 @@
-"""Thin ctypes binding of libtetm.so (include/tetm.h), same names as the C ABI.
+"""Thin ctypes binding of libtetm.so (include/tetm.h, include/tetm_rz.h), same
+names as the C ABI.
 
 Argument marshalling only: every step of the solve runs in the library's
 CUDA kernels. Importing this module loads the in-tree library and raises
@@ -40,7 +41,12 @@ EXPORTS = ("tetm_create", "tetm_set_bunch", "tetm_step", "tetm_sync", "tetm_wake
            "tetm_get_info", "tetm_bytes_needed", "tetm_save", "tetm_load", "tetm_strerror",
            "tetm_set_balance_every", "tetm_balance_history", "tetm_energy_noalloc",
            "tetm_batch_create", "tetm_batch_step", "tetm_batch_sync", "tetm_batch_info",
-           "tetm_batch_destroy")
+           "tetm_batch_destroy",
+           "tetm_rz_create", "tetm_rz_set_bunch", "tetm_rz_step", "tetm_rz_sync", "tetm_rz_wake",
+           "tetm_rz_energy", "tetm_rz_get_fields", "tetm_rz_set_fields", "tetm_rz_set_tiling",
+           "tetm_rz_set_stream", "tetm_rz_get_info", "tetm_rz_bytes_needed", "tetm_rz_destroy")
+RZ_COMPONENTS = ("er", "ephi", "ez", "hr", "hphi", "hz")
+TETM_RZ_MAX_MODES = 64
 
 
 class tetm_grid(ctypes.Structure):
@@ -56,6 +62,20 @@ class tetm_info(ctypes.Structure):
                 ("tile_x", ctypes.c_int32), ("tile_y", ctypes.c_int32), ("chunk_z", ctypes.c_int32),
                 ("work_items", ctypes.c_int32), ("wake_len", ctypes.c_int32),
                 ("uniform_material", ctypes.c_int32)]
+
+
+class tetm_rz_grid(ctypes.Structure):
+    _fields_ = [("nr", ctypes.c_int32), ("nz", ctypes.c_int32), ("m_lo", ctypes.c_int32),
+                ("m_hi", ctypes.c_int32), ("precision", ctypes.c_int32), ("pad", ctypes.c_int32),
+                ("dr", ctypes.c_double), ("dz", ctypes.c_double), ("cdt", ctypes.c_double)]
+
+
+class tetm_rz_info(ctypes.Structure):
+    _fields_ = [("step", ctypes.c_int64), ("device_bytes", ctypes.c_int64),
+                ("processed_cells", ctypes.c_int64), ("n_modes", ctypes.c_int32),
+                ("chunk_z", ctypes.c_int32), ("work_items", ctypes.c_int32),
+                ("wake_len", ctypes.c_int32), ("resident_warps", ctypes.c_int32),
+                ("pad", ctypes.c_int32)]
 
 
 def _load():
@@ -97,6 +117,20 @@ def _load():
         "tetm_batch_destroy": (None, [vp]),
         "tetm_energy_noalloc": (ctypes.c_int, [ctypes.POINTER(tetm_grid),
                                                ctypes.POINTER(ctypes.c_void_p), vp, vp, vp]),
+        "tetm_rz_create": (ctypes.c_int, [ctypes.POINTER(tetm_rz_grid), vp, vp, vp, pp]),
+        "tetm_rz_set_bunch": (ctypes.c_int, [vp, dbl, dbl, i32]),
+        "tetm_rz_step": (ctypes.c_int, [vp, ctypes.c_int64]),
+        "tetm_rz_sync": (ctypes.c_int, [vp]),
+        "tetm_rz_wake": (ctypes.c_int, [vp, i32, vp, i32, ctypes.POINTER(i32),
+                                        ctypes.POINTER(dbl), ctypes.POINTER(dbl)]),
+        "tetm_rz_energy": (ctypes.c_int, [vp, i32, ctypes.POINTER(dbl)]),
+        "tetm_rz_get_fields": (ctypes.c_int, [vp, i32, i32, vp]),
+        "tetm_rz_set_fields": (ctypes.c_int, [vp, i32, i32, vp]),
+        "tetm_rz_set_tiling": (ctypes.c_int, [vp, i32]),
+        "tetm_rz_set_stream": (ctypes.c_int, [vp, vp]),
+        "tetm_rz_get_info": (ctypes.c_int, [vp, ctypes.POINTER(tetm_rz_info)]),
+        "tetm_rz_bytes_needed": (ctypes.c_int64, [ctypes.POINTER(tetm_rz_grid)]),
+        "tetm_rz_destroy": (ctypes.c_int, [vp]),
     }
     for name, (res, args) in sig.items():
         f = getattr(lib, name)
@@ -317,3 +351,122 @@ class Batch:
 
     def __exit__(self, *exc):
         self.close()
+
+
+# ---------------------------------------------------------------------------
+# Rotationally symmetric solver (include/tetm_rz.h)
+# ---------------------------------------------------------------------------
+
+def make_rz_grid(nr, nz, m_lo, m_hi, dr, dz, cdt=0.0, precision="fp32"):
+    p = {"fp64": TETM_FP64, "fp32": TETM_FP32}[precision] if isinstance(precision, str) else precision
+    return tetm_rz_grid(int(nr), int(nz), int(m_lo), int(m_hi), int(p), 0, float(dr), float(dz),
+                        float(cdt))
+
+
+def tetm_rz_bytes_needed(grid):
+    return int(lib.tetm_rz_bytes_needed(ctypes.byref(grid)))
+
+
+class RzSolver:
+    """Modes m_lo..m_hi of the scheme (24) on one (r, z) grid; fields in the
+    canonical (nz+1, nr+1) layout, r fastest, per radian."""
+
+    def __init__(self, nr, nz, m_lo, m_hi, dr, dz, cdt=0.0, precision="fp32", pec=None):
+        self.grid = make_rz_grid(nr, nz, m_lo, m_hi, dr, dz, cdt, precision)
+        self.nr, self.nz = int(nr), int(nz)
+        self.m_lo, self.m_hi = int(m_lo), int(m_hi)
+        self.shape = (self.nz + 1, self.nr + 1)
+        self.precision = precision
+        pec_a = None
+        if pec is not None:
+            pec_a = np.ascontiguousarray(pec, dtype=np.uint8).reshape(self.nz, self.nr)
+        h = ctypes.c_void_p()
+        _check(lib.tetm_rz_create(ctypes.byref(self.grid), None, None, _ptr(pec_a), ctypes.byref(h)),
+               "tetm_rz_create")
+        self.h = h
+
+    def close(self):
+        if getattr(self, "h", None) is not None and self.h.value:
+            lib.tetm_rz_destroy(self.h)
+            self.h = ctypes.c_void_p()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def _mode(self, m):
+        if not self.m_lo <= m <= self.m_hi:
+            raise ValueError("mode %d outside %d..%d" % (m, self.m_lo, self.m_hi))
+        return m - self.m_lo
+
+    def set_bunch(self, sigma, charge, i0):
+        _check(lib.tetm_rz_set_bunch(self.h, float(sigma), float(charge), int(i0)),
+               "tetm_rz_set_bunch")
+
+    def step(self, n=1):
+        _check(lib.tetm_rz_step(self.h, int(n)), "tetm_rz_step")
+
+    def sync(self):
+        _check(lib.tetm_rz_sync(self.h), "tetm_rz_sync")
+
+    def set_tiling(self, chunk_z):
+        _check(lib.tetm_rz_set_tiling(self.h, int(chunk_z)), "tetm_rz_set_tiling")
+
+    def set_stream(self, stream):
+        _check(lib.tetm_rz_set_stream(self.h, ctypes.c_void_p(int(stream) if stream else 0)),
+               "tetm_rz_set_stream")
+
+    def info(self):
+        inf = tetm_rz_info()
+        _check(lib.tetm_rz_get_info(self.h, ctypes.byref(inf)), "tetm_rz_get_info")
+        return {f[0]: getattr(inf, f[0]) for f in tetm_rz_info._fields_}
+
+    def wake(self, m):
+        n = ctypes.c_int32()
+        s0 = ctypes.c_double()
+        ds = ctypes.c_double()
+        mi = self._mode(m)
+        _check(lib.tetm_rz_wake(self.h, mi, None, 0, ctypes.byref(n), ctypes.byref(s0),
+                                ctypes.byref(ds)), "tetm_rz_wake")
+        out = np.empty(n.value, dtype=np.float64)
+        _check(lib.tetm_rz_wake(self.h, mi, _ptr(out), n.value, None, None, None), "tetm_rz_wake")
+        return out, s0.value, ds.value
+
+    def energy(self, m):
+        w = ctypes.c_double()
+        _check(lib.tetm_rz_energy(self.h, self._mode(m), ctypes.byref(w)), "tetm_rz_energy")
+        return w.value
+
+    def get(self, m, comp):
+        c = RZ_COMPONENTS.index(comp) if isinstance(comp, str) else int(comp)
+        out = np.empty(self.shape, dtype=np.float64)
+        _check(lib.tetm_rz_get_fields(self.h, self._mode(m), c, _ptr(out)), "tetm_rz_get_fields")
+        return out
+
+    def set(self, m, comp, arr):
+        c = RZ_COMPONENTS.index(comp) if isinstance(comp, str) else int(comp)
+        a = np.ascontiguousarray(arr, dtype=np.float64).reshape(self.shape)
+        _check(lib.tetm_rz_set_fields(self.h, self._mode(m), c, _ptr(a)), "tetm_rz_set_fields")
+
+    def fields(self, m):
+        return {c: self.get(m, c) for c in RZ_COMPONENTS}
+
+    def wave_fitted_chunk(self, lo=24, hi=256):
+        """Planes per work item whose item count fills whole waves of the
+        resident warps best (ties go to the longer chunk); leaves that tiling
+        set."""
+        best = None
+        for c in range(lo, hi + 1, 4):
+            self.set_tiling(c)
+            inf = self.info()
+            n, slots = inf["work_items"], max(1, inf["resident_warps"])
+            if n == 0:
+                continue
+            eff = n / (slots * -(-n // slots))
+            if best is None or eff >= best[0] - 1e-9:
+                best = (eff, c)
+        c = best[1] if best else 32
+        self.set_tiling(c)
+        return c

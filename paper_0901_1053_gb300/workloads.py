@@ -227,3 +227,78 @@ def random_materials(nx: int, ny: int, nz: int, seed: int):
     mu = rng.uniform(1.0, 4.0, (nz, ny, nx))
     pec = (rng.uniform(size=(nz, ny, nx)) < 0.1).astype(np.uint8)
     return eps, mu, pec
+
+
+# ---------------------------------------------------------------------------
+# Rotationally symmetric workloads (Sec. 4.3): (r, z) grids, modes m_lo..m_hi
+# ---------------------------------------------------------------------------
+
+@dataclasses.dataclass
+class RzWorkload:
+    name: str
+    nr: int
+    nz: int
+    m_lo: int
+    m_hi: int
+    dr: float
+    dz: float
+    cdt: float
+    pec: Optional[np.ndarray]      # uint8 (nz, nr), 1 = PEC, or None
+    sigma: float
+    charge: float
+    i0: int                        # ring r = i0 * dr of the bunch (0: the axis, m = 0 only)
+    steps: int
+    precision: str = "fp32"
+
+    @property
+    def n_modes(self) -> int:
+        return self.m_hi - self.m_lo + 1
+
+    @property
+    def cells(self) -> int:
+        """Cells of all modes: one (r, z) grid per mode."""
+        return self.n_modes * self.nr * self.nz
+
+
+def rz_radius_mask(nr: int, nz: int, radius_of_k: Callable[[np.ndarray], np.ndarray]) -> np.ndarray:
+    """Staircase body of revolution: cell (ci, ck) is PEC when its centre
+    radius (ci + 1/2) exceeds radius_of_k(ck) (in cells)."""
+    rk = np.asarray(radius_of_k(np.arange(nz)), dtype=np.float64)
+    ci = np.arange(nr) + 0.5
+    return (ci[None, :] > rk[:, None]).astype(np.uint8)
+
+
+def cavity_chain_radius(nz: int, n_cells: int, r_cav: float, r_iris: float, period: int,
+                        gap: int):
+    """Radius per plane of a chain of n_cells pillbox cells (radius r_cav,
+    length gap) separated by irises (radius r_iris, length period - gap),
+    centred in nz planes with beam pipes of radius r_iris on both sides."""
+    start = (nz - n_cells * period) // 2
+
+    def rad(k):
+        k = np.asarray(k)
+        rel = k - start - (period - gap) // 2
+        inside = (rel >= 0) & (rel < n_cells * period) & ((rel % period) < gap)
+        return np.where(inside, r_cav, r_iris)
+    return rad
+
+
+def cavity_chain_rz(nr: int = 512, nz: int = 16384, m_lo: int = 0, m_hi: int = 4,
+                    sigma_cells: float = 8.0, precision: str = "fp32", steps: Optional[int] = None,
+                    n_cells: int = 9, i0: Optional[int] = None) -> RzWorkload:
+    """Chain of 9 pillbox cells on an (r, z) grid (stand-in for the paper's
+    multi-cell structures): cavity radius 400/512 of nr, iris and pipe radius
+    160/512 of nr, period 3/32 of nz with 3/4 of it cavity gap; dr = dz =
+    0.25 mm, c*dt = dz; Gaussian bunch sigma = 8 dz, 1 nC, on the ring
+    i0 = nr/64 (the axis when only m = 0 is solved)."""
+    r_cav, r_iris = 400.0 * nr / 512.0, 160.0 * nr / 512.0
+    period = max(4, (3 * nz) // 32)
+    gap = (3 * period) // 4
+    pec = rz_radius_mask(nr, nz, cavity_chain_radius(nz, n_cells, r_cav, r_iris, period, gap))
+    dz = 0.25 * MM
+    sigma = sigma_cells * dz
+    if i0 is None:
+        i0 = 0 if m_hi == 0 else max(1, nr // 64)
+    st = steps if steps is not None else steps_for_window(nz, sigma, dz)
+    return RzWorkload("cavity_chain_rz_%dx%d_m%d-%d" % (nr, nz, m_lo, m_hi), nr, nz, m_lo, m_hi,
+                      dz, dz, dz, pec, sigma, 1e-9, i0, st, precision)

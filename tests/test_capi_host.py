@@ -1,5 +1,5 @@
 """CPU-side checks of the C ABI: the library loads, exports every function
-include/tetm.h declares, and its host-only paths (argument validation, the
+the headers in include/ declare, and its host-only paths (argument validation, the
 stability bound of Eq. (25), sizes, error strings) answer without a GPU."""
 import os
 import re
@@ -10,7 +10,9 @@ ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
 
 
 def _header_functions():
-    txt = open(os.path.join(ROOT, "include", "tetm.h")).read()
+    inc = os.path.join(ROOT, "include")
+    txt = "".join(open(os.path.join(inc, f)).read() for f in sorted(os.listdir(inc))
+                  if f.endswith(".h"))
     txt = re.sub(r"/\*.*?\*/", "", txt, flags=re.S)
     return sorted(set(re.findall(r"\b(tetm_[a-z_]+)\s*\(", txt)))
 
@@ -60,3 +62,31 @@ def test_bytes_needed(tetm):
     assert 49 * cells < b32 < 60 * cells          # two field sets of six float32 + mask
     assert 97 * cells < b64 < 115 * cells
     assert tetm.tetm_bytes_needed(tetm.make_grid(0, 2, 2, 1, 1, 1)) == 0
+
+
+def test_rz_create_rejects_bad_grids_and_materials_before_touching_the_gpu(tetm):
+    import ctypes
+    h = ctypes.c_void_p(123)
+    bad = tetm.make_rz_grid(1, 8, 0, 0, 1e-3, 1e-3)
+    assert tetm.lib.tetm_rz_create(ctypes.byref(bad), None, None, None, ctypes.byref(h)) == tetm.TETM_E_ARG
+    assert not h.value
+    modes = tetm.make_rz_grid(8, 8, 3, 2, 1e-3, 1e-3)
+    assert tetm.lib.tetm_rz_create(ctypes.byref(modes), None, None, None, ctypes.byref(h)) == tetm.TETM_E_ARG
+    too_long = tetm.make_rz_grid(8, 8, 0, 4, 0.9e-3, 1e-3, 1e-3)      # c*dt > dr (Sec. 4.4)
+    assert tetm.lib.tetm_rz_create(ctypes.byref(too_long), None, None, None, ctypes.byref(h)) == \
+        tetm.TETM_E_UNSTABLE
+    import numpy as np
+    eps = np.ones(64)
+    ok = tetm.make_rz_grid(8, 8, 0, 0, 1e-3, 1e-3)
+    assert tetm.lib.tetm_rz_create(ctypes.byref(ok), ctypes.c_void_p(eps.ctypes.data), None, None,
+                                   ctypes.byref(h)) == tetm.TETM_E_UNSUPPORTED
+
+
+def test_rz_bytes_needed(tetm):
+    g32 = tetm.make_rz_grid(512, 16384, 0, 4, 1e-3, 1e-3, precision="fp32")
+    g64 = tetm.make_rz_grid(512, 16384, 0, 4, 1e-3, 1e-3, precision="fp64")
+    cells = 5 * 513 * 16385
+    b32, b64 = tetm.tetm_rz_bytes_needed(g32), tetm.tetm_rz_bytes_needed(g64)
+    assert 48 * cells < b32 < 56 * cells          # two sets of six float32 per mode + mask
+    assert 96 * cells < b64 < 104 * cells
+    assert tetm.tetm_rz_bytes_needed(tetm.make_rz_grid(0, 8, 0, 0, 1e-3, 1e-3)) == 0
