@@ -50,7 +50,9 @@ def parse_args():
     p.add_argument("--workload", default="collimator",
                    choices=["collimator", "plain_pipe", "batch", "serve", "dielectric", "rz"])
     p.add_argument("--rz-chunk", type=int, default=0,
-                   help="rz: planes per work item (0 = wave-fitted default)")
+                   help="rz: planes per work item (0 = chosen by the autotuner, untimed)")
+    p.add_argument("--rz-kernel", default=None, choices=[None, "async", "register"],
+                   help="rz: step kernel (default: chosen by the autotuner, untimed)")
     p.add_argument("--requests", type=int, default=2000, help="serve: requests in the stream")
     p.add_argument("--rate", type=float, default=40.0, help="serve: mean arrivals per second")
     p.add_argument("--solves", type=int, default=64, help="batch: number of solves")
@@ -551,11 +553,15 @@ def run_rz_mode(args):
     s = tetm.RzSolver(w.nr, w.nz, w.m_lo, w.m_hi, w.dr, w.dz, w.cdt, w.precision, pec=w.pec)
     s.set_bunch(w.sigma, w.charge, w.i0)
     s.set_stream(stream.cuda_stream)
-    if args.rz_chunk:
-        chunk = args.rz_chunk
-        s.set_tiling(chunk)
+    if args.rz_chunk and args.rz_kernel:
+        kern, chunk = args.rz_kernel, args.rz_chunk
     else:
-        chunk = s.wave_fitted_chunk()
+        from paper_0901_1053_gb300.autotune import tune_rz
+        kern, chunk = tune_rz(w)
+        kern = args.rz_kernel or kern
+        chunk = args.rz_chunk or chunk
+    s.set_kernel(kern)
+    s.set_tiling(chunk)
     info = s.info()
     s.step(args.warmup)
     s.sync()
@@ -586,7 +592,8 @@ def run_rz_mode(args):
     proc = info["processed_cells"]
     achieved = bytes_per_cell * proc / (kern_ms * 1e-3) / 1e9
     peak, peak_kind = measured_peak_hbm()
-    traffic = profiled_traffic("rz_step_kernel_%s_%s.md" % (w.precision, w.name))
+    kname = "rz_step_async_kernel" if kern == "async" else "rz_step_kernel"
+    traffic = profiled_traffic("%s_%s_%s.md" % (kname, w.precision, w.name))
     s.close()
 
     e2e = None
@@ -599,6 +606,7 @@ def run_rz_mode(args):
         t0 = time.perf_counter()
         s2 = tetm.RzSolver(w.nr, w.nz, w.m_lo, w.m_hi, w.dr, w.dz, w.cdt, w.precision, pec=pinned)
         s2.set_bunch(w.sigma, w.charge, w.i0)
+        s2.set_kernel(kern)
         s2.set_tiling(chunk)
         s2.step(steps_e2e)
         wakes = [s2.wake(m)[0] for m in range(w.m_lo, w.m_hi + 1)]
@@ -625,14 +633,14 @@ def run_rz_mode(args):
         "config": {"workload": w.name, "nr": w.nr, "nz": w.nz, "modes": [w.m_lo, w.m_hi],
                    "dr_mm": w.dr * 1e3, "dz_mm": w.dz * 1e3, "cdt": "dz",
                    "sigma_dz": round(w.sigma / w.dz, 3), "bunch_ring_i0": w.i0,
-                   "fields": w.precision, "wake": "f64", "chunk_z": chunk,
+                   "fields": w.precision, "wake": "f64", "chunk_z": chunk, "kernel": kern,
                    "work_items": info["work_items"], "cells": w.cells, "processed_cells": proc,
                    "l2": "inputs larger than L2 (two field sets of %.1f GB each)"
                          % (6 * esz * w.cells / 1e9),
                    "parallelism": "replicas x%d" % world},
         "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
                      "frac": achieved / peak, "traffic": traffic, "peak_kind": peak_kind,
-                     "kernel": "rz_step_kernel", "kernel_ms": kern_ms,
+                     "kernel": kname, "kernel_ms": kern_ms,
                      "bytes_per_cell": bytes_per_cell, "cells_per_launch": proc},
         "cpu_baseline": cpu,
         "e2e": e2e,

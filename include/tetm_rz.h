@@ -42,6 +42,10 @@ extern "C" {
 
 #define TETM_RZ_MAX_MODES 64
 
+/* step kernels (same results bit for bit; they differ in how loads run ahead) */
+#define TETM_RZ_KERNEL_ASYNC 0     /* asynchronous copies into a shared-memory ring (default) */
+#define TETM_RZ_KERNEL_REGISTER 1  /* a register ring of four planes                          */
+
 typedef struct tetm_rz_grid {
   int32_t nr, nz;      /* primary cells, each >= 2                                 */
   int32_t m_lo, m_hi;  /* azimuthal modes m_lo..m_hi, 0 <= m_lo <= m_hi,
@@ -61,7 +65,7 @@ typedef struct tetm_rz_info {
   int32_t work_items;       /* (mode, radial tile, z chunk) items per step      */
   int32_t wake_len;         /* samples of each mode's wake, 0 without a bunch  */
   int32_t resident_warps;   /* step-kernel warps resident on the device at once */
-  int32_t pad;
+  int32_t kernel;           /* TETM_RZ_KERNEL_*                                 */
 } tetm_rz_info;
 
 typedef struct tetm_rz tetm_rz;
@@ -106,6 +110,9 @@ int tetm_rz_set_fields(tetm_rz* s, int32_t mode, int32_t comp, const double* in)
 
 /* Planes per work item (>= 4); rebuilds the work list. */
 int tetm_rz_set_tiling(tetm_rz* s, int32_t chunk_z);
+
+/* Selects the step kernel (TETM_RZ_KERNEL_*). */
+int tetm_rz_set_kernel(tetm_rz* s, int32_t kernel);
 
 /* Queue on this CUDA stream (NULL: the solve's own stream). */
 int tetm_rz_set_stream(tetm_rz* s, void* cuda_stream);

@@ -136,3 +136,35 @@ class Autotuner:
         self.cache[k] = list(best)
         self._save()
         return best
+
+
+# ---------------------------------------------------------------------------
+# Rotationally symmetric solver: step kernel and planes per work item
+# ---------------------------------------------------------------------------
+
+def tune_rz(w, precision: Optional[str] = None, steps: int = 8, warmup: int = 3,
+            extra_chunks: Sequence[int] = (32, 64, 128)):
+    """(kernel, chunk_z) with the shortest step on a scratch solve of w's
+    geometry: each step kernel with its wave-fitted chunk and a few fixed
+    ones. Returns ("async" | "register", chunk_z)."""
+    from . import tetm
+    precision = precision or w.precision
+    s = tetm.RzSolver(w.nr, w.nz, w.m_lo, w.m_hi, w.dr, w.dz, w.cdt, precision, pec=w.pec)
+    best = None
+    try:
+        for kern in ("async", "register"):
+            s.set_kernel(kern)
+            chunks = [s.wave_fitted_chunk()] + [c for c in extra_chunks]
+            for c in dict.fromkeys(chunks):
+                s.set_tiling(c)
+                s.step(warmup)
+                s.sync()
+                t0 = time.perf_counter()
+                s.step(steps)
+                s.sync()
+                dt = (time.perf_counter() - t0) / steps
+                if best is None or dt < best[0]:
+                    best = (dt, kern, c)
+    finally:
+        s.close()
+    return best[1], best[2]

@@ -2,28 +2,34 @@
 // azimuthal modes advanced together on one (r, z) grid, with a ring bunch and
 // the wake of every mode.
 //
-// Device layout. Every per-entry array (fields of one component of one mode,
-// mask) has rows k = -1..nz+1 and, per row, entries i = -or..pr-or-1 with the
-// axis i = 0 at column `or`; entry (i, k) of the canonical layout sits at
-// (k+1)*pr + i + or. Entries outside 0..nr, 0..nz hold zero and are
-// inactive, so the stencils and prefetches read them without bounds checks.
-// Field sets: [mode][component][row][column], two sets (ping-pong).
+// Device layout. Fields are stored entry-interleaved: for each mode and each
+// row k = -1..nz+1 (plane k of the canonical layout), columns i = -or..pr-or-1
+// with the axis i = 0 at column `or`, and per column the six components
+// (e_r, e_phi, e_z, h_r, h_phi, h_z) side by side. Entry (mode, comp, i, k) is
+// element ((mode * rows + k + 1) * pr + i + or) * 6 + comp. The activity mask
+// (one byte per entry, shared by the modes) has the same rows and columns.
+// Entries outside 0..nr, 0..nz hold zero and are inactive, so the stencils
+// and prefetches read them without bounds checks. Two field sets (ping-pong).
 //
 // Metric. In the vacuum staircase geometry every coefficient depends on r
 // alone: per mode and radial index the kernel keeps alpha*M^-1 of e_r, e_phi,
-// h_r, h_phi, 2 alpha*M^-1 of e_z, h_z and the two diagonal factors of
-// (24) in registers; one activity byte per entry (shared by all modes) says
-// which objects are non-PEC.
+// h_r, h_phi, 2 alpha*M^-1 of e_z, h_z and the two diagonal factors of (24) in
+// registers; the activity byte of an entry says which objects are non-PEC.
 //
-// Kernel. One warp per (mode, radial tile of 28 entries, z chunk) item; the
-// 32 lanes cover the tile and two halo entries on each side, which is what
-// the r-differences of the ten updates reach. The warp marches through the
-// chunk plane by plane: at plane k it completes the TM stage (h_phi, h_r,
+// Kernel. One warp per (mode, radial tile of 60 entries, z chunk) item. Lane l
+// holds the two consecutive entries 2l, 2l+1 of a 64-entry window (2 halo
+// entries on each side, which is what the r-differences of the ten updates
+// reach), so its six components of both entries are 48 contiguous bytes in
+// float32 (three 16-byte loads) and 96 in float64. The warp marches through
+// the chunk plane by plane: at plane k it completes the TM stage (h_phi, h_r,
 // e_z) with the old e of plane k+1 and then the TE stage (e_phi, e_r, h_z)
 // with the new h of planes k-1 and k, so each plane is read once and written
-// once. The TM stage of the plane before the chunk is recomputed (not
-// written) to supply h^{n+1/2} at k0-1. Loads of the next planes are held in
-// a register ring.
+// once; r-neighbours come from the lane's other entry or a shuffle. The TM
+// stage of the plane before the chunk is recomputed (not written) to supply
+// h^{n+1/2} at k0-1. A plane whose 64 entries are all fully active takes a
+// path without the per-object activity selects. Two variants differ in how
+// the loads run ahead: a register ring, or asynchronous copies into a
+// shared-memory ring.
 #include <cuda_runtime.h>
 #include <math.h>
 
@@ -43,8 +49,12 @@ using tetm::kMu0;
 constexpr int kER = TETM_RZ_ER, kEP = TETM_RZ_EPHI, kEZ = TETM_RZ_EZ;
 constexpr int kHR = TETM_RZ_HR, kHP = TETM_RZ_HPHI, kHZ = TETM_RZ_HZ;
 constexpr double kPi = 3.14159265358979323846;
-constexpr int kTile = 28;  // entries a warp owns
-constexpr int kRing = 4;   // planes prefetched into registers
+constexpr int kTile = 60;   // entries a warp owns (64-entry window minus 2 + 2 halo)
+// planes held ahead: register ring (float32 / float64) and shared-memory ring
+template <typename T>
+__host__ __device__ constexpr int ring_depth() { return sizeof(T) == 4 ? 4 : 2; }
+template <typename T>
+__host__ __device__ constexpr int async_depth() { return sizeof(T) == 4 ? 8 : 4; }
 // per-mode coefficient rows: alpha M^-1 (er, ephi, hr, hphi), 2 alpha M^-1
 // (ez, hz), and the diagonal factors 2 alpha M^-1 / (1 + alpha^2 m^2 M^-1 M^-1)
 // of e_z (paired with h_r) and h_z (paired with e_r)
@@ -52,23 +62,31 @@ enum { kCoER = 0, kCoEP, kCoEZ, kCoHR, kCoHP, kCoHZ, kCoFEZ, kCoFHZ, kNCo };
 
 struct RzLayout {
   int nr, nz, orr;
-  long long pr;     // row pitch (elements)
+  long long pr;     // columns per row
   long long rows;   // nz + 3
-  long long cs;     // elements per array, rows * pr
-  __host__ __device__ __forceinline__ long long idx(int i, int k) const {
+  __host__ __device__ __forceinline__ long long col(int i) const { return i + orr; }
+  // mask element of entry (i, k)
+  __host__ __device__ __forceinline__ long long midx(int i, int k) const {
     return (long long)(k + 1) * pr + i + orr;
   }
+  // field element of (mode, comp, i, k)
+  __host__ __device__ __forceinline__ long long fidx(int mode, int comp, int i, int k) const {
+    return (((long long)mode * rows + k + 1) * pr + i + orr) * 6 + comp;
+  }
+  __host__ __device__ __forceinline__ long long mode_elems() const { return rows * pr * 6; }
 };
 
-RzLayout make_rz_layout(int nr, int nz, int esz) {
+RzLayout make_rz_layout(int nr, int nz) {
   RzLayout L;
   L.nr = nr;
   L.nz = nz;
-  L.orr = 16 / esz;
-  const long long al = 32 / esz;
-  L.pr = (L.orr + nr + 3 + al - 1) / al * al;
+  // a window starts at i = 60 t - 2; with the axis at column 6 it starts on
+  // an even column (16-byte aligned pairs) and a 4-byte boundary of the mask;
+  // the pitch leaves room for the last window
+  L.orr = 6;
+  const long long tiles = (nr + 1 + kTile - 1) / kTile;
+  L.pr = (std::max((long long)L.orr + nr + 3, (long long)kTile * tiles + 8) + 7) / 8 * 8;
   L.rows = nz + 3;
-  L.cs = L.rows * L.pr;
   return L;
 }
 
@@ -95,123 +113,263 @@ __device__ __forceinline__ T shfl_dn(T v) { return __shfl_down_sync(0xffffffffu,
 template <typename T>
 __device__ __forceinline__ T shfl_up(T v) { return __shfl_up_sync(0xffffffffu, v, 1); }
 
-__device__ __forceinline__ float ldg_early(const float* p) {
-  float v;
-  asm volatile("ld.global.nc.f32 %0, [%1];" : "=f"(v) : "l"(p) : "memory");
-  return v;
+// One lane's two entries of one plane: f[6 * e + comp], activity bytes m
+// (low byte: the first entry).
+template <typename T>
+struct Pair6 {
+  T f[12];
+  unsigned m;
+};
+
+// Loads through the non-coherent path, issued where they are written so the
+// scheduler cannot sink them towards their first use.
+__device__ __forceinline__ void ld_pair(const float* p, Pair6<float>& d) {
+  asm volatile("ld.global.nc.v4.f32 {%0,%1,%2,%3}, [%4];"
+               : "=f"(d.f[0]), "=f"(d.f[1]), "=f"(d.f[2]), "=f"(d.f[3]) : "l"(p) : "memory");
+  asm volatile("ld.global.nc.v4.f32 {%0,%1,%2,%3}, [%4];"
+               : "=f"(d.f[4]), "=f"(d.f[5]), "=f"(d.f[6]), "=f"(d.f[7]) : "l"(p + 4) : "memory");
+  asm volatile("ld.global.nc.v4.f32 {%0,%1,%2,%3}, [%4];"
+               : "=f"(d.f[8]), "=f"(d.f[9]), "=f"(d.f[10]), "=f"(d.f[11]) : "l"(p + 8) : "memory");
 }
-__device__ __forceinline__ double ldg_early(const double* p) {
-  double v;
-  asm volatile("ld.global.nc.f64 %0, [%1];" : "=d"(v) : "l"(p) : "memory");
-  return v;
+__device__ __forceinline__ void ld_pair(const double* p, Pair6<double>& d) {
+#pragma unroll
+  for (int q = 0; q < 6; ++q)
+    asm volatile("ld.global.nc.v2.f64 {%0,%1}, [%2];"
+                 : "=d"(d.f[2 * q]), "=d"(d.f[2 * q + 1]) : "l"(p + 2 * q) : "memory");
 }
-__device__ __forceinline__ uint8_t ldg_early(const uint8_t* p) {
+__device__ __forceinline__ unsigned ld_mask2(const uint8_t* p) {
   unsigned short v;
-  asm volatile("ld.global.nc.u8 %0, [%1];" : "=h"(v) : "l"(p) : "memory");
-  return (uint8_t)v;
+  asm volatile("ld.global.nc.u16 %0, [%1];" : "=h"(v) : "l"(p) : "memory");
+  return v;
+}
+__device__ __forceinline__ void st_pair(float* p, const float* v) {
+  reinterpret_cast<float4*>(p)[0] = make_float4(v[0], v[1], v[2], v[3]);
+  reinterpret_cast<float4*>(p)[1] = make_float4(v[4], v[5], v[6], v[7]);
+  reinterpret_cast<float4*>(p)[2] = make_float4(v[8], v[9], v[10], v[11]);
+}
+__device__ __forceinline__ void st_pair(double* p, const double* v) {
+#pragma unroll
+  for (int q = 0; q < 6; ++q) reinterpret_cast<double2*>(p)[q] = make_double2(v[2 * q], v[2 * q + 1]);
 }
 
+// Per-lane constants of a work item.
 template <typename T>
-struct PlaneIn {
-  T er1, ep1;          // plane k+1 (old e)
-  T ez, hr, hp, hz;    // plane k
-  uint8_t m;           // activity bits of plane k
+struct LaneCo {
+  T er[2], ep[2], ez[2], hr[2], hp[2], hz[2], fez[2], fhz[2];
+};
+
+// Per-lane state carried from plane to plane: old e_r, e_phi of the current
+// plane, new h_r, h_phi of the previous plane.
+template <typename T>
+struct LaneState {
+  T er0[2], ep0[2], hr_p[2], hp_p[2];
+};
+
+// Both stages of plane k for the lane's two entries (ten updates of (24)).
+// d0: plane k, d1: plane k+1 (only its e_r, e_phi are used). out receives the
+// new values in the interleaved order. cur0/cur1: bunch current to subtract
+// at the two e_z entries (zero elsewhere).
+template <typename T>
+__device__ __forceinline__ void rz_plane(const Pair6<T>& d0, const Pair6<T>& d1, const LaneCo<T>& c,
+                                         T mm, LaneState<T>& s, T j0, T j1, T* out) {
+  const unsigned m = d0.m;
+  T CER[2], CEP[2], CHR[2], CHP[2], FEZ[2], FHZ[2];
+  if (__all_sync(0xffffffffu, m == 0x3F3Fu)) {
+#pragma unroll
+    for (int e = 0; e < 2; ++e) {
+      CER[e] = c.er[e]; CEP[e] = c.ep[e]; CHR[e] = c.hr[e]; CHP[e] = c.hp[e];
+      FEZ[e] = c.fez[e]; FHZ[e] = c.fhz[e];
+    }
+  } else {
+#pragma unroll
+    for (int e = 0; e < 2; ++e) {
+      const unsigned b = (m >> (8 * e)) & 0xFFu;
+      CER[e] = (b & 1) ? c.er[e] : T(0);
+      CEP[e] = (b & 2) ? c.ep[e] : T(0);
+      CHR[e] = (b & 8) ? c.hr[e] : T(0);
+      CHP[e] = (b & 16) ? c.hp[e] : T(0);
+      FEZ[e] = (b & 4) ? ((b & 8) ? c.fez[e] : c.ez[e]) : T(0);
+      FHZ[e] = (b & 32) ? ((b & 1) ? c.fhz[e] : c.hz[e]) : T(0);
+    }
+  }
+  T ez[2], hr[2], hp[2], hz[2], der[2], dep[2];
+#pragma unroll
+  for (int e = 0; e < 2; ++e) {
+    ez[e] = d0.f[6 * e + kEZ];
+    hr[e] = d0.f[6 * e + kHR];
+    hp[e] = d0.f[6 * e + kHP];
+    hz[e] = d0.f[6 * e + kHZ];
+    der[e] = d1.f[6 * e + kER] - s.er0[e];
+    dep[e] = d1.f[6 * e + kEP] - s.ep0[e];
+  }
+  // TM stage
+  const T ezR[2] = {ez[1], shfl_dn(ez[0])};
+  T hpa[2], hra[2];
+#pragma unroll
+  for (int e = 0; e < 2; ++e) {
+    hpa[e] = hp[e] + CHP[e] * (der[e] - (ezR[e] - ez[e]));
+    hra[e] = hr[e] + CHR[e] * (-dep[e] + mm * ez[e]);
+  }
+  const T hpaL[2] = {shfl_up(hpa[1]), hpa[0]};
+  T ezn[2];
+  const T jj[2] = {j0, j1};
+#pragma unroll
+  for (int e = 0; e < 2; ++e) {
+    const T cur = ((hpaL[e] - hpa[e]) - mm * hra[e]) - jj[e];
+    ezn[e] = ez[e] + FEZ[e] * cur;
+  }
+  const T eznR[2] = {ezn[1], shfl_dn(ezn[0])};
+  T hpn[2], hrn[2];
+#pragma unroll
+  for (int e = 0; e < 2; ++e) {
+    hpn[e] = hpa[e] + CHP[e] * (der[e] - (eznR[e] - ezn[e]));
+    hrn[e] = hra[e] + CHR[e] * (-dep[e] + mm * ezn[e]);
+  }
+  // TE stage
+  T dhr[2], dhp[2], epa[2], era[2];
+  const T hzL[2] = {shfl_up(hz[1]), hz[0]};
+#pragma unroll
+  for (int e = 0; e < 2; ++e) {
+    dhr[e] = s.hr_p[e] - hrn[e];
+    dhp[e] = s.hp_p[e] - hpn[e];
+    epa[e] = s.ep0[e] + CEP[e] * (dhr[e] - (hzL[e] - hz[e]));
+    era[e] = s.er0[e] + CER[e] * (-dhp[e] + mm * hz[e]);
+  }
+  const T epaR[2] = {epa[1], shfl_dn(epa[0])};
+  T hzn[2];
+#pragma unroll
+  for (int e = 0; e < 2; ++e) hzn[e] = hz[e] + FHZ[e] * ((epaR[e] - epa[e]) - mm * era[e]);
+  const T hznL[2] = {shfl_up(hzn[1]), hzn[0]};
+#pragma unroll
+  for (int e = 0; e < 2; ++e) {
+    const T epn = epa[e] + CEP[e] * (dhr[e] - (hznL[e] - hzn[e]));
+    const T ern = era[e] + CER[e] * (-dhp[e] + mm * hzn[e]);
+    out[6 * e + kER] = ern;
+    out[6 * e + kEP] = epn;
+    out[6 * e + kEZ] = ezn[e];
+    out[6 * e + kHR] = hrn[e];
+    out[6 * e + kHP] = hpn[e];
+    out[6 * e + kHZ] = hzn[e];
+    s.er0[e] = d1.f[6 * e + kER];
+    s.ep0[e] = d1.f[6 * e + kEP];
+    s.hr_p[e] = hrn[e];
+    s.hp_p[e] = hpn[e];
+  }
+}
+
+// Work-item geometry shared by both variants.
+template <typename T>
+struct Item {
+  int mode, tile, k0, k1, gi;  // gi: radial index of the lane's first entry
+  bool own;                    // lanes 1..30 store their two entries
+  bool src0, src1;             // the bunch ring is one of the lane's entries
+  long long fbase;             // field element of (mode, comp 0, gi, k = -1)
+  long long mbase;             // mask element of (gi, k = -1)
 };
 
 template <typename T>
-__device__ __forceinline__ void rz_item(const RzArgs<T>& a, int witem) {
+__device__ __forceinline__ Item<T> item_of(const RzArgs<T>& a, int witem) {
+  Item<T> it;
   const int lane = threadIdx.x & 31;
-  const int mode = witem % a.n_modes;
+  it.mode = witem % a.n_modes;
   const int rest = a.work[witem / a.n_modes];
-  const int tile = rest % a.tiles, chunk = rest / a.tiles;
-  const RzLayout L = a.L;
-  const int gi = tile * kTile - 2 + lane;
-  const int ci = min(gi, L.nr + 1);
-  const bool own = lane >= 2 && lane < kTile + 2 && gi <= L.nr;
-  const int k0 = chunk * a.chunk_z;
-  const int k1 = min(k0 + a.chunk_z, L.nz);
-  const long long cs = L.cs;
-  const long long mb = (long long)mode * 6 * cs;
-  const T* __restrict__ ib = a.in + mb + ci + L.orr;
-  T* __restrict__ ob = a.out + mb + ci + L.orr;
-  const uint8_t* __restrict__ mk = a.mask + ci + L.orr;
-  const long long PR = L.pr;
+  it.tile = rest % a.tiles;
+  const int chunk = rest / a.tiles;
+  it.k0 = chunk * a.chunk_z;
+  it.k1 = min(it.k0 + a.chunk_z, a.L.nz);
+  it.gi = it.tile * kTile - 2 + 2 * lane;
+  it.own = lane >= 1 && lane <= 30;
+  it.src0 = a.b_on && it.gi == a.i0;
+  it.src1 = a.b_on && it.gi + 1 == a.i0;
+  it.fbase = a.L.fidx(it.mode, 0, it.gi, -1);
+  it.mbase = a.L.midx(it.gi, -1);
+  return it;
+}
 
-  const T* co = a.coef + (long long)mode * kNCo * PR + ci + L.orr;
-  const T cER = co[kCoER * PR], cEP = co[kCoEP * PR], cEZ = co[kCoEZ * PR];
-  const T cHR = co[kCoHR * PR], cHP = co[kCoHP * PR], cHZ = co[kCoHZ * PR];
-  const T fEZ = co[kCoFEZ * PR], fHZ = co[kCoFHZ * PR];
-  const T mm = T(a.m_lo + mode);
-  const bool src = a.b_on && gi == a.i0;
-  const T* __restrict__ J = a.J + (long long)mode * 2 * a.c0;
+template <typename T>
+__device__ __forceinline__ LaneCo<T> lane_coefs(const RzArgs<T>& a, const Item<T>& it) {
+  LaneCo<T> c;
+  const long long PR = a.L.pr;
+  const T* co = a.coef + (long long)it.mode * kNCo * PR + a.L.col(it.gi);
+#pragma unroll
+  for (int e = 0; e < 2; ++e) {
+    c.er[e] = co[kCoER * PR + e];
+    c.ep[e] = co[kCoEP * PR + e];
+    c.ez[e] = co[kCoEZ * PR + e];
+    c.hr[e] = co[kCoHR * PR + e];
+    c.hp[e] = co[kCoHP * PR + e];
+    c.hz[e] = co[kCoHZ * PR + e];
+    c.fez[e] = co[kCoFEZ * PR + e];
+    c.fhz[e] = co[kCoFHZ * PR + e];
+  }
+  return c;
+}
 
-  auto load = [&](int k, PlaneIn<T>& d) {
-    const long long r = (long long)(min(k, L.nz) + 1) * PR;
-    d.er1 = ldg_early(ib + kER * cs + r + PR);
-    d.ep1 = ldg_early(ib + kEP * cs + r + PR);
-    d.ez = ldg_early(ib + kEZ * cs + r);
-    d.hr = ldg_early(ib + kHR * cs + r);
-    d.hp = ldg_early(ib + kHP * cs + r);
-    d.hz = ldg_early(ib + kHZ * cs + r);
-    d.m = ldg_early(mk + r);
+// Bunch current at the lane's e_z entry of plane k (zero off the ring) and
+// the wake sample of the new e_z.
+template <typename T>
+__device__ __forceinline__ T current_at(const RzArgs<T>& a, const Item<T>& it, bool src, int k) {
+  if (!src || k < 0) return T(0);
+  const long long dd = (long long)k - a.n + a.c0;
+  return (dd >= -a.c0 && dd < a.c0) ? a.J[(long long)it.mode * 2 * a.c0 + dd + a.c0] : T(0);
+}
+template <typename T>
+__device__ __forceinline__ void gather_wake(const RzArgs<T>& a, const Item<T>& it, int k,
+                                            const T* out) {
+  if (!it.own) return;
+  const bool s[2] = {it.src0, it.src1};
+#pragma unroll
+  for (int e = 0; e < 2; ++e)
+    if (s[e]) {
+      const long long w = a.n - k - a.c0 - a.m_min;
+      if (w >= 0 && w < a.nw) a.W[(long long)it.mode * a.nw + w] -= (double)out[6 * e + kEZ] * a.inv_q;
+    }
+}
+
+// --- register-ring variant ---------------------------------------------------
+template <typename T>
+__device__ __forceinline__ void rz_item_reg(const RzArgs<T>& a, int witem) {
+  const Item<T> it = item_of(a, witem);
+  const LaneCo<T> c = lane_coefs(a, it);
+  const T mm = T(a.m_lo + it.mode);
+  const long long RS = a.L.pr * 6;  // field elements per row
+  const long long MS = a.L.pr;      // mask elements per row
+  const T* __restrict__ ip = a.in + it.fbase;
+  T* __restrict__ op = a.out + it.fbase;
+  const uint8_t* __restrict__ mp = a.mask + it.mbase;
+  const int kstart = it.k0 - 1;
+  auto load = [&](int k, Pair6<T>& d) {
+    const int row = min(k, a.L.nz + 1) + 1;
+    ld_pair(ip + row * RS, d);
+    d.m = ld_mask2(mp + row * MS);
   };
-
-  const int kstart = k0 - 1;
-  T er0 = ib[kER * cs + (long long)(kstart + 1) * PR];
-  T ep0 = ib[kEP * cs + (long long)(kstart + 1) * PR];
-  T hr_p = T(0), hp_p = T(0);
-  PlaneIn<T> ring[kRing];
+  // ring[u] holds plane k (u = (k - kstart) mod R); a step uses planes k and
+  // k+1 and then refills the slot of plane k with plane k + R
+  constexpr int R = ring_depth<T>();
+  LaneState<T> s;
+  Pair6<T> ring[R];
 #pragma unroll
-  for (int u = 0; u < kRing; ++u) load(kstart + u, ring[u]);
-
-  for (int kb = kstart; kb < k1; kb += kRing) {
+  for (int u = 0; u < R; ++u) load(kstart + u, ring[u]);
 #pragma unroll
-    for (int u = 0; u < kRing; ++u) {
+  for (int e = 0; e < 2; ++e) {
+    s.er0[e] = ring[0].f[6 * e + kER];
+    s.ep0[e] = ring[0].f[6 * e + kEP];
+    s.hr_p[e] = T(0);
+    s.hp_p[e] = T(0);
+  }
+  for (int kb = kstart; kb < it.k1; kb += R) {
+#pragma unroll
+    for (int u = 0; u < R; ++u) {
       const int k = kb + u;
-      if (k >= k1) break;
-      const PlaneIn<T> d = ring[u];
-      load(k + kRing, ring[u]);
-      const uint8_t m = d.m;
-      const T CER = (m & 1) ? cER : T(0), CEP = (m & 2) ? cEP : T(0);
-      const T CHR = (m & 8) ? cHR : T(0), CHP = (m & 16) ? cHP : T(0);
-      const T FEZ = (m & 4) ? ((m & 8) ? fEZ : cEZ) : T(0);
-      const T FHZ = (m & 32) ? ((m & 1) ? fHZ : cHZ) : T(0);
-      // TM stage, plane k
-      const T der = d.er1 - er0, dep = d.ep1 - ep0;
-      const T hpa = d.hp + CHP * (der - (shfl_dn(d.ez) - d.ez));
-      const T hra = d.hr + CHR * (-dep + mm * d.ez);
-      T cur = (shfl_up(hpa) - hpa) - mm * hra;
-      if (src && k >= 0) {
-        const long long dd = (long long)k - a.n + a.c0;
-        if (dd >= -a.c0 && dd < a.c0) cur -= J[dd + a.c0];
+      if (k >= it.k1) break;
+      T out[12];
+      rz_plane(ring[u], ring[(u + 1) % R], c, mm, s, current_at(a, it, it.src0, k),
+               current_at(a, it, it.src1, k), out);
+      if (it.own && k >= it.k0) {
+        st_pair(op + (long long)(k + 1) * RS, out);
+        gather_wake(a, it, k, out);
       }
-      const T ezn = d.ez + FEZ * cur;
-      const T hpn = hpa + CHP * (der - (shfl_dn(ezn) - ezn));
-      const T hrn = hra + CHR * (-dep + mm * ezn);
-      // TE stage, plane k
-      const T dhr = hr_p - hrn, dhp = hp_p - hpn;
-      const T epa = ep0 + CEP * (dhr - (shfl_up(d.hz) - d.hz));
-      const T era = er0 + CER * (-dhp + mm * d.hz);
-      const T hzn = d.hz + FHZ * ((shfl_dn(epa) - epa) - mm * era);
-      const T epn = epa + CEP * (dhr - (shfl_up(hzn) - hzn));
-      const T ern = era + CER * (-dhp + mm * hzn);
-      if (own && k >= k0) {
-        const long long r = (long long)(k + 1) * PR;
-        ob[kEZ * cs + r] = ezn;
-        ob[kHR * cs + r] = hrn;
-        ob[kHP * cs + r] = hpn;
-        ob[kEP * cs + r] = epn;
-        ob[kER * cs + r] = ern;
-        ob[kHZ * cs + r] = hzn;
-        if (src) {
-          const long long w = a.n - k - a.c0 - a.m_min;
-          if (w >= 0 && w < a.nw) a.W[(long long)mode * a.nw + w] -= (double)ezn * a.inv_q;
-        }
-      }
-      er0 = d.er1;
-      ep0 = d.ep1;
-      hr_p = hrn;
-      hp_p = hpn;
+      load(k + R, ring[u]);
     }
   }
 }
@@ -221,7 +379,111 @@ __global__ void __launch_bounds__(128) rz_step_kernel(const RzArgs<T> a) {
   const int nitems = a.n_work * a.n_modes;
   const int nwarps = (int)((gridDim.x * blockDim.x) >> 5);
   for (int w = (int)((blockIdx.x * blockDim.x + threadIdx.x) >> 5); w < nitems; w += nwarps)
-    rz_item<T>(a, w);
+    rz_item_reg<T>(a, w);
+}
+
+// --- asynchronous-copy variant ------------------------------------------------
+// Per warp: a ring of async_depth planes, [slot][lane][12] field words and
+// [slot][64] activity bytes, filled with 16-byte cp.async (each lane copies
+// and reads back only its own 48 / 96 bytes; lanes 0..15 copy the 64
+// activity bytes four at a time, hence the __syncwarp before they are read).
+__device__ __forceinline__ void cp_async_16(void* sdst, const void* gsrc) {
+  const unsigned d = (unsigned)__cvta_generic_to_shared(sdst);
+  asm volatile("cp.async.cg.shared.global [%0], [%1], 16;" ::"r"(d), "l"(gsrc) : "memory");
+}
+__device__ __forceinline__ void cp_async_4(void* sdst, const void* gsrc) {
+  const unsigned d = (unsigned)__cvta_generic_to_shared(sdst);
+  asm volatile("cp.async.ca.shared.global [%0], [%1], 4;" ::"r"(d), "l"(gsrc) : "memory");
+}
+__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;" ::: "memory"); }
+template <int N>
+__device__ __forceinline__ void cp_async_wait() {
+  asm volatile("cp.async.wait_group %0;" ::"n"(N) : "memory");
+}
+
+template <typename T>
+constexpr size_t rz_async_warp_bytes() {
+  return (size_t)async_depth<T>() * 32 * 12 * sizeof(T) + (size_t)async_depth<T>() * 64;
+}
+
+template <typename T>
+__device__ __forceinline__ void rz_item_async(const RzArgs<T>& a, int witem, unsigned char* wsm) {
+  const int lane = threadIdx.x & 31;
+  const Item<T> it = item_of(a, witem);
+  const LaneCo<T> c = lane_coefs(a, it);
+  const T mm = T(a.m_lo + it.mode);
+  const long long RS = a.L.pr * 6;
+  const long long MS = a.L.pr;
+  const T* __restrict__ ip = a.in + it.fbase;
+  T* __restrict__ op = a.out + it.fbase;
+  // the window's activity bytes: lanes 0..15 copy bytes 4 l .. 4 l + 3
+  const uint8_t* __restrict__ mwin = a.mask + a.L.midx(it.tile * kTile - 2, -1) + 4 * (lane & 15);
+  constexpr int kADepth = async_depth<T>();
+  T* ring = reinterpret_cast<T*>(wsm) + lane * 12;
+  uint8_t* mring = wsm + (size_t)kADepth * 32 * 12 * sizeof(T);
+  const int kstart = it.k0 - 1;
+  constexpr int kChunks = 12 * (int)sizeof(T) / 16;  // 16-byte copies per lane and plane
+
+  auto issue = [&](int p) {
+    if (p <= it.k1) {
+      const int slot = (p - kstart) & (kADepth - 1);
+      const T* g = ip + (long long)(p + 1) * RS;
+      T* sl = ring + slot * 32 * 12;
+#pragma unroll
+      for (int q = 0; q < kChunks; ++q) cp_async_16(sl + q * (16 / sizeof(T)), g + q * (16 / sizeof(T)));
+      if (lane < 16) cp_async_4(mring + slot * 64 + 4 * lane, mwin + (long long)(p + 1) * MS);
+    }
+    cp_async_commit();
+  };
+  auto fetch = [&](int p, Pair6<T>& d) {
+    const int slot = (p - kstart) & (kADepth - 1);
+    const T* sl = ring + slot * 32 * 12;
+#pragma unroll
+    for (int q = 0; q < 12; ++q) d.f[q] = sl[q];
+    d.m = *reinterpret_cast<const unsigned short*>(mring + slot * 64 + 2 * lane);
+  };
+
+  __syncwarp();
+#pragma unroll
+  for (int p = 0; p < kADepth - 1; ++p) issue(kstart + p);
+  LaneState<T> s;
+  Pair6<T> d0, d1;
+  cp_async_wait<kADepth - 2>();
+  __syncwarp();
+  fetch(kstart, d0);
+#pragma unroll
+  for (int e = 0; e < 2; ++e) {
+    s.er0[e] = d0.f[6 * e + kER];
+    s.ep0[e] = d0.f[6 * e + kEP];
+    s.hr_p[e] = T(0);
+    s.hp_p[e] = T(0);
+  }
+  for (int k = kstart; k < it.k1; ++k) {
+    __syncwarp();
+    issue(k + kADepth - 1);
+    cp_async_wait<kADepth - 2>();
+    __syncwarp();
+    fetch(k + 1, d1);
+    T out[12];
+    rz_plane(d0, d1, c, mm, s, current_at(a, it, it.src0, k), current_at(a, it, it.src1, k), out);
+    if (it.own && k >= it.k0) {
+      st_pair(op + (long long)(k + 1) * RS, out);
+      gather_wake(a, it, k, out);
+    }
+    d0 = d1;
+  }
+  cp_async_wait<0>();
+  __syncwarp();
+}
+
+template <typename T>
+__global__ void __launch_bounds__(128) rz_step_async_kernel(const RzArgs<T> a) {
+  extern __shared__ __align__(16) unsigned char rz_smem[];
+  unsigned char* wsm = rz_smem + (size_t)(threadIdx.x >> 5) * rz_async_warp_bytes<T>();
+  const int nitems = a.n_work * a.n_modes;
+  const int nwarps = (int)((gridDim.x * blockDim.x) >> 5);
+  for (int w = (int)((blockIdx.x * blockDim.x + threadIdx.x) >> 5); w < nitems; w += nwarps)
+    rz_item_async<T>(a, w, wsm);
 }
 
 // Activity bits from the cell geometry (staircase; the rules of the
@@ -232,7 +494,7 @@ __device__ __forceinline__ bool cell_pec(const uint8_t* pec, int nr, int nz, int
 }
 
 __global__ void rz_build_mask(const uint8_t* pec, RzLayout L, uint8_t* mask) {
-  const long long total = L.cs;
+  const long long total = L.rows * L.pr;
   for (long long q = (long long)blockIdx.x * blockDim.x + threadIdx.x; q < total;
        q += (long long)gridDim.x * blockDim.x) {
     const int k = (int)(q / L.pr) - 1;
@@ -272,32 +534,32 @@ __global__ void rz_item_flags(const uint8_t* mask, RzLayout L, int tiles, int ch
   int any = 0;
   for (int k = k_lo; k < k_hi && !any; ++k)
     for (int i = i_lo; i < i_hi; ++i)
-      if (mask[L.idx(i, k)]) { any = 1; break; }
+      if (mask[L.midx(i, k)]) { any = 1; break; }
   flags[q] = any;
 }
 
-// Canonical <-> device layout for one array; `act` zeroes inactive entries
-// (mask bit c clear or the mode's metric zero there).
+// Canonical <-> device layout for one component of one mode; inactive
+// entries (mask bit clear or the mode's metric zero there) are written as
+// zero.
 template <typename T>
-__global__ void rz_to_canonical(const T* src, RzLayout L, double* dst) {
+__global__ void rz_to_canonical(const T* src, RzLayout L, int mode, int comp, double* dst) {
   const long long n = (long long)(L.nr + 1) * (L.nz + 1);
   for (long long q = (long long)blockIdx.x * blockDim.x + threadIdx.x; q < n;
        q += (long long)gridDim.x * blockDim.x) {
     const int i = (int)(q % (L.nr + 1)), k = (int)(q / (L.nr + 1));
-    dst[q] = (double)src[L.idx(i, k)];
+    dst[q] = (double)src[L.fidx(mode, comp, i, k)];
   }
 }
 
 template <typename T>
-__global__ void rz_from_canonical(const double* src, RzLayout L, const uint8_t* mask, int comp,
-                                  const double* metric, T* dst) {
+__global__ void rz_from_canonical(const double* src, RzLayout L, const uint8_t* mask, int mode,
+                                  int comp, const double* metric, T* dst) {
   const long long n = (long long)(L.nr + 1) * (L.nz + 1);
   for (long long q = (long long)blockIdx.x * blockDim.x + threadIdx.x; q < n;
        q += (long long)gridDim.x * blockDim.x) {
     const int i = (int)(q % (L.nr + 1)), k = (int)(q / (L.nr + 1));
-    const long long id = L.idx(i, k);
-    const bool act = ((mask[id] >> comp) & 1) && metric[i] != 0.0;
-    dst[id] = act ? (T)src[q] : T(0);
+    const bool act = ((mask[L.midx(i, k)] >> comp) & 1) && metric[i] != 0.0;
+    dst[L.fidx(mode, comp, i, k)] = act ? (T)src[q] : T(0);
   }
 }
 
@@ -312,31 +574,34 @@ constexpr int kEnergyThreads = 256;
 
 template <typename T>
 __global__ void __launch_bounds__(kEnergyThreads)
-rz_energy_partial(const T* f, RzLayout L, const uint8_t* mask, const double* metric, double alpha,
-                  double* partial) {
-  const long long cs = L.cs, PR = L.pr;
+rz_energy_partial(const T* f, RzLayout L, int mode, const uint8_t* mask, const double* metric,
+                  double alpha, double* partial) {
+  const long long PR = L.pr;
   const long long n = (long long)(L.nr + 1) * (L.nz + 1);
   double acc = 0.0;
   for (long long q = (long long)blockIdx.x * blockDim.x + threadIdx.x; q < n;
        q += (long long)gridDim.x * blockDim.x) {
     const int i = (int)(q % (L.nr + 1)), k = (int)(q / (L.nr + 1));
-    const long long id = L.idx(i, k);
-    const uint8_t m = mask[id];
+    const T* e = f + L.fidx(mode, 0, i, k);      // this entry's six components
+    const T* eR = e + 6;                          // entry (i+1, k)
+    const T* eL = e - 6;                          // entry (i-1, k)
+    const T* eU = e + 6 * PR;                     // entry (i, k+1)
+    const uint8_t m = mask[L.midx(i, k)];
     double w = 0.0;
     double c[6];
     for (int comp = 0; comp < 6; ++comp) {
       c[comp] = ((m >> comp) & 1) ? metric[comp * PR + i] : 0.0;
       if (c[comp] != 0.0) {
-        const double v = (double)f[comp * cs + id];
+        const double v = (double)e[comp];
         w += 0.5 * v * v / c[comp];
       }
     }
-    const double ez = (double)f[kEZ * cs + id], hz = (double)f[kHZ * cs + id];
-    const double t1 = (double)f[kEZ * cs + id + 1] - ez;
-    const double t2 = (double)f[kHZ * cs + id - 1] - hz;
+    const double ez = (double)e[kEZ], hz = (double)e[kHZ];
+    const double t1 = (double)eR[kEZ] - ez;
+    const double t2 = (double)eL[kHZ] - hz;
     const double r = c[kHP] * t1 * t1 + c[kEP] * t2 * t2;
-    const double l = (double)f[kHP * cs + id] * ((double)f[kER * cs + id + PR] - (double)f[kER * cs + id]) -
-                     (double)f[kHR * cs + id] * ((double)f[kEP * cs + id + PR] - (double)f[kEP * cs + id]);
+    const double l = (double)e[kHP] * ((double)eU[kER] - (double)e[kER]) -
+                     (double)e[kHR] * ((double)eU[kEP] - (double)e[kEP]);
     acc += w - 0.5 * alpha * alpha * r + alpha * l;
   }
   __shared__ double sh[kEnergyThreads / 32];
@@ -404,6 +669,7 @@ struct tetm_rz {
   long long device_bytes = 0;
   cudaStream_t own = nullptr, st = nullptr;
   int resident = 0;
+  int kernel = TETM_RZ_KERNEL_ASYNC;
 };
 
 namespace {
@@ -435,7 +701,10 @@ int rz_launch_steps(tetm_rz* s, long long n) {
     a.out = static_cast<T*>(s->set[s->cur ^ 1]);
     a.n = s->step;
     if (items > 0) {
-      rz_step_kernel<T><<<blocks, 128, 0, s->st>>>(a);
+      if (s->kernel == TETM_RZ_KERNEL_ASYNC)
+        rz_step_async_kernel<T><<<blocks, 128, 4 * rz_async_warp_bytes<T>(), s->st>>>(a);
+      else
+        rz_step_kernel<T><<<blocks, 128, 0, s->st>>>(a);
       cudaError_t e = cudaGetLastError();
       if (e != cudaSuccess) return rz_fail(e);
     }
@@ -451,8 +720,16 @@ int rz_occupancy(tetm_rz* s) {
   int dev = 0, sms = 0, per_sm = 0;
   cudaError_t e = cudaGetDevice(&dev);
   if (e == cudaSuccess) e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-  if (e == cudaSuccess)
-    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, rz_step_kernel<T>, 128, 0);
+  const size_t smem = 4 * rz_async_warp_bytes<T>();
+  if (e == cudaSuccess && smem > 48 * 1024)
+    e = cudaFuncSetAttribute(rz_step_async_kernel<T>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                             (int)smem);
+  if (e == cudaSuccess) {
+    if (s->kernel == TETM_RZ_KERNEL_ASYNC)
+      e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, rz_step_async_kernel<T>, 128, smem);
+    else
+      e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, rz_step_kernel<T>, 128, 0);
+  }
   if (e != cudaSuccess) return rz_fail(e);
   s->resident = std::max(1, sms * per_sm);
   return TETM_OK;
@@ -549,7 +826,7 @@ int rz_upload_coefs(tetm_rz* s) {
 }
 
 size_t rz_field_bytes(const RzLayout& L, int esz, int n_modes) {
-  return (size_t)n_modes * 6 * (size_t)L.cs * (size_t)esz;
+  return (size_t)n_modes * (size_t)L.mode_elems() * (size_t)esz;
 }
 
 bool rz_mode_ok(const tetm_rz* s, int mode) { return s && mode >= 0 && mode < s->n_modes; }
@@ -562,8 +839,8 @@ int64_t tetm_rz_bytes_needed(const tetm_rz_grid* g) {
   if (!rz_grid_ok(g)) return 0;
   const int esz = g->precision == TETM_FP64 ? 8 : 4;
   const int nm = g->m_hi - g->m_lo + 1;
-  const RzLayout L = make_rz_layout(g->nr, g->nz, esz);
-  return (int64_t)(2 * rz_field_bytes(L, esz, nm) + (size_t)L.cs +
+  const RzLayout L = make_rz_layout(g->nr, g->nz);
+  return (int64_t)(2 * rz_field_bytes(L, esz, nm) + (size_t)(L.rows * L.pr) +
                    (size_t)nm * L.pr * (kNCo * esz + 6 * 8)) + (int64_t)(1 << 20);
 }
 
@@ -583,7 +860,7 @@ int tetm_rz_create(const tetm_rz_grid* g, const double* eps_r, const double* mu_
   s->alpha = 0.5 * (cdt / kC);
   s->esz = g->precision == TETM_FP64 ? 8 : 4;
   s->n_modes = g->m_hi - g->m_lo + 1;
-  s->L = make_rz_layout(g->nr, g->nz, s->esz);
+  s->L = make_rz_layout(g->nr, g->nz);
   int rc = TETM_OK;
   uint8_t* dpec = nullptr;
   cudaError_t e = cudaStreamCreateWithFlags(&s->own, cudaStreamNonBlocking);
@@ -598,7 +875,7 @@ int tetm_rz_create(const tetm_rz_grid* g, const double* eps_r, const double* mu_
   do {
     if ((e = cudaMalloc(&s->set[0], fb)) != cudaSuccess) break;
     if ((e = cudaMalloc(&s->set[1], fb)) != cudaSuccess) break;
-    if ((e = cudaMalloc(&s->mask, (size_t)s->L.cs)) != cudaSuccess) break;
+    if ((e = cudaMalloc(&s->mask, (size_t)(s->L.rows * s->L.pr))) != cudaSuccess) break;
     if ((e = cudaMalloc(&s->coef, cob)) != cudaSuccess) break;
     if ((e = cudaMalloc(&s->metric, meb)) != cudaSuccess) break;
     if ((e = cudaMalloc(&s->partial, sizeof(double) * (kEnergyBlocks + 1))) != cudaSuccess) break;
@@ -622,7 +899,7 @@ int tetm_rz_create(const tetm_rz_grid* g, const double* eps_r, const double* mu_
     tetm_rz_destroy(s);
     return rc;
   }
-  s->device_bytes = (long long)(2 * fb + (size_t)s->L.cs + cob + meb);
+  s->device_bytes = (long long)(2 * fb + (size_t)(s->L.rows * s->L.pr) + cob + meb);
   *out = s;
   return TETM_OK;
 }
@@ -713,15 +990,14 @@ int tetm_rz_wake(tetm_rz* s, int32_t mode, double* out, int32_t cap, int32_t* n_
 
 int tetm_rz_energy(tetm_rz* s, int32_t mode, double* w) {
   if (!rz_mode_ok(s, mode) || !w) return TETM_E_ARG;
-  const size_t off = (size_t)mode * 6 * s->L.cs * s->esz;
-  const char* f = static_cast<const char*>(s->set[s->cur]) + off;
+  const void* f = s->set[s->cur];
   const double* me = s->metric + (size_t)mode * 6 * s->L.pr + s->L.orr;
   if (s->esz == 8)
     rz_energy_partial<double><<<kEnergyBlocks, kEnergyThreads, 0, s->st>>>(
-        reinterpret_cast<const double*>(f), s->L, s->mask, me, s->alpha, s->partial);
+        static_cast<const double*>(f), s->L, mode, s->mask, me, s->alpha, s->partial);
   else
     rz_energy_partial<float><<<kEnergyBlocks, kEnergyThreads, 0, s->st>>>(
-        reinterpret_cast<const float*>(f), s->L, s->mask, me, s->alpha, s->partial);
+        static_cast<const float*>(f), s->L, mode, s->mask, me, s->alpha, s->partial);
   rz_energy_final<<<1, 32, 0, s->st>>>(s->partial, kEnergyBlocks, s->partial + kEnergyBlocks);
   cudaError_t e = cudaGetLastError();
   if (e == cudaSuccess)
@@ -736,12 +1012,11 @@ int tetm_rz_get_fields(tetm_rz* s, int32_t mode, int32_t comp, double* out) {
   double* tmp = nullptr;
   cudaError_t e = cudaMallocAsync(&tmp, sizeof(double) * n, s->st);
   if (e != cudaSuccess) return rz_fail(e);
-  const size_t off = ((size_t)mode * 6 + comp) * s->L.cs * s->esz;
-  const char* f = static_cast<const char*>(s->set[s->cur]) + off;
+  const void* f = s->set[s->cur];
   if (s->esz == 8)
-    rz_to_canonical<double><<<512, 256, 0, s->st>>>(reinterpret_cast<const double*>(f), s->L, tmp);
+    rz_to_canonical<double><<<512, 256, 0, s->st>>>(static_cast<const double*>(f), s->L, mode, comp, tmp);
   else
-    rz_to_canonical<float><<<512, 256, 0, s->st>>>(reinterpret_cast<const float*>(f), s->L, tmp);
+    rz_to_canonical<float><<<512, 256, 0, s->st>>>(static_cast<const float*>(f), s->L, mode, comp, tmp);
   e = cudaGetLastError();
   if (e == cudaSuccess) e = cudaMemcpyAsync(out, tmp, sizeof(double) * n, cudaMemcpyDeviceToHost, s->st);
   cudaFreeAsync(tmp, s->st);
@@ -756,16 +1031,15 @@ int tetm_rz_set_fields(tetm_rz* s, int32_t mode, int32_t comp, const double* in)
   cudaError_t e = cudaMallocAsync(&tmp, sizeof(double) * n, s->st);
   if (e != cudaSuccess) return rz_fail(e);
   e = cudaMemcpyAsync(tmp, in, sizeof(double) * n, cudaMemcpyHostToDevice, s->st);
-  const size_t off = ((size_t)mode * 6 + comp) * s->L.cs * s->esz;
-  char* f = static_cast<char*>(s->set[s->cur]) + off;
+  void* f = s->set[s->cur];
   const double* me = s->metric + ((size_t)mode * 6 + comp) * s->L.pr + s->L.orr;
   if (e == cudaSuccess) {
     if (s->esz == 8)
-      rz_from_canonical<double><<<512, 256, 0, s->st>>>(tmp, s->L, s->mask, comp, me,
-                                                        reinterpret_cast<double*>(f));
+      rz_from_canonical<double><<<512, 256, 0, s->st>>>(tmp, s->L, s->mask, mode, comp, me,
+                                                        static_cast<double*>(f));
     else
-      rz_from_canonical<float><<<512, 256, 0, s->st>>>(tmp, s->L, s->mask, comp, me,
-                                                       reinterpret_cast<float*>(f));
+      rz_from_canonical<float><<<512, 256, 0, s->st>>>(tmp, s->L, s->mask, mode, comp, me,
+                                                       static_cast<float*>(f));
     e = cudaGetLastError();
   }
   cudaFreeAsync(tmp, s->st);
@@ -778,6 +1052,12 @@ int tetm_rz_set_tiling(tetm_rz* s, int32_t chunk_z) {
   s->chunk_z = chunk_z;
   s->work_dirty = true;
   return rz_rebuild_work(s);
+}
+
+int tetm_rz_set_kernel(tetm_rz* s, int32_t kernel) {
+  if (!s || (kernel != TETM_RZ_KERNEL_REGISTER && kernel != TETM_RZ_KERNEL_ASYNC)) return TETM_E_ARG;
+  s->kernel = kernel;
+  return s->esz == 8 ? rz_occupancy<double>(s) : rz_occupancy<float>(s);
 }
 
 int tetm_rz_set_stream(tetm_rz* s, void* cuda_stream) {
@@ -796,7 +1076,7 @@ int tetm_rz_get_info(tetm_rz* s, tetm_rz_info* info) {
   info->work_items = s->n_work * s->n_modes;
   info->wake_len = s->bunch ? s->nw : 0;
   info->resident_warps = 4 * s->resident;
-  info->pad = 0;
+  info->kernel = s->kernel;
   return TETM_OK;
 }
 

@@ -44,7 +44,10 @@ EXPORTS = ("tetm_create", "tetm_set_bunch", "tetm_step", "tetm_sync", "tetm_wake
            "tetm_batch_destroy",
            "tetm_rz_create", "tetm_rz_set_bunch", "tetm_rz_step", "tetm_rz_sync", "tetm_rz_wake",
            "tetm_rz_energy", "tetm_rz_get_fields", "tetm_rz_set_fields", "tetm_rz_set_tiling",
-           "tetm_rz_set_stream", "tetm_rz_get_info", "tetm_rz_bytes_needed", "tetm_rz_destroy")
+           "tetm_rz_set_stream", "tetm_rz_get_info", "tetm_rz_bytes_needed", "tetm_rz_destroy",
+           "tetm_rz_set_kernel")
+TETM_RZ_KERNEL_ASYNC = 0
+TETM_RZ_KERNEL_REGISTER = 1
 RZ_COMPONENTS = ("er", "ephi", "ez", "hr", "hphi", "hz")
 TETM_RZ_MAX_MODES = 64
 
@@ -75,7 +78,7 @@ class tetm_rz_info(ctypes.Structure):
                 ("processed_cells", ctypes.c_int64), ("n_modes", ctypes.c_int32),
                 ("chunk_z", ctypes.c_int32), ("work_items", ctypes.c_int32),
                 ("wake_len", ctypes.c_int32), ("resident_warps", ctypes.c_int32),
-                ("pad", ctypes.c_int32)]
+                ("kernel", ctypes.c_int32)]
 
 
 def _load():
@@ -128,6 +131,7 @@ def _load():
         "tetm_rz_set_fields": (ctypes.c_int, [vp, i32, i32, vp]),
         "tetm_rz_set_tiling": (ctypes.c_int, [vp, i32]),
         "tetm_rz_set_stream": (ctypes.c_int, [vp, vp]),
+        "tetm_rz_set_kernel": (ctypes.c_int, [vp, i32]),
         "tetm_rz_get_info": (ctypes.c_int, [vp, ctypes.POINTER(tetm_rz_info)]),
         "tetm_rz_bytes_needed": (ctypes.c_int64, [ctypes.POINTER(tetm_rz_grid)]),
         "tetm_rz_destroy": (ctypes.c_int, [vp]),
@@ -413,6 +417,11 @@ class RzSolver:
 
     def set_tiling(self, chunk_z):
         _check(lib.tetm_rz_set_tiling(self.h, int(chunk_z)), "tetm_rz_set_tiling")
+
+    def set_kernel(self, kernel):
+        k = {"async": TETM_RZ_KERNEL_ASYNC, "register": TETM_RZ_KERNEL_REGISTER}[kernel] \
+            if isinstance(kernel, str) else int(kernel)
+        _check(lib.tetm_rz_set_kernel(self.h, k), "tetm_rz_set_kernel")
 
     def set_stream(self, stream):
         _check(lib.tetm_rz_set_stream(self.h, ctypes.c_void_p(int(stream) if stream else 0)),

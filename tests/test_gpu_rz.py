@@ -39,8 +39,9 @@ def small_chain(nr, nz, m_lo, m_hi, sigma_cells=3.0, i0=None, steps=None, precis
     return w
 
 
-def gpu_solver(tetm, w, chunk=None):
+def gpu_solver(tetm, w, chunk=None, kernel="async"):
     s = tetm.RzSolver(w.nr, w.nz, w.m_lo, w.m_hi, w.dr, w.dz, w.cdt, w.precision, pec=w.pec)
+    s.set_kernel(kernel)
     if chunk:
         s.set_tiling(chunk)
     return s
@@ -77,12 +78,16 @@ def rel(a, b):
 # FP64 parity, field by field and wake by wake
 # ---------------------------------------------------------------------------
 
+KERNELS = ("async", "register")
+
+
+@pytest.mark.parametrize("kernel", KERNELS)
 @pytest.mark.parametrize("chunk", [5, 32, 200])
-def test_axis_bunch_m0_matches_oracle(tetm, chunk):
+def test_axis_bunch_m0_matches_oracle(tetm, chunk, kernel):
     """m = 0, bunch on the axis, 3-cell chain, 61 radial entries (3 tiles, the
     last ragged), nz = 150 (chunks with a ragged tail)."""
     w = small_chain(60, 150, 0, 0, steps=None)
-    s = gpu_solver(tetm, w, chunk)
+    s = gpu_solver(tetm, w, chunk, kernel)
     s.set_bunch(w.sigma, w.charge, w.i0)
     s.step(w.steps)
     o = oracle_mode(w, 0)
@@ -92,9 +97,10 @@ def test_axis_bunch_m0_matches_oracle(tetm, chunk):
     assert s.wake(0)[1] == o.wake()[1]
 
 
-def test_ring_bunch_modes_0_to_3_match_oracle(tetm):
+@pytest.mark.parametrize("kernel", KERNELS)
+def test_ring_bunch_modes_0_to_3_match_oracle(tetm, kernel):
     w = small_chain(45, 120, 0, 3, i0=4, steps=150)
-    s = gpu_solver(tetm, w, 16)
+    s = gpu_solver(tetm, w, 16, kernel)
     s.set_bunch(w.sigma, w.charge, w.i0)
     s.step(w.steps)
     for m in range(4):
@@ -137,12 +143,13 @@ def test_random_initial_state_matches_oracle(tetm, m):
     assert max(errs.values()) <= TOL64, errs
 
 
-def test_chunk_sizes_are_bitwise_identical(tetm):
+def test_chunk_sizes_and_kernels_are_bitwise_identical(tetm):
     for prec in ("fp64", "fp32"):
         w = small_chain(70, 130, 0, 2, i0=5, steps=90, precision=prec)
         res = []
-        for chunk in (4, 13, 64):
-            s = gpu_solver(tetm, w, chunk)
+        for chunk, kernel in ((4, "async"), (13, "async"), (64, "async"), (13, "register"),
+                              (64, "register")):
+            s = gpu_solver(tetm, w, chunk, kernel)
             s.set_bunch(w.sigma, w.charge, w.i0)
             s.step(w.steps)
             res.append([s.get(2, c) for c in E_NAMES + H_NAMES] + [s.wake(1)[0]])
@@ -201,10 +208,11 @@ def test_fp32_wakes_against_oracle(tetm):
 
 @pytest.mark.parametrize("precision,tol", [("fp32", 2e-5), ("fp64", TOL64)])
 def test_full_size_chain_head_matches_oracle(tetm, precision, tol):
+    from paper_0901_1053_gb300.autotune import tune_rz
     w = wl.cavity_chain_rz(precision=precision)
     n = 60
-    s = gpu_solver(tetm, w)
-    s.wave_fitted_chunk()
+    kernel, chunk = tune_rz(w)
+    s = gpu_solver(tetm, w, chunk, kernel)
     s.set_bunch(w.sigma, w.charge, w.i0)
     s.step(n)
     head = dataclasses.replace(w, nz=n + 10, pec=w.pec[:n + 10].copy(), steps=n)
