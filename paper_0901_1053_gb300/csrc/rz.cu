@@ -52,7 +52,10 @@ constexpr double kPi = 3.14159265358979323846;
 constexpr int kTile = 60;   // entries a warp owns (64-entry window minus 2 + 2 halo)
 // planes held ahead: register ring (float32 / float64) and shared-memory ring
 template <typename T>
-__host__ __device__ constexpr int ring_depth() { return sizeof(T) == 4 ? 4 : 2; }
+__host__ __device__ constexpr int ring_depth() { return sizeof(T) == 4 ? 3 : 2; }
+// resident blocks of 128 threads the register variant is compiled for
+template <typename T>
+__host__ __device__ constexpr int reg_min_blocks() { return sizeof(T) == 4 ? 4 : 1; }
 template <typename T>
 __host__ __device__ constexpr int async_depth() { return sizeof(T) == 4 ? 8 : 4; }
 // per-mode coefficient rows: alpha M^-1 (er, ephi, hr, hphi), 2 alpha M^-1
@@ -375,7 +378,7 @@ __device__ __forceinline__ void rz_item_reg(const RzArgs<T>& a, int witem) {
 }
 
 template <typename T>
-__global__ void __launch_bounds__(128) rz_step_kernel(const RzArgs<T> a) {
+__global__ void __launch_bounds__(128, reg_min_blocks<T>()) rz_step_kernel(const RzArgs<T> a) {
   const int nitems = a.n_work * a.n_modes;
   const int nwarps = (int)((gridDim.x * blockDim.x) >> 5);
   for (int w = (int)((blockIdx.x * blockDim.x + threadIdx.x) >> 5); w < nitems; w += nwarps)
