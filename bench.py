@@ -39,6 +39,8 @@ sys.path.insert(0, ROOT)
 
 METRIC = "Gcell-updates/s"
 UNIT = "Gcell-updates/s"
+RZ_FLOPS_PER_CELL = 47
+FP64_PEAK_TFLOPS = 1.25
 
 
 def parse_args():
@@ -51,7 +53,7 @@ def parse_args():
                    choices=["collimator", "plain_pipe", "batch", "serve", "dielectric", "rz"])
     p.add_argument("--rz-chunk", type=int, default=0,
                    help="rz: planes per work item (0 = chosen by the autotuner, untimed)")
-    p.add_argument("--rz-kernel", default=None, choices=[None, "async", "register"],
+    p.add_argument("--rz-kernel", default=None, choices=[None, "async", "register", "bulk"],
                    help="rz: step kernel (default: chosen by the autotuner, untimed)")
     p.add_argument("--requests", type=int, default=2000, help="serve: requests in the stream")
     p.add_argument("--rate", type=float, default=40.0, help="serve: mean arrivals per second")
@@ -590,9 +592,18 @@ def run_rz_mode(args):
     esz = 4 if w.precision == "fp32" else 8
     bytes_per_cell = 12 * esz + 1
     proc = info["processed_cells"]
-    achieved = bytes_per_cell * proc / (kern_ms * 1e-3) / 1e9
-    peak, peak_kind = measured_peak_hbm()
-    kname = "rz_step_async_kernel" if kern == "async" else "rz_step_kernel"
+    kname = {"async": "rz_step_async_kernel", "bulk": "rz_step_bulk_kernel"}.get(kern, "rz_step_kernel")
+    if w.precision == "fp32":
+        achieved = bytes_per_cell * proc / (kern_ms * 1e-3) / 1e9
+        peak, peak_kind = measured_peak_hbm()
+        roof = {"bound": "hbm", "unit": "GB/s", "bytes_per_cell": bytes_per_cell}
+    else:
+        # float64 arithmetic sets the pace on this part: 47 flops per entry
+        # and step (the ten updates, a fused multiply-add counted as two)
+        achieved = RZ_FLOPS_PER_CELL * proc / (kern_ms * 1e-3) / 1e12
+        peak, peak_kind = FP64_PEAK_TFLOPS, "nominal fp64 rate of the part"
+        roof = {"bound": "alu", "unit": "TFLOP/s", "flops_per_cell": RZ_FLOPS_PER_CELL,
+                "hbm_gbs": bytes_per_cell * proc / (kern_ms * 1e-3) / 1e9}
     traffic = profiled_traffic("%s_%s_%s.md" % (kname, w.precision, w.name))
     s.close()
 
@@ -638,10 +649,9 @@ def run_rz_mode(args):
                    "l2": "inputs larger than L2 (two field sets of %.1f GB each)"
                          % (6 * esz * w.cells / 1e9),
                    "parallelism": "replicas x%d" % world},
-        "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
-                     "frac": achieved / peak, "traffic": traffic, "peak_kind": peak_kind,
-                     "kernel": kname, "kernel_ms": kern_ms,
-                     "bytes_per_cell": bytes_per_cell, "cells_per_launch": proc},
+        "roofline": dict(roof, achieved=achieved, peak=peak, frac=achieved / peak, traffic=traffic,
+                         peak_kind=peak_kind, kernel=kname, kernel_ms=kern_ms,
+                         cells_per_launch=proc),
         "cpu_baseline": cpu,
         "e2e": e2e,
         "gpu_launches": K,

@@ -44,7 +44,9 @@ extern "C" {
 
 /* step kernels (same results bit for bit; they differ in how loads run ahead) */
 #define TETM_RZ_KERNEL_ASYNC 0     /* asynchronous copies into a shared-memory ring (default) */
-#define TETM_RZ_KERNEL_REGISTER 1  /* a register ring of four planes                          */
+#define TETM_RZ_KERNEL_REGISTER 1  /* a register ring of planes                               */
+#define TETM_RZ_KERNEL_BULK 2      /* one bulk (TMA) copy per plane and work item into a
+                                      shared-memory ring, mbarrier completion               */
 
 typedef struct tetm_rz_grid {
   int32_t nr, nz;      /* primary cells, each >= 2                                 */
@@ -88,7 +90,9 @@ int tetm_rz_set_bunch(tetm_rz* s, double sigma, double q, int32_t i0);
 /* Queues n steps of Eq. (24) for every mode (n >= 0). */
 int tetm_rz_step(tetm_rz* s, int64_t n);
 
-/* Waits for the solve's stream. */
+/* Waits for the solve's stream. Returns TETM_E_TIMEOUT when a bounded
+ * device-side wait of the bulk-copy kernel gave up since the solve was
+ * created (the state is then not advanced correctly). */
 int tetm_rz_sync(tetm_rz* s);
 
 /* Wake potential of mode m_lo + mode [V/C], W(s) = -(1/q) * sum of e_z at the

@@ -146,13 +146,13 @@ def tune_rz(w, precision: Optional[str] = None, steps: int = 8, warmup: int = 3,
             extra_chunks: Sequence[int] = (32, 64, 128)):
     """(kernel, chunk_z) with the shortest step on a scratch solve of w's
     geometry: each step kernel with its wave-fitted chunk and a few fixed
-    ones. Returns ("async" | "register", chunk_z)."""
+    ones. Returns ("bulk" | "register" | "async", chunk_z)."""
     from . import tetm
     precision = precision or w.precision
     s = tetm.RzSolver(w.nr, w.nz, w.m_lo, w.m_hi, w.dr, w.dz, w.cdt, precision, pec=w.pec)
     best = None
     try:
-        for kern in ("async", "register"):
+        for kern in ("bulk", "register", "async"):
             s.set_kernel(kern)
             chunks = [s.wave_fitted_chunk()] + [c for c in extra_chunks]
             for c in dict.fromkeys(chunks):

@@ -84,11 +84,12 @@ RzLayout make_rz_layout(int nr, int nz) {
   L.nr = nr;
   L.nz = nz;
   // a window starts at i = 60 t - 2; with the axis at column 6 it starts on
-  // an even column (16-byte aligned pairs) and a 4-byte boundary of the mask;
-  // the pitch leaves room for the last window
+  // an even column (16-byte aligned pairs, a 16-byte aligned window of
+  // entries) and a 4-byte boundary of the mask; the pitch is a multiple of 16
+  // and leaves room for the 80 mask bytes copied for the last window
   L.orr = 6;
   const long long tiles = (nr + 1 + kTile - 1) / kTile;
-  L.pr = (std::max((long long)L.orr + nr + 3, (long long)kTile * tiles + 8) + 7) / 8 * 8;
+  L.pr = (std::max((long long)L.orr + nr + 3, (long long)kTile * tiles + 24) + 15) / 16 * 16;
   L.rows = nz + 3;
   return L;
 }
@@ -109,6 +110,7 @@ struct RzArgs {
   const T* J;             // [mode][2 c0]: share * c * Q_cell / dz
   double* W;              // [mode][nw]
   double inv_q;
+  int* err;               // set to 1 when a bounded wait gives up
 };
 
 template <typename T>
@@ -489,6 +491,164 @@ __global__ void __launch_bounds__(128) rz_step_async_kernel(const RzArgs<T> a) {
     rz_item_async<T>(a, w, wsm);
 }
 
+// --- bulk-copy variant -------------------------------------------------------
+// A warp's window of one plane is one contiguous block of 64 entries x 6
+// components (1536 bytes in float32, 3072 in float64), so one bulk copy
+// (cp.async.bulk, the TMA engine) per plane fills a ring slot, and a second
+// one brings the 80-byte aligned block that holds the window's 64 activity
+// bytes. Lane 0 issues both with an mbarrier expecting their byte count;
+// every lane waits on the slot's mbarrier phase (bounded: after kMaxPolls
+// polls the kernel raises the error word and stops) and reads its own 48 /
+// 96 bytes. The ring runs bulk_depth planes ahead without registers.
+constexpr int kMaxPolls = 1 << 22;
+constexpr int kMaskBlock = 80;
+
+template <typename T>
+__host__ __device__ constexpr int bulk_depth() { return sizeof(T) == 4 ? 8 : 4; }
+template <typename T>
+__host__ __device__ constexpr int window_bytes() { return 64 * 6 * (int)sizeof(T); }
+template <typename T>
+constexpr size_t rz_bulk_warp_bytes() {
+  return (size_t)bulk_depth<T>() * (window_bytes<T>() + kMaskBlock) + (size_t)bulk_depth<T>() * 8;
+}
+
+__device__ __forceinline__ unsigned smem_u32(const void* p) {
+  return (unsigned)__cvta_generic_to_shared(p);
+}
+__device__ __forceinline__ void mbar_init(uint64_t* bar, unsigned count) {
+  asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(bar)), "r"(count) : "memory");
+}
+__device__ __forceinline__ void mbar_expect_tx(uint64_t* bar, unsigned bytes) {
+  asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_u32(bar)), "r"(bytes)
+               : "memory");
+}
+__device__ __forceinline__ void bulk_g2s(void* dst, const void* src, unsigned bytes, uint64_t* bar) {
+  asm volatile(
+      "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(
+          smem_u32(dst)),
+      "l"(src), "r"(bytes), "r"(smem_u32(bar))
+      : "memory");
+}
+__device__ __forceinline__ bool mbar_try_wait(uint64_t* bar, unsigned parity) {
+  unsigned ok;
+  asm volatile(
+      "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n selp.u32 %0, 1, 0, p;\n}"
+      : "=r"(ok)
+      : "r"(smem_u32(bar)), "r"(parity)
+      : "memory");
+  return ok != 0;
+}
+
+// Returns false when the wait gave up.
+__device__ __forceinline__ bool mbar_wait(uint64_t* bar, unsigned parity) {
+  for (int it = 0; it < kMaxPolls; ++it)
+    if (mbar_try_wait(bar, parity)) return true;
+  return false;
+}
+
+template <typename T>
+__device__ __forceinline__ bool rz_item_bulk(const RzArgs<T>& a, int witem, unsigned char* wsm,
+                                             unsigned& phases) {
+  constexpr int D = bulk_depth<T>();
+  constexpr int WB = window_bytes<T>();
+  const int lane = threadIdx.x & 31;
+  const Item<T> it = item_of(a, witem);
+  const LaneCo<T> c = lane_coefs(a, it);
+  const T mm = T(a.m_lo + it.mode);
+  const long long RS = a.L.pr * 6;
+  const long long MS = a.L.pr;
+  T* __restrict__ op = a.out + it.fbase;
+  const int wcol = it.tile * kTile - 2 + a.L.orr;          // window's first column
+  const T* __restrict__ wsrc = a.in + a.L.fidx(it.mode, 0, it.tile * kTile - 2, -1);
+  const int mcol = wcol & ~15;                              // 16-byte aligned mask block
+  const uint8_t* __restrict__ msrc = a.mask + mcol;
+  unsigned char* fring = wsm;
+  unsigned char* mring = wsm + (size_t)D * WB;
+  uint64_t* bars = reinterpret_cast<uint64_t*>(wsm + (size_t)D * (WB + kMaskBlock));
+  const int kstart = it.k0 - 1;
+  const int moff = wcol - mcol + 2 * lane;                  // lane's activity bytes in a block
+  int issued = kstart - 1;                                  // last plane whose copies are queued
+  int fetched = kstart - 1;                                 // last plane read
+
+  auto issue = [&](int p) {
+    if (p > it.k1) return;
+    const int slot = (p - kstart) % D;
+    if (lane == 0) {
+      asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+      mbar_expect_tx(bars + slot, WB + kMaskBlock);
+      bulk_g2s(fring + (size_t)slot * WB, wsrc + (long long)(p + 1) * RS, WB, bars + slot);
+      bulk_g2s(mring + (size_t)slot * kMaskBlock, msrc + (long long)(p + 1) * MS, kMaskBlock, bars + slot);
+    }
+    issued = p;
+  };
+  bool ok = true;
+  auto fetch = [&](int p, Pair6<T>& d) {
+    const int slot = (p - kstart) % D;
+    if (ok) ok = mbar_wait(bars + slot, (phases >> slot) & 1u);
+    if (ok) {
+      phases ^= 1u << slot;
+      fetched = p;
+    }
+    const T* src = reinterpret_cast<const T*>(fring + (size_t)slot * WB) + 12 * lane;
+#pragma unroll
+    for (int q = 0; q < 12; ++q) d.f[q] = src[q];
+    d.m = *reinterpret_cast<const unsigned short*>(mring + (size_t)slot * kMaskBlock + moff);
+  };
+
+  __syncwarp();
+  for (int p = 0; p < D - 1; ++p) issue(kstart + p);
+  LaneState<T> s;
+  Pair6<T> d0, d1;
+  fetch(kstart, d0);
+#pragma unroll
+  for (int e = 0; e < 2; ++e) {
+    s.er0[e] = d0.f[6 * e + kER];
+    s.ep0[e] = d0.f[6 * e + kEP];
+    s.hr_p[e] = T(0);
+    s.hp_p[e] = T(0);
+  }
+  for (int k = kstart; k < it.k1 && __all_sync(0xffffffffu, ok); ++k) {
+    __syncwarp();  // every lane is done with the slot refilled next
+    issue(k + D - 1);
+    fetch(k + 1, d1);
+    if (!__all_sync(0xffffffffu, ok)) break;
+    T out[12];
+    rz_plane(d0, d1, c, mm, s, current_at(a, it, it.src0, k), current_at(a, it, it.src1, k), out);
+    if (it.own && k >= it.k0) {
+      st_pair(op + (long long)(k + 1) * RS, out);
+      gather_wake(a, it, k, out);
+    }
+    d0 = d1;
+  }
+  if (__all_sync(0xffffffffu, ok)) return true;
+  // a wait gave up: raise the error word and drain the copies still queued
+  // (each wait bounded again) before the ring's memory is left
+  if (lane == 0) atomicExch(a.err, 1);
+  for (int p = fetched + 1; p <= issued; ++p) {
+    const int slot = (p - kstart) % D;
+    mbar_wait(bars + slot, (phases >> slot) & 1u);
+    phases ^= 1u << slot;
+  }
+  return false;
+}
+
+template <typename T>
+__global__ void __launch_bounds__(128) rz_step_bulk_kernel(const RzArgs<T> a) {
+  extern __shared__ __align__(128) unsigned char rz_bulk_smem[];
+  constexpr int D = bulk_depth<T>();
+  unsigned char* wsm = rz_bulk_smem + (size_t)(threadIdx.x >> 5) * rz_bulk_warp_bytes<T>();
+  uint64_t* bars = reinterpret_cast<uint64_t*>(wsm + (size_t)D * (window_bytes<T>() + kMaskBlock));
+  if ((threadIdx.x & 31) == 0)
+    for (int q = 0; q < D; ++q) mbar_init(bars + q, 1);
+  asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+  __syncwarp();
+  unsigned phases = 0;
+  const int nitems = a.n_work * a.n_modes;
+  const int nwarps = (int)((gridDim.x * blockDim.x) >> 5);
+  for (int w = (int)((blockIdx.x * blockDim.x + threadIdx.x) >> 5); w < nitems; w += nwarps)
+    if (!rz_item_bulk<T>(a, w, wsm, phases)) return;
+}
+
 // Activity bits from the cell geometry (staircase; the rules of the
 // per-radian metric): bit c set <=> object c at entry (i, k) is non-PEC.
 __device__ __forceinline__ bool cell_pec(const uint8_t* pec, int nr, int nz, int ci, int ck) {
@@ -673,6 +833,7 @@ struct tetm_rz {
   cudaStream_t own = nullptr, st = nullptr;
   int resident = 0;
   int kernel = TETM_RZ_KERNEL_ASYNC;
+  int* err = nullptr;            // device error word of the bulk-copy kernel
 };
 
 namespace {
@@ -697,6 +858,7 @@ int rz_launch_steps(tetm_rz* s, long long n) {
   a.J = static_cast<const T*>(s->J);
   a.W = s->W;
   a.inv_q = s->bunch ? 1.0 / s->q : 0.0;
+  a.err = s->err;
   const int items = s->n_work * s->n_modes;
   const int blocks = std::max(1, std::min(s->resident, (items + 3) / 4));
   for (long long t = 0; t < n; ++t) {
@@ -704,7 +866,9 @@ int rz_launch_steps(tetm_rz* s, long long n) {
     a.out = static_cast<T*>(s->set[s->cur ^ 1]);
     a.n = s->step;
     if (items > 0) {
-      if (s->kernel == TETM_RZ_KERNEL_ASYNC)
+      if (s->kernel == TETM_RZ_KERNEL_BULK)
+        rz_step_bulk_kernel<T><<<blocks, 128, 4 * rz_bulk_warp_bytes<T>(), s->st>>>(a);
+      else if (s->kernel == TETM_RZ_KERNEL_ASYNC)
         rz_step_async_kernel<T><<<blocks, 128, 4 * rz_async_warp_bytes<T>(), s->st>>>(a);
       else
         rz_step_kernel<T><<<blocks, 128, 0, s->st>>>(a);
@@ -727,8 +891,14 @@ int rz_occupancy(tetm_rz* s) {
   if (e == cudaSuccess && smem > 48 * 1024)
     e = cudaFuncSetAttribute(rz_step_async_kernel<T>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                              (int)smem);
+  const size_t bsmem = 4 * rz_bulk_warp_bytes<T>();
+  if (e == cudaSuccess && bsmem > 48 * 1024)
+    e = cudaFuncSetAttribute(rz_step_bulk_kernel<T>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                             (int)bsmem);
   if (e == cudaSuccess) {
-    if (s->kernel == TETM_RZ_KERNEL_ASYNC)
+    if (s->kernel == TETM_RZ_KERNEL_BULK)
+      e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, rz_step_bulk_kernel<T>, 128, bsmem);
+    else if (s->kernel == TETM_RZ_KERNEL_ASYNC)
       e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, rz_step_async_kernel<T>, 128, smem);
     else
       e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, rz_step_kernel<T>, 128, 0);
@@ -882,6 +1052,8 @@ int tetm_rz_create(const tetm_rz_grid* g, const double* eps_r, const double* mu_
     if ((e = cudaMalloc(&s->coef, cob)) != cudaSuccess) break;
     if ((e = cudaMalloc(&s->metric, meb)) != cudaSuccess) break;
     if ((e = cudaMalloc(&s->partial, sizeof(double) * (kEnergyBlocks + 1))) != cudaSuccess) break;
+    if ((e = cudaMalloc(&s->err, sizeof(int))) != cudaSuccess) break;
+    if ((e = cudaMemsetAsync(s->err, 0, sizeof(int), s->st)) != cudaSuccess) break;
     if ((e = cudaMemsetAsync(s->set[0], 0, fb, s->st)) != cudaSuccess) break;
     if ((e = cudaMemsetAsync(s->set[1], 0, fb, s->st)) != cudaSuccess) break;
     if (pec) {
@@ -972,8 +1144,11 @@ int tetm_rz_step(tetm_rz* s, int64_t n) {
 
 int tetm_rz_sync(tetm_rz* s) {
   if (!s) return TETM_E_ARG;
-  cudaError_t e = cudaStreamSynchronize(s->st);
-  return e == cudaSuccess ? TETM_OK : rz_fail(e);
+  int flag = 0;
+  cudaError_t e = cudaMemcpyAsync(&flag, s->err, sizeof(int), cudaMemcpyDeviceToHost, s->st);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(s->st);
+  if (e != cudaSuccess) return rz_fail(e);
+  return flag ? TETM_E_TIMEOUT : TETM_OK;
 }
 
 int tetm_rz_wake(tetm_rz* s, int32_t mode, double* out, int32_t cap, int32_t* n_out, double* s0,
@@ -1058,7 +1233,9 @@ int tetm_rz_set_tiling(tetm_rz* s, int32_t chunk_z) {
 }
 
 int tetm_rz_set_kernel(tetm_rz* s, int32_t kernel) {
-  if (!s || (kernel != TETM_RZ_KERNEL_REGISTER && kernel != TETM_RZ_KERNEL_ASYNC)) return TETM_E_ARG;
+  if (!s || (kernel != TETM_RZ_KERNEL_REGISTER && kernel != TETM_RZ_KERNEL_ASYNC &&
+             kernel != TETM_RZ_KERNEL_BULK))
+    return TETM_E_ARG;
   s->kernel = kernel;
   return s->esz == 8 ? rz_occupancy<double>(s) : rz_occupancy<float>(s);
 }
@@ -1097,6 +1274,7 @@ int tetm_rz_destroy(tetm_rz* s) {
   cudaFree(s->J);
   cudaFree(s->W);
   cudaFree(s->partial);
+  cudaFree(s->err);
   if (s->own) cudaStreamDestroy(s->own);
   cudaGetLastError();
   delete s;

@@ -48,6 +48,7 @@ EXPORTS = ("tetm_create", "tetm_set_bunch", "tetm_step", "tetm_sync", "tetm_wake
            "tetm_rz_set_kernel")
 TETM_RZ_KERNEL_ASYNC = 0
 TETM_RZ_KERNEL_REGISTER = 1
+TETM_RZ_KERNEL_BULK = 2
 RZ_COMPONENTS = ("er", "ephi", "ez", "hr", "hphi", "hz")
 TETM_RZ_MAX_MODES = 64
 
@@ -419,7 +420,8 @@ class RzSolver:
         _check(lib.tetm_rz_set_tiling(self.h, int(chunk_z)), "tetm_rz_set_tiling")
 
     def set_kernel(self, kernel):
-        k = {"async": TETM_RZ_KERNEL_ASYNC, "register": TETM_RZ_KERNEL_REGISTER}[kernel] \
+        k = {"async": TETM_RZ_KERNEL_ASYNC, "register": TETM_RZ_KERNEL_REGISTER,
+             "bulk": TETM_RZ_KERNEL_BULK}[kernel] \
             if isinstance(kernel, str) else int(kernel)
         _check(lib.tetm_rz_set_kernel(self.h, k), "tetm_rz_set_kernel")
 

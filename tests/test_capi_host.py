@@ -87,6 +87,6 @@ def test_rz_bytes_needed(tetm):
     g64 = tetm.make_rz_grid(512, 16384, 0, 4, 1e-3, 1e-3, precision="fp64")
     cells = 5 * 513 * 16385
     b32, b64 = tetm.tetm_rz_bytes_needed(g32), tetm.tetm_rz_bytes_needed(g64)
-    assert 48 * cells < b32 < 56 * cells          # two sets of six float32 per mode + mask
-    assert 96 * cells < b64 < 104 * cells
+    assert 48 * cells < b32 < 57 * cells          # two sets of six float32 per mode + mask
+    assert 96 * cells < b64 < 112 * cells         # row pitch padded to whole windows
     assert tetm.tetm_rz_bytes_needed(tetm.make_rz_grid(0, 8, 0, 0, 1e-3, 1e-3)) == 0

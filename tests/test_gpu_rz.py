@@ -78,7 +78,7 @@ def rel(a, b):
 # FP64 parity, field by field and wake by wake
 # ---------------------------------------------------------------------------
 
-KERNELS = ("async", "register")
+KERNELS = ("async", "register", "bulk")
 
 
 @pytest.mark.parametrize("kernel", KERNELS)
@@ -148,7 +148,7 @@ def test_chunk_sizes_and_kernels_are_bitwise_identical(tetm):
         w = small_chain(70, 130, 0, 2, i0=5, steps=90, precision=prec)
         res = []
         for chunk, kernel in ((4, "async"), (13, "async"), (64, "async"), (13, "register"),
-                              (64, "register")):
+                              (64, "register"), (4, "bulk"), (13, "bulk"), (64, "bulk")):
             s = gpu_solver(tetm, w, chunk, kernel)
             s.set_bunch(w.sigma, w.charge, w.i0)
             s.step(w.steps)
