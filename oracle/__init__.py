@@ -71,6 +71,10 @@ def _load():
     lib.oracle_step_count.argtypes = [vp]
     lib.oracle_dt.restype = d
     lib.oracle_dt.argtypes = [vp]
+    lib.oracle_set_bunch_static.restype = i
+    lib.oracle_set_bunch_static.argtypes = [vp, d, d, i, i, i]
+    lib.oracle_kshift.restype = ctypes.c_long
+    lib.oracle_kshift.argtypes = [vp]
     lib.oracle_bunch_info.restype = i
     lib.oracle_bunch_info.argtypes = [vp, ctypes.POINTER(i), ctypes.POINTER(i),
                                       ctypes.POINTER(i), vp]
@@ -146,6 +150,17 @@ class Oracle:
     def set_bunch(self, sigma, charge, i0, j0):
         if self.lib.oracle_set_bunch(self.h, float(sigma), float(charge), int(i0), int(j0)) != 0:
             raise ValueError("oracle_set_bunch: bad argument")
+
+    def set_bunch_static(self, sigma, charge, i0, j0, k_head):
+        """Bunch with its head at plane k_head at step 0, carrying its discrete
+        TEM field (static start in a uniform vacuum entry section)."""
+        if self.lib.oracle_set_bunch_static(self.h, float(sigma), float(charge), int(i0), int(j0),
+                                            int(k_head)) != 0:
+            raise ValueError("oracle_set_bunch_static: bad argument or non-uniform entry section")
+
+    @property
+    def kshift(self):
+        return int(self.lib.oracle_kshift(self.h))
 
     def current(self, n):
         out = np.zeros(self.shape, dtype=np.float64)

@@ -51,6 +51,8 @@ typedef struct oracle {
   double *wake;         /* W(s_m), m = m_min .. m_max */
   double *jz;           /* work array for the current of one step */
   long step;            /* n of the state y^n = (u^{n-1/2}, v^n) */
+  long kshift;          /* bunch head at plane step + kshift (0: cold start at the wall) */
+  int vacuum;           /* no material arrays were given */
 } oracle_t;
 
 enum { EX = 0, EY, EZ, HX, HY, HZ };
@@ -108,6 +110,7 @@ oracle_t *oracle_new(int nx, int ny, int nz, double dx, double dy, double dz, do
   o->mx = nx + 1; o->my = ny + 1; o->mz = nz + 1;
   o->n = o->mx * o->my * o->mz;
   o->sx = 1; o->sy = o->mx; o->sz = o->mx * o->my;
+  o->vacuum = (eps_r == NULL && mu_r == NULL);
   o->dx = dx; o->dy = dy; o->dz = dz;
   o->dt = (cdt > 0 ? cdt : dz) / OR_C0;
   o->at = 0.5 * o->dt;
@@ -196,7 +199,7 @@ void oracle_current(const oracle_t *o, long n, double *jz) {
   memset(jz, 0, sizeof(double) * (size_t)o->n);
   if (!o->has_bunch) return;
   for (long k = 0; k < o->nz; ++k) {
-    long d = k - n + o->c0;
+    long d = k - (n + o->kshift) + o->c0;
     if (d < -o->c0 || d >= o->c0) continue;
     jz[idx(o, o->i0, o->j0, k)] = OR_C0 * o->qcell[d + o->c0] / o->dz;
   }
@@ -245,7 +248,7 @@ void oracle_step_j(oracle_t *o, const double *jz, const double *jx, const double
 static void wake_gather(oracle_t *o, long n) {
   const double *ez = o->f[EZ];
   for (int m = o->m_min; m <= o->m_max; ++m) {
-    long k = n - m - o->c0;
+    long k = (n + o->kshift) - m - o->c0;
     if (k < 0 || k >= o->nz) continue;
     o->wake[m - o->m_min] -= ez[idx(o, o->i0, o->j0, k)] / o->q;
   }
@@ -386,3 +389,128 @@ int oracle_bunch_info(const oracle_t *o, int *c0, int *m_min, int *m_max, double
   if (qcell) memcpy(qcell, o->qcell, sizeof(double) * (size_t)(2 * o->c0));
   return 0;
 }
+
+
+/* ------------------------------------------------------------------------
+ * Static start: the bunch begins inside a uniform entry pipe carrying its own
+ * discrete TEM field, as if it had come from an infinite ingoing pipe (the
+ * paper's examples, Sec. 5). At c*dt = dz such a field moves exactly one
+ * cell per step with the bunch (zero z-dispersion, Sec. 4.5), so nothing is
+ * radiated until the bunch meets a change of cross-section.
+ *
+ * Transverse part: the potential phi on the nodes of the entry cross-section
+ * solves (dy/dx P_x^T P_x + dx/dy P_y^T P_y) phi = delta(i0, j0) over the
+ * non-PEC edges, phi = 0 on every node that touches a PEC cell or the wall.
+ * Longitudinal part: with the head at plane K at step 0, the line current of
+ * step n on edge k is jj(u) = c Q_cell(u - K + c0)/dz with u = k - n; a TEM
+ * field ex = -P_x phi G(u), ey = -P_y phi G(u) at time n and
+ * hx = (dx/dy) P_y phi G(u+1)/eta0, hy = -(dy/dx) P_x phi G(u+1)/eta0 at
+ * n - 1/2 carries the current (G(u) + G(u+1))/(2 eta0), so
+ * G(u) + G(u+1) = 2 eta0 jj(u), G = 0 ahead of the head. (The alternating
+ * remainder behind the tail is the alternating sum of the symmetric
+ * Q_cell, which vanishes.)
+ * ---------------------------------------------------------------------- */
+
+/* plain conjugate gradients on the unknown nodes of one cross-section */
+static void cg_solve(int n, const long *ex_a, const long *ex_b, const double *ex_w, long nex,
+                     const long *node_of, const double *rhs, double *x) {
+  double *r = (double *)calloc((size_t)n, sizeof(double));
+  double *p = (double *)calloc((size_t)n, sizeof(double));
+  double *ap = (double *)calloc((size_t)n, sizeof(double));
+  (void)node_of;
+  for (int q = 0; q < n; ++q) { x[q] = 0.0; r[q] = rhs[q]; p[q] = rhs[q]; }
+  double rr = 0.0, bb = 0.0;
+  for (int q = 0; q < n; ++q) { rr += r[q] * r[q]; bb += rhs[q] * rhs[q]; }
+  for (int it = 0; it < 20 * n + 100 && rr > 1e-30 * bb; ++it) {
+    for (int q = 0; q < n; ++q) ap[q] = 0.0;
+    for (long e = 0; e < nex; ++e) {       /* each edge couples nodes a, b (-1: on the wall) */
+      const long a = ex_a[e], b = ex_b[e];
+      const double pa = a >= 0 ? p[a] : 0.0, pb = b >= 0 ? p[b] : 0.0;
+      if (a >= 0) ap[a] += ex_w[e] * (pa - pb);
+      if (b >= 0) ap[b] += ex_w[e] * (pb - pa);
+    }
+    double pap = 0.0;
+    for (int q = 0; q < n; ++q) pap += p[q] * ap[q];
+    const double alpha = rr / pap;
+    double rr2 = 0.0;
+    for (int q = 0; q < n; ++q) {
+      x[q] += alpha * p[q];
+      r[q] -= alpha * ap[q];
+      rr2 += r[q] * r[q];
+    }
+    const double beta = rr2 / rr;
+    for (int q = 0; q < n; ++q) p[q] = r[q] + beta * p[q];
+    rr = rr2;
+  }
+  free(r); free(p); free(ap);
+}
+
+int oracle_set_bunch_static(oracle_t *o, double sigma, double q, int i0, int j0, int k_head) {
+  if (!o->vacuum || o->step != 0 || o->has_bunch) return -1;
+  if (oracle_set_bunch(o, sigma, q, i0, j0) != 0) return -1;
+  const int c0 = o->c0, K = k_head;
+  if (K < 2 * c0 + 2 || K > o->nz) { o->has_bunch = 0; return -1; }
+  /* the entry section: planes 1..K carry the same objects as plane 1 */
+  for (int c = 0; c < 6; ++c)
+    for (long k = 2; k <= K; ++k)
+      for (long j = 0; j <= o->ny; ++j)
+        for (long i = 0; i <= o->nx; ++i)
+          if (o->m[c][idx(o, i, j, k)] != o->m[c][idx(o, i, j, 1)]) { o->has_bunch = 0; return -1; }
+  /* unknown nodes: those whose ez edge in plane 1 is non-PEC (all four cells) */
+  const long nn = o->mx * o->my;
+  long *node_of = (long *)malloc(sizeof(long) * (size_t)nn);
+  int n_unk = 0;
+  for (long j = 0; j <= o->ny; ++j)
+    for (long i = 0; i <= o->nx; ++i)
+      node_of[i + o->mx * j] = o->m[EZ][idx(o, i, j, 1)] != 0.0 ? n_unk++ : -1;
+  if (node_of[i0 + o->mx * j0] < 0 || n_unk == 0) { free(node_of); o->has_bunch = 0; return -1; }
+  /* non-PEC transverse edges of the section with their weights */
+  long cap = 2 * nn, nex = 0;
+  long *ea = (long *)malloc(sizeof(long) * (size_t)cap);
+  long *eb = (long *)malloc(sizeof(long) * (size_t)cap);
+  double *ew = (double *)malloc(sizeof(double) * (size_t)cap);
+  for (long j = 0; j <= o->ny; ++j)
+    for (long i = 0; i <= o->nx; ++i) {
+      if (i < o->nx && o->m[EX][idx(o, i, j, 1)] != 0.0) {
+        ea[nex] = node_of[i + o->mx * j]; eb[nex] = node_of[i + 1 + o->mx * j];
+        ew[nex++] = o->dy / o->dx;
+      }
+      if (j < o->ny && o->m[EY][idx(o, i, j, 1)] != 0.0) {
+        ea[nex] = node_of[i + o->mx * j]; eb[nex] = node_of[i + o->mx * (j + 1)];
+        ew[nex++] = o->dx / o->dy;
+      }
+    }
+  double *rhs = (double *)calloc((size_t)n_unk, sizeof(double));
+  double *x = (double *)calloc((size_t)n_unk, sizeof(double));
+  rhs[node_of[i0 + o->mx * j0]] = 1.0;
+  cg_solve(n_unk, ea, eb, ew, nex, node_of, rhs, x);
+  double *phi = (double *)calloc((size_t)nn, sizeof(double));
+  for (long t = 0; t < nn; ++t) phi[t] = node_of[t] >= 0 ? x[node_of[t]] : 0.0;
+  /* longitudinal profile G(u), u = -1 .. K (G = 0 elsewhere) */
+  const double eta0 = OR_MU0 * OR_C0;
+  double *G = (double *)calloc((size_t)(K + 3), sizeof(double));   /* G[u + 1] */
+  for (long u = K - 1; u >= K - 2 * c0; --u) {
+    const double jj = OR_C0 * o->qcell[u - K + 2 * c0] / o->dz;
+    G[u + 1] = 2.0 * eta0 * jj - G[u + 2];
+  }
+  for (long k = 0; k <= o->nz; ++k)
+    for (long j = 0; j <= o->ny; ++j)
+      for (long i = 0; i <= o->nx; ++i) {
+        const long n = idx(o, i, j, k);
+        const double g0 = (k <= K) ? G[k + 1] : 0.0;
+        const double g1 = (k + 1 <= K) ? G[k + 2] : 0.0;
+        const double pxp = (i < o->nx) ? phi[i + 1 + o->mx * j] - phi[i + o->mx * j] : 0.0;
+        const double pyp = (j < o->ny) ? phi[i + o->mx * (j + 1)] - phi[i + o->mx * j] : 0.0;
+        o->f[EX][n] = o->m[EX][n] != 0.0 ? -pxp * g0 : 0.0;
+        o->f[EY][n] = o->m[EY][n] != 0.0 ? -pyp * g0 : 0.0;
+        o->f[EZ][n] = 0.0;
+        o->f[HX][n] = o->m[HX][n] != 0.0 ? (o->dx / o->dy) * pyp * g1 / eta0 : 0.0;
+        o->f[HY][n] = o->m[HY][n] != 0.0 ? -(o->dy / o->dx) * pxp * g1 / eta0 : 0.0;
+        o->f[HZ][n] = 0.0;
+      }
+  o->kshift = K;
+  free(node_of); free(ea); free(eb); free(ew); free(rhs); free(x); free(phi); free(G);
+  return 0;
+}
+
+long oracle_kshift(const oracle_t *o) { return o->kshift; }

@@ -521,3 +521,100 @@ def test_as_written_cubic_config_fails_stability_check():
     assert not oracle.stable(w.dx, w.dy, w.dz, w.cdt)
     w2 = wl.plain_pipe()
     assert oracle.stable(w2.dx, w2.dy, w2.dz, w2.cdt)
+
+
+# ---------------------------------------------------------------------------
+# Static start: the bunch enters from an infinite ingoing pipe (Sec. 5) with
+# its discrete TEM field; at c*dt = dz that field moves one cell per step
+# (Sec. 4.5), so a smooth pipe radiates nothing
+# ---------------------------------------------------------------------------
+
+def _round_pipe(nx, ny, nz, radius_of_k):
+    return wl.radius_mask(nx, ny, nz, radius_of_k)
+
+
+def test_static_start_moves_rigidly_and_leaves_no_wake_in_a_smooth_pipe():
+    nx = ny = 14
+    nz = 90
+    pec = _round_pipe(nx, ny, nz, lambda k: np.full(k.shape, 5.5))
+    sigma, q, K = 3 * MM, 1e-9, 34
+    o = Oracle(nx, ny, nz, DXY, DXY, MM, pec=pec)
+    o.set_bunch_static(sigma, q, 7, 7, K)
+    assert o.kshift == K
+    f0 = o.fields()
+    assert not f0["ez"].any() and not f0["hz"].any()
+    n = 40
+    o.step(n)
+    escale, hscale = np.max(np.abs(f0["ex"])), np.max(np.abs(f0["hx"]))
+    for c in oracle.COMPONENTS:
+        shifted = np.zeros_like(f0[c])
+        shifted[n:] = f0[c][:-n]
+        scale = escale if c[0] == "e" else hscale
+        assert np.max(np.abs(o.get(c) - shifted)) <= 1e-13 * scale, c
+    cold = Oracle(nx, ny, nz, DXY, DXY, MM, pec=pec)
+    cold.set_bunch(sigma, q, 7, 7)
+    cold.step(n + K)
+    assert np.max(np.abs(o.wake()[0])) <= 1e-13 * np.max(np.abs(cold.wake()[0]))
+
+
+def test_static_start_gauss_law():
+    """The static field carries the bunch charge from the first step on: the
+    node charges of Eq. (35) equal the closed-form charges of the shifted
+    bunch at the bunch nodes and vanish elsewhere."""
+    nx = ny = 12
+    nz = 70
+    pec = _round_pipe(nx, ny, nz, lambda k: np.where((k >= 40) & (k < 50), 5.5, 4.5))
+    q, sigma, K = 1e-9, 2.5 * MM, 30
+    c0 = math.ceil(5 * sigma / MM - 1e-12)
+    for n in (0, 7, 21):
+        o = Oracle(nx, ny, nz, DXY, DXY, MM, pec=pec)
+        o.set_bunch_static(sigma, q, 6, 6, K)
+        o.step(n)
+        f0 = o.fields()
+        o.step(1)
+        f1 = o.fields()
+        qe = o.qbar_e(f1["ex"], f0["ex"], f1["ey"], f0["ey"], f1["ez"])
+        zc = (n + K + 0.5 - c0) * MM
+        expect = np.zeros(o.shape)
+        for k in range(nz + 1):
+            expect[k, 6, 6] = _node_charge_closed_form(q, sigma, MM, zc, k)
+        inode = _interior_nodes(o)
+        assert np.max(np.abs(qe[inode] - expect[inode])) <= 1e-12 * q
+        assert np.max(np.abs(expect[inode])) > 0.05 * q
+
+
+def test_static_start_energy_identity_in_a_cavity():
+    """Energy law (19) summed over the passage (until the bunch has left the
+    grid): W^N - W^0 = Q/2 sum_d Q_cell(d) [W(m_d) + W(m_d - 1)], with the
+    static field's own energy in W^0."""
+    nx = ny = 12
+    nz = 60
+    pec = _round_pipe(nx, ny, nz, lambda k: np.where((k >= 30) & (k < 40), 5.5, 3.5))
+    q, sigma, K = 1e-9, 2.0 * MM, 24
+    o = Oracle(nx, ny, nz, DXY, DXY, MM, pec=pec)
+    o.set_bunch_static(sigma, q, 6, 6, K)
+    w0 = o.energy()
+    assert w0 > 0
+    o.step(nz - (K - 2 * math.ceil(5 * sigma / MM - 1e-12)) + 1)
+    wk, s0, ds = o.wake()
+    info = o.bunch_info()
+    c0, m_min = info["c0"], info["m_min"]
+    rhs = 0.0
+    for d in range(-c0, c0):
+        rhs += 0.5 * q * info["qcell"][d + c0] * (wk[-d - m_min] + wk[-d - 1 - m_min])
+    assert o.energy() - w0 == pytest.approx(rhs, rel=1e-10, abs=1e-12 * w0)
+    assert abs(rhs) > 1e-6 * w0                       # the cavity takes energy from the bunch
+
+
+def test_static_start_rejects_what_it_cannot_represent():
+    nx = ny = 10
+    nz = 60
+    pec = _round_pipe(nx, ny, nz, lambda k: np.where(k < 20, 4.5, 3.5))
+    o = Oracle(nx, ny, nz, DXY, DXY, MM, pec=pec)
+    with pytest.raises(ValueError):
+        o.set_bunch_static(2 * MM, 1e-9, 5, 5, 30)        # entry section not uniform up to K
+    with pytest.raises(ValueError):
+        Oracle(nx, ny, nz, DXY, DXY, MM, pec=pec).set_bunch_static(2 * MM, 1e-9, 5, 5, 12)  # K < 2 c0 + 2
+    eps = np.ones((nz, ny, nx))
+    with pytest.raises(ValueError):
+        Oracle(nx, ny, nz, DXY, DXY, MM, eps_r=eps, pec=pec).set_bunch_static(MM, 1e-9, 5, 5, 15)
