@@ -115,6 +115,23 @@ int tetm_create(const tetm_grid* g, const double* eps_r, const double* mu_r, con
  * s_m = m dz, m = -c0-1 .. ceil(15 sigma/dz). */
 int tetm_set_bunch(tetm_solver* s, double sigma_z, double charge, int32_t i0, int32_t j0);
 
+/* Static start (Sec. 5: the paper's structures sit between infinite ingoing
+ * and outgoing pipes): the bunch of tetm_set_bunch (same sigma_z, charge,
+ * i0, j0, profile and wake window) begins with its head at plane k_head
+ * instead of at the wall, carrying its own discrete TEM field, so it moves
+ * through the uniform entry section without radiating (at c*dt = dz the field
+ * shifts one cell per step, Sec. 4.5). The transverse potential solves the
+ * discrete Poisson problem of the entry cross-section (non-PEC edges, zero on
+ * nodes touching PEC); the longitudinal profile carries the bunch current.
+ * Current and wake samples then refer to step + k_head. Requires: vacuum
+ * (no eps_r/mu_r, else TETM_E_UNSUPPORTED); step 0 and no bunch yet
+ * (TETM_E_STATE); c*dt == dz (TETM_E_NOT_MAGIC); 2*c0 + 2 <= k_head <= nz
+ * with c0 = ceil(5 sigma_z/dz), planes 1..k_head of the grid carrying the
+ * same objects, and (i0, j0) a node whose ez edge is not PEC (TETM_E_ARG).
+ * Writes planes 0..k_head+1 of the state. Synchronizes. */
+int tetm_set_bunch_static(tetm_solver* s, double sigma_z, double charge, int32_t i0, int32_t j0,
+                          int32_t k_head);
+
 /* Advance n >= 0 steps of Eq. (23): per step the ten updates of Sec. 4.2
  * (TM stage hx, hy, ez, hx, hy; TE stage ex, ey, hz, ex, ey), the bunch
  * current in the ez update and one wake sample per window point. Queued on

@@ -292,6 +292,7 @@ StepArgs<T> tetm::step_args(tetm_solver* s, bool fused) {
   a.b.i0 = s->i0;
   a.b.j0 = s->j0;
   a.b.c0 = s->c0;
+  a.b.kshift = s->kshift;
   a.b.m_min = s->m_min;
   a.b.m_max = s->m_max;
   a.b.inv_q = s->bunch ? 1.0 / s->q : 0.0;
@@ -327,7 +328,7 @@ WorkView work_view(const tetm_solver* s) {
 
 template <typename T>
 int queue_balances(tetm_solver* s, double* rec) {
-  const double zc = ((double)(s->step - 1) + 0.5 - s->c0) * s->g.dz;
+  const double zc = ((double)(s->step + s->kshift - 1) + 0.5 - s->c0) * s->g.dz;
   CK(launch_bunch_charge(s->bunch ? s->q : 0.0, s->bunch ? s->sigma : 1.0, s->g.dz, zc, s->g.nz,
                          s->qline, rec + 4, (double)s->step, rec, s->stream));
   const T *cur[6], *prv[6];
@@ -503,6 +504,7 @@ int tetm_create(const tetm_grid* g, const double* eps_r, const double* mu_r, con
   s->stream = nullptr;
   s->kernel = TETM_KERNEL_FUSED;
   s->uniform = uniform;
+  s->vacuum = uniform && eps_u == 1.0 && mu_u == 1.0;
   s->tile_x = 28;   // warp-tiled kernel (kernels_warp.cu)
   s->tile_y = 20;
   s->chunk_z = 32;
@@ -838,6 +840,7 @@ struct CkptHeader {
   int64_t step;
   int64_t count;
   int32_t bunch, nw;
+  int64_t kshift;
 };
 
 int tetm_save(tetm_solver* s, void* buf, size_t cap, size_t* used) {
@@ -850,13 +853,14 @@ int tetm_save(tetm_solver* s, void* buf, size_t cap, size_t* used) {
   if (cap < need) return TETM_E_ARG;
   CkptHeader h;
   memset(&h, 0, sizeof(h));
-  memcpy(h.magic, "TETMCKP1", 8);
+  memcpy(h.magic, "TETMCKP2", 8);
   h.nx = s->g.nx; h.ny = s->g.ny; h.nz = s->g.nz; h.precision = s->g.precision;
   h.dx = s->g.dx; h.dy = s->g.dy; h.dz = s->g.dz; h.cdt = s->g.cdt;
   h.step = s->step;
   h.count = s->L.count;
   h.bunch = s->bunch;
   h.nw = nw;
+  h.kshift = s->kshift;
   char* p = (char*)buf;
   memcpy(p, &h, sizeof(h));
   p += sizeof(h);
@@ -874,9 +878,10 @@ int tetm_load(tetm_solver* s, const void* buf, size_t size) {
   memcpy(&h, buf, sizeof(h));
   const int nw = s->bunch ? s->m_max - s->m_min + 1 : 0;
   const size_t fb = (size_t)s->L.count * s->esz;
-  if (memcmp(h.magic, "TETMCKP1", 8) != 0 || h.nx != s->g.nx || h.ny != s->g.ny || h.nz != s->g.nz ||
+  if (memcmp(h.magic, "TETMCKP2", 8) != 0 || h.nx != s->g.nx || h.ny != s->g.ny || h.nz != s->g.nz ||
       h.precision != s->g.precision || h.count != s->L.count || h.bunch != (int)s->bunch || h.nw != nw ||
-      h.dx != s->g.dx || h.dy != s->g.dy || h.dz != s->g.dz || h.cdt != s->g.cdt)
+      h.dx != s->g.dx || h.dy != s->g.dy || h.dz != s->g.dz || h.cdt != s->g.cdt ||
+      h.kshift != s->kshift)
     return TETM_E_ARG;
   if (size < sizeof(CkptHeader) + 6 * fb + sizeof(double) * (size_t)nw) return TETM_E_ARG;
   const char* p = (const char*)buf + sizeof(h);

@@ -59,13 +59,13 @@ __global__ void ref_update(StepArgs<T> a) {
     T cur = (hx[id - sy] - hx[id]) - (hy[id - sx] - hy[id]);
     const bool line = a.b.on && i == a.b.i0 && j == a.b.j0;
     if (line) {
-      const long long d = (long long)k - a.n + a.b.c0;
+      const long long d = (long long)k - (a.n + a.b.kshift) + a.b.c0;
       if (d >= -a.b.c0 && d < a.b.c0) cur -= a.b.J[d + a.b.c0];
     }
     const T ezn = ez[id] + c * cur;
     F[kEZ][id] = ezn;
     if (line) {  // wake sample: W(s_m) -= ez^{n+1/2}(k) / Q with m = n - k - c0
-      const long long mm = a.n - k - a.b.c0;
+      const long long mm = (a.n + a.b.kshift) - k - a.b.c0;
       if (mm >= a.b.m_min && mm <= a.b.m_max) a.b.W[mm - a.b.m_min] -= (double)ezn * a.b.inv_q;
     }
   } else if (C == kEX) {  // U6 / U9: ex += a M^-1 (P_z^T hy - P_y^T hz)
@@ -149,7 +149,7 @@ fused_step(const StepArgs<T> a) {
     __syncthreads();
     T cur = (sC[sy - 1][sx] - hxa) - (sD[sy][sx - 1] - hya);
     if (line && k >= 0) {
-      const long long d = (long long)k - a.n + a.b.c0;
+      const long long d = (long long)k - (a.n + a.b.kshift) + a.b.c0;
       if (d >= -a.b.c0 && d < a.b.c0) cur -= a.b.J[d + a.b.c0];
     }
     const T ezn = ez + cEZ * cur;                               // U3
@@ -163,7 +163,7 @@ fused_step(const StepArgs<T> a) {
         a.out[kHY][id] = hyn;
         a.out[kEZ][id] = ezn;
         if (line) {
-          const long long mm = a.n - k - a.b.c0;
+          const long long mm = (a.n + a.b.kshift) - k - a.b.c0;
           if (mm >= a.b.m_min && mm <= a.b.m_max) a.b.W[mm - a.b.m_min] -= (double)ezn * a.b.inv_q;
         }
       }

@@ -183,7 +183,7 @@ __device__ __forceinline__ void fused_step_warp_item(const StepArgs<T>& a, int i
         T cur = (hxa_p - hxa) - (shfl_up1(hya) - hya);
         const bool line = line_x && r == line_r;
         if (line && k >= 0) {
-          const long long dd = (long long)k - a.n + a.b.c0;
+          const long long dd = (long long)k - (a.n + a.b.kshift) + a.b.c0;
           if (dd >= -a.b.c0 && dd < a.b.c0) cur -= a.b.J[dd + a.b.c0];
         }
         const T ezn = ez + cEZ * cur;                                            // U3
@@ -194,7 +194,7 @@ __device__ __forceinline__ void fused_step_warp_item(const StepArgs<T>& a, int i
             oez[id] = ezn;
             ohy[id] = hyn;
             if (line) {
-              const long long mm = a.n - k - a.b.c0;
+              const long long mm = (a.n + a.b.kshift) - k - a.b.c0;
               if (mm >= a.b.m_min && mm <= a.b.m_max)
                 a.b.W[mm - a.b.m_min] -= (double)ezn * a.b.inv_q;
             }
@@ -433,7 +433,7 @@ __device__ __forceinline__ void fused_step_warp_reg_item(const StepArgs<T>& a, i
         T cur = (hxa_p - hxa) - (shfl_up1(hya) - hya);
         const bool line = line_x && r == line_r;
         if (line && k >= 0) {
-          const long long dd = (long long)k - a.n + a.b.c0;
+          const long long dd = (long long)k - (a.n + a.b.kshift) + a.b.c0;
           if (dd >= -a.b.c0 && dd < a.b.c0) cur -= a.b.J[dd + a.b.c0];
         }
         const T ezn = d.ez + cEZ * cur;                                         // U3
@@ -444,7 +444,7 @@ __device__ __forceinline__ void fused_step_warp_reg_item(const StepArgs<T>& a, i
             oez[id] = ezn;
             ohy[id] = hyn;
             if (line) {
-              const long long mm = a.n - k - a.b.c0;
+              const long long mm = (a.n + a.b.kshift) - k - a.b.c0;
               if (mm >= a.b.m_min && mm <= a.b.m_max)
                 a.b.W[mm - a.b.m_min] -= (double)ezn * a.b.inv_q;
             }
@@ -713,7 +713,7 @@ __device__ __forceinline__ void fused_step_warp_mat_item(const StepArgs<T>& a, i
         T cur = (hxa_p - hxa) - (shfl_up1(hya) - hya);
         const bool line = line_x && r == line_r;
         if (line && k >= 0) {
-          const long long dd = (long long)k - a.n + a.b.c0;
+          const long long dd = (long long)k - (a.n + a.b.kshift) + a.b.c0;
           if (dd >= -a.b.c0 && dd < a.b.c0) cur -= a.b.J[dd + a.b.c0];
         }
         const T ezn = ez + cEZ * cur;                                            // U3
@@ -724,7 +724,7 @@ __device__ __forceinline__ void fused_step_warp_mat_item(const StepArgs<T>& a, i
             oez[id] = ezn;
             ohy[id] = hyn;
             if (line) {
-              const long long mm = a.n - k - a.b.c0;
+              const long long mm = (a.n + a.b.kshift) - k - a.b.c0;
               if (mm >= a.b.m_min && mm <= a.b.m_max)
                 a.b.W[mm - a.b.m_min] -= (double)ezn * a.b.inv_q;
             }

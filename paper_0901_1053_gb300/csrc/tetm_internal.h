@@ -45,6 +45,7 @@ struct BunchDev {
   int on;               // 0: no bunch
   int i0, j0;           // bunch line node
   int c0;               // start offset in cells
+  long long kshift;     // the bunch head is at plane n + kshift at step n (0: cold start)
   int m_min, m_max;     // wake window
   double inv_q;         // 1/Q
   const T* J;           // J[d + c0] = c*Q_cell(d)/dz [A], d = -c0..c0-1
@@ -151,6 +152,7 @@ struct tetm_solver {
   double* minv_a[6];
   void* ua[6];
   bool uniform;
+  bool vacuum;    // no material arrays (eps_r = mu_r = 1)
   double alpha;   // dt/2
   cudaStream_t stream;
   int kernel;
@@ -164,6 +166,7 @@ struct tetm_solver {
   // bunch
   bool bunch;
   int i0, j0, c0, m_min, m_max;
+  long long kshift;   // static start: head at plane step + kshift
   double sigma, q;
   std::vector<double> qcell;
   void* J;

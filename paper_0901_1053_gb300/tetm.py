@@ -41,7 +41,7 @@ EXPORTS = ("tetm_create", "tetm_set_bunch", "tetm_step", "tetm_sync", "tetm_wake
            "tetm_get_info", "tetm_bytes_needed", "tetm_save", "tetm_load", "tetm_strerror",
            "tetm_set_balance_every", "tetm_balance_history", "tetm_energy_noalloc",
            "tetm_batch_create", "tetm_batch_step", "tetm_batch_sync", "tetm_batch_info",
-           "tetm_batch_destroy",
+           "tetm_batch_destroy", "tetm_set_bunch_static",
            "tetm_rz_create", "tetm_rz_set_bunch", "tetm_rz_step", "tetm_rz_sync", "tetm_rz_wake",
            "tetm_rz_energy", "tetm_rz_get_fields", "tetm_rz_set_fields", "tetm_rz_set_tiling",
            "tetm_rz_set_stream", "tetm_rz_get_info", "tetm_rz_bytes_needed", "tetm_rz_destroy",
@@ -92,6 +92,7 @@ def _load():
     sig = {
         "tetm_create": (ctypes.c_int, [ctypes.POINTER(tetm_grid), vp, vp, vp, pp]),
         "tetm_set_bunch": (ctypes.c_int, [vp, dbl, dbl, i32, i32]),
+        "tetm_set_bunch_static": (ctypes.c_int, [vp, dbl, dbl, i32, i32, i32]),
         "tetm_step": (ctypes.c_int, [vp, i32]),
         "tetm_sync": (ctypes.c_int, [vp]),
         "tetm_wake": (ctypes.c_int, [vp, vp, i32, ctypes.POINTER(i32), ctypes.POINTER(dbl),
@@ -230,6 +231,10 @@ class Solver:
     def set_bunch(self, sigma, charge, i0, j0):
         _check(lib.tetm_set_bunch(self.h, float(sigma), float(charge), int(i0), int(j0)),
                "tetm_set_bunch")
+
+    def set_bunch_static(self, sigma, charge, i0, j0, k_head):
+        _check(lib.tetm_set_bunch_static(self.h, float(sigma), float(charge), int(i0), int(j0),
+                                         int(k_head)), "tetm_set_bunch_static")
 
     def step(self, n=1):
         _check(lib.tetm_step(self.h, int(n)), "tetm_step")
