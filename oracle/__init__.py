@@ -250,6 +250,10 @@ def _load_rz():
     lib.rz_oracle_step_custom.argtypes = [vp, vp]
     lib.rz_oracle_wake.restype = i
     lib.rz_oracle_wake.argtypes = [vp, vp, i, ctypes.POINTER(i), dp, dp]
+    lib.rz_oracle_set_observer.restype = i
+    lib.rz_oracle_set_observer.argtypes = [vp, i]
+    lib.rz_oracle_wake_extra.restype = i
+    lib.rz_oracle_wake_extra.argtypes = [vp, i, vp, i]
     lib.rz_oracle_energy.restype = d
     lib.rz_oracle_energy.argtypes = [vp]
     lib.rz_oracle_get.argtypes = [vp, i, vp]
@@ -354,6 +358,26 @@ class RzOracle:
 
     def energy(self):
         return float(self.lib.rz_oracle_energy(self.h))
+
+    def set_observer(self, obs):
+        """Transverse wake at r_{obs+1/2} (before the first step)."""
+        if self.lib.rz_oracle_set_observer(self.h, int(obs)) != 0:
+            raise ValueError("rz_oracle_set_observer: bad argument or state")
+
+    def _extra(self, which):
+        n = len(self.wake()[0])
+        out = np.empty(n, dtype=np.float64)
+        if self.lib.rz_oracle_wake_extra(self.h, int(which), _ptr(out), n) != 0:
+            raise RuntimeError("no bunch set")
+        return out
+
+    def transverse_wake(self):
+        """Radial transverse wake (1/Q) sum (E_r - c mu0 H_phi) dz at r_{obs+1/2}, phi = 0."""
+        return self._extra(0)
+
+    def wake_at_observer(self):
+        """Longitudinal wakes at rings obs and obs+1."""
+        return self._extra(1), self._extra(2)
 
 
 def _rz_comp(c):

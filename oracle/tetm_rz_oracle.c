@@ -47,6 +47,9 @@ typedef struct rz_oracle {
   int has_bunch, i0, c0, m_min, m_max;
   double sigma, q, weight;
   double *qcell, *wake, *jz;
+  /* transverse wake at r_{obs+1/2} and longitudinal wakes at rings obs, obs+1 */
+  int obs;
+  double *twake, *wake_o0, *wake_o1;
   long step;
 } rz_oracle_t;
 
@@ -152,6 +155,7 @@ void rz_oracle_free(rz_oracle_t *o) {
   if (!o) return;
   for (int q = 0; q < 6; ++q) { free(o->f[q]); free(o->c[q]); }
   free(o->jz); free(o->qcell); free(o->wake);
+  free(o->twake); free(o->wake_o0); free(o->wake_o1);
   free(o);
 }
 
@@ -169,9 +173,13 @@ int rz_oracle_set_bunch(rz_oracle_t *o, double sigma, double q, int i0) {
   o->c0 = (int)ceil(5.0 * sigma / o->dz - 1e-12);
   o->m_min = -o->c0 - 1;
   o->m_max = (int)ceil(15.0 * sigma / o->dz - 1e-12);
-  free(o->qcell); free(o->wake);
+  free(o->qcell); free(o->wake); free(o->twake); free(o->wake_o0); free(o->wake_o1);
   o->qcell = (double *)calloc((size_t)(2 * o->c0), sizeof(double));
   o->wake = (double *)calloc((size_t)(o->m_max - o->m_min + 1), sizeof(double));
+  o->twake = (double *)calloc((size_t)(o->m_max - o->m_min + 1), sizeof(double));
+  o->wake_o0 = (double *)calloc((size_t)(o->m_max - o->m_min + 1), sizeof(double));
+  o->wake_o1 = (double *)calloc((size_t)(o->m_max - o->m_min + 1), sizeof(double));
+  o->obs = i0;
   for (int d = -o->c0; d < o->c0; ++d) {
     double a = d * o->dz, b = (d + 1) * o->dz;
     if (a < -5.0 * sigma) a = -5.0 * sigma;
@@ -216,27 +224,68 @@ void rz_oracle_step_j(rz_oracle_t *o, const double *jz) {
   for (long n = 0; n < N; ++n) er[n] += a * cer[n] * (-PzT(o, hp, n) + m * hz[n]);
 }
 
-static void rz_wake_gather(rz_oracle_t *o, long n) {
+/* Wakes (Sec. 5) along the path s = m*dz behind the bunch centre: with
+ * c*dt = dz the path meets e_z(k+1/2) at time n+1/2, e_r(k) at time n and
+ * h_phi(k+1/2) at time n+1/2 for the same n = k + m + c0.
+ * Longitudinal: W(s) = -(1/Q) sum e_z at the bunch ring (and at rings obs,
+ * obs+1). Transverse, radial component at r = r_{obs+1/2}, phi = 0 (the
+ * paper's dipole wake, Sec. 5): W_r(s) = (1/Q) sum (E_r - c mu0 H_phi) dz,
+ * with E_r = e_r/dr and, per radian, h_phi = -r H_phi (the sign with which
+ * the m-terms of (24) are written), so E_r - c mu0 H_phi =
+ * e_r/dr + eta0 h_phi/r_{obs+1/2}. er_n: e_r before the step. */
+static void rz_wake_gather(rz_oracle_t *o, long n, const double *er_n) {
+  const double eta0 = RZ_MU0 * RZ_C0;
+  const double rh = (o->obs + 0.5) * o->dr;
   for (int mm = o->m_min; mm <= o->m_max; ++mm) {
     const long k = n - mm - o->c0;
     if (k < 0 || k >= o->nz) continue;
-    o->wake[mm - o->m_min] -= o->f[EZ][o->i0 + o->mr * k] / o->q;
+    const int w = mm - o->m_min;
+    o->wake[w] -= o->f[EZ][o->i0 + o->mr * k] / o->q;
+    o->wake_o0[w] -= o->f[EZ][o->obs + o->mr * k] / o->q;
+    o->wake_o1[w] -= o->f[EZ][o->obs + 1 + o->mr * k] / o->q;
+    o->twake[w] += (er_n[o->obs + o->mr * k] / o->dr + eta0 * o->f[HPHI][o->obs + o->mr * k] / rh) *
+                   o->dz / o->q;
   }
+}
+
+static void rz_step_gather(rz_oracle_t *o, const double *jz) {
+  double *er_n = NULL;
+  if (o->has_bunch) {
+    er_n = (double *)malloc(sizeof(double) * (size_t)o->n);
+    memcpy(er_n, o->f[ER], sizeof(double) * (size_t)o->n);
+  }
+  rz_oracle_step_j(o, jz);
+  if (o->has_bunch) rz_wake_gather(o, o->step, er_n);
+  free(er_n);
+  o->step += 1;
 }
 
 void rz_oracle_step(rz_oracle_t *o, int nsteps) {
   for (int s = 0; s < nsteps; ++s) {
     if (o->has_bunch) rz_oracle_current(o, o->step, o->jz);
-    rz_oracle_step_j(o, o->has_bunch ? o->jz : NULL);
-    if (o->has_bunch) rz_wake_gather(o, o->step);
-    o->step += 1;
+    rz_step_gather(o, o->has_bunch ? o->jz : NULL);
   }
 }
 
-void rz_oracle_step_custom(rz_oracle_t *o, const double *jz) {
-  rz_oracle_step_j(o, jz);
-  if (o->has_bunch) rz_wake_gather(o, o->step);
-  o->step += 1;
+void rz_oracle_step_custom(rz_oracle_t *o, const double *jz) { rz_step_gather(o, jz); }
+
+/* Observation radius of the transverse wake: r_{obs+1/2}, 0 <= obs < nr - 1
+ * (before the first step; the bunch ring by default). */
+int rz_oracle_set_observer(rz_oracle_t *o, int obs) {
+  if (!o->has_bunch || o->step != 0 || obs < 0 || obs >= o->nr - 1) return -1;
+  o->obs = obs;
+  return 0;
+}
+
+/* which: 0 the transverse wake at r_{obs+1/2}, 1 / 2 the longitudinal wakes
+ * at rings obs / obs+1 (same window as rz_oracle_wake) */
+int rz_oracle_wake_extra(const rz_oracle_t *o, int which, double *out, int cap) {
+  if (!o->has_bunch || which < 0 || which > 2) return -1;
+  const int nw = o->m_max - o->m_min + 1;
+  if (cap < nw) return -1;
+  const double *src = which == 0 ? o->twake : (which == 1 ? o->wake_o0 : o->wake_o1);
+  memcpy(out, src, sizeof(double) * (size_t)nw);
+  return 0;
 }
 
 int rz_oracle_wake(const rz_oracle_t *o, double *out, int cap, int *n_out, double *s0, double *ds) {

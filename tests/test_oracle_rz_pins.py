@@ -439,3 +439,58 @@ def test_factor_pairing_reading():
                 np.testing.assert_allclose(g, d.propagator(), atol=1e-12)
         assert grow["derived"] < 1.0 + 1e-9
         assert grow["printed"] > 1.5
+
+
+# ---------------------------------------------------------------------------
+# Transverse wake (Sec. 5: the dipole wake of the transverse deflecting
+# structure) and the Panofsky-Wenzel theorem, dW_perp/ds = grad_perp W_par
+# (with W_par = -(1/Q) int E_z): in the scheme at c*dt = dz it holds exactly
+# between the radial wake at r_{i+1/2} and the longitudinal wakes at the
+# rings i and i+1, with the half-sample average the staggering asks for:
+#   W_r(m+1) - W_r(m) = dz/dr * [(W_{i+1} - W_i)(m) + (W_{i+1} - W_i)(m+1)] / 2
+# ---------------------------------------------------------------------------
+
+@pytest.mark.parametrize("m,i0,obs", [(1, 3, 3), (1, 3, 6), (2, 4, 5), (0, 0, 2)])
+def test_discrete_panofsky_wenzel(m, i0, obs):
+    nr, nz = 20, 100
+    pec = _cavity_pec(nr, nz, 7, 40, 70)
+    o = RzOracle(nr, nz, m, MM, MM, pec=pec)
+    o.set_bunch(2.5 * MM, 1e-9, i0)
+    o.set_observer(obs)
+    c0 = math.ceil(5 * 2.5 - 1e-12)
+    o.step(nz + 2 * c0 + math.ceil(15 * 2.5) + 2)
+    wr = o.transverse_wake()
+    w0, w1 = o.wake_at_observer()
+    grad = (w1 - w0) * (MM / MM)
+    rhs = 0.5 * (grad[:-1] + grad[1:])
+    lhs = np.diff(wr)
+    assert np.max(np.abs(rhs)) > 0
+    np.testing.assert_allclose(lhs, rhs, rtol=0, atol=1e-11 * np.max(np.abs(rhs)))
+    # the bunch-ring wake of the main accumulator is the one at ring i0
+    if obs == i0:
+        np.testing.assert_array_equal(w0, o.wake()[0])
+
+
+def test_transverse_wake_vanishes_for_the_tem_field_of_a_smooth_pipe():
+    """E_r - c mu0 H_phi of the bunch's own field cancels along the path: in a
+    coaxial smooth pipe the TEM pulse of the shift test exerts no force."""
+    nr, nz, dr, dz = 12, 40, 1.3 * MM, MM
+    pec = np.zeros((nz, nr), np.uint8)
+    pec[:, :3] = 1
+    eta0 = MU0 * C_LIGHT
+    kk = np.arange(nz + 1)
+    rh = (np.arange(nr + 1) + 0.5) * dr
+    x = (kk - 8.0) / 3.0
+    F = np.where(np.abs(x) < 1.0, (1 - x * x) ** 3, 0.0)
+    x1 = (kk + 1 - 8.0) / 3.0
+    F1 = np.where(np.abs(x1) < 1.0, (1 - x1 * x1) ** 3, 0.0)
+    o = RzOracle(nr, nz, 0, dr, dz, cdt=dz, pec=pec)
+    o.set("er", (dr / rh)[None, :] * F[:, None] * np.ones(o.shape))
+    o.set("hphi", -F1[:, None] / eta0 * np.ones(o.shape))
+    er = o.get("er")
+    for _ in range(20):
+        er_n = o.get("er")
+        o.step(1)
+        hp = o.get("hphi")
+        force = er_n / dr + eta0 * hp / rh[None, :]
+        assert np.max(np.abs(force)) <= 1e-12 * np.max(np.abs(er / dr))
