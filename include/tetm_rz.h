@@ -102,6 +102,22 @@ int tetm_rz_sync(tetm_rz* s);
 int tetm_rz_wake(tetm_rz* s, int32_t mode, double* out, int32_t cap, int32_t* n_out,
                  double* s0, double* ds);
 
+/* Radius of the transverse wake: r_{obs+1/2} = (obs + 1/2) dr, 0 <= obs <
+ * nr - 1 (default: the bunch ring i0, or nr - 2 if i0 = nr - 1). After
+ * tetm_rz_set_bunch, before the first step (TETM_E_STATE otherwise). */
+int tetm_rz_set_observer(tetm_rz* s, int32_t obs);
+
+/* Radial transverse wake of mode m_lo + mode at r_{obs+1/2}, phi = 0 [V/C]
+ * (Sec. 5, the dipole wake for m = 1): W_r(s) = (1/q) * sum over the passage
+ * of (E_r - c mu0 H_phi) dz along the path s behind the bunch centre, with
+ * E_r from e_r at time n and H_phi from h_phi at time n+1/2 (the same path
+ * point at c*dt = dz), float64, same samples as tetm_rz_wake. The scheme
+ * satisfies the discrete Panofsky-Wenzel relation
+ * W_r(m+1) - W_r(m) = dz/dr * mean over m, m+1 of (W_{obs+1} - W_obs)
+ * with the longitudinal wakes at rings obs, obs+1. Synchronizes. */
+int tetm_rz_transverse_wake(tetm_rz* s, int32_t mode, double* out, int32_t cap, int32_t* n_out,
+                            double* s0, double* ds);
+
 /* Discrete energy per radian of mode m_lo + mode, 0.5 <Q^{e,r} y, y>
  * (Sec. 4.4), reduced in float64 on the device. Synchronizes. */
 int tetm_rz_energy(tetm_rz* s, int32_t mode, double* w);

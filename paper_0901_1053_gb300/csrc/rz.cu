@@ -111,6 +111,10 @@ struct RzArgs {
   double* W;              // [mode][nw]
   double inv_q;
   int* err;               // set to 1 when a bounded wait gives up
+  // transverse wake at r_{obs+1/2}: WT[mode][w] += tw_er e_r^n + tw_hp h_phi^{n+1/2}
+  int obs;
+  double tw_er, tw_hp;
+  double* WT;
 };
 
 template <typename T>
@@ -172,12 +176,15 @@ struct LaneState {
 
 // Both stages of plane k for the lane's two entries (ten updates of (24)).
 // d0: plane k, d1: plane k+1 (only its e_r, e_phi are used). out receives the
-// new values in the interleaved order. cur0/cur1: bunch current to subtract
-// at the two e_z entries (zero elsewhere).
+// new values in the interleaved order, er_old the e_r of plane k before the
+// step. j0/j1: bunch current to subtract at the two e_z entries (zero
+// elsewhere).
 template <typename T>
 __device__ __forceinline__ void rz_plane(const Pair6<T>& d0, const Pair6<T>& d1, const LaneCo<T>& c,
-                                         T mm, LaneState<T>& s, T j0, T j1, T* out) {
+                                         T mm, LaneState<T>& s, T j0, T j1, T* out, T* er_old) {
   const unsigned m = d0.m;
+  er_old[0] = s.er0[0];
+  er_old[1] = s.er0[1];
   T CER[2], CEP[2], CHR[2], CHP[2], FEZ[2], FHZ[2];
   if (__all_sync(0xffffffffu, m == 0x3F3Fu)) {
 #pragma unroll
@@ -318,17 +325,23 @@ __device__ __forceinline__ T current_at(const RzArgs<T>& a, const Item<T>& it, b
   const long long dd = (long long)k - a.n + a.c0;
   return (dd >= -a.c0 && dd < a.c0) ? a.J[(long long)it.mode * 2 * a.c0 + dd + a.c0] : T(0);
 }
+// Wake samples of plane k (Sec. 5): the path s = m dz meets e_z(k+1/2) and
+// h_phi(k+1/2) at time n+1/2 and e_r(k) at time n, n = k + m + c0. The
+// longitudinal wake takes e_z at the bunch ring; the radial transverse wake
+// (E_r - c mu0 H_phi) at r_{obs+1/2}, where per radian h_phi = -r H_phi.
 template <typename T>
 __device__ __forceinline__ void gather_wake(const RzArgs<T>& a, const Item<T>& it, int k,
-                                            const T* out) {
-  if (!it.own) return;
+                                            const T* out, const T* er_old) {
+  if (!it.own || !a.b_on) return;
+  const long long w = a.n - k - a.c0 - a.m_min;
+  if (w < 0 || w >= a.nw) return;
   const bool s[2] = {it.src0, it.src1};
 #pragma unroll
-  for (int e = 0; e < 2; ++e)
-    if (s[e]) {
-      const long long w = a.n - k - a.c0 - a.m_min;
-      if (w >= 0 && w < a.nw) a.W[(long long)it.mode * a.nw + w] -= (double)out[6 * e + kEZ] * a.inv_q;
-    }
+  for (int e = 0; e < 2; ++e) {
+    if (s[e]) a.W[(long long)it.mode * a.nw + w] -= (double)out[6 * e + kEZ] * a.inv_q;
+    if (it.gi + e == a.obs)
+      a.WT[(long long)it.mode * a.nw + w] += a.tw_er * (double)er_old[e] + a.tw_hp * (double)out[6 * e + kHP];
+  }
 }
 
 // --- register-ring variant ---------------------------------------------------
@@ -367,12 +380,12 @@ __device__ __forceinline__ void rz_item_reg(const RzArgs<T>& a, int witem) {
     for (int u = 0; u < R; ++u) {
       const int k = kb + u;
       if (k >= it.k1) break;
-      T out[12];
+      T out[12], er_old[2];
       rz_plane(ring[u], ring[(u + 1) % R], c, mm, s, current_at(a, it, it.src0, k),
-               current_at(a, it, it.src1, k), out);
+               current_at(a, it, it.src1, k), out, er_old);
       if (it.own && k >= it.k0) {
         st_pair(op + (long long)(k + 1) * RS, out);
-        gather_wake(a, it, k, out);
+        gather_wake(a, it, k, out, er_old);
       }
       load(k + R, ring[u]);
     }
@@ -469,11 +482,12 @@ __device__ __forceinline__ void rz_item_async(const RzArgs<T>& a, int witem, uns
     cp_async_wait<kADepth - 2>();
     __syncwarp();
     fetch(k + 1, d1);
-    T out[12];
-    rz_plane(d0, d1, c, mm, s, current_at(a, it, it.src0, k), current_at(a, it, it.src1, k), out);
+    T out[12], er_old[2];
+    rz_plane(d0, d1, c, mm, s, current_at(a, it, it.src0, k), current_at(a, it, it.src1, k), out,
+             er_old);
     if (it.own && k >= it.k0) {
       st_pair(op + (long long)(k + 1) * RS, out);
-      gather_wake(a, it, k, out);
+      gather_wake(a, it, k, out, er_old);
     }
     d0 = d1;
   }
@@ -612,11 +626,12 @@ __device__ __forceinline__ bool rz_item_bulk(const RzArgs<T>& a, int witem, unsi
     issue(k + D - 1);
     fetch(k + 1, d1);
     if (!__all_sync(0xffffffffu, ok)) break;
-    T out[12];
-    rz_plane(d0, d1, c, mm, s, current_at(a, it, it.src0, k), current_at(a, it, it.src1, k), out);
+    T out[12], er_old[2];
+    rz_plane(d0, d1, c, mm, s, current_at(a, it, it.src0, k), current_at(a, it, it.src1, k), out,
+             er_old);
     if (it.own && k >= it.k0) {
       st_pair(op + (long long)(k + 1) * RS, out);
-      gather_wake(a, it, k, out);
+      gather_wake(a, it, k, out, er_old);
     }
     d0 = d1;
   }
@@ -834,6 +849,8 @@ struct tetm_rz {
   int resident = 0;
   int kernel = TETM_RZ_KERNEL_ASYNC;
   int* err = nullptr;            // device error word of the bulk-copy kernel
+  int obs = 0;                   // transverse wake at r_{obs+1/2}
+  double* WT = nullptr;          // [mode][nw]
 };
 
 namespace {
@@ -859,6 +876,15 @@ int rz_launch_steps(tetm_rz* s, long long n) {
   a.W = s->W;
   a.inv_q = s->bunch ? 1.0 / s->q : 0.0;
   a.err = s->err;
+  a.obs = s->obs;
+  a.WT = s->WT;
+  if (s->bunch) {
+    const double rh = (s->obs + 0.5) * s->g.dr;
+    a.tw_er = s->g.dz / (s->q * s->g.dr);
+    a.tw_hp = kMu0 * kC * s->g.dz / (s->q * rh);
+  } else {
+    a.tw_er = a.tw_hp = 0.0;
+  }
   const int items = s->n_work * s->n_modes;
   const int blocks = std::max(1, std::min(s->resident, (items + 3) / 4));
   for (long long t = 0; t < n; ++t) {
@@ -1107,9 +1133,11 @@ int tetm_rz_set_bunch(tetm_rz* s, double sigma, double q, int32_t i0) {
     }
   }
   void* J = nullptr;
-  double* W = nullptr;
+  double *W = nullptr, *WT = nullptr;
   cudaError_t e = cudaMalloc(&J, (size_t)s->esz * nj);
   if (e == cudaSuccess) e = cudaMalloc(&W, sizeof(double) * (size_t)s->n_modes * nw);
+  if (e == cudaSuccess) e = cudaMalloc(&WT, sizeof(double) * (size_t)s->n_modes * nw);
+  if (e == cudaSuccess) e = cudaMemset(WT, 0, sizeof(double) * (size_t)s->n_modes * nw);
   if (e == cudaSuccess)
     e = cudaMemcpy(J, s->esz == 8 ? (const void*)jd.data() : (const void*)jf.data(),
                    (size_t)s->esz * nj, cudaMemcpyHostToDevice);
@@ -1117,10 +1145,13 @@ int tetm_rz_set_bunch(tetm_rz* s, double sigma, double q, int32_t i0) {
   if (e != cudaSuccess) {
     cudaFree(J);
     cudaFree(W);
+    cudaFree(WT);
     return rz_fail(e);
   }
   s->J = J;
   s->W = W;
+  s->WT = WT;
+  s->obs = i0 < s->g.nr - 1 ? i0 : s->g.nr - 2;
   s->bunch = true;
   s->i0 = i0;
   s->c0 = c0;
@@ -1129,7 +1160,7 @@ int tetm_rz_set_bunch(tetm_rz* s, double sigma, double q, int32_t i0) {
   s->nw = nw;
   s->q = q;
   s->sigma = sigma;
-  s->device_bytes += (long long)((size_t)s->esz * nj + sizeof(double) * (size_t)s->n_modes * nw);
+  s->device_bytes += (long long)((size_t)s->esz * nj + 2 * sizeof(double) * (size_t)s->n_modes * nw);
   return TETM_OK;
 }
 
@@ -1161,6 +1192,28 @@ int tetm_rz_wake(tetm_rz* s, int32_t mode, double* out, int32_t cap, int32_t* n_
   if (!out) return TETM_OK;
   if (cap < s->nw) return TETM_E_ARG;
   cudaError_t e = cudaMemcpyAsync(out, s->W + (size_t)mode * s->nw, sizeof(double) * s->nw,
+                                  cudaMemcpyDeviceToHost, s->st);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(s->st);
+  return e == cudaSuccess ? TETM_OK : rz_fail(e);
+}
+
+int tetm_rz_set_observer(tetm_rz* s, int32_t obs) {
+  if (!s || obs < 0 || obs >= s->g.nr - 1) return TETM_E_ARG;
+  if (!s->bunch || s->step != 0) return TETM_E_STATE;
+  s->obs = obs;
+  return TETM_OK;
+}
+
+int tetm_rz_transverse_wake(tetm_rz* s, int32_t mode, double* out, int32_t cap, int32_t* n_out,
+                            double* s0, double* ds) {
+  if (!rz_mode_ok(s, mode)) return TETM_E_ARG;
+  if (!s->bunch) return TETM_E_STATE;
+  if (n_out) *n_out = s->nw;
+  if (s0) *s0 = s->m_min * s->g.dz;
+  if (ds) *ds = s->g.dz;
+  if (!out) return TETM_OK;
+  if (cap < s->nw) return TETM_E_ARG;
+  cudaError_t e = cudaMemcpyAsync(out, s->WT + (size_t)mode * s->nw, sizeof(double) * s->nw,
                                   cudaMemcpyDeviceToHost, s->st);
   if (e == cudaSuccess) e = cudaStreamSynchronize(s->st);
   return e == cudaSuccess ? TETM_OK : rz_fail(e);
@@ -1273,6 +1326,7 @@ int tetm_rz_destroy(tetm_rz* s) {
   cudaFree(s->flags);
   cudaFree(s->J);
   cudaFree(s->W);
+  cudaFree(s->WT);
   cudaFree(s->partial);
   cudaFree(s->err);
   if (s->own) cudaStreamDestroy(s->own);

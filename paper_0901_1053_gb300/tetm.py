@@ -45,7 +45,7 @@ EXPORTS = ("tetm_create", "tetm_set_bunch", "tetm_step", "tetm_sync", "tetm_wake
            "tetm_rz_create", "tetm_rz_set_bunch", "tetm_rz_step", "tetm_rz_sync", "tetm_rz_wake",
            "tetm_rz_energy", "tetm_rz_get_fields", "tetm_rz_set_fields", "tetm_rz_set_tiling",
            "tetm_rz_set_stream", "tetm_rz_get_info", "tetm_rz_bytes_needed", "tetm_rz_destroy",
-           "tetm_rz_set_kernel")
+           "tetm_rz_set_kernel", "tetm_rz_set_observer", "tetm_rz_transverse_wake")
 TETM_RZ_KERNEL_ASYNC = 0
 TETM_RZ_KERNEL_REGISTER = 1
 TETM_RZ_KERNEL_BULK = 2
@@ -134,6 +134,9 @@ def _load():
         "tetm_rz_set_tiling": (ctypes.c_int, [vp, i32]),
         "tetm_rz_set_stream": (ctypes.c_int, [vp, vp]),
         "tetm_rz_set_kernel": (ctypes.c_int, [vp, i32]),
+        "tetm_rz_set_observer": (ctypes.c_int, [vp, i32]),
+        "tetm_rz_transverse_wake": (ctypes.c_int, [vp, i32, vp, i32, ctypes.POINTER(i32),
+                                                   ctypes.POINTER(dbl), ctypes.POINTER(dbl)]),
         "tetm_rz_get_info": (ctypes.c_int, [vp, ctypes.POINTER(tetm_rz_info)]),
         "tetm_rz_bytes_needed": (ctypes.c_int64, [ctypes.POINTER(tetm_rz_grid)]),
         "tetm_rz_destroy": (ctypes.c_int, [vp]),
@@ -449,6 +452,19 @@ class RzSolver:
         out = np.empty(n.value, dtype=np.float64)
         _check(lib.tetm_rz_wake(self.h, mi, _ptr(out), n.value, None, None, None), "tetm_rz_wake")
         return out, s0.value, ds.value
+
+    def set_observer(self, obs):
+        _check(lib.tetm_rz_set_observer(self.h, int(obs)), "tetm_rz_set_observer")
+
+    def transverse_wake(self, m):
+        n = ctypes.c_int32()
+        mi = self._mode(m)
+        _check(lib.tetm_rz_transverse_wake(self.h, mi, None, 0, ctypes.byref(n), None, None),
+               "tetm_rz_transverse_wake")
+        out = np.empty(n.value, dtype=np.float64)
+        _check(lib.tetm_rz_transverse_wake(self.h, mi, _ptr(out), n.value, None, None, None),
+               "tetm_rz_transverse_wake")
+        return out
 
     def energy(self, m):
         w = ctypes.c_double()

@@ -197,6 +197,8 @@ def test_fp32_wakes_against_oracle(tetm):
     for m in range(5):
         o = oracle_mode(w, m)
         assert rel(s.wake(m)[0], o.wake()[0]) <= (TOL32_WAKE if m <= 2 else 1e-3), m
+        # the transverse wake at the ring meets 1e-4 for every mode
+        assert rel(s.transverse_wake(m), o.transverse_wake()) <= TOL32_WAKE, m
 
 
 # ---------------------------------------------------------------------------
@@ -250,3 +252,46 @@ def test_state_and_argument_errors(tetm):
     with pytest.raises(tetm.TetmError) as e:
         s2.set_bunch(2e-3, 1e-9, 0)
     assert e.value.code == tetm.TETM_E_NOT_MAGIC
+
+
+# ---------------------------------------------------------------------------
+# Transverse (dipole) wake at r_{obs+1/2}
+# ---------------------------------------------------------------------------
+
+@pytest.mark.parametrize("kernel", KERNELS)
+@pytest.mark.parametrize("obs", [None, 9])
+def test_transverse_wake_matches_oracle(tetm, kernel, obs):
+    w = small_chain(40, 130, 0, 2, i0=4, steps=None)
+    s = gpu_solver(tetm, w, 24, kernel)
+    s.set_bunch(w.sigma, w.charge, w.i0)
+    if obs is not None:
+        s.set_observer(obs)
+    s.step(w.steps)
+    for m in range(3):
+        o = RzOracle(w.nr, w.nz, m, w.dr, w.dz, w.cdt, pec=w.pec)
+        o.set_bunch(w.sigma, w.charge, w.i0)
+        if obs is not None:
+            o.set_observer(obs)
+        o.step(w.steps)
+        wt = o.transverse_wake()
+        if m == 0 and np.max(np.abs(wt)) == 0:
+            continue
+        assert rel(s.transverse_wake(m), wt) <= TOL64, m
+        assert rel(s.wake(m)[0], o.wake()[0]) <= TOL64, m
+
+
+def test_observer_state_errors(tetm):
+    w = small_chain(20, 40, 0, 1, i0=3, steps=0)
+    s = gpu_solver(tetm, w)
+    with pytest.raises(tetm.TetmError) as e:
+        s.set_observer(3)                          # no bunch yet
+    assert e.value.code == tetm.TETM_E_STATE
+    s.set_bunch(w.sigma, w.charge, w.i0)
+    with pytest.raises(tetm.TetmError) as e:
+        s.set_observer(19)                         # r_{obs+1/2} must lie inside the wall
+    assert e.value.code == tetm.TETM_E_ARG
+    s.set_observer(5)
+    s.step(1)
+    with pytest.raises(tetm.TetmError) as e:
+        s.set_observer(6)
+    assert e.value.code == tetm.TETM_E_STATE
