@@ -198,16 +198,16 @@ def measured_peak_hbm():
     return 6800.0, "fallback"
 
 
-def kernel_source_hash():
-    """Hash of the step-kernel sources (both tilings' translation units)."""
+def kernel_source_hash(names=("kernels_step.cu", "kernels_warp.cu")):
+    """Hash of the step-kernel sources (the translation units of the kernel)."""
     h = hashlib.sha256()
-    for name in ("kernels_step.cu", "kernels_warp.cu"):
+    for name in names:
         with open(os.path.join(ROOT, "paper_0901_1053_gb300", "csrc", name), "rb") as f:
             h.update(f.read())
     return h.hexdigest()[:16]
 
 
-def profiled_traffic(name):
+def profiled_traffic(name, sources=("kernels_step.cu", "kernels_warp.cu")):
     """DRAM bytes per launch from the committed ncu summary for this kernel
     and workload; None if absent or taken on a different kernel source."""
     path = os.path.join(ROOT, "profiles", name)
@@ -216,7 +216,7 @@ def profiled_traffic(name):
     txt = open(path).read()
     m = re.search(r"traffic_bytes_per_launch:\s*([0-9.eE+]+)", txt)
     h = re.search(r"kernel_source_sha256_16:\s*([0-9a-f]+)", txt)
-    if not m or not h or h.group(1) != kernel_source_hash():
+    if not m or not h or h.group(1) != kernel_source_hash(sources):
         return None
     return float(m.group(1))
 
@@ -604,7 +604,7 @@ def run_rz_mode(args):
         peak, peak_kind = FP64_PEAK_TFLOPS, "nominal fp64 rate of the part"
         roof = {"bound": "alu", "unit": "TFLOP/s", "flops_per_cell": RZ_FLOPS_PER_CELL,
                 "hbm_gbs": bytes_per_cell * proc / (kern_ms * 1e-3) / 1e9}
-    traffic = profiled_traffic("%s_%s_%s.md" % (kname, w.precision, w.name))
+    traffic = profiled_traffic("%s_%s_%s.md" % (kname, w.precision, w.name), ("rz.cu",))
     s.close()
 
     e2e = None
