@@ -250,6 +250,8 @@ def _load_rz():
     lib.rz_oracle_step_custom.argtypes = [vp, vp]
     lib.rz_oracle_wake.restype = i
     lib.rz_oracle_wake.argtypes = [vp, vp, i, ctypes.POINTER(i), dp, dp]
+    lib.rz_oracle_set_bunch_static.restype = i
+    lib.rz_oracle_set_bunch_static.argtypes = [vp, d, d, i, i]
     lib.rz_oracle_set_observer.restype = i
     lib.rz_oracle_set_observer.argtypes = [vp, i]
     lib.rz_oracle_wake_extra.restype = i
@@ -328,6 +330,13 @@ class RzOracle:
     def set_bunch(self, sigma, charge, i0=0):
         if self.lib.rz_oracle_set_bunch(self.h, float(sigma), float(charge), int(i0)) != 0:
             raise ValueError("rz_oracle_set_bunch: bad argument")
+
+    def set_bunch_static(self, sigma, charge, i0, k_head):
+        """Bunch with its head at plane k_head at step 0 carrying its discrete
+        TEM field (static start in a uniform vacuum entry section)."""
+        if self.lib.rz_oracle_set_bunch_static(self.h, float(sigma), float(charge), int(i0),
+                                               int(k_head)) != 0:
+            raise ValueError("rz_oracle_set_bunch_static: bad argument or non-uniform entry section")
 
     def current(self, n):
         out = np.zeros(self.shape, dtype=np.float64)

@@ -50,6 +50,8 @@ typedef struct rz_oracle {
   /* transverse wake at r_{obs+1/2} and longitudinal wakes at rings obs, obs+1 */
   int obs;
   double *twake, *wake_o0, *wake_o1;
+  long kshift;   /* bunch head at plane step + kshift (0: cold start at the wall) */
+  int vacuum;    /* no material arrays were given */
   long step;
 } rz_oracle_t;
 
@@ -98,6 +100,7 @@ rz_oracle_t *rz_oracle_new(int nr, int nz, int m, double dr, double dz, double c
   o->n = (long)(nr + 1) * (nz + 1);
   o->dr = dr; o->dz = dz;
   o->dt = (cdt > 0 ? cdt : (dr < dz ? dr : dz)) / RZ_C0;
+  o->vacuum = (eps_r == NULL && mu_r == NULL);
   o->at = 0.5 * o->dt;
   for (int q = 0; q < 6; ++q) {
     o->f[q] = (double *)calloc((size_t)o->n, sizeof(double));
@@ -193,7 +196,7 @@ void rz_oracle_current(const rz_oracle_t *o, long n, double *jz) {
   memset(jz, 0, sizeof(double) * (size_t)o->n);
   if (!o->has_bunch) return;
   for (long k = 0; k < o->nz; ++k) {
-    const long d = k - n + o->c0;
+    const long d = k - (n + o->kshift) + o->c0;
     if (d < -o->c0 || d >= o->c0) continue;
     jz[o->i0 + o->mr * k] = o->weight * RZ_C0 * o->qcell[d + o->c0] / o->dz;
   }
@@ -237,7 +240,7 @@ static void rz_wake_gather(rz_oracle_t *o, long n, const double *er_n) {
   const double eta0 = RZ_MU0 * RZ_C0;
   const double rh = (o->obs + 0.5) * o->dr;
   for (int mm = o->m_min; mm <= o->m_max; ++mm) {
-    const long k = n - mm - o->c0;
+    const long k = (n + o->kshift) - mm - o->c0;
     if (k < 0 || k >= o->nz) continue;
     const int w = mm - o->m_min;
     o->wake[w] -= o->f[EZ][o->i0 + o->mr * k] / o->q;
@@ -335,4 +338,88 @@ long rz_oracle_step_count(const rz_oracle_t *o) { return o->step; }
  * step does not depend on the azimuthal mode number. */
 int rz_oracle_stable(double dr, double dz, double cdt) {
   return cdt > 0 && cdt <= dz * (1.0 + 1e-12) && cdt <= dr * (1.0 + 1e-12);
+}
+
+
+/* Static start (the paper's structures sit between infinite ingoing and
+ * outgoing pipes, Sec. 5): the bunch begins with its head at plane K inside a
+ * uniform vacuum entry section carrying its discrete TEM field, which at
+ * c*dt = dz moves one cell per step with the bunch (Sec. 4.5). It is the TEM
+ * field of the Cartesian case with x -> phi, y -> r and P_x -> m:
+ *   psi solves (P_r^T diag(r_{i+1/2}/dr) P_r + m^2 diag(dr/r_i)) psi = delta(i0)
+ *   on the nodes whose e_z is not PEC (psi = 0 elsewhere),
+ *   e_r = -P_r psi G(u), e_phi = -m psi G(u)                     (time n)
+ *   h_phi = (r_{i+1/2}/(dr eta0)) P_r psi G(u+1),
+ *   h_r = -(dr/(r_i eta0)) m psi G(u+1)                          (n - 1/2)
+ * with u = k - n and G(u) + G(u+1) = 2 eta0 jj(u), jj the mode's line current,
+ * G = 0 ahead of the head. */
+int rz_oracle_set_bunch_static(rz_oracle_t *o, double sigma, double q, int i0, int k_head) {
+  if (!o->vacuum || o->step != 0 || o->has_bunch) return -1;
+  if (rz_oracle_set_bunch(o, sigma, q, i0) != 0) return -1;
+  const int c0 = o->c0, K = k_head;
+  const long mr = o->mr;
+  if (K < 2 * c0 + 2 || K > o->nz) { o->has_bunch = 0; return -1; }
+  for (int c = 0; c < 6; ++c)
+    for (long k = 2; k <= K; ++k)
+      for (long i = 0; i <= o->nr; ++i)
+        if (o->c[c][i + mr * k] != o->c[c][i + mr]) { o->has_bunch = 0; return -1; }
+  const int nn = o->nr + 1;
+  const double dr = o->dr, m = (double)o->m;
+  /* dense normal equations on the unknown nodes (a tridiagonal matrix,
+   * solved by Gaussian elimination without pivoting: it is diagonally
+   * dominant and symmetric positive definite) */
+  int *unk = (int *)malloc(sizeof(int) * (size_t)nn);
+  for (int i = 0; i < nn; ++i) unk[i] = o->c[EZ][i + mr] != 0.0;
+  if (!unk[i0]) { free(unk); o->has_bunch = 0; return -1; }
+  double *a = (double *)calloc((size_t)nn, sizeof(double));  /* sub-diagonal */
+  double *b = (double *)calloc((size_t)nn, sizeof(double));  /* diagonal */
+  double *cc = (double *)calloc((size_t)nn, sizeof(double)); /* super-diagonal */
+  double *rhs = (double *)calloc((size_t)nn, sizeof(double));
+  for (int i = 0; i < nn; ++i) {
+    if (!unk[i]) { b[i] = 1.0; continue; }        /* psi = 0 */
+    if (i + 1 < nn && o->c[ER][i + mr] != 0.0) {  /* e_r edge (i+1/2) */
+      const double w = (i + 0.5) * dr / dr;
+      b[i] += w;
+      if (unk[i + 1]) cc[i] = -w;
+    }
+    if (i >= 1 && o->c[ER][i - 1 + mr] != 0.0) {  /* e_r edge (i-1/2) */
+      const double w = (i - 0.5) * dr / dr;
+      b[i] += w;
+      if (unk[i - 1]) a[i] = -w;
+    }
+    if (i >= 1) b[i] += m * m * dr / (i * dr);
+  }
+  rhs[i0] = 1.0;
+  for (int i = 1; i < nn; ++i) {                   /* forward elimination */
+    const double f = a[i] / b[i - 1];
+    b[i] -= f * cc[i - 1];
+    rhs[i] -= f * rhs[i - 1];
+  }
+  double *psi = (double *)calloc((size_t)nn, sizeof(double));
+  psi[nn - 1] = rhs[nn - 1] / b[nn - 1];
+  for (int i = nn - 2; i >= 0; --i) psi[i] = (rhs[i] - cc[i] * psi[i + 1]) / b[i];
+  for (int i = 0; i < nn; ++i) if (!unk[i]) psi[i] = 0.0;
+  const double eta0 = RZ_MU0 * RZ_C0;
+  double *G = (double *)calloc((size_t)(K + 3), sizeof(double));   /* G[u + 1] */
+  for (long u = K - 1; u >= K - 2 * c0; --u) {
+    const double jj = o->weight * RZ_C0 * o->qcell[u - K + 2 * c0] / o->dz;
+    G[u + 1] = 2.0 * eta0 * jj - G[u + 2];
+  }
+  for (long k = 0; k <= o->nz; ++k)
+    for (long i = 0; i <= o->nr; ++i) {
+      const long n = i + mr * k;
+      const double g0 = (k <= K) ? G[k + 1] : 0.0;
+      const double g1 = (k + 1 <= K) ? G[k + 2] : 0.0;
+      const double prp = (i < o->nr) ? psi[i + 1] - psi[i] : 0.0;
+      const double rh = (i + 0.5) * dr, ri = i * dr;
+      o->f[ER][n] = o->c[ER][n] != 0.0 ? -prp * g0 : 0.0;
+      o->f[EPHI][n] = o->c[EPHI][n] != 0.0 ? -m * psi[i] * g0 : 0.0;
+      o->f[EZ][n] = 0.0;
+      o->f[HPHI][n] = o->c[HPHI][n] != 0.0 ? (rh / (dr * eta0)) * prp * g1 : 0.0;
+      o->f[HR][n] = (o->c[HR][n] != 0.0 && i > 0) ? -(dr / (ri * eta0)) * m * psi[i] * g1 : 0.0;
+      o->f[HZ][n] = 0.0;
+    }
+  o->kshift = K;
+  free(unk); free(a); free(b); free(cc); free(rhs); free(psi); free(G);
+  return 0;
 }

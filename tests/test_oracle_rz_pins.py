@@ -494,3 +494,60 @@ def test_transverse_wake_vanishes_for_the_tem_field_of_a_smooth_pipe():
         hp = o.get("hphi")
         force = er_n / dr + eta0 * hp / rh[None, :]
         assert np.max(np.abs(force)) <= 1e-12 * np.max(np.abs(er / dr))
+
+
+# ---------------------------------------------------------------------------
+# Static start (infinite ingoing pipe, Sec. 5): the discrete TEM field of the
+# ring bunch, mode by mode, moves one cell per step (Sec. 4.5)
+# ---------------------------------------------------------------------------
+
+@pytest.mark.parametrize("m,i0", [(0, 0), (0, 3), (1, 3), (2, 4), (4, 2)])
+def test_static_start_moves_rigidly_and_leaves_no_wake(m, i0):
+    nr, nz, K = 16, 90, 34
+    pec = _cavity_pec(nr, nz, 10, nz, nz)          # smooth pipe of radius 10 cells
+    o = RzOracle(nr, nz, m, MM, MM, pec=pec)
+    o.set_bunch_static(3 * MM, 1e-9, i0, K)
+    f0 = o.fields()
+    assert not f0["ez"].any() and not f0["hz"].any()
+    n = 40
+    o.step(n)
+    escale = max(np.max(np.abs(f0["er"])), np.max(np.abs(f0["ephi"])))
+    hscale = max(np.max(np.abs(f0["hphi"])), np.max(np.abs(f0["hr"])))
+    for c in NAMES:
+        shifted = np.zeros_like(f0[c])
+        shifted[n:] = f0[c][:-n]
+        assert np.max(np.abs(o.get(c) - shifted)) <= 1e-13 * (escale if c[0] == "e" else hscale), c
+    cold = RzOracle(nr, nz, m, MM, MM, pec=pec)
+    cold.set_bunch(3 * MM, 1e-9, i0)
+    cold.step(n + K)
+    assert np.max(np.abs(o.wake()[0])) <= 1e-13 * np.max(np.abs(cold.wake()[0]))
+    assert np.max(np.abs(o.transverse_wake())) <= 1e-13 * np.max(np.abs(cold.transverse_wake()))
+
+
+def test_static_start_energy_identity_in_a_cavity():
+    nr, nz, K = 14, 70, 24
+    pec = _cavity_pec(nr, nz, 6, 32, 46)
+    sigma, q, m, i0 = 2 * MM, 1e-9, 1, 3
+    o = RzOracle(nr, nz, m, MM, MM, pec=pec)
+    o.set_bunch_static(sigma, q, i0, K)
+    w0 = o.energy()
+    c0 = math.ceil(5 * sigma / MM - 1e-12)
+    o.step(nz - (K - 2 * c0) + 1)
+    wk = o.wake()[0]
+    edges = np.arange(-c0, c0 + 1) * MM
+    qcell = q * np.diff(0.5 * (1 + sp.erf(np.clip(edges, -5 * sigma, 5 * sigma) / (sigma * math.sqrt(2)))))
+    m_min = -c0 - 1
+    rhs = sum(0.5 * q * qcell[d + c0] * (wk[-d - m_min] + wk[-d - 1 - m_min]) for d in range(-c0, c0))
+    assert o.energy() - w0 == pytest.approx(rhs / math.pi, rel=1e-10, abs=1e-12 * w0)
+    assert abs(rhs) > 1e-6 * w0
+
+
+def test_static_start_rejections():
+    nr, nz = 12, 60
+    pec = _cavity_pec(nr, nz, 6, 20, 40)
+    with pytest.raises(ValueError):
+        RzOracle(nr, nz, 1, MM, MM, pec=pec).set_bunch_static(2 * MM, 1e-9, 3, 30)  # K past k = 20
+    with pytest.raises(ValueError):
+        RzOracle(nr, nz, 1, MM, MM, pec=pec).set_bunch_static(2 * MM, 1e-9, 3, 10)  # K < 2 c0 + 2
+    with pytest.raises(ValueError):
+        RzOracle(nr, nz, 1, MM, MM, eps_r=np.ones((nz, nr)), pec=pec).set_bunch_static(MM, 1e-9, 3, 14)
