@@ -87,6 +87,20 @@ int tetm_rz_create(const tetm_rz_grid* g, const double* eps_r, const double* mu_
  * is s = m*dz, m = -c0-1 .. ceil(15 sigma/dz), c0 = ceil(5 sigma/dz). */
 int tetm_rz_set_bunch(tetm_rz* s, double sigma, double q, int32_t i0);
 
+/* Static start (Sec. 5: the paper's structures sit between infinite
+ * ingoing and outgoing pipes): the bunch of tetm_rz_set_bunch (same sigma,
+ * q, i0, profile and wake window) begins with its head at plane k_head,
+ * carrying the discrete TEM field of every mode, so it crosses the uniform
+ * entry section without radiating (the field moves one cell per step at
+ * c*dt = dz, Sec. 4.5). Per mode m the radial potential solves
+ * (P_r^T diag(r_{i+1/2}/dr) P_r + m^2 diag(dr/r_i)) psi = delta(i0) on the
+ * nodes whose e_z is not PEC. Current and wakes then refer to step + k_head.
+ * Requires step 0 and no bunch (TETM_E_STATE), c*dt == dz
+ * (TETM_E_NOT_MAGIC), 2*c0 + 2 <= k_head <= nz, planes 1..k_head carrying
+ * the same objects, i0 as for tetm_rz_set_bunch (TETM_E_ARG). Writes planes
+ * 0..k_head+1 of every mode. Synchronizes. */
+int tetm_rz_set_bunch_static(tetm_rz* s, double sigma, double q, int32_t i0, int32_t k_head);
+
 /* Queues n steps of Eq. (24) for every mode (n >= 0). */
 int tetm_rz_step(tetm_rz* s, int64_t n);
 

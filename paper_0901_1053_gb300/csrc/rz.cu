@@ -107,6 +107,7 @@ struct RzArgs {
   int n_work;
   int b_on, i0, c0, m_min, nw;
   long long n;            // step being taken (n -> n+1)
+  long long kshift;       // static start: the bunch head is at plane n + kshift
   const T* J;             // [mode][2 c0]: share * c * Q_cell / dz
   double* W;              // [mode][nw]
   double inv_q;
@@ -322,7 +323,7 @@ __device__ __forceinline__ LaneCo<T> lane_coefs(const RzArgs<T>& a, const Item<T
 template <typename T>
 __device__ __forceinline__ T current_at(const RzArgs<T>& a, const Item<T>& it, bool src, int k) {
   if (!src || k < 0) return T(0);
-  const long long dd = (long long)k - a.n + a.c0;
+  const long long dd = (long long)k - (a.n + a.kshift) + a.c0;
   return (dd >= -a.c0 && dd < a.c0) ? a.J[(long long)it.mode * 2 * a.c0 + dd + a.c0] : T(0);
 }
 // Wake samples of plane k (Sec. 5): the path s = m dz meets e_z(k+1/2) and
@@ -333,7 +334,7 @@ template <typename T>
 __device__ __forceinline__ void gather_wake(const RzArgs<T>& a, const Item<T>& it, int k,
                                             const T* out, const T* er_old) {
   if (!it.own || !a.b_on) return;
-  const long long w = a.n - k - a.c0 - a.m_min;
+  const long long w = (a.n + a.kshift) - k - a.c0 - a.m_min;
   if (w < 0 || w >= a.nw) return;
   const bool s[2] = {it.src0, it.src1};
 #pragma unroll
@@ -800,6 +801,51 @@ __global__ void rz_energy_final(const double* partial, int n, double* out) {
   if (threadIdx.x == 0) *out = v;
 }
 
+// Static start: number of activity bytes of rows 2..K that differ from row 1
+__global__ void rz_row_mismatch(const uint8_t* mask, RzLayout L, int K, unsigned long long* out) {
+  const long long total = (long long)(K - 1) * L.pr;
+  unsigned long long c = 0;
+  for (long long q = (long long)blockIdx.x * blockDim.x + threadIdx.x; q < total;
+       q += (long long)gridDim.x * blockDim.x) {
+    const long long k = 2 + q / L.pr, col = q % L.pr;
+    c += mask[(k + 1) * L.pr + col] != mask[2 * L.pr + col];
+  }
+  for (int o = 16; o > 0; o >>= 1) c += __shfl_down_sync(0xffffffffu, c, o);
+  if ((threadIdx.x & 31) == 0 && c) atomicAdd(out, c);
+}
+
+// Static start: the TEM field of every mode on planes 0..K+1 (see
+// tetm_rz_set_bunch_static); psi [mode][nr+1], G [mode][K+4] (G[u+1]),
+// metric [mode][6][pr] (column orr = axis).
+template <typename T>
+__global__ void rz_write_tem(T* f, RzLayout L, const uint8_t* mask, const double* metric, int m_lo,
+                             int n_modes, const double* psi, const double* G, int K, double dr,
+                             double eta0) {
+  const long long per_mode = (long long)(L.nr + 1) * (K + 2);
+  const long long total = per_mode * n_modes;
+  for (long long q = (long long)blockIdx.x * blockDim.x + threadIdx.x; q < total;
+       q += (long long)gridDim.x * blockDim.x) {
+    const int mode = (int)(q / per_mode);
+    const long long t = q % per_mode;
+    const int i = (int)(t % (L.nr + 1)), k = (int)(t / (L.nr + 1));
+    const uint8_t b = mask[L.midx(i, k)];
+    const double* me = metric + (long long)mode * 6 * L.pr + L.orr + i;
+    auto act = [&](int c) { return ((b >> c) & 1) && me[c * L.pr] != 0.0; };
+    const double* ps = psi + (long long)mode * (L.nr + 1);
+    const double* g = G + (long long)mode * (K + 4);
+    const double g0 = g[k + 1], g1 = g[k + 2];
+    const double m = (double)(m_lo + mode);
+    const double prp = i < L.nr ? ps[i + 1] - ps[i] : 0.0;
+    T* e = f + L.fidx(mode, 0, i, k);
+    e[kER] = act(kER) ? (T)(-prp * g0) : T(0);
+    e[kEP] = act(kEP) ? (T)(-m * ps[i] * g0) : T(0);
+    e[kEZ] = T(0);
+    e[kHP] = act(kHP) ? (T)(((i + 0.5) * dr / (dr * eta0)) * prp * g1) : T(0);
+    e[kHR] = (act(kHR) && i > 0) ? (T)(-(dr / (i * dr * eta0)) * m * ps[i] * g1) : T(0);
+    e[kHZ] = T(0);
+  }
+}
+
 double rz_phi(double x) { return 0.5 * erfc(-x / sqrt(2.0)); }
 
 int rz_fail(cudaError_t e) {
@@ -850,6 +896,7 @@ struct tetm_rz {
   int kernel = TETM_RZ_KERNEL_ASYNC;
   int* err = nullptr;            // device error word of the bulk-copy kernel
   int obs = 0;                   // transverse wake at r_{obs+1/2}
+  long long kshift = 0;          // static start: head at plane step + kshift
   double* WT = nullptr;          // [mode][nw]
 };
 
@@ -876,6 +923,7 @@ int rz_launch_steps(tetm_rz* s, long long n) {
   a.W = s->W;
   a.inv_q = s->bunch ? 1.0 / s->q : 0.0;
   a.err = s->err;
+  a.kshift = s->kshift;
   a.obs = s->obs;
   a.WT = s->WT;
   if (s->bunch) {
@@ -1195,6 +1243,108 @@ int tetm_rz_wake(tetm_rz* s, int32_t mode, double* out, int32_t cap, int32_t* n_
                                   cudaMemcpyDeviceToHost, s->st);
   if (e == cudaSuccess) e = cudaStreamSynchronize(s->st);
   return e == cudaSuccess ? TETM_OK : rz_fail(e);
+}
+
+int tetm_rz_set_bunch_static(tetm_rz* s, double sigma, double q, int32_t i0, int32_t k_head) {
+  if (!s) return TETM_E_ARG;
+  if (s->step != 0 || s->bunch) return TETM_E_STATE;
+  if (!(sigma > 0) || !isfinite(sigma)) return TETM_E_ARG;
+  const double dz = s->g.dz, dr = s->g.dr;
+  const int c0 = (int)ceil(5.0 * sigma / dz - 1e-12);
+  const int K = k_head;
+  if (K < 2 * c0 + 2 || K > s->g.nz || i0 < 0 || i0 >= s->g.nr) return TETM_E_ARG;
+  const RzLayout& L = s->L;
+  // the entry section: rows 2..K carry the activity bytes of row 1
+  unsigned long long* dcount = nullptr;
+  cudaError_t e = cudaMalloc(&dcount, sizeof(unsigned long long));
+  if (e != cudaSuccess) return rz_fail(e);
+  unsigned long long mism = 0;
+  std::vector<uint8_t> row((size_t)L.pr);
+  e = cudaMemsetAsync(dcount, 0, sizeof(unsigned long long), s->st);
+  if (e == cudaSuccess) {
+    rz_row_mismatch<<<256, 256, 0, s->st>>>(s->mask, L, K, dcount);
+    e = cudaGetLastError();
+  }
+  if (e == cudaSuccess) e = cudaMemcpyAsync(&mism, dcount, sizeof(mism), cudaMemcpyDeviceToHost, s->st);
+  if (e == cudaSuccess)
+    e = cudaMemcpyAsync(row.data(), s->mask + 2 * L.pr, (size_t)L.pr, cudaMemcpyDeviceToHost, s->st);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(s->st);
+  cudaFree(dcount);
+  if (e != cudaSuccess) return rz_fail(e);
+  if (mism) return TETM_E_ARG;
+  // per mode: the radial potential (tridiagonal, symmetric positive definite,
+  // eliminated without pivoting) and the longitudinal profile
+  const int nn = s->g.nr + 1;
+  const double eta0 = kMu0 * kC;
+  std::vector<double> psi((size_t)s->n_modes * nn, 0.0), G((size_t)s->n_modes * (K + 4), 0.0);
+  std::vector<double> qc((size_t)(2 * c0));
+  for (int d = -c0; d < c0; ++d) {
+    const double lo = std::max((double)d * dz, -5.0 * sigma);
+    const double hi = std::min((double)(d + 1) * dz, 5.0 * sigma);
+    qc[(size_t)(d + c0)] = hi > lo ? q * (rz_phi(hi / sigma) - rz_phi(lo / sigma)) : 0.0;
+  }
+  for (int mi = 0; mi < s->n_modes; ++mi) {
+    const int m = s->g.m_lo + mi;
+    std::vector<int> unk((size_t)nn);
+    for (int i = 0; i < nn; ++i) {
+      double c[6];
+      rz_metric_row(s->g, m, i, c);
+      unk[(size_t)i] = ((row[(size_t)L.col(i)] >> kEZ) & 1) && c[kEZ] != 0.0;
+    }
+    if (!unk[(size_t)i0]) return TETM_E_ARG;   // the axis carries only m = 0
+    std::vector<double> a((size_t)nn, 0.0), b((size_t)nn, 0.0), cc((size_t)nn, 0.0), r((size_t)nn, 0.0);
+    auto er_on = [&](int i) { return i >= 0 && i < s->g.nr && ((row[(size_t)L.col(i)] >> kER) & 1); };
+    for (int i = 0; i < nn; ++i) {
+      if (!unk[(size_t)i]) { b[(size_t)i] = 1.0; continue; }
+      if (i + 1 < nn && er_on(i)) {
+        const double w = (i + 0.5) * dr / dr;
+        b[(size_t)i] += w;
+        if (unk[(size_t)i + 1]) cc[(size_t)i] = -w;
+      }
+      if (i >= 1 && er_on(i - 1)) {
+        const double w = (i - 0.5) * dr / dr;
+        b[(size_t)i] += w;
+        if (unk[(size_t)i - 1]) a[(size_t)i] = -w;
+      }
+      if (i >= 1) b[(size_t)i] += (double)m * m * dr / (i * dr);
+    }
+    r[(size_t)i0] = 1.0;
+    for (int i = 1; i < nn; ++i) {
+      const double f = a[(size_t)i] / b[(size_t)i - 1];
+      b[(size_t)i] -= f * cc[(size_t)i - 1];
+      r[(size_t)i] -= f * r[(size_t)i - 1];
+    }
+    double* ps = psi.data() + (size_t)mi * nn;
+    ps[nn - 1] = r[(size_t)nn - 1] / b[(size_t)nn - 1];
+    for (int i = nn - 2; i >= 0; --i) ps[i] = (r[(size_t)i] - cc[(size_t)i] * ps[i + 1]) / b[(size_t)i];
+    for (int i = 0; i < nn; ++i) if (!unk[(size_t)i]) ps[i] = 0.0;
+    const double share = (m == 0 ? 1.0 : 2.0) / (2.0 * kPi);
+    double* g = G.data() + (size_t)mi * (K + 4);
+    for (int u = K - 1; u >= K - 2 * c0; --u)
+      g[u + 1] = 2.0 * eta0 * (share * kC * qc[(size_t)(u - K + 2 * c0)] / dz) - g[u + 2];
+  }
+  int rc = tetm_rz_set_bunch(s, sigma, q, i0);
+  if (rc != TETM_OK) return rc;
+  double *dpsi = nullptr, *dg = nullptr;
+  e = cudaMalloc(&dpsi, sizeof(double) * psi.size());
+  if (e == cudaSuccess) e = cudaMalloc(&dg, sizeof(double) * G.size());
+  if (e == cudaSuccess) e = cudaMemcpyAsync(dpsi, psi.data(), sizeof(double) * psi.size(), cudaMemcpyHostToDevice, s->st);
+  if (e == cudaSuccess) e = cudaMemcpyAsync(dg, G.data(), sizeof(double) * G.size(), cudaMemcpyHostToDevice, s->st);
+  if (e == cudaSuccess) {
+    if (s->esz == 8)
+      rz_write_tem<double><<<512, 256, 0, s->st>>>(static_cast<double*>(s->set[s->cur]), L, s->mask,
+                                                   s->metric, s->g.m_lo, s->n_modes, dpsi, dg, K, dr, eta0);
+    else
+      rz_write_tem<float><<<512, 256, 0, s->st>>>(static_cast<float*>(s->set[s->cur]), L, s->mask,
+                                                  s->metric, s->g.m_lo, s->n_modes, dpsi, dg, K, dr, eta0);
+    e = cudaGetLastError();
+  }
+  if (e == cudaSuccess) e = cudaStreamSynchronize(s->st);
+  cudaFree(dpsi);
+  cudaFree(dg);
+  if (e != cudaSuccess) return rz_fail(e);
+  s->kshift = K;
+  return TETM_OK;
 }
 
 int tetm_rz_set_observer(tetm_rz* s, int32_t obs) {

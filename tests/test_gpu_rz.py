@@ -8,6 +8,7 @@ and the order in which the diagonal factor of (24) is applied); FP32 fields
 with FP64 wake sums: wakes within 1e-4 of their peak for m <= 2 (higher
 modes: see test_fp32_wakes_against_oracle)."""
 import dataclasses
+import math
 
 import numpy as np
 import pytest
@@ -294,4 +295,67 @@ def test_observer_state_errors(tetm):
     s.step(1)
     with pytest.raises(tetm.TetmError) as e:
         s.set_observer(6)
+    assert e.value.code == tetm.TETM_E_STATE
+
+
+# ---------------------------------------------------------------------------
+# Static start: the ring bunch enters from an infinite pipe with its TEM field
+# ---------------------------------------------------------------------------
+
+@pytest.mark.parametrize("kernel", KERNELS)
+def test_static_start_matches_oracle(tetm, kernel):
+    w = small_chain(45, 160, 0, 3, i0=4)             # entry pipe uniform for k < 59
+    K = 2 * math.ceil(5 * w.sigma / w.dz - 1e-12) + 2
+    s = gpu_solver(tetm, w, 20, kernel)
+    s.set_bunch_static(w.sigma, w.charge, w.i0, K)
+    n = w.steps - K + 40
+    s.step(n)
+    for m in range(4):
+        o = RzOracle(w.nr, w.nz, m, w.dr, w.dz, w.cdt, pec=w.pec)
+        o.set_bunch_static(w.sigma, w.charge, w.i0, K)
+        o.step(n)
+        errs = family_errors(s.fields(m), o.fields())
+        assert max(errs.values()) <= TOL64, (m, errs)
+        assert rel(s.wake(m)[0], o.wake()[0]) <= TOL64, m
+        assert rel(s.transverse_wake(m), o.transverse_wake()) <= TOL64, m
+
+
+def test_static_start_smooth_pipe_moves_rigidly(tetm):
+    nr, nz = 30, 150
+    pec = wl.rz_radius_mask(nr, nz, lambda k: np.full(k.shape, 14.5))
+    s = tetm.RzSolver(nr, nz, 0, 2, 0.25e-3, 0.25e-3, 0.0, "fp64", pec=pec)
+    sigma = 3 * 0.25e-3
+    K = 2 * 15 + 2
+    s.set_bunch_static(sigma, 1e-9, 5, K)
+    f0 = [s.fields(m) for m in range(3)]
+    n = nz - K - 2
+    s.step(n)
+    for m in range(3):
+        escale = max(np.max(np.abs(f0[m]["er"])), np.max(np.abs(f0[m]["ephi"])))
+        hscale = max(np.max(np.abs(f0[m]["hphi"])), np.max(np.abs(f0[m]["hr"])))
+        for c in E_NAMES + H_NAMES:
+            shifted = np.zeros_like(f0[m][c])
+            shifted[n:] = f0[m][c][:-n]
+            tol = 1e-12 * (escale if c[0] == "e" else hscale)
+            assert np.max(np.abs(s.get(m, c) - shifted)) <= tol, (m, c)
+    cold = tetm.RzSolver(nr, nz, 0, 2, 0.25e-3, 0.25e-3, 0.0, "fp64", pec=pec)
+    cold.set_bunch(sigma, 1e-9, 5)
+    cold.step(n + K)
+    for m in range(3):
+        assert np.max(np.abs(s.wake(m)[0])) <= 1e-12 * np.max(np.abs(cold.wake(m)[0]))
+        assert np.max(np.abs(s.transverse_wake(m))) <= 1e-12 * np.max(np.abs(cold.transverse_wake(m)))
+
+
+def test_static_start_errors(tetm):
+    w = small_chain(30, 120, 0, 1, i0=3, steps=0)
+    s = gpu_solver(tetm, w)
+    with pytest.raises(tetm.TetmError) as e:
+        s.set_bunch_static(w.sigma, w.charge, 3, 100)        # past the entry pipe
+    assert e.value.code == tetm.TETM_E_ARG
+    with pytest.raises(tetm.TetmError) as e:
+        s.set_bunch_static(w.sigma, w.charge, 0, 20)         # the axis with m = 1 solved
+    assert e.value.code == tetm.TETM_E_ARG
+    s.step(1)
+    with pytest.raises(tetm.TetmError) as e:
+        s.set_bunch_static(w.sigma, w.charge, 3, 20)
     assert e.value.code == tetm.TETM_E_STATE
