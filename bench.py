@@ -40,6 +40,7 @@ sys.path.insert(0, ROOT)
 METRIC = "Gcell-updates/s"
 UNIT = "Gcell-updates/s"
 RZ_FLOPS_PER_CELL = 47
+FLOPS_PER_CELL_3D = 48
 FP64_PEAK_TFLOPS = 1.25
 
 
@@ -207,6 +208,38 @@ def kernel_source_hash(names=("kernels_step.cu", "kernels_warp.cu")):
     return h.hexdigest()[:16]
 
 
+def fp64_peak(tetm):
+    """(TFLOP/s, kind): the device's float64 FMA rate measured by the
+    library's microbenchmark, else the part's nominal rate."""
+    try:
+        return tetm.tetm_measure_fma_rate("fp64"), "measured fp64 FMA rate (tetm_measure_fma_rate)"
+    except Exception:
+        return FP64_PEAK_TFLOPS, "nominal fp64 rate of the part"
+
+
+def host_cpu():
+    """nproc and the CPU model of the host (lscpu, else /proc/cpuinfo)."""
+    model = None
+    try:
+        out = subprocess.run(["lscpu"], capture_output=True, text=True, timeout=10).stdout
+        for line in out.splitlines():
+            if line.startswith("Model name:"):
+                model = line.split(":", 1)[1].strip()
+                break
+    except (OSError, subprocess.SubprocessError):
+        pass
+    if not model:
+        try:
+            with open("/proc/cpuinfo") as f:
+                for line in f:
+                    if line.lower().startswith("model name"):
+                        model = line.split(":", 1)[1].strip()
+                        break
+        except OSError:
+            pass
+    return {"nproc": os.cpu_count(), "model": model or __import__("platform").machine()}
+
+
 def profiled_traffic(name, sources=("kernels_step.cu", "kernels_warp.cu")):
     """DRAM bytes per launch from the committed ncu summary for this kernel
     and workload; None if absent or taken on a different kernel source."""
@@ -243,7 +276,7 @@ def cpu_baseline(w):
     steps = 20 if w.nx * w.ny >= 256 * 256 else 400
     v, dt, desc = oracle_sample(w, planes, steps)
     return {"value": v, "unit": UNIT, "cores": 1, "kind": "oracle", "sample": desc,
-            "seconds": round(dt, 2)}
+            "seconds": round(dt, 2), "host": host_cpu()}
 
 
 def run_reference(args):
@@ -343,8 +376,18 @@ def run_tetm(args):
     # the six coefficient words
     bytes_per_cell = 12 * esz + 1 if args.eps is None else 18 * esz
     proc = info["processed_cells"] if args.kernel != "reference" else w.cells
-    achieved = bytes_per_cell * proc / (kern_ms * 1e-3) / 1e9
-    peak, peak_kind = measured_peak_hbm()
+    gbs = bytes_per_cell * proc / (kern_ms * 1e-3) / 1e9
+    if w.precision == "fp32":
+        achieved = gbs
+        peak, peak_kind = measured_peak_hbm()
+        roof = {"bound": "hbm", "unit": "GB/s", "bytes_per_cell": bytes_per_cell}
+    else:
+        # float64 arithmetic sets the pace on this part: 48 flops per cell
+        # and step (the ten updates, a fused multiply-add counted as two)
+        achieved = FLOPS_PER_CELL_3D * proc / (kern_ms * 1e-3) / 1e12
+        peak, peak_kind = fp64_peak(tetm)
+        roof = {"bound": "alu", "unit": "TFLOP/s", "flops_per_cell": FLOPS_PER_CELL_3D,
+                "hbm_gbs": gbs, "bytes_per_cell": bytes_per_cell}
     kname = "fused_step_warp" if info["tile_x"] == 28 else "fused_step"
     if args.eps is not None:
         kname = "fused_step_warp_mat"
@@ -404,10 +447,9 @@ def run_tetm(args):
                    "l2": "inputs larger than L2 (two field sets of %.1f GB each)"
                          % (12 * esz * w.cells / 2 / 1e9),
                    "parallelism": "replicas x%d" % world},
-        "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
-                     "frac": achieved / peak, "traffic": traffic, "peak_kind": peak_kind,
-                     "kernel": kname, "kernel_ms": kern_ms,
-                     "bytes_per_cell": bytes_per_cell, "cells_per_launch": proc},
+        "roofline": dict(roof, achieved=achieved, peak=peak, frac=achieved / peak, traffic=traffic,
+                         peak_kind=peak_kind, kernel=kname, kernel_ms=kern_ms,
+                         cells_per_launch=proc),
         "cpu_baseline": cpu,
         "e2e": e2e,
         "gpu_launches": (10 * K if args.kernel == "reference" else K) + 6 * n_bal,
@@ -601,7 +643,7 @@ def run_rz_mode(args):
         # float64 arithmetic sets the pace on this part: 47 flops per entry
         # and step (the ten updates, a fused multiply-add counted as two)
         achieved = RZ_FLOPS_PER_CELL * proc / (kern_ms * 1e-3) / 1e12
-        peak, peak_kind = FP64_PEAK_TFLOPS, "nominal fp64 rate of the part"
+        peak, peak_kind = fp64_peak(tetm)
         roof = {"bound": "alu", "unit": "TFLOP/s", "flops_per_cell": RZ_FLOPS_PER_CELL,
                 "hbm_gbs": bytes_per_cell * proc / (kern_ms * 1e-3) / 1e9}
     traffic = profiled_traffic("%s_%s_%s.md" % (kname, w.precision, w.name), ("rz.cu",))
@@ -634,7 +676,7 @@ def run_rz_mode(args):
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         v, dt, desc = rz_oracle_sample(w, min(w.nz, 1024), 60)
         cpu = {"value": v, "unit": UNIT, "cores": 1, "kind": "oracle", "sample": desc,
-               "seconds": round(dt, 2)}
+               "seconds": round(dt, 2), "host": host_cpu()}
     value = world * w.cells * K / (max_ms * 1e-3) / 1e9
     line = {
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": K,

@@ -287,6 +287,13 @@ int tetm_batch_info(tetm_batch* b, int32_t* n_members, int32_t* n_active, int32_
 void tetm_batch_destroy(tetm_batch* b);
 
 /* Static description of a return code. */
+/* Measured fused multiply-add rate of the current device in TFLOP/s (2 flops
+ * per FMA) for TETM_FP64 or TETM_FP32 arithmetic: eight independent chains
+ * per thread on every SM, timed with CUDA events on the given stream (NULL:
+ * the default stream). The float64 rate is the ALU roofline of the float64
+ * update kernels. Synchronizes. */
+int tetm_measure_fma_rate(int32_t precision, double* tflops, void* stream);
+
 const char* tetm_strerror(int code);
 
 #ifdef __cplusplus

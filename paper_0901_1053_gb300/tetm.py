@@ -41,7 +41,7 @@ EXPORTS = ("tetm_create", "tetm_set_bunch", "tetm_step", "tetm_sync", "tetm_wake
            "tetm_get_info", "tetm_bytes_needed", "tetm_save", "tetm_load", "tetm_strerror",
            "tetm_set_balance_every", "tetm_balance_history", "tetm_energy_noalloc",
            "tetm_batch_create", "tetm_batch_step", "tetm_batch_sync", "tetm_batch_info",
-           "tetm_batch_destroy", "tetm_set_bunch_static",
+           "tetm_batch_destroy", "tetm_set_bunch_static", "tetm_measure_fma_rate",
            "tetm_rz_create", "tetm_rz_set_bunch", "tetm_rz_step", "tetm_rz_sync", "tetm_rz_wake",
            "tetm_rz_energy", "tetm_rz_get_fields", "tetm_rz_set_fields", "tetm_rz_set_tiling",
            "tetm_rz_set_stream", "tetm_rz_get_info", "tetm_rz_bytes_needed", "tetm_rz_destroy",
@@ -94,6 +94,7 @@ def _load():
         "tetm_create": (ctypes.c_int, [ctypes.POINTER(tetm_grid), vp, vp, vp, pp]),
         "tetm_set_bunch": (ctypes.c_int, [vp, dbl, dbl, i32, i32]),
         "tetm_set_bunch_static": (ctypes.c_int, [vp, dbl, dbl, i32, i32, i32]),
+        "tetm_measure_fma_rate": (ctypes.c_int, [i32, ctypes.POINTER(dbl), vp]),
         "tetm_step": (ctypes.c_int, [vp, i32]),
         "tetm_sync": (ctypes.c_int, [vp]),
         "tetm_wake": (ctypes.c_int, [vp, vp, i32, ctypes.POINTER(i32), ctypes.POINTER(dbl),
@@ -172,6 +173,15 @@ def _ptr(a):
 def make_grid(nx, ny, nz, dx, dy, dz, cdt=0.0, precision="fp32"):
     p = {"fp64": TETM_FP64, "fp32": TETM_FP32}[precision] if isinstance(precision, str) else precision
     return tetm_grid(int(nx), int(ny), int(nz), int(p), float(dx), float(dy), float(dz), float(cdt))
+
+
+def tetm_measure_fma_rate(precision="fp64", stream=0):
+    """Measured FMA rate of the device in TFLOP/s (see include/tetm.h)."""
+    p = {"fp64": TETM_FP64, "fp32": TETM_FP32}[precision] if isinstance(precision, str) else precision
+    out = ctypes.c_double()
+    _check(lib.tetm_measure_fma_rate(int(p), ctypes.byref(out), ctypes.c_void_p(int(stream) if stream else 0)),
+           "tetm_measure_fma_rate")
+    return out.value
 
 
 def tetm_bytes_needed(grid):
