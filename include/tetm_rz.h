@@ -42,11 +42,15 @@ extern "C" {
 
 #define TETM_RZ_MAX_MODES 64
 
-/* step kernels (same results bit for bit; they differ in how loads run ahead) */
+/* step kernels (same results bit for bit; they differ in how loads run ahead
+ * and in how many steps one pass over the fields takes) */
 #define TETM_RZ_KERNEL_ASYNC 0     /* asynchronous copies into a shared-memory ring (default) */
 #define TETM_RZ_KERNEL_REGISTER 1  /* a register ring of planes                               */
 #define TETM_RZ_KERNEL_BULK 2      /* one bulk (TMA) copy per plane and work item into a
                                       shared-memory ring, mbarrier completion               */
+#define TETM_RZ_KERNEL_BULK2 3     /* the bulk-copy sweep advancing two time steps per pass
+                                      (temporal blocking: y^n read and y^{n+2} written once;
+                                      an odd remaining step runs one-step)                  */
 
 typedef struct tetm_rz_grid {
   int32_t nr, nz;      /* primary cells, each >= 2                                 */

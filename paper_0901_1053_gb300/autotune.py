@@ -146,23 +146,24 @@ def tune_rz(w, precision: Optional[str] = None, steps: int = 8, warmup: int = 3,
             extra_chunks: Sequence[int] = (32, 64, 128)):
     """(kernel, chunk_z) with the shortest step on a scratch solve of w's
     geometry: each step kernel with its wave-fitted chunk and a few fixed
-    ones. Returns ("bulk" | "register" | "async", chunk_z)."""
+    ones (the two-steps-per-pass kernel timed over pairs of steps). Returns
+    ("bulk2" | "bulk" | "register" | "async", chunk_z)."""
     from . import tetm
     precision = precision or w.precision
     s = tetm.RzSolver(w.nr, w.nz, w.m_lo, w.m_hi, w.dr, w.dz, w.cdt, precision, pec=w.pec)
     best = None
     try:
-        for kern in ("bulk", "register", "async"):
+        for kern in ("bulk2", "bulk", "register", "async"):
             s.set_kernel(kern)
             chunks = [s.wave_fitted_chunk()] + [c for c in extra_chunks]
             for c in dict.fromkeys(chunks):
                 s.set_tiling(c)
-                s.step(warmup)
+                s.step(2 * warmup)
                 s.sync()
                 t0 = time.perf_counter()
-                s.step(steps)
+                s.step(2 * steps)
                 s.sync()
-                dt = (time.perf_counter() - t0) / steps
+                dt = (time.perf_counter() - t0) / (2 * steps)
                 if best is None or dt < best[0]:
                     best = (dt, kern, c)
     finally:

@@ -50,6 +50,7 @@ constexpr int kER = TETM_RZ_ER, kEP = TETM_RZ_EPHI, kEZ = TETM_RZ_EZ;
 constexpr int kHR = TETM_RZ_HR, kHP = TETM_RZ_HPHI, kHZ = TETM_RZ_HZ;
 constexpr double kPi = 3.14159265358979323846;
 constexpr int kTile = 60;   // entries a warp owns (64-entry window minus 2 + 2 halo)
+constexpr int kTile2 = 56;  // the same for two steps per pass (4 + 4 halo)
 // planes held ahead: register ring (float32 / float64) and shared-memory ring
 template <typename T>
 __host__ __device__ constexpr int ring_depth() { return sizeof(T) == 4 ? 3 : 2; }
@@ -83,13 +84,16 @@ RzLayout make_rz_layout(int nr, int nz) {
   RzLayout L;
   L.nr = nr;
   L.nz = nz;
-  // a window starts at i = 60 t - 2; with the axis at column 6 it starts on
+  // a window starts at i = 60 t - 2 (56 t - 4 for two steps per pass); with
+  // the axis at column 6 it starts on
   // an even column (16-byte aligned pairs, a 16-byte aligned window of
   // entries) and a 4-byte boundary of the mask; the pitch is a multiple of 16
   // and leaves room for the 80 mask bytes copied for the last window
   L.orr = 6;
   const long long tiles = (nr + 1 + kTile - 1) / kTile;
-  L.pr = (std::max((long long)L.orr + nr + 3, (long long)kTile * tiles + 24) + 15) / 16 * 16;
+  const long long tiles2 = (nr + 1 + kTile2 - 1) / kTile2;
+  L.pr = (std::max({(long long)L.orr + nr + 3, (long long)kTile * tiles + 24,
+                    (long long)kTile2 * tiles2 + 24}) + 15) / 16 * 16;
   L.rows = nz + 3;
   return L;
 }
@@ -103,6 +107,7 @@ struct RzArgs {
   const T* coef;          // [mode][kNCo][pr]
   int m_lo, n_modes;
   int tiles, chunk_z;
+  int tile_w, halo;       // owned entries per window and halo entries per side (60/2 or 56/4)
   const int* work;        // active (chunk * tiles + tile)
   int n_work;
   int b_on, i0, c0, m_min, nw;
@@ -290,8 +295,8 @@ __device__ __forceinline__ Item<T> item_of(const RzArgs<T>& a, int witem) {
   const int chunk = rest / a.tiles;
   it.k0 = chunk * a.chunk_z;
   it.k1 = min(it.k0 + a.chunk_z, a.L.nz);
-  it.gi = it.tile * kTile - 2 + 2 * lane;
-  it.own = lane >= 1 && lane <= 30;
+  it.gi = it.tile * a.tile_w - a.halo + 2 * lane;
+  it.own = 2 * lane >= a.halo && 2 * lane < 64 - a.halo;
   it.src0 = a.b_on && it.gi == a.i0;
   it.src1 = a.b_on && it.gi + 1 == a.i0;
   it.fbase = a.L.fidx(it.mode, 0, it.gi, -1);
@@ -330,18 +335,22 @@ __device__ __forceinline__ T current_at(const RzArgs<T>& a, const Item<T>& it, b
 // h_phi(k+1/2) at time n+1/2 and e_r(k) at time n, n = k + m + c0. The
 // longitudinal wake takes e_z at the bunch ring; the radial transverse wake
 // (E_r - c mu0 H_phi) at r_{obs+1/2}, where per radian h_phi = -r H_phi.
+// W and WT are [parity of n][mode][nw]; a wake is the sum of its two halves.
 template <typename T>
 __device__ __forceinline__ void gather_wake(const RzArgs<T>& a, const Item<T>& it, int k,
                                             const T* out, const T* er_old) {
   if (!it.own || !a.b_on) return;
   const long long w = (a.n + a.kshift) - k - a.c0 - a.m_min;
   if (w < 0 || w >= a.nw) return;
+  // even and odd steps accumulate into separate halves: a pass that takes
+  // two steps writes step n and step n+1 samples from different work items
+  const long long par = (a.n & 1) * (long long)a.n_modes * a.nw;
   const bool s[2] = {it.src0, it.src1};
 #pragma unroll
   for (int e = 0; e < 2; ++e) {
-    if (s[e]) a.W[(long long)it.mode * a.nw + w] -= (double)out[6 * e + kEZ] * a.inv_q;
+    if (s[e]) a.W[par + (long long)it.mode * a.nw + w] -= (double)out[6 * e + kEZ] * a.inv_q;
     if (it.gi + e == a.obs)
-      a.WT[(long long)it.mode * a.nw + w] += a.tw_er * (double)er_old[e] + a.tw_hp * (double)out[6 * e + kHP];
+      a.WT[par + (long long)it.mode * a.nw + w] += a.tw_er * (double)er_old[e] + a.tw_hp * (double)out[6 * e + kHP];
   }
 }
 
@@ -436,7 +445,7 @@ __device__ __forceinline__ void rz_item_async(const RzArgs<T>& a, int witem, uns
   const T* __restrict__ ip = a.in + it.fbase;
   T* __restrict__ op = a.out + it.fbase;
   // the window's activity bytes: lanes 0..15 copy bytes 4 l .. 4 l + 3
-  const uint8_t* __restrict__ mwin = a.mask + a.L.midx(it.tile * kTile - 2, -1) + 4 * (lane & 15);
+  const uint8_t* __restrict__ mwin = a.mask + a.L.midx(it.tile * a.tile_w - a.halo, -1) + 4 * (lane & 15);
   constexpr int kADepth = async_depth<T>();
   T* ring = reinterpret_cast<T*>(wsm) + lane * 12;
   uint8_t* mring = wsm + (size_t)kADepth * 32 * 12 * sizeof(T);
@@ -573,8 +582,8 @@ __device__ __forceinline__ bool rz_item_bulk(const RzArgs<T>& a, int witem, unsi
   const long long RS = a.L.pr * 6;
   const long long MS = a.L.pr;
   T* __restrict__ op = a.out + it.fbase;
-  const int wcol = it.tile * kTile - 2 + a.L.orr;          // window's first column
-  const T* __restrict__ wsrc = a.in + a.L.fidx(it.mode, 0, it.tile * kTile - 2, -1);
+  const int wcol = it.tile * a.tile_w - a.halo + a.L.orr;  // window's first column
+  const T* __restrict__ wsrc = a.in + a.L.fidx(it.mode, 0, it.tile * a.tile_w - a.halo, -1);
   const int mcol = wcol & ~15;                              // 16-byte aligned mask block
   const uint8_t* __restrict__ msrc = a.mask + mcol;
   unsigned char* fring = wsm;
@@ -665,6 +674,144 @@ __global__ void __launch_bounds__(128) rz_step_bulk_kernel(const RzArgs<T> a) {
     if (!rz_item_bulk<T>(a, w, wsm, phases)) return;
 }
 
+// --- two steps per pass (temporal blocking) -----------------------------------
+// The bulk-copy sweep with a second time step riding one plane behind the
+// first: at plane k the warp takes y^n -> y^{n+1} (step 1) as above, then
+// y^{n+1} -> y^{n+2} at plane k-1 (step 2) from the step-1 values of planes
+// k-1 and k it holds in registers, and stores only y^{n+2}. Each plane of y^n
+// is read once and each plane of y^{n+2} written once for two steps. Step 1
+// is valid on the window entries 2..61, so step 2 owns 4..59 (56-entry tiles,
+// 4 halo entries each side). Step 1 recomputes two planes before the chunk and
+// one after; step 2 recomputes one before. Both steps deposit their current;
+// each gathers its wake samples on the item's own planes.
+template <typename T>
+__device__ __forceinline__ bool rz_item_bulk2(const RzArgs<T>& a, int witem, unsigned char* wsm,
+                                              unsigned& phases) {
+  constexpr int D = bulk_depth<T>();
+  constexpr int WB = window_bytes<T>();
+  const int lane = threadIdx.x & 31;
+  const Item<T> it = item_of(a, witem);
+  const LaneCo<T> c = lane_coefs(a, it);
+  const T mm = T(a.m_lo + it.mode);
+  const long long RS = a.L.pr * 6;
+  const long long MS = a.L.pr;
+  T* __restrict__ op = a.out + it.fbase;
+  const int wcol = it.tile * a.tile_w - a.halo + a.L.orr;
+  const T* __restrict__ wsrc = a.in + a.L.fidx(it.mode, 0, it.tile * a.tile_w - a.halo, -1);
+  const int mcol = wcol & ~15;
+  const uint8_t* __restrict__ msrc = a.mask + mcol;
+  unsigned char* fring = wsm;
+  unsigned char* mring = wsm + (size_t)D * WB;
+  uint64_t* bars = reinterpret_cast<uint64_t*>(wsm + (size_t)D * (WB + kMaskBlock));
+  const int kfirst = max(it.k0 - 2, -1);    // first plane of step 1 (plane -1 is all guard)
+  const int klast = it.k1;                  // last plane of step 1
+  const int moff = wcol - mcol + 2 * lane;
+  int issued = kfirst - 1, fetched = kfirst - 1;
+  // a second item view for step 2: same geometry, one step later
+  RzArgs<T> a2 = a;
+  a2.n = a.n + 1;
+
+  auto issue = [&](int p) {
+    if (p > klast + 1) return;
+    const int slot = (p - kfirst) % D;
+    if (lane == 0) {
+      asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+      mbar_expect_tx(bars + slot, WB + kMaskBlock);
+      bulk_g2s(fring + (size_t)slot * WB, wsrc + (long long)(p + 1) * RS, WB, bars + slot);
+      bulk_g2s(mring + (size_t)slot * kMaskBlock, msrc + (long long)(p + 1) * MS, kMaskBlock, bars + slot);
+    }
+    issued = p;
+  };
+  bool ok = true;
+  auto fetch = [&](int p, Pair6<T>& d) {
+    const int slot = (p - kfirst) % D;
+    if (ok) ok = mbar_wait(bars + slot, (phases >> slot) & 1u);
+    if (ok) {
+      phases ^= 1u << slot;
+      fetched = p;
+    }
+    const T* src = reinterpret_cast<const T*>(fring + (size_t)slot * WB) + 12 * lane;
+#pragma unroll
+    for (int q = 0; q < 12; ++q) d.f[q] = src[q];
+    d.m = *reinterpret_cast<const unsigned short*>(mring + (size_t)slot * kMaskBlock + moff);
+  };
+
+  __syncwarp();
+  for (int p = 0; p < D - 1; ++p) issue(kfirst + p);
+  LaneState<T> s1, s2;
+  Pair6<T> d0, d1, y1prev;     // y^n of planes k, k+1; y^{n+1} of plane k-1
+  fetch(kfirst, d0);
+#pragma unroll
+  for (int e = 0; e < 2; ++e) {
+    s1.er0[e] = d0.f[6 * e + kER];
+    s1.ep0[e] = d0.f[6 * e + kEP];
+    s1.hr_p[e] = T(0);
+    s1.hp_p[e] = T(0);
+    s2.hr_p[e] = T(0);
+    s2.hp_p[e] = T(0);
+    s2.er0[e] = T(0);
+    s2.ep0[e] = T(0);
+  }
+  for (int k = kfirst; k <= klast && __all_sync(0xffffffffu, ok); ++k) {
+    __syncwarp();
+    issue(k + D - 1);
+    fetch(k + 1, d1);
+    if (!__all_sync(0xffffffffu, ok)) break;
+    // step 1 at plane k
+    Pair6<T> y1;
+    T er_old[2];
+    rz_plane(d0, d1, c, mm, s1, current_at(a, it, it.src0, k), current_at(a, it, it.src1, k), y1.f,
+             er_old);
+    y1.m = d0.m;
+    if (k >= it.k0 && k < it.k1) gather_wake(a, it, k, y1.f, er_old);
+    // step 2 at plane k - 1 (from step-1 planes k-1 and k)
+    const int k2 = k - 1;
+    if (k2 == it.k0 - 1) {
+#pragma unroll
+      for (int e = 0; e < 2; ++e) {
+        s2.er0[e] = y1prev.f[6 * e + kER];
+        s2.ep0[e] = y1prev.f[6 * e + kEP];
+      }
+    }
+    if (k2 >= it.k0 - 1) {
+      T y2[12], er_old2[2];
+      rz_plane(y1prev, y1, c, mm, s2, current_at(a2, it, it.src0, k2), current_at(a2, it, it.src1, k2),
+               y2, er_old2);
+      if (it.own && k2 >= it.k0) {
+        st_pair(op + (long long)(k2 + 1) * RS, y2);
+        gather_wake(a2, it, k2, y2, er_old2);
+      }
+    }
+    y1prev = y1;
+    d0 = d1;
+  }
+  if (__all_sync(0xffffffffu, ok)) return true;
+  if (lane == 0) atomicExch(a.err, 1);
+  for (int p = fetched + 1; p <= issued; ++p) {
+    const int slot = (p - kfirst) % D;
+    mbar_wait(bars + slot, (phases >> slot) & 1u);
+    phases ^= 1u << slot;
+  }
+  return false;
+}
+
+template <typename T>
+__global__ void __launch_bounds__(128, sizeof(T) == 4 ? 4 : 1) rz_step_bulk2_kernel(const RzArgs<T> a) {
+  extern __shared__ __align__(128) unsigned char rz_bulk2_smem[];
+  constexpr int D = bulk_depth<T>();
+  unsigned char* wsm = rz_bulk2_smem + (size_t)(threadIdx.x >> 5) * rz_bulk_warp_bytes<T>();
+  uint64_t* bars = reinterpret_cast<uint64_t*>(wsm + (size_t)D * (window_bytes<T>() + kMaskBlock));
+  if ((threadIdx.x & 31) == 0)
+    for (int q = 0; q < D; ++q) mbar_init(bars + q, 1);
+  asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+  __syncwarp();
+  unsigned phases = 0;
+  const int nitems = a.n_work * a.n_modes;
+  const int nwarps = (int)((gridDim.x * blockDim.x) >> 5);
+  for (int w = (int)((blockIdx.x * blockDim.x + threadIdx.x) >> 5); w < nitems; w += nwarps)
+    if (!rz_item_bulk2<T>(a, w, wsm, phases)) return;
+}
+
 // Activity bits from the cell geometry (staircase; the rules of the
 // per-radian metric): bit c set <=> object c at entry (i, k) is non-PEC.
 __device__ __forceinline__ bool cell_pec(const uint8_t* pec, int nr, int nz, int ci, int ck) {
@@ -703,12 +850,12 @@ __global__ void rz_build_mask(const uint8_t* pec, RzLayout L, uint8_t* mask) {
 
 // A (radial tile, z chunk) pair is worth a work item when one of its owned
 // entries carries a field.
-__global__ void rz_item_flags(const uint8_t* mask, RzLayout L, int tiles, int chunk_z,
+__global__ void rz_item_flags(const uint8_t* mask, RzLayout L, int tiles, int tile_w, int chunk_z,
                               int n_chunks, int* flags) {
   const int q = blockIdx.x * blockDim.x + threadIdx.x;
   if (q >= tiles * n_chunks) return;
   const int tile = q % tiles, chunk = q / tiles;
-  const int i_lo = tile * kTile, i_hi = min(i_lo + kTile, L.nr + 1);
+  const int i_lo = tile * tile_w, i_hi = min(i_lo + tile_w, L.nr + 1);
   const int k_lo = chunk * chunk_z, k_hi = min(k_lo + chunk_z, L.nz);
   int any = 0;
   for (int k = k_lo; k < k_hi && !any; ++k)
@@ -897,6 +1044,7 @@ struct tetm_rz {
   int* err = nullptr;            // device error word of the bulk-copy kernel
   int obs = 0;                   // transverse wake at r_{obs+1/2}
   long long kshift = 0;          // static start: head at plane step + kshift
+  int tile_w = kTile;            // owned entries per window of the current work list
   double* WT = nullptr;          // [mode][nw]
 };
 
@@ -912,6 +1060,8 @@ int rz_launch_steps(tetm_rz* s, long long n) {
   a.n_modes = s->n_modes;
   a.tiles = s->tiles;
   a.chunk_z = s->chunk_z;
+  a.tile_w = s->tile_w;
+  a.halo = s->tile_w == kTile2 ? 4 : 2;
   a.work = s->work;
   a.n_work = s->n_work;
   a.b_on = s->bunch ? 1 : 0;
@@ -939,8 +1089,19 @@ int rz_launch_steps(tetm_rz* s, long long n) {
     a.in = static_cast<const T*>(s->set[s->cur]);
     a.out = static_cast<T*>(s->set[s->cur ^ 1]);
     a.n = s->step;
+    if (s->kernel == TETM_RZ_KERNEL_BULK2 && t + 1 < n) {  // two steps in one pass
+      if (items > 0) {
+        rz_step_bulk2_kernel<T><<<blocks, 128, 4 * rz_bulk_warp_bytes<T>(), s->st>>>(a);
+        cudaError_t e = cudaGetLastError();
+        if (e != cudaSuccess) return rz_fail(e);
+      }
+      s->cur ^= 1;
+      s->step += 2;
+      ++t;
+      continue;
+    }
     if (items > 0) {
-      if (s->kernel == TETM_RZ_KERNEL_BULK)
+      if (s->kernel == TETM_RZ_KERNEL_BULK || s->kernel == TETM_RZ_KERNEL_BULK2)
         rz_step_bulk_kernel<T><<<blocks, 128, 4 * rz_bulk_warp_bytes<T>(), s->st>>>(a);
       else if (s->kernel == TETM_RZ_KERNEL_ASYNC)
         rz_step_async_kernel<T><<<blocks, 128, 4 * rz_async_warp_bytes<T>(), s->st>>>(a);
@@ -969,8 +1130,13 @@ int rz_occupancy(tetm_rz* s) {
   if (e == cudaSuccess && bsmem > 48 * 1024)
     e = cudaFuncSetAttribute(rz_step_bulk_kernel<T>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                              (int)bsmem);
+  if (e == cudaSuccess && bsmem > 48 * 1024)
+    e = cudaFuncSetAttribute(rz_step_bulk2_kernel<T>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                             (int)bsmem);
   if (e == cudaSuccess) {
-    if (s->kernel == TETM_RZ_KERNEL_BULK)
+    if (s->kernel == TETM_RZ_KERNEL_BULK2)
+      e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, rz_step_bulk2_kernel<T>, 128, bsmem);
+    else if (s->kernel == TETM_RZ_KERNEL_BULK)
       e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, rz_step_bulk_kernel<T>, 128, bsmem);
     else if (s->kernel == TETM_RZ_KERNEL_ASYNC)
       e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, rz_step_async_kernel<T>, 128, smem);
@@ -984,7 +1150,9 @@ int rz_occupancy(tetm_rz* s) {
 
 int rz_rebuild_work(tetm_rz* s) {
   const RzLayout& L = s->L;
-  s->tiles = (L.nr + 1 + kTile - 1) / kTile;
+  const int tw = s->kernel == TETM_RZ_KERNEL_BULK2 ? kTile2 : kTile;
+  s->tile_w = tw;
+  s->tiles = (L.nr + 1 + tw - 1) / tw;
   s->n_chunks = (L.nz + s->chunk_z - 1) / s->chunk_z;
   const int nf = s->tiles * s->n_chunks;
   if (nf > s->flags_cap) {
@@ -995,8 +1163,8 @@ int rz_rebuild_work(tetm_rz* s) {
     if (e != cudaSuccess) return rz_fail(e);
     s->flags_cap = nf;
   }
-  rz_item_flags<<<(nf + 255) / 256, 256, 0, s->st>>>(s->mask, L, s->tiles, s->chunk_z, s->n_chunks,
-                                                      s->flags);
+  rz_item_flags<<<(nf + 255) / 256, 256, 0, s->st>>>(s->mask, L, s->tiles, tw, s->chunk_z,
+                                                      s->n_chunks, s->flags);
   cudaError_t e = cudaGetLastError();
   if (e != cudaSuccess) return rz_fail(e);
   std::vector<int> fl((size_t)nf);
@@ -1009,7 +1177,7 @@ int rz_rebuild_work(tetm_rz* s) {
     if (!fl[(size_t)q]) continue;
     w.push_back(q);
     const int tile = q % s->tiles, chunk = q / s->tiles;
-    const int width = std::min(kTile, L.nr + 1 - tile * kTile);
+    const int width = std::min(tw, L.nr + 1 - tile * tw);
     const int planes = std::min(s->chunk_z, L.nz - chunk * s->chunk_z);
     processed += (long long)width * planes;
   }
@@ -1077,6 +1245,21 @@ size_t rz_field_bytes(const RzLayout& L, int esz, int n_modes) {
 }
 
 bool rz_mode_ok(const tetm_rz* s, int mode) { return s && mode >= 0 && mode < s->n_modes; }
+
+// a wake of one mode: the sum of its even-step and odd-step halves
+int rz_read_wake(tetm_rz* s, const double* W, int mode, double* out) {
+  std::vector<double> h((size_t)2 * s->nw);
+  const size_t half = (size_t)s->n_modes * s->nw;
+  cudaError_t e = cudaMemcpyAsync(h.data(), W + (size_t)mode * s->nw, sizeof(double) * s->nw,
+                                  cudaMemcpyDeviceToHost, s->st);
+  if (e == cudaSuccess)
+    e = cudaMemcpyAsync(h.data() + s->nw, W + half + (size_t)mode * s->nw, sizeof(double) * s->nw,
+                        cudaMemcpyDeviceToHost, s->st);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(s->st);
+  if (e != cudaSuccess) return rz_fail(e);
+  for (int q = 0; q < s->nw; ++q) out[q] = h[(size_t)q] + h[(size_t)(s->nw + q)];
+  return TETM_OK;
+}
 
 }  // namespace
 
@@ -1183,13 +1366,13 @@ int tetm_rz_set_bunch(tetm_rz* s, double sigma, double q, int32_t i0) {
   void* J = nullptr;
   double *W = nullptr, *WT = nullptr;
   cudaError_t e = cudaMalloc(&J, (size_t)s->esz * nj);
-  if (e == cudaSuccess) e = cudaMalloc(&W, sizeof(double) * (size_t)s->n_modes * nw);
-  if (e == cudaSuccess) e = cudaMalloc(&WT, sizeof(double) * (size_t)s->n_modes * nw);
-  if (e == cudaSuccess) e = cudaMemset(WT, 0, sizeof(double) * (size_t)s->n_modes * nw);
+  if (e == cudaSuccess) e = cudaMalloc(&W, 2 * sizeof(double) * (size_t)s->n_modes * nw);
+  if (e == cudaSuccess) e = cudaMalloc(&WT, 2 * sizeof(double) * (size_t)s->n_modes * nw);
+  if (e == cudaSuccess) e = cudaMemset(WT, 0, 2 * sizeof(double) * (size_t)s->n_modes * nw);
   if (e == cudaSuccess)
     e = cudaMemcpy(J, s->esz == 8 ? (const void*)jd.data() : (const void*)jf.data(),
                    (size_t)s->esz * nj, cudaMemcpyHostToDevice);
-  if (e == cudaSuccess) e = cudaMemset(W, 0, sizeof(double) * (size_t)s->n_modes * nw);
+  if (e == cudaSuccess) e = cudaMemset(W, 0, 2 * sizeof(double) * (size_t)s->n_modes * nw);
   if (e != cudaSuccess) {
     cudaFree(J);
     cudaFree(W);
@@ -1208,7 +1391,7 @@ int tetm_rz_set_bunch(tetm_rz* s, double sigma, double q, int32_t i0) {
   s->nw = nw;
   s->q = q;
   s->sigma = sigma;
-  s->device_bytes += (long long)((size_t)s->esz * nj + 2 * sizeof(double) * (size_t)s->n_modes * nw);
+  s->device_bytes += (long long)((size_t)s->esz * nj + 4 * sizeof(double) * (size_t)s->n_modes * nw);
   return TETM_OK;
 }
 
@@ -1239,10 +1422,7 @@ int tetm_rz_wake(tetm_rz* s, int32_t mode, double* out, int32_t cap, int32_t* n_
   if (ds) *ds = s->g.dz;
   if (!out) return TETM_OK;
   if (cap < s->nw) return TETM_E_ARG;
-  cudaError_t e = cudaMemcpyAsync(out, s->W + (size_t)mode * s->nw, sizeof(double) * s->nw,
-                                  cudaMemcpyDeviceToHost, s->st);
-  if (e == cudaSuccess) e = cudaStreamSynchronize(s->st);
-  return e == cudaSuccess ? TETM_OK : rz_fail(e);
+  return rz_read_wake(s, s->W, mode, out);
 }
 
 int tetm_rz_set_bunch_static(tetm_rz* s, double sigma, double q, int32_t i0, int32_t k_head) {
@@ -1363,10 +1543,7 @@ int tetm_rz_transverse_wake(tetm_rz* s, int32_t mode, double* out, int32_t cap, 
   if (ds) *ds = s->g.dz;
   if (!out) return TETM_OK;
   if (cap < s->nw) return TETM_E_ARG;
-  cudaError_t e = cudaMemcpyAsync(out, s->WT + (size_t)mode * s->nw, sizeof(double) * s->nw,
-                                  cudaMemcpyDeviceToHost, s->st);
-  if (e == cudaSuccess) e = cudaStreamSynchronize(s->st);
-  return e == cudaSuccess ? TETM_OK : rz_fail(e);
+  return rz_read_wake(s, s->WT, mode, out);
 }
 
 int tetm_rz_energy(tetm_rz* s, int32_t mode, double* w) {
@@ -1437,10 +1614,13 @@ int tetm_rz_set_tiling(tetm_rz* s, int32_t chunk_z) {
 
 int tetm_rz_set_kernel(tetm_rz* s, int32_t kernel) {
   if (!s || (kernel != TETM_RZ_KERNEL_REGISTER && kernel != TETM_RZ_KERNEL_ASYNC &&
-             kernel != TETM_RZ_KERNEL_BULK))
+             kernel != TETM_RZ_KERNEL_BULK && kernel != TETM_RZ_KERNEL_BULK2))
     return TETM_E_ARG;
+  const bool retile = (kernel == TETM_RZ_KERNEL_BULK2) != (s->kernel == TETM_RZ_KERNEL_BULK2);
   s->kernel = kernel;
-  return s->esz == 8 ? rz_occupancy<double>(s) : rz_occupancy<float>(s);
+  int rc = s->esz == 8 ? rz_occupancy<double>(s) : rz_occupancy<float>(s);
+  if (rc == TETM_OK && retile) rc = rz_rebuild_work(s);
+  return rc;
 }
 
 int tetm_rz_set_stream(tetm_rz* s, void* cuda_stream) {

@@ -50,6 +50,7 @@ EXPORTS = ("tetm_create", "tetm_set_bunch", "tetm_step", "tetm_sync", "tetm_wake
 TETM_RZ_KERNEL_ASYNC = 0
 TETM_RZ_KERNEL_REGISTER = 1
 TETM_RZ_KERNEL_BULK = 2
+TETM_RZ_KERNEL_BULK2 = 3
 RZ_COMPONENTS = ("er", "ephi", "ez", "hr", "hphi", "hz")
 TETM_RZ_MAX_MODES = 64
 
@@ -441,7 +442,7 @@ class RzSolver:
 
     def set_kernel(self, kernel):
         k = {"async": TETM_RZ_KERNEL_ASYNC, "register": TETM_RZ_KERNEL_REGISTER,
-             "bulk": TETM_RZ_KERNEL_BULK}[kernel] \
+             "bulk": TETM_RZ_KERNEL_BULK, "bulk2": TETM_RZ_KERNEL_BULK2}[kernel] \
             if isinstance(kernel, str) else int(kernel)
         _check(lib.tetm_rz_set_kernel(self.h, k), "tetm_rz_set_kernel")
 

@@ -79,7 +79,7 @@ def rel(a, b):
 # FP64 parity, field by field and wake by wake
 # ---------------------------------------------------------------------------
 
-KERNELS = ("async", "register", "bulk")
+KERNELS = ("async", "register", "bulk", "bulk2")
 
 
 @pytest.mark.parametrize("kernel", KERNELS)
@@ -149,7 +149,8 @@ def test_chunk_sizes_and_kernels_are_bitwise_identical(tetm):
         w = small_chain(70, 130, 0, 2, i0=5, steps=90, precision=prec)
         res = []
         for chunk, kernel in ((4, "async"), (13, "async"), (64, "async"), (13, "register"),
-                              (64, "register"), (4, "bulk"), (13, "bulk"), (64, "bulk")):
+                              (64, "register"), (4, "bulk"), (13, "bulk"), (64, "bulk"),
+                              (4, "bulk2"), (13, "bulk2"), (64, "bulk2")):
             s = gpu_solver(tetm, w, chunk, kernel)
             s.set_bunch(w.sigma, w.charge, w.i0)
             s.step(w.steps)
