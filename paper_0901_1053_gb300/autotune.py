@@ -143,7 +143,7 @@ class Autotuner:
 # ---------------------------------------------------------------------------
 
 def tune_rz(w, precision: Optional[str] = None, steps: int = 8, warmup: int = 3,
-            extra_chunks: Sequence[int] = (32, 64, 128)):
+            extra_chunks: Sequence[int] = (16, 24, 32, 64, 128)):
     """(kernel, chunk_z) with the shortest step on a scratch solve of w's
     geometry: each step kernel with its wave-fitted chunk and a few fixed
     ones (the two-steps-per-pass kernel timed over pairs of steps). Returns
