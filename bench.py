@@ -56,6 +56,13 @@ def parse_args():
                    help="rz: planes per work item (0 = chosen by the autotuner, untimed)")
     p.add_argument("--rz-kernel", default=None, choices=[None, "async", "register", "bulk", "bulk2"],
                    help="rz: step kernel (default: chosen by the autotuner, untimed)")
+    p.add_argument("--rz-start", default="scattered", choices=["cold", "static", "scattered"],
+                   help="rz: bunch start (cold: through the entry wall; static: with its TEM "
+                        "field in the entry pipe; scattered: the static start with the "
+                        "incident TEM field split off, default)")
+    p.add_argument("--rz-check", action="store_true",
+                   help="rz, float32: also run the full solve in float64 (total-field static "
+                        "start) and report every wake's error against it")
     p.add_argument("--requests", type=int, default=2000, help="serve: requests in the stream")
     p.add_argument("--rate", type=float, default=40.0, help="serve: mean arrivals per second")
     p.add_argument("--solves", type=int, default=64, help="batch: number of solves")
@@ -399,7 +406,7 @@ def run_tetm(args):
 
     e2e = None
     if not args.no_e2e:
-        steps_e2e = args.e2e_steps or w.steps
+        steps_e2e = args.e2e_steps or full_steps
         pinned = None
         if w.pec is not None:
             pinned = torch.empty(w.pec.shape, dtype=torch.uint8, pin_memory=True).numpy()
@@ -566,6 +573,39 @@ def rz_workload(args):
     return wl.cavity_chain_rz(nz=args.nz or 16384, precision=args.precision or "fp32")
 
 
+def rz_start(s, w, start):
+    """Starts the bunch; returns the steps of a full solve (the wake window
+    complete)."""
+    K = 2 * math.ceil(5 * w.sigma / w.dz - 1e-12) + 2
+    if start == "cold":
+        s.set_bunch(w.sigma, w.charge, w.i0)
+        return w.steps
+    if start == "static":
+        s.set_bunch_static(w.sigma, w.charge, w.i0, K)
+    else:
+        s.set_bunch_scattered(w.sigma, w.charge, w.i0, K)
+    return w.steps - K
+
+
+def rz_source_launches(start, warmup, steps, stride, slots=8):
+    """Source launches of the scattered form among `steps` steps taken after
+    `warmup` (one launch computes the sources of `slots` steps)."""
+    if start != "scattered":
+        return 0
+    n = until = 0
+    count = 0
+    for t in range(warmup + steps):
+        if t < n:
+            continue
+        p = stride if t + stride <= warmup + steps else 1
+        if n + p > until:
+            until = n + slots
+            if n >= warmup:
+                count += 1
+        n += p
+    return count
+
+
 def rz_oracle_sample(w, planes, steps):
     import dataclasses
     from oracle import RzOracle
@@ -595,7 +635,7 @@ def run_rz_mode(args):
     w = rz_workload(args)
     stream = torch.cuda.Stream()
     s = tetm.RzSolver(w.nr, w.nz, w.m_lo, w.m_hi, w.dr, w.dz, w.cdt, w.precision, pec=w.pec)
-    s.set_bunch(w.sigma, w.charge, w.i0)
+    full_steps = rz_start(s, w, args.rz_start)
     s.set_stream(stream.cuda_stream)
     if args.rz_chunk and args.rz_kernel:
         kern, chunk = args.rz_kernel, args.rz_chunk
@@ -657,26 +697,46 @@ def run_rz_mode(args):
 
     e2e = None
     if not args.no_e2e:
-        steps_e2e = args.e2e_steps or w.steps
+        steps_e2e = args.e2e_steps or full_steps
         pinned = torch.empty(w.pec.shape, dtype=torch.uint8, pin_memory=True).numpy()
         pinned[...] = w.pec
         dist.barrier()
         torch.cuda.synchronize()
         t0 = time.perf_counter()
         s2 = tetm.RzSolver(w.nr, w.nz, w.m_lo, w.m_hi, w.dr, w.dz, w.cdt, w.precision, pec=pinned)
-        s2.set_bunch(w.sigma, w.charge, w.i0)
+        rz_start(s2, w, args.rz_start)
         s2.set_kernel(kern)
         s2.set_tiling(chunk)
         s2.step(steps_e2e)
         wakes = [s2.wake(m)[0] for m in range(w.m_lo, w.m_hi + 1)]
         t1 = time.perf_counter()
+        twakes = [s2.transverse_wake(m) for m in range(w.m_lo, w.m_hi + 1)]
         s2.close()
         e2e_s = dist.max(t1 - t0)
         e2e = {"value": world * w.cells * steps_e2e / e2e_s / 1e9, "unit": UNIT,
                "h2d_bytes_per_step": int(pinned.nbytes),
                "d2h_bytes_per_step": int(sum(x.nbytes for x in wakes)), "steps_per_call": steps_e2e,
                "seconds": round(e2e_s, 3),
-               "call": "tetm_rz_create(host pec) + tetm_rz_set_bunch + tetm_rz_step + tetm_rz_wake(host)"}
+               "call": "tetm_rz_create(host pec) + tetm_rz_set_bunch%s + tetm_rz_step + tetm_rz_wake(host)"
+                       % ("" if args.rz_start == "cold" else "_" + args.rz_start)}
+        if args.rz_check and w.precision == "fp32" and steps_e2e == full_steps:
+            # every wake of the float32 solve against the float64 total-field
+            # static start (same physics in exact arithmetic for the static
+            # and scattered starts; the cold start is checked against a cold
+            # float64 solve)
+            r = tetm.RzSolver(w.nr, w.nz, w.m_lo, w.m_hi, w.dr, w.dz, w.cdt, "fp64", pec=w.pec)
+            rz_start(r, w, "cold" if args.rz_start == "cold" else "static")
+            r.set_kernel("bulk")
+            r.set_tiling(32)
+            r.step(steps_e2e)
+            err = []
+            for i, m in enumerate(range(w.m_lo, w.m_hi + 1)):
+                ref, tref = r.wake(m)[0], r.transverse_wake(m)
+                err.append({"m": m,
+                            "longitudinal": float(np.max(np.abs(wakes[i] - ref)) / np.max(np.abs(ref))),
+                            "transverse": float(np.max(np.abs(twakes[i] - tref)) / np.max(np.abs(tref)))})
+            r.close()
+            e2e["wake_error_vs_fp64"] = err
 
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
@@ -693,6 +753,7 @@ def run_rz_mode(args):
                    "dr_mm": w.dr * 1e3, "dz_mm": w.dz * 1e3, "cdt": "dz",
                    "sigma_dz": round(w.sigma / w.dz, 3), "bunch_ring_i0": w.i0,
                    "fields": w.precision, "wake": "f64", "chunk_z": chunk, "kernel": kern,
+                   "start": args.rz_start,
                    "work_items": info["work_items"], "cells": w.cells, "processed_cells": proc,
                    "l2": "inputs larger than L2 (two field sets of %.1f GB each)"
                          % (6 * esz * w.cells / 1e9),
@@ -702,7 +763,10 @@ def run_rz_mode(args):
                          cells_per_launch=proc),
         "cpu_baseline": cpu,
         "e2e": e2e,
-        "gpu_launches": R,
+        # per pass: the plain step kernel, plus in the scattered form the same
+        # kernel over the items meeting the source window, and the sources
+        "gpu_launches": R * (2 if args.rz_start == "scattered" else 1)
+                        + rz_source_launches(args.rz_start, args.warmup, K, stride),
         "clocks": clk,
     }
     if rank == 0:

@@ -105,6 +105,24 @@ int tetm_rz_set_bunch(tetm_rz* s, double sigma, double q, int32_t i0);
  * 0..k_head+1 of every mode. Synchronizes. */
 int tetm_rz_set_bunch_static(tetm_rz* s, double sigma, double q, int32_t i0, int32_t k_head);
 
+/* Scattered-field form of the static start: the same solve as
+ * tetm_rz_set_bunch_static (same arguments, the same fields, wakes and energy
+ * in exact arithmetic), but the field kept on the device is the total minus
+ * the incident field, the static start's TEM field moving one plane per step
+ * through a continuation of the entry section. Each step first evaluates, in
+ * the field precision, the incident field's mismatch with the geometry (one
+ * step of (24) applied to it, bunch current included, minus its next
+ * position: an exact zero wherever the geometry is the entry section) on the
+ * 2*c0 + 3 planes around the bunch and adds it to the new field; the step
+ * kernels deposit no current. The stored field thus carries no near field of
+ * the bunch, which keeps float32 wakes accurate for every mode.
+ * tetm_rz_get_fields, tetm_rz_set_fields and tetm_rz_energy take and return
+ * the total field. Extra requirement: every object of the entry section
+ * (plane 1) is present on planes 1..nz-1 (TETM_E_ARG otherwise). Device
+ * memory: eight source windows of 2*c0 + 3 planes of all modes (the sources
+ * of eight steps are computed per launch). Synchronizes. */
+int tetm_rz_set_bunch_scattered(tetm_rz* s, double sigma, double q, int32_t i0, int32_t k_head);
+
 /* Queues n steps of Eq. (24) for every mode (n >= 0). */
 int tetm_rz_step(tetm_rz* s, int64_t n);
 

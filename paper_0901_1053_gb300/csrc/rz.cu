@@ -51,6 +51,11 @@ constexpr int kHR = TETM_RZ_HR, kHP = TETM_RZ_HPHI, kHZ = TETM_RZ_HZ;
 constexpr double kPi = 3.14159265358979323846;
 constexpr int kTile = 60;   // entries a warp owns (64-entry window minus 2 + 2 halo)
 constexpr int kTile2 = 56;  // the same for two steps per pass (4 + 4 halo)
+// scattered-field form: steps whose sources one launch computes (a power of 2)
+constexpr int kSourceSlots = 8;
+// scattered-field form: planes per work item of the step kernels over the
+// items meeting a source window
+constexpr int kSubPlanes = 4;
 // planes held ahead: register ring (float32 / float64) and shared-memory ring
 template <typename T>
 __host__ __device__ constexpr int ring_depth() { return sizeof(T) == 4 ? 3 : 2; }
@@ -121,6 +126,16 @@ struct RzArgs {
   int obs;
   double tw_er, tw_hp;
   double* WT;
+  // scattered-field form: the stored field is the total minus the incident
+  // TEM field; S [n mod kSourceSlots][mode][sc_len][pr * 6] is the step's
+  // source on planes n + sc_off .. n + sc_off + sc_len - 1 (null otherwise;
+  // in the scattered form J holds zeros)
+  const T* S;
+  long long sc_off;
+  int sc_len;
+  // work items [sc_lo, sc_hi) meet a source window: the kernels instantiated
+  // with SC take exactly those, the plain ones skip them
+  int sc_lo, sc_hi;
 };
 
 template <typename T>
@@ -286,7 +301,7 @@ struct Item {
 };
 
 template <typename T>
-__device__ __forceinline__ Item<T> item_of(const RzArgs<T>& a, int witem) {
+__device__ __forceinline__ Item<T> item_of(const RzArgs<T>& a, int witem, int sub = -1) {
   Item<T> it;
   const int lane = threadIdx.x & 31;
   it.mode = witem % a.n_modes;
@@ -295,6 +310,10 @@ __device__ __forceinline__ Item<T> item_of(const RzArgs<T>& a, int witem) {
   const int chunk = rest / a.tiles;
   it.k0 = chunk * a.chunk_z;
   it.k1 = min(it.k0 + a.chunk_z, a.L.nz);
+  if (sub >= 0) {  // planes sub * kSubPlanes .. of the chunk only
+    it.k0 += sub * kSubPlanes;
+    it.k1 = min(it.k0 + kSubPlanes, it.k1);
+  }
   it.gi = it.tile * a.tile_w - a.halo + 2 * lane;
   it.own = 2 * lane >= a.halo && 2 * lane < 64 - a.halo;
   it.src0 = a.b_on && it.gi == a.i0;
@@ -331,6 +350,19 @@ __device__ __forceinline__ T current_at(const RzArgs<T>& a, const Item<T>& it, b
   const long long dd = (long long)k - (a.n + a.kshift) + a.c0;
   return (dd >= -a.c0 && dd < a.c0) ? a.J[(long long)it.mode * 2 * a.c0 + dd + a.c0] : T(0);
 }
+// Scattered-field form: add the step's source to the new values of plane k
+// (all lanes; the window of planes is warp-uniform).
+template <typename T>
+__device__ __forceinline__ void add_source(const RzArgs<T>& a, const Item<T>& it, int k, T* out) {
+  if (!a.S) return;
+  const long long w = (long long)k - (a.n + a.sc_off);
+  if (w < 0 || w >= a.sc_len) return;
+  const T* p =
+      a.S + ((((a.n & (kSourceSlots - 1)) * a.n_modes + it.mode) * a.sc_len + w) * a.L.pr + a.L.col(it.gi)) * 6;
+#pragma unroll
+  for (int q = 0; q < 12; ++q) out[q] += p[q];
+}
+
 // Wake samples of plane k (Sec. 5): the path s = m dz meets e_z(k+1/2) and
 // h_phi(k+1/2) at time n+1/2 and e_r(k) at time n, n = k + m + c0. The
 // longitudinal wake takes e_z at the bunch ring; the radial transverse wake
@@ -355,9 +387,9 @@ __device__ __forceinline__ void gather_wake(const RzArgs<T>& a, const Item<T>& i
 }
 
 // --- register-ring variant ---------------------------------------------------
-template <typename T>
-__device__ __forceinline__ void rz_item_reg(const RzArgs<T>& a, int witem) {
-  const Item<T> it = item_of(a, witem);
+template <typename T, bool SC>
+__device__ __forceinline__ void rz_item_reg(const RzArgs<T>& a, int witem, int sub) {
+  const Item<T> it = item_of(a, witem, sub);
   const LaneCo<T> c = lane_coefs(a, it);
   const T mm = T(a.m_lo + it.mode);
   const long long RS = a.L.pr * 6;  // field elements per row
@@ -393,6 +425,7 @@ __device__ __forceinline__ void rz_item_reg(const RzArgs<T>& a, int witem) {
       T out[12], er_old[2];
       rz_plane(ring[u], ring[(u + 1) % R], c, mm, s, current_at(a, it, it.src0, k),
                current_at(a, it, it.src1, k), out, er_old);
+      if (SC) add_source(a, it, k, out);
       if (it.own && k >= it.k0) {
         st_pair(op + (long long)(k + 1) * RS, out);
         gather_wake(a, it, k, out, er_old);
@@ -402,12 +435,25 @@ __device__ __forceinline__ void rz_item_reg(const RzArgs<T>& a, int witem) {
   }
 }
 
-template <typename T>
+// SC: the instantiation for the work items [sc_lo, sc_hi) that meet a source
+// window of the scattered-field form; the plain one takes all others.
+template <typename T, bool SC>
 __global__ void __launch_bounds__(128, reg_min_blocks<T>()) rz_step_kernel(const RzArgs<T> a) {
-  const int nitems = a.n_work * a.n_modes;
   const int nwarps = (int)((gridDim.x * blockDim.x) >> 5);
-  for (int w = (int)((blockIdx.x * blockDim.x + threadIdx.x) >> 5); w < nitems; w += nwarps)
-    rz_item_reg<T>(a, w);
+  const int nsub = SC ? (a.chunk_z + kSubPlanes - 1) / kSubPlanes : 1;
+  const int hi = SC ? (a.sc_hi - a.sc_lo) * nsub : a.n_work * a.n_modes;
+  for (int w = (int)((blockIdx.x * blockDim.x + threadIdx.x) >> 5); w < hi; w += nwarps) {
+    // plain: every item outside [sc_lo, sc_hi); SC: the items inside, split
+    // into runs of kSubPlanes planes (more warps, shorter marches)
+    if (!SC && w >= a.sc_lo && w < a.sc_hi) continue;
+    const int it_w = SC ? a.sc_lo + w / nsub : w;
+    const int sub = SC ? w % nsub : -1;
+    if (SC) {
+      const int chunk = a.work[it_w / a.n_modes] / a.tiles;
+      if (chunk * a.chunk_z + sub * kSubPlanes >= a.L.nz) continue;
+    }
+    rz_item_reg<T, SC>(a, it_w, sub);
+  }
 }
 
 // --- asynchronous-copy variant ------------------------------------------------
@@ -434,10 +480,10 @@ constexpr size_t rz_async_warp_bytes() {
   return (size_t)async_depth<T>() * 32 * 12 * sizeof(T) + (size_t)async_depth<T>() * 64;
 }
 
-template <typename T>
-__device__ __forceinline__ void rz_item_async(const RzArgs<T>& a, int witem, unsigned char* wsm) {
+template <typename T, bool SC>
+__device__ __forceinline__ void rz_item_async(const RzArgs<T>& a, int witem, int sub, unsigned char* wsm) {
   const int lane = threadIdx.x & 31;
-  const Item<T> it = item_of(a, witem);
+  const Item<T> it = item_of(a, witem, sub);
   const LaneCo<T> c = lane_coefs(a, it);
   const T mm = T(a.m_lo + it.mode);
   const long long RS = a.L.pr * 6;
@@ -495,6 +541,7 @@ __device__ __forceinline__ void rz_item_async(const RzArgs<T>& a, int witem, uns
     T out[12], er_old[2];
     rz_plane(d0, d1, c, mm, s, current_at(a, it, it.src0, k), current_at(a, it, it.src1, k), out,
              er_old);
+    if (SC) add_source(a, it, k, out);
     if (it.own && k >= it.k0) {
       st_pair(op + (long long)(k + 1) * RS, out);
       gather_wake(a, it, k, out, er_old);
@@ -505,14 +552,25 @@ __device__ __forceinline__ void rz_item_async(const RzArgs<T>& a, int witem, uns
   __syncwarp();
 }
 
-template <typename T>
+template <typename T, bool SC>
 __global__ void __launch_bounds__(128) rz_step_async_kernel(const RzArgs<T> a) {
   extern __shared__ __align__(16) unsigned char rz_smem[];
   unsigned char* wsm = rz_smem + (size_t)(threadIdx.x >> 5) * rz_async_warp_bytes<T>();
-  const int nitems = a.n_work * a.n_modes;
   const int nwarps = (int)((gridDim.x * blockDim.x) >> 5);
-  for (int w = (int)((blockIdx.x * blockDim.x + threadIdx.x) >> 5); w < nitems; w += nwarps)
-    rz_item_async<T>(a, w, wsm);
+  const int nsub = SC ? (a.chunk_z + kSubPlanes - 1) / kSubPlanes : 1;
+  const int hi = SC ? (a.sc_hi - a.sc_lo) * nsub : a.n_work * a.n_modes;
+  for (int w = (int)((blockIdx.x * blockDim.x + threadIdx.x) >> 5); w < hi; w += nwarps) {
+    // plain: every item outside [sc_lo, sc_hi); SC: the items inside, split
+    // into runs of kSubPlanes planes (more warps, shorter marches)
+    if (!SC && w >= a.sc_lo && w < a.sc_hi) continue;
+    const int it_w = SC ? a.sc_lo + w / nsub : w;
+    const int sub = SC ? w % nsub : -1;
+    if (SC) {
+      const int chunk = a.work[it_w / a.n_modes] / a.tiles;
+      if (chunk * a.chunk_z + sub * kSubPlanes >= a.L.nz) continue;
+    }
+    rz_item_async<T, SC>(a, it_w, sub, wsm);
+  }
 }
 
 // --- bulk-copy variant -------------------------------------------------------
@@ -570,13 +628,13 @@ __device__ __forceinline__ bool mbar_wait(uint64_t* bar, unsigned parity) {
   return false;
 }
 
-template <typename T>
-__device__ __forceinline__ bool rz_item_bulk(const RzArgs<T>& a, int witem, unsigned char* wsm,
+template <typename T, bool SC>
+__device__ __forceinline__ bool rz_item_bulk(const RzArgs<T>& a, int witem, int sub, unsigned char* wsm,
                                              unsigned& phases) {
   constexpr int D = bulk_depth<T>();
   constexpr int WB = window_bytes<T>();
   const int lane = threadIdx.x & 31;
-  const Item<T> it = item_of(a, witem);
+  const Item<T> it = item_of(a, witem, sub);
   const LaneCo<T> c = lane_coefs(a, it);
   const T mm = T(a.m_lo + it.mode);
   const long long RS = a.L.pr * 6;
@@ -639,6 +697,7 @@ __device__ __forceinline__ bool rz_item_bulk(const RzArgs<T>& a, int witem, unsi
     T out[12], er_old[2];
     rz_plane(d0, d1, c, mm, s, current_at(a, it, it.src0, k), current_at(a, it, it.src1, k), out,
              er_old);
+    if (SC) add_source(a, it, k, out);
     if (it.own && k >= it.k0) {
       st_pair(op + (long long)(k + 1) * RS, out);
       gather_wake(a, it, k, out, er_old);
@@ -657,7 +716,7 @@ __device__ __forceinline__ bool rz_item_bulk(const RzArgs<T>& a, int witem, unsi
   return false;
 }
 
-template <typename T>
+template <typename T, bool SC>
 __global__ void __launch_bounds__(128) rz_step_bulk_kernel(const RzArgs<T> a) {
   extern __shared__ __align__(128) unsigned char rz_bulk_smem[];
   constexpr int D = bulk_depth<T>();
@@ -668,10 +727,21 @@ __global__ void __launch_bounds__(128) rz_step_bulk_kernel(const RzArgs<T> a) {
   asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
   __syncwarp();
   unsigned phases = 0;
-  const int nitems = a.n_work * a.n_modes;
   const int nwarps = (int)((gridDim.x * blockDim.x) >> 5);
-  for (int w = (int)((blockIdx.x * blockDim.x + threadIdx.x) >> 5); w < nitems; w += nwarps)
-    if (!rz_item_bulk<T>(a, w, wsm, phases)) return;
+  const int nsub = SC ? (a.chunk_z + kSubPlanes - 1) / kSubPlanes : 1;
+  const int hi = SC ? (a.sc_hi - a.sc_lo) * nsub : a.n_work * a.n_modes;
+  for (int w = (int)((blockIdx.x * blockDim.x + threadIdx.x) >> 5); w < hi; w += nwarps) {
+    // plain: every item outside [sc_lo, sc_hi); SC: the items inside, split
+    // into runs of kSubPlanes planes (more warps, shorter marches)
+    if (!SC && w >= a.sc_lo && w < a.sc_hi) continue;
+    const int it_w = SC ? a.sc_lo + w / nsub : w;
+    const int sub = SC ? w % nsub : -1;
+    if (SC) {
+      const int chunk = a.work[it_w / a.n_modes] / a.tiles;
+      if (chunk * a.chunk_z + sub * kSubPlanes >= a.L.nz) continue;
+    }
+    if (!rz_item_bulk<T, SC>(a, it_w, sub, wsm, phases)) return;
+  }
 }
 
 // --- two steps per pass (temporal blocking) -----------------------------------
@@ -684,13 +754,13 @@ __global__ void __launch_bounds__(128) rz_step_bulk_kernel(const RzArgs<T> a) {
 // 4 halo entries each side). Step 1 recomputes two planes before the chunk and
 // one after; step 2 recomputes one before. Both steps deposit their current;
 // each gathers its wake samples on the item's own planes.
-template <typename T>
-__device__ __forceinline__ bool rz_item_bulk2(const RzArgs<T>& a, int witem, unsigned char* wsm,
+template <typename T, bool SC>
+__device__ __forceinline__ bool rz_item_bulk2(const RzArgs<T>& a, int witem, int sub, unsigned char* wsm,
                                               unsigned& phases) {
   constexpr int D = bulk_depth<T>();
   constexpr int WB = window_bytes<T>();
   const int lane = threadIdx.x & 31;
-  const Item<T> it = item_of(a, witem);
+  const Item<T> it = item_of(a, witem, sub);
   const LaneCo<T> c = lane_coefs(a, it);
   const T mm = T(a.m_lo + it.mode);
   const long long RS = a.L.pr * 6;
@@ -762,6 +832,7 @@ __device__ __forceinline__ bool rz_item_bulk2(const RzArgs<T>& a, int witem, uns
     T er_old[2];
     rz_plane(d0, d1, c, mm, s1, current_at(a, it, it.src0, k), current_at(a, it, it.src1, k), y1.f,
              er_old);
+    if (SC) add_source(a, it, k, y1.f);
     y1.m = d0.m;
     if (k >= it.k0 && k < it.k1) gather_wake(a, it, k, y1.f, er_old);
     // step 2 at plane k - 1 (from step-1 planes k-1 and k)
@@ -777,6 +848,7 @@ __device__ __forceinline__ bool rz_item_bulk2(const RzArgs<T>& a, int witem, uns
       T y2[12], er_old2[2];
       rz_plane(y1prev, y1, c, mm, s2, current_at(a2, it, it.src0, k2), current_at(a2, it, it.src1, k2),
                y2, er_old2);
+      if (SC) add_source(a2, it, k2, y2);
       if (it.own && k2 >= it.k0) {
         st_pair(op + (long long)(k2 + 1) * RS, y2);
         gather_wake(a2, it, k2, y2, er_old2);
@@ -795,7 +867,7 @@ __device__ __forceinline__ bool rz_item_bulk2(const RzArgs<T>& a, int witem, uns
   return false;
 }
 
-template <typename T>
+template <typename T, bool SC>
 __global__ void __launch_bounds__(128, sizeof(T) == 4 ? 4 : 1) rz_step_bulk2_kernel(const RzArgs<T> a) {
   extern __shared__ __align__(128) unsigned char rz_bulk2_smem[];
   constexpr int D = bulk_depth<T>();
@@ -806,10 +878,203 @@ __global__ void __launch_bounds__(128, sizeof(T) == 4 ? 4 : 1) rz_step_bulk2_ker
   asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
   __syncwarp();
   unsigned phases = 0;
-  const int nitems = a.n_work * a.n_modes;
   const int nwarps = (int)((gridDim.x * blockDim.x) >> 5);
-  for (int w = (int)((blockIdx.x * blockDim.x + threadIdx.x) >> 5); w < nitems; w += nwarps)
-    if (!rz_item_bulk2<T>(a, w, wsm, phases)) return;
+  const int nsub = SC ? (a.chunk_z + kSubPlanes - 1) / kSubPlanes : 1;
+  const int hi = SC ? (a.sc_hi - a.sc_lo) * nsub : a.n_work * a.n_modes;
+  for (int w = (int)((blockIdx.x * blockDim.x + threadIdx.x) >> 5); w < hi; w += nwarps) {
+    // plain: every item outside [sc_lo, sc_hi); SC: the items inside, split
+    // into runs of kSubPlanes planes (more warps, shorter marches)
+    if (!SC && w >= a.sc_lo && w < a.sc_hi) continue;
+    const int it_w = SC ? a.sc_lo + w / nsub : w;
+    const int sub = SC ? w % nsub : -1;
+    if (SC) {
+      const int chunk = a.work[it_w / a.n_modes] / a.tiles;
+      if (chunk * a.chunk_z + sub * kSubPlanes >= a.L.nz) continue;
+    }
+    if (!rz_item_bulk2<T, SC>(a, it_w, sub, wsm, phases)) return;
+  }
+}
+
+// Scattered-field form. The incident field is the discrete TEM field of the
+// ring bunch in the entry pipe (the static start's field), continued along
+// the grid and moving one plane per step: at step n it is the static-start
+// field shifted by n planes, zero outside planes 0..nz-1. prof [mode][6][pr]
+// holds its transverse profile (the entry section's activity, the metric
+// zeros and the constant factors folded in; zero for e_z and h_z), G
+// [mode][glen] its longitudinal profile: e at plane k takes G[k - n + 1], h
+// takes G[k - n + 2]. prof == null: no incident field.
+struct RzIncident {
+  const double* prof;
+  const double* G;
+  int glen;
+  long long n;
+  RzLayout L;
+};
+
+__device__ __forceinline__ double inc_value(const RzIncident& x, int mode, int comp, int i, int k) {
+  if (!x.prof || k < 0 || k >= x.L.nz || i < 0 || i > x.L.nr || comp == kEZ || comp == kHZ) return 0.0;
+  const long long u = (long long)k - x.n + ((comp == kHR || comp == kHP) ? 2 : 1);
+  if (u < 0 || u >= x.glen) return 0.0;
+  return x.prof[((long long)mode * 6 + comp) * x.L.pr + x.L.col(i)] * x.G[(long long)mode * x.glen + u];
+}
+
+// Source of the scattered-field form for steps x.n .. x.n + n_steps - 1 on
+// the window planes n + sc_off .. n + sc_off + sc_len - 1. With the stored
+// field y = total - x (x^n the incident field) the step is y^{n+1} = F_0(y^n)
+// + S^n (F_0: one step of (24) in the grid's geometry without current), where
+// S^n = F(x^n) - x^{n+1} and F is the step with the bunch current. The
+// incident field solves the step of the continued entry pipe exactly,
+// x^{n+1} = F_pipe(x^n), except where the grid ends cut it off (planes 0 and
+// nz-1), so on the other planes S^n is evaluated as F(x^n) - F_pipe(x^n):
+// both by the step kernels' own per-plane routine, in the field precision, on
+// the synthesised incident field, once with the geometry's activity and once
+// with the entry section's. The two agree bit for bit wherever the activity
+// within the stencil's reach agrees, so S is an exact zero there, and the
+// rounding of S scales with the incident field at the wall, not with the
+// bunch's near field. One warp per (step, mode, radial tile, group of ch
+// planes); the plane before a group is recomputed for the new h of its
+// previous plane. A group none of whose rows k0-1..k1-1 differs from the
+// entry section within the tile's reach (differs[(k + 1) * s_tiles + tile])
+// and that holds no grid end writes zeros.
+template <typename T>
+__global__ void __launch_bounds__(128) rz_source_kernel(RzArgs<T> a, RzIncident x,
+                                                        const uint8_t* differs, int s_tiles, int ch,
+                                                        int n_groups, int n_steps, T* S) {
+  const int lane = threadIdx.x & 31;
+  const int nz = a.L.nz;
+  const long long nitems = (long long)n_steps * a.n_modes * s_tiles * n_groups;
+  const long long nwarps = ((long long)gridDim.x * blockDim.x) >> 5;
+  for (long long w = ((long long)blockIdx.x * blockDim.x + threadIdx.x) >> 5; w < nitems; w += nwarps) {
+    long long r = w;
+    const int grp = (int)(r % n_groups);
+    r /= n_groups;
+    const int tile = (int)(r % s_tiles);
+    r /= s_tiles;
+    const int mode = (int)(r % a.n_modes);
+    const long long n = x.n + r / a.n_modes;
+    const long long w0 = n + a.sc_off;
+    const long long k0l = max(w0 + (long long)grp * ch, 0LL);
+    const long long k1l = min(min(w0 + (long long)(grp + 1) * ch, w0 + a.sc_len), (long long)nz);
+    if (k0l >= k1l) continue;  // the same for every lane
+    const int k0 = (int)k0l, k1 = (int)k1l;
+    Item<T> it;
+    it.mode = mode;
+    it.tile = tile;
+    it.k0 = k0;
+    it.k1 = k1;
+    it.gi = tile * kTile - 2 + 2 * lane;
+    it.own = lane >= 1 && lane <= 30;
+    it.src0 = it.gi == a.i0;
+    it.src1 = it.gi + 1 == a.i0;
+    it.fbase = 0;
+    it.mbase = 0;
+    auto slot = [&](int k) {
+      return S + ((((n & (kSourceSlots - 1)) * a.n_modes + mode) * a.sc_len + (k - w0)) * a.L.pr +
+                  a.L.col(it.gi)) * 6;
+    };
+    bool any = k0 == 0 || k1 == nz;
+    for (int k = k0 - 1; k < k1; ++k) any = any || differs[(long long)(k + 1) * s_tiles + tile] != 0;
+    if (!any) {
+      if (it.own)
+        for (int k = k0; k < k1; ++k) {
+          T* p = slot(k);
+#pragma unroll
+          for (int q = 0; q < 12; ++q) p[q] = T(0);
+        }
+      continue;
+    }
+    const LaneCo<T> c = lane_coefs(a, it);
+    const T mm = T(a.m_lo + mode);
+    RzArgs<T> an = a;
+    an.n = n;
+    RzIncident xi = x, xo = x;
+    xi.n = n;
+    xo.n = n + 1;
+    // the entry section's activity bytes of the lane's two entries
+    const unsigned m_pipe =
+        (unsigned)a.mask[a.L.midx(it.gi, 1)] | ((unsigned)a.mask[a.L.midx(it.gi + 1, 1)] << 8);
+    auto synth = [&](int k, Pair6<T>& d) {
+#pragma unroll
+      for (int e = 0; e < 2; ++e)
+#pragma unroll
+        for (int comp = 0; comp < 6; ++comp) d.f[6 * e + comp] = (T)inc_value(xi, mode, comp, it.gi + e, k);
+      d.m = (unsigned)a.mask[a.L.midx(it.gi, k)] | ((unsigned)a.mask[a.L.midx(it.gi + 1, k)] << 8);
+    };
+    Pair6<T> d0, d1, p0, p1;
+    LaneState<T> sg, sp;
+    synth(k0 - 1, d0);
+#pragma unroll
+    for (int e = 0; e < 2; ++e) {
+      sg.er0[e] = sp.er0[e] = d0.f[6 * e + kER];
+      sg.ep0[e] = sp.ep0[e] = d0.f[6 * e + kEP];
+      sg.hr_p[e] = sp.hr_p[e] = T(0);
+      sg.hp_p[e] = sp.hp_p[e] = T(0);
+    }
+    for (int k = k0 - 1; k < k1; ++k) {
+      synth(k + 1, d1);
+      p0 = d0;
+      p0.m = m_pipe;
+      p1 = d1;
+      p1.m = m_pipe;
+      const T j0 = current_at(an, it, it.src0, k), j1 = current_at(an, it, it.src1, k);
+      T out[12], ref[12], er_old[2];
+      rz_plane(d0, d1, c, mm, sg, j0, j1, out, er_old);
+      rz_plane(p0, p1, c, mm, sp, j0, j1, ref, er_old);
+      if (it.own && k >= k0) {
+        const bool cut = k == 0 || k == nz - 1;  // the incident field cut off by a grid end
+        T* p = slot(k);
+#pragma unroll
+        for (int e = 0; e < 2; ++e)
+#pragma unroll
+          for (int comp = 0; comp < 6; ++comp) {
+            const T next = cut ? (T)inc_value(xo, mode, comp, it.gi + e, k) : ref[6 * e + comp];
+            p[6 * e + comp] = out[6 * e + comp] - next;
+          }
+      }
+      d0 = d1;
+    }
+  }
+}
+
+// Scattered-field form: per row (planes -1..nz) and source tile, whether the
+// row's activity bytes differ from the entry section's (plane 1) within the
+// tile's reach (its 60 entries and 4 more on each side)
+__global__ void rz_row_differs(const uint8_t* mask, RzLayout L, int s_tiles, uint8_t* out) {
+  const int row = blockIdx.x;
+  if (row > L.nz + 1) return;
+  for (int tile = 0; tile < s_tiles; ++tile) {
+    const long long lo = max((long long)tile * kTile - 4 + L.orr, 0LL);
+    const long long hi = min((long long)tile * kTile + kTile + 4 + L.orr, L.pr);
+    int d = 0;
+    for (long long col = lo + threadIdx.x; col < hi; col += blockDim.x)
+      d |= mask[row * L.pr + col] != mask[2 * L.pr + col];
+    d = __syncthreads_or(d);
+    if (threadIdx.x == 0) out[(long long)row * s_tiles + tile] = (uint8_t)(d != 0);
+  }
+}
+
+// Scattered-field form: entries of planes 1..nz-1 where the entry section
+// (plane 1) has an object that the geometry lacks
+__global__ void rz_row_not_covered(const uint8_t* mask, RzLayout L, unsigned long long* out) {
+  const long long total = (long long)(L.nz - 1) * L.pr;
+  unsigned long long c = 0;
+  for (long long q = (long long)blockIdx.x * blockDim.x + threadIdx.x; q < total;
+       q += (long long)gridDim.x * blockDim.x) {
+    const long long k = 1 + q / L.pr, col = q % L.pr;
+    c += (mask[2 * L.pr + col] & ~mask[(k + 1) * L.pr + col]) != 0;
+  }
+  for (int o = 16; o > 0; o >>= 1) c += __shfl_down_sync(0xffffffffu, c, o);
+  if ((threadIdx.x & 31) == 0 && c) atomicAdd(out, c);
+}
+
+// Add sign times the incident field to a canonical array of one component.
+__global__ void rz_canonical_add_inc(double* dst, RzIncident x, int mode, int comp, double sign) {
+  const long long n = (long long)(x.L.nr + 1) * (x.L.nz + 1);
+  for (long long q = (long long)blockIdx.x * blockDim.x + threadIdx.x; q < n;
+       q += (long long)gridDim.x * blockDim.x) {
+    const int i = (int)(q % (x.L.nr + 1)), k = (int)(q / (x.L.nr + 1));
+    dst[q] += sign * inc_value(x, mode, comp, i, k);
+  }
 }
 
 // Activity bits from the cell geometry (staircase; the rules of the
@@ -877,15 +1142,17 @@ __global__ void rz_to_canonical(const T* src, RzLayout L, int mode, int comp, do
   }
 }
 
+// (scattered-field form: the stored value is the given total minus the
+// incident field x)
 template <typename T>
 __global__ void rz_from_canonical(const double* src, RzLayout L, const uint8_t* mask, int mode,
-                                  int comp, const double* metric, T* dst) {
+                                  int comp, const double* metric, T* dst, RzIncident x) {
   const long long n = (long long)(L.nr + 1) * (L.nz + 1);
   for (long long q = (long long)blockIdx.x * blockDim.x + threadIdx.x; q < n;
        q += (long long)gridDim.x * blockDim.x) {
     const int i = (int)(q % (L.nr + 1)), k = (int)(q / (L.nr + 1));
     const bool act = ((mask[L.midx(i, k)] >> comp) & 1) && metric[i] != 0.0;
-    dst[L.fidx(mode, comp, i, k)] = act ? (T)src[q] : T(0);
+    dst[L.fidx(mode, comp, i, k)] = (T)((act ? src[q] : 0.0) - inc_value(x, mode, comp, i, k));
   }
 }
 
@@ -901,33 +1168,34 @@ constexpr int kEnergyThreads = 256;
 template <typename T>
 __global__ void __launch_bounds__(kEnergyThreads)
 rz_energy_partial(const T* f, RzLayout L, int mode, const uint8_t* mask, const double* metric,
-                  double alpha, double* partial) {
+                  double alpha, double* partial, RzIncident x) {
   const long long PR = L.pr;
   const long long n = (long long)(L.nr + 1) * (L.nz + 1);
   double acc = 0.0;
   for (long long q = (long long)blockIdx.x * blockDim.x + threadIdx.x; q < n;
        q += (long long)gridDim.x * blockDim.x) {
     const int i = (int)(q % (L.nr + 1)), k = (int)(q / (L.nr + 1));
-    const T* e = f + L.fidx(mode, 0, i, k);      // this entry's six components
-    const T* eR = e + 6;                          // entry (i+1, k)
-    const T* eL = e - 6;                          // entry (i-1, k)
-    const T* eU = e + 6 * PR;                     // entry (i, k+1)
+    // the field of entry (i + di, k + dk), plus the incident field in the
+    // scattered-field form
+    auto v = [&](int comp, int di, int dk) {
+      return (double)f[L.fidx(mode, comp, i + di, k + dk)] + inc_value(x, mode, comp, i + di, k + dk);
+    };
     const uint8_t m = mask[L.midx(i, k)];
     double w = 0.0;
     double c[6];
     for (int comp = 0; comp < 6; ++comp) {
       c[comp] = ((m >> comp) & 1) ? metric[comp * PR + i] : 0.0;
       if (c[comp] != 0.0) {
-        const double v = (double)e[comp];
-        w += 0.5 * v * v / c[comp];
+        const double val = v(comp, 0, 0);
+        w += 0.5 * val * val / c[comp];
       }
     }
-    const double ez = (double)e[kEZ], hz = (double)e[kHZ];
-    const double t1 = (double)eR[kEZ] - ez;
-    const double t2 = (double)eL[kHZ] - hz;
+    const double ez = v(kEZ, 0, 0), hz = v(kHZ, 0, 0);
+    const double t1 = v(kEZ, 1, 0) - ez;
+    const double t2 = v(kHZ, -1, 0) - hz;
     const double r = c[kHP] * t1 * t1 + c[kEP] * t2 * t2;
-    const double l = (double)e[kHP] * ((double)eU[kER] - (double)e[kER]) -
-                     (double)e[kHR] * ((double)eU[kEP] - (double)e[kEP]);
+    const double l = v(kHP, 0, 0) * (v(kER, 0, 1) - v(kER, 0, 0)) -
+                     v(kHR, 0, 0) * (v(kEP, 0, 1) - v(kEP, 0, 0));
     acc += w - 0.5 * alpha * alpha * r + alpha * l;
   }
   __shared__ double sh[kEnergyThreads / 32];
@@ -1046,9 +1314,58 @@ struct tetm_rz {
   long long kshift = 0;          // static start: head at plane step + kshift
   int tile_w = kTile;            // owned entries per window of the current work list
   double* WT = nullptr;          // [mode][nw]
+  // scattered-field form (tetm_rz_set_bunch_scattered)
+  bool scattered = false;
+  double* inc_prof = nullptr;    // [mode][6][pr]
+  double* inc_G = nullptr;       // [mode][inc_glen]
+  int inc_glen = 0;
+  void* S = nullptr;             // [kSourceSlots][mode][sc_len][pr * 6], field precision
+  long long sc_until = 0;        // sources are ready for steps below this one
+  std::vector<int> chunk_first;  // [n_chunks + 1]: first work-list entry of each chunk
+  void* Jzero = nullptr;         // the step kernels' current in the scattered form (zeros)
+  uint8_t* differs = nullptr;    // [nz + 2][s_tiles]: row k + 1 differs from the entry section
+  long long sc_off = 0;          // source window: planes n + sc_off .. + sc_len - 1
+  int sc_len = 0;
+  int s_tiles = 0;               // radial tiles (of 60 entries) the source covers
 };
 
 namespace {
+
+RzIncident rz_incident(const tetm_rz* s, long long n) {
+  RzIncident x;
+  x.prof = s->scattered ? s->inc_prof : nullptr;
+  x.G = s->inc_G;
+  x.glen = s->inc_glen;
+  x.n = n;
+  x.L = s->L;
+  return x;
+}
+
+constexpr int kSourcePlanes = 2;  // planes per source work item
+
+// Sources of the scattered-field form for steps s->step .. s->step + n_steps - 1.
+template <typename T>
+cudaError_t rz_launch_source(tetm_rz* s, int n_steps) {
+  RzArgs<T> a{};
+  a.L = s->L;
+  a.mask = s->mask;
+  a.coef = static_cast<const T*>(s->coef);
+  a.m_lo = s->g.m_lo;
+  a.n_modes = s->n_modes;
+  a.b_on = 1;
+  a.i0 = s->i0;
+  a.c0 = s->c0;
+  a.J = static_cast<const T*>(s->J);
+  a.kshift = s->kshift;
+  a.sc_off = s->sc_off;
+  a.sc_len = s->sc_len;
+  const int n_groups = (s->sc_len + kSourcePlanes - 1) / kSourcePlanes;
+  const long long items = (long long)n_steps * s->n_modes * s->s_tiles * n_groups;
+  const int blocks = (int)std::max(1LL, std::min((items + 3) / 4, (long long)4 * s->resident));
+  rz_source_kernel<T><<<blocks, 128, 0, s->st>>>(a, rz_incident(s, s->step), s->differs, s->s_tiles,
+                                                  kSourcePlanes, n_groups, n_steps, static_cast<T*>(s->S));
+  return cudaGetLastError();
+}
 
 template <typename T>
 int rz_launch_steps(tetm_rz* s, long long n) {
@@ -1069,7 +1386,10 @@ int rz_launch_steps(tetm_rz* s, long long n) {
   a.c0 = s->c0;
   a.m_min = s->m_min;
   a.nw = s->nw;
-  a.J = static_cast<const T*>(s->J);
+  a.J = static_cast<const T*>(s->scattered ? s->Jzero : s->J);
+  a.S = s->scattered ? static_cast<const T*>(s->S) : nullptr;
+  a.sc_off = s->sc_off;
+  a.sc_len = s->sc_len;
   a.W = s->W;
   a.inv_q = s->bunch ? 1.0 / s->q : 0.0;
   a.err = s->err;
@@ -1085,33 +1405,63 @@ int rz_launch_steps(tetm_rz* s, long long n) {
   }
   const int items = s->n_work * s->n_modes;
   const int blocks = std::max(1, std::min(s->resident, (items + 3) / 4));
+  // launches one step kernel over the plain items (SC = false) or over the
+  // items meeting a source window (SC = true)
+  auto launch = [&](bool sc, int steps, int nblocks) {
+    if (steps == 2) {
+      if (sc) rz_step_bulk2_kernel<T, true><<<nblocks, 128, 4 * rz_bulk_warp_bytes<T>(), s->st>>>(a);
+      else rz_step_bulk2_kernel<T, false><<<nblocks, 128, 4 * rz_bulk_warp_bytes<T>(), s->st>>>(a);
+    } else if (s->kernel == TETM_RZ_KERNEL_BULK || s->kernel == TETM_RZ_KERNEL_BULK2) {
+      if (sc) rz_step_bulk_kernel<T, true><<<nblocks, 128, 4 * rz_bulk_warp_bytes<T>(), s->st>>>(a);
+      else rz_step_bulk_kernel<T, false><<<nblocks, 128, 4 * rz_bulk_warp_bytes<T>(), s->st>>>(a);
+    } else if (s->kernel == TETM_RZ_KERNEL_ASYNC) {
+      if (sc) rz_step_async_kernel<T, true><<<nblocks, 128, 4 * rz_async_warp_bytes<T>(), s->st>>>(a);
+      else rz_step_async_kernel<T, false><<<nblocks, 128, 4 * rz_async_warp_bytes<T>(), s->st>>>(a);
+    } else {
+      if (sc) rz_step_kernel<T, true><<<nblocks, 128, 0, s->st>>>(a);
+      else rz_step_kernel<T, false><<<nblocks, 128, 0, s->st>>>(a);
+    }
+    return cudaGetLastError();
+  };
   for (long long t = 0; t < n; ++t) {
     a.in = static_cast<const T*>(s->set[s->cur]);
     a.out = static_cast<T*>(s->set[s->cur ^ 1]);
     a.n = s->step;
-    if (s->kernel == TETM_RZ_KERNEL_BULK2 && t + 1 < n) {  // two steps in one pass
-      if (items > 0) {
-        rz_step_bulk2_kernel<T><<<blocks, 128, 4 * rz_bulk_warp_bytes<T>(), s->st>>>(a);
-        cudaError_t e = cudaGetLastError();
+    const int p = (s->kernel == TETM_RZ_KERNEL_BULK2 && t + 1 < n) ? 2 : 1;  // steps in this pass
+    a.sc_lo = a.sc_hi = 0;
+    if (s->scattered) {
+      if (s->step + p > s->sc_until) {
+        // the sources of the next kSourceSlots steps in one launch (their
+        // slots were last read by passes queued before it)
+        cudaError_t e = rz_launch_source<T>(s, kSourceSlots);
         if (e != cudaSuccess) return rz_fail(e);
+        s->sc_until = s->step + kSourceSlots;
       }
-      s->cur ^= 1;
-      s->step += 2;
-      ++t;
-      continue;
+      // the items whose planes (with the recomputed ones: k0-2 .. k1) meet
+      // the windows [lo, hi) of this pass's steps: chunks c with
+      // (c+1) cz + 1 > lo and c cz - 2 < hi, a contiguous run of the work
+      // list (ordered by chunk)
+      const long long lo = s->step + s->sc_off, hi = s->step + p - 1 + s->sc_off + s->sc_len;
+      const long long cz = s->chunk_z;
+      const long long c_lo = lo >= 1 ? (lo - 1) / cz : 0;
+      const long long c_hi = std::min((long long)s->n_chunks, hi + 2 > 0 ? (hi + 2 + cz - 1) / cz : 0LL);
+      if (c_lo < c_hi) {
+        a.sc_lo = s->chunk_first[(size_t)c_lo] * s->n_modes;
+        a.sc_hi = s->chunk_first[(size_t)c_hi] * s->n_modes;
+      }
     }
     if (items > 0) {
-      if (s->kernel == TETM_RZ_KERNEL_BULK || s->kernel == TETM_RZ_KERNEL_BULK2)
-        rz_step_bulk_kernel<T><<<blocks, 128, 4 * rz_bulk_warp_bytes<T>(), s->st>>>(a);
-      else if (s->kernel == TETM_RZ_KERNEL_ASYNC)
-        rz_step_async_kernel<T><<<blocks, 128, 4 * rz_async_warp_bytes<T>(), s->st>>>(a);
-      else
-        rz_step_kernel<T><<<blocks, 128, 0, s->st>>>(a);
-      cudaError_t e = cudaGetLastError();
+      if (a.sc_hi > a.sc_lo) {
+        const int nsub = (s->chunk_z + kSubPlanes - 1) / kSubPlanes;
+        cudaError_t e = launch(true, p, std::max(1, std::min(blocks, ((a.sc_hi - a.sc_lo) * nsub + 3) / 4)));
+        if (e != cudaSuccess) return rz_fail(e);
+      }
+      cudaError_t e = launch(false, p, blocks);
       if (e != cudaSuccess) return rz_fail(e);
     }
     s->cur ^= 1;
-    s->step += 1;
+    s->step += p;
+    t += p - 1;
   }
   return TETM_OK;
 }
@@ -1124,24 +1474,33 @@ int rz_occupancy(tetm_rz* s) {
   if (e == cudaSuccess) e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
   const size_t smem = 4 * rz_async_warp_bytes<T>();
   if (e == cudaSuccess && smem > 48 * 1024)
-    e = cudaFuncSetAttribute(rz_step_async_kernel<T>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+    e = cudaFuncSetAttribute(rz_step_async_kernel<T, false>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                             (int)smem);
+  if (e == cudaSuccess && smem > 48 * 1024)
+    e = cudaFuncSetAttribute(rz_step_async_kernel<T, true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                              (int)smem);
   const size_t bsmem = 4 * rz_bulk_warp_bytes<T>();
   if (e == cudaSuccess && bsmem > 48 * 1024)
-    e = cudaFuncSetAttribute(rz_step_bulk_kernel<T>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+    e = cudaFuncSetAttribute(rz_step_bulk_kernel<T, false>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                              (int)bsmem);
   if (e == cudaSuccess && bsmem > 48 * 1024)
-    e = cudaFuncSetAttribute(rz_step_bulk2_kernel<T>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+    e = cudaFuncSetAttribute(rz_step_bulk_kernel<T, true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                             (int)bsmem);
+  if (e == cudaSuccess && bsmem > 48 * 1024)
+    e = cudaFuncSetAttribute(rz_step_bulk2_kernel<T, false>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                             (int)bsmem);
+  if (e == cudaSuccess && bsmem > 48 * 1024)
+    e = cudaFuncSetAttribute(rz_step_bulk2_kernel<T, true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                              (int)bsmem);
   if (e == cudaSuccess) {
     if (s->kernel == TETM_RZ_KERNEL_BULK2)
-      e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, rz_step_bulk2_kernel<T>, 128, bsmem);
+      e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, rz_step_bulk2_kernel<T, false>, 128, bsmem);
     else if (s->kernel == TETM_RZ_KERNEL_BULK)
-      e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, rz_step_bulk_kernel<T>, 128, bsmem);
+      e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, rz_step_bulk_kernel<T, false>, 128, bsmem);
     else if (s->kernel == TETM_RZ_KERNEL_ASYNC)
-      e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, rz_step_async_kernel<T>, 128, smem);
+      e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, rz_step_async_kernel<T, false>, 128, smem);
     else
-      e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, rz_step_kernel<T>, 128, 0);
+      e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, rz_step_kernel<T, false>, 128, 0);
   }
   if (e != cudaSuccess) return rz_fail(e);
   s->resident = std::max(1, sms * per_sm);
@@ -1173,7 +1532,9 @@ int rz_rebuild_work(tetm_rz* s) {
   if (e != cudaSuccess) return rz_fail(e);
   std::vector<int> w;
   long long processed = 0;
+  s->chunk_first.assign((size_t)s->n_chunks + 1, 0);
   for (int q = 0; q < nf; ++q) {
+    if (q % s->tiles == 0) s->chunk_first[(size_t)(q / s->tiles)] = (int)w.size();
     if (!fl[(size_t)q]) continue;
     w.push_back(q);
     const int tile = q % s->tiles, chunk = q / s->tiles;
@@ -1190,6 +1551,7 @@ int rz_rebuild_work(tetm_rz* s) {
     if (e != cudaSuccess) return rz_fail(e);
   }
   s->n_work = (int)w.size();
+  s->chunk_first[(size_t)s->n_chunks] = s->n_work;
   s->processed = processed * s->n_modes;
   s->work_dirty = false;
   return TETM_OK;
@@ -1425,7 +1787,16 @@ int tetm_rz_wake(tetm_rz* s, int32_t mode, double* out, int32_t cap, int32_t* n_
   return rz_read_wake(s, s->W, mode, out);
 }
 
-int tetm_rz_set_bunch_static(tetm_rz* s, double sigma, double q, int32_t i0, int32_t k_head) {
+}  // extern "C"
+
+namespace {
+
+// The entry pipe's TEM field of the ring bunch (static start and scattered
+// form): checks the arguments and that planes 1..K carry the activity bytes of
+// plane 1 (row: those bytes), solves every mode's radial potential psi
+// [mode][nr+1] and the longitudinal profile G [mode][K+4] (G[u+1]).
+int rz_tem_setup(tetm_rz* s, double sigma, double q, int i0, int k_head, std::vector<uint8_t>& row,
+                 std::vector<double>& psi, std::vector<double>& G) {
   if (!s) return TETM_E_ARG;
   if (s->step != 0 || s->bunch) return TETM_E_STATE;
   if (!(sigma > 0) || !isfinite(sigma)) return TETM_E_ARG;
@@ -1439,7 +1810,7 @@ int tetm_rz_set_bunch_static(tetm_rz* s, double sigma, double q, int32_t i0, int
   cudaError_t e = cudaMalloc(&dcount, sizeof(unsigned long long));
   if (e != cudaSuccess) return rz_fail(e);
   unsigned long long mism = 0;
-  std::vector<uint8_t> row((size_t)L.pr);
+  row.assign((size_t)L.pr, 0);
   e = cudaMemsetAsync(dcount, 0, sizeof(unsigned long long), s->st);
   if (e == cudaSuccess) {
     rz_row_mismatch<<<256, 256, 0, s->st>>>(s->mask, L, K, dcount);
@@ -1456,7 +1827,8 @@ int tetm_rz_set_bunch_static(tetm_rz* s, double sigma, double q, int32_t i0, int
   // eliminated without pivoting) and the longitudinal profile
   const int nn = s->g.nr + 1;
   const double eta0 = kMu0 * kC;
-  std::vector<double> psi((size_t)s->n_modes * nn, 0.0), G((size_t)s->n_modes * (K + 4), 0.0);
+  psi.assign((size_t)s->n_modes * nn, 0.0);
+  G.assign((size_t)s->n_modes * (K + 4), 0.0);
   std::vector<double> qc((size_t)(2 * c0));
   for (int d = -c0; d < c0; ++d) {
     const double lo = std::max((double)d * dz, -5.0 * sigma);
@@ -1503,7 +1875,25 @@ int tetm_rz_set_bunch_static(tetm_rz* s, double sigma, double q, int32_t i0, int
     for (int u = K - 1; u >= K - 2 * c0; --u)
       g[u + 1] = 2.0 * eta0 * (share * kC * qc[(size_t)(u - K + 2 * c0)] / dz) - g[u + 2];
   }
-  int rc = tetm_rz_set_bunch(s, sigma, q, i0);
+  return TETM_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+int tetm_rz_set_bunch_static(tetm_rz* s, double sigma, double q, int32_t i0, int32_t k_head) {
+  if (!s) return TETM_E_ARG;
+  if (s->step != 0 || s->bunch) return TETM_E_STATE;
+  std::vector<uint8_t> row;
+  std::vector<double> psi, G;
+  int rc = rz_tem_setup(s, sigma, q, i0, k_head, row, psi, G);
+  if (rc != TETM_OK) return rc;
+  const RzLayout& L = s->L;
+  const int K = k_head;
+  const double dr = s->g.dr, eta0 = kMu0 * kC;
+  cudaError_t e = cudaSuccess;
+  rc = tetm_rz_set_bunch(s, sigma, q, i0);
   if (rc != TETM_OK) return rc;
   double *dpsi = nullptr, *dg = nullptr;
   e = cudaMalloc(&dpsi, sizeof(double) * psi.size());
@@ -1524,6 +1914,105 @@ int tetm_rz_set_bunch_static(tetm_rz* s, double sigma, double q, int32_t i0, int
   cudaFree(dg);
   if (e != cudaSuccess) return rz_fail(e);
   s->kshift = K;
+  return TETM_OK;
+}
+
+int tetm_rz_set_bunch_scattered(tetm_rz* s, double sigma, double q, int32_t i0, int32_t k_head) {
+  if (!s) return TETM_E_ARG;
+  if (s->step != 0 || s->bunch) return TETM_E_STATE;
+  std::vector<uint8_t> row;
+  std::vector<double> psi, G;
+  int rc = rz_tem_setup(s, sigma, q, i0, k_head, row, psi, G);
+  if (rc != TETM_OK) return rc;
+  const RzLayout& L = s->L;
+  const int K = k_head;
+  const int nr = s->g.nr, nn = nr + 1;
+  const double dr = s->g.dr, eta0 = kMu0 * kC;
+  // the geometry holds every object of the entry section on planes 1..nz-1
+  // (the incident field then vanishes wherever the geometry is PEC)
+  unsigned long long* dcount = nullptr;
+  unsigned long long uncovered = 0;
+  cudaError_t e = cudaMalloc(&dcount, sizeof(unsigned long long));
+  if (e != cudaSuccess) return rz_fail(e);
+  e = cudaMemsetAsync(dcount, 0, sizeof(unsigned long long), s->st);
+  if (e == cudaSuccess) {
+    rz_row_not_covered<<<256, 256, 0, s->st>>>(s->mask, L, dcount);
+    e = cudaGetLastError();
+  }
+  if (e == cudaSuccess) e = cudaMemcpyAsync(&uncovered, dcount, sizeof(uncovered), cudaMemcpyDeviceToHost, s->st);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(s->st);
+  cudaFree(dcount);
+  if (e != cudaSuccess) return rz_fail(e);
+  if (uncovered) return TETM_E_ARG;
+  // the incident field's transverse profile (as the static start writes it)
+  const long long PR = L.pr;
+  std::vector<double> prof((size_t)s->n_modes * 6 * PR, 0.0);
+  int i_top = 0;
+  for (int mi = 0; mi < s->n_modes; ++mi) {
+    const int m = s->g.m_lo + mi;
+    const double* ps = psi.data() + (size_t)mi * nn;
+    for (int i = 0; i <= nr; ++i) {
+      double c[6];
+      rz_metric_row(s->g, m, i, c);
+      const uint8_t b = row[(size_t)L.col(i)];
+      auto act = [&](int comp) { return ((b >> comp) & 1) && c[comp] != 0.0; };
+      const double prp = i < nr ? ps[i + 1] - ps[i] : 0.0;
+      double* pr = prof.data() + (size_t)mi * 6 * PR + L.col(i);
+      pr[kER * PR] = act(kER) ? -prp : 0.0;
+      pr[kEP * PR] = act(kEP) ? -m * ps[i] : 0.0;
+      pr[kHP * PR] = act(kHP) ? ((i + 0.5) * dr / (dr * eta0)) * prp : 0.0;
+      pr[kHR * PR] = (act(kHR) && i > 0) ? -(dr / (i * dr * eta0)) * m * ps[i] : 0.0;
+      for (int comp = 0; comp < 6; ++comp)
+        if (pr[comp * PR] != 0.0) i_top = std::max(i_top, i);
+    }
+  }
+  const int c0 = (int)ceil(5.0 * sigma / s->g.dz - 1e-12);  // as tetm_rz_set_bunch
+  const int tiles60 = (nr + 1 + kTile - 1) / kTile;
+  const int s_tiles = std::min(tiles60, (i_top + 3 + kTile - 1) / kTile);  // the step reaches 2 entries out
+  const int sc_len = 2 * c0 + 3;
+  const size_t sbytes = (size_t)kSourceSlots * s->n_modes * sc_len * PR * 6 * s->esz;
+  const size_t dbytes = (size_t)(s->g.nz + 2) * s_tiles;
+  double *dprof = nullptr, *dG = nullptr;
+  void *dS = nullptr, *dJ0 = nullptr;
+  uint8_t* ddiff = nullptr;
+  const size_t jbytes = (size_t)s->n_modes * 2 * c0 * s->esz;
+  e = cudaMalloc(&dprof, sizeof(double) * prof.size());
+  if (e == cudaSuccess) e = cudaMalloc(&dG, sizeof(double) * G.size());
+  if (e == cudaSuccess) e = cudaMalloc(&dS, sbytes);
+  if (e == cudaSuccess) e = cudaMalloc(&ddiff, dbytes);
+  if (e == cudaSuccess) e = cudaMalloc(&dJ0, jbytes);
+  if (e == cudaSuccess) e = cudaMemsetAsync(dJ0, 0, jbytes, s->st);
+  if (e == cudaSuccess) e = cudaMemsetAsync(dS, 0, sbytes, s->st);
+  if (e == cudaSuccess) {
+    rz_row_differs<<<s->g.nz + 2, 256, 0, s->st>>>(s->mask, L, s_tiles, ddiff);
+    e = cudaGetLastError();
+  }
+  if (e == cudaSuccess)
+    e = cudaMemcpyAsync(dprof, prof.data(), sizeof(double) * prof.size(), cudaMemcpyHostToDevice, s->st);
+  if (e == cudaSuccess)
+    e = cudaMemcpyAsync(dG, G.data(), sizeof(double) * G.size(), cudaMemcpyHostToDevice, s->st);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(s->st);
+  rc = e == cudaSuccess ? tetm_rz_set_bunch(s, sigma, q, i0) : rz_fail(e);
+  if (rc != TETM_OK) {
+    cudaFree(dprof);
+    cudaFree(dG);
+    cudaFree(dS);
+    cudaFree(ddiff);
+    cudaFree(dJ0);
+    return rc;
+  }
+  s->inc_prof = dprof;
+  s->inc_G = dG;
+  s->S = dS;
+  s->differs = ddiff;
+  s->Jzero = dJ0;
+  s->s_tiles = s_tiles;
+  s->sc_off = (long long)K - 2 * c0 - 2;
+  s->sc_len = sc_len;
+  s->inc_glen = K + 4;
+  s->device_bytes += (long long)(sizeof(double) * (prof.size() + G.size()) + sbytes + dbytes + jbytes);
+  s->kshift = K;
+  s->scattered = true;
   return TETM_OK;
 }
 
@@ -1552,10 +2041,12 @@ int tetm_rz_energy(tetm_rz* s, int32_t mode, double* w) {
   const double* me = s->metric + (size_t)mode * 6 * s->L.pr + s->L.orr;
   if (s->esz == 8)
     rz_energy_partial<double><<<kEnergyBlocks, kEnergyThreads, 0, s->st>>>(
-        static_cast<const double*>(f), s->L, mode, s->mask, me, s->alpha, s->partial);
+        static_cast<const double*>(f), s->L, mode, s->mask, me, s->alpha, s->partial,
+        rz_incident(s, s->step));
   else
     rz_energy_partial<float><<<kEnergyBlocks, kEnergyThreads, 0, s->st>>>(
-        static_cast<const float*>(f), s->L, mode, s->mask, me, s->alpha, s->partial);
+        static_cast<const float*>(f), s->L, mode, s->mask, me, s->alpha, s->partial,
+        rz_incident(s, s->step));
   rz_energy_final<<<1, 32, 0, s->st>>>(s->partial, kEnergyBlocks, s->partial + kEnergyBlocks);
   cudaError_t e = cudaGetLastError();
   if (e == cudaSuccess)
@@ -1575,6 +2066,7 @@ int tetm_rz_get_fields(tetm_rz* s, int32_t mode, int32_t comp, double* out) {
     rz_to_canonical<double><<<512, 256, 0, s->st>>>(static_cast<const double*>(f), s->L, mode, comp, tmp);
   else
     rz_to_canonical<float><<<512, 256, 0, s->st>>>(static_cast<const float*>(f), s->L, mode, comp, tmp);
+  if (s->scattered) rz_canonical_add_inc<<<512, 256, 0, s->st>>>(tmp, rz_incident(s, s->step), mode, comp, 1.0);
   e = cudaGetLastError();
   if (e == cudaSuccess) e = cudaMemcpyAsync(out, tmp, sizeof(double) * n, cudaMemcpyDeviceToHost, s->st);
   cudaFreeAsync(tmp, s->st);
@@ -1594,10 +2086,10 @@ int tetm_rz_set_fields(tetm_rz* s, int32_t mode, int32_t comp, const double* in)
   if (e == cudaSuccess) {
     if (s->esz == 8)
       rz_from_canonical<double><<<512, 256, 0, s->st>>>(tmp, s->L, s->mask, mode, comp, me,
-                                                        static_cast<double*>(f));
+                                                        static_cast<double*>(f), rz_incident(s, s->step));
     else
       rz_from_canonical<float><<<512, 256, 0, s->st>>>(tmp, s->L, s->mask, mode, comp, me,
-                                                       static_cast<float*>(f));
+                                                       static_cast<float*>(f), rz_incident(s, s->step));
     e = cudaGetLastError();
   }
   cudaFreeAsync(tmp, s->st);
@@ -1659,6 +2151,11 @@ int tetm_rz_destroy(tetm_rz* s) {
   cudaFree(s->WT);
   cudaFree(s->partial);
   cudaFree(s->err);
+  cudaFree(s->inc_prof);
+  cudaFree(s->inc_G);
+  cudaFree(s->S);
+  cudaFree(s->differs);
+  cudaFree(s->Jzero);
   if (s->own) cudaStreamDestroy(s->own);
   cudaGetLastError();
   delete s;

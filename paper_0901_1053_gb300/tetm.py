@@ -46,7 +46,7 @@ EXPORTS = ("tetm_create", "tetm_set_bunch", "tetm_step", "tetm_sync", "tetm_wake
            "tetm_rz_energy", "tetm_rz_get_fields", "tetm_rz_set_fields", "tetm_rz_set_tiling",
            "tetm_rz_set_stream", "tetm_rz_get_info", "tetm_rz_bytes_needed", "tetm_rz_destroy",
            "tetm_rz_set_kernel", "tetm_rz_set_observer", "tetm_rz_transverse_wake",
-           "tetm_rz_set_bunch_static")
+           "tetm_rz_set_bunch_static", "tetm_rz_set_bunch_scattered")
 TETM_RZ_KERNEL_ASYNC = 0
 TETM_RZ_KERNEL_REGISTER = 1
 TETM_RZ_KERNEL_BULK = 2
@@ -139,6 +139,7 @@ def _load():
         "tetm_rz_set_kernel": (ctypes.c_int, [vp, i32]),
         "tetm_rz_set_observer": (ctypes.c_int, [vp, i32]),
         "tetm_rz_set_bunch_static": (ctypes.c_int, [vp, dbl, dbl, i32, i32]),
+        "tetm_rz_set_bunch_scattered": (ctypes.c_int, [vp, dbl, dbl, i32, i32]),
         "tetm_rz_transverse_wake": (ctypes.c_int, [vp, i32, vp, i32, ctypes.POINTER(i32),
                                                    ctypes.POINTER(dbl), ctypes.POINTER(dbl)]),
         "tetm_rz_get_info": (ctypes.c_int, [vp, ctypes.POINTER(tetm_rz_info)]),
@@ -472,6 +473,12 @@ class RzSolver:
     def set_bunch_static(self, sigma, charge, i0, k_head):
         _check(lib.tetm_rz_set_bunch_static(self.h, float(sigma), float(charge), int(i0), int(k_head)),
                "tetm_rz_set_bunch_static")
+
+    def set_bunch_scattered(self, sigma, charge, i0, k_head):
+        """The static start kept as scattered field: the stored field is the
+        total minus the moving TEM field of the entry section."""
+        _check(lib.tetm_rz_set_bunch_scattered(self.h, float(sigma), float(charge), int(i0),
+                                               int(k_head)), "tetm_rz_set_bunch_scattered")
 
     def transverse_wake(self, m):
         n = ctypes.c_int32()
