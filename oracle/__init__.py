@@ -60,6 +60,10 @@ def _load():
     lib.oracle_step_custom.argtypes = [vp, vp, vp, vp]
     lib.oracle_wake.restype = i
     lib.oracle_wake.argtypes = [vp, vp, i, ctypes.POINTER(i), dp, dp]
+    lib.oracle_set_observer.restype = i
+    lib.oracle_set_observer.argtypes = [vp, i, i]
+    lib.oracle_wake_extra.restype = i
+    lib.oracle_wake_extra.argtypes = [vp, i, vp, i]
     lib.oracle_energy.restype = d
     lib.oracle_energy.argtypes = [vp]
     lib.oracle_qbar_e.argtypes = [vp] + [vp] * 6
@@ -189,6 +193,27 @@ class Oracle:
         out = np.empty(n.value, dtype=np.float64)
         self.lib.oracle_wake(self.h, _ptr(out), n.value, None, None, None)
         return out, s0.value, ds.value
+
+    def set_observer(self, i, j):
+        """Observer line of the transverse wake (before the first step)."""
+        if self.lib.oracle_set_observer(self.h, int(i), int(j)) != 0:
+            raise ValueError("oracle_set_observer: bad argument or state")
+
+    def _extra(self, which):
+        n = len(self.wake()[0])
+        out = np.empty(n, dtype=np.float64)
+        if self.lib.oracle_wake_extra(self.h, int(which), _ptr(out), n) != 0:
+            raise RuntimeError("no bunch set")
+        return out
+
+    def transverse_wake(self):
+        """(W_x on the x-edge line (i+1/2, j), W_y on the y-edge line (i, j+1/2)),
+        (1/Q) sum (E_x - c mu0 H_y) dz and (1/Q) sum (E_y + c mu0 H_x) dz."""
+        return self._extra(0), self._extra(1)
+
+    def wake_at_observer(self):
+        """Longitudinal wakes on the node lines (i, j), (i+1, j), (i, j+1)."""
+        return self._extra(2), self._extra(3), self._extra(4)
 
     def bunch_info(self):
         c0, mn, mx = ctypes.c_int(), ctypes.c_int(), ctypes.c_int()

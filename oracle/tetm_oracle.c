@@ -53,6 +53,12 @@ typedef struct oracle {
   long step;            /* n of the state y^n = (u^{n-1/2}, v^n) */
   long kshift;          /* bunch head at plane step + kshift (0: cold start at the wall) */
   int vacuum;           /* no material arrays were given */
+  /* transverse wake on the observer line (io, jo): W_x on the x-edge line
+   * (io+1/2, jo), W_y on the y-edge line (io, jo+1/2); longitudinal wakes on
+   * the node lines (io, jo), (io+1, jo), (io, jo+1) */
+  int io, jo;
+  double *twx, *twy, *w00, *w10, *w01;
+  double *exo, *eyo;    /* e_x, e_y of the observer column before a step */
 } oracle_t;
 
 enum { EX = 0, EY, EZ, HX, HY, HZ };
@@ -155,6 +161,7 @@ void oracle_free(oracle_t *o) {
   if (!o) return;
   for (int c = 0; c < 6; ++c) { free(o->f[c]); free(o->m[c]); }
   free(o->jz); free(o->qcell); free(o->wake);
+  free(o->twx); free(o->twy); free(o->w00); free(o->w10); free(o->w01); free(o->exo); free(o->eyo);
   free(o);
 }
 
@@ -181,7 +188,18 @@ int oracle_set_bunch(oracle_t *o, double sigma, double q, int i0, int j0) {
   o->m_max = (int)ceil(15.0 * sigma / o->dz - 1e-12);
   free(o->qcell); free(o->wake);
   o->qcell = (double *)calloc((size_t)(2 * o->c0), sizeof(double));
-  o->wake = (double *)calloc((size_t)(o->m_max - o->m_min + 1), sizeof(double));
+  const size_t nw = (size_t)(o->m_max - o->m_min + 1);
+  o->wake = (double *)calloc(nw, sizeof(double));
+  free(o->twx); free(o->twy); free(o->w00); free(o->w10); free(o->w01); free(o->exo); free(o->eyo);
+  o->twx = (double *)calloc(nw, sizeof(double));
+  o->twy = (double *)calloc(nw, sizeof(double));
+  o->w00 = (double *)calloc(nw, sizeof(double));
+  o->w10 = (double *)calloc(nw, sizeof(double));
+  o->w01 = (double *)calloc(nw, sizeof(double));
+  o->exo = (double *)calloc((size_t)o->mz, sizeof(double));
+  o->eyo = (double *)calloc((size_t)o->mz, sizeof(double));
+  o->io = i0 < o->nx ? i0 : o->nx - 1;
+  o->jo = j0 < o->ny ? j0 : o->ny - 1;
   double lo = -5.0 * sigma, hi = 5.0 * sigma;
   for (int d = -o->c0; d < o->c0; ++d) {
     double a = d * o->dz, b = (d + 1) * o->dz;
@@ -254,22 +272,80 @@ static void wake_gather(oracle_t *o, long n) {
   }
 }
 
+/* Observer line of the transverse wake (before the first step). */
+int oracle_set_observer(oracle_t *o, int io, int jo) {
+  if (!o->has_bunch || o->step != 0 || io < 0 || jo < 0 || io >= o->nx || jo >= o->ny) return -1;
+  o->io = io;
+  o->jo = jo;
+  return 0;
+}
+
+static void keep_observer_e(oracle_t *o) {
+  for (long k = 0; k < o->mz; ++k) {
+    o->exo[k] = o->f[EX][idx(o, o->io, o->jo, k)];
+    o->eyo[k] = o->f[EY][idx(o, o->io, o->jo, k)];
+  }
+}
+
+/* Transverse wake (Sec. 5): W_perp(s) = (1/Q) * integral of the Lorentz
+ * force per charge (E + v x B)_perp on the test charge moving along +z at c,
+ * i.e. E_x - c B_y and E_y + c B_x. On the x-edge line (io+1/2, jo) the path
+ * meets e_x (edge length dx) at plane k at time n and h_y (dual edge length
+ * dy) at k+1/2 at time n+1/2, with the same n = k + m + c0 as the
+ * longitudinal wake; likewise e_y (dy) and h_x (dx) on the y-edge line
+ * (io, jo+1/2). B = mu0 H. Also the longitudinal wakes of the three node
+ * lines around the observer. e of time n was kept before the step. */
+static void transverse_gather(oracle_t *o, long n) {
+  const double eta0 = OR_MU0 * OR_C0;
+  for (int m = o->m_min; m <= o->m_max; ++m) {
+    long k = (n + o->kshift) - m - o->c0;
+    if (k < 0 || k >= o->nz) continue;
+    const long id = idx(o, o->io, o->jo, k);
+    o->twx[m - o->m_min] += o->dz / o->q * (o->exo[k] / o->dx - eta0 * o->f[HY][id] / o->dy);
+    o->twy[m - o->m_min] += o->dz / o->q * (o->eyo[k] / o->dy + eta0 * o->f[HX][id] / o->dx);
+    o->w00[m - o->m_min] -= o->f[EZ][id] / o->q;
+    o->w10[m - o->m_min] -= o->f[EZ][idx(o, o->io + 1, o->jo, k)] / o->q;
+    o->w01[m - o->m_min] -= o->f[EZ][idx(o, o->io, o->jo + 1, k)] / o->q;
+  }
+}
+
 /* Advance nsteps steps with the bunch current (if a bunch is set) and
- * accumulate the wake. */
+ * accumulate the wakes. */
 void oracle_step(oracle_t *o, int nsteps) {
   for (int s = 0; s < nsteps; ++s) {
-    if (o->has_bunch) oracle_current(o, o->step, o->jz);
+    if (o->has_bunch) {
+      oracle_current(o, o->step, o->jz);
+      keep_observer_e(o);
+    }
     oracle_step_j(o, o->has_bunch ? o->jz : NULL, NULL, NULL);
-    if (o->has_bunch) wake_gather(o, o->step);
+    if (o->has_bunch) {
+      wake_gather(o, o->step);
+      transverse_gather(o, o->step);
+    }
     o->step += 1;
   }
 }
 
-/* Same as oracle_step_j but also counts the step and gathers the wake. */
+/* Same as oracle_step_j but also counts the step and gathers the wakes. */
 void oracle_step_custom(oracle_t *o, const double *jz, const double *jx, const double *jy) {
+  if (o->has_bunch) keep_observer_e(o);
   oracle_step_j(o, jz, jx, jy);
-  if (o->has_bunch) wake_gather(o, o->step);
+  if (o->has_bunch) {
+    wake_gather(o, o->step);
+    transverse_gather(o, o->step);
+  }
   o->step += 1;
+}
+
+/* which: 0 W_x, 1 W_y, 2..4 the longitudinal wakes at (io, jo), (io+1, jo),
+ * (io, jo+1); same window as oracle_wake. */
+int oracle_wake_extra(const oracle_t *o, int which, double *out, int cap) {
+  if (!o->has_bunch || which < 0 || which > 4) return -1;
+  int nw = o->m_max - o->m_min + 1;
+  if (cap < nw) return -1;
+  const double *src[5] = {o->twx, o->twy, o->w00, o->w10, o->w01};
+  memcpy(out, src[which], sizeof(double) * (size_t)nw);
+  return 0;
 }
 
 int oracle_wake(const oracle_t *o, double *out, int cap, int *n_out, double *s0, double *ds) {

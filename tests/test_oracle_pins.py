@@ -618,3 +618,105 @@ def test_static_start_rejects_what_it_cannot_represent():
     eps = np.ones((nz, ny, nx))
     with pytest.raises(ValueError):
         Oracle(nx, ny, nz, DXY, DXY, MM, eps_r=eps, pec=pec).set_bunch_static(MM, 1e-9, 5, 5, 15)
+
+
+# ---------------------------------------------------------------------------
+# Transverse wake (Sec. 5: the dipole wake of off-axis bunches and deflecting
+# structures), W_perp = (1/Q) integral of (E + c z^ x B)_perp along the path.
+# The Panofsky-Wenzel theorem dW_perp/ds = grad_perp W_par holds exactly in
+# the scheme at c*dt = dz between W_x on the x-edge line (i+1/2, j) and the
+# longitudinal wakes on the node lines i and i+1, with the half-sample
+# average the staggering asks for (likewise W_y with the lines j and j+1):
+#   W_x(m+1) - W_x(m) = dz/dx * [(W_{i+1} - W_i)(m) + (W_{i+1} - W_i)(m+1)] / 2
+# ---------------------------------------------------------------------------
+
+def _cavity_box(nx, ny, nz, ic, jc, r_pipe, r_cav, k_lo, k_hi):
+    jj, ii = np.mgrid[0:ny, 0:nx]
+    pec = np.zeros((nz, ny, nx), np.uint8)
+    for k in range(nz):
+        r = r_cav if k_lo <= k < k_hi else r_pipe
+        pec[k] = ((ii + 0.5 - ic) ** 2 + (jj + 0.5 - jc) ** 2) > r * r
+    return pec
+
+
+@pytest.mark.parametrize("bunch,obs", [((6, 5), (5, 5)), ((5, 5), (5, 5)), ((5, 6), (4, 4)),
+                                       ((6, 4), (6, 6))])
+def test_discrete_panofsky_wenzel_3d(bunch, obs):
+    nx, ny, nz = 10, 10, 60
+    pec = _cavity_box(nx, ny, nz, 5, 5, 3.2, 4.4, 25, 35)
+    sigma = 2 * MM
+    o = Oracle(nx, ny, nz, DXY, DXY, MM, pec=pec)
+    o.set_bunch(sigma, 1e-9, *bunch)
+    o.set_observer(*obs)
+    c0 = math.ceil(5 * sigma / MM - 1e-12)
+    o.step(nz + 2 * c0 + math.ceil(15 * sigma / MM) + 2)
+    wx, wy = o.transverse_wake()
+    w00, w10, w01 = o.wake_at_observer()
+    for w, nb in ((wx, w10), (wy, w01)):
+        grad = (nb - w00) * (MM / DXY)
+        rhs = 0.5 * (grad[:-1] + grad[1:])
+        assert np.max(np.abs(rhs)) > 0
+        np.testing.assert_allclose(np.diff(w), rhs, rtol=0, atol=1e-12 * np.max(np.abs(rhs)))
+    if tuple(obs) == tuple(bunch):  # the default observer is the bunch line
+        np.testing.assert_array_equal(w00, o.wake()[0])
+
+
+def test_transverse_wake_mirror_antisymmetry():
+    """Geometry and bunch symmetric about the planes x = x_i0 and y = y_j0:
+    the x-edge lines i0 +- 1/2 are mirror images, so W_x there is equal and
+    opposite (likewise W_y on j0 +- 1/2)."""
+    nx = ny = 10
+    nz = 50
+    pec = _cavity_box(nx, ny, nz, 5, 5, 3.2, 4.4, 20, 30)
+    pec[20:30, 2, 1:4] = 1                       # a symmetric set of posts breaks the
+    pec[20:30, 2, 6:9] = 1                       # rotational symmetry, not the mirror ones
+    pec[20:30, 7, 1:4] = 1
+    pec[20:30, 7, 6:9] = 1
+    out = {}
+    for obs in ((5, 5), (4, 5), (5, 4)):
+        o = Oracle(nx, ny, nz, DXY, DXY, MM, pec=pec)
+        o.set_bunch(2 * MM, 1e-9, 5, 5)
+        o.set_observer(*obs)
+        o.step(nz + 20 + 30 + 2)
+        out[obs] = o.transverse_wake()
+    # W_x on (5 + 1/2, 5) mirrors W_x on (4 + 1/2, 5); W_y on (5, 5 + 1/2) mirrors (5, 4 + 1/2)
+    for c, mirror in ((0, (4, 5)), (1, (5, 4))):
+        a, b = out[(5, 5)][c], out[mirror][c]
+        assert np.max(np.abs(a)) > 0
+        np.testing.assert_allclose(a, -b, rtol=0, atol=1e-12 * np.max(np.abs(a)))
+
+
+def test_transverse_wake_of_the_static_tem_field_vanishes():
+    """The bunch's own discrete TEM field (static start) exerts no force on a
+    test charge moving with it: in a smooth pipe the transverse wake of an
+    off-axis bunch stays zero, while the cold start's entry transient gives
+    one."""
+    nx = ny = 14
+    nz = 90
+    pec = _round_pipe(nx, ny, nz, lambda k: np.full(k.shape, 5.5))
+    sigma, q, K = 3 * MM, 1e-9, 34
+    o = Oracle(nx, ny, nz, DXY, DXY, MM, pec=pec)
+    o.set_bunch_static(sigma, q, 8, 7, K)
+    o.set_observer(6, 7)
+    o.step(40)
+    cold = Oracle(nx, ny, nz, DXY, DXY, MM, pec=pec)
+    cold.set_bunch(sigma, q, 8, 7)
+    cold.set_observer(6, 7)
+    cold.step(40 + K)
+    for a, b in zip(o.transverse_wake(), cold.transverse_wake()):
+        assert np.max(np.abs(b)) > 0
+        assert np.max(np.abs(a)) <= 1e-13 * np.max(np.abs(b))
+
+
+def test_observer_arguments_and_state():
+    o = Oracle(6, 6, 20, DXY, DXY, MM)
+    with pytest.raises(ValueError):
+        o.set_observer(2, 2)                      # no bunch
+    o.set_bunch(MM, 1e-9, 3, 3)
+    for bad in ((-1, 2), (6, 2), (2, 6)):
+        with pytest.raises(ValueError):
+            o.set_observer(*bad)
+    o.set_observer(5, 5)
+    o.step(1)
+    with pytest.raises(ValueError):
+        o.set_observer(2, 2)                      # after the first step
