@@ -60,6 +60,9 @@ def parse_args():
                    help="rz: bunch start (cold: through the entry wall; static: with its TEM "
                         "field in the entry pipe; scattered: the static start with the "
                         "incident TEM field split off, default)")
+    p.add_argument("--check", action="store_true",
+                   help="Cartesian, float32: also run the full solve in float64 and report the "
+                        "error of the longitudinal and transverse wakes against it")
     p.add_argument("--rz-check", action="store_true",
                    help="rz, float32: also run the full solve in float64 (total-field static "
                         "start) and report every wake's error against it")
@@ -406,7 +409,7 @@ def run_tetm(args):
 
     e2e = None
     if not args.no_e2e:
-        steps_e2e = args.e2e_steps or full_steps
+        steps_e2e = args.e2e_steps or w.steps
         pinned = None
         if w.pec is not None:
             pinned = torch.empty(w.pec.shape, dtype=torch.uint8, pin_memory=True).numpy()
@@ -425,6 +428,7 @@ def run_tetm(args):
         wk2 = s2.wake()[0]
         out[:] = wk2
         t1 = time.perf_counter()
+        twx, twy = s2.transverse_wake()
         s2.close()
         e2e_s = dist.max(t1 - t0)
         e2e = {"value": world * w.cells * steps_e2e / e2e_s / 1e9, "unit": UNIT,
@@ -432,6 +436,21 @@ def run_tetm(args):
                "d2h_bytes_per_step": int(out.nbytes), "steps_per_call": steps_e2e,
                "seconds": round(e2e_s, 3),
                "call": "tetm_create(host pec) + tetm_set_bunch + tetm_step + tetm_wake(host)"}
+        if args.check and w.precision == "fp32" and steps_e2e == w.steps:
+            # the same full solve with float64 fields (default observer: the
+            # bunch line), every wake's error relative to its peak
+            r = tetm.Solver(w.nx, w.ny, w.nz, w.dx, w.dy, w.dz, w.cdt, "fp64", eps_r=args.eps,
+                            pec=w.pec)
+            r.set_bunch(w.sigma, w.charge, w.i0, w.j0)
+            r.step(steps_e2e)
+            rl = r.wake()[0]
+            rx, ry = r.transverse_wake()
+            r.close()
+
+            def rel(a, b):
+                return float(np.max(np.abs(a - b)) / np.max(np.abs(b)))
+            e2e["wake_error_vs_fp64"] = {"longitudinal": rel(wk2, rl), "transverse_x": rel(twx, rx),
+                                         "transverse_y": rel(twy, ry)}
 
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
@@ -459,7 +478,8 @@ def run_tetm(args):
                          cells_per_launch=proc),
         "cpu_baseline": cpu,
         "e2e": e2e,
-        "gpu_launches": (10 * K if args.kernel == "reference" else K) + 6 * n_bal,
+        # per step: the step kernel(s) and the transverse-wake gather
+        "gpu_launches": (11 * K if args.kernel == "reference" else 2 * K) + 6 * n_bal,
         "clocks": clk,
         "balances": {"records": int(hist.shape[0]),
                      "max_charge_residual_rel": float(np.max(hist[:, 2] / np.maximum(hist[:, 4], 1e-300)))

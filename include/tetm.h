@@ -148,6 +148,22 @@ int tetm_sync(tetm_solver* s);
  * first sample, *ds = dz. Any output pointer may be NULL. Synchronizes. */
 int tetm_wake(tetm_solver* s, double* out, int32_t cap, int32_t* n_out, double* s0, double* ds);
 
+/* Observer line of the transverse (dipole) wake W_perp = (1/Q) * integral of
+ * (E + c z^ x B)_perp along the test-charge path (Sec. 5), 0 <= i <= nx-1,
+ * 0 <= j <= ny-1; default the bunch line (i0, j0). Needs a bunch and step 0
+ * (TETM_E_STATE). */
+int tetm_set_observer(tetm_solver* s, int32_t i, int32_t j);
+
+/* Transverse wake [V/C] on the window of tetm_wake, accumulated in float64:
+ * wx = (1/Q) sum (E_x - c mu0 H_y) dz on the x-edge line (i + 1/2, j),
+ * from e_x of time n at plane k and h_y of time n+1/2 at k+1/2 (both met by
+ * the test charge at c*dt = dz); wy = (1/Q) sum (E_y + c mu0 H_x) dz on the
+ * y-edge line (i, j + 1/2), from e_y and h_x. E = e / (edge length), H = h /
+ * (dual edge length). Either output may be NULL; cap >= the window length
+ * (TETM_E_ARG), TETM_E_STATE without a bunch. Synchronizes. */
+int tetm_transverse_wake(tetm_solver* s, double* wx, double* wy, int32_t cap, int32_t* n_out,
+                         double* s0, double* ds);
+
 /* Release the solve and all its device memory. NULL-safe. */
 void tetm_destroy(tetm_solver* s);
 

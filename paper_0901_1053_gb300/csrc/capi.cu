@@ -298,6 +298,21 @@ StepArgs<T> tetm::step_args(tetm_solver* s, bool fused) {
   a.b.inv_q = s->bunch ? 1.0 / s->q : 0.0;
   a.b.J = (const T*)s->J;
   a.b.W = s->W;
+  {
+    const int nw = s->bunch ? s->m_max - s->m_min + 1 : 0;
+    const double eta0 = kMu0 * kC;
+    a.b.obs_i = s->obs_i;
+    a.b.obs_j = s->obs_j;
+    a.b.WX = s->bunch ? s->W + nw : nullptr;
+    a.b.WY = s->bunch ? s->W + 2 * nw : nullptr;
+    const double iq = s->bunch ? 1.0 / s->q : 0.0;
+    // E_x - c mu0 H_y and E_y + c mu0 H_x times dz/Q, with e = E * (edge
+    // length) and h = H * (dual edge length): dy for h_y, dx for h_x
+    a.b.tw_ex = s->g.dz * iq / s->g.dx;
+    a.b.tw_hy = -eta0 * s->g.dz * iq / s->g.dy;
+    a.b.tw_ey = s->g.dz * iq / s->g.dy;
+    a.b.tw_hx = eta0 * s->g.dz * iq / s->g.dx;
+  }
   a.tiles_x = s->tiles_x;
   a.tiles_y = s->tiles_y;
   a.chunk_z = s->chunk_z;
@@ -358,6 +373,7 @@ int do_steps(tetm_solver* s, int n) {
         else
           CK(launch_fused_step<T>(a, s->tile_x, s->tile_y, s->stream));
       }
+      if (s->bunch) CK(launch_transverse_after_step<T>(a, s->stream));
       s->cur = 1 - s->cur;
     } else {
       if (q == n - 1 || bal) {  // keep y^n beside y^{n+1} for the charge balance
@@ -668,7 +684,7 @@ int tetm_set_bunch(tetm_solver* s, double sigma_z, double charge, int32_t i0, in
   const int nw = m_max + c0 + 2;
   void* J = nullptr;
   double* W = nullptr;
-  if (cudaMalloc(&J, s->esz * qc.size()) != cudaSuccess || cudaMalloc(&W, sizeof(double) * nw) != cudaSuccess) {
+  if (cudaMalloc(&J, s->esz * qc.size()) != cudaSuccess || cudaMalloc(&W, 3 * sizeof(double) * nw) != cudaSuccess) {
     cudaFree(J); cudaFree(W);
     cudaGetLastError();
     return TETM_E_NOMEM;
@@ -683,18 +699,20 @@ int tetm_set_bunch(tetm_solver* s, double sigma_z, double charge, int32_t i0, in
     for (size_t q = 0; q < qc.size(); ++q) j[q] = (float)(kC * qc[q] / dz);
     if (cudaMemcpy(J, j.data(), sizeof(float) * j.size(), cudaMemcpyHostToDevice) != cudaSuccess) rc = TETM_E_CUDA;
   }
-  if (rc == TETM_OK && cudaMemset(W, 0, sizeof(double) * nw) != cudaSuccess) rc = TETM_E_CUDA;
+  if (rc == TETM_OK && cudaMemset(W, 0, 3 * sizeof(double) * nw) != cudaSuccess) rc = TETM_E_CUDA;
   if (rc != TETM_OK) {
     cudaFree(J); cudaFree(W);
     return rc;
   }
   s->J = J;
   s->W = W;
-  s->device_bytes += (long long)(s->esz * qc.size() + sizeof(double) * nw);
+  s->device_bytes += (long long)(s->esz * qc.size() + 3 * sizeof(double) * nw);
   s->qcell = qc;
   s->bunch = true;
   s->i0 = i0;
   s->j0 = j0;
+  s->obs_i = i0;
+  s->obs_j = j0;
   s->c0 = c0;
   s->m_min = -c0 - 1;
   s->m_max = m_max;
@@ -730,6 +748,30 @@ int tetm_wake(tetm_solver* s, double* out, int32_t cap, int32_t* n_out, double* 
     if (cap < nw) return TETM_E_ARG;
     CK(cudaMemcpyAsync(out, s->W, sizeof(double) * nw, cudaMemcpyDeviceToHost, s->stream));
   }
+  CK(cudaStreamSynchronize(s->stream));
+  return TETM_OK;
+}
+
+int tetm_set_observer(tetm_solver* s, int32_t i, int32_t j) {
+  if (!s) return TETM_E_ARG;
+  if (s->in_batch || !s->bunch || s->step != 0) return TETM_E_STATE;
+  if (i < 0 || i > s->g.nx - 1 || j < 0 || j > s->g.ny - 1) return TETM_E_ARG;
+  s->obs_i = i;
+  s->obs_j = j;
+  return TETM_OK;
+}
+
+int tetm_transverse_wake(tetm_solver* s, double* wx, double* wy, int32_t cap, int32_t* n_out, double* s0,
+                         double* ds) {
+  if (!s) return TETM_E_ARG;
+  if (!s->bunch) return TETM_E_STATE;
+  const int nw = s->m_max - s->m_min + 1;
+  if (n_out) *n_out = nw;
+  if (s0) *s0 = s->m_min * s->g.dz;
+  if (ds) *ds = s->g.dz;
+  if ((wx || wy) && cap < nw) return TETM_E_ARG;
+  if (wx) CK(cudaMemcpyAsync(wx, s->W + nw, sizeof(double) * nw, cudaMemcpyDeviceToHost, s->stream));
+  if (wy) CK(cudaMemcpyAsync(wy, s->W + 2 * nw, sizeof(double) * nw, cudaMemcpyDeviceToHost, s->stream));
   CK(cudaStreamSynchronize(s->stream));
   return TETM_OK;
 }
@@ -841,19 +883,20 @@ struct CkptHeader {
   int64_t count;
   int32_t bunch, nw;
   int64_t kshift;
+  int32_t obs_i, obs_j;
 };
 
 int tetm_save(tetm_solver* s, void* buf, size_t cap, size_t* used) {
   if (!s) return TETM_E_ARG;
   const int nw = s->bunch ? s->m_max - s->m_min + 1 : 0;
   const size_t fb = (size_t)s->L.count * s->esz;
-  const size_t need = sizeof(CkptHeader) + 6 * fb + sizeof(double) * (size_t)nw;
+  const size_t need = sizeof(CkptHeader) + 6 * fb + 3 * sizeof(double) * (size_t)nw;
   if (used) *used = need;
   if (!buf) return TETM_OK;
   if (cap < need) return TETM_E_ARG;
   CkptHeader h;
   memset(&h, 0, sizeof(h));
-  memcpy(h.magic, "TETMCKP2", 8);
+  memcpy(h.magic, "TETMCKP3", 8);
   h.nx = s->g.nx; h.ny = s->g.ny; h.nz = s->g.nz; h.precision = s->g.precision;
   h.dx = s->g.dx; h.dy = s->g.dy; h.dz = s->g.dz; h.cdt = s->g.cdt;
   h.step = s->step;
@@ -861,12 +904,14 @@ int tetm_save(tetm_solver* s, void* buf, size_t cap, size_t* used) {
   h.bunch = s->bunch;
   h.nw = nw;
   h.kshift = s->kshift;
+  h.obs_i = s->bunch ? s->obs_i : 0;
+  h.obs_j = s->bunch ? s->obs_j : 0;
   char* p = (char*)buf;
   memcpy(p, &h, sizeof(h));
   p += sizeof(h);
   for (int c = 0; c < 6; ++c, p += fb)
     CK(cudaMemcpyAsync(p, s->set[s->cur][c], fb, cudaMemcpyDeviceToHost, s->stream));
-  if (nw) CK(cudaMemcpyAsync(p, s->W, sizeof(double) * nw, cudaMemcpyDeviceToHost, s->stream));
+  if (nw) CK(cudaMemcpyAsync(p, s->W, 3 * sizeof(double) * nw, cudaMemcpyDeviceToHost, s->stream));
   CK(cudaStreamSynchronize(s->stream));
   return TETM_OK;
 }
@@ -878,16 +923,17 @@ int tetm_load(tetm_solver* s, const void* buf, size_t size) {
   memcpy(&h, buf, sizeof(h));
   const int nw = s->bunch ? s->m_max - s->m_min + 1 : 0;
   const size_t fb = (size_t)s->L.count * s->esz;
-  if (memcmp(h.magic, "TETMCKP2", 8) != 0 || h.nx != s->g.nx || h.ny != s->g.ny || h.nz != s->g.nz ||
+  if (memcmp(h.magic, "TETMCKP3", 8) != 0 || h.nx != s->g.nx || h.ny != s->g.ny || h.nz != s->g.nz ||
       h.precision != s->g.precision || h.count != s->L.count || h.bunch != (int)s->bunch || h.nw != nw ||
       h.dx != s->g.dx || h.dy != s->g.dy || h.dz != s->g.dz || h.cdt != s->g.cdt ||
       h.kshift != s->kshift)
     return TETM_E_ARG;
-  if (size < sizeof(CkptHeader) + 6 * fb + sizeof(double) * (size_t)nw) return TETM_E_ARG;
+  if (s->bunch && (h.obs_i != s->obs_i || h.obs_j != s->obs_j)) return TETM_E_ARG;
+  if (size < sizeof(CkptHeader) + 6 * fb + 3 * sizeof(double) * (size_t)nw) return TETM_E_ARG;
   const char* p = (const char*)buf + sizeof(h);
   for (int c = 0; c < 6; ++c, p += fb)
     CK(cudaMemcpyAsync(s->set[s->cur][c], p, fb, cudaMemcpyHostToDevice, s->stream));
-  if (nw) CK(cudaMemcpyAsync(s->W, p, sizeof(double) * nw, cudaMemcpyHostToDevice, s->stream));
+  if (nw) CK(cudaMemcpyAsync(s->W, p, 3 * sizeof(double) * nw, cudaMemcpyHostToDevice, s->stream));
   CK(cudaStreamSynchronize(s->stream));
   s->step = h.step;
   s->prev_valid = false;

@@ -18,6 +18,8 @@
 // which makes blocks independent: no block reads what another writes in the
 // same launch. A chunk starting at plane k0 recomputes the TM stage of plane
 // k0-1 (without storing it) for its first TE plane.
+#include <algorithm>
+
 #include "tetm_internal.h"
 
 namespace tetm {
@@ -33,6 +35,71 @@ __device__ __forceinline__ T coef_of(const Coefs<T>& co, int c, uint8_t m, long 
 // ---------------------------------------------------------------------------
 // Reference kernels
 // ---------------------------------------------------------------------------
+
+// Transverse wake of the reference path, between U5 and U6: e_x, e_y still
+// of time n, h_x, h_y already of time n+1/2; one thread per plane.
+template <typename T>
+__global__ void ref_transverse_gather(StepArgs<T> a) {
+  const int k = blockIdx.x * blockDim.x + threadIdx.x;
+  if (!a.b.on || k >= a.L.nz) return;
+  const long long id = a.L.idx(a.b.obs_i, a.b.obs_j, k);
+  gather_wx(a.b, a.n, k, a.out[kEX][id], a.out[kHY][id]);
+  gather_wy(a.b, a.n, k, a.out[kEY][id], a.out[kHX][id]);
+}
+
+}  // namespace
+
+// Transverse wake of a ping-pong step: after the step the input set still
+// holds e_x, e_y of time n and the output set h_x, h_y of time n+1/2, so one
+// small launch gathers the observer column and the step kernels carry no
+// extra registers for it. Threads stride over the planes.
+template <typename T>
+__device__ __forceinline__ void transverse_of_step(const StepArgs<T>& a, int k) {
+  const long long id = a.L.idx(a.b.obs_i, a.b.obs_j, k);
+  gather_wx(a.b, a.n, k, a.in[kEX][id], a.out[kHY][id]);
+  gather_wy(a.b, a.n, k, a.in[kEY][id], a.out[kHX][id]);
+}
+
+template <typename T>
+__global__ void transverse_after_step(StepArgs<T> a) {
+  if (!a.b.on) return;
+  for (int k = blockIdx.x * blockDim.x + threadIdx.x; k < a.L.nz; k += gridDim.x * blockDim.x)
+    transverse_of_step(a, k);
+}
+
+template <typename T>
+__global__ void transverse_after_batch_step(const BatchMember<T>* members) {
+  const BatchMember<T>& mb = members[blockIdx.y];
+  if (!mb.active || !mb.a.b.on) return;
+  for (int k = blockIdx.x * blockDim.x + threadIdx.x; k < mb.a.L.nz; k += gridDim.x * blockDim.x)
+    transverse_of_step(mb.a, k);
+}
+
+template <typename T>
+cudaError_t launch_transverse_after_step(const StepArgs<T>& a, cudaStream_t st) {
+  const int blocks = std::min(64, (a.L.nz + 127) / 128);
+  transverse_after_step<T><<<blocks, 128, 0, st>>>(a);
+  return cudaGetLastError();
+}
+
+template <typename T>
+cudaError_t launch_transverse_after_batch_step(const BatchMember<T>* members, int n_members, int nz_max,
+                                               cudaStream_t st) {
+  if (n_members <= 0) return cudaSuccess;
+  const dim3 grid(std::min(16, (nz_max + 127) / 128), n_members);
+  transverse_after_batch_step<T><<<grid, 128, 0, st>>>(members);
+  return cudaGetLastError();
+}
+
+template cudaError_t launch_transverse_after_step<float>(const StepArgs<float>&, cudaStream_t);
+template cudaError_t launch_transverse_after_step<double>(const StepArgs<double>&, cudaStream_t);
+template cudaError_t launch_transverse_after_batch_step<float>(const BatchMember<float>*, int, int,
+                                                                cudaStream_t);
+template cudaError_t launch_transverse_after_batch_step<double>(const BatchMember<double>*, int, int,
+                                                                 cudaStream_t);
+
+namespace {
+
 template <typename T, int C>
 __global__ void ref_update(StepArgs<T> a) {
   const int i = blockIdx.x * blockDim.x + threadIdx.x;
@@ -227,6 +294,7 @@ cudaError_t launch_reference_step(const StepArgs<T>& a, cudaStream_t st) {
   ref_update<T, kEZ><<<grd, blk, 0, st>>>(a);  // U3 (+ current, + wake)
   ref_update<T, kHX><<<grd, blk, 0, st>>>(a);  // U4
   ref_update<T, kHY><<<grd, blk, 0, st>>>(a);  // U5
+  if (a.b.on) ref_transverse_gather<T><<<(a.L.nz + 127) / 128, 128, 0, st>>>(a);
   ref_update<T, kEX><<<grd, blk, 0, st>>>(a);  // U6
   ref_update<T, kEY><<<grd, blk, 0, st>>>(a);  // U7
   ref_update<T, kHZ><<<grd, blk, 0, st>>>(a);  // U8

@@ -844,7 +844,7 @@ cudaError_t launch_fused_warp_step(const StepArgs<T>& a, int tx, int ty, cudaStr
 
 template <typename T>
 cudaError_t launch_fused_warp_batch(const BatchMember<T>* members, int n_members, const int2* work,
-                                    int n_work, int ty, cudaStream_t st) {
+                                    int n_work, int ty, int nz_max, cudaStream_t st) {
   cudaError_t e = cudaErrorInvalidValue;
   if constexpr (sizeof(T) == 8) {
     if (ty == 4) e = launch_batch_shape<T, 4, true>(members, work, n_work, st);
@@ -862,15 +862,17 @@ cudaError_t launch_fused_warp_batch(const BatchMember<T>* members, int n_members
     else if (ty == 28) e = launch_batch_shape<T, 28, false>(members, work, n_work, st);
   }
   if (e != cudaSuccess) return e;
+  e = launch_transverse_after_batch_step<T>(members, n_members, nz_max, st);
+  if (e != cudaSuccess) return e;
   batch_advance<T><<<(n_members + 127) / 128, 128, 0, st>>>(const_cast<BatchMember<T>*>(members),
                                                             n_members);
   return cudaGetLastError();
 }
 
 template cudaError_t launch_fused_warp_batch<float>(const BatchMember<float>*, int, const int2*, int,
-                                                    int, cudaStream_t);
+                                                    int, int, cudaStream_t);
 template cudaError_t launch_fused_warp_batch<double>(const BatchMember<double>*, int, const int2*,
-                                                     int, int, cudaStream_t);
+                                                     int, int, int, cudaStream_t);
 
 template cudaError_t launch_fused_warp_step<float>(const StepArgs<float>&, int, int, cudaStream_t);
 template cudaError_t launch_fused_warp_step<double>(const StepArgs<double>&, int, int, cudaStream_t);

@@ -50,7 +50,31 @@ struct BunchDev {
   double inv_q;         // 1/Q
   const T* J;           // J[d + c0] = c*Q_cell(d)/dz [A], d = -c0..c0-1
   double* W;            // W[m - m_min], float64 accumulators
+  // transverse wake on the observer line (obs_i, obs_j): W_x at the x-edge
+  // line (obs_i + 1/2, obs_j) from e_x^n and h_y^{n+1/2}, W_y at the y-edge
+  // line (obs_i, obs_j + 1/2) from e_y^n and h_x^{n+1/2}, float64
+  int obs_i, obs_j;
+  double tw_ex, tw_hy;  // W_x += tw_ex e_x + tw_hy h_y
+  double tw_ey, tw_hx;  // W_y += tw_ey e_y + tw_hx h_x
+  double* WX;           // [m - m_min]
+  double* WY;
 };
+
+// Transverse wake samples of plane k (step n -> n+1): W_x from the old e_x
+// and the new h_y of the x-edge at the observer line, W_y from the old e_y
+// and the new h_x of the y-edge; sample m = n + kshift - k - c0 as for W.
+template <typename T>
+__device__ __forceinline__ void gather_wx(const BunchDev<T>& b, long long n, int k, T ex_old, T hy_new) {
+  const long long mm = (n + b.kshift) - k - b.c0;
+  if (mm >= b.m_min && mm <= b.m_max)
+    b.WX[mm - b.m_min] += b.tw_ex * (double)ex_old + b.tw_hy * (double)hy_new;
+}
+template <typename T>
+__device__ __forceinline__ void gather_wy(const BunchDev<T>& b, long long n, int k, T ey_old, T hx_new) {
+  const long long mm = (n + b.kshift) - k - b.c0;
+  if (mm >= b.m_min && mm <= b.m_max)
+    b.WY[mm - b.m_min] += b.tw_ey * (double)ey_old + b.tw_hx * (double)hx_new;
+}
 
 // Per-component coefficients: either one constant per component with the
 // activity mask, or (material runs) one array per component.
@@ -100,7 +124,15 @@ bool warp_shape_ok(int tile_x, int tile_y);
 // then the device-side advance of all members
 template <typename T>
 cudaError_t launch_fused_warp_batch(const BatchMember<T>* members, int n_members, const int2* work,
-                                    int n_work, int tile_y, cudaStream_t st);
+                                    int n_work, int tile_y, int nz_max, cudaStream_t st);
+
+// transverse wake of a ping-pong step (kernels_step.cu): after the step
+// kernel, before the sets are swapped
+template <typename T>
+cudaError_t launch_transverse_after_step(const StepArgs<T>& a, cudaStream_t st);
+template <typename T>
+cudaError_t launch_transverse_after_batch_step(const BatchMember<T>* members, int n_members, int nz_max,
+                                               cudaStream_t st);
 
 // ---- diagnostics (kernels_diag.cu) ----------------------------------------
 struct DiagScratch {
@@ -170,7 +202,8 @@ struct tetm_solver {
   double sigma, q;
   std::vector<double> qcell;
   void* J;
-  double* W;
+  double* W;          // [3][nw]: W, then the transverse W_x, W_y
+  int obs_i, obs_j;   // observer line of the transverse wake (default i0, j0)
   double* qline;
   // periodic balances: records {n, W, max_e, max_h, q_scale}
   int bal_every;

@@ -38,6 +38,7 @@ COMPONENTS = ("ex", "ey", "ez", "hx", "hy", "hz")
 EXPORTS = ("tetm_create", "tetm_set_bunch", "tetm_step", "tetm_sync", "tetm_wake",
            "tetm_destroy", "tetm_energy", "tetm_charge_residual", "tetm_get_fields",
            "tetm_set_fields", "tetm_set_stream", "tetm_set_kernel", "tetm_set_tiling",
+           "tetm_set_observer", "tetm_transverse_wake",
            "tetm_get_info", "tetm_bytes_needed", "tetm_save", "tetm_load", "tetm_strerror",
            "tetm_set_balance_every", "tetm_balance_history", "tetm_energy_noalloc",
            "tetm_batch_create", "tetm_batch_step", "tetm_batch_sync", "tetm_batch_info",
@@ -100,6 +101,8 @@ def _load():
         "tetm_sync": (ctypes.c_int, [vp]),
         "tetm_wake": (ctypes.c_int, [vp, vp, i32, ctypes.POINTER(i32), ctypes.POINTER(dbl),
                                      ctypes.POINTER(dbl)]),
+        "tetm_set_observer": (ctypes.c_int, [vp, i32, i32]),
+        "tetm_transverse_wake": (ctypes.c_int, [vp, vp, vp, i32, vp, vp, vp]),
         "tetm_destroy": (None, [vp]),
         "tetm_energy": (ctypes.c_int, [vp, ctypes.POINTER(dbl)]),
         "tetm_charge_residual": (ctypes.c_int, [vp, ctypes.POINTER(dbl), ctypes.POINTER(dbl),
@@ -267,6 +270,21 @@ class Solver:
         out = np.empty(n.value, dtype=np.float64)
         _check(lib.tetm_wake(self.h, _ptr(out), n.value, None, None, None), "tetm_wake")
         return out, s0.value, ds.value
+
+    def set_observer(self, i, j):
+        """Observer line of the transverse wake (before the first step)."""
+        _check(lib.tetm_set_observer(self.h, int(i), int(j)), "tetm_set_observer")
+
+    def transverse_wake(self):
+        """(W_x on the x-edge line (i+1/2, j), W_y on the y-edge line (i, j+1/2)) [V/C]."""
+        n = ctypes.c_int32()
+        _check(lib.tetm_transverse_wake(self.h, None, None, 0, ctypes.byref(n), None, None),
+               "tetm_transverse_wake")
+        wx = np.empty(n.value, dtype=np.float64)
+        wy = np.empty(n.value, dtype=np.float64)
+        _check(lib.tetm_transverse_wake(self.h, _ptr(wx), _ptr(wy), n.value, None, None, None),
+               "tetm_transverse_wake")
+        return wx, wy
 
     def energy(self):
         w = ctypes.c_double()
