@@ -148,10 +148,11 @@ int tetm_sync(tetm_solver* s);
  * first sample, *ds = dz. Any output pointer may be NULL. Synchronizes. */
 int tetm_wake(tetm_solver* s, double* out, int32_t cap, int32_t* n_out, double* s0, double* ds);
 
-/* Observer line of the transverse (dipole) wake W_perp = (1/Q) * integral of
- * (E + c z^ x B)_perp along the test-charge path (Sec. 5), 0 <= i <= nx-1,
- * 0 <= j <= ny-1; default the bunch line (i0, j0). Needs a bunch and step 0
- * (TETM_E_STATE). */
+/* Turns on the transverse (dipole) wake W_perp = (1/Q) * integral of
+ * (E + c z^ x B)_perp along the test-charge path (Sec. 5) on the observer
+ * line through node (i, j), 0 <= i <= nx-1, 0 <= j <= ny-1 (pass i0, j0 for
+ * the bunch line). Each step then adds one small gather launch (none without
+ * an observer). Needs a bunch and step 0 (TETM_E_STATE). */
 int tetm_set_observer(tetm_solver* s, int32_t i, int32_t j);
 
 /* Transverse wake [V/C] on the window of tetm_wake, accumulated in float64:
@@ -160,7 +161,7 @@ int tetm_set_observer(tetm_solver* s, int32_t i, int32_t j);
  * the test charge at c*dt = dz); wy = (1/Q) sum (E_y + c mu0 H_x) dz on the
  * y-edge line (i, j + 1/2), from e_y and h_x. E = e / (edge length), H = h /
  * (dual edge length). Either output may be NULL; cap >= the window length
- * (TETM_E_ARG), TETM_E_STATE without a bunch. Synchronizes. */
+ * (TETM_E_ARG), TETM_E_STATE without a bunch or an observer. Synchronizes. */
 int tetm_transverse_wake(tetm_solver* s, double* wx, double* wy, int32_t cap, int32_t* n_out,
                          double* s0, double* ds);
 

@@ -62,8 +62,9 @@ int build_members(tetm_batch* b) {
 
 template <typename T>
 cudaError_t launch_one(tetm_batch* b) {
-  int nz_max = 0;
-  for (tetm_solver* s : b->members) nz_max = std::max(nz_max, s->g.nz);
+  int nz_max = 0;  // over the members that gather a transverse wake
+  for (tetm_solver* s : b->members)
+    if (s->bunch && s->obs_on) nz_max = std::max(nz_max, s->g.nz);
   return launch_fused_warp_batch<T>((const BatchMember<T>*)b->d_members, (int)b->members.size(),
                                     b->d_work, b->n_work, b->tile_y, nz_max, b->stream);
 }

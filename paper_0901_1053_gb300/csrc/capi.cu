@@ -301,6 +301,7 @@ StepArgs<T> tetm::step_args(tetm_solver* s, bool fused) {
   {
     const int nw = s->bunch ? s->m_max - s->m_min + 1 : 0;
     const double eta0 = kMu0 * kC;
+    a.b.obs_on = (s->bunch && s->obs_on) ? 1 : 0;
     a.b.obs_i = s->obs_i;
     a.b.obs_j = s->obs_j;
     a.b.WX = s->bunch ? s->W + nw : nullptr;
@@ -373,7 +374,7 @@ int do_steps(tetm_solver* s, int n) {
         else
           CK(launch_fused_step<T>(a, s->tile_x, s->tile_y, s->stream));
       }
-      if (s->bunch) CK(launch_transverse_after_step<T>(a, s->stream));
+      if (s->bunch && s->obs_on) CK(launch_transverse_after_step<T>(a, s->stream));
       s->cur = 1 - s->cur;
     } else {
       if (q == n - 1 || bal) {  // keep y^n beside y^{n+1} for the charge balance
@@ -711,6 +712,7 @@ int tetm_set_bunch(tetm_solver* s, double sigma_z, double charge, int32_t i0, in
   s->bunch = true;
   s->i0 = i0;
   s->j0 = j0;
+  s->obs_on = false;
   s->obs_i = i0;
   s->obs_j = j0;
   s->c0 = c0;
@@ -756,6 +758,7 @@ int tetm_set_observer(tetm_solver* s, int32_t i, int32_t j) {
   if (!s) return TETM_E_ARG;
   if (s->in_batch || !s->bunch || s->step != 0) return TETM_E_STATE;
   if (i < 0 || i > s->g.nx - 1 || j < 0 || j > s->g.ny - 1) return TETM_E_ARG;
+  s->obs_on = true;
   s->obs_i = i;
   s->obs_j = j;
   return TETM_OK;
@@ -764,7 +767,7 @@ int tetm_set_observer(tetm_solver* s, int32_t i, int32_t j) {
 int tetm_transverse_wake(tetm_solver* s, double* wx, double* wy, int32_t cap, int32_t* n_out, double* s0,
                          double* ds) {
   if (!s) return TETM_E_ARG;
-  if (!s->bunch) return TETM_E_STATE;
+  if (!s->bunch || !s->obs_on) return TETM_E_STATE;
   const int nw = s->m_max - s->m_min + 1;
   if (n_out) *n_out = nw;
   if (s0) *s0 = s->m_min * s->g.dz;
@@ -904,8 +907,8 @@ int tetm_save(tetm_solver* s, void* buf, size_t cap, size_t* used) {
   h.bunch = s->bunch;
   h.nw = nw;
   h.kshift = s->kshift;
-  h.obs_i = s->bunch ? s->obs_i : 0;
-  h.obs_j = s->bunch ? s->obs_j : 0;
+  h.obs_i = (s->bunch && s->obs_on) ? s->obs_i : -1;  // -1: no transverse wake
+  h.obs_j = (s->bunch && s->obs_on) ? s->obs_j : -1;
   char* p = (char*)buf;
   memcpy(p, &h, sizeof(h));
   p += sizeof(h);
@@ -928,7 +931,8 @@ int tetm_load(tetm_solver* s, const void* buf, size_t size) {
       h.dx != s->g.dx || h.dy != s->g.dy || h.dz != s->g.dz || h.cdt != s->g.cdt ||
       h.kshift != s->kshift)
     return TETM_E_ARG;
-  if (s->bunch && (h.obs_i != s->obs_i || h.obs_j != s->obs_j)) return TETM_E_ARG;
+  const int oi = (s->bunch && s->obs_on) ? s->obs_i : -1, oj = (s->bunch && s->obs_on) ? s->obs_j : -1;
+  if (h.obs_i != oi || h.obs_j != oj) return TETM_E_ARG;
   if (size < sizeof(CkptHeader) + 6 * fb + 3 * sizeof(double) * (size_t)nw) return TETM_E_ARG;
   const char* p = (const char*)buf + sizeof(h);
   for (int c = 0; c < 6; ++c, p += fb)

@@ -41,7 +41,7 @@ __device__ __forceinline__ T coef_of(const Coefs<T>& co, int c, uint8_t m, long 
 template <typename T>
 __global__ void ref_transverse_gather(StepArgs<T> a) {
   const int k = blockIdx.x * blockDim.x + threadIdx.x;
-  if (!a.b.on || k >= a.L.nz) return;
+  if (!a.b.obs_on || k >= a.L.nz) return;
   const long long id = a.L.idx(a.b.obs_i, a.b.obs_j, k);
   gather_wx(a.b, a.n, k, a.out[kEX][id], a.out[kHY][id]);
   gather_wy(a.b, a.n, k, a.out[kEY][id], a.out[kHX][id]);
@@ -62,7 +62,7 @@ __device__ __forceinline__ void transverse_of_step(const StepArgs<T>& a, int k) 
 
 template <typename T>
 __global__ void transverse_after_step(StepArgs<T> a) {
-  if (!a.b.on) return;
+  if (!a.b.obs_on) return;
   for (int k = blockIdx.x * blockDim.x + threadIdx.x; k < a.L.nz; k += gridDim.x * blockDim.x)
     transverse_of_step(a, k);
 }
@@ -70,7 +70,7 @@ __global__ void transverse_after_step(StepArgs<T> a) {
 template <typename T>
 __global__ void transverse_after_batch_step(const BatchMember<T>* members) {
   const BatchMember<T>& mb = members[blockIdx.y];
-  if (!mb.active || !mb.a.b.on) return;
+  if (!mb.active || !mb.a.b.obs_on) return;
   for (int k = blockIdx.x * blockDim.x + threadIdx.x; k < mb.a.L.nz; k += gridDim.x * blockDim.x)
     transverse_of_step(mb.a, k);
 }
@@ -85,7 +85,7 @@ cudaError_t launch_transverse_after_step(const StepArgs<T>& a, cudaStream_t st) 
 template <typename T>
 cudaError_t launch_transverse_after_batch_step(const BatchMember<T>* members, int n_members, int nz_max,
                                                cudaStream_t st) {
-  if (n_members <= 0) return cudaSuccess;
+  if (n_members <= 0 || nz_max <= 0) return cudaSuccess;  // no member gathers a transverse wake
   const dim3 grid(std::min(16, (nz_max + 127) / 128), n_members);
   transverse_after_batch_step<T><<<grid, 128, 0, st>>>(members);
   return cudaGetLastError();
@@ -294,7 +294,7 @@ cudaError_t launch_reference_step(const StepArgs<T>& a, cudaStream_t st) {
   ref_update<T, kEZ><<<grd, blk, 0, st>>>(a);  // U3 (+ current, + wake)
   ref_update<T, kHX><<<grd, blk, 0, st>>>(a);  // U4
   ref_update<T, kHY><<<grd, blk, 0, st>>>(a);  // U5
-  if (a.b.on) ref_transverse_gather<T><<<(a.L.nz + 127) / 128, 128, 0, st>>>(a);
+  if (a.b.obs_on) ref_transverse_gather<T><<<(a.L.nz + 127) / 128, 128, 0, st>>>(a);
   ref_update<T, kEX><<<grd, blk, 0, st>>>(a);  // U6
   ref_update<T, kEY><<<grd, blk, 0, st>>>(a);  // U7
   ref_update<T, kHZ><<<grd, blk, 0, st>>>(a);  // U8

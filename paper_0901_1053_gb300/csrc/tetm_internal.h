@@ -53,6 +53,7 @@ struct BunchDev {
   // transverse wake on the observer line (obs_i, obs_j): W_x at the x-edge
   // line (obs_i + 1/2, obs_j) from e_x^n and h_y^{n+1/2}, W_y at the y-edge
   // line (obs_i, obs_j + 1/2) from e_y^n and h_x^{n+1/2}, float64
+  int obs_on;           // the transverse wake is gathered (an observer was set)
   int obs_i, obs_j;
   double tw_ex, tw_hy;  // W_x += tw_ex e_x + tw_hy h_y
   double tw_ey, tw_hx;  // W_y += tw_ey e_y + tw_hx h_x
@@ -203,7 +204,8 @@ struct tetm_solver {
   std::vector<double> qcell;
   void* J;
   double* W;          // [3][nw]: W, then the transverse W_x, W_y
-  int obs_i, obs_j;   // observer line of the transverse wake (default i0, j0)
+  bool obs_on;        // transverse wake gathered (tetm_set_observer was called)
+  int obs_i, obs_j;   // its observer line
   double* qline;
   // periodic balances: records {n, W, max_e, max_h, q_scale}
   int bal_every;

@@ -4,12 +4,12 @@ the y-edge line (i, j+1/2) of the observer, against the FP64 oracle
 (oracle/tetm_oracle.c), whose definition is pinned by the exact discrete
 Panofsky-Wenzel relation in tests/test_oracle_pins.py.
 
-Every kernel path gathers them: the reference updates (a gather between U5
-and U6), the block-tiled kernel, the three warp-tiled sweeps (float64
-asynchronous-copy ring, register ring, per-entry coefficients) and the
-batched launch. Observers on tile boundaries check which lane and row own
-the sample. Tolerances as for the longitudinal wake: 1e-12 of the peak in
-float64, 1e-4 in float32."""
+Every kernel path is covered: the reference updates (a gather between U5
+and U6) and, after a ping-pong step of the block-tiled kernel, the three
+warp-tiled sweeps (float64 asynchronous-copy ring, register ring, per-entry
+coefficients) or a batch, one gather launch over the observer column. The
+wake is gathered once an observer is set. Tolerances as for the
+longitudinal wake: 1e-12 of the peak in float64, 1e-4 in float32."""
 import math
 
 import numpy as np
@@ -182,6 +182,10 @@ def test_checkpoint_carries_the_transverse_wake(tetm):
     with pytest.raises(tetm.TetmError) as e:
         c.load(buf)
     assert e.value.code == tetm.TETM_E_ARG
+    d = tetm.Solver.from_workload(w)            # no observer at all
+    with pytest.raises(tetm.TetmError) as e:
+        d.load(buf)
+    assert e.value.code == tetm.TETM_E_ARG
 
 
 def test_observer_arguments_and_state(tetm):
@@ -194,6 +198,9 @@ def test_observer_arguments_and_state(tetm):
         s.transverse_wake()
     assert e.value.code == tetm.TETM_E_STATE
     s.set_bunch(w.sigma, w.charge, w.i0, w.j0)
+    with pytest.raises(tetm.TetmError) as e:
+        s.transverse_wake()                        # not turned on (no observer)
+    assert e.value.code == tetm.TETM_E_STATE
     for bad in ((-1, 3), (w.nx, 3), (3, w.ny)):
         with pytest.raises(tetm.TetmError) as e:
             s.set_observer(*bad)
