@@ -41,6 +41,11 @@ extern "C" {
 #define TETM_RZ_HZ 5
 
 #define TETM_RZ_MAX_MODES 64
+/* Polls of an mbarrier after which the bulk-copy step kernels give up on a
+ * copy, raise the error word and drain (tetm_rz_sync then reports
+ * TETM_E_TIMEOUT); a poll suspends for a few microseconds, so the limit is
+ * about one second. */
+#define TETM_RZ_MAX_POLLS (1 << 18)
 
 /* step kernels (same results bit for bit; they differ in how loads run ahead
  * and in how many steps one pass over the fields takes) */
@@ -122,6 +127,13 @@ int tetm_rz_set_bunch_static(tetm_rz* s, double sigma, double q, int32_t i0, int
  * memory: eight source windows of 2*c0 + 3 planes of all modes (the sources
  * of eight steps are computed per launch). Synchronizes. */
 int tetm_rz_set_bunch_scattered(tetm_rz* s, double sigma, double q, int32_t i0, int32_t k_head);
+
+/* Failure-detection self-test (no solve needed): one warp waits, with the
+ * bulk-copy kernels' bounded poll loop, on an mbarrier that nothing ever
+ * completes; after polls polls (1 .. 2^26, else TETM_E_ARG) it raises a
+ * device error word, which this call reads: TETM_E_TIMEOUT is the expected
+ * result, and the context stays usable. Synchronizes (default stream). */
+int tetm_rz_selftest_wait(int32_t polls);
 
 /* Queues n steps of Eq. (24) for every mode (n >= 0). */
 int tetm_rz_step(tetm_rz* s, int64_t n);

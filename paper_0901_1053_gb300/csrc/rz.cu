@@ -582,7 +582,7 @@ __global__ void __launch_bounds__(128) rz_step_async_kernel(const RzArgs<T> a) {
 // every lane waits on the slot's mbarrier phase (bounded: after kMaxPolls
 // polls the kernel raises the error word and stops) and reads its own 48 /
 // 96 bytes. The ring runs bulk_depth planes ahead without registers.
-constexpr int kMaxPolls = 1 << 22;
+constexpr int kMaxPolls = TETM_RZ_MAX_POLLS;
 constexpr int kMaskBlock = 80;
 
 template <typename T>
@@ -622,10 +622,25 @@ __device__ __forceinline__ bool mbar_try_wait(uint64_t* bar, unsigned parity) {
 }
 
 // Returns false when the wait gave up.
-__device__ __forceinline__ bool mbar_wait(uint64_t* bar, unsigned parity) {
-  for (int it = 0; it < kMaxPolls; ++it)
+__device__ __forceinline__ bool mbar_wait_n(uint64_t* bar, unsigned parity, int polls) {
+  for (int it = 0; it < polls; ++it)
     if (mbar_try_wait(bar, parity)) return true;
   return false;
+}
+__device__ __forceinline__ bool mbar_wait(uint64_t* bar, unsigned parity) {
+  return mbar_wait_n(bar, parity, kMaxPolls);
+}
+
+// Bounded-wait self-test: one warp waits with the step kernels' poll loop on
+// an mbarrier that nothing arrives at (a copy that never lands), gives up
+// after `polls` polls and raises the error word, as a step kernel would.
+__global__ void rz_selftest_wait_kernel(int polls, int* err) {
+  __shared__ uint64_t bar;
+  if (threadIdx.x == 0) mbar_init(&bar, 1);
+  asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+  __syncwarp();
+  const bool ok = mbar_wait_n(&bar, 0, polls);
+  if (!__all_sync(0xffffffffu, ok) && threadIdx.x == 0) atomicExch(err, 1);
 }
 
 template <typename T, bool SC>
@@ -2014,6 +2029,23 @@ int tetm_rz_set_bunch_scattered(tetm_rz* s, double sigma, double q, int32_t i0, 
   s->kshift = K;
   s->scattered = true;
   return TETM_OK;
+}
+
+int tetm_rz_selftest_wait(int32_t polls) {
+  if (polls < 1 || polls > (1 << 26)) return TETM_E_ARG;
+  int* err = nullptr;
+  cudaError_t e = cudaMalloc(&err, sizeof(int));
+  if (e != cudaSuccess) return rz_fail(e);
+  int flag = 0;
+  e = cudaMemset(err, 0, sizeof(int));
+  if (e == cudaSuccess) {
+    rz_selftest_wait_kernel<<<1, 32>>>(polls, err);
+    e = cudaGetLastError();
+  }
+  if (e == cudaSuccess) e = cudaMemcpy(&flag, err, sizeof(int), cudaMemcpyDeviceToHost);
+  cudaFree(err);
+  if (e != cudaSuccess) return rz_fail(e);
+  return flag ? TETM_E_TIMEOUT : TETM_OK;
 }
 
 int tetm_rz_set_observer(tetm_rz* s, int32_t obs) {

@@ -47,7 +47,7 @@ EXPORTS = ("tetm_create", "tetm_set_bunch", "tetm_step", "tetm_sync", "tetm_wake
            "tetm_rz_energy", "tetm_rz_get_fields", "tetm_rz_set_fields", "tetm_rz_set_tiling",
            "tetm_rz_set_stream", "tetm_rz_get_info", "tetm_rz_bytes_needed", "tetm_rz_destroy",
            "tetm_rz_set_kernel", "tetm_rz_set_observer", "tetm_rz_transverse_wake",
-           "tetm_rz_set_bunch_static", "tetm_rz_set_bunch_scattered")
+           "tetm_rz_set_bunch_static", "tetm_rz_set_bunch_scattered", "tetm_rz_selftest_wait")
 TETM_RZ_KERNEL_ASYNC = 0
 TETM_RZ_KERNEL_REGISTER = 1
 TETM_RZ_KERNEL_BULK = 2
@@ -143,6 +143,7 @@ def _load():
         "tetm_rz_set_observer": (ctypes.c_int, [vp, i32]),
         "tetm_rz_set_bunch_static": (ctypes.c_int, [vp, dbl, dbl, i32, i32]),
         "tetm_rz_set_bunch_scattered": (ctypes.c_int, [vp, dbl, dbl, i32, i32]),
+        "tetm_rz_selftest_wait": (ctypes.c_int, [i32]),
         "tetm_rz_transverse_wake": (ctypes.c_int, [vp, i32, vp, i32, ctypes.POINTER(i32),
                                                    ctypes.POINTER(dbl), ctypes.POINTER(dbl)]),
         "tetm_rz_get_info": (ctypes.c_int, [vp, ctypes.POINTER(tetm_rz_info)]),
@@ -544,3 +545,9 @@ class RzSolver:
         c = best[1] if best else 32
         self.set_tiling(c)
         return c
+
+
+def rz_selftest_wait(polls):
+    """Bounded-wait self-test (tetm_rz_selftest_wait): returns the status code,
+    TETM_E_TIMEOUT when the wait gave up as designed."""
+    return int(lib.tetm_rz_selftest_wait(int(polls)))
