@@ -52,6 +52,9 @@ def parse_args():
     p.add_argument("--impl", default="tetm", choices=["tetm", "reference"])
     p.add_argument("--workload", default="collimator",
                    choices=["collimator", "plain_pipe", "batch", "serve", "dielectric", "rz"])
+    p.add_argument("--config", default=None, choices=["cfg1", "cfg2", "cfg3", "cfg4", "cfg5"],
+                   help="the benchmark configurations by number: cfg1 = plain_pipe (FP64), "
+                        "cfg2 = collimator (FP32), cfg3 = rz, cfg4 = batch, cfg5 = serve")
     p.add_argument("--rz-chunk", type=int, default=0,
                    help="rz: planes per work item (0 = chosen by the autotuner, untimed)")
     p.add_argument("--rz-kernel", default=None, choices=[None, "async", "register", "bulk", "bulk2"],
@@ -82,7 +85,13 @@ def parse_args():
                    help="smaller case of the same workload (profiling): number of z cells")
     p.add_argument("--n", type=int, default=0,
                    help="plain_pipe only: transverse cells (profiling a fully active box)")
-    return p.parse_args()
+    args = p.parse_args()
+    if args.config:
+        args.workload = {"cfg1": "plain_pipe", "cfg2": "collimator", "cfg3": "rz", "cfg4": "batch",
+                         "cfg5": "serve"}[args.config]
+        if args.config == "cfg1" and args.precision is None:
+            args.precision = "fp64"
+    return args
 
 
 def make_workload(args):

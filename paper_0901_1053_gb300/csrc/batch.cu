@@ -11,6 +11,7 @@
 #include <vector>
 
 #include "tetm_internal.h"
+#include <nvtx3/nvToolsExt.h>
 
 using namespace tetm;
 
@@ -137,7 +138,7 @@ int tetm_batch_create(tetm_solver* const* solvers, const int64_t* step_limits, i
   return TETM_OK;
 }
 
-int tetm_batch_step(tetm_batch* b, int32_t nsteps) {
+static int batch_step_impl(tetm_batch* b, int32_t nsteps) {
   if (!b || nsteps < 0) return TETM_E_ARG;
   int left = nsteps;
   if (left > 0 && !b->warmed) {  // first launch outside any capture (one-time launch set-up)
@@ -171,6 +172,13 @@ int tetm_batch_step(tetm_batch* b, int32_t nsteps) {
     if (taken > 0) s->prev_valid = true;
   }
   return TETM_OK;
+}
+
+int tetm_batch_step(tetm_batch* b, int32_t nsteps) {
+  nvtxRangePushA("tetm_batch_step");
+  const int rc = batch_step_impl(b, nsteps);
+  nvtxRangePop();
+  return rc;
 }
 
 int tetm_batch_sync(tetm_batch* b) {

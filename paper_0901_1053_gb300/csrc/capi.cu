@@ -11,6 +11,7 @@
 #include <vector>
 
 #include "tetm_internal.h"
+#include <nvtx3/nvToolsExt.h>
 
 using namespace tetm;
 
@@ -730,7 +731,10 @@ int tetm_step(tetm_solver* s, int32_t n) {
     int rc = rebuild_work(s);
     if (rc) return rc;
   }
-  return s->esz == 8 ? do_steps<double>(s, n) : do_steps<float>(s, n);
+  nvtxRangePushA("tetm_step");  // a range in a profiler's timeline (no cost without one)
+  const int rc = s->esz == 8 ? do_steps<double>(s, n) : do_steps<float>(s, n);
+  nvtxRangePop();
+  return rc;
 }
 
 int tetm_sync(tetm_solver* s) {

@@ -39,6 +39,7 @@
 
 #include "tetm_internal.h"
 #include "tetm_rz.h"
+#include <nvtx3/nvToolsExt.h>
 
 namespace {
 
@@ -1778,7 +1779,10 @@ int tetm_rz_step(tetm_rz* s, int64_t n) {
     int rc = rz_rebuild_work(s);
     if (rc) return rc;
   }
-  return s->esz == 8 ? rz_launch_steps<double>(s, n) : rz_launch_steps<float>(s, n);
+  nvtxRangePushA("tetm_rz_step");
+  const int rc = s->esz == 8 ? rz_launch_steps<double>(s, n) : rz_launch_steps<float>(s, n);
+  nvtxRangePop();
+  return rc;
 }
 
 int tetm_rz_sync(tetm_rz* s) {
