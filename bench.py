@@ -351,7 +351,7 @@ def run_tetm(args):
         args.tiling_used = tuple(int(x) for x in args.tiling.split(","))
     elif args.kernel == "fused" and not args.no_autotune:
         from paper_0901_1053_gb300.autotune import Autotuner
-        args.tiling_used = Autotuner().tune(w, w.precision)
+        args.tiling_used = Autotuner().tune(w, w.precision, materials=args.eps is not None)
     else:
         args.tiling_used = None
     if args.tiling_used:
@@ -407,11 +407,12 @@ def run_tetm(args):
         peak, peak_kind = fp64_peak(tetm)
         roof = {"bound": "alu", "unit": "TFLOP/s", "flops_per_cell": FLOPS_PER_CELL_3D,
                 "hbm_gbs": gbs, "bytes_per_cell": bytes_per_cell}
-    kname = "fused_step_warp" if info["tile_x"] == 28 else "fused_step"
+    kname = {28: "fused_step_warp", 56: "fused_step_slab"}.get(info["tile_x"], "fused_step")
     if args.eps is not None:
         kname = "fused_step_warp_mat"
     prof_name = "%s_%s_%s.md" % (kname, w.precision, w.name)
-    traffic = profiled_traffic(prof_name) if args.kernel != "reference" else None
+    sources = ("kernels_slab.cu",) if kname == "fused_step_slab" else ("kernels_step.cu", "kernels_warp.cu")
+    traffic = profiled_traffic(prof_name, sources) if args.kernel != "reference" else None
     wake = s.wake()[0]
     hist = s.balance_history()
     s.close()

@@ -16,7 +16,8 @@ from typing import Dict, List, Optional, Sequence, Tuple
 
 Shape = Tuple[int, int, int]
 
-CANDIDATES_FP32: List[Shape] = [(28, 20, 32), (28, 20, 16), (28, 12, 32), (28, 12, 16),
+CANDIDATES_FP32: List[Shape] = [(56, 28, 32), (56, 28, 16), (56, 28, 64),
+                                (28, 20, 32), (28, 20, 16), (28, 12, 32), (28, 12, 16),
                                 (28, 28, 32), (28, 8, 32), (28, 4, 32), (32, 8, 64)]
 CANDIDATES_FP64: List[Shape] = [(28, 20, 32), (28, 20, 16), (28, 12, 32), (28, 28, 32),
                                 (28, 4, 32), (32, 8, 64)]
@@ -123,14 +124,18 @@ class Autotuner:
         return sorted(set(out))
 
     def tune(self, w, precision: Optional[str] = None,
-             candidates: Optional[Sequence[Shape]] = None) -> Shape:
+             candidates: Optional[Sequence[Shape]] = None, materials: bool = False) -> Shape:
+        """materials: the solve has eps/mu arrays (per-entry coefficients run on
+        the warp-tiled kernel only, tile_x = 28)."""
         precision = precision or w.precision
-        k = self.key(w, precision)
+        k = self.key(w, precision) + ("|materials" if materials else "")
         if k in self.cache:
             return tuple(self.cache[k])
         cands = list(candidates or (CANDIDATES_FP32 if precision == "fp32" else CANDIDATES_FP64))
         if candidates is None:
             cands += [c for c in self.wave_fitted(w, precision) if c not in cands]
+        if materials:
+            cands = [c for c in cands if c[0] == 28]
         times = self.measure(w, precision, cands)
         best = min(times, key=times.get)
         self.cache[k] = list(best)

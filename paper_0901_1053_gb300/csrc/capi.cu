@@ -22,8 +22,13 @@ Layout make_layout(int nx, int ny, int nz, int elem_bytes) {
   L.nx = nx;
   L.ny = ny;
   L.nz = nz;
-  L.ox = 16 / elem_bytes;                          // i = 0 on a 16-byte boundary, >= 2 guards
-  const int align = 32 / elem_bytes;               // rows on 32-byte sectors
+  // i = 0 after the guard columns: at column 8 in float32 (the 56-column tiles
+  // of the slab kernel then write whole 32-byte sectors, and its tensor copies
+  // start on 16-byte boundaries), at 2 in float64
+  L.ox = elem_bytes == 4 ? 8 : 2;
+  // rows on 32-byte sectors; float32 rows a multiple of 16 entries, so the
+  // byte-wide activity rows are 16-byte strides for tensor copies
+  const int align = elem_bytes == 4 ? 16 : 32 / elem_bytes;
   long long px = L.ox + nx + 3;                    // >= 2 zero columns past nx, plus one
                                                    // so a column pair starting at nx + 1 stays in the row
   px = (px + align - 1) / align * align;
@@ -370,10 +375,27 @@ int do_steps(tetm_solver* s, int n) {
     if (s->kernel == TETM_KERNEL_FUSED) {
       StepArgs<T> a = step_args<T>(s, true);
       if (s->n_work > 0) {
-        if (warp_shape_ok(s->tile_x, s->tile_y))
+        if (warp_shape_ok(s->tile_x, s->tile_y)) {
           CK(launch_fused_warp_step<T>(a, s->tile_x, s->tile_y, s->stream));
-        else
+        } else if (slab_shape_ok(s->tile_x, s->tile_y)) {
+          if constexpr (sizeof(T) == 4) {
+            if (!s->slab) {  // tensor maps of both field sets and the mask (fixed addresses)
+              s->slab = new (std::nothrow) SlabMaps();
+              void* ez[2] = {s->set[0][kEZ], s->set[1][kEZ]};
+              void* hz[2] = {s->set[0][kHZ], s->set[1][kHZ]};
+              if (!s->slab || build_slab_maps(s->slab, ez, hz, s->mask, s->L) != 0) {
+                delete s->slab;
+                s->slab = nullptr;
+                return TETM_E_UNSUPPORTED;
+              }
+            }
+            CK(launch_fused_slab_step(a, *s->slab, s->cur, s->err, s->stream));
+          } else {
+            return TETM_E_UNSUPPORTED;
+          }
+        } else {
           CK(launch_fused_step<T>(a, s->tile_x, s->tile_y, s->stream));
+        }
       }
       if (s->bunch && s->obs_on) CK(launch_transverse_after_step<T>(a, s->stream));
       s->cur = 1 - s->cur;
@@ -456,6 +478,9 @@ void free_all(tetm_solver* s) {
   cudaFree(s->diag.out);
   cudaFree(s->hist);
   cudaFree(s->staging);
+  cudaFree(s->err);
+  delete s->slab;
+  s->slab = nullptr;
 }
 
 }  // namespace
@@ -523,8 +548,10 @@ int tetm_create(const tetm_grid* g, const double* eps_r, const double* mu_r, con
   s->kernel = TETM_KERNEL_FUSED;
   s->uniform = uniform;
   s->vacuum = uniform && eps_u == 1.0 && mu_u == 1.0;
-  s->tile_x = 28;   // warp-tiled kernel (kernels_warp.cu)
-  s->tile_y = 20;
+  // float32 without material arrays: the slab kernel (kernels_slab.cu); else
+  // the warp-tiled kernel (kernels_warp.cu)
+  s->tile_x = (s->esz == 4 && uniform) ? 56 : 28;
+  s->tile_y = (s->esz == 4 && uniform) ? 28 : 20;
   s->chunk_z = 32;
   int rc = TETM_OK;
   const size_t fbytes = (size_t)s->L.count * s->esz;
@@ -537,6 +564,8 @@ int tetm_create(const tetm_grid* g, const double* eps_r, const double* mu_r, con
   if (rc == TETM_OK) rc = cudaMemsetAsync(s->mask, 0, (size_t)s->L.count, s->stream) == cudaSuccess ? TETM_OK : TETM_E_CUDA;
   if (rc == TETM_OK) rc = dalloc(s, (void**)&s->diag.part, sizeof(double) * 2048);
   if (rc == TETM_OK) rc = dalloc(s, (void**)&s->diag.out, sizeof(double) * 8);
+  if (rc == TETM_OK) rc = dalloc(s, (void**)&s->err, sizeof(int));
+  if (rc == TETM_OK) rc = cudaMemsetAsync(s->err, 0, sizeof(int), s->stream) == cudaSuccess ? TETM_OK : TETM_E_CUDA;
   s->diag.cap = 2048;
   s->hist_cap = 4096;
   if (rc == TETM_OK) rc = dalloc(s, (void**)&s->hist, sizeof(double) * 5 * (size_t)s->hist_cap);
@@ -658,9 +687,12 @@ int tetm_set_tiling(tetm_solver* s, int32_t tile_x, int32_t tile_y, int32_t chun
   const int tx = tile_x ? tile_x : s->tile_x;
   const int ty = tile_y ? tile_y : s->tile_y;
   const int cz = chunk_z ? chunk_z : s->chunk_z;
-  if ((!fused_shape_ok(tx, ty) && !warp_shape_ok(tx, ty)) || cz < 4) return TETM_E_ARG;
+  if ((!fused_shape_ok(tx, ty) && !warp_shape_ok(tx, ty) && !slab_shape_ok(tx, ty)) || cz < 4)
+    return TETM_E_ARG;
   // per-entry coefficients (general materials) run on the warp-tiled kernel only
   if (!s->uniform && tx != 28 && s->kernel == TETM_KERNEL_FUSED) return TETM_E_UNSUPPORTED;
+  // the slab kernel is float32 only
+  if (slab_shape_ok(tx, ty) && s->esz != 4) return TETM_E_UNSUPPORTED;
   if (tx == s->tile_x && ty == s->tile_y && cz == s->chunk_z && s->work) return TETM_OK;
   s->tile_x = tx;
   s->tile_y = ty;
@@ -739,8 +771,10 @@ int tetm_step(tetm_solver* s, int32_t n) {
 
 int tetm_sync(tetm_solver* s) {
   if (!s) return TETM_E_ARG;
+  int flag = 0;
+  CK(cudaMemcpyAsync(&flag, s->err, sizeof(int), cudaMemcpyDeviceToHost, s->stream));
   CK(cudaStreamSynchronize(s->stream));
-  return TETM_OK;
+  return flag ? TETM_E_TIMEOUT : TETM_OK;
 }
 
 int tetm_wake(tetm_solver* s, double* out, int32_t cap, int32_t* n_out, double* s0, double* ds) {

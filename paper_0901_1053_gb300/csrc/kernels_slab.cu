@@ -1,0 +1,393 @@
+// Block-tiled fused step with tensor staging, float32 (Sec. 4.2, Eq. (23)).
+//
+// One CTA of 512 threads per SM takes (tile, z chunk) work items in turn. A
+// tile owns 56 x 28 nodes and loads 64 x 32 (4 halo columns and 2 halo rows on
+// each side: the ten updates reach two nodes sideways). Thread t holds the
+// four consecutive columns 4 (t mod 16) .. +3 of row t / 16, so its loads and
+// stores are 16-byte vectors, and marches through the chunk plane by plane
+// with the z-state of its four nodes in registers (old e_x, e_y of the plane,
+// new h_x, h_y of the plane below): no per-row state in shared memory.
+//
+// e_z and h_z are the only inputs a node reads at its neighbours; they and the
+// activity bytes arrive through a ring of kSD planes in shared memory, one
+// 3D tensor copy (TMA) per array and plane issued kSD - 1 planes ahead,
+// completion on an mbarrier per slot (bounded waits: after kSlabPolls polls
+// the CTA raises the error word, drains the copies in flight and stops). h_x,
+// h_y, e_x, e_y are read at the node itself, with 16-byte loads one plane
+// ahead. The intermediates a stage reads at its neighbours (hx~, hy~, ez',
+// ex~, ey~, hz') go through three exchange buffers, four block barriers per
+// plane:
+//   S1 hx~, hy~ (U1, U2)  | S2 ez' (U3, + current) | S3 hx', hy' (U4, U5)
+//   S4 ex~, ey~ (U6, U7)  | S5 hz' (U8)            | S6 ex', ey' (U9, U10)
+// The column of i = 0 sits at 8 in the float32 layout, so the 224-byte rows a
+// tile writes start and end on 32-byte sectors and no two tiles write into
+// the same sector.
+#include <cuda.h>
+#include <cudaTypedefs.h>
+
+#include <algorithm>
+
+#include "tetm_internal.h"
+
+namespace tetm {
+
+namespace {
+
+constexpr int kSX = 64, kSY = 32;   // loaded columns, rows
+constexpr int kOX = 56, kOY = 28;   // owned columns, rows
+constexpr int kQ = kSX / 4;         // column quads per row
+constexpr int kSThreads = kQ * kSY; // 512
+constexpr int kSD = 6;              // planes in the ring
+constexpr int kMaskW = 80;          // activity bytes per row (from a 16-byte aligned column)
+constexpr int kSlabPolls = 1 << 18;
+constexpr unsigned kSlotBytes = 2u * kSX * kSY * 4u + (unsigned)kMaskW * kSY;
+
+struct SlabSmem {
+  float ez[kSD][kSY][kSX];
+  float hz[kSD][kSY][kSX];
+  uint8_t mk[kSD][kSY][kMaskW];
+  float x1[kSY][kSX], x2[kSY][kSX], x3[kSY][kSX];
+  uint64_t bar[kSD];
+};
+
+__device__ __forceinline__ unsigned su32(const void* p) { return (unsigned)__cvta_generic_to_shared(p); }
+__device__ __forceinline__ void bar_init(uint64_t* b) {
+  asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(su32(b)) : "memory");
+}
+__device__ __forceinline__ void bar_expect(uint64_t* b, unsigned bytes) {
+  asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(su32(b)), "r"(bytes) : "memory");
+}
+__device__ __forceinline__ bool bar_try(uint64_t* b, unsigned parity) {
+  unsigned ok;
+  asm volatile(
+      "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n selp.u32 %0, 1, 0, p;\n}"
+      : "=r"(ok)
+      : "r"(su32(b)), "r"(parity)
+      : "memory");
+  return ok != 0;
+}
+__device__ __forceinline__ bool bar_wait(uint64_t* b, unsigned parity) {
+  for (int it = 0; it < kSlabPolls; ++it)
+    if (bar_try(b, parity)) return true;
+  return false;
+}
+// 3D tensor copy of the box at (x, y, z) into shared memory
+__device__ __forceinline__ void tma3(void* dst, const CUtensorMap* map, int x, int y, int z, uint64_t* b) {
+  asm volatile(
+      "cp.async.bulk.tensor.3d.shared::cluster.global.tile.mbarrier::complete_tx::bytes [%0], [%1, {%2, %3, %4}], [%5];"
+      ::"r"(su32(dst)), "l"(reinterpret_cast<uint64_t>(map)), "r"(x), "r"(y), "r"(z), "r"(su32(b))
+      : "memory");
+}
+__device__ __forceinline__ float4 ld4(const float* p) {
+  float4 v;
+  asm volatile("ld.global.nc.v4.f32 {%0,%1,%2,%3}, [%4];" : "=f"(v.x), "=f"(v.y), "=f"(v.z), "=f"(v.w) : "l"(p));
+  return v;
+}
+
+struct Q4 {
+  float v[4];
+};
+__device__ __forceinline__ Q4 q4(float4 a) { return Q4{{a.x, a.y, a.z, a.w}}; }
+__device__ __forceinline__ Q4 lds4(const float* p) { return q4(*reinterpret_cast<const float4*>(p)); }
+__device__ __forceinline__ void sts4(float* p, const Q4& a) {
+  *reinterpret_cast<float4*>(p) = make_float4(a.v[0], a.v[1], a.v[2], a.v[3]);
+}
+
+__global__ void __launch_bounds__(kSThreads, 1)
+fused_step_slab(const StepArgs<float> a, const __grid_constant__ CUtensorMap tm_ez,
+                const __grid_constant__ CUtensorMap tm_hz, const __grid_constant__ CUtensorMap tm_mk,
+                int* err) {
+  extern __shared__ __align__(128) unsigned char slab_raw[];
+  SlabSmem& S = *reinterpret_cast<SlabSmem*>(slab_raw);
+  const int tid = threadIdx.x, q = tid % kQ, row = tid / kQ;
+  if (tid == 0)
+    for (int s = 0; s < kSD; ++s) bar_init(&S.bar[s]);
+  asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+  __syncthreads();
+  unsigned phases = 0;
+
+  const Layout L = a.L;
+  const long long SZ = L.sz, PX = L.px;
+  const float uEX = a.co.u[kEX], uEY = a.co.u[kEY], uEZ = a.co.u[kEZ];
+  const float uHX = a.co.u[kHX], uHY = a.co.u[kHY], uHZ = a.co.u[kHZ];
+  const int ntile = a.tiles_x * a.tiles_y;
+  const int nitems = a.work ? a.n_work : ntile * a.n_chunks;
+
+  for (int wi = blockIdx.x; wi < nitems; wi += gridDim.x) {
+    const int item = a.work ? a.work[wi] : wi;
+    const int tile = item % ntile, chunk = item / ntile;
+    const int gx0 = (tile % a.tiles_x) * kOX - 4;  // global i of loaded column 0
+    const int gy0 = (tile / a.tiles_x) * kOY - 2;  // global j of loaded row 0
+    const int k0 = chunk * a.chunk_z, k1 = min(k0 + a.chunk_z, L.nz);
+    const int kstart = k0 - 1;
+    const int nplanes = k1 - kstart;
+    const int cx = gx0 + L.ox, cy = gy0 + 2;     // tensor coordinates (column, row)
+    const int mx = cx & ~15, moff = cx - mx;     // activity bytes: 16-byte aligned box
+
+    // this thread's four nodes
+    const int gi = gx0 + 4 * q, gj = gy0 + row;
+    const int jc = min(gj, L.ny + 1);
+    const bool vec = gi + 3 <= L.nx + 1;         // the quad lies inside the padded row
+    const bool own_q = q >= 1 && q <= kQ - 2 && row >= 2 && row < kSY - 2 && gj < L.ny;
+    auto gidx = [&](int k) { return (long long)(k + 1) * SZ + (long long)(jc + 2) * PX + (gi + L.ox); };
+    auto load_q = [&](const float* base, int k) -> Q4 {
+      const long long id = gidx(k);
+      if (vec) return q4(ld4(base + id));
+      Q4 r;
+#pragma unroll
+      for (int e = 0; e < 4; ++e) r.v[e] = gi + e <= L.nx + 1 ? base[id + e] : 0.f;
+      return r;
+    };
+    auto store_q = [&](float* base, int k, const Q4& v) {
+      const long long id = gidx(k);
+      if (gi + 3 < L.nx) {
+        *reinterpret_cast<float4*>(base + id) = make_float4(v.v[0], v.v[1], v.v[2], v.v[3]);
+      } else {
+#pragma unroll
+        for (int e = 0; e < 4; ++e)
+          if (gi + e < L.nx) base[id + e] = v.v[e];
+      }
+    };
+    auto issue = [&](int k) {  // plane k into its slot (one thread)
+      const int s = (k - kstart) % kSD;
+      asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+      bar_expect(&S.bar[s], kSlotBytes);
+      tma3(&S.ez[s][0][0], &tm_ez, cx, cy, k + 1, &S.bar[s]);
+      tma3(&S.hz[s][0][0], &tm_hz, cx, cy, k + 1, &S.bar[s]);
+      tma3(&S.mk[s][0][0], &tm_mk, mx, cy, k + 1, &S.bar[s]);
+    };
+    if (tid == 0)
+      for (int k = kstart; k < kstart + min(kSD, nplanes); ++k) issue(k);
+    int issued = kstart + min(kSD, nplanes) - 1;  // last plane queued (thread 0 keeps it)
+
+    // z-state and the register prefetch (plane k: hx, hy of k; ex, ey of k+1)
+    Q4 ex0 = load_q(a.in[kEX], kstart), ey0 = load_q(a.in[kEY], kstart);
+    Q4 hxc = load_q(a.in[kHX], kstart), hyc = load_q(a.in[kHY], kstart);
+    Q4 ex1 = load_q(a.in[kEX], kstart + 1), ey1 = load_q(a.in[kEY], kstart + 1);
+    Q4 hxp{{0.f, 0.f, 0.f, 0.f}}, hyp{{0.f, 0.f, 0.f, 0.f}};
+    const bool line_row = a.b.on && gj == a.b.j0;
+
+    for (int k = kstart; k < k1; ++k) {
+      const int s = (k - kstart) % kSD;
+      const bool ok = bar_wait(&S.bar[s], (phases >> s) & 1u);
+      if (!__syncthreads_and(ok)) {
+        // a copy did not land: raise the error word, wait (bounded) for the
+        // copies still in flight, stop
+        if (tid == 0) {
+          atomicExch(err, 1);
+          for (int kk = k; kk <= issued; ++kk) {
+            const int ss = (kk - kstart) % kSD;
+            bar_wait(&S.bar[ss], (phases >> ss) & 1u);
+          }
+        }
+        __syncthreads();
+        return;
+      }
+      phases ^= 1u << s;
+      // next plane's register inputs, early
+      Q4 hxn_in, hyn_in, exn_in, eyn_in;
+      const bool more = k + 1 < k1;
+      if (more) {
+        hxn_in = load_q(a.in[kHX], k + 1);
+        hyn_in = load_q(a.in[kHY], k + 1);
+        exn_in = load_q(a.in[kEX], k + 2);
+        eyn_in = load_q(a.in[kEY], k + 2);
+      }
+      // slot inputs: e_z, h_z of this quad and its neighbours, activity bytes
+      const float* sez = &S.ez[s][0][0];
+      const float* shz = &S.hz[s][0][0];
+      const Q4 ez = lds4(sez + row * kSX + 4 * q);
+      const Q4 ezU = row + 1 < kSY ? lds4(sez + (row + 1) * kSX + 4 * q) : Q4{{0.f, 0.f, 0.f, 0.f}};
+      const float ezR = q + 1 < kQ ? sez[row * kSX + 4 * q + 4] : 0.f;
+      const Q4 hz = lds4(shz + row * kSX + 4 * q);
+      const Q4 hzD = row >= 1 ? lds4(shz + (row - 1) * kSX + 4 * q) : Q4{{0.f, 0.f, 0.f, 0.f}};
+      const float hzL = q >= 1 ? shz[row * kSX + 4 * q - 1] : 0.f;
+      const unsigned mw = *reinterpret_cast<const unsigned*>(&S.mk[s][row][moff + 4 * q]);
+
+      float cHX[4], cHY[4], cEZ[4], cEX[4], cEY[4], cHZ[4], dey[4], dex[4];
+      Q4 hxa, hya;
+#pragma unroll
+      for (int e = 0; e < 4; ++e) {
+        const unsigned m = (mw >> (8 * e)) & 0xFFu;
+        cEX[e] = (m & 1) ? uEX : 0.f;
+        cEY[e] = (m & 2) ? uEY : 0.f;
+        cEZ[e] = (m & 4) ? uEZ : 0.f;
+        cHX[e] = (m & 8) ? uHX : 0.f;
+        cHY[e] = (m & 16) ? uHY : 0.f;
+        cHZ[e] = (m & 32) ? uHZ : 0.f;
+        dey[e] = ey1.v[e] - ey0.v[e];
+        dex[e] = ex1.v[e] - ex0.v[e];
+        const float ezx = e < 3 ? ez.v[e + 1] : ezR;
+        hxa.v[e] = hxc.v[e] + cHX[e] * (dey[e] - (ezU.v[e] - ez.v[e]));   // U1
+        hya.v[e] = hyc.v[e] + cHY[e] * (-dex[e] + (ezx - ez.v[e]));      // U2
+      }
+      sts4(&S.x1[row][4 * q], hxa);
+      sts4(&S.x2[row][4 * q], hya);
+      __syncthreads();  // (1) the slot is read and hx~, hy~ are out
+      if (tid == 0 && k + kSD < k1) {
+        issue(k + kSD);
+        issued = k + kSD;
+      }
+      // S2: ez' = ez + 2a M^-1 (P_y^T hx~ - P_x^T hy~ - jj_z)
+      const Q4 hxaD = row >= 1 ? lds4(&S.x1[row - 1][4 * q]) : Q4{{0.f, 0.f, 0.f, 0.f}};
+      const float hyaL = q >= 1 ? S.x2[row][4 * q - 1] : 0.f;
+      Q4 ezn;
+#pragma unroll
+      for (int e = 0; e < 4; ++e) {
+        const float hyl = e > 0 ? hya.v[e - 1] : hyaL;
+        float cur = (hxaD.v[e] - hxa.v[e]) - (hyl - hya.v[e]);
+        if (line_row && gi + e == a.b.i0 && k >= 0) {
+          const long long dd = (long long)k - (a.n + a.b.kshift) + a.b.c0;
+          if (dd >= -a.b.c0 && dd < a.b.c0) cur -= a.b.J[dd + a.b.c0];
+        }
+        ezn.v[e] = ez.v[e] + cEZ[e] * cur;                                // U3
+      }
+      sts4(&S.x3[row][4 * q], ezn);
+      __syncthreads();  // (2)
+      // S3: hx', hy'
+      const Q4 eznU = row + 1 < kSY ? lds4(&S.x3[row + 1][4 * q]) : Q4{{0.f, 0.f, 0.f, 0.f}};
+      const float eznR = q + 1 < kQ ? S.x3[row][4 * q + 4] : 0.f;
+      Q4 hxn, hyn;
+#pragma unroll
+      for (int e = 0; e < 4; ++e) {
+        const float ezx = e < 3 ? ezn.v[e + 1] : eznR;
+        hxn.v[e] = hxa.v[e] + cHX[e] * (dey[e] - (eznU.v[e] - ezn.v[e]));  // U4
+        hyn.v[e] = hya.v[e] + cHY[e] * (-dex[e] + (ezx - ezn.v[e]));     // U5
+      }
+      const bool te = k >= k0;
+      if (te && own_q) {
+        store_q(a.out[kEZ], k, ezn);
+        store_q(a.out[kHX], k, hxn);
+        store_q(a.out[kHY], k, hyn);
+        if (line_row && a.b.i0 >= gi && a.b.i0 < gi + 4 && a.b.i0 < L.nx) {
+          const long long mm = (a.n + a.b.kshift) - k - a.b.c0;
+          if (mm >= a.b.m_min && mm <= a.b.m_max)
+            a.b.W[mm - a.b.m_min] -= (double)ezn.v[a.b.i0 - gi] * a.b.inv_q;
+        }
+      }
+      // S4: ex~, ey~ with the new hx, hy of this plane and of the plane below
+      Q4 exa, eya;
+#pragma unroll
+      for (int e = 0; e < 4; ++e) {
+        const float hzl = e > 0 ? hz.v[e - 1] : hzL;
+        exa.v[e] = ex0.v[e] + cEX[e] * ((hyp.v[e] - hyn.v[e]) - (hzD.v[e] - hz.v[e]));   // U6
+        eya.v[e] = ey0.v[e] + cEY[e] * (-(hxp.v[e] - hxn.v[e]) + (hzl - hz.v[e]));       // U7
+      }
+      sts4(&S.x1[row][4 * q], exa);
+      sts4(&S.x2[row][4 * q], eya);
+      __syncthreads();  // (3)
+      // S5: hz'
+      const Q4 exaU = row + 1 < kSY ? lds4(&S.x1[row + 1][4 * q]) : Q4{{0.f, 0.f, 0.f, 0.f}};
+      const float eyaR = q + 1 < kQ ? S.x2[row][4 * q + 4] : 0.f;
+      Q4 hzn;
+#pragma unroll
+      for (int e = 0; e < 4; ++e) {
+        const float eyx = e < 3 ? eya.v[e + 1] : eyaR;
+        hzn.v[e] = hz.v[e] + cHZ[e] * ((exaU.v[e] - exa.v[e]) - (eyx - eya.v[e]));      // U8
+      }
+      sts4(&S.x3[row][4 * q], hzn);
+      __syncthreads();  // (4)
+      // S6: ex', ey'
+      const Q4 hznD = row >= 1 ? lds4(&S.x3[row - 1][4 * q]) : Q4{{0.f, 0.f, 0.f, 0.f}};
+      const float hznL = q >= 1 ? S.x3[row][4 * q - 1] : 0.f;
+      Q4 exn, eyn;
+#pragma unroll
+      for (int e = 0; e < 4; ++e) {
+        const float hzl = e > 0 ? hzn.v[e - 1] : hznL;
+        exn.v[e] = exa.v[e] + cEX[e] * ((hyp.v[e] - hyn.v[e]) - (hznD.v[e] - hzn.v[e]));   // U9
+        eyn.v[e] = eya.v[e] + cEY[e] * (-(hxp.v[e] - hxn.v[e]) + (hzl - hzn.v[e]));       // U10
+      }
+      if (te && own_q) {
+        store_q(a.out[kEX], k, exn);
+        store_q(a.out[kEY], k, eyn);
+        store_q(a.out[kHZ], k, hzn);
+      }
+      // carry the z-state, take the prefetched inputs
+      hxp = hxn;
+      hyp = hyn;
+      ex0 = ex1;
+      ey0 = ey1;
+      if (more) {
+        hxc = hxn_in;
+        hyc = hyn_in;
+        ex1 = exn_in;
+        ey1 = eyn_in;
+      }
+    }
+    __syncthreads();  // every thread is done with the ring before the next item refills it
+  }
+}
+
+// The driver's tensor-map encoder, looked up through the runtime (the library
+// does not link the driver library, so it also loads where no driver is).
+PFN_cuTensorMapEncodeTiled_v12000 encoder() {
+  static PFN_cuTensorMapEncodeTiled_v12000 fn = nullptr;
+  if (!fn) {
+    void* p = nullptr;
+    cudaDriverEntryPointQueryResult q;
+    if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &p, 12000, cudaEnableDefault, &q) ==
+            cudaSuccess &&
+        q == cudaDriverEntryPointSuccess)
+      fn = reinterpret_cast<PFN_cuTensorMapEncodeTiled_v12000>(p);
+  }
+  return fn;
+}
+
+CUresult encode3d(CUtensorMap* map, CUtensorMapDataType type, void* base, const Layout& L, int esz,
+                  unsigned box_x) {
+  PFN_cuTensorMapEncodeTiled_v12000 fn = encoder();
+  if (!fn) return CUDA_ERROR_NOT_FOUND;
+  const cuuint64_t dims[3] = {(cuuint64_t)L.px, (cuuint64_t)(L.ny + 4), (cuuint64_t)(L.nz + 3)};
+  const cuuint64_t strides[2] = {(cuuint64_t)L.px * esz, (cuuint64_t)L.sz * esz};
+  const cuuint32_t box[3] = {box_x, (cuuint32_t)kSY, 1};
+  const cuuint32_t estr[3] = {1, 1, 1};
+  return fn(map, type, 3, base, dims, strides, box, estr, CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE,
+            CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+}
+
+}  // namespace
+
+bool slab_shape_ok(int tx, int ty) { return tx == kOX && ty == kOY; }
+
+int build_slab_maps(SlabMaps* m, void* const ez[2], void* const hz[2], const uint8_t* mask, const Layout& L) {
+  static_assert(sizeof(CUtensorMap) <= sizeof(m->ez[0]), "tensor map storage");
+  // the tiled copies need 16-byte row strides and 16-byte box starts
+  if ((L.px * 4) % 16 != 0 || L.px % 16 != 0 || (L.ox % 4) != 0) return -1;
+  for (int c = 0; c < 2; ++c) {
+    if (encode3d(reinterpret_cast<CUtensorMap*>(m->ez[c]), CU_TENSOR_MAP_DATA_TYPE_FLOAT32, ez[c], L, 4, kSX) !=
+            CUDA_SUCCESS ||
+        encode3d(reinterpret_cast<CUtensorMap*>(m->hz[c]), CU_TENSOR_MAP_DATA_TYPE_FLOAT32, hz[c], L, 4, kSX) !=
+            CUDA_SUCCESS)
+      return -1;
+  }
+  if (encode3d(reinterpret_cast<CUtensorMap*>(m->mk), CU_TENSOR_MAP_DATA_TYPE_UINT8, const_cast<uint8_t*>(mask),
+               L, 1, kMaskW) != CUDA_SUCCESS)
+    return -1;
+  return 0;
+}
+
+cudaError_t launch_fused_slab_step(const StepArgs<float>& a, const SlabMaps& m, int cur, int* err,
+                                   cudaStream_t st) {
+  static int sms = 0;
+  const size_t smem = sizeof(SlabSmem);
+  if (!sms) {
+    int dev = 0;
+    cudaError_t e = cudaGetDevice(&dev);
+    if (e == cudaSuccess) e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    if (e == cudaSuccess)
+      e = cudaFuncSetAttribute(fused_step_slab, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e != cudaSuccess) {
+      sms = 0;
+      return e;
+    }
+  }
+  const int items = a.work ? a.n_work : a.tiles_x * a.tiles_y * a.n_chunks;
+  if (items <= 0) return cudaSuccess;
+  const CUtensorMap& mez = *reinterpret_cast<const CUtensorMap*>(m.ez[cur]);
+  const CUtensorMap& mhz = *reinterpret_cast<const CUtensorMap*>(m.hz[cur]);
+  const CUtensorMap& mmk = *reinterpret_cast<const CUtensorMap*>(m.mk);
+  fused_step_slab<<<std::min(items, sms), kSThreads, smem, st>>>(a, mez, mhz, mmk, err);
+  return cudaGetLastError();
+}
+
+}  // namespace tetm

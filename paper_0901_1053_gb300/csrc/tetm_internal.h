@@ -127,6 +127,18 @@ template <typename T>
 cudaError_t launch_fused_warp_batch(const BatchMember<T>* members, int n_members, const int2* work,
                                     int n_work, int tile_y, int nz_max, cudaStream_t st);
 
+// ---- block-tiled float32 step with tensor staging (kernels_slab.cu): tile
+// 56 x 28, one CTA of 512 threads per SM ----------------------------------
+struct SlabMaps {  // tensor maps (CUtensorMap) of e_z and h_z of both field sets, and the mask
+  alignas(64) unsigned char ez[2][128];
+  alignas(64) unsigned char hz[2][128];
+  alignas(64) unsigned char mk[128];
+};
+bool slab_shape_ok(int tile_x, int tile_y);
+int build_slab_maps(SlabMaps* m, void* const ez[2], void* const hz[2], const uint8_t* mask, const Layout& L);
+cudaError_t launch_fused_slab_step(const StepArgs<float>& a, const SlabMaps& m, int cur, int* err,
+                                   cudaStream_t st);
+
 // transverse wake of a ping-pong step (kernels_step.cu): after the step
 // kernel, before the sets are swapped
 template <typename T>
@@ -190,6 +202,8 @@ struct tetm_solver {
   cudaStream_t stream;
   int kernel;
   int tile_x, tile_y, chunk_z;
+  tetm::SlabMaps* slab;          // tensor maps of the slab kernel (built on first use)
+  int* err;                      // device error word of the slab kernel's bounded waits
   int tiles_x, tiles_y, n_chunks;
   int* work;
   int n_work;

@@ -370,3 +370,71 @@ def test_register_ring_fp32_matches_block_kernel(tetm, tiling):
     for a, b in zip(out[0], out[1]):
         scale = np.max(np.abs(a)) or 1.0
         assert np.max(np.abs(a - b)) <= 1e-6 * scale
+
+
+# ---------------------------------------------------------------------------
+# Block-tiled float32 kernel with tensor staging (tiling 56 x 28): against the
+# float64 oracle at float32 tolerance, against the warp-tiled float32 kernel
+# (the same ten updates, up to FMA contraction), bitwise over chunk lengths
+# ---------------------------------------------------------------------------
+
+@pytest.mark.parametrize("dims", [(40, 36, 70), (130, 70, 41), (57, 29, 33), (9, 7, 12), (200, 120, 21)])
+def test_slab_kernel_fp32_matches_oracle_and_warp_kernel(tetm, dims):
+    nx, ny, nz = dims
+    w = wl.scaled_collimator(max(nx, ny), nz, sigma_cells=2.5, precision="fp32")
+    w.nx, w.ny = nx, ny
+    r = min(nx, ny)
+    w.pec = wl.radius_mask(nx, ny, nz, wl.collimator_radius(nz, 0.45 * r, 0.2 * r, nz // 4, nz // 2))
+    w.i0, w.j0 = nx // 2, ny // 2
+    w.steps = nz + 25
+    rng = np.random.default_rng(sum(dims))
+    init = {c: rng.standard_normal((nz + 1, ny + 1, nx + 1)) for c in ("ex", "ey", "ez", "hx", "hy", "hz")}
+    out = {}
+    for tiling in [(56, 28, 32), (28, 20, 32)]:
+        s = tetm.Solver(nx, ny, nz, w.dx, w.dy, w.dz, w.cdt, "fp32", pec=w.pec)
+        s.set_tiling(*tiling)
+        for c, a in init.items():
+            s.set(c, a)
+        s.set_bunch(w.sigma, w.charge, w.i0, w.j0)
+        s.step(w.steps)
+        s.sync()                       # raises on a timed-out wait
+        out[tiling] = ({c: s.get(c) for c in init}, s.wake()[0])
+        s.close()
+    o = oracle_run(dataclasses.replace(w, precision="fp64"), fields=init)
+    slab, warp = out[(56, 28, 32)], out[(28, 20, 32)]
+    for fam in (("ex", "ey", "ez"), ("hx", "hy", "hz")):
+        peak = max(np.max(np.abs(o.get(c))) for c in fam)
+        for c in fam:
+            # float32 rounding of the random high-frequency start grows over the
+            # steps; the slab kernel's error is that of the warp kernel
+            e_slab = np.max(np.abs(slab[0][c] - o.get(c)))
+            e_warp = np.max(np.abs(warp[0][c] - o.get(c)))
+            assert e_slab <= 2.0 * e_warp + 1e-6 * peak, (c, e_slab / peak, e_warp / peak)
+            assert np.max(np.abs(slab[0][c] - warp[0][c])) <= 2.0 * e_warp + 1e-6 * peak, c
+    assert rel_err(slab[1], o.wake()[0]) <= TOL32_WAKE
+    assert rel_err(slab[1], warp[1]) <= 1e-5
+
+
+def test_slab_kernel_chunk_lengths_are_bitwise_identical(tetm):
+    w = wl.scaled_collimator(120, 80, sigma_cells=3.0, precision="fp32")
+    w.steps = 90
+    ref = None
+    for cz in (32, 5, 64, 7):
+        s = tetm.Solver.from_workload(w)
+        s.set_tiling(56, 28, cz)
+        s.step(w.steps)
+        got = [s.get(c) for c in ("ex", "ey", "ez", "hx", "hy", "hz")] + [s.wake()[0]]
+        s.close()
+        if ref is None:
+            ref = got
+            continue
+        for a, b in zip(got, ref):
+            assert np.array_equal(a, b), cz
+
+
+def test_slab_kernel_is_float32_only(tetm):
+    w = wl.plain_pipe(nz=40, n=12, steps=10, precision="fp64")
+    s = tetm.Solver.from_workload(w)
+    with pytest.raises(tetm.TetmError) as e:
+        s.set_tiling(56, 28, 32)
+    assert e.value.code == tetm.TETM_E_UNSUPPORTED
