@@ -14,9 +14,10 @@
 // completion on an mbarrier per slot (bounded waits: after kSlabPolls polls
 // the CTA raises the error word, drains the copies in flight and stops). h_x,
 // h_y, e_x, e_y are read at the node itself, with 16-byte loads one plane
-// ahead. The intermediates a stage reads at its neighbours (hx~, hy~, ez',
-// ex~, ey~, hz') go through three exchange buffers, four block barriers per
-// plane:
+// ahead. The intermediates a stage reads one row up or down (hx~, ez', ex~,
+// hz') go through two shared-memory buffers, those one column left or right
+// through warp shuffles; four block barriers per plane, the first of which
+// also settles the slot waits:
 //   S1 hx~, hy~ (U1, U2)  | S2 ez' (U3, + current) | S3 hx', hy' (U4, U5)
 //   S4 ex~, ey~ (U6, U7)  | S5 hz' (U8)            | S6 ex', ey' (U9, U10)
 // The column of i = 0 sits at 8 in the float32 layout, so the 224-byte rows a
@@ -46,7 +47,7 @@ struct SlabSmem {
   float ez[kSD][kSY][kSX];
   float hz[kSD][kSY][kSX];
   uint8_t mk[kSD][kSY][kMaskW];
-  float x1[kSY][kSX], x2[kSY][kSX], x3[kSY][kSX];
+  float x1[kSY][kSX], x2[kSY][kSX];
   uint64_t bar[kSD];
 };
 
@@ -91,6 +92,17 @@ __device__ __forceinline__ Q4 q4(float4 a) { return Q4{{a.x, a.y, a.z, a.w}}; }
 __device__ __forceinline__ Q4 lds4(const float* p) { return q4(*reinterpret_cast<const float4*>(p)); }
 __device__ __forceinline__ void sts4(float* p, const Q4& a) {
   *reinterpret_cast<float4*>(p) = make_float4(a.v[0], a.v[1], a.v[2], a.v[3]);
+}
+
+// the neighbouring quad's value one column left (x-1) or right (x+1) of this
+// quad, zero at the tile edge (lanes: one row per half warp)
+__device__ __forceinline__ float left_of(float v3, int q) {
+  const float t = __shfl_up_sync(0xffffffffu, v3, 1);
+  return q >= 1 ? t : 0.f;
+}
+__device__ __forceinline__ float right_of(float v0, int q) {
+  const float t = __shfl_down_sync(0xffffffffu, v0, 1);
+  return q + 1 < kQ ? t : 0.f;
 }
 
 __global__ void __launch_bounds__(kSThreads, 1)
@@ -169,21 +181,10 @@ fused_step_slab(const StepArgs<float> a, const __grid_constant__ CUtensorMap tm_
 
     for (int k = kstart; k < k1; ++k) {
       const int s = (k - kstart) % kSD;
+      // every thread waits for the slot itself; the block decides at barrier
+      // (1) (a thread whose wait gave up computes on stale data until then,
+      // nothing is stored before it)
       const bool ok = bar_wait(&S.bar[s], (phases >> s) & 1u);
-      if (!__syncthreads_and(ok)) {
-        // a copy did not land: raise the error word, wait (bounded) for the
-        // copies still in flight, stop
-        if (tid == 0) {
-          atomicExch(err, 1);
-          for (int kk = k; kk <= issued; ++kk) {
-            const int ss = (kk - kstart) % kSD;
-            bar_wait(&S.bar[ss], (phases >> ss) & 1u);
-          }
-        }
-        __syncthreads();
-        return;
-      }
-      phases ^= 1u << s;
       // next plane's register inputs, early
       Q4 hxn_in, hyn_in, exn_in, eyn_in;
       const bool more = k + 1 < k1;
@@ -222,15 +223,27 @@ fused_step_slab(const StepArgs<float> a, const __grid_constant__ CUtensorMap tm_
         hya.v[e] = hyc.v[e] + cHY[e] * (-dex[e] + (ezx - ez.v[e]));      // U2
       }
       sts4(&S.x1[row][4 * q], hxa);
-      sts4(&S.x2[row][4 * q], hya);
-      __syncthreads();  // (1) the slot is read and hx~, hy~ are out
+      if (!__syncthreads_and(ok)) {  // (1) the slot is read and hx~ is out
+        // a copy did not land: raise the error word, wait (bounded) for the
+        // copies still in flight, stop
+        if (tid == 0) {
+          atomicExch(err, 1);
+          for (int kk = k; kk <= issued; ++kk) {
+            const int ss = (kk - kstart) % kSD;
+            bar_wait(&S.bar[ss], (phases >> ss) & 1u);
+          }
+        }
+        __syncthreads();
+        return;
+      }
+      phases ^= 1u << s;
       if (tid == 0 && k + kSD < k1) {
         issue(k + kSD);
         issued = k + kSD;
       }
       // S2: ez' = ez + 2a M^-1 (P_y^T hx~ - P_x^T hy~ - jj_z)
       const Q4 hxaD = row >= 1 ? lds4(&S.x1[row - 1][4 * q]) : Q4{{0.f, 0.f, 0.f, 0.f}};
-      const float hyaL = q >= 1 ? S.x2[row][4 * q - 1] : 0.f;
+      const float hyaL = left_of(hya.v[3], q);
       Q4 ezn;
 #pragma unroll
       for (int e = 0; e < 4; ++e) {
@@ -242,11 +255,11 @@ fused_step_slab(const StepArgs<float> a, const __grid_constant__ CUtensorMap tm_
         }
         ezn.v[e] = ez.v[e] + cEZ[e] * cur;                                // U3
       }
-      sts4(&S.x3[row][4 * q], ezn);
+      sts4(&S.x2[row][4 * q], ezn);
       __syncthreads();  // (2)
       // S3: hx', hy'
-      const Q4 eznU = row + 1 < kSY ? lds4(&S.x3[row + 1][4 * q]) : Q4{{0.f, 0.f, 0.f, 0.f}};
-      const float eznR = q + 1 < kQ ? S.x3[row][4 * q + 4] : 0.f;
+      const Q4 eznU = row + 1 < kSY ? lds4(&S.x2[row + 1][4 * q]) : Q4{{0.f, 0.f, 0.f, 0.f}};
+      const float eznR = right_of(ezn.v[0], q);
       Q4 hxn, hyn;
 #pragma unroll
       for (int e = 0; e < 4; ++e) {
@@ -274,22 +287,21 @@ fused_step_slab(const StepArgs<float> a, const __grid_constant__ CUtensorMap tm_
         eya.v[e] = ey0.v[e] + cEY[e] * (-(hxp.v[e] - hxn.v[e]) + (hzl - hz.v[e]));       // U7
       }
       sts4(&S.x1[row][4 * q], exa);
-      sts4(&S.x2[row][4 * q], eya);
       __syncthreads();  // (3)
       // S5: hz'
       const Q4 exaU = row + 1 < kSY ? lds4(&S.x1[row + 1][4 * q]) : Q4{{0.f, 0.f, 0.f, 0.f}};
-      const float eyaR = q + 1 < kQ ? S.x2[row][4 * q + 4] : 0.f;
+      const float eyaR = right_of(eya.v[0], q);
       Q4 hzn;
 #pragma unroll
       for (int e = 0; e < 4; ++e) {
         const float eyx = e < 3 ? eya.v[e + 1] : eyaR;
         hzn.v[e] = hz.v[e] + cHZ[e] * ((exaU.v[e] - exa.v[e]) - (eyx - eya.v[e]));      // U8
       }
-      sts4(&S.x3[row][4 * q], hzn);
+      sts4(&S.x2[row][4 * q], hzn);
       __syncthreads();  // (4)
       // S6: ex', ey'
-      const Q4 hznD = row >= 1 ? lds4(&S.x3[row - 1][4 * q]) : Q4{{0.f, 0.f, 0.f, 0.f}};
-      const float hznL = q >= 1 ? S.x3[row][4 * q - 1] : 0.f;
+      const Q4 hznD = row >= 1 ? lds4(&S.x2[row - 1][4 * q]) : Q4{{0.f, 0.f, 0.f, 0.f}};
+      const float hznL = left_of(hzn.v[3], q);
       Q4 exn, eyn;
 #pragma unroll
       for (int e = 0; e < 4; ++e) {
