@@ -16,7 +16,9 @@ integral units (edge voltages [V], dual-edge currents [A]).
 Parity status: every function here is pinned by the ``-m "not gpu"`` tests
 (dense matrix form of Eq. (23), eigen-angles of Eq. (27), energy law (19),
 charge laws (34)/(35), exact z-shift at c*dt = dz, loss-factor identity).
-``RzOracle`` (tetm_rz_oracle.c) is pinned by its own tests: the dense form
+``Oracle.yee_step`` (Yee's scheme, Eq. (7), the paper's comparison scheme) is
+pinned by the eigen-angles of the dispersion relation (9), the step bound (8)
+and the exactly conserved leapfrog energy. ``RzOracle`` (tetm_rz_oracle.c) is pinned by its own tests: the dense form
 (24), stability at c*dt = min(dr, dz) for every mode, energy law (19),
 pillbox Bessel-zero frequencies, the coaxial TEM shift, Gauss's law and the
 loss-factor identity.
@@ -58,6 +60,10 @@ def _load():
     lib.oracle_step_j.argtypes = [vp, vp, vp, vp]
     lib.oracle_step.argtypes = [vp, i]
     lib.oracle_step_custom.argtypes = [vp, vp, vp, vp]
+    lib.oracle_yee_step.restype = i
+    lib.oracle_yee_step.argtypes = [vp, i]
+    lib.oracle_yee_stable.restype = i
+    lib.oracle_yee_stable.argtypes = [d, d, d, d]
     lib.oracle_wake.restype = i
     lib.oracle_wake.argtypes = [vp, vp, i, ctypes.POINTER(i), dp, dp]
     lib.oracle_set_observer.restype = i
@@ -93,6 +99,11 @@ def _ptr(a):
 def stable(dx, dy, dz, cdt):
     """Eq. (25): c*dt <= dz and c*dt <= (dx^-2 + dy^-2)^-1/2."""
     return bool(_load().oracle_stable(dx, dy, dz, cdt))
+
+
+def yee_stable(dx, dy, dz, cdt):
+    """Eq. (8), the step bound of Yee's scheme: c*dt <= (dx^-2 + dy^-2 + dz^-2)^-1/2."""
+    return bool(_load().oracle_yee_stable(dx, dy, dz, cdt))
 
 
 class Oracle:
@@ -178,6 +189,12 @@ class Oracle:
         arrs = [None if a is None else np.ascontiguousarray(a, dtype=np.float64).reshape(self.shape)
                 for a in (jz, jx, jy)]
         self.lib.oracle_step_custom(self.h, *[_ptr(a) for a in arrs])
+
+    def yee_step(self, n=1):
+        """n steps of Yee's E/M leapfrog, Eq. (7), on this grid: state
+        (e^{n-1/2}, h^n), source-free."""
+        if self.lib.oracle_yee_step(self.h, int(n)) != 0:
+            raise ValueError("oracle_yee_step: a solve with a bunch")
 
     @property
     def step_count(self):

@@ -457,6 +457,48 @@ void oracle_set(oracle_t *o, int comp, const double *in) {
 void oracle_coef(const oracle_t *o, int comp, double *out) {
   memcpy(out, o->m[comp], sizeof(double) * (size_t)o->n);
 }
+/* Yee's E/M leapfrog (Sec. 3, Eq. (7)) on the same grid doublet and material
+ * matrices: the scheme the paper measures the TE/TM scheme against. The state
+ * is (e^{n-1/2}, h^n) and one step is
+ *     e^{n+1/2} = e^{n-1/2} + dt M_eps^-1 C~ h^n,
+ *     h^{n+1}   = h^n - dt M_mu^-1 C e^{n+1/2},
+ * C the curl of the primary grid, C~ = C^T that of the dual grid. Written in
+ * components with the P operators above (the same difference terms as the TE/TM
+ * updates, each with the full step dt). Source-free: it serves the field-only
+ * comparison (dispersion (9), stability (8), cost per step), so it refuses a
+ * solve that carries a bunch. */
+int oracle_yee_step(oracle_t *o, int nsteps) {
+  if (o->has_bunch) return -1;
+  double *ex = o->f[EX], *ey = o->f[EY], *ez = o->f[EZ];
+  double *hx = o->f[HX], *hy = o->f[HY], *hz = o->f[HZ];
+  const double *iex = o->m[EX], *iey = o->m[EY], *iez = o->m[EZ];
+  const double *ihx = o->m[HX], *ihy = o->m[HY], *ihz = o->m[HZ];
+  const double dt = o->dt;
+  const long N = o->n, sx = o->sx, sy = o->sy, sz = o->sz;
+  for (int s = 0; s < nsteps; ++s) {
+    /* electric half: e^{n-1/2} -> e^{n+1/2} from h^n */
+    for (long n = 0; n < N; ++n) {
+      ex[n] += dt * iex[n] * (PT(hy, n, sz) - PT(hz, n, sy));
+      ey[n] += dt * iey[n] * (-PT(hx, n, sz) + PT(hz, n, sx));
+      ez[n] += dt * iez[n] * (PT(hx, n, sy) - PT(hy, n, sx));
+    }
+    /* magnetic half: h^n -> h^{n+1} from e^{n+1/2} */
+    for (long n = 0; n < N; ++n) {
+      hx[n] += dt * ihx[n] * (P(o, ey, n, sz) - P(o, ez, n, sy));
+      hy[n] += dt * ihy[n] * (-P(o, ex, n, sz) + P(o, ez, n, sx));
+      hz[n] += dt * ihz[n] * (P(o, ex, n, sy) - P(o, ey, n, sx));
+    }
+    o->step += 1;
+  }
+  return 0;
+}
+
+/* Step bound of Yee's scheme in vacuum, Eq. (8):
+ * c*dt <= (dx^-2 + dy^-2 + dz^-2)^-1/2. */
+int oracle_yee_stable(double dx, double dy, double dz, double cdt) {
+  return cdt <= (1.0 + 1e-12) / sqrt(1.0 / (dx * dx) + 1.0 / (dy * dy) + 1.0 / (dz * dz));
+}
+
 long oracle_step_count(const oracle_t *o) { return o->step; }
 double oracle_dt(const oracle_t *o) { return o->dt; }
 int oracle_bunch_info(const oracle_t *o, int *c0, int *m_min, int *m_max, double *qcell) {
