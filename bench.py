@@ -78,6 +78,9 @@ def parse_args():
                    help="tile_x,tile_y,chunk_z (default: chosen by the autotuner, untimed)")
     p.add_argument("--no-autotune", action="store_true", help="keep the library's default shape")
     p.add_argument("--kernel", default="fused", choices=["fused", "reference"])
+    p.add_argument("--scheme", default="tetm", choices=["tetm", "yee"],
+                   help="yee: Yee's E/M leapfrog (Eq. (7)) on the same grid at its step bound (8), "
+                        "field-only, timed beside the TE/TM scheme per unit of simulated length")
     p.add_argument("--no-e2e", action="store_true")
     p.add_argument("--no-cpu-baseline", action="store_true")
     p.add_argument("--e2e-steps", type=int, default=0, help="0 = the workload's full step count")
@@ -841,10 +844,204 @@ def run_rz_reference(args):
     return 0
 
 
+# ---------------------------------------------------------------------------
+# Yee's scheme (Sec. 3, Eq. (7)) beside the TE/TM scheme
+# ---------------------------------------------------------------------------
+def yee_cdt(w):
+    """The step bound of Yee's scheme, Eq. (8): (dx^-2 + dy^-2 + dz^-2)^-1/2."""
+    return 1.0 / math.sqrt(w.dx ** -2 + w.dy ** -2 + w.dz ** -2)
+
+
+def yee_initial_ex(w):
+    """A smooth pulse of e_x along z (canonical layout; the library drops it on
+    entries that carry no field). Field-only runs need some initial field."""
+    import numpy as np
+    k = np.arange(w.nz + 1, dtype=np.float64)
+    prof = np.exp(-((k - w.nz / 4.0) / 20.0) ** 2)
+    return np.ascontiguousarray(np.broadcast_to(prof[:, None, None], (w.nz + 1, w.ny + 1, w.nx + 1)))
+
+
+def run_yee_mode(args):
+    """Yee's scheme on the workload's grid at c*dt = the bound (8), one fused
+    launch per step, and the TE/TM scheme (c*dt = dz) on the same grid and
+    initial field timed beside it: kernel time per step and per dz of simulated
+    length (the paper's cost comparison of Sec. 1 and Sec. 4.2)."""
+    rank, world, local = dist_env()
+    import numpy as np
+    import torch
+    torch.cuda.set_device(local)
+    dist = Dist(world)
+    from paper_0901_1053_gb300 import tetm
+    w = make_workload(args)
+    if args.eps is not None:
+        raise SystemExit("--scheme yee times the uniform-material workloads")
+    cdt = yee_cdt(w)
+    stream = torch.cuda.current_stream()
+    ex0 = yee_initial_ex(w)
+    K = args.steps
+
+    def make(scheme):
+        s = tetm.Solver(w.nx, w.ny, w.nz, w.dx, w.dy, w.dz, cdt if scheme == "yee" else w.cdt,
+                        w.precision, pec=w.pec)
+        if scheme == "yee":
+            s.set_scheme("yee")
+        s.set_kernel(args.kernel)
+        s.set(0, ex0)
+        s.set_stream(stream.cuda_stream)
+        return s
+
+    def timed(s, clocks=None):
+        s.step(args.warmup)
+        s.sync()
+        if clocks:
+            clocks.start()
+            time.sleep(0.5)
+        evs = [torch.cuda.Event(enable_timing=True) for _ in range(K + 1)]
+        dist.barrier()
+        torch.cuda.synchronize()
+        for i in range(K):
+            evs[i].record(stream)
+            s.step(1)
+        evs[K].record(stream)
+        torch.cuda.synchronize()
+        dist.barrier()
+        clk = clocks.stop() if clocks else None
+        total = evs[0].elapsed_time(evs[K])
+        return total, total / K, clk
+
+    # the TE/TM scheme first (no balances: kernel against kernel)
+    st = make("tetm")
+    info_t = st.info()
+    _, tetm_ms, _ = timed(st)
+    st.close()
+
+    s = make("yee")
+    info = s.info()
+    try:
+        uuid = str(torch.cuda.get_device_properties(local).uuid)
+    except Exception:
+        uuid = None
+    total_ms, kern_ms, clk = timed(s, ClockSampler(uuid))
+    max_ms = dist.max(total_ms)
+    s.close()
+
+    esz = 4 if w.precision == "fp32" else 8
+    bytes_per_cell = 12 * esz + 1
+    proc = info["processed_cells"] if args.kernel != "reference" else w.cells
+    gbs = bytes_per_cell * proc / (kern_ms * 1e-3) / 1e9
+    peak, peak_kind = measured_peak_hbm()
+    kname = "yee_fused" if args.kernel != "reference" else "yee_reference"
+    traffic = (profiled_traffic("%s_%s_%s.md" % (kname, w.precision, w.name), ("kernels_yee.cu",))
+               if args.kernel != "reference" else None)
+
+    e2e = None
+    if not args.no_e2e:
+        steps_e2e = args.e2e_steps or int(math.ceil(w.steps * w.dz / cdt))
+        pinned = torch.empty(w.pec.shape, dtype=torch.uint8, pin_memory=True).numpy()
+        pinned[...] = w.pec
+        ex_h = torch.empty(ex0.shape, dtype=torch.float64, pin_memory=True).numpy()
+        ex_h[...] = ex0
+        out = torch.empty(ex0.shape, dtype=torch.float64, pin_memory=True).numpy()
+        dist.barrier()
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        s2 = tetm.Solver(w.nx, w.ny, w.nz, w.dx, w.dy, w.dz, cdt, w.precision, pec=pinned)
+        s2.set_scheme("yee")
+        s2.set_kernel(args.kernel)
+        s2.set(0, ex_h)
+        s2.step(steps_e2e)
+        out[...] = s2.get(2)
+        t1 = time.perf_counter()
+        s2.close()
+        e2e_s = dist.max(t1 - t0)
+        e2e = {"value": world * w.cells * steps_e2e / e2e_s / 1e9, "unit": UNIT,
+               "h2d_bytes_per_step": int(pinned.nbytes + ex_h.nbytes), "d2h_bytes_per_step": int(out.nbytes),
+               "steps_per_call": steps_e2e, "seconds": round(e2e_s, 3),
+               "call": "tetm_create(host pec) + tetm_set_scheme(yee) + tetm_set_fields(ex, host) + "
+                       "tetm_step + tetm_get_fields(ez, host); the TE/TM solve's simulated length"}
+
+    cpu = None
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        v, dt, desc = yee_oracle_sample(w, min(w.nz, 256), 20 if w.nx * w.ny >= 256 * 256 else 400)
+        cpu = {"value": v, "unit": UNIT, "cores": 1, "kind": "oracle", "sample": desc,
+               "seconds": round(dt, 2), "host": host_cpu()}
+
+    yee_per_dz = kern_ms * w.dz / cdt
+    line = {
+        "metric": METRIC, "value": world * w.cells * K / (max_ms * 1e-3) / 1e9, "unit": UNIT,
+        "n_gpus": world, "steps": K, "warmup": args.warmup, "ms_per_step": max_ms / K,
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+        "dtype": "f32" if w.precision == "fp32" else "f64", "data": "synthetic",
+        "config": {"workload": w.name, "scheme": "yee (Eq. (7))", "nx": w.nx, "ny": w.ny, "nz": w.nz,
+                   "dx_mm": round(w.dx * 1e3, 4), "dz_mm": w.dz * 1e3,
+                   "cdt_over_dz": round(cdt / w.dz, 6), "cdt": "Eq. (8) bound", "fields": w.precision,
+                   "kernel": args.kernel, "tiling": [info["tile_x"], info["tile_y"], info["chunk_z"]],
+                   "work_items": info["work_items"], "cells": w.cells, "processed_cells": proc,
+                   "l2": "inputs larger than L2 (two field sets of %.1f GB each)"
+                         % (12 * esz * w.cells / 2 / 1e9),
+                   "parallelism": "replicas x%d" % world},
+        "roofline": {"bound": "hbm", "unit": "GB/s", "bytes_per_cell": bytes_per_cell, "achieved": gbs,
+                     "peak": peak, "frac": gbs / peak, "traffic": traffic, "peak_kind": peak_kind,
+                     "kernel": kname, "kernel_ms": kern_ms, "cells_per_launch": proc},
+        "versus_tetm": {"tetm_kernel_ms_per_step": tetm_ms, "tetm_cdt_over_dz": 1.0,
+                        "tetm_tiling": [info_t["tile_x"], info_t["tile_y"], info_t["chunk_z"]],
+                        "yee_kernel_ms_per_step": kern_ms,
+                        "tetm_ms_per_dz": tetm_ms, "yee_ms_per_dz": yee_per_dz,
+                        "tetm_time_over_yee_time": tetm_ms / yee_per_dz},
+        "cpu_baseline": cpu,
+        "e2e": e2e,
+        "gpu_launches": K if args.kernel != "reference" else 2 * K,
+        "clocks": clk,
+    }
+    if rank == 0:
+        print(json.dumps(line), flush=True)
+    dist.close()
+    return 0
+
+
+def yee_oracle_sample(w, planes, steps):
+    import dataclasses
+    from oracle import Oracle
+    sub = dataclasses.replace(w, nz=planes, pec=None if w.pec is None else w.pec[:planes].copy())
+    o = Oracle(sub.nx, sub.ny, sub.nz, sub.dx, sub.dy, sub.dz, yee_cdt(w), pec=sub.pec)
+    o.set(0, yee_initial_ex(sub))
+    t0 = time.perf_counter()
+    o.yee_step(steps)
+    dt = time.perf_counter() - t0
+    cells = sub.nx * sub.ny * sub.nz
+    return cells * steps / dt / 1e9, dt, "Yee's scheme on the first %d of %d planes of %s, %d steps, " \
+        "FP64, 1 thread" % (planes, w.nz, w.name, steps)
+
+
+def run_yee_reference(args):
+    """The oracle's Yee scheme on a bounded sample of the workload."""
+    rank, world, _ = dist_env()
+    if rank != 0:
+        return 0
+    w = make_workload(args)
+    budget_cells = 2.0e7 * 120.0 / max(1, args.steps + args.warmup)
+    planes = int(max(2, min(w.nz, budget_cells // (w.nx * w.ny))))
+    v, dt, desc = yee_oracle_sample(w, planes, args.steps)
+    line = {"metric": METRIC, "value": v, "unit": UNIT, "impl": "reference", "n_gpus": world,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": dt * 1e3 / args.steps,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+            "data": "synthetic", "config": {"workload": w.name, "scheme": "yee (Eq. (7))",
+                                            "sample_planes": planes},
+            "cpu_baseline": {"value": v, "unit": UNIT, "cores": 1, "kind": "oracle", "sample": desc},
+            "e2e": {"value": v, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+            "gpu_launches": 0}
+    print(json.dumps(line), flush=True)
+    return 0
+
+
 def main():
     args = parse_args()
     if args.impl == "reference":
+        if args.scheme == "yee":
+            return run_yee_reference(args)
         return run_rz_reference(args) if args.workload == "rz" else run_reference(args)
+    if args.scheme == "yee":
+        return run_yee_mode(args)
     if args.workload == "rz":
         return run_rz_mode(args)
     if args.workload == "batch":

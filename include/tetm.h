@@ -59,6 +59,10 @@ extern "C" {
 #define TETM_KERNEL_FUSED 0     /* one z-marching launch per step (default)        */
 #define TETM_KERNEL_REFERENCE 1 /* one launch per update equation: 10 per step     */
 
+/* ---- time-stepping schemes ------------------------------------------------ */
+#define TETM_SCHEME_TETM 0      /* the explicit TE/TM scheme, Eq. (23) (default)   */
+#define TETM_SCHEME_YEE 1       /* Yee's E/M leapfrog, Eq. (7), field-only         */
+
 /* ---- components ---------------------------------------------------------- */
 #define TETM_EX 0
 #define TETM_EY 1
@@ -224,6 +228,23 @@ int tetm_set_kernel(tetm_solver* s, int32_t kernel);
  * in {4, 8}) the block-tiled kernel. Any value 0 keeps the current one.
  * TETM_E_ARG for other values. */
 int tetm_set_tiling(tetm_solver* s, int32_t tile_x, int32_t tile_y, int32_t chunk_z);
+
+/* Time-stepping scheme (TETM_SCHEME_*), before the first step. Yee's scheme
+ * (Sec. 3, Eq. (7)) is the paper's comparison scheme on the same grid and
+ * material matrices: state (e^{n-1/2}, h^n), e^{n+1/2} = e^{n-1/2} +
+ * dt M_eps^-1 C~ h^n, h^{n+1} = h^n - dt M_mu^-1 C e^{n+1/2}. It carries no
+ * bunch (its step bound (8), c*dt <= (dx^-2 + dy^-2 + dz^-2)^-1/2, excludes
+ * the TE/TM scheme's c*dt = dz that the wake needs): initial fields come from
+ * tetm_set_fields, where e is read as e^{-1/2} and h as h^0. The fused path
+ * is one z-marching launch per step (float32: 56 x 30 owned of 64 x 32 loaded
+ * nodes per CTA; float64: 60 x 14 of 64 x 16; any chunk_z >= 4); material
+ * arrays run on the reference updates (two launches per step).
+ * TETM_E_UNSTABLE if c*dt breaks (8), TETM_E_STATE after the first step,
+ * with a bunch, in a batch or with periodic balances on. With Yee's scheme
+ * tetm_energy, tetm_charge_residual, tetm_set_balance_every (> 0),
+ * tetm_save and tetm_load give TETM_E_UNSUPPORTED (their quantities are the
+ * TE/TM scheme's), and tetm_set_tiling accepts only the chunk length. */
+int tetm_set_scheme(tetm_solver* s, int32_t scheme);
 
 /* Snapshot of the solve's bookkeeping. */
 int tetm_get_info(tetm_solver* s, tetm_info* info);

@@ -368,8 +368,30 @@ int queue_balances(tetm_solver* s, double* rec) {
   return TETM_OK;
 }
 
+// Yee's scheme (Eq. (7)): the fused launch (ping-pong) for one material,
+// else the two in-place reference launches
+template <typename T>
+int do_yee_steps(tetm_solver* s, int n) {
+  const bool fused = s->kernel == TETM_KERNEL_FUSED && s->uniform;
+  for (int q = 0; q < n; ++q) {
+    StepArgs<T> a = step_args<T>(s, fused);
+    for (int c = 0; c < 6; ++c) a.co.u[c] = (T)(2.0 * s->alpha * s->minv_c[c]);  // dt M^-1
+    a.b.on = 0;
+    a.b.obs_on = 0;
+    if (fused) {
+      if (s->n_work > 0) CK(launch_yee_fused_step<T>(a, s->stream));
+      s->cur = 1 - s->cur;
+    } else {
+      CK(launch_yee_reference_step<T>(a, s->stream));
+    }
+    s->step += 1;
+  }
+  return TETM_OK;
+}
+
 template <typename T>
 int do_steps(tetm_solver* s, int n) {
+  if (s->scheme == TETM_SCHEME_YEE) return do_yee_steps<T>(s, n);
   for (int q = 0; q < n; ++q) {
     const bool bal = s->bal_every > 0 && (s->step + 1) % s->bal_every == 0;
     if (s->kernel == TETM_KERNEL_FUSED) {
@@ -545,6 +567,7 @@ int tetm_create(const tetm_grid* g, const double* eps_r, const double* mu_r, con
   s->L = make_layout(g->nx, g->ny, g->nz, (int)s->esz);
   s->alpha = 0.5 * cdt / kC;
   s->stream = nullptr;
+  s->scheme = TETM_SCHEME_TETM;
   s->kernel = TETM_KERNEL_FUSED;
   s->uniform = uniform;
   s->vacuum = uniform && eps_u == 1.0 && mu_u == 1.0;
@@ -676,7 +699,9 @@ int tetm_set_stream(tetm_solver* s, void* st) {
 int tetm_set_kernel(tetm_solver* s, int32_t kernel) {
   if (!s || (kernel != TETM_KERNEL_FUSED && kernel != TETM_KERNEL_REFERENCE)) return TETM_E_ARG;
   if (s->in_batch) return TETM_E_STATE;
-  if (kernel == TETM_KERNEL_FUSED && !s->uniform && s->tile_x != 28) return TETM_E_UNSUPPORTED;
+  // (Yee's scheme runs material arrays on the reference updates whatever the kernel)
+  if (kernel == TETM_KERNEL_FUSED && !s->uniform && s->tile_x != 28 && s->scheme == TETM_SCHEME_TETM)
+    return TETM_E_UNSUPPORTED;
   s->kernel = kernel;
   return TETM_OK;
 }
@@ -687,6 +712,12 @@ int tetm_set_tiling(tetm_solver* s, int32_t tile_x, int32_t tile_y, int32_t chun
   const int tx = tile_x ? tile_x : s->tile_x;
   const int ty = tile_y ? tile_y : s->tile_y;
   const int cz = chunk_z ? chunk_z : s->chunk_z;
+  if (s->scheme == TETM_SCHEME_YEE) {  // Yee's fused kernel has one tile shape
+    if (tx != s->tile_x || ty != s->tile_y) return TETM_E_UNSUPPORTED;
+    if (cz < 4) return TETM_E_ARG;
+    s->chunk_z = cz;
+    return rebuild_work(s);
+  }
   if ((!fused_shape_ok(tx, ty) && !warp_shape_ok(tx, ty) && !slab_shape_ok(tx, ty)) || cz < 4)
     return TETM_E_ARG;
   // per-entry coefficients (general materials) run on the warp-tiled kernel only
@@ -700,9 +731,27 @@ int tetm_set_tiling(tetm_solver* s, int32_t tile_x, int32_t tile_y, int32_t chun
   return rebuild_work(s);
 }
 
+int tetm_set_scheme(tetm_solver* s, int32_t scheme) {
+  if (!s || (scheme != TETM_SCHEME_TETM && scheme != TETM_SCHEME_YEE)) return TETM_E_ARG;
+  if (scheme == s->scheme) return TETM_OK;
+  if (s->step != 0 || s->bunch || s->in_batch || s->bal_every > 0) return TETM_E_STATE;
+  if (scheme == TETM_SCHEME_YEE) {
+    const double dx = s->g.dx, dy = s->g.dy, dz = s->g.dz;
+    const double lim = 1.0 / sqrt(1.0 / (dx * dx) + 1.0 / (dy * dy) + 1.0 / (dz * dz));  // Eq. (8)
+    if (s->g.cdt > lim * (1.0 + 1e-12)) return TETM_E_UNSTABLE;
+    yee_shape((int)s->esz, &s->tile_x, &s->tile_y);
+  } else {  // the TE/TM scheme's default work shape
+    s->tile_x = (s->esz == 4 && s->uniform) ? 56 : 28;
+    s->tile_y = (s->esz == 4 && s->uniform) ? 28 : 20;
+  }
+  s->scheme = scheme;
+  return rebuild_work(s);
+}
+
 int tetm_set_bunch(tetm_solver* s, double sigma_z, double charge, int32_t i0, int32_t j0) {
   if (!s || !(sigma_z > 0) || !isfinite(sigma_z) || charge == 0 || !isfinite(charge)) return TETM_E_ARG;
   if (i0 < 1 || i0 > s->g.nx - 1 || j0 < 1 || j0 > s->g.ny - 1) return TETM_E_ARG;
+  if (s->scheme == TETM_SCHEME_YEE) return TETM_E_UNSUPPORTED;
   if (fabs(s->g.cdt - s->g.dz) > 1e-12 * s->g.dz) return TETM_E_NOT_MAGIC;
   if (s->step != 0 || s->bunch) return TETM_E_STATE;
   const double dz = s->g.dz;
@@ -819,6 +868,7 @@ int tetm_transverse_wake(tetm_solver* s, double* wx, double* wy, int32_t cap, in
 
 int tetm_energy(tetm_solver* s, double* w) {
   if (!s || !w) return TETM_E_ARG;
+  if (s->scheme != TETM_SCHEME_TETM) return TETM_E_UNSUPPORTED;
   const double* ma[6];
   for (int c = 0; c < 6; ++c) ma[c] = s->minv_a[c];
   cudaError_t e;
@@ -841,6 +891,7 @@ int tetm_energy(tetm_solver* s, double* w) {
 
 int tetm_charge_residual(tetm_solver* s, double* max_e, double* max_h, double* q_scale) {
   if (!s) return TETM_E_ARG;
+  if (s->scheme != TETM_SCHEME_TETM) return TETM_E_UNSUPPORTED;
   if (!s->prev_valid || s->step < 1) return TETM_E_STATE;
   int rc = s->esz == 8 ? queue_balances<double>(s, s->diag.out) : queue_balances<float>(s, s->diag.out);
   if (rc) return rc;
@@ -855,6 +906,7 @@ int tetm_charge_residual(tetm_solver* s, double* max_e, double* max_h, double* q
 
 int tetm_set_balance_every(tetm_solver* s, int32_t every) {
   if (!s || every < 0) return TETM_E_ARG;
+  if (every > 0 && s->scheme != TETM_SCHEME_TETM) return TETM_E_UNSUPPORTED;
   s->bal_every = every;
   return TETM_OK;
 }
@@ -929,6 +981,7 @@ struct CkptHeader {
 
 int tetm_save(tetm_solver* s, void* buf, size_t cap, size_t* used) {
   if (!s) return TETM_E_ARG;
+  if (s->scheme != TETM_SCHEME_TETM) return TETM_E_UNSUPPORTED;
   const int nw = s->bunch ? s->m_max - s->m_min + 1 : 0;
   const size_t fb = (size_t)s->L.count * s->esz;
   const size_t need = sizeof(CkptHeader) + 6 * fb + 3 * sizeof(double) * (size_t)nw;
@@ -959,6 +1012,7 @@ int tetm_save(tetm_solver* s, void* buf, size_t cap, size_t* used) {
 
 int tetm_load(tetm_solver* s, const void* buf, size_t size) {
   if (!s || !buf || size < sizeof(CkptHeader)) return TETM_E_ARG;
+  if (s->scheme != TETM_SCHEME_TETM) return TETM_E_UNSUPPORTED;
   if (s->in_batch) return TETM_E_STATE;
   CkptHeader h;
   memcpy(&h, buf, sizeof(h));

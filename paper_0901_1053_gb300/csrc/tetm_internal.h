@@ -139,6 +139,14 @@ int build_slab_maps(SlabMaps* m, void* const ez[2], void* const hz[2], const uin
 cudaError_t launch_fused_slab_step(const StepArgs<float>& a, const SlabMaps& m, int cur, int* err,
                                    cudaStream_t st);
 
+// ---- Yee's E/M leapfrog, Eq. (7) (kernels_yee.cu): the step arguments carry
+// dt M^-1 as the per-component constants --------------------------------------
+template <typename T>
+cudaError_t launch_yee_reference_step(const StepArgs<T>& a, cudaStream_t st);
+template <typename T>
+cudaError_t launch_yee_fused_step(const StepArgs<T>& a, cudaStream_t st);
+void yee_shape(int elem_bytes, int* tile_x, int* tile_y);  // owned tile of the fused kernel
+
 // transverse wake of a ping-pong step (kernels_step.cu): after the step
 // kernel, before the sets are swapped
 template <typename T>
@@ -200,6 +208,7 @@ struct tetm_solver {
   bool vacuum;    // no material arrays (eps_r = mu_r = 1)
   double alpha;   // dt/2
   cudaStream_t stream;
+  int scheme;     // TETM_SCHEME_*
   int kernel;
   int tile_x, tile_y, chunk_z;
   tetm::SlabMaps* slab;          // tensor maps of the slab kernel (built on first use)

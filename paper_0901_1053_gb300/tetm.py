@@ -32,12 +32,14 @@ TETM_FP64 = 0
 TETM_FP32 = 1
 TETM_KERNEL_FUSED = 0
 TETM_KERNEL_REFERENCE = 1
+TETM_SCHEME_TETM = 0
+TETM_SCHEME_YEE = 1
 COMPONENTS = ("ex", "ey", "ez", "hx", "hy", "hz")
 
 # Every function the header declares (checked by the CPU test suite).
 EXPORTS = ("tetm_create", "tetm_set_bunch", "tetm_step", "tetm_sync", "tetm_wake",
            "tetm_destroy", "tetm_energy", "tetm_charge_residual", "tetm_get_fields",
-           "tetm_set_fields", "tetm_set_stream", "tetm_set_kernel", "tetm_set_tiling",
+           "tetm_set_fields", "tetm_set_stream", "tetm_set_kernel", "tetm_set_tiling", "tetm_set_scheme",
            "tetm_set_observer", "tetm_transverse_wake",
            "tetm_get_info", "tetm_bytes_needed", "tetm_save", "tetm_load", "tetm_strerror",
            "tetm_set_balance_every", "tetm_balance_history", "tetm_energy_noalloc",
@@ -112,6 +114,7 @@ def _load():
         "tetm_set_stream": (ctypes.c_int, [vp, vp]),
         "tetm_set_kernel": (ctypes.c_int, [vp, i32]),
         "tetm_set_tiling": (ctypes.c_int, [vp, i32, i32, i32]),
+        "tetm_set_scheme": (ctypes.c_int, [vp, i32]),
         "tetm_get_info": (ctypes.c_int, [vp, ctypes.POINTER(tetm_info)]),
         "tetm_bytes_needed": (ctypes.c_int64, [ctypes.POINTER(tetm_grid)]),
         "tetm_save": (ctypes.c_int, [vp, vp, ctypes.c_size_t, ctypes.POINTER(ctypes.c_size_t)]),
@@ -333,6 +336,12 @@ class Solver:
 
     def set_tiling(self, tile_x=0, tile_y=0, chunk_z=0):
         _check(lib.tetm_set_tiling(self.h, int(tile_x), int(tile_y), int(chunk_z)), "tetm_set_tiling")
+
+    def set_scheme(self, scheme):
+        """'tetm' (Eq. (23), the default) or 'yee' (Yee's E/M leapfrog, Eq. (7),
+        field-only: e is read as e^{n-1/2}, h as h^n), before the first step."""
+        k = {"tetm": TETM_SCHEME_TETM, "yee": TETM_SCHEME_YEE}.get(scheme, scheme)
+        _check(lib.tetm_set_scheme(self.h, int(k)), "tetm_set_scheme")
 
     def info(self):
         i = tetm_info()
