@@ -412,9 +412,9 @@ def run_tetm(args):
                 "hbm_gbs": gbs, "bytes_per_cell": bytes_per_cell}
     kname = {28: "fused_step_warp", 56: "fused_step_slab"}.get(info["tile_x"], "fused_step")
     if args.eps is not None:
-        kname = "fused_step_warp_mat"
+        kname = "fused_step_slab_mat" if info["tile_x"] == 56 else "fused_step_warp_mat"
     prof_name = "%s_%s_%s.md" % (kname, w.precision, w.name)
-    sources = ("kernels_slab.cu",) if kname == "fused_step_slab" else ("kernels_step.cu", "kernels_warp.cu")
+    sources = ("kernels_slab.cu",) if kname.startswith("fused_step_slab") else ("kernels_step.cu", "kernels_warp.cu")
     traffic = profiled_traffic(prof_name, sources) if args.kernel != "reference" else None
     wake = s.wake()[0]
     hist = s.balance_history()

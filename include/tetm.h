@@ -214,19 +214,20 @@ int tetm_set_stream(tetm_solver* s, void* cuda_stream);
 
 /* Select the update kernels (TETM_KERNEL_*). With general materials (per-cell
  * eps_r / mu_r that differ) the fused path streams per-entry coefficient
- * arrays and needs the warp-tiled work shape (tile_x = 28, the default);
- * the block-tiled shapes then give TETM_E_UNSUPPORTED. */
+ * arrays and needs the warp-tiled work shape (tile_x = 28) or, in float32,
+ * the slab shape 56 x 28 (the defaults); the block-tiled shapes then give
+ * TETM_E_UNSUPPORTED. */
 int tetm_set_kernel(tetm_solver* s, int32_t kernel);
 
 /* Fused-kernel work shape: transverse tile tile_x x tile_y and z-chunk
  * length chunk_z >= 4 of one work item. 56 x 28 selects the float32 slab
  * kernel (one CTA of 512 threads per SM, tensor-staged e_z, h_z and activity
- * bytes; TETM_E_UNSUPPORTED in float64 or with material arrays; the default
- * for float32 without them, chunk 32); tile_x = 28 the warp-tiled kernel
- * (one warp per item, tile_y in {4, 8, 12, 16, 20, 28}; the default
- * otherwise, 28 x 20 x 32); tile_x = 32 (tile_y in {4, 8, 16}) or 64 (tile_y
- * in {4, 8}) the block-tiled kernel. Any value 0 keeps the current one.
- * TETM_E_ARG for other values. */
+ * bytes, or with material arrays e_z, h_z and the six coefficient arrays;
+ * TETM_E_UNSUPPORTED in float64; the float32 default, chunk 32); tile_x = 28
+ * the warp-tiled kernel (one warp per item, tile_y in {4, 8, 12, 16, 20, 28};
+ * the float64 default, 28 x 20 x 32); tile_x = 32 (tile_y in {4, 8, 16}) or
+ * 64 (tile_y in {4, 8}) the block-tiled kernel (one material only). Any value
+ * 0 keeps the current one. TETM_E_ARG for other values. */
 int tetm_set_tiling(tetm_solver* s, int32_t tile_x, int32_t tile_y, int32_t chunk_z);
 
 /* Time-stepping scheme (TETM_SCHEME_*), before the first step. Yee's scheme

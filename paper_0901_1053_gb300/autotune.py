@@ -126,7 +126,7 @@ class Autotuner:
     def tune(self, w, precision: Optional[str] = None,
              candidates: Optional[Sequence[Shape]] = None, materials: bool = False) -> Shape:
         """materials: the solve has eps/mu arrays (per-entry coefficients run on
-        the warp-tiled kernel only, tile_x = 28)."""
+        the warp-tiled kernel, tile_x = 28, and the float32 slab kernel, 56 x 28)."""
         precision = precision or w.precision
         k = self.key(w, precision) + ("|materials" if materials else "")
         if k in self.cache:
@@ -135,7 +135,7 @@ class Autotuner:
         if candidates is None:
             cands += [c for c in self.wave_fitted(w, precision) if c not in cands]
         if materials:
-            cands = [c for c in cands if c[0] == 28]
+            cands = [c for c in cands if c[0] == 28 or (c[0], c[1]) == (56, 28)]
         times = self.measure(w, precision, cands)
         best = min(times, key=times.get)
         self.cache[k] = list(best)

@@ -405,7 +405,7 @@ int do_steps(tetm_solver* s, int n) {
               s->slab = new (std::nothrow) SlabMaps();
               void* ez[2] = {s->set[0][kEZ], s->set[1][kEZ]};
               void* hz[2] = {s->set[0][kHZ], s->set[1][kHZ]};
-              if (!s->slab || build_slab_maps(s->slab, ez, hz, s->mask, s->L) != 0) {
+              if (!s->slab || build_slab_maps(s->slab, ez, hz, s->mask, s->uniform ? nullptr : s->ua, s->L) != 0) {
                 delete s->slab;
                 s->slab = nullptr;
                 return TETM_E_UNSUPPORTED;
@@ -571,10 +571,10 @@ int tetm_create(const tetm_grid* g, const double* eps_r, const double* mu_r, con
   s->kernel = TETM_KERNEL_FUSED;
   s->uniform = uniform;
   s->vacuum = uniform && eps_u == 1.0 && mu_u == 1.0;
-  // float32 without material arrays: the slab kernel (kernels_slab.cu); else
-  // the warp-tiled kernel (kernels_warp.cu)
-  s->tile_x = (s->esz == 4 && uniform) ? 56 : 28;
-  s->tile_y = (s->esz == 4 && uniform) ? 28 : 20;
+  // float32: the slab kernel (kernels_slab.cu); float64: the warp-tiled
+  // kernel (kernels_warp.cu)
+  s->tile_x = s->esz == 4 ? 56 : 28;
+  s->tile_y = s->esz == 4 ? 28 : 20;
   s->chunk_z = 32;
   int rc = TETM_OK;
   const size_t fbytes = (size_t)s->L.count * s->esz;
@@ -700,7 +700,8 @@ int tetm_set_kernel(tetm_solver* s, int32_t kernel) {
   if (!s || (kernel != TETM_KERNEL_FUSED && kernel != TETM_KERNEL_REFERENCE)) return TETM_E_ARG;
   if (s->in_batch) return TETM_E_STATE;
   // (Yee's scheme runs material arrays on the reference updates whatever the kernel)
-  if (kernel == TETM_KERNEL_FUSED && !s->uniform && s->tile_x != 28 && s->scheme == TETM_SCHEME_TETM)
+  if (kernel == TETM_KERNEL_FUSED && !s->uniform && s->tile_x != 28 && !slab_shape_ok(s->tile_x, s->tile_y) &&
+      s->scheme == TETM_SCHEME_TETM)
     return TETM_E_UNSUPPORTED;
   s->kernel = kernel;
   return TETM_OK;
@@ -720,8 +721,9 @@ int tetm_set_tiling(tetm_solver* s, int32_t tile_x, int32_t tile_y, int32_t chun
   }
   if ((!fused_shape_ok(tx, ty) && !warp_shape_ok(tx, ty) && !slab_shape_ok(tx, ty)) || cz < 4)
     return TETM_E_ARG;
-  // per-entry coefficients (general materials) run on the warp-tiled kernel only
-  if (!s->uniform && tx != 28 && s->kernel == TETM_KERNEL_FUSED) return TETM_E_UNSUPPORTED;
+  // per-entry coefficients (general materials) run on the warp-tiled and slab kernels
+  if (!s->uniform && tx != 28 && !slab_shape_ok(tx, ty) && s->kernel == TETM_KERNEL_FUSED)
+    return TETM_E_UNSUPPORTED;
   // the slab kernel is float32 only
   if (slab_shape_ok(tx, ty) && s->esz != 4) return TETM_E_UNSUPPORTED;
   if (tx == s->tile_x && ty == s->tile_y && cz == s->chunk_z && s->work) return TETM_OK;
@@ -741,8 +743,8 @@ int tetm_set_scheme(tetm_solver* s, int32_t scheme) {
     if (s->g.cdt > lim * (1.0 + 1e-12)) return TETM_E_UNSTABLE;
     yee_shape((int)s->esz, &s->tile_x, &s->tile_y);
   } else {  // the TE/TM scheme's default work shape
-    s->tile_x = (s->esz == 4 && s->uniform) ? 56 : 28;
-    s->tile_y = (s->esz == 4 && s->uniform) ? 28 : 20;
+    s->tile_x = s->esz == 4 ? 56 : 28;
+    s->tile_y = s->esz == 4 ? 28 : 20;
   }
   s->scheme = scheme;
   return rebuild_work(s);

@@ -27,6 +27,8 @@
 #include <cudaTypedefs.h>
 
 #include <algorithm>
+#include <cstring>
+#include <type_traits>
 
 #include "tetm_internal.h"
 
@@ -38,17 +40,37 @@ constexpr int kSX = 64, kSY = 32;   // loaded columns, rows
 constexpr int kOX = 56, kOY = 28;   // owned columns, rows
 constexpr int kQ = kSX / 4;         // column quads per row
 constexpr int kSThreads = kQ * kSY; // 512
-constexpr int kSD = 6;              // planes in the ring
 constexpr int kMaskW = 80;          // activity bytes per row (from a 16-byte aligned column)
 constexpr int kSlabPolls = 1 << 18;
-constexpr unsigned kSlotBytes = 2u * kSX * kSY * 4u + (unsigned)kMaskW * kSY;
 
-struct SlabSmem {
-  float ez[kSD][kSY][kSX];
-  float hz[kSD][kSY][kSX];
-  uint8_t mk[kSD][kSY][kMaskW];
+// One material: a six-plane ring of e_z, h_z and the activity bytes (one
+// coefficient per component, switched by the bytes).
+struct SlabSmemU {
+  static constexpr int SD = 6;      // planes in the ring
+  static constexpr unsigned slot_bytes = 2u * kSX * kSY * 4u + (unsigned)kMaskW * kSY;
+  float ez[SD][kSY][kSX];
+  float hz[SD][kSY][kSX];
+  uint8_t mk[SD][kSY][kMaskW];
   float x1[kSY][kSX], x2[kSY][kSX];
-  uint64_t bar[kSD];
+  uint64_t bar[SD];
+};
+// Material arrays: a three-plane ring of e_z, h_z and the six per-entry
+// coefficient arrays (alpha M^-1, 2 alpha M^-1 for e_z and h_z), 208 KB.
+struct SlabSmemM {
+  static constexpr int SD = 3;
+  static constexpr unsigned slot_bytes = 8u * kSX * kSY * 4u;
+  float ez[SD][kSY][kSX];
+  float hz[SD][kSY][kSX];
+  float co[SD][6][kSY][kSX];
+  float x1[kSY][kSX], x2[kSY][kSX];
+  uint64_t bar[SD];
+};
+template <bool MAT>
+using SlabSmem = typename std::conditional<MAT, SlabSmemM, SlabSmemU>::type;
+
+// the six coefficient arrays' tensor maps (material runs)
+struct CoefMaps {
+  CUtensorMap m[6];
 };
 
 __device__ __forceinline__ unsigned su32(const void* p) { return (unsigned)__cvta_generic_to_shared(p); }
@@ -105,12 +127,15 @@ __device__ __forceinline__ float right_of(float v0, int q) {
   return q + 1 < kQ ? t : 0.f;
 }
 
+template <bool MAT>
 __global__ void __launch_bounds__(kSThreads, 1)
 fused_step_slab(const StepArgs<float> a, const __grid_constant__ CUtensorMap tm_ez,
                 const __grid_constant__ CUtensorMap tm_hz, const __grid_constant__ CUtensorMap tm_mk,
-                int* err) {
+                const __grid_constant__ CoefMaps tm_co, int* err) {
+  using Smem = SlabSmem<MAT>;
+  constexpr int kSD = Smem::SD;
   extern __shared__ __align__(128) unsigned char slab_raw[];
-  SlabSmem& S = *reinterpret_cast<SlabSmem*>(slab_raw);
+  Smem& S = *reinterpret_cast<Smem*>(slab_raw);
   const int tid = threadIdx.x, q = tid % kQ, row = tid / kQ;
   if (tid == 0)
     for (int s = 0; s < kSD; ++s) bar_init(&S.bar[s]);
@@ -163,10 +188,15 @@ fused_step_slab(const StepArgs<float> a, const __grid_constant__ CUtensorMap tm_
     auto issue = [&](int k) {  // plane k into its slot (one thread)
       const int s = (k - kstart) % kSD;
       asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
-      bar_expect(&S.bar[s], kSlotBytes);
+      bar_expect(&S.bar[s], Smem::slot_bytes);
       tma3(&S.ez[s][0][0], &tm_ez, cx, cy, k + 1, &S.bar[s]);
       tma3(&S.hz[s][0][0], &tm_hz, cx, cy, k + 1, &S.bar[s]);
-      tma3(&S.mk[s][0][0], &tm_mk, mx, cy, k + 1, &S.bar[s]);
+      if constexpr (MAT) {
+#pragma unroll
+        for (int c = 0; c < 6; ++c) tma3(&S.co[s][c][0][0], &tm_co.m[c], cx, cy, k + 1, &S.bar[s]);
+      } else {
+        tma3(&S.mk[s][0][0], &tm_mk, mx, cy, k + 1, &S.bar[s]);
+      }
     };
     if (tid == 0)
       for (int k = kstart; k < kstart + min(kSD, nplanes); ++k) issue(k);
@@ -203,19 +233,36 @@ fused_step_slab(const StepArgs<float> a, const __grid_constant__ CUtensorMap tm_
       const Q4 hz = lds4(shz + row * kSX + 4 * q);
       const Q4 hzD = row >= 1 ? lds4(shz + (row - 1) * kSX + 4 * q) : Q4{{0.f, 0.f, 0.f, 0.f}};
       const float hzL = q >= 1 ? shz[row * kSX + 4 * q - 1] : 0.f;
-      const unsigned mw = *reinterpret_cast<const unsigned*>(&S.mk[s][row][moff + 4 * q]);
-
       float cHX[4], cHY[4], cEZ[4], cEX[4], cEY[4], cHZ[4], dey[4], dex[4];
+      if constexpr (MAT) {  // per-entry coefficients from the slot
+        const Q4 c0 = lds4(&S.co[s][kEX][row][4 * q]), c1 = lds4(&S.co[s][kEY][row][4 * q]);
+        const Q4 c2 = lds4(&S.co[s][kEZ][row][4 * q]), c3 = lds4(&S.co[s][kHX][row][4 * q]);
+        const Q4 c4 = lds4(&S.co[s][kHY][row][4 * q]), c5 = lds4(&S.co[s][kHZ][row][4 * q]);
+#pragma unroll
+        for (int e = 0; e < 4; ++e) {
+          cEX[e] = c0.v[e];
+          cEY[e] = c1.v[e];
+          cEZ[e] = c2.v[e];
+          cHX[e] = c3.v[e];
+          cHY[e] = c4.v[e];
+          cHZ[e] = c5.v[e];
+        }
+      } else {  // one coefficient per component, switched by the activity bytes
+        const unsigned mw = *reinterpret_cast<const unsigned*>(&S.mk[s][row][moff + 4 * q]);
+#pragma unroll
+        for (int e = 0; e < 4; ++e) {
+          const unsigned m = (mw >> (8 * e)) & 0xFFu;
+          cEX[e] = (m & 1) ? uEX : 0.f;
+          cEY[e] = (m & 2) ? uEY : 0.f;
+          cEZ[e] = (m & 4) ? uEZ : 0.f;
+          cHX[e] = (m & 8) ? uHX : 0.f;
+          cHY[e] = (m & 16) ? uHY : 0.f;
+          cHZ[e] = (m & 32) ? uHZ : 0.f;
+        }
+      }
       Q4 hxa, hya;
 #pragma unroll
       for (int e = 0; e < 4; ++e) {
-        const unsigned m = (mw >> (8 * e)) & 0xFFu;
-        cEX[e] = (m & 1) ? uEX : 0.f;
-        cEY[e] = (m & 2) ? uEY : 0.f;
-        cEZ[e] = (m & 4) ? uEZ : 0.f;
-        cHX[e] = (m & 8) ? uHX : 0.f;
-        cHY[e] = (m & 16) ? uHY : 0.f;
-        cHZ[e] = (m & 32) ? uHZ : 0.f;
         dey[e] = ey1.v[e] - ey0.v[e];
         dex[e] = ex1.v[e] - ex0.v[e];
         const float ezx = e < 3 ? ez.v[e + 1] : ezR;
@@ -361,7 +408,8 @@ CUresult encode3d(CUtensorMap* map, CUtensorMapDataType type, void* base, const 
 
 bool slab_shape_ok(int tx, int ty) { return tx == kOX && ty == kOY; }
 
-int build_slab_maps(SlabMaps* m, void* const ez[2], void* const hz[2], const uint8_t* mask, const Layout& L) {
+int build_slab_maps(SlabMaps* m, void* const ez[2], void* const hz[2], const uint8_t* mask,
+                    void* const co[6], const Layout& L) {
   static_assert(sizeof(CUtensorMap) <= sizeof(m->ez[0]), "tensor map storage");
   // the tiled copies need 16-byte row strides and 16-byte box starts
   if ((L.px * 4) % 16 != 0 || L.px % 16 != 0 || (L.ox % 4) != 0) return -1;
@@ -375,19 +423,26 @@ int build_slab_maps(SlabMaps* m, void* const ez[2], void* const hz[2], const uin
   if (encode3d(reinterpret_cast<CUtensorMap*>(m->mk), CU_TENSOR_MAP_DATA_TYPE_UINT8, const_cast<uint8_t*>(mask),
                L, 1, kMaskW) != CUDA_SUCCESS)
     return -1;
+  m->has_co = co != nullptr;
+  if (co)
+    for (int c = 0; c < 6; ++c)
+      if (!co[c] || encode3d(reinterpret_cast<CUtensorMap*>(m->co[c]), CU_TENSOR_MAP_DATA_TYPE_FLOAT32, co[c], L, 4,
+                             kSX) != CUDA_SUCCESS)
+        return -1;
   return 0;
 }
 
-cudaError_t launch_fused_slab_step(const StepArgs<float>& a, const SlabMaps& m, int cur, int* err,
-                                   cudaStream_t st) {
+namespace {
+template <bool MAT>
+cudaError_t launch_slab(const StepArgs<float>& a, const SlabMaps& m, int cur, int* err, cudaStream_t st) {
   static int sms = 0;
-  const size_t smem = sizeof(SlabSmem);
+  const size_t smem = sizeof(SlabSmem<MAT>);
   if (!sms) {
     int dev = 0;
     cudaError_t e = cudaGetDevice(&dev);
     if (e == cudaSuccess) e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
     if (e == cudaSuccess)
-      e = cudaFuncSetAttribute(fused_step_slab, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+      e = cudaFuncSetAttribute(fused_step_slab<MAT>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) {
       sms = 0;
       return e;
@@ -398,8 +453,22 @@ cudaError_t launch_fused_slab_step(const StepArgs<float>& a, const SlabMaps& m, 
   const CUtensorMap& mez = *reinterpret_cast<const CUtensorMap*>(m.ez[cur]);
   const CUtensorMap& mhz = *reinterpret_cast<const CUtensorMap*>(m.hz[cur]);
   const CUtensorMap& mmk = *reinterpret_cast<const CUtensorMap*>(m.mk);
-  fused_step_slab<<<std::min(items, sms), kSThreads, smem, st>>>(a, mez, mhz, mmk, err);
+  CoefMaps mco;
+  if constexpr (MAT) {
+    for (int c = 0; c < 6; ++c) mco.m[c] = *reinterpret_cast<const CUtensorMap*>(m.co[c]);
+  } else {
+    memset(&mco, 0, sizeof(mco));
+  }
+  fused_step_slab<MAT><<<std::min(items, sms), kSThreads, smem, st>>>(a, mez, mhz, mmk, mco, err);
   return cudaGetLastError();
+}
+}  // namespace
+
+cudaError_t launch_fused_slab_step(const StepArgs<float>& a, const SlabMaps& m, int cur, int* err,
+                                   cudaStream_t st) {
+  // per-entry coefficient arrays (material runs) need their tensor maps
+  if (a.co.ua[0]) return m.has_co ? launch_slab<true>(a, m, cur, err, st) : cudaErrorInvalidValue;
+  return launch_slab<false>(a, m, cur, err, st);
 }
 
 }  // namespace tetm

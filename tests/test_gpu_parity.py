@@ -189,11 +189,17 @@ def test_materials_block_tiles_unsupported(tetm):
     assert e.value.code == tetm.TETM_E_UNSUPPORTED
 
 
-def test_dielectric_collimator_fp32_wake(tetm):
+@pytest.mark.parametrize("tiling", [None, (56, 28, 32), (28, 20, 32)])
+def test_dielectric_collimator_fp32_wake(tetm, tiling):
     """A collimator with a dielectric liner (eps_r = 3 over the narrow part),
-    FP32 fused kernel with coefficient arrays, against the FP64 oracle."""
+    FP32 fused kernels with coefficient arrays (slab, the default, and
+    warp-tiled), against the FP64 oracle."""
     w, eps = wl.dielectric_collimator(n=40, nz=120, sigma_cells=3.0, precision="fp32")
     s = tetm.Solver(w.nx, w.ny, w.nz, w.dx, w.dy, w.dz, w.cdt, "fp32", eps_r=eps, pec=w.pec)
+    if tiling:
+        s.set_tiling(*tiling)
+    else:
+        assert (s.info()["tile_x"], s.info()["tile_y"]) == (56, 28)
     s.set_bunch(w.sigma, w.charge, w.i0, w.j0)
     s.step(w.steps)
     o = Oracle(w.nx, w.ny, w.nz, w.dx, w.dy, w.dz, w.cdt, eps_r=eps, pec=w.pec)
@@ -438,3 +444,64 @@ def test_slab_kernel_is_float32_only(tetm):
     with pytest.raises(tetm.TetmError) as e:
         s.set_tiling(56, 28, 32)
     assert e.value.code == tetm.TETM_E_UNSUPPORTED
+
+
+# ---------------------------------------------------------------------------
+# The slab kernel with per-entry coefficient arrays (general materials)
+# ---------------------------------------------------------------------------
+
+@pytest.mark.parametrize("dims", [(130, 70, 41), (57, 29, 33), (9, 7, 12)])
+def test_slab_kernel_with_materials_fp32(tetm, dims):
+    """Random per-cell eps_r, mu_r and PEC on grids of several slab tiles with
+    ragged tails: the slab kernel against the float64 oracle (its error is that
+    of the warp-tiled kernel with coefficient arrays) and against that kernel."""
+    nx, ny, nz = dims
+    eps, mu, pec = wl.random_materials(nx, ny, nz, sum(dims))
+    rng = np.random.default_rng(7 + sum(dims))
+    init = {c: rng.standard_normal((nz + 1, ny + 1, nx + 1)) for c in ("ex", "ey", "ez", "hx", "hy", "hz")}
+    sigma, i0, j0 = 2.5 * wl.DZ, nx // 2, ny // 2
+    pec[:, max(0, j0 - 2):j0 + 2, max(0, i0 - 2):i0 + 2] = 0     # a clear bunch line
+    steps = nz + 20
+    out = {}
+    for tiling in [(56, 28, 32), (28, 20, 32)]:
+        s = tetm.Solver(nx, ny, nz, wl.DXY, wl.DXY, wl.DZ, 0.0, "fp32", eps_r=eps, mu_r=mu, pec=pec)
+        s.set_tiling(*tiling)
+        for c, a in init.items():
+            s.set(c, a)
+        s.set_bunch(sigma, 1e-9, i0, j0)
+        s.step(steps)
+        s.sync()
+        out[tiling] = ({c: s.get(c) for c in init}, s.wake()[0])
+        s.close()
+    o = Oracle(nx, ny, nz, wl.DXY, wl.DXY, wl.DZ, 0.0, eps_r=eps, mu_r=mu, pec=pec)
+    for c, a in init.items():
+        o.set(c, a)
+    o.set_bunch(sigma, 1e-9, i0, j0)
+    o.step(steps)
+    slab, warp = out[(56, 28, 32)], out[(28, 20, 32)]
+    for fam in (("ex", "ey", "ez"), ("hx", "hy", "hz")):
+        peak = max(np.max(np.abs(o.get(c))) for c in fam)
+        for c in fam:
+            e_slab = np.max(np.abs(slab[0][c] - o.get(c)))
+            e_warp = np.max(np.abs(warp[0][c] - o.get(c)))
+            assert e_slab <= 2.0 * e_warp + 1e-6 * peak, (c, e_slab / peak, e_warp / peak)
+            assert np.max(np.abs(slab[0][c] - warp[0][c])) <= 2.0 * e_warp + 1e-6 * peak, c
+    assert rel_err(slab[1], o.wake()[0]) <= TOL32_WAKE
+    assert rel_err(slab[1], warp[1]) <= 1e-5
+
+
+def test_slab_kernel_with_materials_chunk_lengths_are_bitwise_identical(tetm):
+    w, eps = wl.dielectric_collimator(n=100, nz=90, sigma_cells=3.0, precision="fp32")
+    ref = None
+    for cz in (32, 5, 64):
+        s = tetm.Solver(w.nx, w.ny, w.nz, w.dx, w.dy, w.dz, w.cdt, "fp32", eps_r=eps, pec=w.pec)
+        s.set_tiling(56, 28, cz)
+        s.set_bunch(w.sigma, w.charge, w.i0, w.j0)
+        s.step(110)
+        got = [s.get(c) for c in ("ex", "ey", "ez", "hx", "hy", "hz")] + [s.wake()[0]]
+        s.close()
+        if ref is None:
+            ref = got
+            continue
+        for a, b in zip(got, ref):
+            assert np.array_equal(a, b), cz
