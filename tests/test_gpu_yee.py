@@ -171,3 +171,35 @@ def test_yee_api_states(tetm):
         tetm.Batch([s], [10])                                    # batches run the TE/TM scheme
     assert e.value.code == tetm.TETM_E_UNSUPPORTED
     s.close()
+
+
+@pytest.mark.parametrize("precision,tol", [("fp32", TOL32), ("fp64", TOL64)])
+def test_yee_full_size_collimator_head_matches_oracle(tetm, precision, tol):
+    """256x256x2048 step collimator at Yee's bound, the benchmark's launch
+    configuration. The initial field fills planes 0..9 only; one step spreads
+    it by at most one plane, so after n steps the oracle on the first 72 planes
+    of the same geometry reproduces the full box: planes 0..60 entry by entry,
+    nothing beyond plane 11 + n."""
+    w = wl.step_collimator(precision=precision)
+    n = 40
+    cdt = yee_bound(w.dx, w.dy, w.dz)
+    o = Oracle(w.nx, w.ny, 72, w.dx, w.dy, w.dz, cdt=cdt, pec=w.pec[:72].copy())
+    f0 = initial_fields(o, 31)
+    for c in range(6):
+        f0[c][10:] = 0.0
+        o.set(c, f0[c])
+    o.yee_step(n)
+    s = tetm.Solver(w.nx, w.ny, w.nz, w.dx, w.dy, w.dz, cdt, precision, pec=w.pec)
+    s.set_scheme("yee")
+    full = np.zeros((w.nz + 1, w.ny + 1, w.nx + 1))
+    for c in range(6):
+        full[:73] = f0[c]
+        s.set(c, full)
+    s.step(n)
+    s.sync()
+    for c in range(6):
+        g = s.get(c)
+        r = o.get(c)
+        assert np.all(g[12 + n:] == 0.0), c
+        assert rel_err(g[:61], r[:61]) <= tol, c
+    s.close()
