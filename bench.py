@@ -354,7 +354,7 @@ def run_tetm(args):
         args.tiling_used = tuple(int(x) for x in args.tiling.split(","))
     elif args.kernel == "fused" and not args.no_autotune:
         from paper_0901_1053_gb300.autotune import Autotuner
-        args.tiling_used = Autotuner().tune(w, w.precision, materials=args.eps is not None)
+        args.tiling_used = Autotuner().tune(w, w.precision, eps_r=args.eps)
     else:
         args.tiling_used = None
     if args.tiling_used:
