@@ -439,6 +439,7 @@ def run_tetm(args):
         s2.set_kernel(args.kernel)
         if args.tiling_used:
             s2.set_tiling(*args.tiling_used)
+        s2.set_balance_every(args.balance_every)   # the same path as the device-timed steps
         s2.step(steps_e2e)
         wk2 = s2.wake()[0]
         out[:] = wk2
@@ -450,7 +451,8 @@ def run_tetm(args):
                "h2d_bytes_per_step": int(pinned.nbytes if pinned is not None else 0),
                "d2h_bytes_per_step": int(out.nbytes), "steps_per_call": steps_e2e,
                "seconds": round(e2e_s, 3),
-               "call": "tetm_create(host pec) + tetm_set_bunch + tetm_step + tetm_wake(host)"}
+               "call": "tetm_create(host pec) + tetm_set_bunch + tetm_set_balance_every + tetm_step + "
+                       "tetm_wake(host)"}
         if args.check and w.precision == "fp32" and steps_e2e == w.steps:
             # the same full solve with float64 fields (observer on the bunch
             # line), every wake's error relative to its peak
