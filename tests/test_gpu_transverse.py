@@ -210,3 +210,29 @@ def test_observer_arguments_and_state(tetm):
     with pytest.raises(tetm.TetmError) as e:
         s.set_observer(3, 3)                       # after the first step
     assert e.value.code == tetm.TETM_E_STATE
+
+
+@pytest.mark.parametrize("tiling", [None, (28, 20, 16)])
+def test_transverse_wake_with_materials_fp32(tetm, tiling):
+    """Per-cell eps_r, mu_r and PEC in float32: the slab kernel with coefficient
+    arrays (the default) and the warp-tiled one, within 1e-4 of the peak."""
+    nx, ny, nz = 70, 41, 60
+    eps, mu, pec = wl.random_materials(nx, ny, nz, 12)
+    pec[:, 15:27, 28:42] = 0                       # a clear channel around the bunch line
+    s = tetm.Solver(nx, ny, nz, wl.DXY, wl.DXY, wl.DZ, 0.0, "fp32", eps_r=eps, mu_r=mu, pec=pec)
+    if tiling:
+        s.set_tiling(*tiling)
+    sigma = 2.5 * wl.DZ
+    s.set_bunch(sigma, 1e-9, 35, 21)
+    s.set_observer(34, 20)
+    steps = nz + 30
+    s.step(steps)
+    o = Oracle(nx, ny, nz, wl.DXY, wl.DXY, wl.DZ, 0.0, eps_r=eps, mu_r=mu, pec=pec)
+    o.set_bunch(sigma, 1e-9, 35, 21)
+    o.set_observer(34, 20)
+    o.step(steps)
+    rx, ry = o.transverse_wake()
+    gx, gy = s.transverse_wake()
+    assert rel_err(gx, rx) <= TOL32_WAKE
+    assert rel_err(gy, ry) <= TOL32_WAKE
+    assert rel_err(s.wake()[0], o.wake()[0]) <= TOL32_WAKE
