@@ -214,6 +214,58 @@ def request_stream(count: int = 2000, rate: float = 40.0, seed: int = 9011054, n
     return out
 
 
+def coax_pec(nx: int, ny: int, nz: int, rod) -> np.ndarray:
+    """Coaxial line along z: the PEC rod cells [i_lo, i_hi) x [j_lo, j_hi) in every
+    plane; the PEC box is the outer conductor."""
+    i_lo, i_hi, j_lo, j_hi = rod
+    pec = np.zeros((nz, ny, nx), dtype=np.uint8)
+    pec[:, j_lo:j_hi, i_lo:i_hi] = 1
+    return pec
+
+
+def coax_tem_e(nx: int, ny: int, dx: float, dy: float, rod):
+    """Transverse shape of the coaxial line's TEM field, an input profile: the
+    node potential phi = 1 on the rod's nodes, 0 on the box wall, and
+    (phi(i+1) - 2 phi(i) + phi(i-1)) / dx^2 + (phi(j+1) - 2 phi(j) + phi(j-1)) / dy^2 = 0
+    at every other node; returns the edge voltages e_x = -(phi(i+1,j) - phi(i,j)) and
+    e_y = -(phi(i,j+1) - phi(i,j)) as (ny+1, nx+1) arrays."""
+    import scipy.sparse as sp
+    import scipy.sparse.linalg as spl
+    i_lo, i_hi, j_lo, j_hi = rod
+    mx, my = nx + 1, ny + 1
+    fixed = np.zeros((my, mx), dtype=bool)
+    phi = np.zeros((my, mx))
+    fixed[0, :] = fixed[-1, :] = fixed[:, 0] = fixed[:, -1] = True
+    fixed[j_lo:j_hi + 1, i_lo:i_hi + 1] = True
+    phi[j_lo:j_hi + 1, i_lo:i_hi + 1] = 1.0
+    free = np.flatnonzero(~fixed.ravel())
+    pos = -np.ones(mx * my, dtype=np.int64)
+    pos[free] = np.arange(free.size)
+    wx, wy = 1.0 / dx ** 2, 1.0 / dy ** 2
+    rows, cols, vals = [], [], []
+    rhs = np.zeros(free.size)
+    for q, node in enumerate(free):
+        j, i = divmod(int(node), mx)
+        rows.append(q)
+        cols.append(q)
+        vals.append(-2.0 * (wx + wy))
+        for (jj, ii), w in (((j, i - 1), wx), ((j, i + 1), wx), ((j - 1, i), wy), ((j + 1, i), wy)):
+            nb = jj * mx + ii
+            if fixed[jj, ii]:
+                rhs[q] -= w * phi[jj, ii]
+            else:
+                rows.append(q)
+                cols.append(int(pos[nb]))
+                vals.append(w)
+    a = sp.csr_matrix((vals, (rows, cols)), shape=(free.size, free.size))
+    phi.ravel()[free] = spl.spsolve(a.tocsc(), rhs)
+    ex = np.zeros((my, mx))
+    ey = np.zeros((my, mx))
+    ex[:, :-1] = -(phi[:, 1:] - phi[:, :-1])
+    ey[:-1, :] = -(phi[1:, :] - phi[:-1, :])
+    return ex, ey
+
+
 def random_fields(shape, seed: int, scale: float = 1.0):
     """Six seeded standard-normal arrays (ex, ey, ez, hx, hy, hz)."""
     rng = np.random.default_rng(seed)

@@ -8,7 +8,9 @@ What fixes it, other than itself:
 * the step bound (8): no growth at the bound, growth above it, and growth at
   the TE/TM scheme's step c*dt = dz on the paper's mesh dx = dy = sqrt(2) dz;
 * the leapfrog energy 1/2 e^{n+1/2} M_eps e^{n+1/2} + 1/2 h^n M_mu h^{n+1},
-  conserved exactly (to rounding) by the exact skew form of Eq. (7).
+  conserved exactly (to rounding) by the exact skew form of Eq. (7);
+* the z-dispersion of a TEM pulse on a coaxial line against the closed form of
+  Eq. (10), and its phase error against the dispersion-free motion (Eq. (11)).
 """
 import math
 
@@ -151,3 +153,47 @@ def test_yee_keeps_inactive_entries_zero_and_refuses_a_bunch():
     b.set_bunch(2 * MM, 1e-9, 2, 2)
     with pytest.raises(ValueError):
         b.yee_step(1)
+
+
+def test_yee_tem_pulse_on_a_coaxial_line_follows_eq_10():
+    """The z-dispersion of Yee's scheme, Eq. (10). On a coaxial line (a PEC rod
+    through the box) the discrete TEM field e = e0(x, y) a_k is curl-free and
+    divergence-free across the section, so from h = 0 the 3D scheme keeps the
+    fields separable and a_k follows a 1D leapfrog whose standing waves
+    sin(r pi k / nz) turn with sin W = (c dt/dz) sin(r pi / (2 nz)) per half step:
+    a^{n-1/2} = sum_r A_r cos((2n - 1) W_r) / cos(W_r) sin(r pi k / nz) from the
+    sine coefficients A_r of the initial a^{-1/2}."""
+    from paper_0901_1053_gb300 import workloads as wl
+    nx = ny = 10
+    nz = 240
+    rod = (4, 6, 4, 6)
+    cdt = 0.9 * yee_bound(DXY, DXY, MM)
+    o = Oracle(nx, ny, nz, DXY, DXY, MM, cdt=cdt, pec=wl.coax_pec(nx, ny, nz, rod))
+    e0x, e0y = wl.coax_tem_e(nx, ny, DXY, DXY, rod)
+    k = np.arange(nz + 1)
+    a0 = np.exp(-0.5 * ((k - 70.0) / 4.0) ** 2)
+    a0[0] = a0[-1] = 0.0
+    o.set(0, e0x[None] * a0[:, None, None])
+    o.set(1, e0y[None] * a0[:, None, None])
+    n = 150
+    o.yee_step(n)
+    ex, ey = o.get(0), o.get(1)
+    j, i = np.unravel_index(np.argmax(np.abs(e0x)), e0x.shape)
+    a = ex[:, j, i] / e0x[j, i]
+    # separable: every e_x, e_y edge carries e0 * a_k; no e_z, h_z
+    np.testing.assert_allclose(ex, e0x[None] * a[:, None, None], atol=1e-12 * np.abs(ex).max())
+    np.testing.assert_allclose(ey, e0y[None] * a[:, None, None], atol=1e-12 * np.abs(ex).max())
+    assert np.abs(o.get(2)).max() <= 1e-12 * np.abs(ex).max()
+    assert np.abs(o.get(5)).max() <= 1e-12 * np.abs(o.get(3)).max()
+    # closed form of Eq. (10)
+    r = np.arange(1, nz)
+    modes = np.sin(np.pi * np.outer(r, k) / nz)            # (nz-1, nz+1)
+    amp = (2.0 / nz) * modes @ a0
+    w = np.arcsin((cdt / MM) * np.sin(np.pi * r / (2 * nz)))
+    pred = (amp * np.cos((2 * n - 1) * w) / np.cos(w)) @ modes
+    assert np.max(np.abs(a - pred)) <= 1e-11 * np.max(np.abs(a0))
+    # and it is not the dispersion-free motion (c dt < dz): the phase error of
+    # Eq. (11) is visible after 150 steps
+    w_exact = (cdt / MM) * np.pi * r / (2 * nz)
+    exact = (amp * np.cos((2 * n - 1) * w_exact) / np.cos(w_exact)) @ modes
+    assert np.max(np.abs(a - exact)) > 1e-3 * np.max(np.abs(a0))
