@@ -863,6 +863,58 @@ def yee_initial_ex(w):
     return np.ascontiguousarray(np.broadcast_to(prof[:, None, None], (w.nz + 1, w.ny + 1, w.nx + 1)))
 
 
+def yee_z_dispersion(tetm, travel=1500, sigma_cells=6.0, n=24, nz=2048):
+    """The z-dispersion of both schemes on the GPU (float64): a Gaussian TEM pulse
+    (RMS sigma_cells) on a coaxial line n x n x nz (a 4 x 4-cell PEC rod on the axis,
+    the paper's sqrt(2) mesh), moved `travel` cells by each scheme at its step
+    (TE/TM c*dt = dz, Yee at its bound (8)), against the dispersion-free motion of
+    the same initial field: each standing wave sin(r pi k / nz) turning at the
+    exact frequency c k. Yee's error is also predicted from its dispersion relation
+    (10) (the same sum with sin W = (c dt/dz) sin(r pi / (2 nz)))."""
+    import numpy as np
+    from paper_0901_1053_gb300 import workloads as wl
+    dxy, dz = math.sqrt(2.0) * 1e-3, 1e-3
+    rod = (n // 2 - 2, n // 2 + 2, n // 2 - 2, n // 2 + 2)
+    pec = wl.coax_pec(n, n, nz, rod)
+    e0x, e0y = wl.coax_tem_e(n, n, dxy, dxy, rod)
+    k = np.arange(nz + 1)
+    a0 = np.exp(-0.5 * ((k - 300.0) / sigma_cells) ** 2)
+    a0[0] = a0[-1] = 0.0
+    r = np.arange(1, nz)
+    modes = np.sin(np.pi * np.outer(r, k) / nz)
+    amp = (2.0 / nz) * modes @ a0
+    jj, ii = np.unravel_index(np.argmax(np.abs(e0x)), e0x.shape)
+    out = {"line": "%dx%dx%d coaxial line, 4x4-cell rod, dx = dy = sqrt(2) dz" % (n, n, nz),
+           "pulse_sigma_cells": sigma_cells, "travel_cells": travel, "fields": "f64"}
+    for scheme in ("tetm", "yee"):
+        cdt = dz if scheme == "tetm" else 1.0 / math.sqrt(2.0 / dxy ** 2 + 1.0 / dz ** 2)
+        nu = cdt / dz
+        steps = int(round(travel / nu))
+        s = tetm.Solver(n, n, nz, dxy, dxy, dz, cdt, "fp64", pec=pec)
+        if scheme == "yee":
+            s.set_scheme("yee")
+        s.set(0, e0x[None] * a0[:, None, None])
+        s.set(1, e0y[None] * a0[:, None, None])
+        s.step(steps)
+        a = s.get(0)[:, jj, ii] / e0x[jj, ii]
+        s.close()
+        # e^0 and h^{-1/2} = 0 (TE/TM: e at integer times) or e^{-1/2} and h^0 = 0
+        # (Yee): each standing wave a_r(t) = A_r cos(omega (t + 1/2)) / cos(omega / 2)
+        # or cos(omega t) / cos(omega / 2) at the e time level reached
+        m = 2 * steps + 1 if scheme == "tetm" else 2 * steps - 1
+        w_exact = nu * np.pi * r / (2 * nz)
+        exact = (amp * np.cos(m * w_exact) / np.cos(w_exact)) @ modes
+        d = {"cdt_over_dz": round(nu, 6), "steps": steps,
+             "max_error_vs_dispersion_free": float(np.max(np.abs(a - exact)) / np.max(np.abs(a0)))}
+        if scheme == "yee":
+            w = np.arcsin(nu * np.sin(np.pi * r / (2 * nz)))
+            pred = (amp * np.cos(m * w) / np.cos(w)) @ modes
+            d["predicted_by_eq10"] = float(np.max(np.abs(pred - exact)) / np.max(np.abs(a0)))
+            d["max_error_vs_eq10"] = float(np.max(np.abs(a - pred)) / np.max(np.abs(a0)))
+        out[scheme] = d
+    return out
+
+
 def run_yee_mode(args):
     """Yee's scheme on the workload's grid at c*dt = the bound (8), one fused
     launch per step, and the TE/TM scheme (c*dt = dz) on the same grid and
@@ -910,6 +962,8 @@ def run_yee_mode(args):
         clk = clocks.stop() if clocks else None
         total = evs[0].elapsed_time(evs[K])
         return total, total / K, clk
+
+    zdisp = yee_z_dispersion(tetm) if rank == 0 else None
 
     # the TE/TM scheme first (no balances: kernel against kernel)
     st = make("tetm")
@@ -990,6 +1044,7 @@ def run_yee_mode(args):
                         "yee_kernel_ms_per_step": kern_ms,
                         "tetm_ms_per_dz": tetm_ms, "yee_ms_per_dz": yee_per_dz,
                         "tetm_time_over_yee_time": tetm_ms / yee_per_dz},
+        "z_dispersion": zdisp,
         "cpu_baseline": cpu,
         "e2e": e2e,
         "gpu_launches": K if args.kernel != "reference" else 2 * K,

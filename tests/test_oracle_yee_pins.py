@@ -197,3 +197,31 @@ def test_yee_tem_pulse_on_a_coaxial_line_follows_eq_10():
     w_exact = (cdt / MM) * np.pi * r / (2 * nz)
     exact = (amp * np.cos((2 * n - 1) * w_exact) / np.cos(w_exact)) @ modes
     assert np.max(np.abs(a - exact)) > 1e-3 * np.max(np.abs(a0))
+
+
+def test_tetm_moves_the_coaxial_tem_pulse_without_dispersion():
+    """The same pulse under the TE/TM scheme at c dt = dz (its "magic" step,
+    Sec. 4.5): every standing wave turns at the exact frequency c k, so the
+    field equals the dispersion-free motion of the initial e^0 (h^{-1/2} = 0):
+    a^n = sum_r A_r cos((2n + 1) W_r) / cos(W_r) sin(r pi k / nz), W_r = r pi / (2 nz)."""
+    from paper_0901_1053_gb300 import workloads as wl
+    nx = ny = 10
+    nz = 240
+    rod = (4, 6, 4, 6)
+    o = Oracle(nx, ny, nz, DXY, DXY, MM, cdt=MM, pec=wl.coax_pec(nx, ny, nz, rod))
+    e0x, e0y = wl.coax_tem_e(nx, ny, DXY, DXY, rod)
+    k = np.arange(nz + 1)
+    a0 = np.exp(-0.5 * ((k - 70.0) / 4.0) ** 2)
+    a0[0] = a0[-1] = 0.0
+    o.set(0, e0x[None] * a0[:, None, None])
+    o.set(1, e0y[None] * a0[:, None, None])
+    n = 150
+    o.step(n)
+    j, i = np.unravel_index(np.argmax(np.abs(e0x)), e0x.shape)
+    a = o.get(0)[:, j, i] / e0x[j, i]
+    r = np.arange(1, nz)
+    modes = np.sin(np.pi * np.outer(r, k) / nz)
+    amp = (2.0 / nz) * modes @ a0
+    w = np.pi * r / (2 * nz)
+    exact = (amp * np.cos((2 * n + 1) * w) / np.cos(w)) @ modes
+    assert np.max(np.abs(a - exact)) <= 1e-11 * np.max(np.abs(a0))
