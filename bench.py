@@ -52,9 +52,11 @@ def parse_args():
     p.add_argument("--impl", default="tetm", choices=["tetm", "reference"])
     p.add_argument("--workload", default="collimator",
                    choices=["collimator", "plain_pipe", "batch", "serve", "dielectric", "rz"])
-    p.add_argument("--config", default=None, choices=["cfg1", "cfg2", "cfg3", "cfg4", "cfg5"],
-                   help="the benchmark configurations by number: cfg1 = plain_pipe (FP64), "
-                        "cfg2 = collimator (FP32), cfg3 = rz, cfg4 = batch, cfg5 = serve")
+    p.add_argument("--config", default=None,
+                   choices=["plain-pipe-fp64", "collimator-fp32", "rz-chain", "batch-64", "serve-2000"],
+                   help="a named workload with its precision: the 24x24x96 plain pipe in float64, the "
+                        "256x256x2048 step collimator in float32, the 512x16384 nine-cell r-z chain, "
+                        "the 64-solve batch, the 2000-request served stream")
     p.add_argument("--rz-chunk", type=int, default=0,
                    help="rz: planes per work item (0 = chosen by the autotuner, untimed)")
     p.add_argument("--rz-kernel", default=None, choices=[None, "async", "register", "bulk", "bulk2"],
@@ -90,9 +92,9 @@ def parse_args():
                    help="plain_pipe only: transverse cells (profiling a fully active box)")
     args = p.parse_args()
     if args.config:
-        args.workload = {"cfg1": "plain_pipe", "cfg2": "collimator", "cfg3": "rz", "cfg4": "batch",
-                         "cfg5": "serve"}[args.config]
-        if args.config == "cfg1" and args.precision is None:
+        args.workload = {"plain-pipe-fp64": "plain_pipe", "collimator-fp32": "collimator", "rz-chain": "rz",
+                         "batch-64": "batch", "serve-2000": "serve"}[args.config]
+        if args.config == "plain-pipe-fp64" and args.precision is None:
             args.precision = "fp64"
     return args
 

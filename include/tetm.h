@@ -48,7 +48,7 @@ extern "C" {
 #define TETM_E_STATE (-6)      /* call not valid in the solver's current state      */
 #define TETM_E_TIMEOUT (-7)    /* a bounded device-side wait gave up                */
 #define TETM_E_DIVERGED (-8)   /* non-finite energy: the run blew up               */
-#define TETM_E_UNSUPPORTED (-9) /* combination of options this build does not offer */
+#define TETM_E_UNSUPPORTED (-9) /* combination of options the library does not offer */
 #define TETM_E_TOO_LARGE (-10) /* problem exceeds the fixed scratch of tetm_energy_noalloc */
 
 /* ---- field precision ---------------------------------------------------- */
