@@ -534,7 +534,7 @@ def run_batch_mode(args):
     ws = sharding.shard_workloads(allw, world, rank)
     big = max(ws, key=lambda w: w.cells)
     tuner = Autotuner()
-    t32 = tuner.tune(big, "fp32")
+    t32 = tuner.tune(big, "fp32", batch=True)
     t64 = tuner.tune(big, "fp64")
     dist.barrier()
     wakes32, t_step, t_total = run_batch(ws, "fp32", t32, graph_steps=32)
@@ -577,7 +577,7 @@ def run_serve_mode(args):
         return 0
     reqs = wl.request_stream(count=args.requests, rate=args.rate)
     probe = max(reqs[:32], key=lambda r: r.n).workload("fp32")
-    tiling = Autotuner().tune(probe, "fp32")
+    tiling = Autotuner().tune(probe, "fp32", batch=True)
     srv = Server(GpuBackend("fp32", tiling), hbm_budget=150e9, max_slots=64, round_steps=64)
     res = srv.run_stream(reqs, lambda r: r.workload("fp32"))
     st = latency_stats(res)

@@ -147,12 +147,15 @@ class Autotuner:
         return sorted(set(out))
 
     def tune(self, w, precision: Optional[str] = None,
-             candidates: Optional[Sequence[Shape]] = None, materials: bool = False, eps_r=None) -> Shape:
+             candidates: Optional[Sequence[Shape]] = None, materials: bool = False, eps_r=None,
+             batch: bool = False) -> Shape:
         """materials: the solve has eps/mu arrays (per-entry coefficients run on
-        the warp-tiled kernel, tile_x = 28, and the float32 slab kernel, 56 x 28)."""
+        the warp-tiled kernel, tile_x = 28, and the float32 slab kernel, 56 x 28);
+        batch: the shape is for a batch of solves (the batched launch is the
+        warp-tiled kernel, tile_x = 28)."""
         precision = precision or w.precision
         materials = materials or eps_r is not None
-        k = self.key(w, precision) + ("|materials" if materials else "")
+        k = self.key(w, precision) + ("|materials" if materials else "") + ("|batch" if batch else "")
         if eps_r is not None:
             k += "|" + hashlib.sha1(memoryview(np.ascontiguousarray(eps_r)).tobytes()).hexdigest()[:16]
         if k in self.cache:
@@ -162,6 +165,8 @@ class Autotuner:
             cands += [c for c in self.wave_fitted(w, precision) if c not in cands]
         if materials:
             cands = [c for c in cands if c[0] == 28 or (c[0], c[1]) == (56, 28)]
+        if batch:
+            cands = [c for c in cands if c[0] == 28]
         times = self.measure(w, precision, cands, eps_r=eps_r)
         best = min(times, key=times.get)
         self.cache[k] = list(best)
