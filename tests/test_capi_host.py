@@ -90,3 +90,64 @@ def test_rz_bytes_needed(tetm):
     assert 48 * cells < b32 < 57 * cells          # two sets of six float32 per mode + mask
     assert 96 * cells < b64 < 112 * cells         # row pitch padded to whole windows
     assert tetm.tetm_rz_bytes_needed(tetm.make_rz_grid(0, 8, 0, 0, 1e-3, 1e-3)) == 0
+
+
+def test_every_handle_call_rejects_a_null_handle_without_a_gpu(tetm):
+    """A NULL handle is an argument error (destroy calls are no-ops), answered
+    before any device work, so it needs no GPU."""
+    import ctypes
+    L = tetm.lib
+    E = tetm.TETM_E_ARG
+    d = ctypes.c_double()
+    i = ctypes.c_int32()
+    calls = {
+        "tetm_set_stream": lambda: L.tetm_set_stream(None, None),
+        "tetm_set_kernel": lambda: L.tetm_set_kernel(None, 0),
+        "tetm_set_tiling": lambda: L.tetm_set_tiling(None, 0, 0, 0),
+        "tetm_set_scheme": lambda: L.tetm_set_scheme(None, 1),
+        "tetm_set_bunch": lambda: L.tetm_set_bunch(None, 1e-3, 1e-9, 1, 1),
+        "tetm_set_bunch_static": lambda: L.tetm_set_bunch_static(None, 1e-3, 1e-9, 1, 1, 10),
+        "tetm_step": lambda: L.tetm_step(None, 1),
+        "tetm_sync": lambda: L.tetm_sync(None),
+        "tetm_wake": lambda: L.tetm_wake(None, None, 0, None, None, None),
+        "tetm_set_observer": lambda: L.tetm_set_observer(None, 1, 1),
+        "tetm_transverse_wake": lambda: L.tetm_transverse_wake(None, None, None, 0, None, None, None),
+        "tetm_energy": lambda: L.tetm_energy(None, ctypes.byref(d)),
+        "tetm_charge_residual": lambda: L.tetm_charge_residual(None, None, None, None),
+        "tetm_set_balance_every": lambda: L.tetm_set_balance_every(None, 1),
+        "tetm_balance_history": lambda: L.tetm_balance_history(None, None, 0, None),
+        "tetm_get_fields": lambda: L.tetm_get_fields(None, 0, None),
+        "tetm_set_fields": lambda: L.tetm_set_fields(None, 0, None),
+        "tetm_get_info": lambda: L.tetm_get_info(None, None),
+        "tetm_save": lambda: L.tetm_save(None, None, 0, None),
+        "tetm_load": lambda: L.tetm_load(None, None, 0),
+        "tetm_batch_step": lambda: L.tetm_batch_step(None, 1),
+        "tetm_batch_sync": lambda: L.tetm_batch_sync(None),
+        "tetm_batch_info": lambda: L.tetm_batch_info(None, None, None, None),
+        "tetm_rz_set_bunch": lambda: L.tetm_rz_set_bunch(None, 1e-3, 1e-9, 0),
+        "tetm_rz_step": lambda: L.tetm_rz_step(None, 1),
+        "tetm_rz_sync": lambda: L.tetm_rz_sync(None),
+        "tetm_rz_wake": lambda: L.tetm_rz_wake(None, 0, None, 0, None, None, None),
+        "tetm_rz_energy": lambda: L.tetm_rz_energy(None, 0, ctypes.byref(d)),
+        "tetm_rz_get_fields": lambda: L.tetm_rz_get_fields(None, 0, 0, None),
+        "tetm_rz_set_fields": lambda: L.tetm_rz_set_fields(None, 0, 0, None),
+        "tetm_rz_set_tiling": lambda: L.tetm_rz_set_tiling(None, 16),
+        "tetm_rz_set_kernel": lambda: L.tetm_rz_set_kernel(None, 0),
+        "tetm_rz_set_stream": lambda: L.tetm_rz_set_stream(None, None),
+        "tetm_rz_get_info": lambda: L.tetm_rz_get_info(None, None),
+        "tetm_rz_set_observer": lambda: L.tetm_rz_set_observer(None, 1),
+        "tetm_rz_transverse_wake": lambda: L.tetm_rz_transverse_wake(None, 0, None, 0, None, None, None),
+        "tetm_rz_set_bunch_static": lambda: L.tetm_rz_set_bunch_static(None, 1e-3, 1e-9, 0, 10),
+        "tetm_rz_set_bunch_scattered": lambda: L.tetm_rz_set_bunch_scattered(None, 1e-3, 1e-9, 0, 10),
+    }
+    for name, call in calls.items():
+        assert call() == E, name
+    L.tetm_destroy(None)
+    L.tetm_batch_destroy(None)
+    assert L.tetm_rz_destroy(None) == tetm.TETM_OK
+    assert L.tetm_batch_create(None, None, 0, 0, None) == E
+    handle_calls = [n for n in tetm.EXPORTS if n not in ("tetm_create", "tetm_rz_create", "tetm_destroy",
+                    "tetm_rz_destroy", "tetm_batch_destroy", "tetm_batch_create", "tetm_bytes_needed",
+                    "tetm_rz_bytes_needed", "tetm_strerror", "tetm_energy_noalloc", "tetm_measure_fma_rate",
+                    "tetm_rz_selftest_wait")]
+    assert sorted(handle_calls) == sorted(calls), set(handle_calls) ^ set(calls)
