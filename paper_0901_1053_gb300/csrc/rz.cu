@@ -1323,6 +1323,10 @@ struct tetm_rz {
   long long step = 0;
   long long device_bytes = 0;
   cudaStream_t own = nullptr, st = nullptr;
+  // the source-window launch of a scattered-form pass runs on a side stream,
+  // beside the plain launch (their items are disjoint), joined before the next pass
+  cudaStream_t side = nullptr;
+  cudaEvent_t ev_fork = nullptr, ev_join = nullptr;
   int resident = 0;
   int kernel = TETM_RZ_KERNEL_ASYNC;
   int* err = nullptr;            // device error word of the bulk-copy kernel
@@ -1423,19 +1427,19 @@ int rz_launch_steps(tetm_rz* s, long long n) {
   const int blocks = std::max(1, std::min(s->resident, (items + 3) / 4));
   // launches one step kernel over the plain items (SC = false) or over the
   // items meeting a source window (SC = true)
-  auto launch = [&](bool sc, int steps, int nblocks) {
+  auto launch = [&](bool sc, int steps, int nblocks, cudaStream_t st) {
     if (steps == 2) {
-      if (sc) rz_step_bulk2_kernel<T, true><<<nblocks, 128, 4 * rz_bulk_warp_bytes<T>(), s->st>>>(a);
-      else rz_step_bulk2_kernel<T, false><<<nblocks, 128, 4 * rz_bulk_warp_bytes<T>(), s->st>>>(a);
+      if (sc) rz_step_bulk2_kernel<T, true><<<nblocks, 128, 4 * rz_bulk_warp_bytes<T>(), st>>>(a);
+      else rz_step_bulk2_kernel<T, false><<<nblocks, 128, 4 * rz_bulk_warp_bytes<T>(), st>>>(a);
     } else if (s->kernel == TETM_RZ_KERNEL_BULK || s->kernel == TETM_RZ_KERNEL_BULK2) {
-      if (sc) rz_step_bulk_kernel<T, true><<<nblocks, 128, 4 * rz_bulk_warp_bytes<T>(), s->st>>>(a);
-      else rz_step_bulk_kernel<T, false><<<nblocks, 128, 4 * rz_bulk_warp_bytes<T>(), s->st>>>(a);
+      if (sc) rz_step_bulk_kernel<T, true><<<nblocks, 128, 4 * rz_bulk_warp_bytes<T>(), st>>>(a);
+      else rz_step_bulk_kernel<T, false><<<nblocks, 128, 4 * rz_bulk_warp_bytes<T>(), st>>>(a);
     } else if (s->kernel == TETM_RZ_KERNEL_ASYNC) {
-      if (sc) rz_step_async_kernel<T, true><<<nblocks, 128, 4 * rz_async_warp_bytes<T>(), s->st>>>(a);
-      else rz_step_async_kernel<T, false><<<nblocks, 128, 4 * rz_async_warp_bytes<T>(), s->st>>>(a);
+      if (sc) rz_step_async_kernel<T, true><<<nblocks, 128, 4 * rz_async_warp_bytes<T>(), st>>>(a);
+      else rz_step_async_kernel<T, false><<<nblocks, 128, 4 * rz_async_warp_bytes<T>(), st>>>(a);
     } else {
-      if (sc) rz_step_kernel<T, true><<<nblocks, 128, 0, s->st>>>(a);
-      else rz_step_kernel<T, false><<<nblocks, 128, 0, s->st>>>(a);
+      if (sc) rz_step_kernel<T, true><<<nblocks, 128, 0, st>>>(a);
+      else rz_step_kernel<T, false><<<nblocks, 128, 0, st>>>(a);
     }
     return cudaGetLastError();
   };
@@ -1467,12 +1471,26 @@ int rz_launch_steps(tetm_rz* s, long long n) {
       }
     }
     if (items > 0) {
-      if (a.sc_hi > a.sc_lo) {
+      const bool win = a.sc_hi > a.sc_lo;
+      if (win && !s->side) {  // the side stream and its two events, once
+        if (cudaStreamCreateWithFlags(&s->side, cudaStreamNonBlocking) != cudaSuccess ||
+            cudaEventCreateWithFlags(&s->ev_fork, cudaEventDisableTiming) != cudaSuccess ||
+            cudaEventCreateWithFlags(&s->ev_join, cudaEventDisableTiming) != cudaSuccess)
+          return rz_fail(cudaGetLastError());
+      }
+      if (win) {
+        // fork: the window items (whose sources were queued on the main stream
+        // before) on the side stream, the plain items on the main stream
         const int nsub = (s->chunk_z + kSubPlanes - 1) / kSubPlanes;
-        cudaError_t e = launch(true, p, std::max(1, std::min(blocks, ((a.sc_hi - a.sc_lo) * nsub + 3) / 4)));
+        cudaError_t e = cudaEventRecord(s->ev_fork, s->st);
+        if (e == cudaSuccess) e = cudaStreamWaitEvent(s->side, s->ev_fork, 0);
+        if (e == cudaSuccess)
+          e = launch(true, p, std::max(1, std::min(blocks, ((a.sc_hi - a.sc_lo) * nsub + 3) / 4)), s->side);
+        if (e == cudaSuccess) e = cudaEventRecord(s->ev_join, s->side);
         if (e != cudaSuccess) return rz_fail(e);
       }
-      cudaError_t e = launch(false, p, blocks);
+      cudaError_t e = launch(false, p, blocks, s->st);
+      if (e == cudaSuccess && win) e = cudaStreamWaitEvent(s->st, s->ev_join, 0);  // join
       if (e != cudaSuccess) return rz_fail(e);
     }
     s->cur ^= 1;
@@ -2192,6 +2210,12 @@ int tetm_rz_destroy(tetm_rz* s) {
   cudaFree(s->S);
   cudaFree(s->differs);
   cudaFree(s->Jzero);
+  if (s->side) {
+    cudaStreamSynchronize(s->side);
+    cudaStreamDestroy(s->side);
+  }
+  if (s->ev_fork) cudaEventDestroy(s->ev_fork);
+  if (s->ev_join) cudaEventDestroy(s->ev_join);
   if (s->own) cudaStreamDestroy(s->own);
   cudaGetLastError();
   delete s;
