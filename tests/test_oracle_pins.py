@@ -720,3 +720,34 @@ def test_observer_arguments_and_state():
     o.step(1)
     with pytest.raises(ValueError):
         o.set_observer(2, 2)                      # after the first step
+
+
+def test_cavity_mode_frequency_converges_at_second_order():
+    """The continuous limit of the scheme: the TM_111 frequency of a rectangular
+    PEC box, c pi ((1/a)^2 + (1/b)^2 + (1/d)^2)^(1/2) (Maxwell's equations, no
+    discretisation), is approached as O(h^2) when the mesh is refined at fixed
+    c dt = dz. The frequency is measured from the time series of the e_z
+    pattern's projection by the three-term recurrence p(n+1) + p(n-1) =
+    2 cos(w dt) p(n) + const (the constant carries the static part)."""
+    errs = []
+    for f in (1, 2, 4):
+        nx, ny, nz = 6 * f, 6 * f, 8 * f
+        dx, dy, dz = DXY / f, DXY / f, MM / f
+        o = Oracle(nx, ny, nz, dx, dy, dz)
+        i, j, k = np.arange(nx + 1), np.arange(ny + 1), np.arange(nz + 1)
+        ez = (np.cos(np.pi * (k + 0.5) / nz)[:, None, None] * np.sin(np.pi * j / ny)[None, :, None]
+              * np.sin(np.pi * i / nx)[None, None, :])
+        ez = np.where(o.coef("ez") > 0, ez, 0.0)
+        o.set("ez", ez)
+        p = []
+        for _ in range(160 * f):
+            o.step(1)
+            p.append(float(np.sum(o.get("ez") * ez)))
+        p = np.array(p)
+        a = np.column_stack([2.0 * p[1:-1], np.ones(len(p) - 2)])
+        (c, _), *_ = np.linalg.lstsq(a, p[2:] + p[:-2], rcond=None)
+        w = math.acos(c) / o.dt
+        w_cont = C_LIGHT * math.pi * math.sqrt((nx * dx) ** -2 + (ny * dy) ** -2 + (nz * dz) ** -2)
+        errs.append(abs(w - w_cont) / w_cont)
+    assert errs[0] < 0.05
+    assert 3.5 < errs[0] / errs[1] < 4.5 and 3.5 < errs[1] / errs[2] < 4.5, errs
