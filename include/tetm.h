@@ -247,6 +247,13 @@ int tetm_set_tiling(tetm_solver* s, int32_t tile_x, int32_t tile_y, int32_t chun
  * TE/TM scheme's), and tetm_set_tiling accepts only the chunk length. */
 int tetm_set_scheme(tetm_solver* s, int32_t scheme);
 
+/* Canary of out-of-place writes: counts, over both field sets and all six
+ * components, the device entries that hold a non-zero value although they
+ * carry no field (the zero guard ring around the cells and the entries of PEC
+ * edges and faces, which every update leaves at zero). A correct run reports
+ * 0. Synchronizes; TETM_E_ARG for NULL arguments. */
+int tetm_check_guards(tetm_solver* s, int64_t* violations);
+
 /* Snapshot of the solve's bookkeeping. */
 int tetm_get_info(tetm_solver* s, tetm_info* info);
 

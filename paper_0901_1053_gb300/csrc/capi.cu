@@ -180,6 +180,20 @@ __global__ void item_flags(const uint8_t* mask, Layout L, int tx, int ty, int cz
   if (threadIdx.x == 0) flags[item] = any;
 }
 
+// Entries of one component that hold a non-zero value where the activity bit
+// is clear: the guard ring around the cells and the entries of PEC objects,
+// which every update leaves at zero (the canary of an out-of-place write).
+template <typename T>
+__global__ void guard_scan(const T* f, const uint8_t* mask, long long count, int comp,
+                           unsigned long long* out) {
+  unsigned long long c = 0;
+  for (long long q = (long long)blockIdx.x * blockDim.x + threadIdx.x; q < count;
+       q += (long long)gridDim.x * blockDim.x)
+    if (f[q] != T(0) && !((mask[q] >> comp) & 1)) ++c;
+  for (int o = 16; o > 0; o >>= 1) c += __shfl_down_sync(0xffffffffu, c, o);
+  if ((threadIdx.x & 31) == 0 && c) atomicAdd(out, c);
+}
+
 __global__ void count_active(const uint8_t* mask, Layout L, unsigned long long* out) {
   const long long total = (long long)L.nx * L.ny * L.nz;
   unsigned long long c = 0;
@@ -948,6 +962,28 @@ int tetm_set_fields(tetm_solver* s, int32_t comp, const double* host) {
   rc = s->esz == 8 ? set_fields_t<double>(s, comp, host) : set_fields_t<float>(s, comp, host);
   s->prev_valid = false;
   return rc;
+}
+
+int tetm_check_guards(tetm_solver* s, int64_t* violations) {
+  if (!s || !violations) return TETM_E_ARG;
+  unsigned long long* cnt = nullptr;
+  unsigned long long h = 0;
+  CK(cudaMalloc(&cnt, sizeof(*cnt)));
+  cudaError_t e = cudaMemsetAsync(cnt, 0, sizeof(*cnt), s->stream);
+  for (int b = 0; b < 2 && e == cudaSuccess; ++b)
+    for (int c = 0; c < 6 && e == cudaSuccess; ++c) {
+      if (s->esz == 8)
+        guard_scan<double><<<1024, 256, 0, s->stream>>>((const double*)s->set[b][c], s->mask, s->L.count, c, cnt);
+      else
+        guard_scan<float><<<1024, 256, 0, s->stream>>>((const float*)s->set[b][c], s->mask, s->L.count, c, cnt);
+      e = cudaGetLastError();
+    }
+  if (e == cudaSuccess) e = cudaMemcpyAsync(&h, cnt, sizeof(h), cudaMemcpyDeviceToHost, s->stream);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(s->stream);
+  cudaFree(cnt);
+  CK(e);
+  *violations = (int64_t)h;
+  return TETM_OK;
 }
 
 int tetm_get_info(tetm_solver* s, tetm_info* info) {

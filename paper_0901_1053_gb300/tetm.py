@@ -40,6 +40,7 @@ COMPONENTS = ("ex", "ey", "ez", "hx", "hy", "hz")
 EXPORTS = ("tetm_create", "tetm_set_bunch", "tetm_step", "tetm_sync", "tetm_wake",
            "tetm_destroy", "tetm_energy", "tetm_charge_residual", "tetm_get_fields",
            "tetm_set_fields", "tetm_set_stream", "tetm_set_kernel", "tetm_set_tiling", "tetm_set_scheme",
+           "tetm_check_guards",
            "tetm_set_observer", "tetm_transverse_wake",
            "tetm_get_info", "tetm_bytes_needed", "tetm_save", "tetm_load", "tetm_strerror",
            "tetm_set_balance_every", "tetm_balance_history", "tetm_energy_noalloc",
@@ -115,6 +116,7 @@ def _load():
         "tetm_set_kernel": (ctypes.c_int, [vp, i32]),
         "tetm_set_tiling": (ctypes.c_int, [vp, i32, i32, i32]),
         "tetm_set_scheme": (ctypes.c_int, [vp, i32]),
+        "tetm_check_guards": (ctypes.c_int, [vp, ctypes.POINTER(ctypes.c_int64)]),
         "tetm_get_info": (ctypes.c_int, [vp, ctypes.POINTER(tetm_info)]),
         "tetm_bytes_needed": (ctypes.c_int64, [ctypes.POINTER(tetm_grid)]),
         "tetm_save": (ctypes.c_int, [vp, vp, ctypes.c_size_t, ctypes.POINTER(ctypes.c_size_t)]),
@@ -342,6 +344,12 @@ class Solver:
         field-only: e is read as e^{n-1/2}, h as h^n), before the first step."""
         k = {"tetm": TETM_SCHEME_TETM, "yee": TETM_SCHEME_YEE}.get(scheme, scheme)
         _check(lib.tetm_set_scheme(self.h, int(k)), "tetm_set_scheme")
+
+    def check_guards(self):
+        """Entries that hold a value although they carry no field (0 in a correct run)."""
+        v = ctypes.c_int64()
+        _check(lib.tetm_check_guards(self.h, ctypes.byref(v)), "tetm_check_guards")
+        return int(v.value)
 
     def info(self):
         i = tetm_info()

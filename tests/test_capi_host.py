@@ -105,6 +105,7 @@ def test_every_handle_call_rejects_a_null_handle_without_a_gpu(tetm):
         "tetm_set_kernel": lambda: L.tetm_set_kernel(None, 0),
         "tetm_set_tiling": lambda: L.tetm_set_tiling(None, 0, 0, 0),
         "tetm_set_scheme": lambda: L.tetm_set_scheme(None, 1),
+        "tetm_check_guards": lambda: L.tetm_check_guards(None, None),
         "tetm_set_bunch": lambda: L.tetm_set_bunch(None, 1e-3, 1e-9, 1, 1),
         "tetm_set_bunch_static": lambda: L.tetm_set_bunch_static(None, 1e-3, 1e-9, 1, 1, 10),
         "tetm_step": lambda: L.tetm_step(None, 1),
