@@ -187,6 +187,12 @@ int tetm_rz_set_stream(tetm_rz* s, void* cuda_stream);
 
 int tetm_rz_get_info(tetm_rz* s, tetm_rz_info* info);
 
+/* Canary of out-of-place writes: counts, over both field sets and every mode,
+ * the entries that hold a non-zero value although their activity bit is clear
+ * (the zero guard rows and columns, PEC objects). A correct run reports 0.
+ * Synchronizes; TETM_E_ARG for NULL arguments. */
+int tetm_rz_check_guards(tetm_rz* s, int64_t* violations);
+
 /* Device bytes tetm_rz_create would allocate for g (0 for a bad grid). */
 int64_t tetm_rz_bytes_needed(const tetm_rz_grid* g);
 

@@ -1100,6 +1100,21 @@ __device__ __forceinline__ bool cell_pec(const uint8_t* pec, int nr, int nz, int
   return pec ? pec[ci + (long long)nr * ck] != 0 : false;
 }
 
+// Entries that hold a non-zero value where the entry's activity bit is clear
+// (the guard rows and columns, PEC objects): the canary of an out-of-place
+// write. The six components of a column sit side by side over the mask's entry.
+template <typename T>
+__global__ void rz_guard_scan(const T* f, const uint8_t* mask, RzLayout L, long long total,
+                              unsigned long long* out) {
+  const long long per_mode = L.rows * L.pr;
+  unsigned long long c = 0;
+  for (long long q = (long long)blockIdx.x * blockDim.x + threadIdx.x; q < total;
+       q += (long long)gridDim.x * blockDim.x)
+    if (f[q] != T(0) && !((mask[(q / 6) % per_mode] >> (int)(q % 6)) & 1)) ++c;
+  for (int o = 16; o > 0; o >>= 1) c += __shfl_down_sync(0xffffffffu, c, o);
+  if ((threadIdx.x & 31) == 0 && c) atomicAdd(out, c);
+}
+
 __global__ void rz_build_mask(const uint8_t* pec, RzLayout L, uint8_t* mask) {
   const long long total = L.rows * L.pr;
   for (long long q = (long long)blockIdx.x * blockDim.x + threadIdx.x; q < total;
@@ -2172,6 +2187,29 @@ int tetm_rz_set_kernel(tetm_rz* s, int32_t kernel) {
 int tetm_rz_set_stream(tetm_rz* s, void* cuda_stream) {
   if (!s) return TETM_E_ARG;
   s->st = cuda_stream ? static_cast<cudaStream_t>(cuda_stream) : s->own;
+  return TETM_OK;
+}
+
+int tetm_rz_check_guards(tetm_rz* s, int64_t* violations) {
+  if (!s || !violations) return TETM_E_ARG;
+  unsigned long long* cnt = nullptr;
+  unsigned long long h = 0;
+  cudaError_t e = cudaMalloc(&cnt, sizeof(*cnt));
+  if (e != cudaSuccess) return rz_fail(e);
+  e = cudaMemsetAsync(cnt, 0, sizeof(*cnt), s->st);
+  const long long total = (long long)s->n_modes * s->L.mode_elems();
+  for (int b = 0; b < 2 && e == cudaSuccess; ++b) {
+    if (s->esz == 8)
+      rz_guard_scan<double><<<1024, 256, 0, s->st>>>(static_cast<const double*>(s->set[b]), s->mask, s->L, total, cnt);
+    else
+      rz_guard_scan<float><<<1024, 256, 0, s->st>>>(static_cast<const float*>(s->set[b]), s->mask, s->L, total, cnt);
+    e = cudaGetLastError();
+  }
+  if (e == cudaSuccess) e = cudaMemcpyAsync(&h, cnt, sizeof(h), cudaMemcpyDeviceToHost, s->st);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(s->st);
+  cudaFree(cnt);
+  if (e != cudaSuccess) return rz_fail(e);
+  *violations = (int64_t)h;
   return TETM_OK;
 }
 

@@ -50,7 +50,8 @@ EXPORTS = ("tetm_create", "tetm_set_bunch", "tetm_step", "tetm_sync", "tetm_wake
            "tetm_rz_energy", "tetm_rz_get_fields", "tetm_rz_set_fields", "tetm_rz_set_tiling",
            "tetm_rz_set_stream", "tetm_rz_get_info", "tetm_rz_bytes_needed", "tetm_rz_destroy",
            "tetm_rz_set_kernel", "tetm_rz_set_observer", "tetm_rz_transverse_wake",
-           "tetm_rz_set_bunch_static", "tetm_rz_set_bunch_scattered", "tetm_rz_selftest_wait")
+           "tetm_rz_set_bunch_static", "tetm_rz_set_bunch_scattered", "tetm_rz_selftest_wait",
+           "tetm_rz_check_guards")
 TETM_RZ_KERNEL_ASYNC = 0
 TETM_RZ_KERNEL_REGISTER = 1
 TETM_RZ_KERNEL_BULK = 2
@@ -117,6 +118,7 @@ def _load():
         "tetm_set_tiling": (ctypes.c_int, [vp, i32, i32, i32]),
         "tetm_set_scheme": (ctypes.c_int, [vp, i32]),
         "tetm_check_guards": (ctypes.c_int, [vp, ctypes.POINTER(ctypes.c_int64)]),
+        "tetm_rz_check_guards": (ctypes.c_int, [vp, ctypes.POINTER(ctypes.c_int64)]),
         "tetm_get_info": (ctypes.c_int, [vp, ctypes.POINTER(tetm_info)]),
         "tetm_bytes_needed": (ctypes.c_int64, [ctypes.POINTER(tetm_grid)]),
         "tetm_save": (ctypes.c_int, [vp, vp, ctypes.c_size_t, ctypes.POINTER(ctypes.c_size_t)]),
@@ -486,6 +488,12 @@ class RzSolver:
     def set_stream(self, stream):
         _check(lib.tetm_rz_set_stream(self.h, ctypes.c_void_p(int(stream) if stream else 0)),
                "tetm_rz_set_stream")
+
+    def check_guards(self):
+        """Entries that hold a value although they carry no field (0 in a correct run)."""
+        v = ctypes.c_int64()
+        _check(lib.tetm_rz_check_guards(self.h, ctypes.byref(v)), "tetm_rz_check_guards")
+        return int(v.value)
 
     def info(self):
         inf = tetm_rz_info()

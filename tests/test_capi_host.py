@@ -140,6 +140,7 @@ def test_every_handle_call_rejects_a_null_handle_without_a_gpu(tetm):
         "tetm_rz_transverse_wake": lambda: L.tetm_rz_transverse_wake(None, 0, None, 0, None, None, None),
         "tetm_rz_set_bunch_static": lambda: L.tetm_rz_set_bunch_static(None, 1e-3, 1e-9, 0, 10),
         "tetm_rz_set_bunch_scattered": lambda: L.tetm_rz_set_bunch_scattered(None, 1e-3, 1e-9, 0, 10),
+        "tetm_rz_check_guards": lambda: L.tetm_rz_check_guards(None, None),
     }
     for name, call in calls.items():
         assert call() == E, name

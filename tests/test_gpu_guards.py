@@ -117,3 +117,22 @@ def test_the_canary_sees_a_value_in_the_guard_ring(tetm, precision):
     assert t.check_guards() == 1
     s.close()
     t.close()
+
+
+@pytest.mark.parametrize("kernel", ["async", "register", "bulk", "bulk2"])
+@pytest.mark.parametrize("start", ["cold", "scattered"])
+@pytest.mark.parametrize("precision", ["fp32", "fp64"])
+def test_rz_kernels_keep_the_guards(tetm, kernel, start, precision):
+    """Every r-z step kernel, cold and in the scattered-field form, modes 0..2,
+    on a two-cell chain whose radial size leaves a ragged last window."""
+    w = wl.cavity_chain_rz(70, 160, 0, 2, sigma_cells=3.0, precision=precision, n_cells=2, i0=3)
+    s = tetm.RzSolver(w.nr, w.nz, w.m_lo, w.m_hi, w.dr, w.dz, w.cdt, precision, pec=w.pec)
+    s.set_kernel(kernel)
+    if start == "cold":
+        s.set_bunch(w.sigma, w.charge, w.i0)
+    else:
+        s.set_bunch_scattered(w.sigma, w.charge, w.i0, 2 * math.ceil(5 * w.sigma / w.dz - 1e-12) + 2)
+    s.step(w.nz // 2 + 1)
+    s.sync()
+    assert s.check_guards() == 0
+    s.close()
