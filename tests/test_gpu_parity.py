@@ -505,3 +505,35 @@ def test_slab_kernel_with_materials_chunk_lengths_are_bitwise_identical(tetm):
             continue
         for a, b in zip(got, ref):
             assert np.array_equal(a, b), cz
+
+
+def test_full_size_dielectric_collimator_head_matches_oracle(tetm):
+    """256x256x1024 dielectric collimator (per-cell eps array) in the benchmark's
+    launch configuration (slab kernel with coefficient arrays, 56 x 28 x 16): as
+    for the vacuum collimator, nothing ahead of plane n has moved after n steps,
+    so the oracle on the first 80 planes reproduces planes 0..n entry by entry."""
+    w, eps = wl.dielectric_collimator(n=256, nz=1024, precision="fp32")
+    # a dielectric ring (eps_r = 3) inside the entry pipe from plane 20 on, so
+    # that the compared head holds material interfaces too
+    ring = wl.radius_mask(w.nx, w.ny, w.nz, lambda k: np.full(k.shape, 90.0)) & (w.pec == 0)
+    ring[:20] = False
+    eps = np.where(ring, 3.0, eps)
+    assert np.any(eps[:80] != 1.0)
+    n = 60
+    s = tetm.Solver(w.nx, w.ny, w.nz, w.dx, w.dy, w.dz, w.cdt, "fp32", eps_r=eps, pec=w.pec)
+    s.set_tiling(56, 28, 16)
+    s.set_bunch(w.sigma, w.charge, w.i0, w.j0)
+    s.step(n)
+    s.sync()
+    o = Oracle(w.nx, w.ny, 80, w.dx, w.dy, w.dz, w.cdt, eps_r=eps[:80].copy(), pec=w.pec[:80].copy())
+    o.set_bunch(w.sigma, w.charge, w.i0, w.j0)
+    o.step(n)
+    g = {c: s.get(c) for c in ("ex", "ey", "ez", "hx", "hy", "hz")}
+    r = {c: o.get(c) for c in g}
+    for fam in (("ex", "ey", "ez"), ("hx", "hy", "hz")):
+        peak = max(np.max(np.abs(r[c][:n + 1])) for c in fam)
+        for c in fam:
+            assert np.all(g[c][n + 2:] == 0.0), c
+            assert float(np.max(np.abs(g[c][:n + 1] - r[c][:n + 1])) / peak) <= 2e-5, c
+    assert rel_err(s.wake()[0], o.wake()[0]) <= 1e-4
+    s.close()
