@@ -17,8 +17,9 @@ Parity status: every function here is pinned by the ``-m "not gpu"`` tests
 (dense matrix form of Eq. (23), eigen-angles of Eq. (27), energy law (19),
 charge laws (34)/(35), exact z-shift at c*dt = dz, loss-factor identity).
 ``Oracle.yee_step`` (Yee's scheme, Eq. (7), the paper's comparison scheme) is
-pinned by the eigen-angles of the dispersion relation (9), the step bound (8)
-and the exactly conserved leapfrog energy. ``RzOracle`` (tetm_rz_oracle.c) is pinned by its own tests: the dense form
+pinned by the eigen-angles of the dispersion relation (9), the step bound (8),
+the exactly conserved leapfrog energy and the z-dispersion (10) of a TEM pulse
+on a coaxial line. ``RzOracle`` (tetm_rz_oracle.c) is pinned by its own tests: the dense form
 (24), stability at c*dt = min(dr, dz) for every mode, energy law (19),
 pillbox Bessel-zero frequencies, the coaxial TEM shift, Gauss's law and the
 loss-factor identity.
