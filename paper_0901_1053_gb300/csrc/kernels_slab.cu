@@ -46,7 +46,7 @@ constexpr int kSlabPolls = 1 << 18;
 // One material: a six-plane ring of e_z, h_z and the activity bytes (one
 // coefficient per component, switched by the bytes).
 struct SlabSmemU {
-  static constexpr int SD = 6;      // planes in the ring
+  static constexpr int SD = 2;      // planes in the ring (the next plane lands while this one is worked on)
   static constexpr unsigned slot_bytes = 2u * kSX * kSY * 4u + (unsigned)kMaskW * kSY;
   float ez[SD][kSY][kSX];
   float hz[SD][kSY][kSX];
