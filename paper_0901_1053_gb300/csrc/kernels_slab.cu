@@ -43,7 +43,7 @@ constexpr int kSThreads = kQ * kSY; // 512
 constexpr int kMaskW = 80;          // activity bytes per row (from a 16-byte aligned column)
 constexpr int kSlabPolls = 1 << 18;
 
-// One material: a six-plane ring of e_z, h_z and the activity bytes (one
+// One material: a two-plane ring of e_z, h_z and the activity bytes (one
 // coefficient per component, switched by the bytes).
 struct SlabSmemU {
   static constexpr int SD = 2;      // planes in the ring (the next plane lands while this one is worked on)
