@@ -14,8 +14,14 @@ e2e    = the same metric for one complete solve through the C ABI from host
          buffers: tetm_create from a pinned host PEC array, tetm_set_bunch,
          tetm_step(all steps), tetm_wake into host memory.
 roofline: the fused step kernel, algorithmic bytes = 12 field words + 1 mask
-         byte per processed cell (49 B in float32) per launch, over its mean
-         launch duration measured with CUDA events on its stream.
+         byte per cell that carries a field (49 B in float32; cells inside
+         PEC hold zero fields and are no work of the method) per launch, over
+         its mean launch duration measured with CUDA events on its stream;
+         the same figure over the cells of the launched work items is kept
+         beside it (achieved_on_processed_cells).
+active_gcell_updates_s: the field-carrying cells advanced per second.
+balances: the cost of one float64 energy and charge balance (a9), measured
+         apart, and its share of a step at the --balance-every cadence.
 
 --impl reference times the FP64 CPU oracle (test infrastructure) on the
 host, on a bounded sample of the same workload.
@@ -264,9 +270,10 @@ def host_cpu():
     return {"nproc": os.cpu_count(), "model": model or __import__("platform").machine()}
 
 
-def profiled_traffic(name, sources=("kernels_step.cu", "kernels_warp.cu")):
+def profiled_traffic(name, sources=("kernels_step.cu", "kernels_warp.cu"), tiling=None):
     """DRAM bytes per launch from the committed ncu summary for this kernel
-    and workload; None if absent or taken on a different kernel source."""
+    and workload; None if absent, taken on a different kernel source or (when
+    the summary names one) on a different work shape than `tiling`."""
     path = os.path.join(ROOT, "profiles", name)
     if not os.path.exists(path):
         return None
@@ -275,7 +282,30 @@ def profiled_traffic(name, sources=("kernels_step.cu", "kernels_warp.cu")):
     h = re.search(r"kernel_source_sha256_16:\s*([0-9a-f]+)", txt)
     if not m or not h or h.group(1) != kernel_source_hash(sources):
         return None
+    t = re.search(r"tiling:\s*([0-9]+)\s*,\s*([0-9]+)\s*,\s*([0-9]+)", txt)
+    if tiling is not None and t and tuple(int(x) for x in t.groups()) != tuple(tiling):
+        return None
     return float(m.group(1))
+
+
+def balance_cost(s, steps=4):
+    """(ms per float64 balance, plain ms per step) on solve s: device time
+    of `steps` steps with a balance after every step against the same steps
+    without, CUDA events on the solve's stream. Leaves the balances off."""
+    import torch
+    st = torch.cuda.current_stream()
+    out = []
+    for every in (1, 0):
+        s.set_balance_every(every)
+        s.step(1)
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        torch.cuda.synchronize()
+        e0.record(st)
+        s.step(steps)
+        e1.record(st)
+        torch.cuda.synchronize()
+        out.append(e0.elapsed_time(e1) / steps)
+    return out[0] - out[1], out[1]
 
 
 # ---------------------------------------------------------------------------
@@ -397,29 +427,36 @@ def run_tetm(args):
 
     esz = 4 if w.precision == "fp32" else 8
     # 12 field words and either the activity byte or, with per-cell materials,
-    # the six coefficient words
+    # the six coefficient words, per cell that carries a field: the work of
+    # the method (a cell in PEC holds zero fields for ever)
     bytes_per_cell = 12 * esz + 1 if args.eps is None else 18 * esz
     proc = info["processed_cells"] if args.kernel != "reference" else w.cells
-    gbs = bytes_per_cell * proc / (kern_ms * 1e-3) / 1e9
+    act = info["active_cells"]
+    gbs = bytes_per_cell * act / (kern_ms * 1e-3) / 1e9
+    gbs_proc = bytes_per_cell * proc / (kern_ms * 1e-3) / 1e9
     if w.precision == "fp32":
         achieved = gbs
         peak, peak_kind = measured_peak_hbm()
-        roof = {"bound": "hbm", "unit": "GB/s", "bytes_per_cell": bytes_per_cell}
+        roof = {"bound": "hbm", "unit": "GB/s", "bytes_per_cell": bytes_per_cell, "basis": "active cells",
+                "achieved_on_processed_cells": gbs_proc, "frac_on_processed_cells": gbs_proc / peak}
     else:
         # float64 arithmetic sets the pace on this part: 48 flops per cell
         # and step (the ten updates, a fused multiply-add counted as two)
-        achieved = FLOPS_PER_CELL_3D * proc / (kern_ms * 1e-3) / 1e12
+        achieved = FLOPS_PER_CELL_3D * act / (kern_ms * 1e-3) / 1e12
         peak, peak_kind = fp64_peak(tetm)
-        roof = {"bound": "alu", "unit": "TFLOP/s", "flops_per_cell": FLOPS_PER_CELL_3D,
+        roof = {"bound": "alu", "unit": "TFLOP/s", "flops_per_cell": FLOPS_PER_CELL_3D, "basis": "active cells",
+                "achieved_on_processed_cells": FLOPS_PER_CELL_3D * proc / (kern_ms * 1e-3) / 1e12,
                 "hbm_gbs": gbs, "bytes_per_cell": bytes_per_cell}
     kname = {28: "fused_step_warp", 56: "fused_step_slab"}.get(info["tile_x"], "fused_step")
     if args.eps is not None:
         kname = "fused_step_slab_mat" if info["tile_x"] == 56 else "fused_step_warp_mat"
     prof_name = "%s_%s_%s.md" % (kname, w.precision, w.name)
     sources = ("kernels_slab.cu",) if kname.startswith("fused_step_slab") else ("kernels_step.cu", "kernels_warp.cu")
-    traffic = profiled_traffic(prof_name, sources) if args.kernel != "reference" else None
+    traffic = (profiled_traffic(prof_name, sources, (info["tile_x"], info["tile_y"], info["chunk_z"]))
+               if args.kernel != "reference" else None)
     wake = s.wake()[0]
     hist = s.balance_history()
+    bal_ms, plain_ms = balance_cost(s) if be > 0 else (0.0, kern_ms)
     s.close()
 
     e2e = None
@@ -449,9 +486,11 @@ def run_tetm(args):
         twx, twy = s2.transverse_wake() if args.check else (None, None)
         s2.close()
         e2e_s = dist.max(t1 - t0)
+        h2d = int(pinned.nbytes if pinned is not None else 0)
         e2e = {"value": world * w.cells * steps_e2e / e2e_s / 1e9, "unit": UNIT,
-               "h2d_bytes_per_step": int(pinned.nbytes if pinned is not None else 0),
-               "d2h_bytes_per_step": int(out.nbytes), "steps_per_call": steps_e2e,
+               "active_gcell_updates_s": world * act * steps_e2e / e2e_s / 1e9,
+               "h2d_bytes_per_step": h2d / steps_e2e, "d2h_bytes_per_step": out.nbytes / steps_e2e,
+               "h2d_bytes_per_call": h2d, "d2h_bytes_per_call": int(out.nbytes), "steps_per_call": steps_e2e,
                "seconds": round(e2e_s, 3),
                "call": "tetm_create(host pec) + tetm_set_bunch + tetm_set_balance_every + tetm_step + "
                        "tetm_wake(host)"}
@@ -479,7 +518,9 @@ def run_tetm(args):
     value = world * w.cells * K / (max_ms * 1e-3) / 1e9
     n_bal = len(bal_steps)
     line = {
-        "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": K,
+        "metric": METRIC, "value": value, "unit": UNIT,
+        "active_gcell_updates_s": world * act * K / (max_ms * 1e-3) / 1e9,
+        "n_gpus": world, "steps": K,
         "warmup": args.warmup, "ms_per_step": max_ms / K, "higher_is_better": True,
         "scaling": "weak", "vs_baseline": None, "dtype": "f32" if w.precision == "fp32" else "f64",
         "data": "synthetic",
@@ -500,7 +541,10 @@ def run_tetm(args):
         "e2e": e2e,
         "gpu_launches": (10 * K if args.kernel == "reference" else K) + 6 * n_bal,
         "clocks": clk,
-        "balances": {"records": int(hist.shape[0]),
+        "balances": {"records": int(hist.shape[0]), "in_timed_region": n_bal,
+                     "ms_per_balance": bal_ms,
+                     "amortised_ms_per_step": bal_ms / be if be > 0 else 0.0,
+                     "share_of_step": (bal_ms / be) / (plain_ms + bal_ms / be) if be > 0 else 0.0,
                      "max_charge_residual_rel": float(np.max(hist[:, 2] / np.maximum(hist[:, 4], 1e-300)))
                      if hist.shape[0] else None,
                      "energy_last_J": float(hist[-1, 1]) if hist.shape[0] else None},

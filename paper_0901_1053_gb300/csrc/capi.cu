@@ -162,22 +162,27 @@ __global__ void from_canonical(const double* src, Layout L, int k0, int nk, cons
   dst[id] = ((mask[id] >> comp) & 1) ? (T)src[q] : T(0);
 }
 
-// One flag per fused work item (tile, z-chunk): 1 if any own cell carries a field.
-__global__ void item_flags(const uint8_t* mask, Layout L, int tx, int ty, int cz, int tiles_x,
-                           int tiles_y, int n_items, int* flags) {
+// Per fused work item (tile, z-chunk): the number of its own cells that
+// carry a field (0: the item lies in PEC and is skipped).
+__global__ void item_counts(const uint8_t* mask, Layout L, int tx, int ty, int cz, int tiles_x,
+                            int tiles_y, int n_items, int* counts) {
+  __shared__ int total;
   const int item = blockIdx.x;
   if (item >= n_items) return;
+  if (threadIdx.x == 0) total = 0;
+  __syncthreads();
   const int ntile = tiles_x * tiles_y;
   const int tile = item % ntile, chunk = item / ntile;
   const int i0 = (tile % tiles_x) * tx, j0 = (tile / tiles_x) * ty, k0 = chunk * cz;
-  int any = 0;
+  int c = 0;
   const int cells = tx * ty * cz;
-  for (int q = threadIdx.x; q < cells && !any; q += blockDim.x) {
+  for (int q = threadIdx.x; q < cells; q += blockDim.x) {
     const int i = i0 + q % tx, j = j0 + (q / tx) % ty, k = k0 + q / (tx * ty);
-    if (i < L.nx && j < L.ny && k < L.nz && mask[L.idx(i, j, k)] != 0) any = 1;
+    if (i < L.nx && j < L.ny && k < L.nz && mask[L.idx(i, j, k)] != 0) ++c;
   }
-  any = __syncthreads_or(any);
-  if (threadIdx.x == 0) flags[item] = any;
+  atomicAdd(&total, c);
+  __syncthreads();
+  if (threadIdx.x == 0) counts[item] = total;
 }
 
 // Entries of one component that hold a non-zero value where the activity bit
@@ -254,20 +259,22 @@ int tetm::rebuild_work(tetm_solver* s) {
   if (items >= (1LL << 31)) return TETM_E_ARG;
   if (s->work) {
     cudaFree(s->work);
-    s->device_bytes -= s->n_work > 0 ? 0 : 0;
     s->work = nullptr;
   }
-  int* flags = nullptr;
-  CK(cudaMalloc(&flags, sizeof(int) * (size_t)items));
-  item_flags<<<(unsigned)items, 256, 0, s->stream>>>(s->mask, L, s->tile_x, s->tile_y, s->chunk_z,
-                                                     s->tiles_x, s->tiles_y, (int)items, flags);
+  int* counts = nullptr;
+  CK(cudaMalloc(&counts, sizeof(int) * (size_t)items));
+  item_counts<<<(unsigned)items, 256, 0, s->stream>>>(s->mask, L, s->tile_x, s->tile_y, s->chunk_z,
+                                                      s->tiles_x, s->tiles_y, (int)items, counts);
   std::vector<int> h((size_t)items);
   cudaError_t e = cudaGetLastError();
-  if (e == cudaSuccess) e = cudaMemcpyAsync(h.data(), flags, sizeof(int) * (size_t)items,
+  if (e == cudaSuccess) e = cudaMemcpyAsync(h.data(), counts, sizeof(int) * (size_t)items,
                                             cudaMemcpyDeviceToHost, s->stream);
   if (e == cudaSuccess) e = cudaStreamSynchronize(s->stream);
-  cudaFree(flags);
+  cudaFree(counts);
   if (e != cudaSuccess) return cuda_fail(e);
+  // the items that own a field-carrying cell, in grid order: items that run
+  // at the same time are neighbours and share their halo rows through L2
+  // (ordering the list by work instead was measured 1.3x slower)
   std::vector<int> list;
   list.reserve((size_t)items);
   for (long long q = 0; q < items; ++q)
@@ -415,11 +422,11 @@ int do_steps(tetm_solver* s, int n) {
           CK(launch_fused_warp_step<T>(a, s->tile_x, s->tile_y, s->stream));
         } else if (slab_shape_ok(s->tile_x, s->tile_y)) {
           if constexpr (sizeof(T) == 4) {
-            if (!s->slab) {  // tensor maps of both field sets and the mask (fixed addresses)
+            if (!s->slab) {  // tensor maps of both field sets (fixed addresses)
               s->slab = new (std::nothrow) SlabMaps();
               void* ez[2] = {s->set[0][kEZ], s->set[1][kEZ]};
               void* hz[2] = {s->set[0][kHZ], s->set[1][kHZ]};
-              if (!s->slab || build_slab_maps(s->slab, ez, hz, s->mask, s->uniform ? nullptr : s->ua, s->L) != 0) {
+              if (!s->slab || build_slab_maps(s->slab, ez, hz, s->uniform ? nullptr : s->ua, s->L) != 0) {
                 delete s->slab;
                 s->slab = nullptr;
                 return TETM_E_UNSUPPORTED;

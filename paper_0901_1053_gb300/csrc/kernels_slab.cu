@@ -3,21 +3,30 @@
 // One CTA of 512 threads per SM takes (tile, z chunk) work items in turn. A
 // tile owns 56 x 28 nodes and loads 64 x 32 (4 halo columns and 2 halo rows on
 // each side: the ten updates reach two nodes sideways). Thread t holds the
-// four consecutive columns 4 (t mod 16) .. +3 of row t / 16, so its loads and
-// stores are 16-byte vectors, and marches through the chunk plane by plane
-// with the z-state of its four nodes in registers (old e_x, e_y of the plane,
+// four consecutive columns 4 (t mod 16) .. +3 of row t / 16 (a quad), so its
+// loads and stores are 16-byte vectors, and marches through the chunk plane by
+// plane with the z-state of its quad in registers (old e_x, e_y of the plane,
 // new h_x, h_y of the plane below): no per-row state in shared memory.
 //
-// e_z and h_z are the only inputs a node reads at its neighbours; they and the
-// activity bytes arrive through a ring of kSD planes in shared memory, one
-// 3D tensor copy (TMA) per array and plane issued kSD - 1 planes ahead,
-// completion on an mbarrier per slot (bounded waits: after kSlabPolls polls
-// the CTA raises the error word, drains the copies in flight and stops). h_x,
-// h_y, e_x, e_y are read at the node itself, with 16-byte loads one plane
-// ahead. The intermediates a stage reads one row up or down (hx~, ez', ex~,
-// hz') go through two shared-memory buffers, those one column left or right
-// through warp shuffles; four block barriers per plane, the first of which
-// also settles the slot waits:
+// Only entries that carry a field move through the per-thread loads and
+// stores. Each thread reads the activity bytes of its quad (one 32-bit word
+// per plane, three planes ahead) and
+//  * loads h_x, h_y, e_x, e_y of the quad (16-byte loads one plane ahead) only
+//    when one of its four nodes carries that component, else takes zero (an
+//    entry without a field holds zero for ever);
+//  * stores each new component of the quad only when one of its nodes
+//    carries it (the other field set's entry already holds that zero).
+// e_z and h_z (and with material arrays the six per-entry coefficient arrays)
+// are the inputs a node reads at its neighbours; they arrive through a ring
+// of kSD planes in shared memory, one 3D tensor copy (TMA) per array and plane
+// issued kSD planes ahead, completion on an mbarrier per slot (bounded waits:
+// after kSlabPolls polls the CTA raises the error word, drains the copies in
+// flight and stops).
+//
+// The intermediates a stage reads one row up or down (hx~, ez', ex~, hz') go
+// through two shared-memory buffers, those one column left or right through
+// warp shuffles; four block barriers per plane, the first of which also
+// settles the slot waits:
 //   S1 hx~, hy~ (U1, U2)  | S2 ez' (U3, + current) | S3 hx', hy' (U4, U5)
 //   S4 ex~, ey~ (U6, U7)  | S5 hz' (U8)            | S6 ex', ey' (U9, U10)
 // The column of i = 0 sits at 8 in the float32 layout, so the 224-byte rows a
@@ -40,17 +49,15 @@ constexpr int kSX = 64, kSY = 32;   // loaded columns, rows
 constexpr int kOX = 56, kOY = 28;   // owned columns, rows
 constexpr int kQ = kSX / 4;         // column quads per row
 constexpr int kSThreads = kQ * kSY; // 512
-constexpr int kMaskW = 80;          // activity bytes per row (from a 16-byte aligned column)
 constexpr int kSlabPolls = 1 << 18;
 
-// One material: a two-plane ring of e_z, h_z and the activity bytes (one
-// coefficient per component, switched by the bytes).
+// One material: a two-plane ring of e_z and h_z (one coefficient per
+// component, switched by the activity bytes).
 struct SlabSmemU {
   static constexpr int SD = 2;      // planes in the ring (the next plane lands while this one is worked on)
-  static constexpr unsigned slot_bytes = 2u * kSX * kSY * 4u + (unsigned)kMaskW * kSY;
+  static constexpr unsigned slot_bytes = 2u * kSX * kSY * 4u;
   float ez[SD][kSY][kSX];
   float hz[SD][kSY][kSX];
-  uint8_t mk[SD][kSY][kMaskW];
   float x1[kSY][kSX], x2[kSY][kSX];
   uint64_t bar[SD];
 };
@@ -101,16 +108,37 @@ __device__ __forceinline__ void tma3(void* dst, const CUtensorMap* map, int x, i
       ::"r"(su32(dst)), "l"(reinterpret_cast<uint64_t>(map)), "r"(x), "r"(y), "r"(z), "r"(su32(b))
       : "memory");
 }
-__device__ __forceinline__ float4 ld4(const float* p) {
-  float4 v;
-  asm volatile("ld.global.nc.v4.f32 {%0,%1,%2,%3}, [%4];" : "=f"(v.x), "=f"(v.y), "=f"(v.z), "=f"(v.w) : "l"(p));
+// loads and stores under a predicate, without a branch (zero where not loaded)
+__device__ __forceinline__ unsigned ld_word_if(const uint8_t* p, bool c) {
+  unsigned v;
+  asm volatile(
+      "{\n .reg .pred q;\n setp.ne.u32 q, %2, 0;\n mov.u32 %0, 0;\n @q ld.global.nc.u32 %0, [%1];\n}"
+      : "=r"(v)
+      : "l"(p), "r"((unsigned)c));
   return v;
 }
+// the quad's word holds one activity byte per node: component c of any node
+__device__ __forceinline__ bool has(unsigned m, int c) { return (m & (0x01010101u << c)) != 0u; }
 
 struct Q4 {
   float v[4];
 };
 __device__ __forceinline__ Q4 q4(float4 a) { return Q4{{a.x, a.y, a.z, a.w}}; }
+__device__ __forceinline__ Q4 ld4_if(const float* p, bool c) {
+  Q4 r;
+  asm volatile(
+      "{\n .reg .pred q;\n setp.ne.u32 q, %5, 0;\n mov.f32 %0, 0f00000000;\n mov.f32 %1, 0f00000000;\n"
+      " mov.f32 %2, 0f00000000;\n mov.f32 %3, 0f00000000;\n"
+      " @q ld.global.nc.v4.f32 {%0,%1,%2,%3}, [%4];\n}"
+      : "=f"(r.v[0]), "=f"(r.v[1]), "=f"(r.v[2]), "=f"(r.v[3])
+      : "l"(p), "r"((unsigned)c));
+  return r;
+}
+__device__ __forceinline__ void st4_if(float* p, const Q4& v, bool c) {
+  asm volatile("{\n .reg .pred q;\n setp.ne.u32 q, %5, 0;\n @q st.global.v4.f32 [%0], {%1,%2,%3,%4};\n}" ::"l"(p),
+               "f"(v.v[0]), "f"(v.v[1]), "f"(v.v[2]), "f"(v.v[3]), "r"((unsigned)c)
+               : "memory");
+}
 __device__ __forceinline__ Q4 lds4(const float* p) { return q4(*reinterpret_cast<const float4*>(p)); }
 __device__ __forceinline__ void sts4(float* p, const Q4& a) {
   *reinterpret_cast<float4*>(p) = make_float4(a.v[0], a.v[1], a.v[2], a.v[3]);
@@ -130,8 +158,7 @@ __device__ __forceinline__ float right_of(float v0, int q) {
 template <bool MAT>
 __global__ void __launch_bounds__(kSThreads, 1)
 fused_step_slab(const StepArgs<float> a, const __grid_constant__ CUtensorMap tm_ez,
-                const __grid_constant__ CUtensorMap tm_hz, const __grid_constant__ CUtensorMap tm_mk,
-                const __grid_constant__ CoefMaps tm_co, int* err) {
+                const __grid_constant__ CUtensorMap tm_hz, const __grid_constant__ CoefMaps tm_co, int* err) {
   using Smem = SlabSmem<MAT>;
   constexpr int kSD = Smem::SD;
   extern __shared__ __align__(128) unsigned char slab_raw[];
@@ -149,8 +176,15 @@ fused_step_slab(const StepArgs<float> a, const __grid_constant__ CUtensorMap tm_
   const float uHX = a.co.u[kHX], uHY = a.co.u[kHY], uHZ = a.co.u[kHZ];
   const int ntile = a.tiles_x * a.tiles_y;
   const int nitems = a.work ? a.n_work : ntile * a.n_chunks;
+  const Q4 zero{{0.f, 0.f, 0.f, 0.f}};
 
-  for (int wi = blockIdx.x; wi < nitems; wi += gridDim.x) {
+  // CTAs take the work list in snake order (rounds alternate direction): a
+  // round's items are neighbours (shared halo rows in L2) and a CTA that drew
+  // an item from one end of a round draws from the other end in the next
+  const int G = gridDim.x, rounds = (nitems + G - 1) / G;
+  for (int r = 0; r < rounds; ++r) {
+    const int wi = (r & 1) ? r * G + (G - 1 - (int)blockIdx.x) : r * G + (int)blockIdx.x;
+    if (wi >= nitems) continue;  // CTA-uniform: only in the last round
     const int item = a.work ? a.work[wi] : wi;
     const int tile = item % ntile, chunk = item / ntile;
     const int gx0 = (tile % a.tiles_x) * kOX - 4;  // global i of loaded column 0
@@ -159,32 +193,18 @@ fused_step_slab(const StepArgs<float> a, const __grid_constant__ CUtensorMap tm_
     const int kstart = k0 - 1;
     const int nplanes = k1 - kstart;
     const int cx = gx0 + L.ox, cy = gy0 + 2;     // tensor coordinates (column, row)
-    const int mx = cx & ~15, moff = cx - mx;     // activity bytes: 16-byte aligned box
 
-    // this thread's four nodes
+    // this thread's quad; a quad with an active node lies inside its layout
+    // row (columns i <= nx + 2 < px - ox), so every predicated access is a
+    // whole 16-byte vector (a quad across i = nx stores the zeros its entries
+    // past the cells compute: zero input, zero coefficient)
     const int gi = gx0 + 4 * q, gj = gy0 + row;
-    const int jc = min(gj, L.ny + 1);
-    const bool vec = gi + 3 <= L.nx + 1;         // the quad lies inside the padded row
+    const bool inq = gj + 2 < L.ny + 4 && cx + 4 * q + 4 <= PX;  // the quad lies inside the arrays
+    const long long qoff = (long long)(gj + 2) * PX + cx + 4 * q;
     const bool own_q = q >= 1 && q <= kQ - 2 && row >= 2 && row < kSY - 2 && gj < L.ny;
-    auto gidx = [&](int k) { return (long long)(k + 1) * SZ + (long long)(jc + 2) * PX + (gi + L.ox); };
-    auto load_q = [&](const float* base, int k) -> Q4 {
-      const long long id = gidx(k);
-      if (vec) return q4(ld4(base + id));
-      Q4 r;
-#pragma unroll
-      for (int e = 0; e < 4; ++e) r.v[e] = gi + e <= L.nx + 1 ? base[id + e] : 0.f;
-      return r;
-    };
-    auto store_q = [&](float* base, int k, const Q4& v) {
-      const long long id = gidx(k);
-      if (gi + 3 < L.nx) {
-        *reinterpret_cast<float4*>(base + id) = make_float4(v.v[0], v.v[1], v.v[2], v.v[3]);
-      } else {
-#pragma unroll
-        for (int e = 0; e < 4; ++e)
-          if (gi + e < L.nx) base[id + e] = v.v[e];
-      }
-    };
+    auto gidx = [&](int k) { return (long long)(k + 1) * SZ + qoff; };
+    auto word = [&](int k) -> unsigned { return ld_word_if(a.co.mask + gidx(k), inq); };
+    auto load_if = [&](const float* base, int k, bool p) -> Q4 { return ld4_if(base + gidx(k), p); };
     auto issue = [&](int k) {  // plane k into its slot (one thread)
       const int s = (k - kstart) % kSD;
       asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
@@ -194,20 +214,22 @@ fused_step_slab(const StepArgs<float> a, const __grid_constant__ CUtensorMap tm_
       if constexpr (MAT) {
 #pragma unroll
         for (int c = 0; c < 6; ++c) tma3(&S.co[s][c][0][0], &tm_co.m[c], cx, cy, k + 1, &S.bar[s]);
-      } else {
-        tma3(&S.mk[s][0][0], &tm_mk, mx, cy, k + 1, &S.bar[s]);
       }
     };
     if (tid == 0)
       for (int k = kstart; k < kstart + min(kSD, nplanes); ++k) issue(k);
     int issued = kstart + min(kSD, nplanes) - 1;  // last plane queued (thread 0 keeps it)
 
-    // z-state and the register prefetch (plane k: hx, hy of k; ex, ey of k+1)
-    Q4 ex0 = load_q(a.in[kEX], kstart), ey0 = load_q(a.in[kEY], kstart);
-    Q4 hxc = load_q(a.in[kHX], kstart), hyc = load_q(a.in[kHY], kstart);
-    Q4 ex1 = load_q(a.in[kEX], kstart + 1), ey1 = load_q(a.in[kEY], kstart + 1);
-    Q4 hxp{{0.f, 0.f, 0.f, 0.f}}, hyp{{0.f, 0.f, 0.f, 0.f}};
+    // activity words of planes kstart .. kstart + 2 (m0 of the plane being
+    // worked on, m1, m2 of the next two); z-state and the register prefetch
+    // (plane k: hx, hy of k; ex, ey of k+1)
+    unsigned m0 = word(kstart), m1 = word(kstart + 1), m2 = word(kstart + 2);
+    Q4 ex0 = load_if(a.in[kEX], kstart, has(m0, kEX)), ey0 = load_if(a.in[kEY], kstart, has(m0, kEY));
+    Q4 hxc = load_if(a.in[kHX], kstart, has(m0, kHX)), hyc = load_if(a.in[kHY], kstart, has(m0, kHY));
+    Q4 ex1 = load_if(a.in[kEX], kstart + 1, has(m1, kEX)), ey1 = load_if(a.in[kEY], kstart + 1, has(m1, kEY));
+    Q4 hxp = zero, hyp = zero;
     const bool line_row = a.b.on && gj == a.b.j0;
+    const bool line_q = line_row && a.b.i0 >= gi && a.b.i0 < gi + 4;  // the quad holds the bunch line node
 
     for (int k = kstart; k < k1; ++k) {
       const int s = (k - kstart) % kSD;
@@ -215,23 +237,25 @@ fused_step_slab(const StepArgs<float> a, const __grid_constant__ CUtensorMap tm_
       // (1) (a thread whose wait gave up computes on stale data until then,
       // nothing is stored before it)
       const bool ok = bar_wait(&S.bar[s], (phases >> s) & 1u);
-      // next plane's register inputs, early
+      // next plane's register inputs and the activity word three planes on, early
       Q4 hxn_in, hyn_in, exn_in, eyn_in;
+      unsigned m3 = 0u;
       const bool more = k + 1 < k1;
       if (more) {
-        hxn_in = load_q(a.in[kHX], k + 1);
-        hyn_in = load_q(a.in[kHY], k + 1);
-        exn_in = load_q(a.in[kEX], k + 2);
-        eyn_in = load_q(a.in[kEY], k + 2);
+        hxn_in = load_if(a.in[kHX], k + 1, has(m1, kHX));
+        hyn_in = load_if(a.in[kHY], k + 1, has(m1, kHY));
+        exn_in = load_if(a.in[kEX], k + 2, has(m2, kEX));
+        eyn_in = load_if(a.in[kEY], k + 2, has(m2, kEY));
+        if (k + 3 <= k1) m3 = word(k + 3);
       }
-      // slot inputs: e_z, h_z of this quad and its neighbours, activity bytes
+      // slot inputs: e_z, h_z of this quad and its neighbours
       const float* sez = &S.ez[s][0][0];
       const float* shz = &S.hz[s][0][0];
       const Q4 ez = lds4(sez + row * kSX + 4 * q);
-      const Q4 ezU = row + 1 < kSY ? lds4(sez + (row + 1) * kSX + 4 * q) : Q4{{0.f, 0.f, 0.f, 0.f}};
+      const Q4 ezU = row + 1 < kSY ? lds4(sez + (row + 1) * kSX + 4 * q) : zero;
       const float ezR = q + 1 < kQ ? sez[row * kSX + 4 * q + 4] : 0.f;
       const Q4 hz = lds4(shz + row * kSX + 4 * q);
-      const Q4 hzD = row >= 1 ? lds4(shz + (row - 1) * kSX + 4 * q) : Q4{{0.f, 0.f, 0.f, 0.f}};
+      const Q4 hzD = row >= 1 ? lds4(shz + (row - 1) * kSX + 4 * q) : zero;
       const float hzL = q >= 1 ? shz[row * kSX + 4 * q - 1] : 0.f;
       float cHX[4], cHY[4], cEZ[4], cEX[4], cEY[4], cHZ[4], dey[4], dex[4];
       if constexpr (MAT) {  // per-entry coefficients from the slot
@@ -248,10 +272,9 @@ fused_step_slab(const StepArgs<float> a, const __grid_constant__ CUtensorMap tm_
           cHZ[e] = c5.v[e];
         }
       } else {  // one coefficient per component, switched by the activity bytes
-        const unsigned mw = *reinterpret_cast<const unsigned*>(&S.mk[s][row][moff + 4 * q]);
 #pragma unroll
         for (int e = 0; e < 4; ++e) {
-          const unsigned m = (mw >> (8 * e)) & 0xFFu;
+          const unsigned m = (m0 >> (8 * e)) & 0xFFu;
           cEX[e] = (m & 1) ? uEX : 0.f;
           cEY[e] = (m & 2) ? uEY : 0.f;
           cEZ[e] = (m & 4) ? uEZ : 0.f;
@@ -289,23 +312,30 @@ fused_step_slab(const StepArgs<float> a, const __grid_constant__ CUtensorMap tm_
         issued = k + kSD;
       }
       // S2: ez' = ez + 2a M^-1 (P_y^T hx~ - P_x^T hy~ - jj_z)
-      const Q4 hxaD = row >= 1 ? lds4(&S.x1[row - 1][4 * q]) : Q4{{0.f, 0.f, 0.f, 0.f}};
+      const Q4 hxaD = row >= 1 ? lds4(&S.x1[row - 1][4 * q]) : zero;
       const float hyaL = left_of(hya.v[3], q);
-      Q4 ezn;
+      float cur[4];
 #pragma unroll
       for (int e = 0; e < 4; ++e) {
         const float hyl = e > 0 ? hya.v[e - 1] : hyaL;
-        float cur = (hxaD.v[e] - hxa.v[e]) - (hyl - hya.v[e]);
-        if (line_row && gi + e == a.b.i0 && k >= 0) {
-          const long long dd = (long long)k - (a.n + a.b.kshift) + a.b.c0;
-          if (dd >= -a.b.c0 && dd < a.b.c0) cur -= a.b.J[dd + a.b.c0];
-        }
-        ezn.v[e] = ez.v[e] + cEZ[e] * cur;                                // U3
+        cur[e] = (hxaD.v[e] - hxa.v[e]) - (hyl - hya.v[e]);
       }
+      if (line_q && k >= 0) {  // the bunch current on its line (one quad of a tile row)
+        const long long dd = (long long)k - (a.n + a.b.kshift) + a.b.c0;
+        if (dd >= -a.b.c0 && dd < a.b.c0) {
+          const float jj = a.b.J[dd + a.b.c0];
+#pragma unroll
+          for (int e = 0; e < 4; ++e)
+            if (gi + e == a.b.i0) cur[e] -= jj;
+        }
+      }
+      Q4 ezn;
+#pragma unroll
+      for (int e = 0; e < 4; ++e) ezn.v[e] = ez.v[e] + cEZ[e] * cur[e];   // U3
       sts4(&S.x2[row][4 * q], ezn);
       __syncthreads();  // (2)
       // S3: hx', hy'
-      const Q4 eznU = row + 1 < kSY ? lds4(&S.x2[row + 1][4 * q]) : Q4{{0.f, 0.f, 0.f, 0.f}};
+      const Q4 eznU = row + 1 < kSY ? lds4(&S.x2[row + 1][4 * q]) : zero;
       const float eznR = right_of(ezn.v[0], q);
       Q4 hxn, hyn;
 #pragma unroll
@@ -314,15 +344,19 @@ fused_step_slab(const StepArgs<float> a, const __grid_constant__ CUtensorMap tm_
         hxn.v[e] = hxa.v[e] + cHX[e] * (dey[e] - (eznU.v[e] - ezn.v[e]));  // U4
         hyn.v[e] = hya.v[e] + cHY[e] * (-dex[e] + (ezx - ezn.v[e]));     // U5
       }
-      const bool te = k >= k0;
-      if (te && own_q) {
-        store_q(a.out[kEZ], k, ezn);
-        store_q(a.out[kHX], k, hxn);
-        store_q(a.out[kHY], k, hyn);
-        if (line_row && a.b.i0 >= gi && a.b.i0 < gi + 4 && a.b.i0 < L.nx) {
+      const bool st = k >= k0 && own_q;
+      st4_if(a.out[kEZ] + gidx(k), ezn, st && has(m0, kEZ));
+      st4_if(a.out[kHX] + gidx(k), hxn, st && has(m0, kHX));
+      st4_if(a.out[kHY] + gidx(k), hyn, st && has(m0, kHY));
+      if (st) {
+        if (line_q && a.b.i0 < L.nx) {
           const long long mm = (a.n + a.b.kshift) - k - a.b.c0;
           if (mm >= a.b.m_min && mm <= a.b.m_max)
-            a.b.W[mm - a.b.m_min] -= (double)ezn.v[a.b.i0 - gi] * a.b.inv_q;
+          {
+            const int e = a.b.i0 - gi;  // the quad's entry on the bunch line (no indexed register array)
+            const float v = e == 0 ? ezn.v[0] : e == 1 ? ezn.v[1] : e == 2 ? ezn.v[2] : ezn.v[3];
+            a.b.W[mm - a.b.m_min] -= (double)v * a.b.inv_q;
+          }
         }
       }
       // S4: ex~, ey~ with the new hx, hy of this plane and of the plane below
@@ -336,7 +370,7 @@ fused_step_slab(const StepArgs<float> a, const __grid_constant__ CUtensorMap tm_
       sts4(&S.x1[row][4 * q], exa);
       __syncthreads();  // (3)
       // S5: hz'
-      const Q4 exaU = row + 1 < kSY ? lds4(&S.x1[row + 1][4 * q]) : Q4{{0.f, 0.f, 0.f, 0.f}};
+      const Q4 exaU = row + 1 < kSY ? lds4(&S.x1[row + 1][4 * q]) : zero;
       const float eyaR = right_of(eya.v[0], q);
       Q4 hzn;
 #pragma unroll
@@ -347,7 +381,7 @@ fused_step_slab(const StepArgs<float> a, const __grid_constant__ CUtensorMap tm_
       sts4(&S.x2[row][4 * q], hzn);
       __syncthreads();  // (4)
       // S6: ex', ey'
-      const Q4 hznD = row >= 1 ? lds4(&S.x2[row - 1][4 * q]) : Q4{{0.f, 0.f, 0.f, 0.f}};
+      const Q4 hznD = row >= 1 ? lds4(&S.x2[row - 1][4 * q]) : zero;
       const float hznL = left_of(hzn.v[3], q);
       Q4 exn, eyn;
 #pragma unroll
@@ -356,16 +390,17 @@ fused_step_slab(const StepArgs<float> a, const __grid_constant__ CUtensorMap tm_
         exn.v[e] = exa.v[e] + cEX[e] * ((hyp.v[e] - hyn.v[e]) - (hznD.v[e] - hzn.v[e]));   // U9
         eyn.v[e] = eya.v[e] + cEY[e] * (-(hxp.v[e] - hxn.v[e]) + (hzl - hzn.v[e]));       // U10
       }
-      if (te && own_q) {
-        store_q(a.out[kEX], k, exn);
-        store_q(a.out[kEY], k, eyn);
-        store_q(a.out[kHZ], k, hzn);
-      }
+      st4_if(a.out[kEX] + gidx(k), exn, st && has(m0, kEX));
+      st4_if(a.out[kEY] + gidx(k), eyn, st && has(m0, kEY));
+      st4_if(a.out[kHZ] + gidx(k), hzn, st && has(m0, kHZ));
       // carry the z-state, take the prefetched inputs
       hxp = hxn;
       hyp = hyn;
       ex0 = ex1;
       ey0 = ey1;
+      m0 = m1;
+      m1 = m2;
+      m2 = m3;
       if (more) {
         hxc = hxn_in;
         hyc = hyn_in;
@@ -408,8 +443,7 @@ CUresult encode3d(CUtensorMap* map, CUtensorMapDataType type, void* base, const 
 
 bool slab_shape_ok(int tx, int ty) { return tx == kOX && ty == kOY; }
 
-int build_slab_maps(SlabMaps* m, void* const ez[2], void* const hz[2], const uint8_t* mask,
-                    void* const co[6], const Layout& L) {
+int build_slab_maps(SlabMaps* m, void* const ez[2], void* const hz[2], void* const co[6], const Layout& L) {
   static_assert(sizeof(CUtensorMap) <= sizeof(m->ez[0]), "tensor map storage");
   // the tiled copies need 16-byte row strides and 16-byte box starts
   if ((L.px * 4) % 16 != 0 || L.px % 16 != 0 || (L.ox % 4) != 0) return -1;
@@ -420,9 +454,6 @@ int build_slab_maps(SlabMaps* m, void* const ez[2], void* const hz[2], const uin
             CUDA_SUCCESS)
       return -1;
   }
-  if (encode3d(reinterpret_cast<CUtensorMap*>(m->mk), CU_TENSOR_MAP_DATA_TYPE_UINT8, const_cast<uint8_t*>(mask),
-               L, 1, kMaskW) != CUDA_SUCCESS)
-    return -1;
   m->has_co = co != nullptr;
   if (co)
     for (int c = 0; c < 6; ++c)
@@ -452,14 +483,13 @@ cudaError_t launch_slab(const StepArgs<float>& a, const SlabMaps& m, int cur, in
   if (items <= 0) return cudaSuccess;
   const CUtensorMap& mez = *reinterpret_cast<const CUtensorMap*>(m.ez[cur]);
   const CUtensorMap& mhz = *reinterpret_cast<const CUtensorMap*>(m.hz[cur]);
-  const CUtensorMap& mmk = *reinterpret_cast<const CUtensorMap*>(m.mk);
   CoefMaps mco;
   if constexpr (MAT) {
     for (int c = 0; c < 6; ++c) mco.m[c] = *reinterpret_cast<const CUtensorMap*>(m.co[c]);
   } else {
     memset(&mco, 0, sizeof(mco));
   }
-  fused_step_slab<MAT><<<std::min(items, sms), kSThreads, smem, st>>>(a, mez, mhz, mmk, mco, err);
+  fused_step_slab<MAT><<<std::min(items, sms), kSThreads, smem, st>>>(a, mez, mhz, mco, err);
   return cudaGetLastError();
 }
 }  // namespace

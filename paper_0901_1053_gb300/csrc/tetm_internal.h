@@ -129,18 +129,16 @@ cudaError_t launch_fused_warp_batch(const BatchMember<T>* members, int n_members
 
 // ---- block-tiled float32 step with tensor staging (kernels_slab.cu): tile
 // 56 x 28, one CTA of 512 threads per SM ----------------------------------
-struct SlabMaps {  // tensor maps (CUtensorMap) of e_z and h_z of both field sets, the mask
-                  // and (material runs) the six coefficient arrays
+struct SlabMaps {  // tensor maps (CUtensorMap) of e_z and h_z of both field sets and
+                  // (material runs) the six coefficient arrays
   alignas(64) unsigned char ez[2][128];
   alignas(64) unsigned char hz[2][128];
-  alignas(64) unsigned char mk[128];
   alignas(64) unsigned char co[6][128];
   bool has_co;
 };
 bool slab_shape_ok(int tile_x, int tile_y);
 // co: the six per-entry coefficient arrays, or nullptr (one material)
-int build_slab_maps(SlabMaps* m, void* const ez[2], void* const hz[2], const uint8_t* mask,
-                    void* const co[6], const Layout& L);
+int build_slab_maps(SlabMaps* m, void* const ez[2], void* const hz[2], void* const co[6], const Layout& L);
 cudaError_t launch_fused_slab_step(const StepArgs<float>& a, const SlabMaps& m, int cur, int* err,
                                    cudaStream_t st);
 
