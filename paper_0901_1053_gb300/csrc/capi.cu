@@ -432,7 +432,7 @@ int do_steps(tetm_solver* s, int n) {
                 return TETM_E_UNSUPPORTED;
               }
             }
-            CK(launch_fused_slab_step(a, *s->slab, s->cur, s->err, s->stream));
+            CK(launch_fused_slab_step(a, *s->slab, s->cur, s->err, s->sched, s->stream));
           } else {
             return TETM_E_UNSUPPORTED;
           }
@@ -522,6 +522,7 @@ void free_all(tetm_solver* s) {
   cudaFree(s->hist);
   cudaFree(s->staging);
   cudaFree(s->err);
+  cudaFree(s->sched);
   delete s->slab;
   s->slab = nullptr;
 }
@@ -610,6 +611,8 @@ int tetm_create(const tetm_grid* g, const double* eps_r, const double* mu_r, con
   if (rc == TETM_OK) rc = dalloc(s, (void**)&s->diag.out, sizeof(double) * 8);
   if (rc == TETM_OK) rc = dalloc(s, (void**)&s->err, sizeof(int));
   if (rc == TETM_OK) rc = cudaMemsetAsync(s->err, 0, sizeof(int), s->stream) == cudaSuccess ? TETM_OK : TETM_E_CUDA;
+  if (rc == TETM_OK) rc = dalloc(s, (void**)&s->sched, 2 * sizeof(int));
+  if (rc == TETM_OK) rc = cudaMemsetAsync(s->sched, 0, 2 * sizeof(int), s->stream) == cudaSuccess ? TETM_OK : TETM_E_CUDA;
   s->diag.cap = 2048;
   s->hist_cap = 4096;
   if (rc == TETM_OK) rc = dalloc(s, (void**)&s->hist, sizeof(double) * 5 * (size_t)s->hist_cap);

@@ -56,24 +56,27 @@ constexpr int kSlabPolls = 1 << 18;
 struct SlabSmemU {
   static constexpr int SD = 2;      // planes in the ring (the next plane lands while this one is worked on)
   static constexpr unsigned slot_bytes = 2u * kSX * kSY * 4u;
-  float ez[SD][kSY][kSX];
-  float hz[SD][kSY][kSX];
+  float ez[SD][kSY * kSX];
+  float hz[SD][kSY * kSX];
   float x1[kSY][kSX], x2[kSY][kSX];
   uint64_t bar[SD];
+  int next[2];                      // the CTA's next work item (dynamic schedule)
 };
 // Material arrays: a three-plane ring of e_z, h_z and the six per-entry
 // coefficient arrays (alpha M^-1, 2 alpha M^-1 for e_z and h_z), 208 KB.
 struct SlabSmemM {
   static constexpr int SD = 3;
   static constexpr unsigned slot_bytes = 8u * kSX * kSY * 4u;
-  float ez[SD][kSY][kSX];
-  float hz[SD][kSY][kSX];
+  float ez[SD][kSY * kSX];
+  float hz[SD][kSY * kSX];
   float co[SD][6][kSY][kSX];
   float x1[kSY][kSX], x2[kSY][kSX];
   uint64_t bar[SD];
+  int next[2];
 };
 template <bool MAT>
 using SlabSmem = typename std::conditional<MAT, SlabSmemM, SlabSmemU>::type;
+
 
 // the six coefficient arrays' tensor maps (material runs)
 struct CoefMaps {
@@ -81,9 +84,10 @@ struct CoefMaps {
 };
 
 __device__ __forceinline__ unsigned su32(const void* p) { return (unsigned)__cvta_generic_to_shared(p); }
-__device__ __forceinline__ void bar_init(uint64_t* b) {
-  asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(su32(b)) : "memory");
+__device__ __forceinline__ void bar_init(uint64_t* b, unsigned count) {
+  asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(su32(b)), "r"(count) : "memory");
 }
+
 __device__ __forceinline__ void bar_expect(uint64_t* b, unsigned bytes) {
   asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(su32(b)), "r"(bytes) : "memory");
 }
@@ -158,14 +162,16 @@ __device__ __forceinline__ float right_of(float v0, int q) {
 template <bool MAT>
 __global__ void __launch_bounds__(kSThreads, 1)
 fused_step_slab(const StepArgs<float> a, const __grid_constant__ CUtensorMap tm_ez,
-                const __grid_constant__ CUtensorMap tm_hz, const __grid_constant__ CoefMaps tm_co, int* err) {
+                const __grid_constant__ CUtensorMap tm_hz, const __grid_constant__ CoefMaps tm_co, int* err,
+                int* sched) {
   using Smem = SlabSmem<MAT>;
   constexpr int kSD = Smem::SD;
   extern __shared__ __align__(128) unsigned char slab_raw[];
   Smem& S = *reinterpret_cast<Smem*>(slab_raw);
   const int tid = threadIdx.x, q = tid % kQ, row = tid / kQ;
-  if (tid == 0)
-    for (int s = 0; s < kSD; ++s) bar_init(&S.bar[s]);
+  if (tid == 0) {
+    for (int s = 0; s < kSD; ++s) bar_init(&S.bar[s], 1u);
+  }
   asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
   __syncthreads();
   unsigned phases = 0;
@@ -177,14 +183,16 @@ fused_step_slab(const StepArgs<float> a, const __grid_constant__ CUtensorMap tm_
   const int ntile = a.tiles_x * a.tiles_y;
   const int nitems = a.work ? a.n_work : ntile * a.n_chunks;
   const Q4 zero{{0.f, 0.f, 0.f, 0.f}};
+  bool failed = false;
 
-  // CTAs take the work list in snake order (rounds alternate direction): a
-  // round's items are neighbours (shared halo rows in L2) and a CTA that drew
-  // an item from one end of a round draws from the other end in the next
-  const int G = gridDim.x, rounds = (nitems + G - 1) / G;
-  for (int r = 0; r < rounds; ++r) {
-    const int wi = (r & 1) ? r * G + (G - 1 - (int)blockIdx.x) : r * G + (int)blockIdx.x;
-    if (wi >= nitems) continue;  // CTA-uniform: only in the last round
+  // Items in list order: the first per CTA by its index, then (with a
+  // schedule counter) whichever item is next when the CTA gets free, fetched
+  // one item ahead. Items that run at the same time stay neighbours (shared
+  // halo rows in L2) and CTAs that drew cheap items (much PEC) take more.
+  const int G = gridDim.x;
+  int wi = blockIdx.x, par = 0;
+  while (wi < nitems && !failed) {
+    if (tid == 0 && sched) S.next[par] = G + atomicAdd(sched, 1);
     const int item = a.work ? a.work[wi] : wi;
     const int tile = item % ntile, chunk = item / ntile;
     const int gx0 = (tile % a.tiles_x) * kOX - 4;  // global i of loaded column 0
@@ -205,12 +213,13 @@ fused_step_slab(const StepArgs<float> a, const __grid_constant__ CUtensorMap tm_
     auto gidx = [&](int k) { return (long long)(k + 1) * SZ + qoff; };
     auto word = [&](int k) -> unsigned { return ld_word_if(a.co.mask + gidx(k), inq); };
     auto load_if = [&](const float* base, int k, bool p) -> Q4 { return ld4_if(base + gidx(k), p); };
-    auto issue = [&](int k) {  // plane k into its slot (one thread)
+    // plane k into its slot (one thread): whole 64 x 32 boxes
+    auto issue = [&](int k) {
       const int s = (k - kstart) % kSD;
       asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
       bar_expect(&S.bar[s], Smem::slot_bytes);
-      tma3(&S.ez[s][0][0], &tm_ez, cx, cy, k + 1, &S.bar[s]);
-      tma3(&S.hz[s][0][0], &tm_hz, cx, cy, k + 1, &S.bar[s]);
+      tma3(&S.ez[s][0], &tm_ez, cx, cy, k + 1, &S.bar[s]);
+      tma3(&S.hz[s][0], &tm_hz, cx, cy, k + 1, &S.bar[s]);
       if constexpr (MAT) {
 #pragma unroll
         for (int c = 0; c < 6; ++c) tma3(&S.co[s][c][0][0], &tm_co.m[c], cx, cy, k + 1, &S.bar[s]);
@@ -218,7 +227,7 @@ fused_step_slab(const StepArgs<float> a, const __grid_constant__ CUtensorMap tm_
     };
     if (tid == 0)
       for (int k = kstart; k < kstart + min(kSD, nplanes); ++k) issue(k);
-    int issued = kstart + min(kSD, nplanes) - 1;  // last plane queued (thread 0 keeps it)
+    int issued = kstart + min(kSD, nplanes) - 1;  // last plane queued (the same in every thread)
 
     // activity words of planes kstart .. kstart + 2 (m0 of the plane being
     // worked on, m1, m2 of the next two); z-state and the register prefetch
@@ -249,8 +258,8 @@ fused_step_slab(const StepArgs<float> a, const __grid_constant__ CUtensorMap tm_
         if (k + 3 <= k1) m3 = word(k + 3);
       }
       // slot inputs: e_z, h_z of this quad and its neighbours
-      const float* sez = &S.ez[s][0][0];
-      const float* shz = &S.hz[s][0][0];
+      const float* sez = &S.ez[s][0];
+      const float* shz = &S.hz[s][0];
       const Q4 ez = lds4(sez + row * kSX + 4 * q);
       const Q4 ezU = row + 1 < kSY ? lds4(sez + (row + 1) * kSX + 4 * q) : zero;
       const float ezR = q + 1 < kQ ? sez[row * kSX + 4 * q + 4] : 0.f;
@@ -304,11 +313,12 @@ fused_step_slab(const StepArgs<float> a, const __grid_constant__ CUtensorMap tm_
           }
         }
         __syncthreads();
-        return;
+        failed = true;
+        break;
       }
       phases ^= 1u << s;
-      if (tid == 0 && k + kSD < k1) {
-        issue(k + kSD);
+      if (k + kSD < k1) {
+        if (tid == 0) issue(k + kSD);
         issued = k + kSD;
       }
       // S2: ez' = ez + 2a M^-1 (P_y^T hx~ - P_x^T hy~ - jj_z)
@@ -409,6 +419,16 @@ fused_step_slab(const StepArgs<float> a, const __grid_constant__ CUtensorMap tm_
       }
     }
     __syncthreads();  // every thread is done with the ring before the next item refills it
+    wi = sched ? S.next[par] : wi + G;
+    par ^= 1;
+  }
+  // the last CTA to finish resets the schedule counter for the next launch
+  if (tid == 0 && sched) {
+    __threadfence();
+    if (atomicAdd(sched + 1, 1) == G - 1) {
+      atomicExch(sched, 0);
+      atomicExch(sched + 1, 0);
+    }
   }
 }
 
@@ -465,7 +485,8 @@ int build_slab_maps(SlabMaps* m, void* const ez[2], void* const hz[2], void* con
 
 namespace {
 template <bool MAT>
-cudaError_t launch_slab(const StepArgs<float>& a, const SlabMaps& m, int cur, int* err, cudaStream_t st) {
+cudaError_t launch_slab(const StepArgs<float>& a, const SlabMaps& m, int cur, int* err, int* sched,
+                        cudaStream_t st) {
   static int sms = 0;
   const size_t smem = sizeof(SlabSmem<MAT>);
   if (!sms) {
@@ -489,16 +510,16 @@ cudaError_t launch_slab(const StepArgs<float>& a, const SlabMaps& m, int cur, in
   } else {
     memset(&mco, 0, sizeof(mco));
   }
-  fused_step_slab<MAT><<<std::min(items, sms), kSThreads, smem, st>>>(a, mez, mhz, mco, err);
+  fused_step_slab<MAT><<<std::min(items, sms), kSThreads, smem, st>>>(a, mez, mhz, mco, err, sched);
   return cudaGetLastError();
 }
 }  // namespace
 
-cudaError_t launch_fused_slab_step(const StepArgs<float>& a, const SlabMaps& m, int cur, int* err,
+cudaError_t launch_fused_slab_step(const StepArgs<float>& a, const SlabMaps& m, int cur, int* err, int* sched,
                                    cudaStream_t st) {
   // per-entry coefficient arrays (material runs) need their tensor maps
-  if (a.co.ua[0]) return m.has_co ? launch_slab<true>(a, m, cur, err, st) : cudaErrorInvalidValue;
-  return launch_slab<false>(a, m, cur, err, st);
+  if (a.co.ua[0]) return m.has_co ? launch_slab<true>(a, m, cur, err, sched, st) : cudaErrorInvalidValue;
+  return launch_slab<false>(a, m, cur, err, sched, st);
 }
 
 }  // namespace tetm

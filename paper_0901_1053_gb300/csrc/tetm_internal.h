@@ -139,7 +139,9 @@ struct SlabMaps {  // tensor maps (CUtensorMap) of e_z and h_z of both field set
 bool slab_shape_ok(int tile_x, int tile_y);
 // co: the six per-entry coefficient arrays, or nullptr (one material)
 int build_slab_maps(SlabMaps* m, void* const ez[2], void* const hz[2], void* const co[6], const Layout& L);
-cudaError_t launch_fused_slab_step(const StepArgs<float>& a, const SlabMaps& m, int cur, int* err,
+// sched: two ints of device memory, zero before the first launch, that the
+// kernel's dynamic schedule uses and leaves zero (nullptr: static order)
+cudaError_t launch_fused_slab_step(const StepArgs<float>& a, const SlabMaps& m, int cur, int* err, int* sched,
                                    cudaStream_t st);
 
 // ---- Yee's E/M leapfrog, Eq. (7) (kernels_yee.cu): the step arguments carry
@@ -216,6 +218,7 @@ struct tetm_solver {
   int tile_x, tile_y, chunk_z;
   tetm::SlabMaps* slab;          // tensor maps of the slab kernel (built on first use)
   int* err;                      // device error word of the slab kernel's bounded waits
+  int* sched;                    // the slab kernel's schedule counters (two ints)
   int tiles_x, tiles_y, n_chunks;
   int* work;
   int n_work;
