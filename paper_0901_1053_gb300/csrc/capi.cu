@@ -281,11 +281,11 @@ int tetm::rebuild_work(tetm_solver* s) {
     if (h[(size_t)q]) list.push_back((int)q);
   s->n_work = (int)list.size();
   s->work_host = list;
-  if (2 * s->n_work > s->diag.cap) {  // balance reductions keep one partial per work item
+  if (3 * s->n_work > s->diag.cap) {  // balance reductions keep three partials per work item
     cudaFree(s->diag.part);
     s->diag.part = nullptr;
     s->diag.cap = 0;
-    const int cap = std::max(2048, 2 * s->n_work);
+    const int cap = std::max(2048, 3 * s->n_work);
     CK(cudaMalloc(&s->diag.part, sizeof(double) * (size_t)cap));
     s->diag.cap = cap;
   }
@@ -382,6 +382,11 @@ int queue_balances(tetm_solver* s, double* rec) {
     ma[c] = s->minv_a[c];
   }
   const WorkView wv = work_view(s);
+  if (s->uniform) {  // one pass for both
+    CK(launch_balances<T>(cur, prv, s->mask, s->minv_c, s->L, s->alpha, s->bunch ? s->qline : nullptr, s->i0,
+                          s->j0, wv, s->diag, rec + 1, rec + 2, rec + 3, s->stream));
+    return TETM_OK;
+  }
   CK(launch_energy<T>(cur, s->mask, s->minv_c, ma, s->L, s->alpha, wv, s->diag, rec + 1, s->stream));
   CK(launch_charge<T>(cur, prv, s->mask, s->minv_c, ma, s->L, s->alpha,
                       s->bunch ? s->qline : nullptr, s->i0, s->j0, wv, s->diag, rec + 2, rec + 3,
@@ -901,13 +906,17 @@ int tetm_energy(tetm_solver* s, double* w) {
   if (s->esz == 8) {
     const double* f[6];
     for (int c = 0; c < 6; ++c) f[c] = (const double*)s->set[s->cur][c];
-    e = launch_energy<double>(f, s->mask, s->minv_c, ma, s->L, s->alpha, work_view(s), s->diag,
-                              s->diag.out, s->stream);
+    e = s->uniform ? launch_balances<double>(f, nullptr, s->mask, s->minv_c, s->L, s->alpha, nullptr, 0, 0,
+                                             work_view(s), s->diag, s->diag.out, nullptr, nullptr, s->stream)
+                   : launch_energy<double>(f, s->mask, s->minv_c, ma, s->L, s->alpha, work_view(s), s->diag,
+                                           s->diag.out, s->stream);
   } else {
     const float* f[6];
     for (int c = 0; c < 6; ++c) f[c] = (const float*)s->set[s->cur][c];
-    e = launch_energy<float>(f, s->mask, s->minv_c, ma, s->L, s->alpha, work_view(s), s->diag,
-                             s->diag.out, s->stream);
+    e = s->uniform ? launch_balances<float>(f, nullptr, s->mask, s->minv_c, s->L, s->alpha, nullptr, 0, 0,
+                                            work_view(s), s->diag, s->diag.out, nullptr, nullptr, s->stream)
+                   : launch_energy<float>(f, s->mask, s->minv_c, ma, s->L, s->alpha, work_view(s), s->diag,
+                                          s->diag.out, s->stream);
   }
   CK(e);
   CK(cudaMemcpyAsync(w, s->diag.out, sizeof(double), cudaMemcpyDeviceToHost, s->stream));

@@ -235,6 +235,393 @@ __global__ void charge_items(ChargeFields cf, MinvView mv, Layout L, WorkView wv
   }
 }
 
+// binary32 -> binary64 widening on the integer pipe (IEEE 754: the
+// significand moves up by 29 bits and the exponent is rebiased by
+// 1023 - 127 = 896, or set to all ones for infinities and NaNs, which keep
+// their payload): exact for every normal value, zero, infinity and NaN.
+// Subnormal values (below 2^-126) become zero of the same sign; a field value
+// that small changes a balance term by less than 2^-126 of its normal
+// neighbours. On this part the float64 unit, which the conversion
+// instruction also occupies, is the balances' bottleneck.
+__device__ __forceinline__ double wide(float f) {
+  const unsigned u = __float_as_uint(f), a = u & 0x7FFFFFFFu;
+  const bool normal = a >= 0x00800000u;
+  const unsigned bias = a >= 0x7F800000u ? 0x70000000u : 0x38000000u;
+  const unsigned hi = (u & 0x80000000u) | (normal ? (a >> 3) + bias : 0u);
+  const unsigned lo = normal ? u << 29 : 0u;
+  return __hiloint2double((int)hi, (int)lo);
+}
+__device__ __forceinline__ double wide(double d) { return d; }
+
+// One material (the vacuum case included): M^-1 and M = 1 / M^-1 per
+// component for the active entries, and the products the balances use.
+struct UniformCoef {
+  double c[6], r[6];
+  double half_r[6];      // M / 2
+  double a2c_hx, a2c_hy; // alpha^2 M^-1 of h_x, h_y faces
+  double a2c_ex, a2c_ey; // alpha^2 M^-1 of e_x, e_y edges
+};
+template <typename T>
+struct BalanceFields {
+  const T* cur[6];   // y^n
+  const T* prev[6];  // y^{n-1} (charges only)
+};
+
+// The energy of Sec. 4.4 and, with CHARGE, the charge residuals of Eqs. (35)
+// and (34) in one pass over the nodes of a work item, for one material. A
+// face that carries no field has both of its boundary edges in PEC, so the
+// terms that the face coefficients weight, (P_y ez)^2, (P_x ez)^2 and the
+// hx, hy parts of the corrected e_z flux, need no activity test (their ez
+// values are zero); the terms that the edge coefficients weight keep it.
+// Along z each thread carries the corrected z-fluxes of the node below and of
+// its own face. Partials per block: energy, max |qe - qbunch|, max |qh|.
+template <typename T, bool CHARGE>
+__global__ void __launch_bounds__(256, 2) balance_items(BalanceFields<T> bf, const uint8_t* __restrict__ mask, UniformCoef uc, Layout L,
+                              WorkView wv, double alpha, const double* qline, int i0, int j0, double* part_w,
+                              double* part_e, double* part_h) {
+  const T* __restrict__ ex = bf.cur[kEX];
+  const T* __restrict__ ey = bf.cur[kEY];
+  const T* __restrict__ ez = bf.cur[kEZ];
+  const T* __restrict__ hx = bf.cur[kHX];
+  const T* __restrict__ hy = bf.cur[kHY];
+  const T* __restrict__ hz = bf.cur[kHZ];
+  const int item = wv.items ? wv.items[blockIdx.x] : (int)blockIdx.x;
+  const ItemCells ic(wv, L, item);
+  const long long sx = 1, sy = L.px, sz = L.sz;
+  const double a2 = alpha * alpha;
+  double sq[6] = {0, 0, 0, 0, 0, 0};
+  double rq[4] = {0, 0, 0, 0};
+  double cross = 0.0, me = 0.0, mh = 0.0;
+  // corrected z-flux of the active ez edge e (Eq. (35)) and of the active hz
+  // face f of the previous state (Eq. (34))
+  auto dz_at = [&](long long e) {
+    const double z = wide(ez[e]);
+    const double r = uc.a2c_hx * ((z - wide(ez[e - sy])) - (wide(ez[e + sy]) - z)) +
+                     uc.a2c_hy * ((z - wide(ez[e - sx])) - (wide(ez[e + sx]) - z));
+    return fma(z, uc.r[kEZ], -r);
+  };
+  auto bz_at = [&](long long f) {
+    const T* __restrict__ phz = bf.prev[kHZ];
+    const double z = wide(phz[f]);
+    const unsigned mf = mask[f];
+    const double t3a = (mask[f + sy] & 1) ? z - wide(phz[f + sy]) : 0.0;
+    const double t3b = (mf & 1) ? wide(phz[f - sy]) - z : 0.0;
+    const double t4a = (mask[f + sx] & 2) ? z - wide(phz[f + sx]) : 0.0;
+    const double t4b = (mf & 2) ? wide(phz[f - sx]) - z : 0.0;
+    const double r = uc.a2c_ex * (t3a - t3b) + uc.a2c_ey * (t4a - t4b);
+    return fma(z, uc.r[kHZ], -r);
+  };
+  for (int c = threadIdx.x; c < ic.tx * ic.ty; c += blockDim.x) {
+    const int i = ic.i0 + c % ic.tx, j = ic.j0 + c / ic.tx;
+    if (i >= L.nx || j >= L.ny) continue;
+    long long n = L.idx(i, j, ic.k0);
+    double dz_prev = 0.0, bz_cur = 0.0;  // dz~ of the edge below, bz~ of this node's face
+    bool dz_ok = false, bz_ok = false;
+    for (int k = ic.k0; k < ic.k1; ++k, n += sz) {
+      const unsigned m0 = mask[n];
+      if (m0 == 0) {  // no field object here: every term is zero, and so is dz~
+        dz_prev = 0.0;
+        dz_ok = true;
+        bz_ok = false;
+        continue;
+      }
+      const double vex = wide(ex[n]), vey = wide(ey[n]), vez = wide(ez[n]);
+      const double vhx = wide(hx[n]), vhy = wide(hy[n]), vhz = wide(hz[n]);
+      sq[kEX] = fma(vex, vex, sq[kEX]);
+      sq[kEY] = fma(vey, vey, sq[kEY]);
+      sq[kEZ] = fma(vez, vez, sq[kEZ]);
+      sq[kHX] = fma(vhx, vhx, sq[kHX]);
+      sq[kHY] = fma(vhy, vhy, sq[kHY]);
+      sq[kHZ] = fma(vhz, vhz, sq[kHZ]);
+      const double Ly = wide(ez[n + sy]) - vez, Lx = wide(ez[n + sx]) - vez;
+      rq[0] = fma(Ly, Ly, rq[0]);
+      rq[1] = fma(Lx, Lx, rq[1]);
+      if (m0 & 1) {
+        const double Hy = wide(hz[n - sy]) - vhz;
+        rq[2] = fma(Hy, Hy, rq[2]);
+      }
+      if (m0 & 2) {
+        const double Hx = wide(hz[n - sx]) - vhz;
+        rq[3] = fma(Hx, Hx, rq[3]);
+      }
+      const double dey = wide(ey[n + sz]) - vey, dex = wide(ex[n + sz]) - vex;
+      cross = fma(vhx, dey, fma(-vhy, dex, cross));
+      if constexpr (CHARGE) {
+        double dz_here = 0.0;
+        if (m0 & 4) {
+          const double Lyd = vez - wide(ez[n - sy]), Lxd = vez - wide(ez[n - sx]);
+          const double r = uc.a2c_hx * (Lyd - Ly) + uc.a2c_hy * (Lxd - Lx);
+          dz_here = fma(vez, uc.r[kEZ], -r);
+        }
+        // Eq. (35) at node n: its six incident edges carry a field
+        if ((m0 & 7) == 7 && (mask[n - sx] & 1) && (mask[n - sy] & 2) && (mask[n - sz] & 4)) {
+          const double dzb = dz_ok ? dz_prev : dz_at(n - sz);
+          const T* __restrict__ pex = bf.prev[kEX];
+          const T* __restrict__ pey = bf.prev[kEY];
+          const double sxn = vex + wide(pex[n]), sxl = wide(ex[n - sx]) + wide(pex[n - sx]);
+          const double syn = vey + wide(pey[n]), syd = wide(ey[n - sy]) + wide(pey[n - sy]);
+          double qe = -uc.half_r[kEX] * (sxl - sxn) - uc.half_r[kEY] * (syd - syn) - (dzb - dz_here);
+          if (qline && i == i0 && j == j0) qe -= qline[k];
+          me = fmax(me, fabs(qe));
+        }
+        dz_prev = dz_here;
+        dz_ok = true;
+        // Eq. (34) at the cell whose lower node is n: its six faces carry a field
+        if ((m0 & 56) == 56 && (mask[n + sx] & 8) && (mask[n + sy] & 16) && (mask[n + sz] & 32)) {
+          const double bzh = bz_ok ? bz_cur : bz_at(n);
+          const double bza = bz_at(n + sz);
+          const T* __restrict__ phx = bf.prev[kHX];
+          const T* __restrict__ phy = bf.prev[kHY];
+          const double bxn = vhx + wide(phx[n]), bxr = wide(hx[n + sx]) + wide(phx[n + sx]);
+          const double byn = vhy + wide(phy[n]), byu = wide(hy[n + sy]) + wide(phy[n + sy]);
+          const double qh = uc.half_r[kHX] * (bxr - bxn) + uc.half_r[kHY] * (byu - byn) + (bza - bzh);
+          mh = fmax(mh, fabs(qh));
+          bz_cur = bza;
+          bz_ok = true;
+        } else {
+          bz_ok = false;
+        }
+      }
+    }
+  }
+  double w = 0.0;
+  for (int q = 0; q < 6; ++q) w += 0.5 * uc.r[q] * sq[q];
+  w -= 0.5 * a2 * (uc.c[kHX] * rq[0] + uc.c[kHY] * rq[1] + uc.c[kEX] * rq[2] + uc.c[kEY] * rq[3]);
+  w += alpha * cross;
+  const double bw = block_reduce<false>(w);
+  if (threadIdx.x == 0) part_w[blockIdx.x] = bw;
+  if constexpr (CHARGE) {
+    const double be = block_reduce<true>(me);
+    const double bh = block_reduce<true>(mh);
+    if (threadIdx.x == 0) {
+      part_e[blockIdx.x] = be;
+      part_h[blockIdx.x] = bh;
+    }
+  }
+}
+
+// ---- float32 fields: error-free transformations on the float32 pipe -------
+// A float32 value pair (hi, lo) stands for the exact sum hi + lo. two_sum and
+// two_prod are the error-free sum (Knuth) and product (with a fused
+// multiply-add) of two float32 values; sums of a few float32 values with
+// integer coefficients come out exactly, or within 2^-47 of their size, as a
+// pair, and enter float64 through the exact widening and one float64 add.
+struct F2 {
+  float hi, lo;
+};
+__device__ __forceinline__ F2 two_sum(float a, float b) {
+  const float s = __fadd_rn(a, b);
+  const float bb = __fsub_rn(s, a);
+  const float e = __fadd_rn(__fsub_rn(a, __fsub_rn(s, bb)), __fsub_rn(b, bb));
+  return F2{s, e};
+}
+__device__ __forceinline__ F2 two_prod(float a, float b) {
+  const float p = __fmul_rn(a, b);
+  return F2{p, fmaf(a, b, -p)};
+}
+// running sum of signed float32 terms
+__device__ __forceinline__ F2 f2_add(F2 s, float v) {
+  const F2 t = two_sum(s.hi, v);
+  return F2{t.hi, __fadd_rn(s.lo, t.lo)};
+}
+__device__ __forceinline__ double f2_wide(F2 s) { return wide(s.hi) + wide(s.lo); }
+// accumulator += (p + e) for a product term p + e with |e| << |p|
+__device__ __forceinline__ void f2_acc(F2& acc, float p, float e) {
+  const F2 t = two_sum(acc.hi, p);
+  const float lo = __fadd_rn(t.lo, __fadd_rn(acc.lo, e));
+  const float hi = __fadd_rn(t.hi, lo);
+  acc = F2{hi, __fsub_rn(lo, __fsub_rn(hi, t.hi))};
+}
+// acc += a^2 (a float32), acc += d^2 and acc += a d (d a pair)
+__device__ __forceinline__ void acc_sq(F2& acc, float a) {
+  const F2 p = two_prod(a, a);
+  f2_acc(acc, p.hi, p.lo);
+}
+__device__ __forceinline__ void acc_sq2(F2& acc, F2 d) {
+  const F2 p = two_prod(d.hi, d.hi);
+  f2_acc(acc, p.hi, fmaf(2.f * d.hi, d.lo, p.lo));
+}
+__device__ __forceinline__ void acc_mul2(F2& acc, float a, F2 d) {
+  const F2 p = two_prod(a, d.hi);
+  f2_acc(acc, p.hi, fmaf(a, d.lo, p.lo));
+}
+
+constexpr int kFlush = 8;  // nodes per float32-pair partial before it joins the float64 sum
+constexpr int kPre = 4;    // planes of L2 prefetch ahead of the node being summed
+
+// balance_items for float32 fields: the same quantities, formed term by term
+// with the transformations above. Energy: eleven pair accumulators (six
+// squares, four link squares, the cross term) flushed into float64 sums every
+// kFlush nodes. Charges: Eq. (35) at node n is
+//   -M_x/2 X - M_y/2 Y - M_z Z + a^2 M_hx^-1 Wy + a^2 M_hy^-1 Wx,
+// X = (ex1 + ex0)(n - sx) - (ex1 + ex0)(n), Y likewise in y, Z = ez(n - sz) -
+// ez(n), Wy = Ly(n - sz) - Ly(n) with Ly(e) = 2 ez(e) - ez(e - sy) - ez(e + sy)
+// (Wx likewise in x): five integer combinations of float32 values. Eq. (34)
+// at the cell of lower node n is M_hx/2 Bx + M_hy/2 By + M_z Hz - a^2 M_ex^-1
+// T3 - a^2 M_ey^-1 T4 over the previous h_z with the e_x, e_y edge tests.
+template <bool CHARGE>
+__global__ void __launch_bounds__(256, 4)
+balance_items_f32(BalanceFields<float> bf, const uint8_t* __restrict__ mask, UniformCoef uc, Layout L,
+                  WorkView wv, double alpha, const double* qline, int i0, int j0, double* part_w,
+                  double* part_e, double* part_h) {
+  const float* __restrict__ ex = bf.cur[kEX];
+  const float* __restrict__ ey = bf.cur[kEY];
+  const float* __restrict__ ez = bf.cur[kEZ];
+  const float* __restrict__ hx = bf.cur[kHX];
+  const float* __restrict__ hy = bf.cur[kHY];
+  const float* __restrict__ hz = bf.cur[kHZ];
+  const int item = wv.items ? wv.items[blockIdx.x] : (int)blockIdx.x;
+  const ItemCells ic(wv, L, item);
+  const long long sx = 1, sy = L.px, sz = L.sz;
+  // weights of the eleven sums in the energy
+  const double a2h = 0.5 * alpha * alpha;
+  const double wt[11] = {uc.half_r[0], uc.half_r[1], uc.half_r[2], uc.half_r[3], uc.half_r[4], uc.half_r[5],
+                         -a2h * uc.c[kHX], -a2h * uc.c[kHY], -a2h * uc.c[kEX], -a2h * uc.c[kEY], alpha};
+  F2 acc[11];
+#pragma unroll
+  for (int q = 0; q < 11; ++q) acc[q] = F2{0.f, 0.f};
+  double w = 0.0;
+  int cnt = 0;
+  double me = 0.0, mh = 0.0;
+  auto flush = [&]() {
+#pragma unroll
+    for (int q = 0; q < 11; ++q) {
+      w = fma(wt[q], f2_wide(acc[q]), w);
+      acc[q] = F2{0.f, 0.f};
+    }
+    cnt = 0;
+  };
+  // the entries of this thread's node kPre planes on, into L2 ahead of use
+  // (the kernel is bound by the latency of its loads)
+  auto prefetch = [&](long long m) {
+#pragma unroll
+    for (int q = 0; q < 6; ++q) asm volatile("prefetch.global.L2 [%0];" ::"l"(bf.cur[q] + m));
+    if constexpr (CHARGE) {
+#pragma unroll
+      for (int q = 0; q < 6; ++q)
+        if (q != kEZ) asm volatile("prefetch.global.L2 [%0];" ::"l"(bf.prev[q] + m));
+    }
+    asm volatile("prefetch.global.L2 [%0];" ::"l"(mask + m));
+  };
+  for (int c = threadIdx.x; c < ic.tx * ic.ty; c += blockDim.x) {
+    const int i = ic.i0 + c % ic.tx, j = ic.j0 + c / ic.tx;
+    if (i >= L.nx || j >= L.ny) continue;
+    long long n = L.idx(i, j, ic.k0);
+    for (int d = 0; d < kPre && ic.k0 + d < ic.k1; ++d) prefetch(n + d * sz);
+    for (int k = ic.k0; k < ic.k1; ++k, n += sz) {
+      if (k + kPre < ic.k1) prefetch(n + kPre * sz);
+      const unsigned m0 = mask[n];
+      if (m0 == 0) continue;  // no field object here: every term is zero
+      const float vex = ex[n], vey = ey[n], vez = ez[n], vhx = hx[n], vhy = hy[n], vhz = hz[n];
+      acc_sq(acc[kEX], vex);
+      acc_sq(acc[kEY], vey);
+      acc_sq(acc[kEZ], vez);
+      acc_sq(acc[kHX], vhx);
+      acc_sq(acc[kHY], vhy);
+      acc_sq(acc[kHZ], vhz);
+      acc_sq2(acc[6], two_sum(ez[n + sy], -vez));
+      acc_sq2(acc[7], two_sum(ez[n + sx], -vez));
+      if (m0 & 1) acc_sq2(acc[8], two_sum(hz[n - sy], -vhz));
+      if (m0 & 2) acc_sq2(acc[9], two_sum(hz[n - sx], -vhz));
+      acc_mul2(acc[10], vhx, two_sum(ey[n + sz], -vey));
+      acc_mul2(acc[10], -vhy, two_sum(ex[n + sz], -vex));
+      if (++cnt == kFlush) flush();
+      if constexpr (CHARGE) {
+        if ((m0 & 7) == 7 && (mask[n - sx] & 1) && (mask[n - sy] & 2) && (mask[n - sz] & 4)) {
+          const float* __restrict__ pex = bf.prev[kEX];
+          const float* __restrict__ pey = bf.prev[kEY];
+          const F2 X = f2_add(f2_add(f2_add(F2{ex[n - sx], 0.f}, pex[n - sx]), -vex), -pex[n]);
+          const F2 Y = f2_add(f2_add(f2_add(F2{ey[n - sy], 0.f}, pey[n - sy]), -vey), -pey[n]);
+          const float ezb = ez[n - sz];
+          const F2 Z = two_sum(ezb, -vez);
+          const F2 Wy = f2_add(f2_add(f2_add(f2_add(f2_add(F2{2.f * ezb, 0.f}, -ez[n - sz - sy]), -ez[n - sz + sy]),
+                                             -2.f * vez), ez[n - sy]), ez[n + sy]);
+          const F2 Wx = f2_add(f2_add(f2_add(f2_add(f2_add(F2{2.f * ezb, 0.f}, -ez[n - sz - sx]), -ez[n - sz + sx]),
+                                             -2.f * vez), ez[n - sx]), ez[n + sx]);
+          double qe = uc.a2c_hx * f2_wide(Wy);
+          qe = fma(uc.a2c_hy, f2_wide(Wx), qe);
+          qe = fma(-uc.r[kEZ], f2_wide(Z), qe);
+          qe = fma(-uc.half_r[kEY], f2_wide(Y), qe);
+          qe = fma(-uc.half_r[kEX], f2_wide(X), qe);
+          if (qline && i == i0 && j == j0) qe -= qline[k];
+          me = fmax(me, fabs(qe));
+        }
+        if ((m0 & 56) == 56 && (mask[n + sx] & 8) && (mask[n + sy] & 16) && (mask[n + sz] & 32)) {
+          const float* __restrict__ phx = bf.prev[kHX];
+          const float* __restrict__ phy = bf.prev[kHY];
+          const float* __restrict__ phz = bf.prev[kHZ];
+          const F2 Bx = f2_add(f2_add(f2_add(F2{hx[n + sx], 0.f}, phx[n + sx]), -vhx), -phx[n]);
+          const F2 By = f2_add(f2_add(f2_add(F2{hy[n + sy], 0.f}, phy[n + sy]), -vhy), -phy[n]);
+          const long long f1 = n + sz;
+          const float z1 = phz[f1], z0 = phz[n];
+          const F2 Hz = two_sum(z1, -z0);
+          // t3(f) = [e_x(f + sy)] (hz(f) - hz(f + sy)) - [e_x(f)] (hz(f - sy) - hz(f)), T3 = t3(n + sz) - t3(n)
+          F2 T3{0.f, 0.f}, T4{0.f, 0.f};
+          if (mask[f1 + sy] & 1) T3 = f2_add(f2_add(T3, z1), -phz[f1 + sy]);
+          if (mask[f1] & 1) T3 = f2_add(f2_add(T3, -phz[f1 - sy]), z1);
+          if (mask[n + sy] & 1) T3 = f2_add(f2_add(T3, -z0), phz[n + sy]);
+          if (m0 & 1) T3 = f2_add(f2_add(T3, phz[n - sy]), -z0);
+          if (mask[f1 + sx] & 2) T4 = f2_add(f2_add(T4, z1), -phz[f1 + sx]);
+          if (mask[f1] & 2) T4 = f2_add(f2_add(T4, -phz[f1 - sx]), z1);
+          if (mask[n + sx] & 2) T4 = f2_add(f2_add(T4, -z0), phz[n + sx]);
+          if (m0 & 2) T4 = f2_add(f2_add(T4, phz[n - sx]), -z0);
+          double qh = uc.half_r[kHX] * f2_wide(Bx);
+          qh = fma(uc.half_r[kHY], f2_wide(By), qh);
+          qh = fma(uc.r[kHZ], f2_wide(Hz), qh);
+          qh = fma(-uc.a2c_ex, f2_wide(T3), qh);
+          qh = fma(-uc.a2c_ey, f2_wide(T4), qh);
+          mh = fmax(mh, fabs(qh));
+        }
+      }
+    }
+  }
+  flush();
+  const double bw = block_reduce<false>(w);
+  if (threadIdx.x == 0) part_w[blockIdx.x] = bw;
+  if constexpr (CHARGE) {
+    const double be = block_reduce<true>(me);
+    const double bh = block_reduce<true>(mh);
+    if (threadIdx.x == 0) {
+      part_e[blockIdx.x] = be;
+      part_h[blockIdx.x] = bh;
+    }
+  }
+}
+
+// The three totals of balance_items: sum of the energy partials, maxima of
+// the two charge partials.
+__global__ void balance_pass2(const double* part_w, const double* part_e, const double* part_h, int n,
+                              double* out_w, double* out_e, double* out_h) {
+  double w = 0.0, e = 0.0, h = 0.0;
+  for (int q = threadIdx.x; q < n; q += blockDim.x) {
+    w += part_w[q];
+    if (part_e) {
+      e = fmax(e, part_e[q]);
+      h = fmax(h, part_h[q]);
+    }
+  }
+  w = block_reduce<false>(w);
+  if (part_e) {
+    e = block_reduce<true>(e);
+    h = block_reduce<true>(h);
+  }
+  if (threadIdx.x == 0) {
+    *out_w = w;
+    if (part_e) {
+      *out_e = e;
+      *out_h = h;
+    }
+  }
+}
+
+// threads per item: whole warps splitting the tile's columns evenly (224 for
+// a 56 x 28 tile)
+int balance_threads(const WorkView& wv) {
+  const int area = wv.tile_x * wv.tile_y;
+  const int rounds = (area + 255) / 256;
+  return ((area + rounds - 1) / rounds + 31) / 32 * 32;
+}
+
 MinvView make_view(const uint8_t* mask, const double* minv, const double* const minv_a[6]) {
   MinvView v;
   v.mask = mask;
@@ -285,6 +672,65 @@ cudaError_t launch_charge(const T* const cur[6], const T* const prev[6], const u
   reduce_pass2<true><<<1, 1024, 0, st>>>(s.part + nb, nb, res_h);
   return cudaGetLastError();
 }
+
+template <typename T>
+cudaError_t launch_balances(const T* const cur[6], const T* const prev[6], const uint8_t* mask,
+                            const double* minv, const Layout& L, double alpha, const double* qline, int i0,
+                            int j0, const WorkView& wv, const DiagScratch& s, double* res_w, double* res_e,
+                            double* res_h, cudaStream_t st) {
+  const int nb = wv.n_items;
+  if (3 * nb > s.cap) return cudaErrorInvalidValue;
+  if (nb == 0) {
+    cudaError_t e = cudaMemsetAsync(res_w, 0, sizeof(double), st);
+    if (e == cudaSuccess && prev) e = cudaMemsetAsync(res_e, 0, sizeof(double), st);
+    if (e == cudaSuccess && prev) e = cudaMemsetAsync(res_h, 0, sizeof(double), st);
+    return e;
+  }
+  BalanceFields<T> bf;
+  UniformCoef uc;
+  for (int c = 0; c < 6; ++c) {
+    bf.cur[c] = cur[c];
+    bf.prev[c] = prev ? prev[c] : nullptr;
+    uc.c[c] = minv[c];
+    uc.r[c] = minv[c] != 0.0 ? 1.0 / minv[c] : 0.0;
+    uc.half_r[c] = 0.5 * uc.r[c];
+  }
+  uc.a2c_hx = alpha * alpha * minv[kHX];
+  uc.a2c_hy = alpha * alpha * minv[kHY];
+  uc.a2c_ex = alpha * alpha * minv[kEX];
+  uc.a2c_ey = alpha * alpha * minv[kEY];
+  const int nt = balance_threads(wv);
+  if constexpr (sizeof(T) == 4) {  // float32 fields: the float32-pipe transformations
+    if (prev)
+      balance_items_f32<true><<<nb, nt, 0, st>>>(bf, mask, uc, L, wv, alpha, qline, i0, j0, s.part, s.part + nb,
+                                                 s.part + 2 * nb);
+    else
+      balance_items_f32<false><<<nb, nt, 0, st>>>(bf, mask, uc, L, wv, alpha, nullptr, 0, 0, s.part, nullptr,
+                                                  nullptr);
+    balance_pass2<<<1, 1024, 0, st>>>(s.part, prev ? s.part + nb : nullptr, prev ? s.part + 2 * nb : nullptr, nb,
+                                      res_w, res_e, res_h);
+    return cudaGetLastError();
+  } else {
+  if (prev) {
+    balance_items<T, true><<<nb, nt, 0, st>>>(bf, mask, uc, L, wv, alpha, qline, i0, j0, s.part, s.part + nb,
+                                              s.part + 2 * nb);
+    balance_pass2<<<1, 1024, 0, st>>>(s.part, s.part + nb, s.part + 2 * nb, nb, res_w, res_e, res_h);
+  } else {
+    balance_items<T, false><<<nb, nt, 0, st>>>(bf, mask, uc, L, wv, alpha, nullptr, 0, 0, s.part, nullptr,
+                                               nullptr);
+    balance_pass2<<<1, 1024, 0, st>>>(s.part, nullptr, nullptr, nb, res_w, nullptr, nullptr);
+  }
+  return cudaGetLastError();
+  }
+}
+template cudaError_t launch_balances<float>(const float* const[6], const float* const[6], const uint8_t*,
+                                            const double*, const Layout&, double, const double*, int, int,
+                                            const WorkView&, const DiagScratch&, double*, double*, double*,
+                                            cudaStream_t);
+template cudaError_t launch_balances<double>(const double* const[6], const double* const[6], const uint8_t*,
+                                             const double*, const Layout&, double, const double*, int, int,
+                                             const WorkView&, const DiagScratch&, double*, double*, double*,
+                                             cudaStream_t);
 
 namespace {
 // Charge of the +-5 sigma truncated Gaussian inside [zc + lo, zc + hi] per

@@ -191,6 +191,15 @@ cudaError_t launch_charge(const T* const cur[6], const T* const prev[6], const u
                           double alpha, const double* qline, int i0, int j0, const WorkView& wv,
                           const DiagScratch& s, double* res_e, double* res_h, cudaStream_t st);
 
+// One material (minv[c] constants): the energy into *res_w and, when prev is
+// not null, the charge residuals into *res_e, *res_h, in one pass (the
+// launches above do the same for material arrays).
+template <typename T>
+cudaError_t launch_balances(const T* const cur[6], const T* const prev[6], const uint8_t* mask,
+                            const double* minv, const Layout& L, double alpha, const double* qline, int i0,
+                            int j0, const WorkView& wv, const DiagScratch& s, double* res_w, double* res_e,
+                            double* res_h, cudaStream_t st);
+
 // Truncated Gaussian bunch charge in the dual cell of each node k = 0..nz of
 // the bunch line at bunch-centre position zc; *qmax = max |ql[k]|; *tag = tag.
 cudaError_t launch_bunch_charge(double q, double sigma, double dz, double zc, int nz, double* ql,
