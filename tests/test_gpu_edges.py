@@ -53,24 +53,28 @@ def test_all_pec_box_has_no_work_and_no_field(tetm, precision):
     s.close()
 
 
-@pytest.mark.parametrize("precision,tol", [("fp32", 1e-4), ("fp64", 1e-11)])
+@pytest.mark.parametrize("precision,tol", [("fp32", 1e-4), ("fp64", 1e-12)])
 def test_short_bunch_on_the_first_node_line(tetm, precision, tol):
     """sigma = 0.15 dz (c0 = 1, a three-sample window) on node line (1, 1)."""
     s, o = run_both(tetm, 9, 7, 12, precision, 0.15 * wl.DZ, 1, 1, 30)
     info = o.bunch_info()
     assert info["c0"] == 1
-    assert wake_err(s, o) <= tol
+    err = wake_err(s, o)
+    print("wake error", precision, err)
+    assert err <= tol, err
     s.close()
 
 
-@pytest.mark.parametrize("precision,tol", [("fp32", 1e-4), ("fp64", 1e-11)])
+@pytest.mark.parametrize("precision,tol", [("fp32", 1e-4), ("fp64", 1e-12)])
 def test_window_longer_than_the_box(tetm, precision, tol):
     """sigma = 8 dz on a 12-cell box: the window (-41 .. 120) is far longer than
     the grid, most samples see no plane."""
     nx, ny, nz = 12, 12, 12
     s, o = run_both(tetm, nx, ny, nz, precision, 8 * wl.DZ, 6, 6, 200)
     assert len(s.wake()[0]) == len(o.wake()[0]) > 10 * nz
-    assert wake_err(s, o) <= tol
+    err = wake_err(s, o)
+    print("wake error", precision, err)
+    assert err <= tol, err
     s.close()
 
 

@@ -227,7 +227,9 @@ def test_full_size_chain_head_matches_oracle(tetm, precision, tol):
             assert not g[c][n + 2:].any(), (m, c)
         errs = family_errors({c: g[c][:n + 1] for c in g}, {c: o.get(c)[:n + 1] for c in g})
         assert max(errs.values()) <= tol, (m, errs)
-        assert rel(s.wake(m)[0], o.wake()[0]) <= (TOL32_WAKE if precision == "fp32" else 1e-11)
+        err = rel(s.wake(m)[0], o.wake()[0])
+        print("wake error", precision, m, err)
+        assert err <= (TOL32_WAKE if precision == "fp32" else 1e-12), (m, err)
 
 
 # ---------------------------------------------------------------------------

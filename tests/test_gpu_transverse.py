@@ -82,7 +82,9 @@ def test_transverse_wake_fp64_matches_oracle(tetm, kernel, tiling, obs):
     gx, gy = s.transverse_wake()
     assert rel_err(gx, rx) <= TOL64
     assert rel_err(gy, ry) <= TOL64
-    assert rel_err(s.wake()[0], rl) <= 1e-11
+    err = rel_err(s.wake()[0], rl)
+    print("wake error", kernel, tiling, obs, err)
+    assert err <= TOL64, err
 
 
 def test_transverse_wake_fp32_within_1e4(tetm):
@@ -137,7 +139,9 @@ def test_transverse_wake_static_start_matches_oracle(tetm):
     gx, gy = s.transverse_wake()
     assert rel_err(gx, rx) <= TOL64
     assert rel_err(gy, ry) <= TOL64
-    assert rel_err(s.wake()[0], rl) <= 1e-11
+    err = rel_err(s.wake()[0], rl)
+    print("wake error static", err)
+    assert err <= TOL64, err
 
 
 def test_batch_member_transverse_wake_equals_solo(tetm):
