@@ -301,6 +301,8 @@ def _load_rz():
     lib.rz_oracle_wake_extra.argtypes = [vp, i, vp, i]
     lib.rz_oracle_energy.restype = d
     lib.rz_oracle_energy.argtypes = [vp]
+    lib.rz_oracle_qbar_e.argtypes = [vp, vp, vp, vp, vp, vp, vp]
+    lib.rz_oracle_qbar_h.argtypes = [vp, vp, vp, vp, vp, vp, vp]
     lib.rz_oracle_get.argtypes = [vp, i, vp]
     lib.rz_oracle_set.argtypes = [vp, i, vp]
     lib.rz_oracle_coef.argtypes = [vp, i, vp]
@@ -410,6 +412,24 @@ class RzOracle:
 
     def energy(self):
         return float(self.lib.rz_oracle_energy(self.h))
+
+    def qbar_e(self, er1, er0, ephi1, ephi0, ez):
+        """Node charge of the mode (per radian) in the form of Eq. (35) for
+        scheme (24): e_r, e_phi at n+1 and n, e_z at n+1/2."""
+        arrs = [np.ascontiguousarray(a, dtype=np.float64).reshape(self.shape)
+                for a in (er1, er0, ephi1, ephi0, ez)]
+        q = np.empty(self.shape, dtype=np.float64)
+        self.lib.rz_oracle_qbar_e(self.h, *[_ptr(a) for a in arrs], _ptr(q))
+        return q
+
+    def qbar_h(self, hphi1, hphi0, hr1, hr0, hz):
+        """Cell charge of the mode (per radian, by lower node) in the form of
+        Eq. (34): h_phi, h_r at n+1/2 and n-1/2, h_z at n."""
+        arrs = [np.ascontiguousarray(a, dtype=np.float64).reshape(self.shape)
+                for a in (hphi1, hphi0, hr1, hr0, hz)]
+        q = np.empty(self.shape, dtype=np.float64)
+        self.lib.rz_oracle_qbar_h(self.h, *[_ptr(a) for a in arrs], _ptr(q))
+        return q
 
     def set_observer(self, obs):
         """Transverse wake at r_{obs+1/2} (before the first step)."""

@@ -322,6 +322,67 @@ double rz_oracle_energy(const rz_oracle_t *o) {
   return w - 0.5 * a * a * r + a * l;
 }
 
+/* Second-order charges of mode m (Sec. 4.5, the analogue of Eqs. (35) and
+ * (34) for the scheme of Eq. (24)). The discrete divergence of the mode
+ * annihilates the curl operators of (24): with the x-differences replaced by
+ * m it is -P_r^T d_r - m d_phi - P_z^T d_z at a node (electric) and
+ * m b_phi + P_r b_r + P_z b_z at a cell (magnetic), per radian. The split
+ * scheme conserves it with the transverse fluxes averaged over the two time
+ * levels and the z-fluxes corrected by the radial part of the splitting
+ * operator only (the m-part stays in B^{e,r}, Sec. 4.3):
+ *   qe = -P_r^T dr - m dphi - P_z^T dz~,  dr = M_er (er1 + er0)/2,
+ *        dphi = M_ephi (ephi1 + ephi0)/2,
+ *        dz~ = M_ez ez - alpha^2 P_r^T M_hphi^-1 P_r ez  (on non-PEC ez edges);
+ *   qh = m bphi + P_r br + P_z bz~,  bphi = M_hphi (hphi1 + hphi0)/2,
+ *        br = M_hr (hr1 + hr0)/2,
+ *        bz~ = M_hz hz - alpha^2 P_r M_ephi^-1 P_r^T hz  (on non-PEC hz faces).
+ * er1/ephi1 at time n+1 and er0/ephi0 at n with ez at n+1/2 (qe at
+ * n+1/2); hphi1/hr1 at n+1/2 and hphi0/hr0 at n-1/2 with hz at n (qh at n).
+ * q per node (electric) or per cell by its lower node (magnetic), canonical
+ * r-fastest layout. */
+static double PrT2(const rz_oracle_t *o, const double *v, long n) {
+  return (n % o->mr > 0 ? v[n - 1] : 0.0) - v[n];
+}
+static double Pr2(const rz_oracle_t *o, const double *v, long n) {
+  return (n % o->mr < o->nr ? v[n + 1] : 0.0) - v[n];
+}
+void rz_oracle_qbar_e(const rz_oracle_t *o, const double *er1, const double *er0, const double *ep1,
+                      const double *ep0, const double *ez, double *q) {
+  const long N = o->n;
+  const double a2 = o->at * o->at, m = (double)o->m;
+  double *dr = (double *)calloc((size_t)N, sizeof(double));
+  double *dp = (double *)calloc((size_t)N, sizeof(double));
+  double *dz = (double *)calloc((size_t)N, sizeof(double));
+  double *t = (double *)calloc((size_t)N, sizeof(double));
+  for (long n = 0; n < N; ++n) {
+    if (o->c[ER][n] != 0.0) dr[n] = 0.5 * (er1[n] + er0[n]) / o->c[ER][n];
+    if (o->c[EPHI][n] != 0.0) dp[n] = 0.5 * (ep1[n] + ep0[n]) / o->c[EPHI][n];
+    t[n] = o->c[HPHI][n] * Pr2(o, ez, n);
+  }
+  for (long n = 0; n < N; ++n)
+    if (o->c[EZ][n] != 0.0) dz[n] = ez[n] / o->c[EZ][n] - a2 * PrT2(o, t, n);
+  for (long n = 0; n < N; ++n) q[n] = -PrT2(o, dr, n) - m * dp[n] - PzT(o, dz, n);
+  free(dr); free(dp); free(dz); free(t);
+}
+void rz_oracle_qbar_h(const rz_oracle_t *o, const double *hp1, const double *hp0, const double *hr1,
+                      const double *hr0, const double *hz, double *q) {
+  const long N = o->n;
+  const double a2 = o->at * o->at, m = (double)o->m;
+  double *bp = (double *)calloc((size_t)N, sizeof(double));
+  double *br = (double *)calloc((size_t)N, sizeof(double));
+  double *bz = (double *)calloc((size_t)N, sizeof(double));
+  double *t = (double *)calloc((size_t)N, sizeof(double));
+  for (long n = 0; n < N; ++n) {
+    if (o->c[HPHI][n] != 0.0) bp[n] = 0.5 * (hp1[n] + hp0[n]) / o->c[HPHI][n];
+    if (o->c[HR][n] != 0.0) br[n] = 0.5 * (hr1[n] + hr0[n]) / o->c[HR][n];
+    t[n] = o->c[EPHI][n] * PrT2(o, hz, n);
+  }
+  for (long n = 0; n < N; ++n)
+    if (o->c[HZ][n] != 0.0) bz[n] = hz[n] / o->c[HZ][n] - a2 * Pr2(o, t, n);
+  for (long n = 0; n < N; ++n) q[n] = m * bp[n] + Pr2(o, br, n) + Pz(o, bz, n);
+  free(bp); free(br); free(bz); free(t);
+}
+
 void rz_oracle_get(const rz_oracle_t *o, int comp, double *out) {
   memcpy(out, o->f[comp], sizeof(double) * (size_t)o->n);
 }

@@ -288,55 +288,127 @@ def _node_charge_closed_form(q, sigma, dz, zc, k):
     return q * 0.5 * (math.erf(b / (sigma * math.sqrt(2))) - math.erf(a / (sigma * math.sqrt(2))))
 
 
-def _qbar_e(o, er1, er0, ez):
-    """Node charge per radian (m = 0) in the form of Eq. (35) with the radial
-    part of the splitting operator: -P_r^T d_r - P_z^T (M_eps_z e_z -
-    alpha^2 P_r^T M_mu_phi^-1 P_r e_z), d_r = M_eps_r (e_r^{n+1} + e_r^n)/2."""
-    c_er, c_ez, c_hp = o.coef("er"), o.coef("ez"), o.coef("hphi")
-    dr_ = np.where(c_er != 0, 0.5 * (er1 + er0) / np.where(c_er != 0, c_er, 1), 0.0)
-    pr_ez = np.zeros_like(ez)
-    pr_ez[:, :-1] = ez[:, 1:] - ez[:, :-1]
-    pr_ez[:, -1] = -ez[:, -1]
-    t = c_hp * pr_ez
-    prt_t = -t.copy()
-    prt_t[:, 1:] += t[:, :-1]
-    dzt = np.where(c_ez != 0, ez / np.where(c_ez != 0, c_ez, 1) - o.alpha ** 2 * prt_t, 0.0)
-
-    def ptr(v):
-        out = -v.copy()
-        out[:, 1:] += v[:, :-1]
-        return out
-
-    def ptz(v):
-        out = -v.copy()
-        out[1:, :] += v[:-1, :]
-        return out
-
-    return -ptr(dr_) - ptz(dzt)
+def _rz_interior_nodes(o):
+    """Nodes whose incident edges all carry a field: e_z below and above, e_r
+    outward and inward (the axis node has no inward e_r), e_phi for m >= 1."""
+    a = {c: o.coef(c) != 0 for c in NAMES}
+    ok = a["ez"].copy()
+    ok[1:, :] &= a["ez"][:-1, :]
+    ok[0, :] = False
+    ok &= a["er"]
+    inward = np.ones_like(ok)
+    inward[:, 1:] = a["er"][:, :-1]
+    ok &= inward
+    if o.m > 0:
+        ok &= a["ephi"]
+    return ok
 
 
-def test_gauss_law_for_the_bunch():
+def _rz_interior_cells(o):
+    """Cells (by lower node) whose faces all carry a field: h_z below and
+    above, h_r outward and inward (none on the axis), h_phi for m >= 1."""
+    a = {c: o.coef(c) != 0 for c in NAMES}
+    ok = a["hz"].copy()
+    ok[:-1, :] &= a["hz"][1:, :]
+    ok[-1, :] = False
+    outward = np.zeros_like(ok)
+    outward[:, :-1] = a["hr"][:, 1:]
+    ok &= outward
+    inward = a["hr"].copy()
+    inward[:, 0] = True
+    ok &= inward
+    if o.m > 0:
+        ok &= a["hphi"]
+    return ok
+
+
+@pytest.mark.parametrize("m", [0, 1, 2, 3])
+def test_rz_charges_with_random_fields_and_currents(m):
+    """The mode-m charges of the oracle (qbar_e, qbar_h) obey the discrete
+    charge laws of Sec. 4.5 for scheme (24): with a current j_z the node
+    charge changes by dt P_z^T j_z per step, the cell charge does not change;
+    on a pillbox between pipes, random fields (charges of the size of the
+    fluxes) and random currents."""
+    nr, nz = 12, 30
+    o = RzOracle(nr, nz, m, MM, MM, pec=_cavity_pec(nr, nz, 6, 10, 20))
+    _random_state(o, 40 + m)
+    rng = np.random.default_rng(50 + m)
+    jz = [rng.standard_normal(o.shape) * (o.coef("ez") != 0) for _ in range(3)]
+    hist = [o.fields()]
+    for n in range(3):
+        o.step_custom(jz[n])
+        hist.append(o.fields())
+    inode, icell = _rz_interior_nodes(o), _rz_interior_cells(o)
+    assert inode.sum() > 20 and icell.sum() > 20
+    qe = [o.qbar_e(hist[n + 1]["er"], hist[n]["er"], hist[n + 1]["ephi"], hist[n]["ephi"], hist[n + 1]["ez"])
+          for n in range(3)]
+    for n in (1, 2):
+        ptz = -jz[n]
+        ptz[1:, :] += jz[n][:-1, :]
+        res = (qe[n] - qe[n - 1]) - o.dt * ptz
+        assert np.max(np.abs(res[inode])) <= 1e-12 * np.max(np.abs(qe[n][inode]))
+    qh = [o.qbar_h(hist[n + 1]["hphi"], hist[n]["hphi"], hist[n + 1]["hr"], hist[n]["hr"], hist[n]["hz"])
+          for n in range(3)]
+    scale = np.max(np.abs(qh[0][icell]))
+    d_scale = np.max(np.abs(hist[0]["hz"] / np.where(o.coef("hz") != 0, o.coef("hz"), np.inf)))
+    assert scale > 0.1 * d_scale
+    for n in (1, 2):
+        assert np.max(np.abs(qh[n][icell] - qh[0][icell])) <= 1e-12 * scale
+
+
+@pytest.mark.parametrize("m", [1, 2])
+def test_rz_charge_keeps_the_m_part_out_of_the_z_flux(m):
+    """Reading of Sec. 4.3: the m-part of the splitting operator stays in
+    B^{e,r}, so the conserved z-flux is corrected by the radial part only.
+    Adding the m-part (alpha^2 m^2 M_hr^-1 e_z) to the corrected flux breaks
+    the conservation at O(1)."""
+    nr, nz = 12, 30
+    o = RzOracle(nr, nz, m, MM, MM, pec=_cavity_pec(nr, nz, 6, 10, 20))
+    _random_state(o, 60 + m)
+    hist = [o.fields()]
+    for n in range(3):
+        o.step(1)
+        hist.append(o.fields())
+    inode = _rz_interior_nodes(o)
+
+    def alt(n):
+        q = o.qbar_e(hist[n + 1]["er"], hist[n]["er"], hist[n + 1]["ephi"], hist[n]["ephi"], hist[n + 1]["ez"])
+        extra = o.alpha ** 2 * m * m * o.coef("hr") * hist[n + 1]["ez"] * (o.coef("ez") != 0)
+        ptz = -extra
+        ptz[1:, :] += extra[:-1, :]
+        return q - ptz, q
+    a0, q0 = alt(0)
+    a2, q2 = alt(2)
+    scale = np.max(np.abs(q0[inode]))
+    assert np.max(np.abs(q2[inode] - q0[inode])) <= 1e-12 * scale
+    assert np.max(np.abs(a2[inode] - a0[inode])) > 1e-3 * scale
+
+
+@pytest.mark.parametrize("m,i0", [(0, 0), (1, 3), (2, 3)])
+def test_gauss_law_for_the_bunch(m, i0):
+    """The node charge of the mode equals the bunch's share of the truncated
+    Gaussian's node charges on the ring: (2 - delta_m0)/(2 pi) per radian."""
     nr, nz = 10, 40
     q, sigma = 1e-9, 2.5 * MM
     pec = _cavity_pec(nr, nz, 5, 15, 25)
+    share = (1.0 if m == 0 else 2.0) / (2 * math.pi)
     for n in (6, 13, 20, 29):
-        o = RzOracle(nr, nz, 0, MM, MM, pec=pec)
-        o.set_bunch(sigma, q, 0)
+        o = RzOracle(nr, nz, m, MM, MM, pec=pec)
+        o.set_bunch(sigma, q, i0)
         c0 = math.ceil(5 * sigma / MM - 1e-12)
         o.step(n)
-        er0 = o.get("er")
+        er0, ep0 = o.get("er"), o.get("ephi")
         o.step(1)
-        qe = _qbar_e(o, o.get("er"), er0, o.get("ez"))
+        qe = o.qbar_e(o.get("er"), er0, o.get("ephi"), ep0, o.get("ez"))
         zc = (n + 0.5 - c0) * MM
         expect = np.zeros(o.shape)
         for k in range(1, nz):
-            expect[k, 0] = _node_charge_closed_form(q, sigma, MM, zc, k) / (2 * math.pi)
-        inner = np.zeros(o.shape, bool)
-        inner[1:nz, :] = True
-        inner &= np.abs(np.arange(nr + 1))[None, :] < 5   # nodes inside the pipe radius
+            expect[k, i0] = share * _node_charge_closed_form(q, sigma, MM, zc, k)
+        inner = _rz_interior_nodes(o)
+        assert inner[:, i0].sum() > nz // 2
         assert np.max(np.abs(qe[inner] - expect[inner])) <= 1e-12 * q
         if n >= 13:
-            assert np.max(np.abs(expect)) > 0.05 * q / (2 * math.pi)
+            assert np.max(np.abs(expect)) > 0.05 * share * q
 
 
 @pytest.mark.parametrize("m,i0", [(0, 0), (1, 3), (2, 4)])
