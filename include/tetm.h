@@ -276,7 +276,7 @@ int tetm_load(tetm_solver* s, const void* buf, size_t size);
  * for cudaMalloc/cudaFree or their implicit synchronisation.
  *
  * tetm_energy_noalloc computes the same discrete energy as tetm_energy
- * (W^{n,e}, Sec. 4.4) for a state the caller keeps in its own device arrays,
+ * for a state the caller keeps in its own device arrays,
  * and allocates nothing: no cudaMalloc, no cudaFree, no allocating library
  * call. Its block partial sums live in one fixed array of 8192 doubles
  * (64 KiB) in the library's device memory, which every GPU that loads the
@@ -291,10 +291,13 @@ int tetm_load(tetm_solver* s, const void* buf, size_t size);
  *   stream  cudaStream_t the two kernels are queued on (NULL = legacy stream);
  *           the call returns once they are queued and does not synchronize.
  * At most TETM_NOALLOC_MAX_ENTRIES canonical entries (e.g. 256 x 256 x 499
- * cells); larger grids return TETM_E_TOO_LARGE. The first call on a device
- * looks up the scratch array's device address (cudaGetSymbolAddress) with
- * that device current and caches it; make that first call before any stream
- * capture. Calls share the scratch array: calls whose kernels overlap on the
+ * cells); larger grids return TETM_E_TOO_LARGE; a grid that tetm_create
+ * would reject (non-finite or non-positive steps, cell counts out of range)
+ * returns TETM_E_ARG. The first call on a device, and in each further
+ * driver context a caller makes current on it, looks up the scratch array's
+ * device address (cudaGetSymbolAddress) with that device current and caches
+ * it; make that first call before any stream capture. Calls share the
+ * scratch array: calls whose kernels overlap on the
  * GPU (several streams or host threads at once) race and must be serialised
  * by the caller. */
 #define TETM_NOALLOC_MAX_ENTRIES 33554432
@@ -324,7 +327,11 @@ typedef struct tetm_batch tetm_batch;
 int tetm_batch_create(tetm_solver* const* solvers, const int64_t* step_limits, int32_t n,
                       int32_t graph_steps, tetm_batch** out);
 
-/* Queue nsteps batch steps; each member advances min(nsteps, limit - step). */
+/* Queue nsteps batch steps; each member advances min(nsteps, limit - step).
+ * If a launch fails (TETM_E_CUDA) the batch refuses further steps
+ * (TETM_E_STATE) and each member's step count and current field set are
+ * re-read from its device descriptor, so member reads see the steps the
+ * device did take. */
 int tetm_batch_step(tetm_batch* b, int32_t nsteps);
 
 /* Wait for the batch's stream (synchronizes). */

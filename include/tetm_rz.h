@@ -193,6 +193,44 @@ int tetm_rz_get_info(tetm_rz* s, tetm_rz_info* info);
  * Synchronizes; TETM_E_ARG for NULL arguments. */
 int tetm_rz_check_guards(tetm_rz* s, int64_t* violations);
 
+/* Charges of mode m_lo + mode in the discrete charge laws of Sec. 4.5 for
+ * scheme (24) (per radian; the x-differences of Eqs. (35), (34) become the
+ * multiplication by m): the node charge -P_r^T d_r - m d_phi - P_z^T d_z~
+ * with d_r, d_phi averaged over the last two states and d_z~ = M_ez e_z -
+ * alpha^2 P_r^T M_hphi^-1 P_r e_z (the m-part of the splitting operator stays
+ * in B^{e,r}, Sec. 4.3), against the bunch's share (2 - delta_m0)/(2 pi) of
+ * its node charges on the bunch ring; the cell charge m b_phi + P_r b_r +
+ * P_z b_z~ with b_z~ = M_hz h_z - alpha^2 P_r M_ephi^-1 P_r^T h_z of the
+ * previous state. *max_e = max |qe - qbunch| over nodes whose every edge
+ * carries a field, *max_h = max |qh| over such cells, *q_scale = the bunch
+ * share's largest node charge (0 without bunch); float64 on the device, on
+ * the total field in the scattered-field form. Needs the state one step
+ * before the current one (TETM_E_STATE after tetm_rz_set_fields,
+ * tetm_rz_load, before the first step, or after a two-step pass of
+ * TETM_RZ_KERNEL_BULK2; a last single step makes it available).
+ * Synchronizes. */
+int tetm_rz_charge_residual(tetm_rz* s, int32_t mode, double* max_e, double* max_h, double* q_scale);
+
+/* Periodic balances: after every step n with n % every == 0 the energy and
+ * the charges of every mode are queued into a device history without host
+ * synchronisation (every = 0 turns them off); the two-step kernel takes a
+ * single step into each such n. tetm_rz_balance_history copies the last
+ * records (up to 1024 steps) into out: rows of six doubles {n, m, energy,
+ * max_e, max_h, q_scale}, one row per mode and step, oldest first;
+ * *n_out = rows (out may be NULL to query it; cap counts rows). Synchronizes. */
+int tetm_rz_set_balance_every(tetm_rz* s, int32_t every);
+int tetm_rz_balance_history(tetm_rz* s, double* out, int32_t cap, int32_t* n_out);
+
+/* Checkpoint: tetm_rz_save writes the solve's current state (every mode, the
+ * device layout), step and wake accumulators into a caller buffer of cap
+ * bytes; *used receives the size (buf may be NULL to query it). tetm_rz_load
+ * restores it into a solve created with the same grid, modes and geometry and
+ * given the same bunch call (tetm_rz_set_bunch, _static or _scattered with the
+ * same arguments; TETM_E_ARG on any mismatch). A run continued from a
+ * checkpoint is bitwise the run without the split. Both synchronize. */
+int tetm_rz_save(tetm_rz* s, void* buf, size_t cap, size_t* used);
+int tetm_rz_load(tetm_rz* s, const void* buf, size_t size);
+
 /* Device bytes tetm_rz_create would allocate for g (0 for a bad grid). */
 int64_t tetm_rz_bytes_needed(const tetm_rz_grid* g);
 

@@ -29,6 +29,7 @@ struct tetm_batch {
   cudaGraph_t graph;
   cudaGraphExec_t exec;
   bool warmed;                    // one uncaptured launch done (launch set-up outside capture)
+  bool failed;                    // a launch failed: no further steps (members resynchronised)
 };
 
 namespace {
@@ -72,6 +73,35 @@ cudaError_t launch_one(tetm_batch* b) {
 
 cudaError_t launch_one_any(tetm_batch* b) {
   return b->esz == 8 ? launch_one<double>(b) : launch_one<float>(b);
+}
+
+// After a failed launch the members' host bookkeeping (step, current field
+// set) may lag the device, where some launches did advance them: read each
+// member's descriptor back and take its step and current set from there.
+template <typename T>
+void resync_members(tetm_batch* b) {
+  cudaGetLastError();
+  const size_t n = b->members.size();
+  std::vector<BatchMember<T>> h(n);
+  if (cudaStreamSynchronize(b->stream) != cudaSuccess ||
+      cudaMemcpy(h.data(), b->d_members, sizeof(BatchMember<T>) * n, cudaMemcpyDeviceToHost) != cudaSuccess) {
+    cudaGetLastError();
+    return;  // the context is lost: nothing on the device can be read
+  }
+  for (size_t i = 0; i < n; ++i) {
+    tetm_solver* s = b->members[i];
+    if (h[i].a.n != s->step) s->prev_valid = true;
+    s->step = h[i].a.n;
+    s->cur = (const void*)h[i].a.in[0] == s->set[1][0] ? 1 : 0;
+  }
+}
+int batch_fail(tetm_batch* b) {
+  b->failed = true;
+  if (b->esz == 8)
+    resync_members<double>(b);
+  else
+    resync_members<float>(b);
+  return TETM_E_CUDA;
 }
 
 void release(tetm_batch* b) {
@@ -141,29 +171,30 @@ int tetm_batch_create(tetm_solver* const* solvers, const int64_t* step_limits, i
 
 static int batch_step_impl(tetm_batch* b, int32_t nsteps) {
   if (!b || nsteps < 0) return TETM_E_ARG;
+  if (b->failed) return TETM_E_STATE;
   int left = nsteps;
   if (left > 0 && !b->warmed) {  // first launch outside any capture (one-time launch set-up)
-    if (launch_one_any(b) != cudaSuccess) return TETM_E_CUDA;
+    if (launch_one_any(b) != cudaSuccess) return batch_fail(b);
     b->warmed = true;
     --left;
   }
   if (b->graph_steps > 0 && left >= b->graph_steps) {
     if (!b->exec) {
       if (cudaStreamBeginCapture(b->stream, cudaStreamCaptureModeThreadLocal) != cudaSuccess)
-        return TETM_E_CUDA;
+        return batch_fail(b);
       cudaError_t e = cudaSuccess;
       for (int q = 0; q < b->graph_steps && e == cudaSuccess; ++q) e = launch_one_any(b);
       cudaError_t e2 = cudaStreamEndCapture(b->stream, &b->graph);
-      if (e != cudaSuccess || e2 != cudaSuccess) return TETM_E_CUDA;
-      if (cudaGraphInstantiate(&b->exec, b->graph, 0) != cudaSuccess) return TETM_E_CUDA;
+      if (e != cudaSuccess || e2 != cudaSuccess) return batch_fail(b);
+      if (cudaGraphInstantiate(&b->exec, b->graph, 0) != cudaSuccess) return batch_fail(b);
     }
     while (left >= b->graph_steps) {
-      if (cudaGraphLaunch(b->exec, b->stream) != cudaSuccess) return TETM_E_CUDA;
+      if (cudaGraphLaunch(b->exec, b->stream) != cudaSuccess) return batch_fail(b);
       left -= b->graph_steps;
     }
   }
   for (; left > 0; --left)
-    if (launch_one_any(b) != cudaSuccess) return TETM_E_CUDA;
+    if (launch_one_any(b) != cudaSuccess) return batch_fail(b);
   // mirror the device-side advance in the members' host bookkeeping
   for (size_t i = 0; i < b->members.size(); ++i) {
     tetm_solver* s = b->members[i];

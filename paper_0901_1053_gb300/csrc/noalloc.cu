@@ -5,6 +5,9 @@
 // synchronisation are not allowed). The caller passes its own device arrays
 // for the state and for the result; the block partial sums live in a fixed
 // file-scope device array instead of solver-owned scratch.
+#include <cuda.h>
+#include <math.h>
+
 #include <mutex>
 
 #include "tetm_internal.h"
@@ -21,9 +24,36 @@ constexpr int kNaMaxPartials = TETM_NOALLOC_MAX_ENTRIES / (kNaBlock * kNaPerThre
 // writes every slot it later reads, so nothing needs clearing between calls.
 static __device__ __align__(256) double g_noalloc_partials[kNaMaxPartials];
 
-constexpr int kMaxDevices = 64;
+// The array's device address depends on the context the library's module
+// is loaded in: a caller on its own driver context sees another address than
+// the runtime's primary context of the same device. The address is resolved
+// once per (device, context) pair and cached.
+constexpr int kMaxDevices = 64, kCtxPerDevice = 8;
 std::mutex g_setup_mu;
-double* g_partials_addr[kMaxDevices];  // device address of the array, per device
+struct CtxAddr {
+  void* ctx;
+  double* addr;
+};
+CtxAddr g_partials_addr[kMaxDevices][kCtxPerDevice];
+
+// the calling thread's current driver context (nullptr when the driver entry
+// point is not available: every call then shares one cache slot per device)
+void* current_context() {
+  using GetCtx = CUresult (*)(CUcontext*);
+  static GetCtx fn = nullptr;
+  static bool looked = false;
+  if (!looked) {
+    void* p = nullptr;
+    cudaDriverEntryPointQueryResult q;
+    if (cudaGetDriverEntryPointByVersion("cuCtxGetCurrent", &p, 12000, cudaEnableDefault, &q) == cudaSuccess &&
+        q == cudaDriverEntryPointSuccess)
+      fn = reinterpret_cast<GetCtx>(p);
+    looked = true;
+  }
+  CUcontext c = nullptr;
+  if (fn && fn(&c) != CUDA_SUCCESS) c = nullptr;
+  return c;
+}
 
 __device__ __forceinline__ double na_warp_sum(double v) {
   for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(0xffffffffu, v, o);
@@ -118,25 +148,35 @@ __global__ void na_energy_pass2(const double* part, int np, double* out) {
   if (threadIdx.x == 0) *out = v;
 }
 
-// Device address of the scratch array on the current device; resolved once
-// per device (first call on that device) and cached.
+// Device address of the scratch array for the current device and context;
+// resolved by the first call in that context (with that device current) and
+// cached. A device with more than kCtxPerDevice contexts resolves it on every
+// call in the contexts beyond those (cudaGetSymbolAddress allocates nothing).
 int partials_on_current_device(double** out) {
   int dev = -1;
   if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= kMaxDevices) {
     cudaGetLastError();
     return TETM_E_CUDA;
   }
+  void* ctx = current_context();
   std::lock_guard<std::mutex> lk(g_setup_mu);
-  if (!g_partials_addr[dev]) {
-    void* p = nullptr;
-    const cudaError_t e = cudaGetSymbolAddress(&p, g_noalloc_partials);
-    if (e != cudaSuccess || !p) {
-      cudaGetLastError();
-      return TETM_E_CUDA;
+  CtxAddr* slots = g_partials_addr[dev];
+  int free_slot = -1;
+  for (int q = 0; q < kCtxPerDevice; ++q) {
+    if (slots[q].addr && slots[q].ctx == ctx) {
+      *out = slots[q].addr;
+      return TETM_OK;
     }
-    g_partials_addr[dev] = (double*)p;
+    if (!slots[q].addr && free_slot < 0) free_slot = q;
   }
-  *out = g_partials_addr[dev];
+  void* p = nullptr;
+  const cudaError_t e = cudaGetSymbolAddress(&p, g_noalloc_partials);
+  if (e != cudaSuccess || !p) {
+    cudaGetLastError();
+    return TETM_E_CUDA;
+  }
+  if (free_slot >= 0) slots[free_slot] = CtxAddr{ctx, (double*)p};
+  *out = (double*)p;
   return TETM_OK;
 }
 
@@ -147,13 +187,17 @@ using namespace tetm;
 
 extern "C" int tetm_energy_noalloc(const tetm_grid* g, const void* const fields[6],
                                    const uint8_t* mask, double* w, void* stream) {
+  // the checks of tetm_create's grid (finite, positive steps, cell counts in
+  // range), then the size limit of the scratch array
   if (!g || !fields || !w || g->nx < 2 || g->ny < 2 || g->nz < 2 || !(g->dx > 0) ||
-      !(g->dy > 0) || !(g->dz > 0) || g->cdt < 0 ||
-      (g->precision != TETM_FP64 && g->precision != TETM_FP32))
+      !(g->dy > 0) || !(g->dz > 0) || !(g->cdt >= 0) || !isfinite(g->dx) || !isfinite(g->dy) ||
+      !isfinite(g->dz) || !isfinite(g->cdt) || (g->precision != TETM_FP64 && g->precision != TETM_FP32) ||
+      (long long)g->nx * g->ny >= (1LL << 31) ||
+      ((long long)g->nx + 1) * ((long long)g->ny + 1) * ((long long)g->nz + 1) >= (1LL << 40))
     return TETM_E_ARG;
   for (int c = 0; c < 6; ++c)
     if (!fields[c]) return TETM_E_ARG;
-  const long long n = (long long)(g->nx + 1) * (g->ny + 1) * (g->nz + 1);
+  const long long n = ((long long)g->nx + 1) * ((long long)g->ny + 1) * ((long long)g->nz + 1);
   if (n > (long long)TETM_NOALLOC_MAX_ENTRIES) return TETM_E_TOO_LARGE;
   double* part = nullptr;
   int rc = partials_on_current_device(&part);
@@ -166,8 +210,8 @@ extern "C" int tetm_energy_noalloc(const tetm_grid* g, const void* const fields[
   a.nz = g->nz;
   a.n = n;
   a.sx = 1;
-  a.sy = g->nx + 1;
-  a.sz = (long long)(g->nx + 1) * (g->ny + 1);
+  a.sy = (long long)g->nx + 1;
+  a.sz = ((long long)g->nx + 1) * ((long long)g->ny + 1);
   const double dx = g->dx, dy = g->dy, dz = g->dz;
   a.minv[kEX] = dx / (kEps0 * dy * dz);
   a.minv[kEY] = dy / (kEps0 * dx * dz);

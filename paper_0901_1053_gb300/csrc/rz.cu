@@ -34,6 +34,7 @@
 #include <math.h>
 
 #include <algorithm>
+#include <cstring>
 #include <new>
 #include <vector>
 
@@ -1195,6 +1196,7 @@ __global__ void rz_from_canonical(const double* src, RzLayout L, const uint8_t* 
 // (zero where the mode has no object). One partial per block.
 constexpr int kEnergyBlocks = 512;
 constexpr int kEnergyThreads = 256;
+constexpr int kRzRec = 6;  // balance record: step, mode, energy, max |qe - qbunch|, max |qh|, bunch charge scale
 
 template <typename T>
 __global__ void __launch_bounds__(kEnergyThreads)
@@ -1245,6 +1247,119 @@ __global__ void rz_energy_final(const double* partial, int n, double* out) {
   for (int q = threadIdx.x; q < n; q += 32) v += partial[q];
   for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(0xffffffffu, v, o);
   if (threadIdx.x == 0) *out = v;
+}
+
+// Charges of mode m (the analogue of Eqs. (35) and (34) for scheme (24)):
+// at node (i, k), qe = -P_r^T dr - m dphi - P_z^T dz~ with dr, dphi the e_r,
+// e_phi fluxes averaged over the two states and dz~ = M_ez ez - alpha^2
+// P_r^T M_hphi^-1 P_r ez; at the cell of lower node (i, k), qh = m bphi +
+// P_r br + P_z bz~ with bz~ = M_hz hz - alpha^2 P_r M_ephi^-1 P_r^T hz of the
+// previous state (the m-part of the splitting operator stays in B^{e,r}). A
+// node (cell) counts when every edge (face) it touches carries a field; at
+// the bunch ring the node charge is compared with the bunch's share of the
+// node charge qline. fc, fp: the current and the previous state (the
+// incident field added in the scattered-field form). One max per block.
+template <typename T>
+__global__ void __launch_bounds__(kEnergyThreads)
+rz_charge_partial(const T* fc, const T* fp, RzLayout L, int mode, double mm, const uint8_t* mask,
+                  const double* metric, double a2, RzIncident xc, RzIncident xp, const double* qline,
+                  double share, int i0, double* part_e, double* part_h) {
+  const long long PR = L.pr;
+  const long long n = (long long)(L.nr + 1) * (L.nz + 1);
+  double me = 0.0, mh = 0.0;
+  for (long long q = (long long)blockIdx.x * blockDim.x + threadIdx.x; q < n;
+       q += (long long)gridDim.x * blockDim.x) {
+    const int i = (int)(q % (L.nr + 1)), k = (int)(q / (L.nr + 1));
+    auto C = [&](int comp, int ii, int kk) -> double {  // M^-1 of the entry, 0 where it has no object
+      if (ii < 0 || ii > L.nr || kk < -1 || kk > L.nz + 1) return 0.0;
+      return ((mask[L.midx(ii, kk)] >> comp) & 1) ? metric[comp * PR + ii] : 0.0;
+    };
+    auto vc = [&](int comp, int ii, int kk) {
+      return (double)fc[L.fidx(mode, comp, ii, kk)] + inc_value(xc, mode, comp, ii, kk);
+    };
+    auto vp = [&](int comp, int ii, int kk) {
+      return (double)fp[L.fidx(mode, comp, ii, kk)] + inc_value(xp, mode, comp, ii, kk);
+    };
+    // Eq. (35) at node (i, k)
+    const double cep = C(kEP, i, k);
+    if (C(kEZ, i, k) != 0.0 && C(kEZ, i, k - 1) != 0.0 && C(kER, i, k) != 0.0 &&
+        (i == 0 || C(kER, i - 1, k) != 0.0) && (mm == 0.0 || cep != 0.0)) {
+      auto dr = [&](int ii) {
+        const double c = C(kER, ii, k);
+        return c != 0.0 ? 0.5 * (vc(kER, ii, k) + vp(kER, ii, k)) / c : 0.0;
+      };
+      auto dzt = [&](int kk) {
+        const double z = vc(kEZ, i, kk), zl = vc(kEZ, i - 1, kk), zr = vc(kEZ, i + 1, kk);
+        const double r = (i > 0 ? C(kHP, i - 1, kk) * (z - zl) : 0.0) - C(kHP, i, kk) * (zr - z);
+        return z / C(kEZ, i, kk) - a2 * r;
+      };
+      const double dp = cep != 0.0 ? 0.5 * (vc(kEP, i, k) + vp(kEP, i, k)) / cep : 0.0;
+      double qe = -((i > 0 ? dr(i - 1) : 0.0) - dr(i)) - mm * dp - (dzt(k - 1) - dzt(k));
+      if (qline && i == i0) qe -= share * qline[k];
+      me = fmax(me, fabs(qe));
+    }
+    // Eq. (34) at the cell of lower node (i, k)
+    const double chp = C(kHP, i, k);
+    if (C(kHZ, i, k) != 0.0 && C(kHZ, i, k + 1) != 0.0 && C(kHR, i + 1, k) != 0.0 &&
+        (i == 0 || C(kHR, i, k) != 0.0) && (mm == 0.0 || chp != 0.0)) {
+      auto br = [&](int ii) {
+        const double c = C(kHR, ii, k);
+        return c != 0.0 ? 0.5 * (vc(kHR, ii, k) + vp(kHR, ii, k)) / c : 0.0;
+      };
+      auto bzt = [&](int kk) {
+        const double z = vp(kHZ, i, kk), zl = vp(kHZ, i - 1, kk), zr = vp(kHZ, i + 1, kk);
+        const double r = C(kEP, i + 1, kk) * (z - zr) - C(kEP, i, kk) * (zl - z);
+        return z / C(kHZ, i, kk) - a2 * r;
+      };
+      const double bp = chp != 0.0 ? 0.5 * (vc(kHP, i, k) + vp(kHP, i, k)) / chp : 0.0;
+      const double qh = mm * bp + (br(i + 1) - br(i)) + (bzt(k + 1) - bzt(k));
+      mh = fmax(mh, fabs(qh));
+    }
+  }
+  __shared__ double sh[2][kEnergyThreads / 32];
+  for (int o = 16; o > 0; o >>= 1) {
+    me = fmax(me, __shfl_down_sync(0xffffffffu, me, o));
+    mh = fmax(mh, __shfl_down_sync(0xffffffffu, mh, o));
+  }
+  if ((threadIdx.x & 31) == 0) {
+    sh[0][threadIdx.x >> 5] = me;
+    sh[1][threadIdx.x >> 5] = mh;
+  }
+  __syncthreads();
+  if (threadIdx.x < 32) {
+    double a = threadIdx.x < kEnergyThreads / 32 ? sh[0][threadIdx.x] : 0.0;
+    double b = threadIdx.x < kEnergyThreads / 32 ? sh[1][threadIdx.x] : 0.0;
+    for (int o = 16; o > 0; o >>= 1) {
+      a = fmax(a, __shfl_down_sync(0xffffffffu, a, o));
+      b = fmax(b, __shfl_down_sync(0xffffffffu, b, o));
+    }
+    if (threadIdx.x == 0) {
+      part_e[blockIdx.x] = a;
+      part_h[blockIdx.x] = b;
+    }
+  }
+}
+
+// the maxima of the charge partials and the record's step, mode and charge
+// scale: rec = {n, m, W (written before), max_e, max_h, share * qmax}
+__global__ void rz_balance_record(const double* part_e, const double* part_h, int nblocks, double n, double m,
+                                  double share, const double* qmax, double* rec) {
+  double a = 0.0, b = 0.0;
+  for (int q = threadIdx.x; q < nblocks; q += 32) {
+    a = fmax(a, part_e[q]);
+    b = fmax(b, part_h[q]);
+  }
+  for (int o = 16; o > 0; o >>= 1) {
+    a = fmax(a, __shfl_down_sync(0xffffffffu, a, o));
+    b = fmax(b, __shfl_down_sync(0xffffffffu, b, o));
+  }
+  if (threadIdx.x == 0) {
+    rec[0] = n;
+    rec[1] = m;
+    rec[3] = a;
+    rec[4] = b;
+    rec[5] = qmax ? share * *qmax : 0.0;
+  }
 }
 
 // Static start: number of activity bytes of rows 2..K that differ from row 1
@@ -1362,6 +1477,14 @@ struct tetm_rz {
   long long sc_off = 0;          // source window: planes n + sc_off .. + sc_len - 1
   int sc_len = 0;
   int s_tiles = 0;               // radial tiles (of 60 entries) the source covers
+  // balances (energy of Sec. 4.4, charges of Sec. 4.5) of every mode
+  bool prev_valid = false;       // set[cur ^ 1] holds the state one step before set[cur]
+  int bal_every = 0;
+  double* hist = nullptr;        // [hist_cap][n_modes][kRzRec] records
+  int hist_cap = 0;
+  long long hist_count = 0;
+  double* cpart = nullptr;       // charge partials [2][kEnergyBlocks], the bunch line [nz + 1] and its max
+  double* rec1 = nullptr;        // [n_modes][kRzRec]: the records of tetm_rz_charge_residual
 };
 
 namespace {
@@ -1400,6 +1523,42 @@ cudaError_t rz_launch_source(tetm_rz* s, int n_steps) {
   rz_source_kernel<T><<<blocks, 128, 0, s->st>>>(a, rz_incident(s, s->step), s->differs, s->s_tiles,
                                                   kSourcePlanes, n_groups, n_steps, static_cast<T*>(s->S));
   return cudaGetLastError();
+}
+
+// Queues the balances of every mode for the state just reached into rec
+// (kRzRec doubles per mode): energy, charges against the bunch (its node
+// charges for the centre of the last step, as in the Cartesian solver).
+template <typename T>
+int rz_queue_balances(tetm_rz* s, double* rec) {
+  if (!s->cpart) {
+    cudaError_t e = cudaMalloc(&s->cpart, sizeof(double) * (2 * kEnergyBlocks + s->g.nz + 2));
+    if (e != cudaSuccess) return rz_fail(e);
+  }
+  double* pe = s->cpart;
+  double* ph = s->cpart + kEnergyBlocks;
+  double* ql = s->cpart + 2 * kEnergyBlocks;
+  double* qmax = ql + s->g.nz + 1;
+  const double zc = ((double)(s->step + s->kshift - 1) + 0.5 - s->c0) * s->g.dz;
+  cudaError_t e = tetm::launch_bunch_charge(s->bunch ? s->q : 0.0, s->bunch ? s->sigma : 1.0, s->g.dz, zc, s->g.nz, ql,
+                                      qmax, 0.0, nullptr, s->st);
+  const T* fc = static_cast<const T*>(s->set[s->cur]);
+  const T* fp = static_cast<const T*>(s->set[s->cur ^ 1]);
+  for (int mi = 0; mi < s->n_modes && e == cudaSuccess; ++mi) {
+    const int m = s->g.m_lo + mi;
+    const double share = (m == 0 ? 1.0 : 2.0) / (2.0 * kPi);
+    double* r = rec + (size_t)mi * kRzRec;
+    const double* me = s->metric + (size_t)mi * 6 * s->L.pr + s->L.orr;
+    rz_energy_partial<T><<<kEnergyBlocks, kEnergyThreads, 0, s->st>>>(fc, s->L, mi, s->mask, me, s->alpha,
+                                                                       s->partial, rz_incident(s, s->step));
+    rz_energy_final<<<1, 32, 0, s->st>>>(s->partial, kEnergyBlocks, r + 2);
+    rz_charge_partial<T><<<kEnergyBlocks, kEnergyThreads, 0, s->st>>>(
+        fc, fp, s->L, mi, (double)m, s->mask, me, s->alpha * s->alpha, rz_incident(s, s->step),
+        rz_incident(s, s->step - 1), s->bunch ? ql : nullptr, share, s->i0, pe, ph);
+    rz_balance_record<<<1, 32, 0, s->st>>>(pe, ph, kEnergyBlocks, (double)s->step, (double)m, share,
+                                           s->bunch ? qmax : nullptr, r);
+    e = cudaGetLastError();
+  }
+  return e == cudaSuccess ? TETM_OK : rz_fail(e);
 }
 
 template <typename T>
@@ -1462,7 +1621,12 @@ int rz_launch_steps(tetm_rz* s, long long n) {
     a.in = static_cast<const T*>(s->set[s->cur]);
     a.out = static_cast<T*>(s->set[s->cur ^ 1]);
     a.n = s->step;
-    const int p = (s->kernel == TETM_RZ_KERNEL_BULK2 && t + 1 < n) ? 2 : 1;  // steps in this pass
+    // steps in this pass: two with the two-step kernel, except past or into
+    // a step that carries balances (they need the state one step before it)
+    int p = (s->kernel == TETM_RZ_KERNEL_BULK2 && t + 1 < n) ? 2 : 1;
+    if (p == 2 && s->bal_every > 0 &&
+        ((s->step + 1) % s->bal_every == 0 || (s->step + 2) % s->bal_every == 0))
+      p = 1;
     a.sc_lo = a.sc_hi = 0;
     if (s->scattered) {
       if (s->step + p > s->sc_until) {
@@ -1510,7 +1674,14 @@ int rz_launch_steps(tetm_rz* s, long long n) {
     }
     s->cur ^= 1;
     s->step += p;
+    s->prev_valid = p == 1;
     t += p - 1;
+    if (s->bal_every > 0 && s->step % s->bal_every == 0) {
+      double* rec = s->hist + (size_t)(s->hist_count % s->hist_cap) * s->n_modes * kRzRec;
+      const int rc = rz_queue_balances<T>(s, rec);
+      if (rc) return rc;
+      s->hist_count += 1;
+    }
   }
   return TETM_OK;
 }
@@ -2163,6 +2334,7 @@ int tetm_rz_set_fields(tetm_rz* s, int32_t mode, int32_t comp, const double* in)
   }
   cudaFreeAsync(tmp, s->st);
   if (e == cudaSuccess) e = cudaStreamSynchronize(s->st);
+  s->prev_valid = false;
   return e == cudaSuccess ? TETM_OK : rz_fail(e);
 }
 
@@ -2227,6 +2399,128 @@ int tetm_rz_get_info(tetm_rz* s, tetm_rz_info* info) {
   return TETM_OK;
 }
 
+int tetm_rz_charge_residual(tetm_rz* s, int32_t mode, double* max_e, double* max_h, double* q_scale) {
+  if (!rz_mode_ok(s, mode)) return TETM_E_ARG;
+  if (!s->prev_valid || s->step < 1) return TETM_E_STATE;
+  if (!s->rec1) {
+    cudaError_t e = cudaMalloc(&s->rec1, sizeof(double) * (size_t)s->n_modes * kRzRec);
+    if (e != cudaSuccess) return rz_fail(e);
+  }
+  const int rc = s->esz == 8 ? rz_queue_balances<double>(s, s->rec1) : rz_queue_balances<float>(s, s->rec1);
+  if (rc) return rc;
+  double h[kRzRec];
+  cudaError_t e = cudaMemcpyAsync(h, s->rec1 + (size_t)mode * kRzRec, sizeof(h), cudaMemcpyDeviceToHost, s->st);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(s->st);
+  if (e != cudaSuccess) return rz_fail(e);
+  if (max_e) *max_e = h[3];
+  if (max_h) *max_h = h[4];
+  if (q_scale) *q_scale = h[5];
+  return TETM_OK;
+}
+
+int tetm_rz_set_balance_every(tetm_rz* s, int32_t every) {
+  if (!s || every < 0) return TETM_E_ARG;
+  if (every > 0 && !s->hist) {
+    const int cap = 1024;
+    cudaError_t e = cudaMalloc(&s->hist, sizeof(double) * (size_t)cap * s->n_modes * kRzRec);
+    if (e != cudaSuccess) return rz_fail(e);
+    s->hist_cap = cap;
+    s->device_bytes += (long long)(sizeof(double) * (size_t)cap * s->n_modes * kRzRec);
+  }
+  s->bal_every = every;
+  return TETM_OK;
+}
+
+int tetm_rz_balance_history(tetm_rz* s, double* out, int32_t cap, int32_t* n_out) {
+  if (!s) return TETM_E_ARG;
+  const long long nrec = std::min<long long>(s->hist_count, s->hist_cap);
+  const long long rows = nrec * s->n_modes;
+  if (n_out) *n_out = (int32_t)rows;
+  cudaError_t e = cudaSuccess;
+  if (out && rows > 0) {
+    if (cap < rows) return TETM_E_ARG;
+    std::vector<double> h((size_t)s->hist_cap * s->n_modes * kRzRec);
+    e = cudaMemcpyAsync(h.data(), s->hist, sizeof(double) * h.size(), cudaMemcpyDeviceToHost, s->st);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(s->st);
+    if (e != cudaSuccess) return rz_fail(e);
+    const long long first = s->hist_count - nrec;
+    const size_t rec = (size_t)s->n_modes * kRzRec;
+    for (long long r = 0; r < nrec; ++r)
+      memcpy(out + (size_t)r * rec, h.data() + (size_t)((first + r) % s->hist_cap) * rec, sizeof(double) * rec);
+  } else {
+    e = cudaStreamSynchronize(s->st);
+  }
+  return e == cudaSuccess ? TETM_OK : rz_fail(e);
+}
+
+namespace {
+// Checkpoint of a rotationally symmetric solve: header, the current state of
+// every mode in the device layout, then the wake accumulators (longitudinal
+// and transverse, even and odd halves).
+struct RzCkpt {
+  char magic[8];
+  int32_t nr, nz, m_lo, m_hi, precision, bunch, nw, obs, scattered, kernel_pairs;
+  double dr, dz, cdt;
+  int64_t step, kshift, elems;
+};
+size_t rz_ckpt_bytes(const tetm_rz* s) {
+  return sizeof(RzCkpt) + rz_field_bytes(s->L, s->esz, s->n_modes) +
+         (s->bunch ? 4 * sizeof(double) * (size_t)s->n_modes * s->nw : 0);
+}
+}  // namespace
+
+int tetm_rz_save(tetm_rz* s, void* buf, size_t cap, size_t* used) {
+  if (!s) return TETM_E_ARG;
+  const size_t need = rz_ckpt_bytes(s);
+  if (used) *used = need;
+  if (!buf) return TETM_OK;
+  if (cap < need) return TETM_E_ARG;
+  RzCkpt h;
+  memset(&h, 0, sizeof(h));
+  memcpy(h.magic, "TETMRZC1", 8);
+  h.nr = s->g.nr; h.nz = s->g.nz; h.m_lo = s->g.m_lo; h.m_hi = s->g.m_hi; h.precision = s->g.precision;
+  h.bunch = s->bunch; h.nw = s->bunch ? s->nw : 0; h.obs = s->obs; h.scattered = s->scattered;
+  h.dr = s->g.dr; h.dz = s->g.dz; h.cdt = s->cdt;
+  h.step = s->step; h.kshift = s->kshift;
+  h.elems = (int64_t)s->n_modes * s->L.mode_elems();
+  char* p = static_cast<char*>(buf);
+  memcpy(p, &h, sizeof(h));
+  p += sizeof(h);
+  const size_t fb = rz_field_bytes(s->L, s->esz, s->n_modes);
+  cudaError_t e = cudaMemcpyAsync(p, s->set[s->cur], fb, cudaMemcpyDeviceToHost, s->st);
+  p += fb;
+  const size_t wb = 2 * sizeof(double) * (size_t)s->n_modes * s->nw;
+  if (e == cudaSuccess && s->bunch) e = cudaMemcpyAsync(p, s->W, wb, cudaMemcpyDeviceToHost, s->st);
+  if (e == cudaSuccess && s->bunch) e = cudaMemcpyAsync(p + wb, s->WT, wb, cudaMemcpyDeviceToHost, s->st);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(s->st);
+  return e == cudaSuccess ? TETM_OK : rz_fail(e);
+}
+
+int tetm_rz_load(tetm_rz* s, const void* buf, size_t size) {
+  if (!s || !buf || size < sizeof(RzCkpt)) return TETM_E_ARG;
+  RzCkpt h;
+  memcpy(&h, buf, sizeof(h));
+  if (memcmp(h.magic, "TETMRZC1", 8) != 0 || h.nr != s->g.nr || h.nz != s->g.nz || h.m_lo != s->g.m_lo ||
+      h.m_hi != s->g.m_hi || h.precision != s->g.precision || h.bunch != (int)s->bunch ||
+      h.nw != (s->bunch ? s->nw : 0) || h.obs != s->obs || h.scattered != (int)s->scattered || h.dr != s->g.dr ||
+      h.dz != s->g.dz || h.cdt != s->cdt || h.kshift != s->kshift ||
+      h.elems != (int64_t)s->n_modes * s->L.mode_elems() || size < rz_ckpt_bytes(s))
+    return TETM_E_ARG;
+  const char* p = static_cast<const char*>(buf) + sizeof(h);
+  const size_t fb = rz_field_bytes(s->L, s->esz, s->n_modes);
+  cudaError_t e = cudaMemcpyAsync(s->set[s->cur], p, fb, cudaMemcpyHostToDevice, s->st);
+  p += fb;
+  const size_t wb = 2 * sizeof(double) * (size_t)s->n_modes * s->nw;
+  if (e == cudaSuccess && s->bunch) e = cudaMemcpyAsync(s->W, p, wb, cudaMemcpyHostToDevice, s->st);
+  if (e == cudaSuccess && s->bunch) e = cudaMemcpyAsync(s->WT, p + wb, wb, cudaMemcpyHostToDevice, s->st);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(s->st);
+  if (e != cudaSuccess) return rz_fail(e);
+  s->step = h.step;
+  s->prev_valid = false;
+  s->sc_until = 0;  // the scattered form's sources are recomputed from the loaded step on
+  return TETM_OK;
+}
+
 int tetm_rz_destroy(tetm_rz* s) {
   if (!s) return TETM_OK;
   if (s->own) cudaStreamSynchronize(s->own);
@@ -2248,6 +2542,9 @@ int tetm_rz_destroy(tetm_rz* s) {
   cudaFree(s->S);
   cudaFree(s->differs);
   cudaFree(s->Jzero);
+  cudaFree(s->hist);
+  cudaFree(s->cpart);
+  cudaFree(s->rec1);
   if (s->side) {
     cudaStreamSynchronize(s->side);
     cudaStreamDestroy(s->side);

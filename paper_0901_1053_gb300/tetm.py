@@ -51,7 +51,8 @@ EXPORTS = ("tetm_create", "tetm_set_bunch", "tetm_step", "tetm_sync", "tetm_wake
            "tetm_rz_set_stream", "tetm_rz_get_info", "tetm_rz_bytes_needed", "tetm_rz_destroy",
            "tetm_rz_set_kernel", "tetm_rz_set_observer", "tetm_rz_transverse_wake",
            "tetm_rz_set_bunch_static", "tetm_rz_set_bunch_scattered", "tetm_rz_selftest_wait",
-           "tetm_rz_check_guards")
+           "tetm_rz_check_guards", "tetm_rz_charge_residual", "tetm_rz_set_balance_every",
+           "tetm_rz_balance_history", "tetm_rz_save", "tetm_rz_load")
 TETM_RZ_KERNEL_ASYNC = 0
 TETM_RZ_KERNEL_REGISTER = 1
 TETM_RZ_KERNEL_BULK = 2
@@ -156,6 +157,12 @@ def _load():
         "tetm_rz_get_info": (ctypes.c_int, [vp, ctypes.POINTER(tetm_rz_info)]),
         "tetm_rz_bytes_needed": (ctypes.c_int64, [ctypes.POINTER(tetm_rz_grid)]),
         "tetm_rz_destroy": (ctypes.c_int, [vp]),
+        "tetm_rz_charge_residual": (ctypes.c_int, [vp, i32, ctypes.POINTER(dbl), ctypes.POINTER(dbl),
+                                                   ctypes.POINTER(dbl)]),
+        "tetm_rz_set_balance_every": (ctypes.c_int, [vp, i32]),
+        "tetm_rz_balance_history": (ctypes.c_int, [vp, vp, i32, ctypes.POINTER(i32)]),
+        "tetm_rz_save": (ctypes.c_int, [vp, vp, ctypes.c_size_t, ctypes.POINTER(ctypes.c_size_t)]),
+        "tetm_rz_load": (ctypes.c_int, [vp, vp, ctypes.c_size_t]),
     }
     for name, (res, args) in sig.items():
         f = getattr(lib, name)
@@ -538,6 +545,37 @@ class RzSolver:
         w = ctypes.c_double()
         _check(lib.tetm_rz_energy(self.h, self._mode(m), ctypes.byref(w)), "tetm_rz_energy")
         return w.value
+
+    def charge_residual(self, m):
+        """(max |qe - qbunch|, max |qh|, bunch charge scale) of mode m."""
+        e, h, q = ctypes.c_double(), ctypes.c_double(), ctypes.c_double()
+        _check(lib.tetm_rz_charge_residual(self.h, self._mode(m), ctypes.byref(e), ctypes.byref(h),
+                                           ctypes.byref(q)), "tetm_rz_charge_residual")
+        return e.value, h.value, q.value
+
+    def set_balance_every(self, every):
+        _check(lib.tetm_rz_set_balance_every(self.h, int(every)), "tetm_rz_set_balance_every")
+
+    def balance_history(self):
+        """Array (rows, 6): step, m, energy, max_e, max_h, q_scale per mode and record."""
+        n = ctypes.c_int32()
+        _check(lib.tetm_rz_balance_history(self.h, None, 0, ctypes.byref(n)), "tetm_rz_balance_history")
+        out = np.zeros((n.value, 6), dtype=np.float64)
+        if n.value:
+            _check(lib.tetm_rz_balance_history(self.h, _ptr(out), n.value, ctypes.byref(n)),
+                   "tetm_rz_balance_history")
+        return out
+
+    def save(self):
+        used = ctypes.c_size_t()
+        _check(lib.tetm_rz_save(self.h, None, 0, ctypes.byref(used)), "tetm_rz_save")
+        buf = (ctypes.c_char * used.value)()
+        _check(lib.tetm_rz_save(self.h, buf, used.value, ctypes.byref(used)), "tetm_rz_save")
+        return bytes(buf)
+
+    def load(self, data):
+        buf = ctypes.create_string_buffer(data, len(data))
+        _check(lib.tetm_rz_load(self.h, buf, len(data)), "tetm_rz_load")
 
     def get(self, m, comp):
         c = RZ_COMPONENTS.index(comp) if isinstance(comp, str) else int(comp)

@@ -141,6 +141,11 @@ def test_every_handle_call_rejects_a_null_handle_without_a_gpu(tetm):
         "tetm_rz_set_bunch_static": lambda: L.tetm_rz_set_bunch_static(None, 1e-3, 1e-9, 0, 10),
         "tetm_rz_set_bunch_scattered": lambda: L.tetm_rz_set_bunch_scattered(None, 1e-3, 1e-9, 0, 10),
         "tetm_rz_check_guards": lambda: L.tetm_rz_check_guards(None, None),
+        "tetm_rz_charge_residual": lambda: L.tetm_rz_charge_residual(None, 0, None, None, None),
+        "tetm_rz_set_balance_every": lambda: L.tetm_rz_set_balance_every(None, 1),
+        "tetm_rz_balance_history": lambda: L.tetm_rz_balance_history(None, None, 0, None),
+        "tetm_rz_save": lambda: L.tetm_rz_save(None, None, 0, None),
+        "tetm_rz_load": lambda: L.tetm_rz_load(None, None, 0),
     }
     for name, call in calls.items():
         assert call() == E, name
