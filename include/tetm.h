@@ -268,6 +268,47 @@ int64_t tetm_bytes_needed(const tetm_grid* g);
 int tetm_save(tetm_solver* s, void* buf, size_t cap, size_t* used);
 int tetm_load(tetm_solver* s, const void* buf, size_t size);
 
+/* ---- z-slabs of one solve ---------------------------------------------------
+ * The scheme couples neighbouring planes only: an update of planes
+ * [k0, k1) reads the state at planes k0 - 1 .. k1 (the TM stage of plane
+ * k0 - 1 is recomputed, e_x and e_y of plane k1 enter the TM stage of plane
+ * k1 - 1). So a grid splits along z into slabs that advance side by side
+ * (Sec. 4, the scheme is easily parallelised) when, before every step, each
+ * slab receives
+ *   from the slab below: the six components of its last plane (into the
+ *   ghost plane below the slab's first plane);
+ *   from the slab above: e_x and e_y of its first plane (into the plane
+ *   above the slab's last plane).
+ * Bunch current and wake stay with the planes that carry them: every slab
+ * adds its own planes' samples, the wake of the grid is the sum of the
+ * slabs' wakes. The results equal the whole-grid solve's (the same
+ * arithmetic per plane; the wake up to the order of that sum).
+ *
+ * tetm_create_slab: a solve of planes [k_lo, k_hi) (k_hi - k_lo >= 2) of the
+ * grid g; eps_r, mu_r, pec cover the whole grid as in tetm_create. Its local
+ * plane k is plane k_lo + k of the grid (tetm_get_fields / tetm_set_fields
+ * give local planes 0 .. k_hi - k_lo, the last being the neighbour's).
+ * tetm_set_bunch takes the grid's bunch line and cold start; the reference
+ * kernel, Yee's scheme, the static start, periodic balances and batches
+ * are not available for a slab (TETM_E_UNSUPPORTED). */
+#define TETM_PLANES_UP 0    /* the message to the slab above: six components of the last plane */
+#define TETM_PLANES_DOWN 1  /* the message to the slab below: e_x, e_y of the first plane      */
+int tetm_create_slab(const tetm_grid* g, int32_t k_lo, int32_t k_hi, const double* eps_r,
+                     const double* mu_r, const uint8_t* pec, tetm_solver** out);
+/* Bytes of a message in direction dir (six or two planes of the device
+ * layout, (ny + 4) * row pitch entries each); 0 for a bad argument. */
+int64_t tetm_plane_bytes(tetm_solver* s, int32_t dir);
+/* tetm_export_plane copies the message for direction dir out of the current
+ * state into buf; tetm_import_plane copies a message received from the
+ * neighbour (a message moving up comes from the slab below) into the
+ * current state's ghost plane (TETM_E_STATE when there is no such
+ * neighbour). buf is host or device memory of tetm_plane_bytes bytes
+ * (pinned host memory or a device buffer for NCCL send/recv); both queue
+ * copies on the solve's stream and return: tetm_sync before reading an
+ * exported host buffer, and import before the next tetm_step. */
+int tetm_export_plane(tetm_solver* s, int32_t dir, void* buf);
+int tetm_import_plane(tetm_solver* s, int32_t dir, const void* buf);
+
 /* ---- no-allocation variant ------------------------------------------------
  * The paper has no counterpart to this entry point; it exists for callers
  * that are not allowed to allocate device memory: code whose device memory

@@ -127,6 +127,7 @@ int tetm_batch_create(tetm_solver* const* solvers, const int64_t* step_limits, i
     tetm_solver* s = solvers[i];
     if (!s || s->esz != esz || s->in_batch) return TETM_E_ARG;
     if (!s->uniform) return TETM_E_UNSUPPORTED;  // the fused kernels need one material
+    if (s->is_slab()) return TETM_E_UNSUPPORTED;     // a z-slab steps between plane exchanges
     if (s->scheme != TETM_SCHEME_TETM) return TETM_E_UNSUPPORTED;  // batches run the TE/TM scheme
     for (int j = 0; j < i; ++j)
       if (solvers[j] == s) return TETM_E_ARG;

@@ -46,19 +46,22 @@ namespace {
 // Geometry on the device (staircase reading of the material matrices)
 // ---------------------------------------------------------------------------
 struct GeomIn {
-  const uint8_t* pec;    // per cell or nullptr
-  const double* eps;     // per cell or nullptr
-  const double* mu;      // per cell or nullptr
-  int nx, ny, nz;
+  const uint8_t* pec;    // per cell of the whole grid or nullptr
+  const double* eps;     // per cell of the whole grid or nullptr
+  const double* mu;      // per cell of the whole grid or nullptr
+  int nx, ny, nz;        // nz: planes of this solve
+  int k_off, nz_all;     // z-slab: global plane of local plane 0, planes of the whole grid
   double dx, dy, dz;
 };
 
+// cell (ci, cj, ck) of this solve (ck local): PEC outside the whole grid
 __device__ __forceinline__ bool gpec(const GeomIn& g, long ci, long cj, long ck) {
-  if (ci < 0 || cj < 0 || ck < 0 || ci >= g.nx || cj >= g.ny || ck >= g.nz) return true;
+  ck += g.k_off;
+  if (ci < 0 || cj < 0 || ck < 0 || ci >= g.nx || cj >= g.ny || ck >= g.nz_all) return true;
   return g.pec ? g.pec[ci + (long)g.nx * (cj + (long)g.ny * ck)] != 0 : false;
 }
 __device__ __forceinline__ double gval(const double* a, const GeomIn& g, long ci, long cj, long ck) {
-  return a ? a[ci + (long)g.nx * (cj + (long)g.ny * ck)] : 1.0;
+  return a ? a[ci + (long)g.nx * (cj + (long)g.ny * (ck + g.k_off))] : 1.0;
 }
 
 // Edge along `axis` at node (i,j,k): the four cells around it.
@@ -109,20 +112,24 @@ struct MinvOut {
   double* a[6];  // per-entry M^-1 arrays (material runs) or nullptr
 };
 
-__global__ void build_geometry(GeomIn g, Layout L, uint8_t* mask, MinvOut mo) {
-  const long long total = (long long)(g.nx + 1) * (g.ny + 1) * (g.nz + 1);
+// Activity bits (and M^-1 arrays) of the node entries of planes k_first ..
+// nz: k_first = 0 for a whole grid, -1 for a z-slab whose plane below its
+// first one is a ghost plane with the geometry of the whole grid.
+__global__ void build_geometry(GeomIn g, Layout L, int k_first, uint8_t* mask, MinvOut mo) {
+  const long long total = (long long)(g.nx + 1) * (g.ny + 1) * (g.nz + 1 - k_first);
   const long long q = (long long)blockIdx.x * blockDim.x + threadIdx.x;
   if (q >= total) return;
   const int i = (int)(q % (g.nx + 1));
   const int j = (int)((q / (g.nx + 1)) % (g.ny + 1));
-  const int k = (int)(q / ((long long)(g.nx + 1) * (g.ny + 1)));
+  const int k = k_first + (int)(q / ((long long)(g.nx + 1) * (g.ny + 1)));
   const long long id = L.idx(i, j, k);
   double v[6] = {0, 0, 0, 0, 0, 0};
+  const bool kin = k + g.k_off < g.nz_all;  // the edge or face along z lies inside the whole grid
   if (i < g.nx) v[kEX] = edge_minv(g, 0, i, j, k);
   if (j < g.ny) v[kEY] = edge_minv(g, 1, i, j, k);
-  if (k < g.nz) v[kEZ] = edge_minv(g, 2, i, j, k);
-  if (j < g.ny && k < g.nz) v[kHX] = face_minv(g, 0, i, j, k);
-  if (i < g.nx && k < g.nz) v[kHY] = face_minv(g, 1, i, j, k);
+  if (kin) v[kEZ] = edge_minv(g, 2, i, j, k);
+  if (j < g.ny && kin) v[kHX] = face_minv(g, 0, i, j, k);
+  if (i < g.nx && kin) v[kHY] = face_minv(g, 1, i, j, k);
   if (i < g.nx && j < g.ny) v[kHZ] = face_minv(g, 2, i, j, k);
   uint8_t m = 0;
   for (int c = 0; c < 6; ++c) {
@@ -319,7 +326,7 @@ StepArgs<T> tetm::step_args(tetm_solver* s, bool fused) {
   a.b.i0 = s->i0;
   a.b.j0 = s->j0;
   a.b.c0 = s->c0;
-  a.b.kshift = s->kshift;
+  a.b.kshift = s->kshift - s->k_lo;  // plane indices of the kernels are local to a z-slab
   a.b.m_min = s->m_min;
   a.b.m_max = s->m_max;
   a.b.inv_q = s->bunch ? 1.0 / s->q : 0.0;
@@ -371,7 +378,7 @@ WorkView work_view(const tetm_solver* s) {
 
 template <typename T>
 int queue_balances(tetm_solver* s, double* rec) {
-  const double zc = ((double)(s->step + s->kshift - 1) + 0.5 - s->c0) * s->g.dz;
+  const double zc = ((double)(s->step + s->kshift - s->k_lo - 1) + 0.5 - s->c0) * s->g.dz;
   CK(launch_bunch_charge(s->bunch ? s->q : 0.0, s->bunch ? s->sigma : 1.0, s->g.dz, zc, s->g.nz,
                          s->qline, rec + 4, (double)s->step, rec, s->stream));
   const T *cur[6], *prv[6];
@@ -560,15 +567,21 @@ int64_t tetm_bytes_needed(const tetm_grid* g) {
   return (int64_t)(12 * esz + 1) * L.count + (int64_t)(1 << 20);
 }
 
-int tetm_create(const tetm_grid* g, const double* eps_r, const double* mu_r, const uint8_t* pec,
-                tetm_solver** out) {
+}  // extern "C"
+
+namespace {
+
+// A solve of planes [k_lo, k_lo + g->nz) of a grid of nz_all planes (the
+// whole grid: k_lo = 0, nz_all = g->nz); the cell arrays cover the whole grid.
+int create_impl(const tetm_grid* g, int k_lo, int nz_all, const double* eps_r, const double* mu_r,
+                const uint8_t* pec, tetm_solver** out) {
   if (!out) return TETM_E_ARG;
   *out = nullptr;
   if (!grid_ok(g)) return TETM_E_ARG;
   const double cdt = cdt_of(g);
   const double lim_t = 1.0 / sqrt(1.0 / (g->dx * g->dx) + 1.0 / (g->dy * g->dy));
   if (cdt > g->dz * (1.0 + 1e-12) || cdt > lim_t * (1.0 + 1e-12)) return TETM_E_UNSTABLE;
-  const long long ncell = (long long)g->nx * g->ny * g->nz;
+  const long long ncell = (long long)g->nx * g->ny * nz_all;
   // materials: physical (>= 1) and finite; uniform if every cell has the same value
   bool uniform = true;
   double eps_u = 1.0, mu_u = 1.0;
@@ -590,6 +603,8 @@ int tetm_create(const tetm_grid* g, const double* eps_r, const double* mu_r, con
   if (!s) return TETM_E_NOMEM;
   s->g = *g;
   s->g.cdt = cdt;
+  s->k_lo = k_lo;
+  s->nz_all = nz_all;
   s->esz = g->precision == TETM_FP64 ? 8 : 4;
   s->L = make_layout(g->nx, g->ny, g->nz, (int)s->esz);
   s->alpha = 0.5 * cdt / kC;
@@ -637,6 +652,8 @@ int tetm_create(const tetm_grid* g, const double* eps_r, const double* mu_r, con
   gi.eps = nullptr;
   gi.mu = nullptr;
   gi.nx = g->nx; gi.ny = g->ny; gi.nz = g->nz;
+  gi.k_off = k_lo;
+  gi.nz_all = nz_all;
   gi.dx = g->dx; gi.dy = g->dy; gi.dz = g->dz;
   uint8_t* dpec = nullptr;
   double *deps = nullptr, *dmu = nullptr;
@@ -659,8 +676,9 @@ int tetm_create(const tetm_grid* g, const double* eps_r, const double* mu_r, con
     gi.mu = dmu;
   }
   if (rc == TETM_OK) {
-    const long long total = (long long)(g->nx + 1) * (g->ny + 1) * (g->nz + 1);
-    build_geometry<<<(unsigned)((total + 255) / 256), 256, 0, s->stream>>>(gi, s->L, s->mask, mo);
+    const int k_first = k_lo > 0 ? -1 : 0;  // a z-slab's ghost plane below takes the whole grid's geometry
+    const long long total = (long long)(g->nx + 1) * (g->ny + 1) * (g->nz + 1 - k_first);
+    build_geometry<<<(unsigned)((total + 255) / 256), 256, 0, s->stream>>>(gi, s->L, k_first, s->mask, mo);
     if (cudaGetLastError() != cudaSuccess || cudaStreamSynchronize(s->stream) != cudaSuccess) rc = TETM_E_CUDA;
   }
   cudaFree(dpec);
@@ -712,6 +730,25 @@ int tetm_create(const tetm_grid* g, const double* eps_r, const double* mu_r, con
   return TETM_OK;
 }
 
+}  // namespace
+
+extern "C" {
+
+int tetm_create(const tetm_grid* g, const double* eps_r, const double* mu_r, const uint8_t* pec,
+                tetm_solver** out) {
+  return create_impl(g, 0, g ? g->nz : 0, eps_r, mu_r, pec, out);
+}
+
+int tetm_create_slab(const tetm_grid* g, int32_t k_lo, int32_t k_hi, const double* eps_r, const double* mu_r,
+                     const uint8_t* pec, tetm_solver** out) {
+  if (!out) return TETM_E_ARG;
+  *out = nullptr;
+  if (!g || k_lo < 0 || k_hi > g->nz || k_hi - k_lo < 2) return TETM_E_ARG;
+  tetm_grid local = *g;
+  local.nz = k_hi - k_lo;
+  return create_impl(&local, k_lo, g->nz, eps_r, mu_r, pec, out);
+}
+
 void tetm_destroy(tetm_solver* s) {
   if (!s) return;
   if (s->stream) cudaStreamSynchronize(s->stream); else cudaDeviceSynchronize();
@@ -728,6 +765,7 @@ int tetm_set_stream(tetm_solver* s, void* st) {
 int tetm_set_kernel(tetm_solver* s, int32_t kernel) {
   if (!s || (kernel != TETM_KERNEL_FUSED && kernel != TETM_KERNEL_REFERENCE)) return TETM_E_ARG;
   if (s->in_batch) return TETM_E_STATE;
+  if (kernel == TETM_KERNEL_REFERENCE && s->is_slab()) return TETM_E_UNSUPPORTED;  // it updates ghost planes in place
   // (Yee's scheme runs material arrays on the reference updates whatever the kernel)
   if (kernel == TETM_KERNEL_FUSED && !s->uniform && s->tile_x != 28 && !slab_shape_ok(s->tile_x, s->tile_y) &&
       s->scheme == TETM_SCHEME_TETM)
@@ -765,6 +803,7 @@ int tetm_set_tiling(tetm_solver* s, int32_t tile_x, int32_t tile_y, int32_t chun
 int tetm_set_scheme(tetm_solver* s, int32_t scheme) {
   if (!s || (scheme != TETM_SCHEME_TETM && scheme != TETM_SCHEME_YEE)) return TETM_E_ARG;
   if (scheme == s->scheme) return TETM_OK;
+  if (s->is_slab()) return TETM_E_UNSUPPORTED;
   if (s->step != 0 || s->bunch || s->in_batch || s->bal_every > 0) return TETM_E_STATE;
   if (scheme == TETM_SCHEME_YEE) {
     const double dx = s->g.dx, dy = s->g.dy, dz = s->g.dz;
@@ -941,6 +980,8 @@ int tetm_charge_residual(tetm_solver* s, double* max_e, double* max_h, double* q
 
 int tetm_set_balance_every(tetm_solver* s, int32_t every) {
   if (!s || every < 0) return TETM_E_ARG;
+  // a z-slab's ghost planes of the new state arrive only with the next exchange
+  if (every > 0 && s->is_slab()) return TETM_E_UNSUPPORTED;
   if (every > 0 && s->scheme != TETM_SCHEME_TETM) return TETM_E_UNSUPPORTED;
   s->bal_every = every;
   return TETM_OK;
@@ -1002,6 +1043,46 @@ int tetm_check_guards(tetm_solver* s, int64_t* violations) {
   cudaFree(cnt);
   CK(e);
   *violations = (int64_t)h;
+  return TETM_OK;
+}
+
+int64_t tetm_plane_bytes(tetm_solver* s, int32_t dir) {
+  if (!s || (dir != TETM_PLANES_UP && dir != TETM_PLANES_DOWN)) return 0;
+  return (int64_t)(dir == TETM_PLANES_UP ? 6 : 2) * s->L.sz * (int64_t)s->esz;
+}
+
+int tetm_export_plane(tetm_solver* s, int32_t dir, void* buf) {
+  if (!s || !buf || (dir != TETM_PLANES_UP && dir != TETM_PLANES_DOWN)) return TETM_E_ARG;
+  if (s->scheme != TETM_SCHEME_TETM || s->in_batch) return TETM_E_STATE;
+  const size_t pb = (size_t)s->L.sz * s->esz;
+  // up: every component of the last plane the solve owns; down: e_x, e_y of its first
+  const int k = dir == TETM_PLANES_UP ? s->L.nz - 1 : 0;
+  const int comps[6] = {kEX, kEY, kEZ, kHX, kHY, kHZ};
+  const int nc = dir == TETM_PLANES_UP ? 6 : 2;
+  char* p = static_cast<char*>(buf);
+  for (int q = 0; q < nc; ++q) {
+    const char* src = static_cast<const char*>(s->set[s->cur][comps[q]]) + (size_t)(k + 1) * pb;
+    CK(cudaMemcpyAsync(p + q * pb, src, pb, cudaMemcpyDefault, s->stream));
+  }
+  return TETM_OK;
+}
+
+int tetm_import_plane(tetm_solver* s, int32_t dir, const void* buf) {
+  if (!s || !buf || (dir != TETM_PLANES_UP && dir != TETM_PLANES_DOWN)) return TETM_E_ARG;
+  if (s->scheme != TETM_SCHEME_TETM || s->in_batch) return TETM_E_STATE;
+  // a message moving up fills the ghost plane below the first owned plane
+  // (needs a neighbour below: k_lo > 0); one moving down fills e_x, e_y of
+  // the plane above the last owned one (needs a neighbour above)
+  if (dir == TETM_PLANES_UP ? s->k_lo == 0 : s->k_lo + s->L.nz >= s->nz_all) return TETM_E_STATE;
+  const size_t pb = (size_t)s->L.sz * s->esz;
+  const int k = dir == TETM_PLANES_UP ? -1 : s->L.nz;
+  const int comps[6] = {kEX, kEY, kEZ, kHX, kHY, kHZ};
+  const int nc = dir == TETM_PLANES_UP ? 6 : 2;
+  const char* p = static_cast<const char*>(buf);
+  for (int q = 0; q < nc; ++q) {
+    char* dst = static_cast<char*>(s->set[s->cur][comps[q]]) + (size_t)(k + 1) * pb;
+    CK(cudaMemcpyAsync(dst, p + q * pb, pb, cudaMemcpyDefault, s->stream));
+  }
   return TETM_OK;
 }
 

@@ -330,7 +330,7 @@ fused_step_slab(const StepArgs<float> a, const __grid_constant__ CUtensorMap tm_
         const float hyl = e > 0 ? hya.v[e - 1] : hyaL;
         cur[e] = (hxaD.v[e] - hxa.v[e]) - (hyl - hya.v[e]);
       }
-      if (line_q && k >= 0) {  // the bunch current on its line (one quad of a tile row)
+      if (line_q) {  // the bunch current on its line (one quad of a tile row)
         const long long dd = (long long)k - (a.n + a.b.kshift) + a.b.c0;
         if (dd >= -a.b.c0 && dd < a.b.c0) {
           const float jj = a.b.J[dd + a.b.c0];

@@ -215,7 +215,7 @@ fused_step(const StepArgs<T> a) {
     sD[sy][sx] = hya;
     __syncthreads();
     T cur = (sC[sy - 1][sx] - hxa) - (sD[sy][sx - 1] - hya);
-    if (line && k >= 0) {
+    if (line) {
       const long long d = (long long)k - (a.n + a.b.kshift) + a.b.c0;
       if (d >= -a.b.c0 && d < a.b.c0) cur -= a.b.J[d + a.b.c0];
     }

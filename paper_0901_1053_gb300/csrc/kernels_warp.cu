@@ -182,7 +182,7 @@ __device__ __forceinline__ void fused_step_warp_item(const StepArgs<T>& a, int i
         const T hya = hy + cHY * (-dex + (shfl_dn(ez) - ez));                    // U2
         T cur = (hxa_p - hxa) - (shfl_up1(hya) - hya);
         const bool line = line_x && r == line_r;
-        if (line && k >= 0) {
+        if (line) {
           const long long dd = (long long)k - (a.n + a.b.kshift) + a.b.c0;
           if (dd >= -a.b.c0 && dd < a.b.c0) cur -= a.b.J[dd + a.b.c0];
         }
@@ -432,7 +432,7 @@ __device__ __forceinline__ void fused_step_warp_reg_item(const StepArgs<T>& a, i
         const T hya = d.hy + cHY * (-dex + (shfl_dn(d.ez) - d.ez));              // U2
         T cur = (hxa_p - hxa) - (shfl_up1(hya) - hya);
         const bool line = line_x && r == line_r;
-        if (line && k >= 0) {
+        if (line) {
           const long long dd = (long long)k - (a.n + a.b.kshift) + a.b.c0;
           if (dd >= -a.b.c0 && dd < a.b.c0) cur -= a.b.J[dd + a.b.c0];
         }
@@ -712,7 +712,7 @@ __device__ __forceinline__ void fused_step_warp_mat_item(const StepArgs<T>& a, i
         const T hya = hy + cHY * (-dex + (shfl_dn(ez) - ez));                    // U2
         T cur = (hxa_p - hxa) - (shfl_up1(hya) - hya);
         const bool line = line_x && r == line_r;
-        if (line && k >= 0) {
+        if (line) {
           const long long dd = (long long)k - (a.n + a.b.kshift) + a.b.c0;
           if (dd >= -a.b.c0 && dd < a.b.c0) cur -= a.b.J[dd + a.b.c0];
         }

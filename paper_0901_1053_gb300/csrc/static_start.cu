@@ -108,7 +108,7 @@ void solve_potential(int n, const std::vector<int>& ea, const std::vector<int>& 
 extern "C" int tetm_set_bunch_static(tetm_solver* s, double sigma_z, double charge, int32_t i0,
                                      int32_t j0, int32_t k_head) {
   if (!s) return TETM_E_ARG;
-  if (!s->vacuum) return TETM_E_UNSUPPORTED;
+  if (!s->vacuum || s->is_slab()) return TETM_E_UNSUPPORTED;
   if (s->in_batch || s->step != 0 || s->bunch) return TETM_E_STATE;
   if (!(sigma_z > 0) || !isfinite(sigma_z)) return TETM_E_ARG;
   const double dz = s->g.dz;

@@ -258,6 +258,10 @@ struct tetm_solver {
   long long staging_elems;
   long long device_bytes;
   long long active_cells;
+  // z-slab of a larger grid: planes [k_lo, k_lo + g.nz) of nz_all (whole grid: 0, g.nz)
+  int k_lo;
+  int nz_all;
+  bool is_slab() const { return k_lo > 0 || g.nz < nz_all; }
 };
 
 namespace tetm {

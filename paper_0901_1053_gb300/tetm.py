@@ -52,7 +52,10 @@ EXPORTS = ("tetm_create", "tetm_set_bunch", "tetm_step", "tetm_sync", "tetm_wake
            "tetm_rz_set_kernel", "tetm_rz_set_observer", "tetm_rz_transverse_wake",
            "tetm_rz_set_bunch_static", "tetm_rz_set_bunch_scattered", "tetm_rz_selftest_wait",
            "tetm_rz_check_guards", "tetm_rz_charge_residual", "tetm_rz_set_balance_every",
-           "tetm_rz_balance_history", "tetm_rz_save", "tetm_rz_load")
+           "tetm_rz_balance_history", "tetm_rz_save", "tetm_rz_load",
+           "tetm_create_slab", "tetm_plane_bytes", "tetm_export_plane", "tetm_import_plane")
+TETM_PLANES_UP = 0
+TETM_PLANES_DOWN = 1
 TETM_RZ_KERNEL_ASYNC = 0
 TETM_RZ_KERNEL_REGISTER = 1
 TETM_RZ_KERNEL_BULK = 2
@@ -163,6 +166,10 @@ def _load():
         "tetm_rz_balance_history": (ctypes.c_int, [vp, vp, i32, ctypes.POINTER(i32)]),
         "tetm_rz_save": (ctypes.c_int, [vp, vp, ctypes.c_size_t, ctypes.POINTER(ctypes.c_size_t)]),
         "tetm_rz_load": (ctypes.c_int, [vp, vp, ctypes.c_size_t]),
+        "tetm_create_slab": (ctypes.c_int, [ctypes.POINTER(tetm_grid), i32, i32, vp, vp, vp, pp]),
+        "tetm_plane_bytes": (ctypes.c_int64, [vp, i32]),
+        "tetm_export_plane": (ctypes.c_int, [vp, i32, vp]),
+        "tetm_import_plane": (ctypes.c_int, [vp, i32, vp]),
     }
     for name, (res, args) in sig.items():
         f = getattr(lib, name)
@@ -188,6 +195,11 @@ def _check(rc, where):
 
 def _ptr(a):
     return None if a is None else ctypes.c_void_p(a.ctypes.data)
+
+
+def _buf_ptr(b):
+    """Address of a numpy array or of a tensor (host or device)."""
+    return ctypes.c_void_p(b.data_ptr() if hasattr(b, "data_ptr") else b.ctypes.data)
 
 
 def make_grid(nx, ny, nz, dx, dy, dz, cdt=0.0, precision="fp32"):
@@ -231,7 +243,9 @@ class Solver:
     """
 
     def __init__(self, nx, ny, nz, dx, dy, dz, cdt=0.0, precision="fp32", eps_r=None, mu_r=None,
-                 pec=None):
+                 pec=None, k_range=None):
+        """k_range=(k_lo, k_hi): the z-slab of planes [k_lo, k_hi) of this grid
+        (tetm_create_slab); the cell arrays still cover the whole grid."""
         self.grid = make_grid(nx, ny, nz, dx, dy, dz, cdt, precision)
         cell = (int(nz), int(ny), int(nx))
         arrs = []
@@ -239,10 +253,18 @@ class Solver:
             arrs.append(None if a is None else np.ascontiguousarray(a, dtype=dt).reshape(cell))
         h = ctypes.c_void_p()
         self.h = None
-        _check(lib.tetm_create(ctypes.byref(self.grid), *[_ptr(a) for a in arrs], ctypes.byref(h)),
-               "tetm_create")
+        if k_range is None:
+            _check(lib.tetm_create(ctypes.byref(self.grid), *[_ptr(a) for a in arrs], ctypes.byref(h)),
+                   "tetm_create")
+            nzl = int(nz)
+        else:
+            k_lo, k_hi = int(k_range[0]), int(k_range[1])
+            _check(lib.tetm_create_slab(ctypes.byref(self.grid), k_lo, k_hi, *[_ptr(a) for a in arrs],
+                                        ctypes.byref(h)), "tetm_create_slab")
+            nzl = k_hi - k_lo
         self.h = h
-        self.shape = (int(nz) + 1, int(ny) + 1, int(nx) + 1)
+        self.k_range = None if k_range is None else (int(k_range[0]), int(k_range[1]))
+        self.shape = (nzl + 1, int(ny) + 1, int(nx) + 1)
 
     @classmethod
     def from_workload(cls, w, precision=None):
@@ -375,6 +397,18 @@ class Solver:
     def load(self, buf):
         b = np.ascontiguousarray(buf, dtype=np.uint8)
         _check(lib.tetm_load(self.h, _ptr(b), b.size), "tetm_load")
+
+    # --- z-slabs: ghost-plane messages (host numpy arrays or device tensors) ---
+    def plane_bytes(self, direction):
+        return int(lib.tetm_plane_bytes(self.h, int(direction)))
+
+    def export_plane(self, direction, buf):
+        """Queue the message for `direction` (TETM_PLANES_UP / _DOWN) into buf:
+        a numpy array or a tensor with a data_ptr() of plane_bytes bytes."""
+        _check(lib.tetm_export_plane(self.h, int(direction), _buf_ptr(buf)), "tetm_export_plane")
+
+    def import_plane(self, direction, buf):
+        _check(lib.tetm_import_plane(self.h, int(direction), _buf_ptr(buf)), "tetm_import_plane")
 
 
 def _comp(c):
