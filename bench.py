@@ -578,7 +578,7 @@ def run_batch_mode(args):
     ws = sharding.shard_workloads(allw, world, rank)
     big = max(ws, key=lambda w: w.cells)
     tuner = Autotuner()
-    t32 = tuner.tune(big, "fp32", batch=True)
+    t32 = tuple(int(x) for x in args.tiling.split(",")) if args.tiling else tuner.tune(big, "fp32", batch=True)
     t64 = tuner.tune(big, "fp64")
     dist.barrier()
     wakes32, t_step, t_total = run_batch(ws, "fp32", t32, graph_steps=32)

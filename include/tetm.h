@@ -347,9 +347,10 @@ int tetm_energy_noalloc(const tetm_grid* g, const void* const fields[6], const u
 
 /* ---- batches of solves ------------------------------------------------------
  * A batch advances several solves together: every batch step is one launch
- * of the warp-tiled kernel over the work items of all members, followed by a
- * device-side advance of every member (field-set swap, step count,
- * retirement at its step limit). Members keep their own grid, geometry,
+ * over the work items of all members (the slab kernel for float32 members
+ * whose first member has its 56 x 28 tile, the float32 default; the
+ * warp-tiled kernel otherwise), followed by a device-side advance of every
+ * member (field-set swap, step count, retirement at its step limit). Members keep their own grid, geometry,
  * bunch, wake and step counter; the paper's scheme is applied to each member
  * exactly as by tetm_step (the results are bit-identical to stepping each
  * solve alone). */
@@ -357,8 +358,9 @@ typedef struct tetm_batch tetm_batch;
 
 /* Group n distinct solves of one precision and one uniform material each.
  * step_limits[i] >= 0: member i stops when its step counter reaches it
- * (NULL or a negative entry: no limit). Members are switched to the
- * warp-tiled kernel with the first member's tile height. graph_steps > 0:
+ * (NULL or a negative entry: no limit). Members take the first member's
+ * tile (the slab kernel's 56 x 28 in float32, else the warp-tiled kernel
+ * with the first member's tile height); each keeps its own z-chunk length. graph_steps > 0:
  * runs of that many steps are captured once as a CUDA graph and replayed;
  * 0 launches every step directly. While in the batch a member rejects
  * tetm_step, tetm_set_fields, tetm_set_kernel, tetm_set_tiling and tetm_load

@@ -3,7 +3,9 @@
 // sizes fill the GPU; the member descriptors live on the device and are
 // advanced there (ping-pong swap, step count, retirement at the member's step
 // limit), which lets a run of steps be captured once as a CUDA graph and
-// replayed.
+// replayed. Float32 batches whose members use the slab kernel's tile (56 x 28)
+// run the batched slab kernel (each member's tensor maps in device memory),
+// the others the batched warp-tiled kernel.
 #include <string.h>
 
 #include <algorithm>
@@ -30,6 +32,10 @@ struct tetm_batch {
   cudaGraphExec_t exec;
   bool warmed;                    // one uncaptured launch done (launch set-up outside capture)
   bool failed;                    // a launch failed: no further steps (members resynchronised)
+  bool slab;                      // the batched slab kernel (float32, 56 x 28 tiles)
+  SlabBatchMaps* d_maps;          // per member (slab batches)
+  int* sched;                     // the slab kernel's schedule counters
+  int* err;                       // the slab kernel's bounded-wait error word
 };
 
 namespace {
@@ -46,6 +52,7 @@ int build_members(tetm_batch* b) {
     h[(size_t)i].a.work = nullptr;  // the batch's combined list is used instead
     h[(size_t)i].limit = b->limit[(size_t)i];
     h[(size_t)i].active = s->step < b->limit[(size_t)i] ? 1 : 0;
+    h[(size_t)i].cur = s->cur;
     for (int item : s->work_host) work.push_back(make_int2(i, item));
   }
   b->n_work = (int)work.size();
@@ -58,6 +65,24 @@ int build_members(tetm_batch* b) {
   if (!work.empty() && cudaMemcpyAsync(b->d_work, work.data(), sizeof(int2) * work.size(),
                                        cudaMemcpyHostToDevice, b->stream) != cudaSuccess)
     return TETM_E_CUDA;
+  if (b->slab) {  // each member's tensor maps of e_z, h_z of both sets
+    std::vector<SlabBatchMaps> hm((size_t)n);
+    for (int i = 0; i < n; ++i) {
+      tetm_solver* s = b->members[(size_t)i];
+      SlabMaps m;
+      void* ez[2] = {s->set[0][kEZ], s->set[1][kEZ]};
+      void* hz[2] = {s->set[0][kHZ], s->set[1][kHZ]};
+      if (build_slab_maps(&m, ez, hz, nullptr, s->L) != 0) return TETM_E_UNSUPPORTED;
+      memcpy(hm[(size_t)i].ez, m.ez, sizeof(m.ez));
+      memcpy(hm[(size_t)i].hz, m.hz, sizeof(m.hz));
+    }
+    if (cudaMalloc(&b->d_maps, sizeof(SlabBatchMaps) * (size_t)n) != cudaSuccess ||
+        cudaMalloc(&b->sched, 2 * sizeof(int)) != cudaSuccess || cudaMalloc(&b->err, sizeof(int)) != cudaSuccess)
+      return TETM_E_NOMEM;
+    if (cudaMemcpy(b->d_maps, hm.data(), sizeof(SlabBatchMaps) * (size_t)n, cudaMemcpyHostToDevice) != cudaSuccess ||
+        cudaMemset(b->sched, 0, 2 * sizeof(int)) != cudaSuccess || cudaMemset(b->err, 0, sizeof(int)) != cudaSuccess)
+      return TETM_E_CUDA;
+  }
   if (cudaStreamSynchronize(b->stream) != cudaSuccess) return TETM_E_CUDA;
   return TETM_OK;
 }
@@ -67,6 +92,11 @@ cudaError_t launch_one(tetm_batch* b) {
   int nz_max = 0;  // over the members that gather a transverse wake
   for (tetm_solver* s : b->members)
     if (s->bunch && s->obs_on) nz_max = std::max(nz_max, s->g.nz);
+  if constexpr (sizeof(T) == 4) {
+    if (b->slab)
+      return launch_fused_slab_batch((BatchMember<float>*)b->d_members, b->d_maps, (int)b->members.size(),
+                                     b->d_work, b->n_work, b->err, b->sched, nz_max, b->stream);
+  }
   return launch_fused_warp_batch<T>((const BatchMember<T>*)b->d_members, (int)b->members.size(),
                                     b->d_work, b->n_work, b->tile_y, nz_max, b->stream);
 }
@@ -109,6 +139,9 @@ void release(tetm_batch* b) {
   if (b->graph) cudaGraphDestroy(b->graph);
   cudaFree(b->d_members);
   cudaFree(b->d_work);
+  cudaFree(b->d_maps);
+  cudaFree(b->sched);
+  cudaFree(b->err);
   if (b->own_stream && b->stream) cudaStreamDestroy(b->stream);
   for (tetm_solver* s : b->members) s->in_batch = false;
 }
@@ -136,15 +169,19 @@ int tetm_batch_create(tetm_solver* const* solvers, const int64_t* step_limits, i
   if (!b) return TETM_E_NOMEM;
   b->esz = esz;
   b->graph_steps = graph_steps;
-  // every member runs the warp-tiled kernel with the first member's tile height
-  b->tile_y = (solvers[0]->tile_x == 28) ? solvers[0]->tile_y : 20;
+  // float32 members of the slab kernel's tile (the float32 default) run the
+  // batched slab kernel; otherwise every member runs the warp-tiled kernel
+  // with the first member's tile height
+  b->slab = esz == 4 && slab_shape_ok(solvers[0]->tile_x, solvers[0]->tile_y);
+  b->tile_y = b->slab ? solvers[0]->tile_y : ((solvers[0]->tile_x == 28) ? solvers[0]->tile_y : 20);
+  const int tx = b->slab ? solvers[0]->tile_x : 28;
   int rc = TETM_OK;
   for (int i = 0; i < n && rc == TETM_OK; ++i) {
     tetm_solver* s = solvers[i];
     b->members.push_back(s);
     b->limit.push_back(step_limits && step_limits[i] >= 0 ? (long long)step_limits[i] : (1LL << 62));
-    if (s->tile_x != 28 || s->tile_y != b->tile_y || s->work_dirty) {
-      s->tile_x = 28;
+    if (s->tile_x != tx || s->tile_y != b->tile_y || s->work_dirty) {
+      s->tile_x = tx;
       s->tile_y = b->tile_y;
       rc = rebuild_work(s);
     }
@@ -216,7 +253,13 @@ int tetm_batch_step(tetm_batch* b, int32_t nsteps) {
 
 int tetm_batch_sync(tetm_batch* b) {
   if (!b) return TETM_E_ARG;
-  return cudaStreamSynchronize(b->stream) == cudaSuccess ? TETM_OK : TETM_E_CUDA;
+  if (cudaStreamSynchronize(b->stream) != cudaSuccess) return TETM_E_CUDA;
+  if (b->err) {  // a bounded wait of the slab kernel gave up
+    int flag = 0;
+    if (cudaMemcpy(&flag, b->err, sizeof(int), cudaMemcpyDeviceToHost) != cudaSuccess) return TETM_E_CUDA;
+    if (flag) return TETM_E_TIMEOUT;
+  }
+  return TETM_OK;
 }
 
 int tetm_batch_info(tetm_batch* b, int32_t* n_members, int32_t* n_active, int32_t* work_items) {

@@ -159,6 +159,251 @@ __device__ __forceinline__ float right_of(float v0, int q) {
   return q + 1 < kQ ? t : 0.f;
 }
 
+// One (tile, z-chunk) work item of solve a (the ten updates of every plane
+// of the chunk); false when a ring copy did not land (the error word is
+// raised and the copies in flight are drained).
+template <bool MAT>
+__device__ __forceinline__ bool slab_item(const StepArgs<float>& a, const CUtensorMap* tm_ez, const CUtensorMap* tm_hz,
+                                          const CoefMaps* tm_co, int item, SlabSmem<MAT>& S, unsigned& phases,
+                                          int* err) {
+  using Smem = SlabSmem<MAT>;
+  constexpr int kSD = Smem::SD;
+  const int tid = threadIdx.x, q = tid % kQ, row = tid / kQ;
+  const Layout L = a.L;
+  const long long SZ = L.sz, PX = L.px;
+  const float uEX = a.co.u[kEX], uEY = a.co.u[kEY], uEZ = a.co.u[kEZ];
+  const float uHX = a.co.u[kHX], uHY = a.co.u[kHY], uHZ = a.co.u[kHZ];
+  const int ntile = a.tiles_x * a.tiles_y;
+  const Q4 zero{{0.f, 0.f, 0.f, 0.f}};
+  bool failed = false;
+  const int tile = item % ntile, chunk = item / ntile;
+  const int gx0 = (tile % a.tiles_x) * kOX - 4;  // global i of loaded column 0
+  const int gy0 = (tile / a.tiles_x) * kOY - 2;  // global j of loaded row 0
+  const int k0 = chunk * a.chunk_z, k1 = min(k0 + a.chunk_z, L.nz);
+  const int kstart = k0 - 1;
+  const int nplanes = k1 - kstart;
+  const int cx = gx0 + L.ox, cy = gy0 + 2;     // tensor coordinates (column, row)
+
+  // this thread's quad; a quad with an active node lies inside its layout
+  // row (columns i <= nx + 2 < px - ox), so every predicated access is a
+  // whole 16-byte vector (a quad across i = nx stores the zeros its entries
+  // past the cells compute: zero input, zero coefficient)
+  const int gi = gx0 + 4 * q, gj = gy0 + row;
+  const bool inq = gj + 2 < L.ny + 4 && cx + 4 * q + 4 <= PX;  // the quad lies inside the arrays
+  const long long qoff = (long long)(gj + 2) * PX + cx + 4 * q;
+  const bool own_q = q >= 1 && q <= kQ - 2 && row >= 2 && row < kSY - 2 && gj < L.ny;
+  auto gidx = [&](int k) { return (long long)(k + 1) * SZ + qoff; };
+  auto word = [&](int k) -> unsigned { return ld_word_if(a.co.mask + gidx(k), inq); };
+  auto load_if = [&](const float* base, int k, bool p) -> Q4 { return ld4_if(base + gidx(k), p); };
+  // plane k into its slot (one thread): whole 64 x 32 boxes
+  auto issue = [&](int k) {
+    const int s = (k - kstart) % kSD;
+    asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+    bar_expect(&S.bar[s], Smem::slot_bytes);
+    tma3(&S.ez[s][0], tm_ez, cx, cy, k + 1, &S.bar[s]);
+    tma3(&S.hz[s][0], tm_hz, cx, cy, k + 1, &S.bar[s]);
+    if constexpr (MAT) {
+#pragma unroll
+      for (int c = 0; c < 6; ++c) tma3(&S.co[s][c][0][0], &tm_co->m[c], cx, cy, k + 1, &S.bar[s]);
+    }
+  };
+  if (tid == 0)
+    for (int k = kstart; k < kstart + min(kSD, nplanes); ++k) issue(k);
+  int issued = kstart + min(kSD, nplanes) - 1;  // last plane queued (the same in every thread)
+
+  // activity words of planes kstart .. kstart + 2 (m0 of the plane being
+  // worked on, m1, m2 of the next two); z-state and the register prefetch
+  // (plane k: hx, hy of k; ex, ey of k+1)
+  unsigned m0 = word(kstart), m1 = word(kstart + 1), m2 = word(kstart + 2);
+  Q4 ex0 = load_if(a.in[kEX], kstart, has(m0, kEX)), ey0 = load_if(a.in[kEY], kstart, has(m0, kEY));
+  Q4 hxc = load_if(a.in[kHX], kstart, has(m0, kHX)), hyc = load_if(a.in[kHY], kstart, has(m0, kHY));
+  Q4 ex1 = load_if(a.in[kEX], kstart + 1, has(m1, kEX)), ey1 = load_if(a.in[kEY], kstart + 1, has(m1, kEY));
+  Q4 hxp = zero, hyp = zero;
+  const bool line_row = a.b.on && gj == a.b.j0;
+  const bool line_q = line_row && a.b.i0 >= gi && a.b.i0 < gi + 4;  // the quad holds the bunch line node
+
+  for (int k = kstart; k < k1; ++k) {
+    const int s = (k - kstart) % kSD;
+    // every thread waits for the slot itself; the block decides at barrier
+    // (1) (a thread whose wait gave up computes on stale data until then,
+    // nothing is stored before it)
+    const bool ok = bar_wait(&S.bar[s], (phases >> s) & 1u);
+    // next plane's register inputs and the activity word three planes on, early
+    Q4 hxn_in, hyn_in, exn_in, eyn_in;
+    unsigned m3 = 0u;
+    const bool more = k + 1 < k1;
+    if (more) {
+      hxn_in = load_if(a.in[kHX], k + 1, has(m1, kHX));
+      hyn_in = load_if(a.in[kHY], k + 1, has(m1, kHY));
+      exn_in = load_if(a.in[kEX], k + 2, has(m2, kEX));
+      eyn_in = load_if(a.in[kEY], k + 2, has(m2, kEY));
+      if (k + 3 <= k1) m3 = word(k + 3);
+    }
+    // slot inputs: e_z, h_z of this quad and its neighbours
+    const float* sez = &S.ez[s][0];
+    const float* shz = &S.hz[s][0];
+    const Q4 ez = lds4(sez + row * kSX + 4 * q);
+    const Q4 ezU = row + 1 < kSY ? lds4(sez + (row + 1) * kSX + 4 * q) : zero;
+    const float ezR = q + 1 < kQ ? sez[row * kSX + 4 * q + 4] : 0.f;
+    const Q4 hz = lds4(shz + row * kSX + 4 * q);
+    const Q4 hzD = row >= 1 ? lds4(shz + (row - 1) * kSX + 4 * q) : zero;
+    const float hzL = q >= 1 ? shz[row * kSX + 4 * q - 1] : 0.f;
+    float cHX[4], cHY[4], cEZ[4], cEX[4], cEY[4], cHZ[4], dey[4], dex[4];
+    if constexpr (MAT) {  // per-entry coefficients from the slot
+      const Q4 c0 = lds4(&S.co[s][kEX][row][4 * q]), c1 = lds4(&S.co[s][kEY][row][4 * q]);
+      const Q4 c2 = lds4(&S.co[s][kEZ][row][4 * q]), c3 = lds4(&S.co[s][kHX][row][4 * q]);
+      const Q4 c4 = lds4(&S.co[s][kHY][row][4 * q]), c5 = lds4(&S.co[s][kHZ][row][4 * q]);
+#pragma unroll
+      for (int e = 0; e < 4; ++e) {
+        cEX[e] = c0.v[e];
+        cEY[e] = c1.v[e];
+        cEZ[e] = c2.v[e];
+        cHX[e] = c3.v[e];
+        cHY[e] = c4.v[e];
+        cHZ[e] = c5.v[e];
+      }
+    } else {  // one coefficient per component, switched by the activity bytes
+#pragma unroll
+      for (int e = 0; e < 4; ++e) {
+        const unsigned m = (m0 >> (8 * e)) & 0xFFu;
+        cEX[e] = (m & 1) ? uEX : 0.f;
+        cEY[e] = (m & 2) ? uEY : 0.f;
+        cEZ[e] = (m & 4) ? uEZ : 0.f;
+        cHX[e] = (m & 8) ? uHX : 0.f;
+        cHY[e] = (m & 16) ? uHY : 0.f;
+        cHZ[e] = (m & 32) ? uHZ : 0.f;
+      }
+    }
+    Q4 hxa, hya;
+#pragma unroll
+    for (int e = 0; e < 4; ++e) {
+      dey[e] = ey1.v[e] - ey0.v[e];
+      dex[e] = ex1.v[e] - ex0.v[e];
+      const float ezx = e < 3 ? ez.v[e + 1] : ezR;
+      hxa.v[e] = hxc.v[e] + cHX[e] * (dey[e] - (ezU.v[e] - ez.v[e]));   // U1
+      hya.v[e] = hyc.v[e] + cHY[e] * (-dex[e] + (ezx - ez.v[e]));      // U2
+    }
+    sts4(&S.x1[row][4 * q], hxa);
+    if (!__syncthreads_and(ok)) {  // (1) the slot is read and hx~ is out
+      // a copy did not land: raise the error word, wait (bounded) for the
+      // copies still in flight, stop
+      if (tid == 0) {
+        atomicExch(err, 1);
+        for (int kk = k; kk <= issued; ++kk) {
+          const int ss = (kk - kstart) % kSD;
+          bar_wait(&S.bar[ss], (phases >> ss) & 1u);
+        }
+      }
+      __syncthreads();
+      failed = true;
+      break;
+    }
+    phases ^= 1u << s;
+    if (k + kSD < k1) {
+      if (tid == 0) issue(k + kSD);
+      issued = k + kSD;
+    }
+    // S2: ez' = ez + 2a M^-1 (P_y^T hx~ - P_x^T hy~ - jj_z)
+    const Q4 hxaD = row >= 1 ? lds4(&S.x1[row - 1][4 * q]) : zero;
+    const float hyaL = left_of(hya.v[3], q);
+    float cur[4];
+#pragma unroll
+    for (int e = 0; e < 4; ++e) {
+      const float hyl = e > 0 ? hya.v[e - 1] : hyaL;
+      cur[e] = (hxaD.v[e] - hxa.v[e]) - (hyl - hya.v[e]);
+    }
+    if (line_q) {  // the bunch current on its line (one quad of a tile row)
+      const long long dd = (long long)k - (a.n + a.b.kshift) + a.b.c0;
+      if (dd >= -a.b.c0 && dd < a.b.c0) {
+        const float jj = a.b.J[dd + a.b.c0];
+#pragma unroll
+        for (int e = 0; e < 4; ++e)
+          if (gi + e == a.b.i0) cur[e] -= jj;
+      }
+    }
+    Q4 ezn;
+#pragma unroll
+    for (int e = 0; e < 4; ++e) ezn.v[e] = ez.v[e] + cEZ[e] * cur[e];   // U3
+    sts4(&S.x2[row][4 * q], ezn);
+    __syncthreads();  // (2)
+    // S3: hx', hy'
+    const Q4 eznU = row + 1 < kSY ? lds4(&S.x2[row + 1][4 * q]) : zero;
+    const float eznR = right_of(ezn.v[0], q);
+    Q4 hxn, hyn;
+#pragma unroll
+    for (int e = 0; e < 4; ++e) {
+      const float ezx = e < 3 ? ezn.v[e + 1] : eznR;
+      hxn.v[e] = hxa.v[e] + cHX[e] * (dey[e] - (eznU.v[e] - ezn.v[e]));  // U4
+      hyn.v[e] = hya.v[e] + cHY[e] * (-dex[e] + (ezx - ezn.v[e]));     // U5
+    }
+    const bool st = k >= k0 && own_q;
+    st4_if(a.out[kEZ] + gidx(k), ezn, st && has(m0, kEZ));
+    st4_if(a.out[kHX] + gidx(k), hxn, st && has(m0, kHX));
+    st4_if(a.out[kHY] + gidx(k), hyn, st && has(m0, kHY));
+    if (st) {
+      if (line_q && a.b.i0 < L.nx) {
+        const long long mm = (a.n + a.b.kshift) - k - a.b.c0;
+        if (mm >= a.b.m_min && mm <= a.b.m_max)
+        {
+          const int e = a.b.i0 - gi;  // the quad's entry on the bunch line (no indexed register array)
+          const float v = e == 0 ? ezn.v[0] : e == 1 ? ezn.v[1] : e == 2 ? ezn.v[2] : ezn.v[3];
+          a.b.W[mm - a.b.m_min] -= (double)v * a.b.inv_q;
+        }
+      }
+    }
+    // S4: ex~, ey~ with the new hx, hy of this plane and of the plane below
+    Q4 exa, eya;
+#pragma unroll
+    for (int e = 0; e < 4; ++e) {
+      const float hzl = e > 0 ? hz.v[e - 1] : hzL;
+      exa.v[e] = ex0.v[e] + cEX[e] * ((hyp.v[e] - hyn.v[e]) - (hzD.v[e] - hz.v[e]));   // U6
+      eya.v[e] = ey0.v[e] + cEY[e] * (-(hxp.v[e] - hxn.v[e]) + (hzl - hz.v[e]));       // U7
+    }
+    sts4(&S.x1[row][4 * q], exa);
+    __syncthreads();  // (3)
+    // S5: hz'
+    const Q4 exaU = row + 1 < kSY ? lds4(&S.x1[row + 1][4 * q]) : zero;
+    const float eyaR = right_of(eya.v[0], q);
+    Q4 hzn;
+#pragma unroll
+    for (int e = 0; e < 4; ++e) {
+      const float eyx = e < 3 ? eya.v[e + 1] : eyaR;
+      hzn.v[e] = hz.v[e] + cHZ[e] * ((exaU.v[e] - exa.v[e]) - (eyx - eya.v[e]));      // U8
+    }
+    sts4(&S.x2[row][4 * q], hzn);
+    __syncthreads();  // (4)
+    // S6: ex', ey'
+    const Q4 hznD = row >= 1 ? lds4(&S.x2[row - 1][4 * q]) : zero;
+    const float hznL = left_of(hzn.v[3], q);
+    Q4 exn, eyn;
+#pragma unroll
+    for (int e = 0; e < 4; ++e) {
+      const float hzl = e > 0 ? hzn.v[e - 1] : hznL;
+      exn.v[e] = exa.v[e] + cEX[e] * ((hyp.v[e] - hyn.v[e]) - (hznD.v[e] - hzn.v[e]));   // U9
+      eyn.v[e] = eya.v[e] + cEY[e] * (-(hxp.v[e] - hxn.v[e]) + (hzl - hzn.v[e]));       // U10
+    }
+    st4_if(a.out[kEX] + gidx(k), exn, st && has(m0, kEX));
+    st4_if(a.out[kEY] + gidx(k), eyn, st && has(m0, kEY));
+    st4_if(a.out[kHZ] + gidx(k), hzn, st && has(m0, kHZ));
+    // carry the z-state, take the prefetched inputs
+    hxp = hxn;
+    hyp = hyn;
+    ex0 = ex1;
+    ey0 = ey1;
+    m0 = m1;
+    m1 = m2;
+    m2 = m3;
+    if (more) {
+      hxc = hxn_in;
+      hyc = hyn_in;
+      ex1 = exn_in;
+      ey1 = eyn_in;
+    }
+  }
+  __syncthreads();  // every thread is done with the ring before the next item refills it
+  return !failed;
+}
+
 template <bool MAT>
 __global__ void __launch_bounds__(kSThreads, 1)
 fused_step_slab(const StepArgs<float> a, const __grid_constant__ CUtensorMap tm_ez,
@@ -168,22 +413,14 @@ fused_step_slab(const StepArgs<float> a, const __grid_constant__ CUtensorMap tm_
   constexpr int kSD = Smem::SD;
   extern __shared__ __align__(128) unsigned char slab_raw[];
   Smem& S = *reinterpret_cast<Smem*>(slab_raw);
-  const int tid = threadIdx.x, q = tid % kQ, row = tid / kQ;
+  const int tid = threadIdx.x;
   if (tid == 0) {
     for (int s = 0; s < kSD; ++s) bar_init(&S.bar[s], 1u);
   }
   asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
   __syncthreads();
   unsigned phases = 0;
-
-  const Layout L = a.L;
-  const long long SZ = L.sz, PX = L.px;
-  const float uEX = a.co.u[kEX], uEY = a.co.u[kEY], uEZ = a.co.u[kEZ];
-  const float uHX = a.co.u[kHX], uHY = a.co.u[kHY], uHZ = a.co.u[kHZ];
-  const int ntile = a.tiles_x * a.tiles_y;
-  const int nitems = a.work ? a.n_work : ntile * a.n_chunks;
-  const Q4 zero{{0.f, 0.f, 0.f, 0.f}};
-  bool failed = false;
+  const int nitems = a.work ? a.n_work : a.tiles_x * a.tiles_y * a.n_chunks;
 
   // Items in list order: the first per CTA by its index, then (with a
   // schedule counter) whichever item is next when the CTA gets free, fetched
@@ -191,238 +428,66 @@ fused_step_slab(const StepArgs<float> a, const __grid_constant__ CUtensorMap tm_
   // halo rows in L2) and CTAs that drew cheap items (much PEC) take more.
   const int G = gridDim.x;
   int wi = blockIdx.x, par = 0;
-  while (wi < nitems && !failed) {
+  bool ok = true;
+  while (wi < nitems && ok) {
     if (tid == 0 && sched) S.next[par] = G + atomicAdd(sched, 1);
     const int item = a.work ? a.work[wi] : wi;
-    const int tile = item % ntile, chunk = item / ntile;
-    const int gx0 = (tile % a.tiles_x) * kOX - 4;  // global i of loaded column 0
-    const int gy0 = (tile / a.tiles_x) * kOY - 2;  // global j of loaded row 0
-    const int k0 = chunk * a.chunk_z, k1 = min(k0 + a.chunk_z, L.nz);
-    const int kstart = k0 - 1;
-    const int nplanes = k1 - kstart;
-    const int cx = gx0 + L.ox, cy = gy0 + 2;     // tensor coordinates (column, row)
-
-    // this thread's quad; a quad with an active node lies inside its layout
-    // row (columns i <= nx + 2 < px - ox), so every predicated access is a
-    // whole 16-byte vector (a quad across i = nx stores the zeros its entries
-    // past the cells compute: zero input, zero coefficient)
-    const int gi = gx0 + 4 * q, gj = gy0 + row;
-    const bool inq = gj + 2 < L.ny + 4 && cx + 4 * q + 4 <= PX;  // the quad lies inside the arrays
-    const long long qoff = (long long)(gj + 2) * PX + cx + 4 * q;
-    const bool own_q = q >= 1 && q <= kQ - 2 && row >= 2 && row < kSY - 2 && gj < L.ny;
-    auto gidx = [&](int k) { return (long long)(k + 1) * SZ + qoff; };
-    auto word = [&](int k) -> unsigned { return ld_word_if(a.co.mask + gidx(k), inq); };
-    auto load_if = [&](const float* base, int k, bool p) -> Q4 { return ld4_if(base + gidx(k), p); };
-    // plane k into its slot (one thread): whole 64 x 32 boxes
-    auto issue = [&](int k) {
-      const int s = (k - kstart) % kSD;
-      asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
-      bar_expect(&S.bar[s], Smem::slot_bytes);
-      tma3(&S.ez[s][0], &tm_ez, cx, cy, k + 1, &S.bar[s]);
-      tma3(&S.hz[s][0], &tm_hz, cx, cy, k + 1, &S.bar[s]);
-      if constexpr (MAT) {
-#pragma unroll
-        for (int c = 0; c < 6; ++c) tma3(&S.co[s][c][0][0], &tm_co.m[c], cx, cy, k + 1, &S.bar[s]);
-      }
-    };
-    if (tid == 0)
-      for (int k = kstart; k < kstart + min(kSD, nplanes); ++k) issue(k);
-    int issued = kstart + min(kSD, nplanes) - 1;  // last plane queued (the same in every thread)
-
-    // activity words of planes kstart .. kstart + 2 (m0 of the plane being
-    // worked on, m1, m2 of the next two); z-state and the register prefetch
-    // (plane k: hx, hy of k; ex, ey of k+1)
-    unsigned m0 = word(kstart), m1 = word(kstart + 1), m2 = word(kstart + 2);
-    Q4 ex0 = load_if(a.in[kEX], kstart, has(m0, kEX)), ey0 = load_if(a.in[kEY], kstart, has(m0, kEY));
-    Q4 hxc = load_if(a.in[kHX], kstart, has(m0, kHX)), hyc = load_if(a.in[kHY], kstart, has(m0, kHY));
-    Q4 ex1 = load_if(a.in[kEX], kstart + 1, has(m1, kEX)), ey1 = load_if(a.in[kEY], kstart + 1, has(m1, kEY));
-    Q4 hxp = zero, hyp = zero;
-    const bool line_row = a.b.on && gj == a.b.j0;
-    const bool line_q = line_row && a.b.i0 >= gi && a.b.i0 < gi + 4;  // the quad holds the bunch line node
-
-    for (int k = kstart; k < k1; ++k) {
-      const int s = (k - kstart) % kSD;
-      // every thread waits for the slot itself; the block decides at barrier
-      // (1) (a thread whose wait gave up computes on stale data until then,
-      // nothing is stored before it)
-      const bool ok = bar_wait(&S.bar[s], (phases >> s) & 1u);
-      // next plane's register inputs and the activity word three planes on, early
-      Q4 hxn_in, hyn_in, exn_in, eyn_in;
-      unsigned m3 = 0u;
-      const bool more = k + 1 < k1;
-      if (more) {
-        hxn_in = load_if(a.in[kHX], k + 1, has(m1, kHX));
-        hyn_in = load_if(a.in[kHY], k + 1, has(m1, kHY));
-        exn_in = load_if(a.in[kEX], k + 2, has(m2, kEX));
-        eyn_in = load_if(a.in[kEY], k + 2, has(m2, kEY));
-        if (k + 3 <= k1) m3 = word(k + 3);
-      }
-      // slot inputs: e_z, h_z of this quad and its neighbours
-      const float* sez = &S.ez[s][0];
-      const float* shz = &S.hz[s][0];
-      const Q4 ez = lds4(sez + row * kSX + 4 * q);
-      const Q4 ezU = row + 1 < kSY ? lds4(sez + (row + 1) * kSX + 4 * q) : zero;
-      const float ezR = q + 1 < kQ ? sez[row * kSX + 4 * q + 4] : 0.f;
-      const Q4 hz = lds4(shz + row * kSX + 4 * q);
-      const Q4 hzD = row >= 1 ? lds4(shz + (row - 1) * kSX + 4 * q) : zero;
-      const float hzL = q >= 1 ? shz[row * kSX + 4 * q - 1] : 0.f;
-      float cHX[4], cHY[4], cEZ[4], cEX[4], cEY[4], cHZ[4], dey[4], dex[4];
-      if constexpr (MAT) {  // per-entry coefficients from the slot
-        const Q4 c0 = lds4(&S.co[s][kEX][row][4 * q]), c1 = lds4(&S.co[s][kEY][row][4 * q]);
-        const Q4 c2 = lds4(&S.co[s][kEZ][row][4 * q]), c3 = lds4(&S.co[s][kHX][row][4 * q]);
-        const Q4 c4 = lds4(&S.co[s][kHY][row][4 * q]), c5 = lds4(&S.co[s][kHZ][row][4 * q]);
-#pragma unroll
-        for (int e = 0; e < 4; ++e) {
-          cEX[e] = c0.v[e];
-          cEY[e] = c1.v[e];
-          cEZ[e] = c2.v[e];
-          cHX[e] = c3.v[e];
-          cHY[e] = c4.v[e];
-          cHZ[e] = c5.v[e];
-        }
-      } else {  // one coefficient per component, switched by the activity bytes
-#pragma unroll
-        for (int e = 0; e < 4; ++e) {
-          const unsigned m = (m0 >> (8 * e)) & 0xFFu;
-          cEX[e] = (m & 1) ? uEX : 0.f;
-          cEY[e] = (m & 2) ? uEY : 0.f;
-          cEZ[e] = (m & 4) ? uEZ : 0.f;
-          cHX[e] = (m & 8) ? uHX : 0.f;
-          cHY[e] = (m & 16) ? uHY : 0.f;
-          cHZ[e] = (m & 32) ? uHZ : 0.f;
-        }
-      }
-      Q4 hxa, hya;
-#pragma unroll
-      for (int e = 0; e < 4; ++e) {
-        dey[e] = ey1.v[e] - ey0.v[e];
-        dex[e] = ex1.v[e] - ex0.v[e];
-        const float ezx = e < 3 ? ez.v[e + 1] : ezR;
-        hxa.v[e] = hxc.v[e] + cHX[e] * (dey[e] - (ezU.v[e] - ez.v[e]));   // U1
-        hya.v[e] = hyc.v[e] + cHY[e] * (-dex[e] + (ezx - ez.v[e]));      // U2
-      }
-      sts4(&S.x1[row][4 * q], hxa);
-      if (!__syncthreads_and(ok)) {  // (1) the slot is read and hx~ is out
-        // a copy did not land: raise the error word, wait (bounded) for the
-        // copies still in flight, stop
-        if (tid == 0) {
-          atomicExch(err, 1);
-          for (int kk = k; kk <= issued; ++kk) {
-            const int ss = (kk - kstart) % kSD;
-            bar_wait(&S.bar[ss], (phases >> ss) & 1u);
-          }
-        }
-        __syncthreads();
-        failed = true;
-        break;
-      }
-      phases ^= 1u << s;
-      if (k + kSD < k1) {
-        if (tid == 0) issue(k + kSD);
-        issued = k + kSD;
-      }
-      // S2: ez' = ez + 2a M^-1 (P_y^T hx~ - P_x^T hy~ - jj_z)
-      const Q4 hxaD = row >= 1 ? lds4(&S.x1[row - 1][4 * q]) : zero;
-      const float hyaL = left_of(hya.v[3], q);
-      float cur[4];
-#pragma unroll
-      for (int e = 0; e < 4; ++e) {
-        const float hyl = e > 0 ? hya.v[e - 1] : hyaL;
-        cur[e] = (hxaD.v[e] - hxa.v[e]) - (hyl - hya.v[e]);
-      }
-      if (line_q) {  // the bunch current on its line (one quad of a tile row)
-        const long long dd = (long long)k - (a.n + a.b.kshift) + a.b.c0;
-        if (dd >= -a.b.c0 && dd < a.b.c0) {
-          const float jj = a.b.J[dd + a.b.c0];
-#pragma unroll
-          for (int e = 0; e < 4; ++e)
-            if (gi + e == a.b.i0) cur[e] -= jj;
-        }
-      }
-      Q4 ezn;
-#pragma unroll
-      for (int e = 0; e < 4; ++e) ezn.v[e] = ez.v[e] + cEZ[e] * cur[e];   // U3
-      sts4(&S.x2[row][4 * q], ezn);
-      __syncthreads();  // (2)
-      // S3: hx', hy'
-      const Q4 eznU = row + 1 < kSY ? lds4(&S.x2[row + 1][4 * q]) : zero;
-      const float eznR = right_of(ezn.v[0], q);
-      Q4 hxn, hyn;
-#pragma unroll
-      for (int e = 0; e < 4; ++e) {
-        const float ezx = e < 3 ? ezn.v[e + 1] : eznR;
-        hxn.v[e] = hxa.v[e] + cHX[e] * (dey[e] - (eznU.v[e] - ezn.v[e]));  // U4
-        hyn.v[e] = hya.v[e] + cHY[e] * (-dex[e] + (ezx - ezn.v[e]));     // U5
-      }
-      const bool st = k >= k0 && own_q;
-      st4_if(a.out[kEZ] + gidx(k), ezn, st && has(m0, kEZ));
-      st4_if(a.out[kHX] + gidx(k), hxn, st && has(m0, kHX));
-      st4_if(a.out[kHY] + gidx(k), hyn, st && has(m0, kHY));
-      if (st) {
-        if (line_q && a.b.i0 < L.nx) {
-          const long long mm = (a.n + a.b.kshift) - k - a.b.c0;
-          if (mm >= a.b.m_min && mm <= a.b.m_max)
-          {
-            const int e = a.b.i0 - gi;  // the quad's entry on the bunch line (no indexed register array)
-            const float v = e == 0 ? ezn.v[0] : e == 1 ? ezn.v[1] : e == 2 ? ezn.v[2] : ezn.v[3];
-            a.b.W[mm - a.b.m_min] -= (double)v * a.b.inv_q;
-          }
-        }
-      }
-      // S4: ex~, ey~ with the new hx, hy of this plane and of the plane below
-      Q4 exa, eya;
-#pragma unroll
-      for (int e = 0; e < 4; ++e) {
-        const float hzl = e > 0 ? hz.v[e - 1] : hzL;
-        exa.v[e] = ex0.v[e] + cEX[e] * ((hyp.v[e] - hyn.v[e]) - (hzD.v[e] - hz.v[e]));   // U6
-        eya.v[e] = ey0.v[e] + cEY[e] * (-(hxp.v[e] - hxn.v[e]) + (hzl - hz.v[e]));       // U7
-      }
-      sts4(&S.x1[row][4 * q], exa);
-      __syncthreads();  // (3)
-      // S5: hz'
-      const Q4 exaU = row + 1 < kSY ? lds4(&S.x1[row + 1][4 * q]) : zero;
-      const float eyaR = right_of(eya.v[0], q);
-      Q4 hzn;
-#pragma unroll
-      for (int e = 0; e < 4; ++e) {
-        const float eyx = e < 3 ? eya.v[e + 1] : eyaR;
-        hzn.v[e] = hz.v[e] + cHZ[e] * ((exaU.v[e] - exa.v[e]) - (eyx - eya.v[e]));      // U8
-      }
-      sts4(&S.x2[row][4 * q], hzn);
-      __syncthreads();  // (4)
-      // S6: ex', ey'
-      const Q4 hznD = row >= 1 ? lds4(&S.x2[row - 1][4 * q]) : zero;
-      const float hznL = left_of(hzn.v[3], q);
-      Q4 exn, eyn;
-#pragma unroll
-      for (int e = 0; e < 4; ++e) {
-        const float hzl = e > 0 ? hzn.v[e - 1] : hznL;
-        exn.v[e] = exa.v[e] + cEX[e] * ((hyp.v[e] - hyn.v[e]) - (hznD.v[e] - hzn.v[e]));   // U9
-        eyn.v[e] = eya.v[e] + cEY[e] * (-(hxp.v[e] - hxn.v[e]) + (hzl - hzn.v[e]));       // U10
-      }
-      st4_if(a.out[kEX] + gidx(k), exn, st && has(m0, kEX));
-      st4_if(a.out[kEY] + gidx(k), eyn, st && has(m0, kEY));
-      st4_if(a.out[kHZ] + gidx(k), hzn, st && has(m0, kHZ));
-      // carry the z-state, take the prefetched inputs
-      hxp = hxn;
-      hyp = hyn;
-      ex0 = ex1;
-      ey0 = ey1;
-      m0 = m1;
-      m1 = m2;
-      m2 = m3;
-      if (more) {
-        hxc = hxn_in;
-        hyc = hyn_in;
-        ex1 = exn_in;
-        ey1 = eyn_in;
-      }
-    }
-    __syncthreads();  // every thread is done with the ring before the next item refills it
+    ok = slab_item<MAT>(a, &tm_ez, &tm_hz, &tm_co, item, S, phases, err);
     wi = sched ? S.next[par] : wi + G;
     par ^= 1;
   }
   // the last CTA to finish resets the schedule counter for the next launch
+  if (tid == 0 && sched) {
+    __threadfence();
+    if (atomicAdd(sched + 1, 1) == G - 1) {
+      atomicExch(sched, 0);
+      atomicExch(sched + 1, 0);
+    }
+  }
+}
+
+// Batches: one launch steps every active member (one material, float32);
+// work = (member, item) pairs in member order, the member's arguments and
+// tensor maps (of the set it reads) from device memory.
+__global__ void __launch_bounds__(kSThreads, 1)
+fused_step_slab_batch(const BatchMember<float>* __restrict__ members, const SlabBatchMaps* __restrict__ maps,
+                      const int2* __restrict__ work, int n_work, int* err, int* sched) {
+  using Smem = SlabSmem<false>;
+  constexpr int kSD = Smem::SD;
+  extern __shared__ __align__(128) unsigned char slab_raw[];
+  Smem& S = *reinterpret_cast<Smem*>(slab_raw);
+  const int tid = threadIdx.x;
+  if (tid == 0) {
+    for (int s = 0; s < kSD; ++s) bar_init(&S.bar[s], 1u);
+  }
+  asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+  __syncthreads();
+  unsigned phases = 0;
+  const int G = gridDim.x;
+  int wi = blockIdx.x, par = 0;
+  bool ok = true;
+  while (wi < n_work && ok) {
+    if (tid == 0 && sched) S.next[par] = G + atomicAdd(sched, 1);
+    const int2 w = work[wi];
+    const BatchMember<float>& mb = members[w.x];
+    if (mb.active) {
+      const int cur = mb.cur;
+      const CUtensorMap* mez = reinterpret_cast<const CUtensorMap*>(maps[w.x].ez[cur]);
+      const CUtensorMap* mhz = reinterpret_cast<const CUtensorMap*>(maps[w.x].hz[cur]);
+      if (tid == 0) {  // the maps were written before the launch, through the generic proxy
+        asm volatile("fence.proxy.tensormap::generic.acquire.gpu [%0], 128;" ::"l"(mez) : "memory");
+        asm volatile("fence.proxy.tensormap::generic.acquire.gpu [%0], 128;" ::"l"(mhz) : "memory");
+      }
+      ok = slab_item<false>(mb.a, mez, mhz, nullptr, w.y, S, phases, err);
+    } else {
+      // an item of a member past its limit: no work, but the ticket thread 0
+      // wrote above must be visible before every thread reads it (slab_item
+      // ends with a block barrier; this branch needs its own)
+      __syncthreads();
+    }
+    wi = sched ? S.next[par] : wi + G;
+    par ^= 1;
+  }
   if (tid == 0 && sched) {
     __threadfence();
     if (atomicAdd(sched + 1, 1) == G - 1) {
@@ -514,6 +579,32 @@ cudaError_t launch_slab(const StepArgs<float>& a, const SlabMaps& m, int cur, in
   return cudaGetLastError();
 }
 }  // namespace
+
+cudaError_t launch_fused_slab_batch(BatchMember<float>* members, const SlabBatchMaps* maps, int n_members,
+                                    const int2* work, int n_work, int* err, int* sched, int nz_max,
+                                    cudaStream_t st) {
+  static int sms = 0;
+  const size_t smem = sizeof(SlabSmem<false>);
+  if (!sms) {
+    int dev = 0;
+    cudaError_t e = cudaGetDevice(&dev);
+    if (e == cudaSuccess) e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    if (e == cudaSuccess)
+      e = cudaFuncSetAttribute(fused_step_slab_batch, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e != cudaSuccess) {
+      sms = 0;
+      return e;
+    }
+  }
+  if (n_work > 0) {
+    fused_step_slab_batch<<<std::min(n_work, sms), kSThreads, smem, st>>>(members, maps, work, n_work, err, sched);
+    cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess) return e;
+  }
+  cudaError_t e = launch_transverse_after_batch_step<float>(members, n_members, nz_max, st);
+  if (e != cudaSuccess) return e;
+  return launch_batch_advance<float>(members, n_members, st);
+}
 
 cudaError_t launch_fused_slab_step(const StepArgs<float>& a, const SlabMaps& m, int cur, int* err, int* sched,
                                    cudaStream_t st) {

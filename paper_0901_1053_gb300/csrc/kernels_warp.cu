@@ -563,6 +563,7 @@ __global__ void batch_advance(BatchMember<T>* members, int n) {
     a.in[c] = t;
   }
   a.n += 1;
+  members[i].cur ^= 1;
   if (a.n >= members[i].limit) members[i].active = 0;
 }
 
@@ -868,6 +869,14 @@ cudaError_t launch_fused_warp_batch(const BatchMember<T>* members, int n_members
                                                             n_members);
   return cudaGetLastError();
 }
+
+template <typename T>
+cudaError_t launch_batch_advance(BatchMember<T>* members, int n_members, cudaStream_t st) {
+  batch_advance<T><<<(n_members + 127) / 128, 128, 0, st>>>(members, n_members);
+  return cudaGetLastError();
+}
+template cudaError_t launch_batch_advance<float>(BatchMember<float>*, int, cudaStream_t);
+template cudaError_t launch_batch_advance<double>(BatchMember<double>*, int, cudaStream_t);
 
 template cudaError_t launch_fused_warp_batch<float>(const BatchMember<float>*, int, const int2*, int,
                                                     int, int, cudaStream_t);

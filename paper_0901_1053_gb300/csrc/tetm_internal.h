@@ -108,7 +108,7 @@ struct BatchMember {
   StepArgs<T> a;
   long long limit;  // last step index + 1 this member may reach
   int active;       // 0 once a.n == limit
-  int pad;
+  int cur;          // the field set a.in points to (0 or 1)
 };
 
 // ---- launchers (kernels_step.cu) -----------------------------------------
@@ -126,6 +126,10 @@ bool warp_shape_ok(int tile_x, int tile_y);
 template <typename T>
 cudaError_t launch_fused_warp_batch(const BatchMember<T>* members, int n_members, const int2* work,
                                     int n_work, int tile_y, int nz_max, cudaStream_t st);
+// after a batch step: every active member swaps its sets, counts the step
+// and retires at its limit
+template <typename T>
+cudaError_t launch_batch_advance(BatchMember<T>* members, int n_members, cudaStream_t st);
 
 // ---- block-tiled float32 step with tensor staging (kernels_slab.cu): tile
 // 56 x 28, one CTA of 512 threads per SM ----------------------------------
@@ -139,6 +143,18 @@ struct SlabMaps {  // tensor maps (CUtensorMap) of e_z and h_z of both field set
 bool slab_shape_ok(int tile_x, int tile_y);
 // co: the six per-entry coefficient arrays, or nullptr (one material)
 int build_slab_maps(SlabMaps* m, void* const ez[2], void* const hz[2], void* const co[6], const Layout& L);
+// Tensor maps of one batch member's e_z, h_z (both field sets), in device
+// memory for the batched slab kernel (one material).
+struct SlabBatchMaps {
+  alignas(128) unsigned char ez[2][128];
+  alignas(128) unsigned char hz[2][128];
+};
+// one step of every active member of a float32 batch on the slab kernel
+// (work = (member, item) pairs, sched as below), the transverse wakes, then
+// the device-side advance
+cudaError_t launch_fused_slab_batch(BatchMember<float>* members, const SlabBatchMaps* maps, int n_members,
+                                    const int2* work, int n_work, int* err, int* sched, int nz_max,
+                                    cudaStream_t st);
 // sched: two ints of device memory, zero before the first launch, that the
 // kernel's dynamic schedule uses and leaves zero (nullptr: static order)
 cudaError_t launch_fused_slab_step(const StepArgs<float>& a, const SlabMaps& m, int cur, int* err, int* sched,

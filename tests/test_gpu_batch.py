@@ -24,21 +24,24 @@ def _mix(precision):
     return ws
 
 
-@pytest.mark.parametrize("precision,graph_steps,tile_y", [("fp32", 8, 20), ("fp32", 0, 12),
-                                                          ("fp64", 16, 20), ("fp64", 4, 8)])
-def test_batch_members_equal_solo_runs_bitwise(tetm, precision, graph_steps, tile_y):
+@pytest.mark.parametrize("precision,graph_steps,tiling", [("fp32", 8, (28, 20, 16)), ("fp32", 0, (28, 12, 16)),
+                                                          ("fp32", 8, (56, 28, 16)), ("fp32", 0, (56, 28, 9)),
+                                                          ("fp64", 16, (28, 20, 16)), ("fp64", 4, (28, 8, 16))])
+def test_batch_members_equal_solo_runs_bitwise(tetm, precision, graph_steps, tiling):
+    """Warp-tiled batches (tile width 28) and, for float32 with the slab
+    kernel's 56 x 28 tile, batched slab kernels."""
     ws = _mix(precision)
     solo = []
     for w in ws:
         s = tetm.Solver.from_workload(w)
-        s.set_tiling(28, tile_y, 16)
+        s.set_tiling(*tiling)
         s.step(w.steps)
         solo.append((s.wake()[0], s.get("ez"), s.get("hy"), s.get("ex")))
         s.close()
     members = []
     for w in ws:
         s = tetm.Solver.from_workload(w)
-        s.set_tiling(28, tile_y, 16)
+        s.set_tiling(*tiling)
         members.append(s)
     b = tetm.Batch(members, [w.steps for w in ws], graph_steps=graph_steps)
     most = max(w.steps for w in ws)
@@ -82,3 +85,28 @@ def test_batch_rejects_mixed_precision(tetm):
     assert e.value.code == tetm.TETM_E_ARG
     with pytest.raises(tetm.TetmError):
         tetm.Batch([a, a])
+
+
+def test_slab_batch_with_many_retired_members_equals_solo_runs(tetm):
+    """Float32 slab-kernel batch of twelve solves whose step limits spread
+    from 6 to 90: most work items of the later launches belong to members
+    that have retired; every member still equals its solo run bit for bit."""
+    ws = wl.batch_solves(count=12, seed=77, n_lo=16, n_hi=40, precision="fp32")
+    for i, w in enumerate(ws):
+        w.steps = 6 + 7 * i
+    solo = []
+    for w in ws:
+        s = tetm.Solver.from_workload(w)
+        s.step(w.steps)
+        solo.append((s.wake()[0], s.get("ez"), s.get("hx")))
+        s.close()
+    members = [tetm.Solver.from_workload(w) for w in ws]
+    assert members[0].info()["tile_x"] == 56                 # the float32 default: the slab kernel
+    b = tetm.Batch(members, [w.steps for w in ws], graph_steps=8)
+    b.step(95)
+    b.sync()
+    for s, w, ref in zip(members, ws, solo):
+        assert s.info()["step"] == w.steps
+        for a, r in zip((s.wake()[0], s.get("ez"), s.get("hx")), ref):
+            assert np.array_equal(a, r)
+    b.close()
