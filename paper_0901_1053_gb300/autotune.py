@@ -151,8 +151,8 @@ class Autotuner:
              batch: bool = False) -> Shape:
         """materials: the solve has eps/mu arrays (per-entry coefficients run on
         the warp-tiled kernel, tile_x = 28, and the float32 slab kernel, 56 x 28);
-        batch: the shape is for a batch of solves (the batched launch is the
-        warp-tiled kernel, tile_x = 28)."""
+        batch: the shape is for a batch of solves (batched launches run the
+        warp-tiled kernel, tile_x = 28, and in float32 the slab kernel)."""
         precision = precision or w.precision
         materials = materials or eps_r is not None
         k = self.key(w, precision) + ("|materials" if materials else "") + ("|batch" if batch else "")
@@ -166,7 +166,7 @@ class Autotuner:
         if materials:
             cands = [c for c in cands if c[0] == 28 or (c[0], c[1]) == (56, 28)]
         if batch:
-            cands = [c for c in cands if c[0] == 28]
+            cands = [c for c in cands if c[0] == 28 or (precision == "fp32" and (c[0], c[1]) == (56, 28))]
         times = self.measure(w, precision, cands, eps_r=eps_r)
         best = min(times, key=times.get)
         self.cache[k] = list(best)
