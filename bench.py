@@ -79,6 +79,7 @@ def parse_args():
                         "start) and report every wake's error against it")
     p.add_argument("--requests", type=int, default=2000, help="serve: requests in the stream")
     p.add_argument("--rate", type=float, default=40.0, help="serve: mean arrivals per second")
+    p.add_argument("--round-steps", type=int, default=16, help="serve: steps per batch call")
     p.add_argument("--solves", type=int, default=64, help="batch: number of solves")
     p.add_argument("--precision", default=None, choices=[None, "fp32", "fp64"])
     p.add_argument("--balance-every", type=int, default=250)
@@ -611,19 +612,35 @@ def run_batch_mode(args):
 def run_serve_mode(args):
     """Poisson stream of solve requests (N ~ U{48..256}, N x N x 4N, pipe /
     cavity / collimator, sigma ~ U[3,10] dz) served with continuous batching
-    under a 150 GB device-memory budget."""
+    under a 150 GB device-memory budget: a 64-slot batch advanced in calls of
+    round_steps steps, geometry and solve creation and the read-back of
+    finished wakes on two worker threads."""
     import numpy as np
+    import torch
     from paper_0901_1053_gb300 import workloads as wl, tetm
     from paper_0901_1053_gb300.serve import GpuBackend, Server, latency_stats
     from paper_0901_1053_gb300.autotune import Autotuner
     rank, world, local = dist_env()
     if rank != 0:
         return 0
+    torch.cuda.set_device(local)
     reqs = wl.request_stream(count=args.requests, rate=args.rate)
     probe = max(reqs[:32], key=lambda r: r.n).workload("fp32")
-    tiling = Autotuner().tune(probe, "fp32", batch=True)
-    srv = Server(GpuBackend("fp32", tiling), hbm_budget=150e9, max_slots=64, round_steps=64)
-    res = srv.run_stream(reqs, lambda r: r.workload("fp32"))
+    tiling = (tuple(int(x) for x in args.tiling.split(",")) if args.tiling
+              else Autotuner().tune(probe, "fp32", batch=True))
+    rs = args.round_steps
+    be = GpuBackend("fp32", tiling, max_slots=64, round_steps=rs, pool_bytes=150e9)
+    srv = Server(be, hbm_budget=150e9, max_slots=64, round_steps=rs, queue_ahead=2, workers=2)
+    try:
+        uuid = str(torch.cuda.get_device_properties(local).uuid)
+    except Exception:
+        uuid = None
+    clocks = ClockSampler(uuid)
+    clocks.start()
+    res = srv.run_stream(reqs, lambda r: r.spec("fp32"))
+    clk = clocks.stop()
+    srv.close()
+    be.close()
     st = latency_stats(res)
     # accuracy of a sample of served wakes against the FP64 path
     errs = []
@@ -633,17 +650,21 @@ def run_serve_mode(args):
         s.step(w.steps)
         errs.append(_rel(res[r.rid].wake, s.wake()[0]))
         s.close()
+    mk = st.get("makespan_s")
     line = {"metric": "served solves/s", "value": st.get("solves_per_s"), "unit": "solves/s",
             "n_gpus": 1, "higher_is_better": True, "vs_baseline": None, "dtype": "f32",
             "data": "synthetic",
             "config": {"workload": "serve_poisson_%d_at_%g_per_s_seed9011054" % (args.requests, args.rate),
-                       "hbm_budget_gb": 150, "max_slots": 64, "round_steps": 64,
-                       "tiling": list(tiling)},
+                       "hbm_budget_gb": 150, "max_slots": 64, "round_steps": rs, "queue_ahead": 2,
+                       "workers": 2, "tiling": list(tiling)},
             "latency": {"p50_s": st.get("p50_s"), "p99_s": st.get("p99_s"), "mean_s": st.get("mean_s")},
-            "gcell_updates_per_s": st.get("cell_steps", 0) / st["makespan_s"] / 1e9 if st.get("makespan_s") else None,
-            "max_active": srv.max_active, "rounds": srv.rounds, "gpu_busy_s": srv.busy_s,
-            "makespan_s": st.get("makespan_s"), "status_counts": {k: st[k] for k in ("ok", "rejected", "cancelled", "error")},
-            "max_wake_err_vs_fp64_rel_peak_sample6": max(errs) if errs else None}
+            "gcell_updates_per_s": st.get("cell_steps", 0) / mk / 1e9 if mk else None,
+            "max_active": srv.max_active, "rounds": srv.rounds,
+            "makespan_s": mk, "gpu_busy_s": srv.busy_s, "idle_no_request_s": srv.idle_s,
+            "gpu_idle_with_requests_s": (mk - srv.busy_s - srv.idle_s) if mk else None,
+            "status_counts": {k: st[k] for k in ("ok", "rejected", "cancelled", "error")},
+            "max_wake_err_vs_fp64_rel_peak_sample6": max(errs) if errs else None,
+            "clocks": clk}
     print(json.dumps(line), flush=True)
     return 0
 

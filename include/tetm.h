@@ -108,6 +108,22 @@ typedef struct tetm_solver tetm_solver;
 int tetm_create(const tetm_grid* g, const double* eps_r, const double* mu_r, const uint8_t* pec,
                 tetm_solver** out);
 
+/* tetm_create with the solve's work, its creation included, queued on
+ * `stream` (a cudaStream_t; NULL = the legacy default stream, as
+ * tetm_create). Creating on a non-blocking stream from another host thread
+ * does not wait for, or hold up, work on other streams (a running batch).
+ * Device memory of every solve comes from a stream-ordered pool of the
+ * library (one per device): allocations and releases are queued on the
+ * solve's stream and never wait for the whole device. */
+int tetm_create_on_stream(const tetm_grid* g, const double* eps_r, const double* mu_r, const uint8_t* pec,
+                          void* stream, tetm_solver** out);
+
+/* Bytes of released device memory the library's pool keeps for reuse
+ * instead of returning them to the device (default 0: everything is
+ * returned at the next synchronization). A server that creates and
+ * destroys solves continuously sets its device-memory budget here. */
+int tetm_pool_reserve(uint64_t bytes);
+
 /* Rigid ultra-relativistic Gaussian bunch (Sec. 3 and Sec. 5): RMS length
  * sigma_z [m] > 0, charge [C] != 0, moving at c along the z-line through
  * node (i0, j0), 1 <= i0 <= nx-1, 1 <= j0 <= ny-1. The line density is
@@ -385,6 +401,43 @@ int tetm_batch_info(tetm_batch* b, int32_t* n_members, int32_t* n_active, int32_
 
 /* Release the batch (synchronizes); members become independent again. */
 void tetm_batch_destroy(tetm_batch* b);
+
+/* Slot table: an empty batch of `capacity` >= 1 slots for members of one
+ * precision (TETM_FP32 / TETM_FP64) on one tile (tile_x, tile_y: 56 x 28
+ * selects the float32 slab kernel; otherwise tile_x = 28 and tile_y one of
+ * the warp-tiled kernel's heights). Members join and leave between calls of
+ * tetm_batch_step without rebuilding the batch: joining writes the member's
+ * descriptor into a free slot and leaving clears the slot's active flag,
+ * both queued on the batch's stream, and the combined work list is uploaded
+ * before the next step (stream-ordered, from pinned host memory). The
+ * captured graph is kept across membership changes; it is captured again
+ * only when the work list outgrows its device buffer or a member needs a
+ * larger transverse-wake grid. */
+int tetm_batch_create_slots(int32_t capacity, int32_t precision, int32_t tile_x, int32_t tile_y,
+                            int32_t graph_steps, tetm_batch** out);
+
+/* Join: solve s (same precision, one uniform material, TE/TM scheme, not a
+ * z-slab, not in a batch: TETM_E_ARG / TETM_E_UNSUPPORTED) takes a free
+ * slot (TETM_E_STATE when all are taken; *slot, which may be NULL, receives
+ * its index) and advances with the batch until its step counter reaches
+ * step_limit (< 0: no limit). The batch's stream first waits for the work
+ * queued on s's stream (its creation); the host does not wait. s takes the
+ * batch's tile (its work list is rebuilt if it had another). */
+int tetm_batch_add(tetm_batch* b, tetm_solver* s, int64_t step_limit, int32_t* slot);
+
+/* Leave: s (a member, else TETM_E_ARG) gives up its slot after the steps
+ * queued so far; s's stream then waits for them, so reads and tetm_destroy
+ * queued on s see its final state. The host does not wait. */
+int tetm_batch_remove(tetm_batch* b, tetm_solver* s);
+
+/* Wait until at most max_pending >= 0 tetm_batch_step calls are still
+ * unfinished on the device (0: all done), bounding how far the host queues
+ * ahead of the GPU. *busy_s (may be NULL) receives the device time of the
+ * batch's finished calls so far (from events bracketing each call on the
+ * batch's stream: time the GPU spent on the batch, not idle gaps between
+ * calls). Calls are tracked in a ring of 64: a 65th unfinished call first
+ * waits for the oldest. */
+int tetm_batch_wait(tetm_batch* b, int32_t max_pending, double* busy_s);
 
 /* Static description of a return code. */
 /* Measured fused multiply-add rate of the current device in TFLOP/s (2 flops

@@ -7,6 +7,7 @@
 #include <string.h>
 
 #include <algorithm>
+#include <mutex>
 #include <new>
 #include <vector>
 
@@ -236,7 +237,7 @@ int cuda_fail(cudaError_t e) {
   } while (0)
 
 int dalloc(tetm_solver* s, void** p, size_t bytes) {
-  cudaError_t e = cudaMalloc(p, bytes);
+  cudaError_t e = dev_alloc(p, bytes, s->stream);
   if (e != cudaSuccess) {
     *p = nullptr;
     cudaGetLastError();
@@ -257,6 +258,48 @@ double cdt_of(const tetm_grid* g) { return g->cdt > 0 ? g->cdt : g->dz; }
 
 }  // namespace
 
+namespace {
+std::mutex g_pool_mu;
+cudaMemPool_t g_pool[64];
+uint64_t g_pool_keep = 0;
+
+cudaMemPool_t lib_pool() {
+  int dev = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= 64) {
+    cudaGetLastError();
+    return nullptr;
+  }
+  std::lock_guard<std::mutex> lock(g_pool_mu);
+  if (!g_pool[dev]) {
+    cudaMemPoolProps props;
+    memset(&props, 0, sizeof(props));
+    props.allocType = cudaMemAllocationTypePinned;
+    props.location.type = cudaMemLocationTypeDevice;
+    props.location.id = dev;
+    cudaMemPool_t p = nullptr;
+    if (cudaMemPoolCreate(&p, &props) != cudaSuccess) {
+      cudaGetLastError();
+      return nullptr;
+    }
+    uint64_t keep = g_pool_keep;
+    cudaMemPoolSetAttribute(p, cudaMemPoolAttrReleaseThreshold, &keep);
+    g_pool[dev] = p;
+  }
+  return g_pool[dev];
+}
+}  // namespace
+
+cudaError_t tetm::dev_alloc(void** p, size_t bytes, cudaStream_t st) {
+  *p = nullptr;
+  cudaMemPool_t pool = lib_pool();
+  if (!pool) return cudaErrorMemoryAllocation;
+  return cudaMallocFromPoolAsync(p, bytes ? bytes : 16, pool, st);
+}
+
+void tetm::dev_free(void* p, cudaStream_t st) {
+  if (p) cudaFreeAsync(p, st);
+}
+
 int tetm::rebuild_work(tetm_solver* s) {
   const Layout& L = s->L;
   s->tiles_x = (L.nx + s->tile_x - 1) / s->tile_x;
@@ -265,11 +308,11 @@ int tetm::rebuild_work(tetm_solver* s) {
   const long long items = (long long)s->tiles_x * s->tiles_y * s->n_chunks;
   if (items >= (1LL << 31)) return TETM_E_ARG;
   if (s->work) {
-    cudaFree(s->work);
+    dev_free(s->work, s->stream);
     s->work = nullptr;
   }
   int* counts = nullptr;
-  CK(cudaMalloc(&counts, sizeof(int) * (size_t)items));
+  CK(dev_alloc((void**)&counts, sizeof(int) * (size_t)items, s->stream));
   item_counts<<<(unsigned)items, 256, 0, s->stream>>>(s->mask, L, s->tile_x, s->tile_y, s->chunk_z,
                                                       s->tiles_x, s->tiles_y, (int)items, counts);
   std::vector<int> h((size_t)items);
@@ -277,7 +320,7 @@ int tetm::rebuild_work(tetm_solver* s) {
   if (e == cudaSuccess) e = cudaMemcpyAsync(h.data(), counts, sizeof(int) * (size_t)items,
                                             cudaMemcpyDeviceToHost, s->stream);
   if (e == cudaSuccess) e = cudaStreamSynchronize(s->stream);
-  cudaFree(counts);
+  dev_free(counts, s->stream);
   if (e != cudaSuccess) return cuda_fail(e);
   // the items that own a field-carrying cell, in grid order: items that run
   // at the same time are neighbours and share their halo rows through L2
@@ -289,15 +332,15 @@ int tetm::rebuild_work(tetm_solver* s) {
   s->n_work = (int)list.size();
   s->work_host = list;
   if (3 * s->n_work > s->diag.cap) {  // balance reductions keep three partials per work item
-    cudaFree(s->diag.part);
+    dev_free(s->diag.part, s->stream);
     s->diag.part = nullptr;
     s->diag.cap = 0;
     const int cap = std::max(2048, 3 * s->n_work);
-    CK(cudaMalloc(&s->diag.part, sizeof(double) * (size_t)cap));
+    CK(dev_alloc((void**)&s->diag.part, sizeof(double) * (size_t)cap, s->stream));
     s->diag.cap = cap;
   }
   if (!list.empty()) {
-    CK(cudaMalloc(&s->work, sizeof(int) * list.size()));
+    CK(dev_alloc((void**)&s->work, sizeof(int) * list.size(), s->stream));
     CK(cudaMemcpyAsync(s->work, list.data(), sizeof(int) * list.size(), cudaMemcpyHostToDevice,
                        s->stream));
     CK(cudaStreamSynchronize(s->stream));
@@ -517,24 +560,26 @@ int set_fields_t(tetm_solver* s, int comp, const double* host) {
   return TETM_OK;
 }
 
+// releases every device array of the solve, in the order of its stream
 void free_all(tetm_solver* s) {
+  cudaStream_t st = s->stream;
   for (int b = 0; b < 2; ++b)
-    for (int c = 0; c < 6; ++c) cudaFree(s->set[b][c]);
+    for (int c = 0; c < 6; ++c) dev_free(s->set[b][c], st);
   for (int c = 0; c < 6; ++c) {
-    cudaFree(s->minv_a[c]);
-    cudaFree(s->ua[c]);
+    dev_free(s->minv_a[c], st);
+    dev_free(s->ua[c], st);
   }
-  cudaFree(s->mask);
-  cudaFree(s->work);
-  cudaFree(s->J);
-  cudaFree(s->W);
-  cudaFree(s->qline);
-  cudaFree(s->diag.part);
-  cudaFree(s->diag.out);
-  cudaFree(s->hist);
-  cudaFree(s->staging);
-  cudaFree(s->err);
-  cudaFree(s->sched);
+  dev_free(s->mask, st);
+  dev_free(s->work, st);
+  dev_free(s->J, st);
+  dev_free(s->W, st);
+  dev_free(s->qline, st);
+  dev_free(s->diag.part, st);
+  dev_free(s->diag.out, st);
+  dev_free(s->hist, st);
+  dev_free(s->staging, st);
+  dev_free(s->err, st);
+  dev_free(s->sched, st);
   delete s->slab;
   s->slab = nullptr;
 }
@@ -574,7 +619,7 @@ namespace {
 // A solve of planes [k_lo, k_lo + g->nz) of a grid of nz_all planes (the
 // whole grid: k_lo = 0, nz_all = g->nz); the cell arrays cover the whole grid.
 int create_impl(const tetm_grid* g, int k_lo, int nz_all, const double* eps_r, const double* mu_r,
-                const uint8_t* pec, tetm_solver** out) {
+                const uint8_t* pec, cudaStream_t st, tetm_solver** out) {
   if (!out) return TETM_E_ARG;
   *out = nullptr;
   if (!grid_ok(g)) return TETM_E_ARG;
@@ -608,7 +653,7 @@ int create_impl(const tetm_grid* g, int k_lo, int nz_all, const double* eps_r, c
   s->esz = g->precision == TETM_FP64 ? 8 : 4;
   s->L = make_layout(g->nx, g->ny, g->nz, (int)s->esz);
   s->alpha = 0.5 * cdt / kC;
-  s->stream = nullptr;
+  s->stream = st;
   s->scheme = TETM_SCHEME_TETM;
   s->kernel = TETM_KERNEL_FUSED;
   s->uniform = uniform;
@@ -658,7 +703,7 @@ int create_impl(const tetm_grid* g, int k_lo, int nz_all, const double* eps_r, c
   uint8_t* dpec = nullptr;
   double *deps = nullptr, *dmu = nullptr;
   if (rc == TETM_OK && pec) {
-    if (cudaMalloc(&dpec, (size_t)ncell) != cudaSuccess ||
+    if (dev_alloc((void**)&dpec, (size_t)ncell, s->stream) != cudaSuccess ||
         cudaMemcpyAsync(dpec, pec, (size_t)ncell, cudaMemcpyHostToDevice, s->stream) != cudaSuccess)
       rc = TETM_E_CUDA;
     gi.pec = dpec;
@@ -668,7 +713,7 @@ int create_impl(const tetm_grid* g, int k_lo, int nz_all, const double* eps_r, c
       const double* a = w == 0 ? eps_r : mu_r;
       if (!a) continue;
       double** d = w == 0 ? &deps : &dmu;
-      if (cudaMalloc(d, sizeof(double) * (size_t)ncell) != cudaSuccess ||
+      if (dev_alloc((void**)d, sizeof(double) * (size_t)ncell, s->stream) != cudaSuccess ||
           cudaMemcpyAsync(*d, a, sizeof(double) * (size_t)ncell, cudaMemcpyHostToDevice, s->stream) != cudaSuccess)
         rc = TETM_E_CUDA;
     }
@@ -681,9 +726,9 @@ int create_impl(const tetm_grid* g, int k_lo, int nz_all, const double* eps_r, c
     build_geometry<<<(unsigned)((total + 255) / 256), 256, 0, s->stream>>>(gi, s->L, k_first, s->mask, mo);
     if (cudaGetLastError() != cudaSuccess || cudaStreamSynchronize(s->stream) != cudaSuccess) rc = TETM_E_CUDA;
   }
-  cudaFree(dpec);
-  cudaFree(deps);
-  cudaFree(dmu);
+  dev_free(dpec, s->stream);
+  dev_free(deps, s->stream);
+  dev_free(dmu, s->stream);
   // per-component constants for the uniform case (vacuum or one material)
   const double dx = g->dx, dy = g->dy, dz = g->dz;
   s->minv_c[kEX] = dx / (kEps0 * eps_u * dy * dz);
@@ -708,14 +753,14 @@ int create_impl(const tetm_grid* g, int k_lo, int nz_all, const double* eps_r, c
   if (rc == TETM_OK) {
     unsigned long long* cnt = nullptr;
     unsigned long long h = 0;
-    if (cudaMalloc(&cnt, sizeof(*cnt)) != cudaSuccess) rc = TETM_E_CUDA;
+    if (dev_alloc((void**)&cnt, sizeof(*cnt), s->stream) != cudaSuccess) rc = TETM_E_CUDA;
     if (rc == TETM_OK) {
       cudaMemsetAsync(cnt, 0, sizeof(*cnt), s->stream);
       count_active<<<256, 256, 0, s->stream>>>(s->mask, s->L, cnt);
       if (cudaMemcpyAsync(&h, cnt, sizeof(h), cudaMemcpyDeviceToHost, s->stream) != cudaSuccess ||
           cudaStreamSynchronize(s->stream) != cudaSuccess)
         rc = TETM_E_CUDA;
-      cudaFree(cnt);
+      dev_free(cnt, s->stream);
     }
     s->active_cells = (long long)h;
   }
@@ -736,7 +781,23 @@ extern "C" {
 
 int tetm_create(const tetm_grid* g, const double* eps_r, const double* mu_r, const uint8_t* pec,
                 tetm_solver** out) {
-  return create_impl(g, 0, g ? g->nz : 0, eps_r, mu_r, pec, out);
+  return create_impl(g, 0, g ? g->nz : 0, eps_r, mu_r, pec, nullptr, out);
+}
+
+int tetm_create_on_stream(const tetm_grid* g, const double* eps_r, const double* mu_r, const uint8_t* pec,
+                          void* stream, tetm_solver** out) {
+  return create_impl(g, 0, g ? g->nz : 0, eps_r, mu_r, pec, (cudaStream_t)stream, out);
+}
+
+int tetm_pool_reserve(uint64_t bytes) {
+  std::lock_guard<std::mutex> lock(g_pool_mu);
+  g_pool_keep = bytes;
+  for (cudaMemPool_t p : g_pool)
+    if (p && cudaMemPoolSetAttribute(p, cudaMemPoolAttrReleaseThreshold, &bytes) != cudaSuccess) {
+      cudaGetLastError();
+      return TETM_E_CUDA;
+    }
+  return TETM_OK;
 }
 
 int tetm_create_slab(const tetm_grid* g, int32_t k_lo, int32_t k_hi, const double* eps_r, const double* mu_r,
@@ -746,7 +807,7 @@ int tetm_create_slab(const tetm_grid* g, int32_t k_lo, int32_t k_hi, const doubl
   if (!g || k_lo < 0 || k_hi > g->nz || k_hi - k_lo < 2) return TETM_E_ARG;
   tetm_grid local = *g;
   local.nz = k_hi - k_lo;
-  return create_impl(&local, k_lo, g->nz, eps_r, mu_r, pec, out);
+  return create_impl(&local, k_lo, g->nz, eps_r, mu_r, pec, nullptr, out);
 }
 
 void tetm_destroy(tetm_solver* s) {
@@ -837,24 +898,35 @@ int tetm_set_bunch(tetm_solver* s, double sigma_z, double charge, int32_t i0, in
   const int nw = m_max + c0 + 2;
   void* J = nullptr;
   double* W = nullptr;
-  if (cudaMalloc(&J, s->esz * qc.size()) != cudaSuccess || cudaMalloc(&W, 3 * sizeof(double) * nw) != cudaSuccess) {
-    cudaFree(J); cudaFree(W);
+  if (dev_alloc(&J, s->esz * qc.size(), s->stream) != cudaSuccess ||
+      dev_alloc((void**)&W, 3 * sizeof(double) * nw, s->stream) != cudaSuccess) {
+    dev_free(J, s->stream);
+    dev_free(W, s->stream);
     cudaGetLastError();
     return TETM_E_NOMEM;
   }
+  // J from a host vector that lives until the stream has read it (the
+  // synchronisation below), all on the solve's stream
   int rc = TETM_OK;
+  std::vector<double> j64;
+  std::vector<float> j32;
+  cudaError_t e = cudaSuccess;
   if (s->esz == 8) {
-    std::vector<double> j(qc.size());
-    for (size_t q = 0; q < qc.size(); ++q) j[q] = kC * qc[q] / dz;
-    if (cudaMemcpy(J, j.data(), sizeof(double) * j.size(), cudaMemcpyHostToDevice) != cudaSuccess) rc = TETM_E_CUDA;
+    j64.resize(qc.size());
+    for (size_t q = 0; q < qc.size(); ++q) j64[q] = kC * qc[q] / dz;
+    e = cudaMemcpyAsync(J, j64.data(), sizeof(double) * j64.size(), cudaMemcpyHostToDevice, s->stream);
   } else {
-    std::vector<float> j(qc.size());
-    for (size_t q = 0; q < qc.size(); ++q) j[q] = (float)(kC * qc[q] / dz);
-    if (cudaMemcpy(J, j.data(), sizeof(float) * j.size(), cudaMemcpyHostToDevice) != cudaSuccess) rc = TETM_E_CUDA;
+    j32.resize(qc.size());
+    for (size_t q = 0; q < qc.size(); ++q) j32[q] = (float)(kC * qc[q] / dz);
+    e = cudaMemcpyAsync(J, j32.data(), sizeof(float) * j32.size(), cudaMemcpyHostToDevice, s->stream);
   }
-  if (rc == TETM_OK && cudaMemset(W, 0, 3 * sizeof(double) * nw) != cudaSuccess) rc = TETM_E_CUDA;
+  if (e == cudaSuccess) e = cudaMemsetAsync(W, 0, 3 * sizeof(double) * nw, s->stream);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(s->stream);
+  if (e != cudaSuccess) rc = TETM_E_CUDA;
   if (rc != TETM_OK) {
-    cudaFree(J); cudaFree(W);
+    dev_free(J, s->stream);
+    dev_free(W, s->stream);
+    cudaGetLastError();
     return rc;
   }
   s->J = J;
@@ -1028,7 +1100,7 @@ int tetm_check_guards(tetm_solver* s, int64_t* violations) {
   if (!s || !violations) return TETM_E_ARG;
   unsigned long long* cnt = nullptr;
   unsigned long long h = 0;
-  CK(cudaMalloc(&cnt, sizeof(*cnt)));
+  CK(dev_alloc((void**)&cnt, sizeof(*cnt), s->stream));
   cudaError_t e = cudaMemsetAsync(cnt, 0, sizeof(*cnt), s->stream);
   for (int b = 0; b < 2 && e == cudaSuccess; ++b)
     for (int c = 0; c < 6 && e == cudaSuccess; ++c) {
@@ -1040,7 +1112,7 @@ int tetm_check_guards(tetm_solver* s, int64_t* violations) {
     }
   if (e == cudaSuccess) e = cudaMemcpyAsync(&h, cnt, sizeof(h), cudaMemcpyDeviceToHost, s->stream);
   if (e == cudaSuccess) e = cudaStreamSynchronize(s->stream);
-  cudaFree(cnt);
+  dev_free(cnt, s->stream);
   CK(e);
   *violations = (int64_t)h;
   return TETM_OK;

@@ -451,7 +451,7 @@ fused_step_slab(const StepArgs<float> a, const __grid_constant__ CUtensorMap tm_
 // tensor maps (of the set it reads) from device memory.
 __global__ void __launch_bounds__(kSThreads, 1)
 fused_step_slab_batch(const BatchMember<float>* __restrict__ members, const SlabBatchMaps* __restrict__ maps,
-                      const int2* __restrict__ work, int n_work, int* err, int* sched) {
+                      const int2* __restrict__ work, const int* __restrict__ n_work_p, int* err, int* sched) {
   using Smem = SlabSmem<false>;
   constexpr int kSD = Smem::SD;
   extern __shared__ __align__(128) unsigned char slab_raw[];
@@ -464,6 +464,7 @@ fused_step_slab_batch(const BatchMember<float>* __restrict__ members, const Slab
   __syncthreads();
   unsigned phases = 0;
   const int G = gridDim.x;
+  const int n_work = *n_work_p;  // written before the launch (stream order)
   int wi = blockIdx.x, par = 0;
   bool ok = true;
   while (wi < n_work && ok) {
@@ -581,8 +582,8 @@ cudaError_t launch_slab(const StepArgs<float>& a, const SlabMaps& m, int cur, in
 }  // namespace
 
 cudaError_t launch_fused_slab_batch(BatchMember<float>* members, const SlabBatchMaps* maps, int n_members,
-                                    const int2* work, int n_work, int* err, int* sched, int nz_max,
-                                    cudaStream_t st) {
+                                    const int2* work, const int* n_work, int n_bound, int* err, int* sched,
+                                    int nz_max, cudaStream_t st) {
   static int sms = 0;
   const size_t smem = sizeof(SlabSmem<false>);
   if (!sms) {
@@ -596,8 +597,8 @@ cudaError_t launch_fused_slab_batch(BatchMember<float>* members, const SlabBatch
       return e;
     }
   }
-  if (n_work > 0) {
-    fused_step_slab_batch<<<std::min(n_work, sms), kSThreads, smem, st>>>(members, maps, work, n_work, err, sched);
+  if (n_bound > 0) {
+    fused_step_slab_batch<<<std::min(n_bound, sms), kSThreads, smem, st>>>(members, maps, work, n_work, err, sched);
     cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess) return e;
   }

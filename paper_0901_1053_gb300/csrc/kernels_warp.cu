@@ -258,8 +258,9 @@ fused_step_warp(const StepArgs<T> a) {
 template <typename T, int TY>
 __global__ void __launch_bounds__(64)
 fused_step_warp_batch(const BatchMember<T>* __restrict__ members,
-                            const int2* __restrict__ work, int n_work) {
+                            const int2* __restrict__ work, const int* __restrict__ n_work_p) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
+  const int n_work = *n_work_p;
   const int nwarps = (int)((gridDim.x * blockDim.x) >> 5);
   for (int witem = (int)((blockIdx.x * blockDim.x + threadIdx.x) >> 5); witem < n_work;
        witem += nwarps) {
@@ -510,8 +511,9 @@ fused_step_warp_reg(const StepArgs<T> a) {
 template <typename T, int TY>
 __global__ void __launch_bounds__(128)
 fused_step_warp_reg_batch(const BatchMember<T>* __restrict__ members,
-                            const int2* __restrict__ work, int n_work) {
+                            const int2* __restrict__ work, const int* __restrict__ n_work_p) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
+  const int n_work = *n_work_p;
   const int nwarps = (int)((gridDim.x * blockDim.x) >> 5);
   for (int witem = (int)((blockIdx.x * blockDim.x + threadIdx.x) >> 5); witem < n_work;
        witem += nwarps) {
@@ -568,8 +570,8 @@ __global__ void batch_advance(BatchMember<T>* members, int n) {
 }
 
 template <typename T, int TY, bool ASYNC, typename K>
-cudaError_t launch_batch_kernel(K kern, const BatchMember<T>* members, const int2* work, int n_work,
-                                cudaStream_t st) {
+cudaError_t launch_batch_kernel(K kern, const BatchMember<T>* members, const int2* work, const int* n_work,
+                                int n_bound, cudaStream_t st) {
   const int warps_per_block = ASYNC ? 2 : 4;
   const size_t smem = ASYNC ? (size_t)warps_per_block * (kDepth * kArrs + 2 * (TY + 4)) * 32 * sizeof(T)
                             : (size_t)warps_per_block * 4 * (TY + 4) * 32 * sizeof(T);
@@ -587,18 +589,19 @@ cudaError_t launch_batch_kernel(K kern, const BatchMember<T>* members, const int
     if (e != cudaSuccess) return e;
     resident = std::max(1, sms * per_sm);
   }
-  const int blocks = std::min(resident, (n_work + warps_per_block - 1) / warps_per_block);
+  const int blocks = std::min(resident, (n_bound + warps_per_block - 1) / warps_per_block);
   if (blocks > 0) kern<<<blocks, 32 * warps_per_block, smem, st>>>(members, work, n_work);
   return cudaGetLastError();
 }
 
 template <typename T, int TY, bool ASYNC>
-cudaError_t launch_batch_shape(const BatchMember<T>* members, const int2* work, int n_work,
-                               cudaStream_t st) {
+cudaError_t launch_batch_shape(const BatchMember<T>* members, const int2* work, const int* n_work,
+                               int n_bound, cudaStream_t st) {
   if constexpr (ASYNC)
-    return launch_batch_kernel<T, TY, true>(fused_step_warp_batch<T, TY>, members, work, n_work, st);
+    return launch_batch_kernel<T, TY, true>(fused_step_warp_batch<T, TY>, members, work, n_work, n_bound, st);
   else
-    return launch_batch_kernel<T, TY, false>(fused_step_warp_reg_batch<T, TY>, members, work, n_work, st);
+    return launch_batch_kernel<T, TY, false>(fused_step_warp_reg_batch<T, TY>, members, work, n_work, n_bound,
+                                             st);
 }
 
 
@@ -845,22 +848,22 @@ cudaError_t launch_fused_warp_step(const StepArgs<T>& a, int tx, int ty, cudaStr
 
 template <typename T>
 cudaError_t launch_fused_warp_batch(const BatchMember<T>* members, int n_members, const int2* work,
-                                    int n_work, int ty, int nz_max, cudaStream_t st) {
+                                    const int* n_work, int n_bound, int ty, int nz_max, cudaStream_t st) {
   cudaError_t e = cudaErrorInvalidValue;
   if constexpr (sizeof(T) == 8) {
-    if (ty == 4) e = launch_batch_shape<T, 4, true>(members, work, n_work, st);
-    else if (ty == 12) e = launch_batch_shape<T, 12, true>(members, work, n_work, st);
-    else if (ty == 20) e = launch_batch_shape<T, 20, true>(members, work, n_work, st);
-    else if (ty == 28) e = launch_batch_shape<T, 28, true>(members, work, n_work, st);
-    else if (ty == 8) e = launch_batch_shape<T, 8, false>(members, work, n_work, st);
-    else if (ty == 16) e = launch_batch_shape<T, 16, false>(members, work, n_work, st);
+    if (ty == 4) e = launch_batch_shape<T, 4, true>(members, work, n_work, n_bound, st);
+    else if (ty == 12) e = launch_batch_shape<T, 12, true>(members, work, n_work, n_bound, st);
+    else if (ty == 20) e = launch_batch_shape<T, 20, true>(members, work, n_work, n_bound, st);
+    else if (ty == 28) e = launch_batch_shape<T, 28, true>(members, work, n_work, n_bound, st);
+    else if (ty == 8) e = launch_batch_shape<T, 8, false>(members, work, n_work, n_bound, st);
+    else if (ty == 16) e = launch_batch_shape<T, 16, false>(members, work, n_work, n_bound, st);
   } else {
-    if (ty == 4) e = launch_batch_shape<T, 4, false>(members, work, n_work, st);
-    else if (ty == 8) e = launch_batch_shape<T, 8, false>(members, work, n_work, st);
-    else if (ty == 12) e = launch_batch_shape<T, 12, false>(members, work, n_work, st);
-    else if (ty == 16) e = launch_batch_shape<T, 16, false>(members, work, n_work, st);
-    else if (ty == 20) e = launch_batch_shape<T, 20, false>(members, work, n_work, st);
-    else if (ty == 28) e = launch_batch_shape<T, 28, false>(members, work, n_work, st);
+    if (ty == 4) e = launch_batch_shape<T, 4, false>(members, work, n_work, n_bound, st);
+    else if (ty == 8) e = launch_batch_shape<T, 8, false>(members, work, n_work, n_bound, st);
+    else if (ty == 12) e = launch_batch_shape<T, 12, false>(members, work, n_work, n_bound, st);
+    else if (ty == 16) e = launch_batch_shape<T, 16, false>(members, work, n_work, n_bound, st);
+    else if (ty == 20) e = launch_batch_shape<T, 20, false>(members, work, n_work, n_bound, st);
+    else if (ty == 28) e = launch_batch_shape<T, 28, false>(members, work, n_work, n_bound, st);
   }
   if (e != cudaSuccess) return e;
   e = launch_transverse_after_batch_step<T>(members, n_members, nz_max, st);
@@ -878,9 +881,9 @@ cudaError_t launch_batch_advance(BatchMember<T>* members, int n_members, cudaStr
 template cudaError_t launch_batch_advance<float>(BatchMember<float>*, int, cudaStream_t);
 template cudaError_t launch_batch_advance<double>(BatchMember<double>*, int, cudaStream_t);
 
-template cudaError_t launch_fused_warp_batch<float>(const BatchMember<float>*, int, const int2*, int,
-                                                    int, int, cudaStream_t);
-template cudaError_t launch_fused_warp_batch<double>(const BatchMember<double>*, int, const int2*,
+template cudaError_t launch_fused_warp_batch<float>(const BatchMember<float>*, int, const int2*, const int*,
+                                                    int, int, int, cudaStream_t);
+template cudaError_t launch_fused_warp_batch<double>(const BatchMember<double>*, int, const int2*, const int*,
                                                      int, int, int, cudaStream_t);
 
 template cudaError_t launch_fused_warp_step<float>(const StepArgs<float>&, int, int, cudaStream_t);

@@ -119,7 +119,7 @@ extern "C" int tetm_set_bunch_static(tetm_solver* s, double sigma_z, double char
   cudaStream_t st = s->stream;
   // the entry section: planes 2..K carry the objects of plane 1
   unsigned long long* dcount = nullptr;
-  if (cudaMalloc(&dcount, sizeof(unsigned long long)) != cudaSuccess) {
+  if (dev_alloc((void**)&dcount, sizeof(unsigned long long), st) != cudaSuccess) {
     cudaGetLastError();
     return TETM_E_NOMEM;
   }
@@ -135,7 +135,7 @@ extern "C" int tetm_set_bunch_static(tetm_solver* s, double sigma_z, double char
   if (e == cudaSuccess)
     e = cudaMemcpyAsync(plane.data(), s->mask + 2 * L.sz, (size_t)L.sz, cudaMemcpyDeviceToHost, st);
   if (e == cudaSuccess) e = cudaStreamSynchronize(st);
-  cudaFree(dcount);
+  dev_free(dcount, st);
   if (e != cudaSuccess) {
     cudaGetLastError();
     return TETM_E_CUDA;
@@ -190,9 +190,9 @@ extern "C" int tetm_set_bunch_static(tetm_solver* s, double sigma_z, double char
   for (int u = K - 1; u >= K - 2 * c0; --u)
     G[(size_t)u + 1] = 2.0 * eta0 * (kC * s->qcell[(size_t)(u - K + 2 * c0)] / dz) - G[(size_t)u + 2];
   double *dp = nullptr, *dq = nullptr, *dg = nullptr;
-  e = cudaMalloc(&dp, sizeof(double) * (size_t)nxy);
-  if (e == cudaSuccess) e = cudaMalloc(&dq, sizeof(double) * (size_t)nxy);
-  if (e == cudaSuccess) e = cudaMalloc(&dg, sizeof(double) * G.size());
+  e = dev_alloc((void**)&dp, sizeof(double) * (size_t)nxy, st);
+  if (e == cudaSuccess) e = dev_alloc((void**)&dq, sizeof(double) * (size_t)nxy, st);
+  if (e == cudaSuccess) e = dev_alloc((void**)&dg, sizeof(double) * G.size(), st);
   if (e == cudaSuccess) e = cudaMemcpyAsync(dp, pxp.data(), sizeof(double) * (size_t)nxy, cudaMemcpyHostToDevice, st);
   if (e == cudaSuccess) e = cudaMemcpyAsync(dq, pyp.data(), sizeof(double) * (size_t)nxy, cudaMemcpyHostToDevice, st);
   if (e == cudaSuccess) e = cudaMemcpyAsync(dg, G.data(), sizeof(double) * G.size(), cudaMemcpyHostToDevice, st);
@@ -209,9 +209,9 @@ extern "C" int tetm_set_bunch_static(tetm_solver* s, double sigma_z, double char
     e = cudaGetLastError();
   }
   if (e == cudaSuccess) e = cudaStreamSynchronize(st);
-  cudaFree(dp);
-  cudaFree(dq);
-  cudaFree(dg);
+  dev_free(dp, st);
+  dev_free(dq, st);
+  dev_free(dg, st);
   if (e != cudaSuccess) {
     cudaGetLastError();
     return TETM_E_CUDA;

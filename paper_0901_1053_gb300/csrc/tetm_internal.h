@@ -121,11 +121,13 @@ bool fused_shape_ok(int tile_x, int tile_y);
 template <typename T>
 cudaError_t launch_fused_warp_step(const StepArgs<T>& a, int tile_x, int tile_y, cudaStream_t st);
 bool warp_shape_ok(int tile_x, int tile_y);
-// one step of every active member of a batch (work = (member, item) pairs),
-// then the device-side advance of all members
+// one step of every active member of a batch (work = (member, item) pairs,
+// their number read from device memory at n_work, at most n_bound: the grid
+// is sized from n_bound so a captured launch stays valid while the list
+// changes), then the device-side advance of all n_members slots
 template <typename T>
 cudaError_t launch_fused_warp_batch(const BatchMember<T>* members, int n_members, const int2* work,
-                                    int n_work, int tile_y, int nz_max, cudaStream_t st);
+                                    const int* n_work, int n_bound, int tile_y, int nz_max, cudaStream_t st);
 // after a batch step: every active member swaps its sets, counts the step
 // and retires at its limit
 template <typename T>
@@ -150,11 +152,12 @@ struct SlabBatchMaps {
   alignas(128) unsigned char hz[2][128];
 };
 // one step of every active member of a float32 batch on the slab kernel
-// (work = (member, item) pairs, sched as below), the transverse wakes, then
-// the device-side advance
+// (work = (member, item) pairs counted at n_work in device memory, at most
+// n_bound; sched as below), the transverse wakes, then the device-side
+// advance of all n_members slots
 cudaError_t launch_fused_slab_batch(BatchMember<float>* members, const SlabBatchMaps* maps, int n_members,
-                                    const int2* work, int n_work, int* err, int* sched, int nz_max,
-                                    cudaStream_t st);
+                                    const int2* work, const int* n_work, int n_bound, int* err, int* sched,
+                                    int nz_max, cudaStream_t st);
 // sched: two ints of device memory, zero before the first launch, that the
 // kernel's dynamic schedule uses and leaves zero (nullptr: static order)
 cudaError_t launch_fused_slab_step(const StepArgs<float>& a, const SlabMaps& m, int cur, int* err, int* sched,
@@ -286,4 +289,12 @@ template <typename T>
 StepArgs<T> step_args(tetm_solver* s, bool fused);
 // (re)build the list of (tile, chunk) work items that own a field-carrying cell
 int rebuild_work(tetm_solver* s);
+// Device memory of solves and batches comes from one stream-ordered pool per
+// device: allocation and release are queued on the given stream, so neither
+// waits for work queued on other streams (cudaFree waits for the whole
+// device, which would stall a batch running beside a solve being created or
+// destroyed on another host thread). Memory is usable on other streams once
+// the allocating stream has reached the allocation.
+cudaError_t dev_alloc(void** p, size_t bytes, cudaStream_t st);
+void dev_free(void* p, cudaStream_t st);
 }  // namespace tetm

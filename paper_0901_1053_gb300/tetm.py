@@ -53,7 +53,9 @@ EXPORTS = ("tetm_create", "tetm_set_bunch", "tetm_step", "tetm_sync", "tetm_wake
            "tetm_rz_set_bunch_static", "tetm_rz_set_bunch_scattered", "tetm_rz_selftest_wait",
            "tetm_rz_check_guards", "tetm_rz_charge_residual", "tetm_rz_set_balance_every",
            "tetm_rz_balance_history", "tetm_rz_save", "tetm_rz_load",
-           "tetm_create_slab", "tetm_plane_bytes", "tetm_export_plane", "tetm_import_plane")
+           "tetm_create_slab", "tetm_plane_bytes", "tetm_export_plane", "tetm_import_plane",
+           "tetm_create_on_stream", "tetm_pool_reserve", "tetm_batch_create_slots", "tetm_batch_add",
+           "tetm_batch_remove", "tetm_batch_wait")
 TETM_PLANES_UP = 0
 TETM_PLANES_DOWN = 1
 TETM_RZ_KERNEL_ASYNC = 0
@@ -137,6 +139,12 @@ def _load():
         "tetm_batch_info": (ctypes.c_int, [vp, ctypes.POINTER(i32), ctypes.POINTER(i32),
                                            ctypes.POINTER(i32)]),
         "tetm_batch_destroy": (None, [vp]),
+        "tetm_create_on_stream": (ctypes.c_int, [ctypes.POINTER(tetm_grid), vp, vp, vp, vp, pp]),
+        "tetm_pool_reserve": (ctypes.c_int, [ctypes.c_uint64]),
+        "tetm_batch_create_slots": (ctypes.c_int, [i32, i32, i32, i32, i32, ctypes.POINTER(ctypes.c_void_p)]),
+        "tetm_batch_add": (ctypes.c_int, [vp, vp, ctypes.c_int64, ctypes.POINTER(i32)]),
+        "tetm_batch_remove": (ctypes.c_int, [vp, vp]),
+        "tetm_batch_wait": (ctypes.c_int, [vp, i32, ctypes.POINTER(dbl)]),
         "tetm_energy_noalloc": (ctypes.c_int, [ctypes.POINTER(tetm_grid),
                                                ctypes.POINTER(ctypes.c_void_p), vp, vp, vp]),
         "tetm_rz_create": (ctypes.c_int, [ctypes.POINTER(tetm_rz_grid), vp, vp, vp, pp]),
@@ -220,6 +228,11 @@ def tetm_bytes_needed(grid):
     return int(lib.tetm_bytes_needed(ctypes.byref(grid)))
 
 
+def tetm_pool_reserve(nbytes):
+    """Released device memory the library's pool keeps for reuse."""
+    _check(lib.tetm_pool_reserve(int(nbytes)), "tetm_pool_reserve")
+
+
 def tetm_energy_noalloc(grid, field_ptrs, mask_ptr, w_ptr, stream=0):
     """Energy of a state held in caller-owned device arrays, without any
     device allocation (see include/tetm.h). All pointers are device
@@ -243,9 +256,12 @@ class Solver:
     """
 
     def __init__(self, nx, ny, nz, dx, dy, dz, cdt=0.0, precision="fp32", eps_r=None, mu_r=None,
-                 pec=None, k_range=None):
+                 pec=None, k_range=None, stream=None):
         """k_range=(k_lo, k_hi): the z-slab of planes [k_lo, k_hi) of this grid
-        (tetm_create_slab); the cell arrays still cover the whole grid."""
+        (tetm_create_slab); the cell arrays still cover the whole grid.
+        stream: a cudaStream_t (int) that the solve's work, its creation
+        included, is queued on (tetm_create_on_stream); None = the default
+        stream."""
         self.grid = make_grid(nx, ny, nz, dx, dy, dz, cdt, precision)
         cell = (int(nz), int(ny), int(nx))
         arrs = []
@@ -253,7 +269,14 @@ class Solver:
             arrs.append(None if a is None else np.ascontiguousarray(a, dtype=dt).reshape(cell))
         h = ctypes.c_void_p()
         self.h = None
-        if k_range is None:
+        if stream is not None:
+            if k_range is not None:
+                raise ValueError("a z-slab is created on the default stream")
+            _check(lib.tetm_create_on_stream(ctypes.byref(self.grid), *[_ptr(a) for a in arrs],
+                                             ctypes.c_void_p(int(stream)), ctypes.byref(h)),
+                   "tetm_create_on_stream")
+            nzl = int(nz)
+        elif k_range is None:
             _check(lib.tetm_create(ctypes.byref(self.grid), *[_ptr(a) for a in arrs], ctypes.byref(h)),
                    "tetm_create")
             nzl = int(nz)
@@ -420,6 +443,10 @@ class Batch:
     members, optionally replayed from a captured CUDA graph."""
 
     def __init__(self, solvers, step_limits=None, graph_steps=0):
+        if solvers is None:   # an empty slot table (Batch.slots)
+            self.h = None
+            self.solvers = []
+            return
         self.solvers = list(solvers)
         n = len(self.solvers)
         hs = (ctypes.c_void_p * n)(*[s.h for s in self.solvers])
@@ -433,8 +460,40 @@ class Batch:
                "tetm_batch_create")
         self.h = h
 
+    @classmethod
+    def slots(cls, capacity, precision="fp32", tile=(56, 28), graph_steps=0):
+        """An empty batch of `capacity` slots (tetm_batch_create_slots):
+        members join (add) and leave (remove) between steps without
+        rebuilding the batch or re-capturing its graph."""
+        b = cls(None)
+        p = {"fp64": TETM_FP64, "fp32": TETM_FP32}[precision]
+        h = ctypes.c_void_p()
+        _check(lib.tetm_batch_create_slots(int(capacity), p, int(tile[0]), int(tile[1]), int(graph_steps),
+                                           ctypes.byref(h)), "tetm_batch_create_slots")
+        b.h = h
+        return b
+
+    def add(self, solver, step_limit=-1):
+        """Join: the solve takes a free slot; returns the slot index."""
+        slot = ctypes.c_int32(-1)
+        _check(lib.tetm_batch_add(self.h, solver.h, int(step_limit), ctypes.byref(slot)), "tetm_batch_add")
+        self.solvers.append(solver)
+        return slot.value
+
+    def remove(self, solver):
+        """Leave after the steps queued so far (no host wait)."""
+        _check(lib.tetm_batch_remove(self.h, solver.h), "tetm_batch_remove")
+        self.solvers = [s for s in self.solvers if s is not solver]
+
     def step(self, n):
         _check(lib.tetm_batch_step(self.h, int(n)), "tetm_batch_step")
+
+    def wait(self, max_pending=0):
+        """Blocks until at most max_pending step calls are unfinished on the
+        device; returns the device seconds of the finished calls so far."""
+        busy = ctypes.c_double(0.0)
+        _check(lib.tetm_batch_wait(self.h, int(max_pending), ctypes.byref(busy)), "tetm_batch_wait")
+        return busy.value
 
     def sync(self):
         _check(lib.tetm_batch_sync(self.h), "tetm_batch_sync")

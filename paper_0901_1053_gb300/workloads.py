@@ -187,6 +187,14 @@ class Request:
     sigma_cells: float
     seed: int
 
+    def spec(self, precision: str = "fp32") -> "RequestSpec":
+        """The request's sizes without its geometry (cheap); .build() makes
+        the Workload, so a server can build it off its scheduling thread."""
+        nz = 4 * self.n
+        sigma = self.sigma_cells * DZ
+        return RequestSpec(self, precision, self.n, self.n, nz, DXY, DXY, DZ, DZ,
+                           steps_for_window(nz, sigma))
+
     def workload(self, precision: str = "fp32") -> Workload:
         rng = np.random.default_rng(self.seed)
         nz, rad = _solve_geometry(self.n, self.kind, rng)
@@ -195,6 +203,27 @@ class Request:
         return Workload("req%04d_%s_%d" % (self.rid, self.kind, self.n), self.n, self.n, nz,
                         DXY, DXY, DZ, DZ, pec, sigma, 1e-9, self.n // 2, self.n // 2,
                         steps_for_window(nz, sigma), precision, self.kind)
+
+
+@dataclasses.dataclass
+class RequestSpec:
+    request: "Request"
+    precision: str
+    nx: int
+    ny: int
+    nz: int
+    dx: float
+    dy: float
+    dz: float
+    cdt: float
+    steps: int
+
+    @property
+    def cells(self) -> int:
+        return self.nx * self.ny * self.nz
+
+    def build(self) -> Workload:
+        return self.request.workload(self.precision)
 
 
 def request_stream(count: int = 2000, rate: float = 40.0, seed: int = 9011054, n_lo: int = 48,

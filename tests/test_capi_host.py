@@ -148,6 +148,9 @@ def test_every_handle_call_rejects_a_null_handle_without_a_gpu(tetm):
         "tetm_rz_load": lambda: L.tetm_rz_load(None, None, 0),
         "tetm_export_plane": lambda: L.tetm_export_plane(None, 0, None),
         "tetm_import_plane": lambda: L.tetm_import_plane(None, 0, None),
+        "tetm_batch_add": lambda: L.tetm_batch_add(None, None, 0, None),
+        "tetm_batch_remove": lambda: L.tetm_batch_remove(None, None),
+        "tetm_batch_wait": lambda: L.tetm_batch_wait(None, 0, None),
     }
     for name, call in calls.items():
         assert call() == E, name
@@ -155,10 +158,17 @@ def test_every_handle_call_rejects_a_null_handle_without_a_gpu(tetm):
     L.tetm_batch_destroy(None)
     assert L.tetm_rz_destroy(None) == tetm.TETM_OK
     assert L.tetm_batch_create(None, None, 0, 0, None) == E
+    assert L.tetm_batch_create_slots(4, tetm.TETM_FP32, 56, 28, 0, None) == E   # no output pointer
+    out = ctypes.c_void_p()
+    for args in ((0, tetm.TETM_FP32, 56, 28, 0), (4, 7, 56, 28, 0), (4, tetm.TETM_FP32, 30, 20, 0),
+                 (4, tetm.TETM_FP64, 56, 28, 0), (4, tetm.TETM_FP32, 56, 28, -1)):
+        assert L.tetm_batch_create_slots(*args, ctypes.byref(out)) == E, args   # rejected before any device call
+    assert L.tetm_create_on_stream(None, None, None, None, None, None) == E
     assert L.tetm_create_slab(None, 0, 2, None, None, None, None) == E
     assert L.tetm_plane_bytes(None, 0) == 0
     handle_calls = [n for n in tetm.EXPORTS if n not in ("tetm_create", "tetm_rz_create", "tetm_destroy",
-                    "tetm_create_slab", "tetm_plane_bytes",
+                    "tetm_create_slab", "tetm_plane_bytes", "tetm_create_on_stream", "tetm_pool_reserve",
+                    "tetm_batch_create_slots",
                     "tetm_rz_destroy", "tetm_batch_destroy", "tetm_batch_create", "tetm_bytes_needed",
                     "tetm_rz_bytes_needed", "tetm_strerror", "tetm_energy_noalloc", "tetm_measure_fma_rate",
                     "tetm_rz_selftest_wait")]
