@@ -153,6 +153,14 @@ class Dist:
         self.d.all_reduce(t, op=self.d.ReduceOp.MAX)
         return float(t.item())
 
+    def sum(self, x):
+        if self.world == 1:
+            return x
+        import torch
+        t = torch.tensor([float(x)], dtype=torch.float64)
+        self.d.all_reduce(t, op=self.d.ReduceOp.SUM)
+        return float(t.item())
+
     def close(self):
         if self.world > 1:
             self.d.destroy_process_group()
@@ -582,7 +590,15 @@ def run_batch_mode(args):
     t32 = tuple(int(x) for x in args.tiling.split(",")) if args.tiling else tuner.tune(big, "fp32", batch=True)
     t64 = tuner.tune(big, "fp64")
     dist.barrier()
-    wakes32, t_step, t_total = run_batch(ws, "fp32", t32, graph_steps=32)
+    try:
+        uuid = str(torch.cuda.get_device_properties(local).uuid)
+    except Exception:
+        uuid = None
+    clocks = ClockSampler(uuid)
+    clocks.start()
+    bstats = {}
+    wakes32, t_step, t_total = run_batch(ws, "fp32", t32, graph_steps=32, stats=bstats)
+    clk = clocks.stop()
     wakes64, t_seq64 = run_sequential(ws, "fp64", t64)
     err = max(_rel(a, b) for a, b in zip(wakes32, wakes64))
     cs = sum(w.cells * w.steps for w in ws)
@@ -595,6 +611,7 @@ def run_batch_mode(args):
                        "n_range": [min(w.nx for w in allw), max(w.nx for w in allw)],
                        "tiling_fp32": list(t32), "tiling_fp64": list(t64), "graph_steps": 32,
                        "cell_steps": cs_all},
+            "active_gcell_updates_per_s": dist.sum(bstats["active_cell_steps"]) / t_step / 1e9,
             "solves_per_s": len(allw) / t_total,
             "fp64_single_solve_path_solves_per_s": len(allw) / t_seq64,
             "max_wake_err_vs_fp64_rel_peak": err,
@@ -602,7 +619,8 @@ def run_batch_mode(args):
                     "h2d_bytes_per_step": int(sum(w.pec.nbytes for w in allw)),
                     "d2h_bytes_per_step": int(sum(8 * len(x) for x in wakes32)),
                     "seconds": t_total},
-            "seconds": {"batch_steps": t_step, "batch_total": t_total, "fp64_sequential": t_seq64}}
+            "seconds": {"batch_steps": t_step, "batch_total": t_total, "fp64_sequential": t_seq64},
+            "clocks": clk}
     if rank == 0:
         print(json.dumps(line), flush=True)
     dist.close()

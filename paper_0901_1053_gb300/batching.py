@@ -6,9 +6,11 @@ from typing import List, Optional, Tuple
 
 
 def run_batch(workloads, precision: str = "fp32", tiling: Optional[Tuple[int, int, int]] = None,
-              graph_steps: int = 32, round_steps: Optional[int] = None):
+              graph_steps: int = 32, round_steps: Optional[int] = None, stats: Optional[dict] = None):
     """Create every solve, advance them together until each reached its own
-    step count, and return (wakes, seconds of stepping, seconds total)."""
+    step count, and return (wakes, seconds of stepping, seconds total).
+    stats (a dict), if given, receives the active cell-steps (cells that
+    carry a field, times each solve's steps)."""
     from . import tetm
     t_start = time.perf_counter()
     solvers = []
@@ -19,6 +21,8 @@ def run_batch(workloads, precision: str = "fp32", tiling: Optional[Tuple[int, in
             s.set_tiling(*tiling)
         solvers.append(s)
     limits = [w.steps for w in workloads]
+    if stats is not None:
+        stats["active_cell_steps"] = sum(s.info()["active_cells"] * n for s, n in zip(solvers, limits))
     b = tetm.Batch(solvers, limits, graph_steps=graph_steps)
     b.sync()
     t0 = time.perf_counter()

@@ -156,8 +156,10 @@ __device__ __forceinline__ void fused_step_warp_item(const StepArgs<T>& a, int i
     T hyn_p = T(0), hyn_pp = T(0), hxn_pp = T(0);              // new hy rows r-1, r-2; new hx row r-2
     T hz_p = T(0), hz_pp = T(0);                               // old hz rows r-1, r-2
     uint8_t m_p = 0, m_pp = 0;
+    unsigned mo_p = 0, mo_pp = 0;                              // the warp's OR of m, rows r-1, r-2
     T ex0_p = T(0), ey0_p = T(0);                              // old ex, ey row r-1
     T exa_pp = T(0), eya_pp = T(0), hzn_ppp = T(0);            // aux ex, ey row r-2; new hz row r-3
+    T dhy_p = T(0), dhx_p = T(0);                              // z-differences of new hy, hx, row r-2
 #pragma unroll 1
     for (int rg = 0; rg < RH; rg += kDepth) {
 #pragma unroll
@@ -168,6 +170,10 @@ __device__ __forceinline__ void fused_step_warp_item(const StepArgs<T>& a, int i
         const T ez = sl[0], hx = sl[32], hy = sl[64], hz = sl[96];
         const T ex0r = sl[128], ey0r = sl[160], ex1 = sl[192], ey1 = sl[224];
         const uint8_t m = mring[u];
+        // which of this row's objects carry a field anywhere in the warp: an
+        // update whose objects carry none in any lane leaves its zeros as
+        // they are (coefficient zero), so the warp skips its arithmetic
+        const unsigned mo = __reduce_or_sync(0xffffffffu, (unsigned)m);
         const T ez_next = ring[((u + 1) % kDepth) * kArrs * 32 + lane];  // row r+1
         mring[u] = issue_row(g + kDepth);  // refill this slot kDepth rows ahead
         ++g;
@@ -178,17 +184,21 @@ __device__ __forceinline__ void fused_step_warp_item(const StepArgs<T>& a, int i
         const T cHX = (m & 8) ? uHX : T(0), cHY = (m & 16) ? uHY : T(0);
         const T cEZ = (m & 4) ? uEZ : T(0);
         const T dey = ey1 - ey0r, dex = ex1 - ex0r;
-        const T hxa = hx + cHX * (dey - (ez_next - ez));                         // U1
-        const T hya = hy + cHY * (-dex + (shfl_dn(ez) - ez));                    // U2
-        T cur = (hxa_p - hxa) - (shfl_up1(hya) - hya);
         const bool line = line_x && r == line_r;
-        if (line) {
-          const long long dd = (long long)k - (a.n + a.b.kshift) + a.b.c0;
-          if (dd >= -a.b.c0 && dd < a.b.c0) cur -= a.b.J[dd + a.b.c0];
+        T hxa = hx, hya = hy, ezn = ez, hyn = hy;
+        if (mo & (4 | 8 | 16)) {
+          hxa = hx + cHX * (dey - (ez_next - ez));                                 // U1
+          hya = hy + cHY * (-dex + (shfl_dn(ez) - ez));                            // U2
+          T cur = (hxa_p - hxa) - (shfl_up1(hya) - hya);
+          if (line) {
+            const long long dd = (long long)k - (a.n + a.b.kshift) + a.b.c0;
+            if (dd >= -a.b.c0 && dd < a.b.c0) cur -= a.b.J[dd + a.b.c0];
+          }
+          ezn = ez + cEZ * cur;                                                    // U3
+          hyn = hya + cHY * (-dex + (shfl_dn(ezn) - ezn));                         // U5
         }
-        const T ezn = ez + cEZ * cur;                                            // U3
-        const T hyn = hya + cHY * (-dex + (shfl_dn(ezn) - ezn));                 // U5
-        const T hxn_p = hxa_p + cHX_p * (dey_p - (ezn - ezn_p));                 // U4, row r-1
+        T hxn_p = hxa_p;
+        if (mo_p & 8) hxn_p = hxa_p + cHX_p * (dey_p - (ezn - ezn_p));             // U4, row r-1
         if (te && own_x) {
           if (own_r) {
             oez[id] = ezn;
@@ -204,18 +214,27 @@ __device__ __forceinline__ void fused_step_warp_item(const StepArgs<T>& a, int i
         // ---------------- TE stage, rows q = r-1 and p = r-2 ----------------
         // (rows 0 and 1 are halo rows: their TE values are never used)
         const int q = r - 1, p = r - 2;
-        const T hxq_old = q >= 0 ? sHXP[q * 32 + lane] : T(0);
-        const T hyq_old = q >= 0 ? sHYP[q * 32 + lane] : T(0);
-        const T cEX = (m_p & 1) ? uEX : T(0), cEY = (m_p & 2) ? uEY : T(0);
-        const T exa = ex0_p + cEX * ((hyq_old - hyn_p) - (hz_pp - hz_p));           // U6, row q
-        const T eya = ey0_p + cEY * (-(hxq_old - hxn_p) + (shfl_up1(hz_p) - hz_p));  // U7, row q
-        const T cHZ = (m_pp & 32) ? uHZ : T(0);
-        const T cEXp = (m_pp & 1) ? uEX : T(0), cEYp = (m_pp & 2) ? uEY : T(0);
-        const T hzn = hz_pp + cHZ * ((exa - exa_pp) - (shfl_dn(eya_pp) - eya_pp));   // U8, row p
-        const T hxp_old = p >= 0 ? sHXP[p * 32 + lane] : T(0);
-        const T hyp_old = p >= 0 ? sHYP[p * 32 + lane] : T(0);
-        const T exn = exa_pp + cEXp * ((hyp_old - hyn_pp) - (hzn_ppp - hzn));       // U9, row p
-        const T eyn = eya_pp + cEYp * (-(hxp_old - hxn_pp) + (shfl_up1(hzn) - hzn));  // U10, row p
+        T exa = ex0_p, eya = ey0_p, dhy = T(0), dhx = T(0);
+        if (mo_p & 3) {
+          const T hxq_old = q >= 0 ? sHXP[q * 32 + lane] : T(0);
+          const T hyq_old = q >= 0 ? sHYP[q * 32 + lane] : T(0);
+          const T cEX = (m_p & 1) ? uEX : T(0), cEY = (m_p & 2) ? uEY : T(0);
+          dhy = hyq_old - hyn_p;  // U9 of this row (next row step) takes the same differences
+          dhx = hxq_old - hxn_p;
+          exa = ex0_p + cEX * (dhy - (hz_pp - hz_p));                              // U6, row q
+          eya = ey0_p + cEY * (-dhx + (shfl_up1(hz_p) - hz_p));                    // U7, row q
+        }
+        T hzn = hz_pp;
+        if (mo_pp & 32) {
+          const T cHZ = (m_pp & 32) ? uHZ : T(0);
+          hzn = hz_pp + cHZ * ((exa - exa_pp) - (shfl_dn(eya_pp) - eya_pp));       // U8, row p
+        }
+        T exn = exa_pp, eyn = eya_pp;
+        if (mo_pp & 3) {
+          const T cEXp = (m_pp & 1) ? uEX : T(0), cEYp = (m_pp & 2) ? uEY : T(0);
+          exn = exa_pp + cEXp * (dhy_p - (hzn_ppp - hzn));                          // U9, row p
+          eyn = eya_pp + cEYp * (-dhx_p + (shfl_up1(hzn) - hzn));                   // U10, row p
+        }
         if (te && own_x && p >= 2 && p < own_r_end) {
           const long long idp = id - 2 * PX;
           oex[idp] = exn;
@@ -234,8 +253,10 @@ __device__ __forceinline__ void fused_step_warp_item(const StepArgs<T>& a, int i
         hxa_p = hxa; dey_p = dey; cHX_p = cHX; ezn_p = ezn;
         hz_pp = hz_p; hz_p = hz;
         m_pp = m_p; m_p = m;
+        mo_pp = mo_p; mo_p = mo;
         ex0_p = ex0r; ey0_p = ey0r;
         exa_pp = exa; eya_pp = eya; hzn_ppp = hzn;
+        dhy_p = dhy; dhx_p = dhx;
       }
     }
   }
