@@ -86,7 +86,9 @@ def parse_args():
     p.add_argument("--tiling", default=None,
                    help="tile_x,tile_y,chunk_z (default: chosen by the autotuner, untimed)")
     p.add_argument("--no-autotune", action="store_true", help="keep the library's default shape")
-    p.add_argument("--kernel", default="fused", choices=["fused", "reference"])
+    p.add_argument("--kernel", default="fused", choices=["fused", "reference", "twostep"],
+                   help="twostep: the block-tiled sweep with two steps per pass (temporal blocking), "
+                        "timed in pairs of steps; needs --tiling 32,4,C / 32,8,C / 64,4,C")
     p.add_argument("--scheme", default="tetm", choices=["tetm", "yee"],
                    help="yee: Yee's E/M leapfrog (Eq. (7)) on the same grid at its step bound (8), "
                         "field-only, timed beside the TE/TM scheme per unit of simulated length")
@@ -398,6 +400,8 @@ def run_tetm(args):
         args.tiling_used = Autotuner().tune(w, w.precision, eps_r=args.eps)
     else:
         args.tiling_used = None
+    if args.kernel == "twostep" and not args.tiling_used:
+        args.tiling_used = (32, 8, 32)
     if args.tiling_used:
         s.set_tiling(*args.tiling_used)
     s.set_kernel(args.kernel)
@@ -414,23 +418,27 @@ def run_tetm(args):
     clocks = ClockSampler(uuid)
     clocks.start()
     time.sleep(0.5)
-    K = args.steps
-    evs = [torch.cuda.Event(enable_timing=True) for _ in range(K + 1)]
+    # steps per timed call: pairs for the two-step kernel (one launch each)
+    per_call = 2 if args.kernel == "twostep" else 1
+    K = args.steps - args.steps % per_call
+    nc = K // per_call
+    evs = [torch.cuda.Event(enable_timing=True) for _ in range(nc + 1)]
     dist.barrier()
     torch.cuda.synchronize()
     n0 = s.info()["step"]
-    for i in range(K):
+    for i in range(nc):
         evs[i].record(stream)
-        s.step(1)
-    evs[K].record(stream)
+        s.step(per_call)
+    evs[nc].record(stream)
     torch.cuda.synchronize()
     dist.barrier()
     clk = clocks.stop()
-    total_ms = evs[0].elapsed_time(evs[K])
-    per = [evs[i].elapsed_time(evs[i + 1]) for i in range(K)]
+    total_ms = evs[0].elapsed_time(evs[nc])
+    per = [evs[i].elapsed_time(evs[i + 1]) / per_call for i in range(nc)]
     be = args.balance_every
     bal_steps = [i for i in range(K) if be > 0 and (n0 + i + 1) % be == 0]
-    plain = [per[i] for i in range(K) if i not in set(bal_steps)]
+    bal_calls = {i // per_call for i in bal_steps}
+    plain = [per[i] for i in range(nc) if i not in bal_calls]
     kern_ms = statistics.mean(plain) if plain else total_ms / K
     max_ms = dist.max(total_ms)
 
@@ -439,6 +447,8 @@ def run_tetm(args):
     # the six coefficient words, per cell that carries a field: the work of
     # the method (a cell in PEC holds zero fields for ever)
     bytes_per_cell = 12 * esz + 1 if args.eps is None else 18 * esz
+    if args.kernel == "twostep":  # y^n read and y^{n+2} written once per two steps
+        bytes_per_cell = bytes_per_cell / 2
     proc = info["processed_cells"] if args.kernel != "reference" else w.cells
     act = info["active_cells"]
     gbs = bytes_per_cell * act / (kern_ms * 1e-3) / 1e9
@@ -457,6 +467,8 @@ def run_tetm(args):
                 "achieved_on_processed_cells": FLOPS_PER_CELL_3D * proc / (kern_ms * 1e-3) / 1e12,
                 "hbm_gbs": gbs, "bytes_per_cell": bytes_per_cell}
     kname = {28: "fused_step_warp", 56: "fused_step_slab"}.get(info["tile_x"], "fused_step")
+    if args.kernel == "twostep":
+        kname = "fused_step2"
     if args.eps is not None:
         kname = "fused_step_slab_mat" if info["tile_x"] == 56 else "fused_step_warp_mat"
     prof_name = "%s_%s_%s.md" % (kname, w.precision, w.name)
@@ -548,7 +560,11 @@ def run_tetm(args):
                          cells_per_launch=proc),
         "cpu_baseline": cpu,
         "e2e": e2e,
-        "gpu_launches": (10 * K if args.kernel == "reference" else K) + 6 * n_bal,
+        # per balance: the bunch charge, the one fused pass and its second
+        # reduction pass (one material); energy and charge passes separately
+        # (material arrays)
+        "gpu_launches": ((10 * K if args.kernel == "reference" else (K // 2 if args.kernel == "twostep" else K))
+                         + (3 if args.eps is None else 6) * n_bal),
         "clocks": clk,
         "balances": {"records": int(hist.shape[0]), "in_timed_region": n_bal,
                      "ms_per_balance": bal_ms,

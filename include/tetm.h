@@ -58,6 +58,7 @@ extern "C" {
 /* ---- update kernels ------------------------------------------------------ */
 #define TETM_KERNEL_FUSED 0     /* one z-marching launch per step (default)        */
 #define TETM_KERNEL_REFERENCE 1 /* one launch per update equation: 10 per step     */
+#define TETM_KERNEL_TWOSTEP 2   /* block-tiled sweep advancing two steps per pass   */
 
 /* ---- time-stepping schemes ------------------------------------------------ */
 #define TETM_SCHEME_TETM 0      /* the explicit TE/TM scheme, Eq. (23) (default)   */
@@ -234,6 +235,16 @@ int tetm_set_stream(tetm_solver* s, void* cuda_stream);
  * the slab shape 56 x 28 (the defaults); the block-tiled shapes then give
  * TETM_E_UNSUPPORTED. */
 int tetm_set_kernel(tetm_solver* s, int32_t kernel);
+/* TETM_KERNEL_TWOSTEP (temporal blocking of the sweep, Eq. (23) applied twice
+ * per pass over the fields: y^n read once, y^{n+2} written once) needs one
+ * material, the TE/TM scheme, a whole grid and a block-tiled shape of 32 x 4,
+ * 32 x 8 or 64 x 4 (TETM_E_UNSUPPORTED otherwise). tetm_step runs pairs of
+ * steps on it, and single steps on the block-tiled one-step kernel where a
+ * pair would skip a balance or a transverse-wake gather and for an odd last
+ * step. After a call that ended on a pair the previous state is not kept:
+ * tetm_charge_residual answers TETM_E_STATE until a call ends on a single
+ * step. Fields equal the one-step kernel's bit for bit; wake samples are
+ * summed with atomic adds (equal up to rounding). */
 
 /* Fused-kernel work shape: transverse tile tile_x x tile_y and z-chunk
  * length chunk_z >= 4 of one work item. 56 x 28 selects the float32 slab

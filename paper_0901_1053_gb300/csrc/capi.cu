@@ -468,9 +468,27 @@ int do_yee_steps(tetm_solver* s, int n) {
 template <typename T>
 int do_steps(tetm_solver* s, int n) {
   if (s->scheme == TETM_SCHEME_YEE) return do_yee_steps<T>(s, n);
+  bool last_pair = false;
   for (int q = 0; q < n; ++q) {
     const bool bal = s->bal_every > 0 && (s->step + 1) % s->bal_every == 0;
-    if (s->kernel == TETM_KERNEL_FUSED) {
+    if (s->kernel == TETM_KERNEL_TWOSTEP) {
+      // a pair of steps per launch, unless a balance or a transverse gather
+      // falls after its first step or a balance after its second (it needs
+      // the state before)
+      const bool bal2 = s->bal_every > 0 && (s->step + 2) % s->bal_every == 0;
+      StepArgs<T> a = step_args<T>(s, true);
+      last_pair = q + 1 < n && !bal && !bal2 && !(s->bunch && s->obs_on);
+      if (last_pair) {
+        if (s->n_work > 0) CK(launch_fused_two_steps<T>(a, s->tile_x, s->tile_y, s->stream));
+        s->cur = 1 - s->cur;
+        s->step += 2;
+        ++q;
+        continue;
+      }
+      if (s->n_work > 0) CK(launch_fused_step<T>(a, s->tile_x, s->tile_y, s->stream));
+      if (s->bunch && s->obs_on) CK(launch_transverse_after_step<T>(a, s->stream));
+      s->cur = 1 - s->cur;
+    } else if (s->kernel == TETM_KERNEL_FUSED) {
       StepArgs<T> a = step_args<T>(s, true);
       if (s->n_work > 0) {
         if (warp_shape_ok(s->tile_x, s->tile_y)) {
@@ -514,7 +532,8 @@ int do_steps(tetm_solver* s, int n) {
       s->hist_count += 1;
     }
   }
-  if (n > 0) s->prev_valid = true;
+  // after a pair the other field set holds the state two steps back
+  if (n > 0) s->prev_valid = !last_pair;
   return TETM_OK;
 }
 
@@ -824,8 +843,12 @@ int tetm_set_stream(tetm_solver* s, void* st) {
 }
 
 int tetm_set_kernel(tetm_solver* s, int32_t kernel) {
-  if (!s || (kernel != TETM_KERNEL_FUSED && kernel != TETM_KERNEL_REFERENCE)) return TETM_E_ARG;
+  if (!s || (kernel != TETM_KERNEL_FUSED && kernel != TETM_KERNEL_REFERENCE && kernel != TETM_KERNEL_TWOSTEP))
+    return TETM_E_ARG;
   if (s->in_batch) return TETM_E_STATE;
+  if (kernel == TETM_KERNEL_TWOSTEP &&
+      (!s->uniform || s->is_slab() || s->scheme != TETM_SCHEME_TETM || !fused2_shape_ok(s->tile_x, s->tile_y)))
+    return TETM_E_UNSUPPORTED;
   if (kernel == TETM_KERNEL_REFERENCE && s->is_slab()) return TETM_E_UNSUPPORTED;  // it updates ghost planes in place
   // (Yee's scheme runs material arrays on the reference updates whatever the kernel)
   if (kernel == TETM_KERNEL_FUSED && !s->uniform && s->tile_x != 28 && !slab_shape_ok(s->tile_x, s->tile_y) &&
@@ -854,6 +877,7 @@ int tetm_set_tiling(tetm_solver* s, int32_t tile_x, int32_t tile_y, int32_t chun
     return TETM_E_UNSUPPORTED;
   // the slab kernel is float32 only
   if (slab_shape_ok(tx, ty) && s->esz != 4) return TETM_E_UNSUPPORTED;
+  if (s->kernel == TETM_KERNEL_TWOSTEP && !fused2_shape_ok(tx, ty)) return TETM_E_UNSUPPORTED;
   if (tx == s->tile_x && ty == s->tile_y && cz == s->chunk_z && s->work) return TETM_OK;
   s->tile_x = tx;
   s->tile_y = ty;
@@ -864,7 +888,7 @@ int tetm_set_tiling(tetm_solver* s, int32_t tile_x, int32_t tile_y, int32_t chun
 int tetm_set_scheme(tetm_solver* s, int32_t scheme) {
   if (!s || (scheme != TETM_SCHEME_TETM && scheme != TETM_SCHEME_YEE)) return TETM_E_ARG;
   if (scheme == s->scheme) return TETM_OK;
-  if (s->is_slab()) return TETM_E_UNSUPPORTED;
+  if (s->is_slab() || s->kernel == TETM_KERNEL_TWOSTEP) return TETM_E_UNSUPPORTED;
   if (s->step != 0 || s->bunch || s->in_batch || s->bal_every > 0) return TETM_E_STATE;
   if (scheme == TETM_SCHEME_YEE) {
     const double dx = s->g.dx, dy = s->g.dy, dz = s->g.dz;

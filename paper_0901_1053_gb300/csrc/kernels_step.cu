@@ -260,6 +260,206 @@ fused_step(const StepArgs<T> a) {
   }
 }
 
+// ---------------------------------------------------------------------------
+// Two steps per pass (temporal blocking): y^n is read once and y^{n+2}
+// written once per two steps. Same block-tiled sweep and arithmetic as
+// fused_step, with a halo of four nodes per side: the first step is valid on
+// the inner (TX+4) x (TY+4) nodes, the second, which rides one plane behind
+// it and reads its results from registers and the exchange planes, on the
+// owned TX x TY. A chunk [k0, k1) computes the first step's TM stage from
+// plane k0-2 and its TE stage from k0-1 up to k1, the second step's TM stage
+// from k0-1 and its TE stage on [k0, k1). Both steps deposit their bunch
+// current in their halo computations too; each adds its wake samples for its
+// owned nodes and planes with an atomic add (the second step of one chunk and
+// the first step of the next may add to the same sample).
+// ---------------------------------------------------------------------------
+template <typename T>
+__device__ __forceinline__ T ld_plane(const T* __restrict__ p, long long id, bool ok) {
+  return ok ? p[id] : T(0);
+}
+
+template <typename T, int TX, int TY>
+__global__ void __launch_bounds__((TX + 8) * (TY + 8))
+fused_step2(const StepArgs<T> a) {
+  constexpr int WX = TX + 8, WY = TY + 8;  // thread columns: tile + halo of 4 per side
+  constexpr int SX = WX + 2, SY = WY + 2;  // shared planes with a zero border of 1
+  __shared__ T sA[SY][SX], sB[SY][SX], sC[SY][SX], sD[SY][SX], sE[SY][SX];
+
+  const int tx = threadIdx.x, ty = threadIdx.y;
+  const int tid = ty * WX + tx;
+  for (int q = tid; q < SX * SY; q += WX * WY) {
+    (&sA[0][0])[q] = T(0); (&sB[0][0])[q] = T(0); (&sC[0][0])[q] = T(0);
+    (&sD[0][0])[q] = T(0); (&sE[0][0])[q] = T(0);
+  }
+
+  const int item = a.work ? a.work[blockIdx.x] : (int)blockIdx.x;
+  const int ntile = a.tiles_x * a.tiles_y;
+  const int tile = item % ntile, chunk = item / ntile;
+  const int gi = (tile % a.tiles_x) * TX - 4 + tx;
+  const int gj = (tile / a.tiles_x) * TY - 4 + ty;
+  const Layout L = a.L;
+  const int ci = min(max(gi, -2), L.nx + 1);
+  const int cj = min(max(gj, -2), L.ny + 1);
+  const bool own = tx >= 4 && tx < TX + 4 && ty >= 4 && ty < TY + 4 && gi < L.nx && gj < L.ny;
+  const bool line = a.b.on && gi == a.b.i0 && gj == a.b.j0;
+  const int k0 = chunk * a.chunk_z;
+  const int k1 = min(k0 + a.chunk_z, L.nz);
+  const long long SZ = L.sz;
+  const int sx = tx + 1, sy = ty + 1;
+
+  const T* __restrict__ iex = a.in[kEX];
+  const T* __restrict__ iey = a.in[kEY];
+  const T* __restrict__ iez = a.in[kEZ];
+  const T* __restrict__ ihx = a.in[kHX];
+  const T* __restrict__ ihy = a.in[kHY];
+  const T* __restrict__ ihz = a.in[kHZ];
+  const uint8_t* __restrict__ msk = a.co.mask;
+  const T uEX = a.co.u[kEX], uEY = a.co.u[kEY], uEZ = a.co.u[kEZ];
+  const T uHX = a.co.u[kHX], uHY = a.co.u[kHY], uHZ = a.co.u[kHZ];
+
+  // planes -1 .. nz+1 exist in the layout (the outer ones are zero guards);
+  // the pass reaches from k0-2 to k1+2, so planes beyond read as zero
+  auto plane_ok = [&](int k) { return k >= -1 && k <= L.nz + 1; };
+  const int ks = k0 - 2;
+  long long id = ((long long)(ks + 1) * (L.ny + 4) + (cj + 2)) * L.px + (ci + L.ox);
+  // first-step inputs of plane ks (and e_x, e_y of plane ks+1)
+  T ex0a = ld_plane(iex, id, plane_ok(ks)), ey0a = ld_plane(iey, id, plane_ok(ks));
+  T ex0b = ld_plane(iex, id + SZ, plane_ok(ks + 1)), ey0b = ld_plane(iey, id + SZ, plane_ok(ks + 1));
+  T ez0 = ld_plane(iez, id, plane_ok(ks)), hx0 = ld_plane(ihx, id, plane_ok(ks));
+  T hy0 = ld_plane(ihy, id, plane_ok(ks)), hz0 = ld_plane(ihz, id, plane_ok(ks));
+  uint8_t m0 = plane_ok(ks) ? msk[id] : (uint8_t)0;
+  // carried: first-step results of the plane below (all six components and
+  // its activity byte), second-step h_x, h_y of the plane below that
+  T hx1p = T(0), hy1p = T(0), ez1p = T(0), ex1p = T(0), ey1p = T(0), hz1p = T(0);
+  uint8_t mp = 0;
+  T hx2p = T(0), hy2p = T(0);
+  __syncthreads();
+
+  for (int k = ks; k <= k1; ++k, id += SZ) {
+    const bool okn = plane_ok(k + 1), okn2 = plane_ok(k + 2);
+    const T nez = ld_plane(iez, id + SZ, okn), nhx = ld_plane(ihx, id + SZ, okn);
+    const T nhy = ld_plane(ihy, id + SZ, okn), nhz = ld_plane(ihz, id + SZ, okn);
+    const uint8_t nm = okn ? msk[id + SZ] : (uint8_t)0;
+    const T nex = ld_plane(iex, id + 2 * SZ, okn2), ney = ld_plane(iey, id + 2 * SZ, okn2);
+
+    // ======== first step (time n -> n+1) at plane k ========
+    const T cHX = (m0 & 8) ? uHX : T(0), cHY = (m0 & 16) ? uHY : T(0), cEZ = (m0 & 4) ? uEZ : T(0);
+    sA[sy][sx] = ez0;
+    sB[sy][sx] = hz0;
+    __syncthreads();
+    const T dey = ey0b - ey0a, dex = ex0b - ex0a;
+    const T hxa = hx0 + cHX * (dey - (sA[sy + 1][sx] - ez0));   // U1
+    const T hya = hy0 + cHY * (-dex + (sA[sy][sx + 1] - ez0));  // U2
+    sC[sy][sx] = hxa;
+    sD[sy][sx] = hya;
+    __syncthreads();
+    T cur = (sC[sy - 1][sx] - hxa) - (sD[sy][sx - 1] - hya);
+    if (line) {
+      const long long d = (long long)k - (a.n + a.b.kshift) + a.b.c0;
+      if (d >= -a.b.c0 && d < a.b.c0) cur -= a.b.J[d + a.b.c0];
+    }
+    const T ez1 = ez0 + cEZ * cur;                               // U3
+    sE[sy][sx] = ez1;
+    __syncthreads();
+    const T hx1 = hxa + cHX * (dey - (sE[sy + 1][sx] - ez1));   // U4
+    const T hy1 = hya + cHY * (-dex + (sE[sy][sx + 1] - ez1));  // U5
+    if (own && line && k >= k0 && k < k1) {
+      const long long mm = (a.n + a.b.kshift) - k - a.b.c0;
+      if (mm >= a.b.m_min && mm <= a.b.m_max) atomicAdd(a.b.W + (mm - a.b.m_min), -(double)ez1 * a.b.inv_q);
+    }
+    T ex1 = T(0), ey1 = T(0), hz1 = T(0);
+    if (k >= k0 - 1) {
+      const T cEX = (m0 & 1) ? uEX : T(0), cEY = (m0 & 2) ? uEY : T(0), cHZ = (m0 & 32) ? uHZ : T(0);
+      const T dhy = hy1p - hy1, dhx = hx1p - hx1;
+      const T exa = ex0a + cEX * (dhy - (sB[sy - 1][sx] - hz0));    // U6
+      const T eya = ey0a + cEY * (-dhx + (sB[sy][sx - 1] - hz0));   // U7
+      __syncthreads();  // the TM stage's reads of sC, sD are done
+      sC[sy][sx] = exa;
+      sD[sy][sx] = eya;
+      __syncthreads();
+      hz1 = hz0 + cHZ * ((sC[sy + 1][sx] - exa) - (sD[sy][sx + 1] - eya));  // U8
+      __syncthreads();  // the TM stage's reads of sE are done
+      sE[sy][sx] = hz1;
+      __syncthreads();
+      ex1 = exa + cEX * (dhy - (sE[sy - 1][sx] - hz1));   // U9
+      ey1 = eya + cEY * (-dhx + (sE[sy][sx - 1] - hz1));  // U10
+    }
+
+    // ======== second step (time n+1 -> n+2) at plane p = k-1 ========
+    if (k >= k0) {
+      const int p = k - 1;
+      const T cHX2 = (mp & 8) ? uHX : T(0), cHY2 = (mp & 16) ? uHY : T(0), cEZ2 = (mp & 4) ? uEZ : T(0);
+      __syncthreads();  // the first step's reads of every exchange plane are done
+      sA[sy][sx] = ez1p;
+      sB[sy][sx] = hz1p;
+      __syncthreads();
+      const T dey2 = ey1 - ey1p, dex2 = ex1 - ex1p;
+      const T hxa2 = hx1p + cHX2 * (dey2 - (sA[sy + 1][sx] - ez1p));   // U1
+      const T hya2 = hy1p + cHY2 * (-dex2 + (sA[sy][sx + 1] - ez1p));  // U2
+      sC[sy][sx] = hxa2;
+      sD[sy][sx] = hya2;
+      __syncthreads();
+      T cur2 = (sC[sy - 1][sx] - hxa2) - (sD[sy][sx - 1] - hya2);
+      if (line) {
+        const long long d = (long long)p - (a.n + 1 + a.b.kshift) + a.b.c0;
+        if (d >= -a.b.c0 && d < a.b.c0) cur2 -= a.b.J[d + a.b.c0];
+      }
+      const T ez2 = ez1p + cEZ2 * cur2;                                 // U3
+      sE[sy][sx] = ez2;
+      __syncthreads();
+      const T hx2 = hxa2 + cHX2 * (dey2 - (sE[sy + 1][sx] - ez2));     // U4
+      const T hy2 = hya2 + cHY2 * (-dex2 + (sE[sy][sx + 1] - ez2));    // U5
+      if (p >= k0) {
+        const long long idp = id - SZ;
+        if (own) {
+          a.out[kHX][idp] = hx2;
+          a.out[kHY][idp] = hy2;
+          a.out[kEZ][idp] = ez2;
+          if (line) {
+            const long long mm = (a.n + 1 + a.b.kshift) - p - a.b.c0;
+            if (mm >= a.b.m_min && mm <= a.b.m_max)
+              atomicAdd(a.b.W + (mm - a.b.m_min), -(double)ez2 * a.b.inv_q);
+          }
+        }
+        const T cEX2 = (mp & 1) ? uEX : T(0), cEY2 = (mp & 2) ? uEY : T(0), cHZ2 = (mp & 32) ? uHZ : T(0);
+        const T dhy2 = hy2p - hy2, dhx2 = hx2p - hx2;
+        const T exa2 = ex1p + cEX2 * (dhy2 - (sB[sy - 1][sx] - hz1p));    // U6
+        const T eya2 = ey1p + cEY2 * (-dhx2 + (sB[sy][sx - 1] - hz1p));   // U7
+        __syncthreads();
+        sC[sy][sx] = exa2;
+        sD[sy][sx] = eya2;
+        __syncthreads();
+        const T hz2 = hz1p + cHZ2 * ((sC[sy + 1][sx] - exa2) - (sD[sy][sx + 1] - eya2));  // U8
+        __syncthreads();
+        sE[sy][sx] = hz2;
+        __syncthreads();
+        const T ex2 = exa2 + cEX2 * (dhy2 - (sE[sy - 1][sx] - hz2));   // U9
+        const T ey2 = eya2 + cEY2 * (-dhx2 + (sE[sy][sx - 1] - hz2));  // U10
+        if (own) {
+          a.out[kEX][idp] = ex2;
+          a.out[kEY][idp] = ey2;
+          a.out[kHZ][idp] = hz2;
+        }
+      }
+      hx2p = hx2;
+      hy2p = hy2;
+    }
+    __syncthreads();  // the next plane's first writes follow every read of this one
+    // shift: first-step results of plane k become the second step's inputs
+    hx1p = hx1; hy1p = hy1; ez1p = ez1; ex1p = ex1; ey1p = ey1; hz1p = hz1; mp = m0;
+    ex0a = ex0b; ey0a = ey0b; ex0b = nex; ey0b = ney;
+    ez0 = nez; hx0 = nhx; hy0 = nhy; hz0 = nhz; m0 = nm;
+  }
+}
+
+template <typename T, int TX, int TY>
+cudaError_t launch_fused2_shape(const StepArgs<T>& a, cudaStream_t st) {
+  const int items = a.work ? a.n_work : a.tiles_x * a.tiles_y * a.n_chunks;
+  if (items <= 0) return cudaSuccess;
+  fused_step2<T, TX, TY><<<items, dim3(TX + 8, TY + 8), 0, st>>>(a);
+  return cudaGetLastError();
+}
+
 template <typename T, int TX, int TY>
 cudaError_t launch_fused_shape(const StepArgs<T>& a, cudaStream_t st) {
   const int items = a.work ? a.n_work : a.tiles_x * a.tiles_y * a.n_chunks;
@@ -284,6 +484,16 @@ cudaError_t launch_fused_step(const StepArgs<T>& a, int tx, int ty, cudaStream_t
   return cudaErrorInvalidValue;
 }
 
+bool fused2_shape_ok(int tx, int ty) { return (tx == 32 && (ty == 4 || ty == 8)) || (tx == 64 && ty == 4); }
+
+template <typename T>
+cudaError_t launch_fused_two_steps(const StepArgs<T>& a, int tx, int ty, cudaStream_t st) {
+  if (tx == 32 && ty == 4) return launch_fused2_shape<T, 32, 4>(a, st);
+  if (tx == 32 && ty == 8) return launch_fused2_shape<T, 32, 8>(a, st);
+  if (tx == 64 && ty == 4) return launch_fused2_shape<T, 64, 4>(a, st);
+  return cudaErrorInvalidValue;
+}
+
 template <typename T>
 cudaError_t launch_reference_step(const StepArgs<T>& a, cudaStream_t st) {
   if (a.L.nz > 65535) return cudaErrorInvalidConfiguration;  // one grid z-slice per plane
@@ -303,6 +513,8 @@ cudaError_t launch_reference_step(const StepArgs<T>& a, cudaStream_t st) {
   return cudaGetLastError();
 }
 
+template cudaError_t launch_fused_two_steps<float>(const StepArgs<float>&, int, int, cudaStream_t);
+template cudaError_t launch_fused_two_steps<double>(const StepArgs<double>&, int, int, cudaStream_t);
 template cudaError_t launch_fused_step<float>(const StepArgs<float>&, int, int, cudaStream_t);
 template cudaError_t launch_fused_step<double>(const StepArgs<double>&, int, int, cudaStream_t);
 template cudaError_t launch_reference_step<float>(const StepArgs<float>&, cudaStream_t);

@@ -117,6 +117,11 @@ cudaError_t launch_reference_step(const StepArgs<T>& a, cudaStream_t st);
 template <typename T>
 cudaError_t launch_fused_step(const StepArgs<T>& a, int tile_x, int tile_y, cudaStream_t st);
 bool fused_shape_ok(int tile_x, int tile_y);
+// two steps per pass of the block-tiled sweep (temporal blocking); shapes
+// 32 x 4, 32 x 8, 64 x 4; one material
+template <typename T>
+cudaError_t launch_fused_two_steps(const StepArgs<T>& a, int tile_x, int tile_y, cudaStream_t st);
+bool fused2_shape_ok(int tile_x, int tile_y);
 // ---- warp-tiled fused step (kernels_warp.cu): tile 28 x tile_y ----------
 template <typename T>
 cudaError_t launch_fused_warp_step(const StepArgs<T>& a, int tile_x, int tile_y, cudaStream_t st);

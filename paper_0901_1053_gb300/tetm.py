@@ -32,6 +32,7 @@ TETM_FP64 = 0
 TETM_FP32 = 1
 TETM_KERNEL_FUSED = 0
 TETM_KERNEL_REFERENCE = 1
+TETM_KERNEL_TWOSTEP = 2
 TETM_SCHEME_TETM = 0
 TETM_SCHEME_YEE = 1
 COMPONENTS = ("ex", "ey", "ez", "hx", "hy", "hz")
@@ -387,7 +388,8 @@ class Solver:
         _check(lib.tetm_set_stream(self.h, ctypes.c_void_p(stream or 0)), "tetm_set_stream")
 
     def set_kernel(self, kernel):
-        k = {"fused": TETM_KERNEL_FUSED, "reference": TETM_KERNEL_REFERENCE}.get(kernel, kernel)
+        k = {"fused": TETM_KERNEL_FUSED, "reference": TETM_KERNEL_REFERENCE,
+             "twostep": TETM_KERNEL_TWOSTEP}.get(kernel, kernel)
         _check(lib.tetm_set_kernel(self.h, int(k)), "tetm_set_kernel")
 
     def set_tiling(self, tile_x=0, tile_y=0, chunk_z=0):
