@@ -121,6 +121,15 @@ __device__ __forceinline__ unsigned ld_word_if(const uint8_t* p, bool c) {
       : "l"(p), "r"((unsigned)c));
   return v;
 }
+// 16 bytes into shared memory by an asynchronous copy, or (c false) 16 zero
+// bytes without a global read
+__device__ __forceinline__ void cp16_or_zero(void* sdst, const void* gsrc, bool c) {
+  asm volatile("cp.async.cg.shared.global [%0], [%1], 16, %2;" ::"r"(su32(sdst)), "l"(gsrc), "r"(c ? 16u : 0u)
+               : "memory");
+}
+__device__ __forceinline__ void cp_commit() { asm volatile("cp.async.commit_group;" ::: "memory"); }
+template <int N>
+__device__ __forceinline__ void cp_wait() { asm volatile("cp.async.wait_group %0;" ::"n"(N) : "memory"); }
 // the quad's word holds one activity byte per node: component c of any node
 __device__ __forceinline__ bool has(unsigned m, int c) { return (m & (0x01010101u << c)) != 0u; }
 
@@ -207,14 +216,33 @@ __device__ __forceinline__ bool slab_item(const StepArgs<float>& a, const CUtens
       for (int c = 0; c < 6; ++c) tma3(&S.co[s][c][0][0], &tm_co->m[c], cx, cy, k + 1, &S.bar[s]);
     }
   };
-  if (tid == 0)
-    for (int k = kstart; k < kstart + min(kSD, nplanes); ++k) issue(k);
-  int issued = kstart + min(kSD, nplanes) - 1;  // last plane queued (the same in every thread)
-
+  // one material: each thread copies the e_z and h_z quad of its own node
+  // row and columns into the slot, only where one of the quad's nodes
+  // carries that component (zeros otherwise: the entry holds zero), so the
+  // ring reads no pipe wall; completion by the thread's copy group and the
+  // block barrier after it
+  auto issue_q = [&](int k, unsigned mw) {
+    const int s = (k - kstart) % kSD;
+    const long long g = inq ? gidx(k) : 0;
+    cp16_or_zero(&S.ez[s][row * kSX + 4 * q], a.in[kEZ] + g, has(mw, kEZ));
+    cp16_or_zero(&S.hz[s][row * kSX + 4 * q], a.in[kHZ] + g, has(mw, kHZ));
+  };
   // activity words of planes kstart .. kstart + 2 (m0 of the plane being
   // worked on, m1, m2 of the next two); z-state and the register prefetch
   // (plane k: hx, hy of k; ex, ey of k+1)
   unsigned m0 = word(kstart), m1 = word(kstart + 1), m2 = word(kstart + 2);
+  if constexpr (MAT) {
+    if (tid == 0)
+      for (int k = kstart; k < kstart + min(kSD, nplanes); ++k) issue(k);
+  } else {
+    issue_q(kstart, m0);
+    cp_commit();
+    if (nplanes > 1) issue_q(kstart + 1, m1);
+    cp_commit();
+    cp_wait<1>();
+    __syncthreads();  // plane kstart's slot is in
+  }
+  int issued = kstart + min(kSD, nplanes) - 1;  // last plane queued (the same in every thread)
   Q4 ex0 = load_if(a.in[kEX], kstart, has(m0, kEX)), ey0 = load_if(a.in[kEY], kstart, has(m0, kEY));
   Q4 hxc = load_if(a.in[kHX], kstart, has(m0, kHX)), hyc = load_if(a.in[kHY], kstart, has(m0, kHY));
   Q4 ex1 = load_if(a.in[kEX], kstart + 1, has(m1, kEX)), ey1 = load_if(a.in[kEY], kstart + 1, has(m1, kEY));
@@ -226,8 +254,9 @@ __device__ __forceinline__ bool slab_item(const StepArgs<float>& a, const CUtens
     const int s = (k - kstart) % kSD;
     // every thread waits for the slot itself; the block decides at barrier
     // (1) (a thread whose wait gave up computes on stale data until then,
-    // nothing is stored before it)
-    const bool ok = bar_wait(&S.bar[s], (phases >> s) & 1u);
+    // nothing is stored before it). One material: the slot is in already.
+    bool ok = true;
+    if constexpr (MAT) ok = bar_wait(&S.bar[s], (phases >> s) & 1u);
     // next plane's register inputs and the activity word three planes on, early
     Q4 hxn_in, hyn_in, exn_in, eyn_in;
     unsigned m3 = 0u;
@@ -298,10 +327,15 @@ __device__ __forceinline__ bool slab_item(const StepArgs<float>& a, const CUtens
       failed = true;
       break;
     }
-    phases ^= 1u << s;
-    if (k + kSD < k1) {
-      if (tid == 0) issue(k + kSD);
-      issued = k + kSD;
+    if constexpr (MAT) {
+      phases ^= 1u << s;
+      if (k + kSD < k1) {
+        if (tid == 0) issue(k + kSD);
+        issued = k + kSD;
+      }
+    } else {
+      if (k + kSD < k1) issue_q(k + kSD, m2);
+      cp_commit();
     }
     // S2: ez' = ez + 2a M^-1 (P_y^T hx~ - P_x^T hy~ - jj_z)
     const Q4 hxaD = row >= 1 ? lds4(&S.x1[row - 1][4 * q]) : zero;
@@ -371,7 +405,8 @@ __device__ __forceinline__ bool slab_item(const StepArgs<float>& a, const CUtens
       hzn.v[e] = hz.v[e] + cHZ[e] * ((exaU.v[e] - exa.v[e]) - (eyx - eya.v[e]));      // U8
     }
     sts4(&S.x2[row][4 * q], hzn);
-    __syncthreads();  // (4)
+    if constexpr (!MAT) cp_wait<1>();  // this thread's copies of the next plane are in
+    __syncthreads();  // (4) (and the next plane's slot is in)
     // S6: ex', ey'
     const Q4 hznD = row >= 1 ? lds4(&S.x2[row - 1][4 * q]) : zero;
     const float hznL = left_of(hzn.v[3], q);
@@ -400,6 +435,7 @@ __device__ __forceinline__ bool slab_item(const StepArgs<float>& a, const CUtens
       ey1 = eyn_in;
     }
   }
+  if constexpr (!MAT) cp_wait<0>();
   __syncthreads();  // every thread is done with the ring before the next item refills it
   return !failed;
 }
