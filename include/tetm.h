@@ -160,7 +160,8 @@ int tetm_set_bunch_static(tetm_solver* s, double sigma_z, double charge, int32_t
 int tetm_step(tetm_solver* s, int32_t n);
 
 /* Wait for the solver's stream (synchronizes). TETM_E_TIMEOUT when a bounded
- * wait of the slab kernel gave up (a tensor copy that did not land). */
+ * wait of the slab kernel gave up (a tensor copy of its material-array
+ * instantiation that did not land). */
 int tetm_sync(tetm_solver* s);
 
 /* Longitudinal wake W(s_m) [V/C], W(s) = -(1/Q) * integral of E_z along the
@@ -248,10 +249,12 @@ int tetm_set_kernel(tetm_solver* s, int32_t kernel);
 
 /* Fused-kernel work shape: transverse tile tile_x x tile_y and z-chunk
  * length chunk_z >= 4 of one work item. 56 x 28 selects the float32 slab
- * kernel (one CTA of 512 threads per SM, tensor-staged e_z, h_z and activity
- * bytes, or with material arrays e_z, h_z and the six coefficient arrays;
- * TETM_E_UNSUPPORTED in float64; the float32 default, chunk 32); tile_x = 28
- * the warp-tiled kernel (one warp per item, tile_y in {4, 8, 12, 16, 20, 28};
+ * kernel (one CTA of 512 threads per SM; e_z, h_z staged in shared memory
+ * by per-thread asynchronous copies of the quads that carry them, or with
+ * material arrays by tensor copies of e_z, h_z and the six coefficient
+ * arrays; TETM_E_UNSUPPORTED in float64; the float32 default, chunk 32);
+ * tile_x = 28 the warp-tiled kernel (one warp per item, tile_y in {4, 8,
+ * 12, 16, 20, 28};
  * the float64 default, 28 x 20 x 32); tile_x = 32 (tile_y in {4, 8, 16}) or
  * 64 (tile_y in {4, 8}) the block-tiled kernel (one material only). Any value
  * 0 keeps the current one. TETM_E_ARG for other values. */

@@ -4,11 +4,10 @@
 // advanced there (ping-pong swap, step count, retirement at the member's step
 // limit), which lets a run of steps be captured once as a CUDA graph and
 // replayed. Float32 batches on the slab kernel's tile (56 x 28) run the
-// batched slab kernel (each member's tensor maps in device memory), the
-// others the batched warp-tiled kernel.
+// batched slab kernel, the others the batched warp-tiled kernel.
 //
 // A batch is a table of slots. Members join and leave between step calls:
-// a join writes the member's descriptor (and tensor maps) into a free slot, a
+// a join writes the member's descriptor into a free slot, a
 // leave clears the slot, and the combined (slot, item) work list is uploaded
 // before the next step; all three are copies queued on the batch's stream
 // from pinned host memory, so the host never waits for the GPU and the
@@ -47,7 +46,6 @@ struct tetm_batch {
   int tile_x, tile_y;
   bool slab;                       // the batched slab kernel (float32, 56 x 28 tiles)
   void* d_members;                 // BatchMember<T>[capacity]
-  SlabBatchMaps* d_maps;           // [capacity] (slab batches)
   int* d_wbuf;                     // kHead ints (entry count first), then int2 entries
   int wcap;                        // entries d_wbuf holds
   int n_work;                      // entries of the list last uploaded
@@ -164,7 +162,7 @@ cudaError_t launch_one(tetm_batch* b) {
   const int2* work = reinterpret_cast<const int2*>(b->d_wbuf + kHead);
   if constexpr (sizeof(T) == 4) {
     if (b->slab)
-      return launch_fused_slab_batch((BatchMember<float>*)b->d_members, b->d_maps, b->capacity, work, b->d_wbuf,
+      return launch_fused_slab_batch((BatchMember<float>*)b->d_members, b->capacity, work, b->d_wbuf,
                                      b->wcap, b->err, b->sched, b->nz_max, b->stream);
   }
   return launch_fused_warp_batch<T>((const BatchMember<T>*)b->d_members, b->capacity, work, b->d_wbuf, b->wcap,
@@ -233,7 +231,6 @@ void release(tetm_batch* b) {
   if (b->stream) {
     dev_free(b->d_members, b->stream);
     dev_free(b->d_wbuf, b->stream);
-    dev_free(b->d_maps, b->stream);
     dev_free(b->sched, b->stream);
     dev_free(b->err, b->stream);
     cudaStreamSynchronize(b->stream);
@@ -287,18 +284,14 @@ int create_slots(int capacity, size_t esz, int tile_x, int tile_y, int graph_ste
       (dev_alloc(&b->d_members, mbytes, b->stream) != cudaSuccess ||
        dev_alloc((void**)&b->d_wbuf, wbytes, b->stream) != cudaSuccess ||
        dev_alloc((void**)&b->sched, 2 * sizeof(int), b->stream) != cudaSuccess ||
-       dev_alloc((void**)&b->err, sizeof(int), b->stream) != cudaSuccess ||
-       (b->slab && dev_alloc((void**)&b->d_maps, sizeof(SlabBatchMaps) * (size_t)capacity, b->stream) !=
-                       cudaSuccess)))
+       dev_alloc((void**)&b->err, sizeof(int), b->stream) != cudaSuccess))
     rc = TETM_E_NOMEM;
   // every slot starts empty (inactive), the list empty, the counters zero
   if (rc == TETM_OK &&
       (cudaMemsetAsync(b->d_members, 0, mbytes, b->stream) != cudaSuccess ||
        cudaMemsetAsync(b->d_wbuf, 0, wbytes, b->stream) != cudaSuccess ||
        cudaMemsetAsync(b->sched, 0, 2 * sizeof(int), b->stream) != cudaSuccess ||
-       cudaMemsetAsync(b->err, 0, sizeof(int), b->stream) != cudaSuccess ||
-       (b->d_maps && cudaMemsetAsync(b->d_maps, 0, sizeof(SlabBatchMaps) * (size_t)capacity, b->stream) !=
-                         cudaSuccess)))
+       cudaMemsetAsync(b->err, 0, sizeof(int), b->stream) != cudaSuccess))
     rc = TETM_E_CUDA;
   if (rc != TETM_OK) {
     cudaGetLastError();
@@ -342,15 +335,6 @@ int add_member(tetm_batch* b, tetm_solver* s, long long limit, int* slot_out) {
     rc = rebuild_work(s);
     if (rc != TETM_OK) return rc;
   }
-  SlabBatchMaps hm;
-  if (b->slab) {  // the member's tensor maps of e_z, h_z of both sets
-    SlabMaps m;
-    void* ez[2] = {s->set[0][kEZ], s->set[1][kEZ]};
-    void* hz[2] = {s->set[0][kHZ], s->set[1][kHZ]};
-    if (build_slab_maps(&m, ez, hz, nullptr, s->L) != 0) return TETM_E_UNSUPPORTED;
-    memcpy(hm.ez, m.ez, sizeof(m.ez));
-    memcpy(hm.hz, m.hz, sizeof(m.hz));
-  }
   // the batch's stream first waits for the work queued on the member's own
   // stream (its creation and set-up)
   if (cudaEventRecord(b->order_ev, s->stream) != cudaSuccess ||
@@ -358,7 +342,6 @@ int add_member(tetm_batch* b, tetm_solver* s, long long limit, int* slot_out) {
     return TETM_E_CUDA;
   b->limit[(size_t)i] = limit;
   rc = b->esz == 8 ? write_member<double>(b, i, s) : write_member<float>(b, i, s);
-  if (rc == TETM_OK && b->slab) rc = stage_copy(b, b->d_maps + i, &hm, sizeof(hm));
   if (rc != TETM_OK) return rc;
   b->slot[(size_t)i] = s;
   s->in_batch = true;

@@ -495,11 +495,13 @@ int do_steps(tetm_solver* s, int n) {
           CK(launch_fused_warp_step<T>(a, s->tile_x, s->tile_y, s->stream));
         } else if (slab_shape_ok(s->tile_x, s->tile_y)) {
           if constexpr (sizeof(T) == 4) {
-            if (!s->slab) {  // tensor maps of both field sets (fixed addresses)
+            if (!s->slab) {  // material arrays: tensor maps of both field sets and the coefficients
               s->slab = new (std::nothrow) SlabMaps();
+              if (!s->slab) return TETM_E_NOMEM;
+              memset(s->slab, 0, sizeof(SlabMaps));  // one material: no tensor copies
               void* ez[2] = {s->set[0][kEZ], s->set[1][kEZ]};
               void* hz[2] = {s->set[0][kHZ], s->set[1][kHZ]};
-              if (!s->slab || build_slab_maps(s->slab, ez, hz, s->uniform ? nullptr : s->ua, s->L) != 0) {
+              if (!s->uniform && build_slab_maps(s->slab, ez, hz, s->ua, s->L) != 0) {
                 delete s->slab;
                 s->slab = nullptr;
                 return TETM_E_UNSUPPORTED;

@@ -18,10 +18,15 @@
 //    carries it (the other field set's entry already holds that zero).
 // e_z and h_z (and with material arrays the six per-entry coefficient arrays)
 // are the inputs a node reads at its neighbours; they arrive through a ring
-// of kSD planes in shared memory, one 3D tensor copy (TMA) per array and plane
-// issued kSD planes ahead, completion on an mbarrier per slot (bounded waits:
-// after kSlabPolls polls the CTA raises the error word, drains the copies in
-// flight and stops).
+// of kSD planes in shared memory, filled kSD planes ahead:
+//  * one material: each thread copies its own quad of e_z and h_z into the
+//    slot with a 16-byte asynchronous copy, or writes zeros without a read
+//    where none of the quad's nodes carries that component, so the ring
+//    reads no pipe wall; completion by the thread's copy group, publication
+//    by the last block barrier of the plane before;
+//  * material arrays: one 3D tensor copy (TMA) per array and plane, completion
+//    on an mbarrier per slot (bounded waits: after kSlabPolls polls the CTA
+//    raises the error word, drains the copies in flight and stops).
 //
 // The intermediates a stage reads one row up or down (hx~, ez', ex~, hz') go
 // through two shared-memory buffers, those one column left or right through
@@ -483,21 +488,16 @@ fused_step_slab(const StepArgs<float> a, const __grid_constant__ CUtensorMap tm_
 }
 
 // Batches: one launch steps every active member (one material, float32);
-// work = (member, item) pairs in member order, the member's arguments and
-// tensor maps (of the set it reads) from device memory.
+// work = (member, item) pairs, the member's arguments from device memory (its
+// e_z, h_z come through the per-thread copies of the one-material ring, so
+// no tensor map is involved).
 __global__ void __launch_bounds__(kSThreads, 1)
-fused_step_slab_batch(const BatchMember<float>* __restrict__ members, const SlabBatchMaps* __restrict__ maps,
-                      const int2* __restrict__ work, const int* __restrict__ n_work_p, int* err, int* sched) {
+fused_step_slab_batch(const BatchMember<float>* __restrict__ members, const int2* __restrict__ work,
+                      const int* __restrict__ n_work_p, int* err, int* sched) {
   using Smem = SlabSmem<false>;
-  constexpr int kSD = Smem::SD;
   extern __shared__ __align__(128) unsigned char slab_raw[];
   Smem& S = *reinterpret_cast<Smem*>(slab_raw);
   const int tid = threadIdx.x;
-  if (tid == 0) {
-    for (int s = 0; s < kSD; ++s) bar_init(&S.bar[s], 1u);
-  }
-  asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
-  __syncthreads();
   unsigned phases = 0;
   const int G = gridDim.x;
   const int n_work = *n_work_p;  // written before the launch (stream order)
@@ -508,14 +508,7 @@ fused_step_slab_batch(const BatchMember<float>* __restrict__ members, const Slab
     const int2 w = work[wi];
     const BatchMember<float>& mb = members[w.x];
     if (mb.active) {
-      const int cur = mb.cur;
-      const CUtensorMap* mez = reinterpret_cast<const CUtensorMap*>(maps[w.x].ez[cur]);
-      const CUtensorMap* mhz = reinterpret_cast<const CUtensorMap*>(maps[w.x].hz[cur]);
-      if (tid == 0) {  // the maps were written before the launch, through the generic proxy
-        asm volatile("fence.proxy.tensormap::generic.acquire.gpu [%0], 128;" ::"l"(mez) : "memory");
-        asm volatile("fence.proxy.tensormap::generic.acquire.gpu [%0], 128;" ::"l"(mhz) : "memory");
-      }
-      ok = slab_item<false>(mb.a, mez, mhz, nullptr, w.y, S, phases, err);
+      ok = slab_item<false>(mb.a, nullptr, nullptr, nullptr, w.y, S, phases, err);
     } else {
       // an item of a member past its limit: no work, but the ticket thread 0
       // wrote above must be visible before every thread reads it (slab_item
@@ -617,7 +610,7 @@ cudaError_t launch_slab(const StepArgs<float>& a, const SlabMaps& m, int cur, in
 }
 }  // namespace
 
-cudaError_t launch_fused_slab_batch(BatchMember<float>* members, const SlabBatchMaps* maps, int n_members,
+cudaError_t launch_fused_slab_batch(BatchMember<float>* members, int n_members,
                                     const int2* work, const int* n_work, int n_bound, int* err, int* sched,
                                     int nz_max, cudaStream_t st) {
   static int sms = 0;
@@ -634,7 +627,7 @@ cudaError_t launch_fused_slab_batch(BatchMember<float>* members, const SlabBatch
     }
   }
   if (n_bound > 0) {
-    fused_step_slab_batch<<<std::min(n_bound, sms), kSThreads, smem, st>>>(members, maps, work, n_work, err, sched);
+    fused_step_slab_batch<<<std::min(n_bound, sms), kSThreads, smem, st>>>(members, work, n_work, err, sched);
     cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess) return e;
   }

@@ -150,17 +150,11 @@ struct SlabMaps {  // tensor maps (CUtensorMap) of e_z and h_z of both field set
 bool slab_shape_ok(int tile_x, int tile_y);
 // co: the six per-entry coefficient arrays, or nullptr (one material)
 int build_slab_maps(SlabMaps* m, void* const ez[2], void* const hz[2], void* const co[6], const Layout& L);
-// Tensor maps of one batch member's e_z, h_z (both field sets), in device
-// memory for the batched slab kernel (one material).
-struct SlabBatchMaps {
-  alignas(128) unsigned char ez[2][128];
-  alignas(128) unsigned char hz[2][128];
-};
 // one step of every active member of a float32 batch on the slab kernel
 // (work = (member, item) pairs counted at n_work in device memory, at most
 // n_bound; sched as below), the transverse wakes, then the device-side
 // advance of all n_members slots
-cudaError_t launch_fused_slab_batch(BatchMember<float>* members, const SlabBatchMaps* maps, int n_members,
+cudaError_t launch_fused_slab_batch(BatchMember<float>* members, int n_members,
                                     const int2* work, const int* n_work, int n_bound, int* err, int* sched,
                                     int nz_max, cudaStream_t st);
 // sched: two ints of device memory, zero before the first launch, that the
