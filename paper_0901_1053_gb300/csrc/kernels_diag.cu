@@ -260,6 +260,11 @@ struct UniformCoef {
   double half_r[6];      // M / 2
   double a2c_hx, a2c_hy; // alpha^2 M^-1 of h_x, h_y faces
   double a2c_ex, a2c_ey; // alpha^2 M^-1 of e_x, e_y edges
+  // float32 fields: the charges' ten coefficients, signs folded in, as float32
+  // pairs (hi + lo equals the float64 value to 2^-48): Eq. (35) a2c_hx (Wy),
+  // a2c_hy (Wx), -M_ez (Z), -M_ey/2 (Y), -M_ex/2 (X); Eq. (34) M_hx/2 (Bx),
+  // M_hy/2 (By), M_hz (Hz), -a2c_ex (T3), -a2c_ey (T4)
+  float qc[10][2];
 };
 template <typename T>
 struct BalanceFields {
@@ -446,6 +451,13 @@ __device__ __forceinline__ void acc_mul2(F2& acc, float a, F2 d) {
   f2_acc(acc, p.hi, fmaf(a, d.lo, p.lo));
 }
 
+// acc += c t for a coefficient pair c and a term pair t, on the float32 pipe
+// (the product's dropped part c.lo t.lo is below 2^-48 of it)
+__device__ __forceinline__ void acc_prod(F2& acc, F2 c, F2 t) {
+  const F2 p = two_prod(c.hi, t.hi);
+  f2_acc(acc, p.hi, fmaf(c.hi, t.lo, fmaf(c.lo, t.hi, p.lo)));
+}
+
 constexpr int kFlush = 8;  // nodes per float32-pair partial before it joins the float64 sum
 constexpr int kPre = 4;    // planes of L2 prefetch ahead of the node being summed
 
@@ -483,6 +495,9 @@ balance_items_f32(BalanceFields<float> bf, const uint8_t* __restrict__ mask, Uni
   double w = 0.0;
   int cnt = 0;
   double me = 0.0, mh = 0.0;
+  // each charge is summed as one float32 pair (coefficient pairs from the
+  // parameters) and widened once
+  auto cq = [&](int q) { return F2{uc.qc[q][0], uc.qc[q][1]}; };
   auto flush = [&]() {
 #pragma unroll
     for (int q = 0; q < 11; ++q) {
@@ -538,11 +553,13 @@ balance_items_f32(BalanceFields<float> bf, const uint8_t* __restrict__ mask, Uni
                                              -2.f * vez), ez[n - sy]), ez[n + sy]);
           const F2 Wx = f2_add(f2_add(f2_add(f2_add(f2_add(F2{2.f * ezb, 0.f}, -ez[n - sz - sx]), -ez[n - sz + sx]),
                                              -2.f * vez), ez[n - sx]), ez[n + sx]);
-          double qe = uc.a2c_hx * f2_wide(Wy);
-          qe = fma(uc.a2c_hy, f2_wide(Wx), qe);
-          qe = fma(-uc.r[kEZ], f2_wide(Z), qe);
-          qe = fma(-uc.half_r[kEY], f2_wide(Y), qe);
-          qe = fma(-uc.half_r[kEX], f2_wide(X), qe);
+          F2 qs{0.f, 0.f};
+          acc_prod(qs, cq(0), Wy);
+          acc_prod(qs, cq(1), Wx);
+          acc_prod(qs, cq(2), Z);
+          acc_prod(qs, cq(3), Y);
+          acc_prod(qs, cq(4), X);
+          double qe = f2_wide(qs);
           if (qline && i == i0 && j == j0) qe -= qline[k];
           me = fmax(me, fabs(qe));
         }
@@ -565,12 +582,13 @@ balance_items_f32(BalanceFields<float> bf, const uint8_t* __restrict__ mask, Uni
           if (mask[f1] & 2) T4 = f2_add(f2_add(T4, -phz[f1 - sx]), z1);
           if (mask[n + sx] & 2) T4 = f2_add(f2_add(T4, -z0), phz[n + sx]);
           if (m0 & 2) T4 = f2_add(f2_add(T4, phz[n - sx]), -z0);
-          double qh = uc.half_r[kHX] * f2_wide(Bx);
-          qh = fma(uc.half_r[kHY], f2_wide(By), qh);
-          qh = fma(uc.r[kHZ], f2_wide(Hz), qh);
-          qh = fma(-uc.a2c_ex, f2_wide(T3), qh);
-          qh = fma(-uc.a2c_ey, f2_wide(T4), qh);
-          mh = fmax(mh, fabs(qh));
+          F2 qs{0.f, 0.f};
+          acc_prod(qs, cq(5), Bx);
+          acc_prod(qs, cq(6), By);
+          acc_prod(qs, cq(7), Hz);
+          acc_prod(qs, cq(8), T3);
+          acc_prod(qs, cq(9), T4);
+          mh = fmax(mh, fabs(f2_wide(qs)));
         }
       }
     }
@@ -699,6 +717,13 @@ cudaError_t launch_balances(const T* const cur[6], const T* const prev[6], const
   uc.a2c_hy = alpha * alpha * minv[kHY];
   uc.a2c_ex = alpha * alpha * minv[kEX];
   uc.a2c_ey = alpha * alpha * minv[kEY];
+  const double qcd[10] = {uc.a2c_hx,       uc.a2c_hy,       -uc.r[kEZ], -uc.half_r[kEY], -uc.half_r[kEX],
+                          uc.half_r[kHX], uc.half_r[kHY], uc.r[kHZ],  -uc.a2c_ex,      -uc.a2c_ey};
+  for (int q = 0; q < 10; ++q) {
+    const float hi = (float)qcd[q];
+    uc.qc[q][0] = hi;
+    uc.qc[q][1] = (float)(qcd[q] - (double)hi);
+  }
   const int nt = balance_threads(wv);
   if constexpr (sizeof(T) == 4) {  // float32 fields: the float32-pipe transformations
     if (prev)
