@@ -81,10 +81,19 @@ typedef struct tetm_rz_info {
 
 typedef struct tetm_rz tetm_rz;
 
-/* Creates a solve (Sec. 4.3). pec: uint8 per cell (1 = PEC), nr*nz entries,
- * or NULL for the empty pipe of radius nr*dr. eps_r, mu_r: reserved, must be
- * NULL (vacuum), else TETM_E_UNSUPPORTED. Fails with TETM_E_UNSTABLE when
- * c*dt > min(dr, dz) (Sec. 4.4). Synchronizes. */
+/* Creates a solve (Sec. 4.3). pec: uint8 per cell (1 = PEC), nr*nz entries
+ * (cell ci + nr*ck), or NULL for the empty pipe of radius nr*dr. eps_r, mu_r:
+ * float64 per cell (>= 1, finite, else TETM_E_ARG) or NULL (vacuum). With
+ * material arrays the per-radian material matrices are the column's metric
+ * over the staircase mean of eps_r of the cells an edge touches (e_r, e_z:
+ * two, e_phi: four, the axis e_z: one) and times the mean of 1/mu_r of the
+ * cells a face touches (h_phi: one, h_r, h_z: two); the coefficients are then
+ * per entry and plane (about (8 esz + 48) bytes per entry and mode more
+ * device memory than tetm_rz_bytes_needed counts), the step runs the
+ * register kernel (tetm_rz_set_kernel of another: TETM_E_UNSUPPORTED) and
+ * the static starts answer TETM_E_UNSUPPORTED (their entry section is
+ * vacuum). Fails with TETM_E_UNSTABLE when c*dt > min(dr, dz) (Sec. 4.4).
+ * Synchronizes. */
 int tetm_rz_create(const tetm_rz_grid* g, const double* eps_r, const double* mu_r,
                    const uint8_t* pec, tetm_rz** out);
 

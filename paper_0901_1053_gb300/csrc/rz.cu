@@ -111,7 +111,9 @@ struct RzArgs {
   T* out;
   RzLayout L;
   const uint8_t* mask;
-  const T* coef;          // [mode][kNCo][pr]
+  const T* coef;          // one material: [mode][kNCo][pr]; material arrays: [mode][rows][kNCo][pr]
+  long long co_mode;      // elements per mode of coef
+  long long co_plane;     // elements per plane row of coef (0: the same coefficients on every plane)
   int m_lo, n_modes;
   int tiles, chunk_z;
   int tile_w, halo;       // owned entries per window and halo entries per side (60/2 or 56/4)
@@ -325,11 +327,13 @@ __device__ __forceinline__ Item<T> item_of(const RzArgs<T>& a, int witem, int su
   return it;
 }
 
+// the lane's coefficients of plane k (k = -1 for a solve of one material,
+// whose coefficients do not depend on the plane)
 template <typename T>
-__device__ __forceinline__ LaneCo<T> lane_coefs(const RzArgs<T>& a, const Item<T>& it) {
+__device__ __forceinline__ LaneCo<T> lane_coefs(const RzArgs<T>& a, const Item<T>& it, int k = -1) {
   LaneCo<T> c;
   const long long PR = a.L.pr;
-  const T* co = a.coef + (long long)it.mode * kNCo * PR + a.L.col(it.gi);
+  const T* co = a.coef + (long long)it.mode * a.co_mode + (long long)(k + 1) * a.co_plane + a.L.col(it.gi);
 #pragma unroll
   for (int e = 0; e < 2; ++e) {
     c.er[e] = co[kCoER * PR + e];
@@ -389,10 +393,11 @@ __device__ __forceinline__ void gather_wake(const RzArgs<T>& a, const Item<T>& i
 }
 
 // --- register-ring variant ---------------------------------------------------
-template <typename T, bool SC>
+// MAT: per-entry material coefficients, read with each plane
+template <typename T, bool SC, bool MAT>
 __device__ __forceinline__ void rz_item_reg(const RzArgs<T>& a, int witem, int sub) {
   const Item<T> it = item_of(a, witem, sub);
-  const LaneCo<T> c = lane_coefs(a, it);
+  LaneCo<T> c = lane_coefs(a, it);
   const T mm = T(a.m_lo + it.mode);
   const long long RS = a.L.pr * 6;  // field elements per row
   const long long MS = a.L.pr;      // mask elements per row
@@ -425,6 +430,7 @@ __device__ __forceinline__ void rz_item_reg(const RzArgs<T>& a, int witem, int s
       const int k = kb + u;
       if (k >= it.k1) break;
       T out[12], er_old[2];
+      if constexpr (MAT) c = lane_coefs(a, it, k);
       rz_plane(ring[u], ring[(u + 1) % R], c, mm, s, current_at(a, it, it.src0, k),
                current_at(a, it, it.src1, k), out, er_old);
       if (SC) add_source(a, it, k, out);
@@ -439,7 +445,7 @@ __device__ __forceinline__ void rz_item_reg(const RzArgs<T>& a, int witem, int s
 
 // SC: the instantiation for the work items [sc_lo, sc_hi) that meet a source
 // window of the scattered-field form; the plain one takes all others.
-template <typename T, bool SC>
+template <typename T, bool SC, bool MAT = false>
 __global__ void __launch_bounds__(128, reg_min_blocks<T>()) rz_step_kernel(const RzArgs<T> a) {
   const int nwarps = (int)((gridDim.x * blockDim.x) >> 5);
   const int nsub = SC ? (a.chunk_z + kSubPlanes - 1) / kSubPlanes : 1;
@@ -454,7 +460,7 @@ __global__ void __launch_bounds__(128, reg_min_blocks<T>()) rz_step_kernel(const
       const int chunk = a.work[it_w / a.n_modes] / a.tiles;
       if (chunk * a.chunk_z + sub * kSubPlanes >= a.L.nz) continue;
     }
-    rz_item_reg<T, SC>(a, it_w, sub);
+    rz_item_reg<T, SC, MAT>(a, it_w, sub);
   }
 }
 
@@ -1176,14 +1182,16 @@ __global__ void rz_to_canonical(const T* src, RzLayout L, int mode, int comp, do
 
 // (scattered-field form: the stored value is the given total minus the
 // incident field x)
+// (metric: the component's row, mplane elements apart from plane to plane, 0
+// for one material)
 template <typename T>
 __global__ void rz_from_canonical(const double* src, RzLayout L, const uint8_t* mask, int mode,
-                                  int comp, const double* metric, T* dst, RzIncident x) {
+                                  int comp, const double* metric, long long mplane, T* dst, RzIncident x) {
   const long long n = (long long)(L.nr + 1) * (L.nz + 1);
   for (long long q = (long long)blockIdx.x * blockDim.x + threadIdx.x; q < n;
        q += (long long)gridDim.x * blockDim.x) {
     const int i = (int)(q % (L.nr + 1)), k = (int)(q / (L.nr + 1));
-    const bool act = ((mask[L.midx(i, k)] >> comp) & 1) && metric[i] != 0.0;
+    const bool act = ((mask[L.midx(i, k)] >> comp) & 1) && metric[(long long)(k + 1) * mplane + i] != 0.0;
     dst[L.fidx(mode, comp, i, k)] = (T)((act ? src[q] : 0.0) - inc_value(x, mode, comp, i, k));
   }
 }
@@ -1193,7 +1201,8 @@ __global__ void rz_from_canonical(const double* src, RzLayout L, const uint8_t* 
 // the splitting operator (M_mu_phi^-1 (P_r e_z)^2 and M_eps_phi^-1
 // (P_r^T h_z)^2), plus alpha times the longitudinal coupling
 // h_phi P_z e_r - h_r P_z e_phi. metric: [6][pr] unscaled M^-1 of the mode
-// (zero where the mode has no object). One partial per block.
+// (zero where the mode has no object), for material arrays one such block per
+// plane, mplane elements apart (0 for one material). One partial per block.
 constexpr int kEnergyBlocks = 512;
 constexpr int kEnergyThreads = 256;
 constexpr int kRzRec = 6;  // balance record: step, mode, energy, max |qe - qbunch|, max |qh|, bunch charge scale
@@ -1201,7 +1210,7 @@ constexpr int kRzRec = 6;  // balance record: step, mode, energy, max |qe - qbun
 template <typename T>
 __global__ void __launch_bounds__(kEnergyThreads)
 rz_energy_partial(const T* f, RzLayout L, int mode, const uint8_t* mask, const double* metric,
-                  double alpha, double* partial, RzIncident x) {
+                  long long mplane, double alpha, double* partial, RzIncident x) {
   const long long PR = L.pr;
   const long long n = (long long)(L.nr + 1) * (L.nz + 1);
   double acc = 0.0;
@@ -1217,7 +1226,7 @@ rz_energy_partial(const T* f, RzLayout L, int mode, const uint8_t* mask, const d
     double w = 0.0;
     double c[6];
     for (int comp = 0; comp < 6; ++comp) {
-      c[comp] = ((m >> comp) & 1) ? metric[comp * PR + i] : 0.0;
+      c[comp] = ((m >> comp) & 1) ? metric[(long long)(k + 1) * mplane + comp * PR + i] : 0.0;
       if (c[comp] != 0.0) {
         const double val = v(comp, 0, 0);
         w += 0.5 * val * val / c[comp];
@@ -1262,8 +1271,8 @@ __global__ void rz_energy_final(const double* partial, int n, double* out) {
 template <typename T>
 __global__ void __launch_bounds__(kEnergyThreads)
 rz_charge_partial(const T* fc, const T* fp, RzLayout L, int mode, double mm, const uint8_t* mask,
-                  const double* metric, double a2, RzIncident xc, RzIncident xp, const double* qline,
-                  double share, int i0, double* part_e, double* part_h) {
+                  const double* metric, long long mplane, double a2, RzIncident xc, RzIncident xp,
+                  const double* qline, double share, int i0, double* part_e, double* part_h) {
   const long long PR = L.pr;
   const long long n = (long long)(L.nr + 1) * (L.nz + 1);
   double me = 0.0, mh = 0.0;
@@ -1272,7 +1281,7 @@ rz_charge_partial(const T* fc, const T* fp, RzLayout L, int mode, double mm, con
     const int i = (int)(q % (L.nr + 1)), k = (int)(q / (L.nr + 1));
     auto C = [&](int comp, int ii, int kk) -> double {  // M^-1 of the entry, 0 where it has no object
       if (ii < 0 || ii > L.nr || kk < -1 || kk > L.nz + 1) return 0.0;
-      return ((mask[L.midx(ii, kk)] >> comp) & 1) ? metric[comp * PR + ii] : 0.0;
+      return ((mask[L.midx(ii, kk)] >> comp) & 1) ? metric[(long long)(kk + 1) * mplane + comp * PR + ii] : 0.0;
     };
     auto vc = [&](int comp, int ii, int kk) {
       return (double)fc[L.fidx(mode, comp, ii, kk)] + inc_value(xc, mode, comp, ii, kk);
@@ -1435,8 +1444,11 @@ struct tetm_rz {
   void* set[2] = {nullptr, nullptr};
   int cur = 0;
   uint8_t* mask = nullptr;
-  void* coef = nullptr;          // [mode][kNCo][pr], T
-  double* metric = nullptr;      // [mode][6][pr]
+  void* coef = nullptr;          // [mode][kNCo][pr], T (material arrays: [mode][rows][kNCo][pr])
+  double* metric = nullptr;      // [mode][6][pr] (material arrays: [mode][rows][6][pr])
+  bool mat = false;              // per-cell eps_r / mu_r: coefficients per entry
+  long long co_mode = 0, co_plane = 0;  // strides of coef per mode and per plane row (0: one row for all)
+  long long me_mode = 0, me_plane = 0;  // the same for metric
   int* work = nullptr;
   int n_work = 0, tiles = 0, chunk_z = 32, n_chunks = 0;
   bool work_dirty = true;
@@ -1508,6 +1520,8 @@ cudaError_t rz_launch_source(tetm_rz* s, int n_steps) {
   a.L = s->L;
   a.mask = s->mask;
   a.coef = static_cast<const T*>(s->coef);
+  a.co_mode = s->co_mode;
+  a.co_plane = s->co_plane;
   a.m_lo = s->g.m_lo;
   a.n_modes = s->n_modes;
   a.b_on = 1;
@@ -1547,12 +1561,12 @@ int rz_queue_balances(tetm_rz* s, double* rec) {
     const int m = s->g.m_lo + mi;
     const double share = (m == 0 ? 1.0 : 2.0) / (2.0 * kPi);
     double* r = rec + (size_t)mi * kRzRec;
-    const double* me = s->metric + (size_t)mi * 6 * s->L.pr + s->L.orr;
-    rz_energy_partial<T><<<kEnergyBlocks, kEnergyThreads, 0, s->st>>>(fc, s->L, mi, s->mask, me, s->alpha,
-                                                                       s->partial, rz_incident(s, s->step));
+    const double* me = s->metric + (size_t)mi * s->me_mode + s->L.orr;
+    rz_energy_partial<T><<<kEnergyBlocks, kEnergyThreads, 0, s->st>>>(fc, s->L, mi, s->mask, me, s->me_plane,
+                                                                       s->alpha, s->partial, rz_incident(s, s->step));
     rz_energy_final<<<1, 32, 0, s->st>>>(s->partial, kEnergyBlocks, r + 2);
     rz_charge_partial<T><<<kEnergyBlocks, kEnergyThreads, 0, s->st>>>(
-        fc, fp, s->L, mi, (double)m, s->mask, me, s->alpha * s->alpha, rz_incident(s, s->step),
+        fc, fp, s->L, mi, (double)m, s->mask, me, s->me_plane, s->alpha * s->alpha, rz_incident(s, s->step),
         rz_incident(s, s->step - 1), s->bunch ? ql : nullptr, share, s->i0, pe, ph);
     rz_balance_record<<<1, 32, 0, s->st>>>(pe, ph, kEnergyBlocks, (double)s->step, (double)m, share,
                                            s->bunch ? qmax : nullptr, r);
@@ -1567,6 +1581,8 @@ int rz_launch_steps(tetm_rz* s, long long n) {
   a.L = s->L;
   a.mask = s->mask;
   a.coef = static_cast<const T*>(s->coef);
+  a.co_mode = s->co_mode;
+  a.co_plane = s->co_plane;
   a.m_lo = s->g.m_lo;
   a.n_modes = s->n_modes;
   a.tiles = s->tiles;
@@ -1611,6 +1627,8 @@ int rz_launch_steps(tetm_rz* s, long long n) {
     } else if (s->kernel == TETM_RZ_KERNEL_ASYNC) {
       if (sc) rz_step_async_kernel<T, true><<<nblocks, 128, 4 * rz_async_warp_bytes<T>(), st>>>(a);
       else rz_step_async_kernel<T, false><<<nblocks, 128, 4 * rz_async_warp_bytes<T>(), st>>>(a);
+    } else if (s->mat) {  // material arrays: the register kernel, coefficients per plane
+      rz_step_kernel<T, false, true><<<nblocks, 128, 0, st>>>(a);
     } else {
       if (sc) rz_step_kernel<T, true><<<nblocks, 128, 0, st>>>(a);
       else rz_step_kernel<T, false><<<nblocks, 128, 0, st>>>(a);
@@ -1779,16 +1797,86 @@ int rz_rebuild_work(tetm_rz* s) {
 
 // Per-radian metric of one mode at radial index i (unscaled M^-1; zero where
 // the mode has no object) and the update coefficients derived from it.
-void rz_metric_row(const tetm_rz_grid& g, int m, int i, double out[6]) {
-  const double dr = g.dr, dz = g.dz;
+__host__ __device__ inline void rz_metric_at(double dr, double dz, int nr, int m, int i, double out[6]) {
   const double ri = i * dr, rh = (i + 0.5) * dr;
-  out[kER] = i < g.nr ? dr / (kEps0 * rh * dz) : 0.0;
-  out[kEP] = (i > 0 && i < g.nr) ? ri / (kEps0 * dr * dz) : 0.0;
+  out[kER] = i < nr ? dr / (kEps0 * rh * dz) : 0.0;
+  out[kEP] = (i > 0 && i < nr) ? ri / (kEps0 * dr * dz) : 0.0;
   if (i == 0) out[kEZ] = m == 0 ? dz / (kEps0 * dr * dr / 4.0) : 0.0;
-  else out[kEZ] = i < g.nr ? dz / (kEps0 * ri * dr) : 0.0;
-  out[kHR] = (i > 0 && i < g.nr) ? dr / (kMu0 * ri * dz) : 0.0;
-  out[kHP] = i < g.nr ? rh / (kMu0 * dr * dz) : 0.0;
-  out[kHZ] = i < g.nr ? dz / (kMu0 * rh * dr) : 0.0;
+  else out[kEZ] = i < nr ? dz / (kEps0 * ri * dr) : 0.0;
+  out[kHR] = (i > 0 && i < nr) ? dr / (kMu0 * ri * dz) : 0.0;
+  out[kHP] = i < nr ? rh / (kMu0 * dr * dz) : 0.0;
+  out[kHZ] = i < nr ? dz / (kMu0 * rh * dr) : 0.0;
+}
+void rz_metric_row(const tetm_rz_grid& g, int m, int i, double out[6]) { rz_metric_at(g.dr, g.dz, g.nr, m, i, out); }
+
+// Material arrays (per cell, eps_r / mu_r at ci + nr ck, nullptr = 1): the
+// metric and coefficients of every entry (i, k), k = -1 .. nz+1, of every
+// mode. The column's metric is divided by the staircase mean of eps_r over
+// the cells an edge touches (e_r, e_z two, e_phi four; the axis e_z its one
+// cell) and multiplied by the mean of 1/mu_r over the cells a face touches
+// (h_phi its cell, h_r and h_z two), as in the 3D material matrices (Sec. 2).
+// A cell outside the grid counts as vacuum: an object that touches one lies
+// in the PEC wall, carries no field and its value is never read.
+template <typename T>
+__global__ void rz_material_coefs(const double* eps, const double* mu, RzLayout L, double dr, double dz,
+                                  int m_lo, int n_modes, double alpha, T* coef, double* metric) {
+  const int nr = L.nr, nz = L.nz;
+  const long long PR = L.pr;
+  const long long n = L.rows * (long long)(nr + 1);
+  for (long long q = (long long)blockIdx.x * blockDim.x + threadIdx.x; q < n;
+       q += (long long)gridDim.x * blockDim.x) {
+    const int i = (int)(q % (nr + 1)), row = (int)(q / (nr + 1)), k = row - 1;
+    auto inside = [&](int ci, int ck) { return ci >= 0 && ci < nr && ck >= 0 && ck < nz; };
+    auto E = [&](int ci, int ck) { return eps && inside(ci, ck) ? eps[ci + (long long)nr * ck] : 1.0; };
+    auto IM = [&](int ci, int ck) { return mu && inside(ci, ck) ? 1.0 / mu[ci + (long long)nr * ck] : 1.0; };
+    double f[6];
+    f[kER] = 1.0 / (0.5 * (E(i, k - 1) + E(i, k)));
+    f[kEP] = 1.0 / ((E(i - 1, k - 1) + E(i - 1, k) + E(i, k - 1) + E(i, k)) / 4.0);
+    f[kEZ] = i == 0 ? 1.0 / E(0, k) : 1.0 / (0.5 * (E(i - 1, k) + E(i, k)));
+    f[kHP] = IM(i, k);
+    f[kHR] = 0.5 * (IM(i - 1, k) + IM(i, k));
+    f[kHZ] = 0.5 * (IM(i, k - 1) + IM(i, k));
+    for (int mi = 0; mi < n_modes; ++mi) {
+      const int m = m_lo + mi;
+      double c[6];
+      rz_metric_at(dr, dz, nr, m, i, c);
+      for (int comp = 0; comp < 6; ++comp) c[comp] *= f[comp];
+      const long long col = i + L.orr;
+      double* me = metric + (((long long)mi * L.rows + row) * 6) * PR + col;
+      for (int comp = 0; comp < 6; ++comp) me[comp * PR] = c[comp];
+      T* co = coef + (((long long)mi * L.rows + row) * kNCo) * PR + col;
+      const double mm = (double)m * m;
+      co[kCoER * PR] = (T)(alpha * c[kER]);
+      co[kCoEP * PR] = (T)(alpha * c[kEP]);
+      co[kCoHR * PR] = (T)(alpha * c[kHR]);
+      co[kCoHP * PR] = (T)(alpha * c[kHP]);
+      co[kCoEZ * PR] = (T)(2.0 * alpha * c[kEZ]);
+      co[kCoHZ * PR] = (T)(2.0 * alpha * c[kHZ]);
+      co[kCoFEZ * PR] = (T)(2.0 * alpha * c[kEZ] / (1.0 + alpha * alpha * mm * c[kEZ] * c[kHR]));
+      co[kCoFHZ * PR] = (T)(2.0 * alpha * c[kHZ] / (1.0 + alpha * alpha * mm * c[kHZ] * c[kER]));
+    }
+  }
+}
+
+// uploads the material arrays and fills coef and metric on the device
+template <typename T>
+int rz_material_setup(tetm_rz* s, const double* eps_r, const double* mu_r) {
+  const size_t nc = (size_t)s->g.nr * s->g.nz;
+  double *deps = nullptr, *dmu = nullptr;
+  cudaError_t e = cudaSuccess;
+  if (eps_r) e = cudaMalloc(&deps, sizeof(double) * nc);
+  if (e == cudaSuccess && mu_r) e = cudaMalloc(&dmu, sizeof(double) * nc);
+  if (e == cudaSuccess && eps_r) e = cudaMemcpyAsync(deps, eps_r, sizeof(double) * nc, cudaMemcpyHostToDevice, s->st);
+  if (e == cudaSuccess && mu_r) e = cudaMemcpyAsync(dmu, mu_r, sizeof(double) * nc, cudaMemcpyHostToDevice, s->st);
+  if (e == cudaSuccess) {
+    rz_material_coefs<T><<<1024, 256, 0, s->st>>>(deps, dmu, s->L, s->g.dr, s->g.dz, s->g.m_lo, s->n_modes, s->alpha,
+                                                  static_cast<T*>(s->coef), s->metric);
+    e = cudaGetLastError();
+  }
+  if (e == cudaSuccess) e = cudaStreamSynchronize(s->st);
+  cudaFree(deps);
+  cudaFree(dmu);
+  return e == cudaSuccess ? TETM_OK : rz_fail(e);
 }
 
 template <typename T>
@@ -1861,7 +1949,16 @@ int tetm_rz_create(const tetm_rz_grid* g, const double* eps_r, const double* mu_
   if (!out) return TETM_E_ARG;
   *out = nullptr;
   if (!rz_grid_ok(g)) return TETM_E_ARG;
-  if (eps_r || mu_r) return TETM_E_UNSUPPORTED;
+  // material arrays: physical (>= 1) and finite; all ones is the vacuum
+  bool mat = false;
+  const long long ncell = (long long)g->nr * g->nz;
+  for (const double* a : {eps_r, mu_r}) {
+    if (!a) continue;
+    for (long long q = 0; q < ncell; ++q) {
+      if (!(a[q] >= 1.0) || !isfinite(a[q])) return TETM_E_ARG;
+      if (a[q] != 1.0) mat = true;
+    }
+  }
   const double cdt = g->cdt > 0 ? g->cdt : std::min(g->dr, g->dz);
   if (cdt > g->dz * (1.0 + 1e-12) || cdt > g->dr * (1.0 + 1e-12)) return TETM_E_UNSTABLE;
   tetm_rz* s = new (std::nothrow) tetm_rz();
@@ -1873,6 +1970,13 @@ int tetm_rz_create(const tetm_rz_grid* g, const double* eps_r, const double* mu_
   s->esz = g->precision == TETM_FP64 ? 8 : 4;
   s->n_modes = g->m_hi - g->m_lo + 1;
   s->L = make_rz_layout(g->nr, g->nz);
+  s->mat = mat;
+  const long long prows = mat ? s->L.rows : 1;  // coefficient rows per mode
+  s->co_plane = mat ? (long long)kNCo * s->L.pr : 0;
+  s->co_mode = prows * kNCo * s->L.pr;
+  s->me_plane = mat ? 6LL * s->L.pr : 0;
+  s->me_mode = prows * 6 * s->L.pr;
+  if (mat) s->kernel = TETM_RZ_KERNEL_REGISTER;  // the kernel that reads coefficients per plane
   int rc = TETM_OK;
   uint8_t* dpec = nullptr;
   cudaError_t e = cudaStreamCreateWithFlags(&s->own, cudaStreamNonBlocking);
@@ -1882,8 +1986,8 @@ int tetm_rz_create(const tetm_rz_grid* g, const double* eps_r, const double* mu_
   }
   s->st = s->own;
   const size_t fb = rz_field_bytes(s->L, s->esz, s->n_modes);
-  const size_t cob = (size_t)s->n_modes * kNCo * s->L.pr * s->esz;
-  const size_t meb = (size_t)s->n_modes * 6 * s->L.pr * sizeof(double);
+  const size_t cob = (size_t)s->n_modes * s->co_mode * s->esz;
+  const size_t meb = (size_t)s->n_modes * s->me_mode * sizeof(double);
   do {
     if ((e = cudaMalloc(&s->set[0], fb)) != cudaSuccess) break;
     if ((e = cudaMalloc(&s->set[1], fb)) != cudaSuccess) break;
@@ -1906,7 +2010,14 @@ int tetm_rz_create(const tetm_rz_grid* g, const double* eps_r, const double* mu_
   } while (0);
   cudaFree(dpec);
   if (e != cudaSuccess) rc = rz_fail(e);
-  if (rc == TETM_OK) rc = s->esz == 8 ? rz_upload_coefs<double>(s) : rz_upload_coefs<float>(s);
+  if (rc == TETM_OK && mat) {
+    if (cudaMemsetAsync(s->coef, 0, cob, s->st) != cudaSuccess || cudaMemsetAsync(s->metric, 0, meb, s->st) != cudaSuccess)
+      rc = TETM_E_CUDA;
+    if (rc == TETM_OK)
+      rc = s->esz == 8 ? rz_material_setup<double>(s, eps_r, mu_r) : rz_material_setup<float>(s, eps_r, mu_r);
+  } else if (rc == TETM_OK) {
+    rc = s->esz == 8 ? rz_upload_coefs<double>(s) : rz_upload_coefs<float>(s);
+  }
   if (rc == TETM_OK) rc = s->esz == 8 ? rz_occupancy<double>(s) : rz_occupancy<float>(s);
   if (rc == TETM_OK) rc = rz_rebuild_work(s);
   if (rc != TETM_OK) {
@@ -2021,6 +2132,7 @@ namespace {
 int rz_tem_setup(tetm_rz* s, double sigma, double q, int i0, int k_head, std::vector<uint8_t>& row,
                  std::vector<double>& psi, std::vector<double>& G) {
   if (!s) return TETM_E_ARG;
+  if (s->mat) return TETM_E_UNSUPPORTED;  // the static start's entry section is vacuum
   if (s->step != 0 || s->bunch) return TETM_E_STATE;
   if (!(sigma > 0) || !isfinite(sigma)) return TETM_E_ARG;
   const double dz = s->g.dz, dr = s->g.dr;
@@ -2278,14 +2390,14 @@ int tetm_rz_transverse_wake(tetm_rz* s, int32_t mode, double* out, int32_t cap, 
 int tetm_rz_energy(tetm_rz* s, int32_t mode, double* w) {
   if (!rz_mode_ok(s, mode) || !w) return TETM_E_ARG;
   const void* f = s->set[s->cur];
-  const double* me = s->metric + (size_t)mode * 6 * s->L.pr + s->L.orr;
+  const double* me = s->metric + (size_t)mode * s->me_mode + s->L.orr;
   if (s->esz == 8)
     rz_energy_partial<double><<<kEnergyBlocks, kEnergyThreads, 0, s->st>>>(
-        static_cast<const double*>(f), s->L, mode, s->mask, me, s->alpha, s->partial,
+        static_cast<const double*>(f), s->L, mode, s->mask, me, s->me_plane, s->alpha, s->partial,
         rz_incident(s, s->step));
   else
     rz_energy_partial<float><<<kEnergyBlocks, kEnergyThreads, 0, s->st>>>(
-        static_cast<const float*>(f), s->L, mode, s->mask, me, s->alpha, s->partial,
+        static_cast<const float*>(f), s->L, mode, s->mask, me, s->me_plane, s->alpha, s->partial,
         rz_incident(s, s->step));
   rz_energy_final<<<1, 32, 0, s->st>>>(s->partial, kEnergyBlocks, s->partial + kEnergyBlocks);
   cudaError_t e = cudaGetLastError();
@@ -2322,13 +2434,13 @@ int tetm_rz_set_fields(tetm_rz* s, int32_t mode, int32_t comp, const double* in)
   if (e != cudaSuccess) return rz_fail(e);
   e = cudaMemcpyAsync(tmp, in, sizeof(double) * n, cudaMemcpyHostToDevice, s->st);
   void* f = s->set[s->cur];
-  const double* me = s->metric + ((size_t)mode * 6 + comp) * s->L.pr + s->L.orr;
+  const double* me = s->metric + (size_t)mode * s->me_mode + (size_t)comp * s->L.pr + s->L.orr;
   if (e == cudaSuccess) {
     if (s->esz == 8)
-      rz_from_canonical<double><<<512, 256, 0, s->st>>>(tmp, s->L, s->mask, mode, comp, me,
+      rz_from_canonical<double><<<512, 256, 0, s->st>>>(tmp, s->L, s->mask, mode, comp, me, s->me_plane,
                                                         static_cast<double*>(f), rz_incident(s, s->step));
     else
-      rz_from_canonical<float><<<512, 256, 0, s->st>>>(tmp, s->L, s->mask, mode, comp, me,
+      rz_from_canonical<float><<<512, 256, 0, s->st>>>(tmp, s->L, s->mask, mode, comp, me, s->me_plane,
                                                        static_cast<float*>(f), rz_incident(s, s->step));
     e = cudaGetLastError();
   }
@@ -2349,6 +2461,7 @@ int tetm_rz_set_kernel(tetm_rz* s, int32_t kernel) {
   if (!s || (kernel != TETM_RZ_KERNEL_REGISTER && kernel != TETM_RZ_KERNEL_ASYNC &&
              kernel != TETM_RZ_KERNEL_BULK && kernel != TETM_RZ_KERNEL_BULK2))
     return TETM_E_ARG;
+  if (s->mat && kernel != TETM_RZ_KERNEL_REGISTER) return TETM_E_UNSUPPORTED;  // per-plane coefficients
   const bool retile = (kernel == TETM_RZ_KERNEL_BULK2) != (s->kernel == TETM_RZ_KERNEL_BULK2);
   s->kernel = kernel;
   int rc = s->esz == 8 ? rz_occupancy<double>(s) : rz_occupancy<float>(s);

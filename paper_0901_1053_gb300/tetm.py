@@ -538,17 +538,22 @@ class RzSolver:
     """Modes m_lo..m_hi of the scheme (24) on one (r, z) grid; fields in the
     canonical (nz+1, nr+1) layout, r fastest, per radian."""
 
-    def __init__(self, nr, nz, m_lo, m_hi, dr, dz, cdt=0.0, precision="fp32", pec=None):
+    def __init__(self, nr, nz, m_lo, m_hi, dr, dz, cdt=0.0, precision="fp32", pec=None, eps_r=None,
+                 mu_r=None):
+        """eps_r, mu_r: float64 per cell (nz, nr) or None (vacuum); pec: uint8
+        per cell or None."""
         self.grid = make_rz_grid(nr, nz, m_lo, m_hi, dr, dz, cdt, precision)
         self.nr, self.nz = int(nr), int(nz)
         self.m_lo, self.m_hi = int(m_lo), int(m_hi)
         self.shape = (self.nz + 1, self.nr + 1)
         self.precision = precision
-        pec_a = None
-        if pec is not None:
-            pec_a = np.ascontiguousarray(pec, dtype=np.uint8).reshape(self.nz, self.nr)
+        cell = (self.nz, self.nr)
+        arrs = []
+        for a, dt in ((eps_r, np.float64), (mu_r, np.float64), (pec, np.uint8)):
+            arrs.append(None if a is None else np.ascontiguousarray(a, dtype=dt).reshape(cell))
         h = ctypes.c_void_p()
-        _check(lib.tetm_rz_create(ctypes.byref(self.grid), None, None, _ptr(pec_a), ctypes.byref(h)),
+        self.h = ctypes.c_void_p()
+        _check(lib.tetm_rz_create(ctypes.byref(self.grid), *[_ptr(a) for a in arrs], ctypes.byref(h)),
                "tetm_rz_create")
         self.h = h
 

@@ -76,10 +76,14 @@ def test_rz_create_rejects_bad_grids_and_materials_before_touching_the_gpu(tetm)
     assert tetm.lib.tetm_rz_create(ctypes.byref(too_long), None, None, None, ctypes.byref(h)) == \
         tetm.TETM_E_UNSTABLE
     import numpy as np
-    eps = np.ones(64)
     ok = tetm.make_rz_grid(8, 8, 0, 0, 1e-3, 1e-3)
-    assert tetm.lib.tetm_rz_create(ctypes.byref(ok), ctypes.c_void_p(eps.ctypes.data), None, None,
-                                   ctypes.byref(h)) == tetm.TETM_E_UNSUPPORTED
+    for bad_value in (0.5, np.nan, np.inf):        # material arrays: physical and finite
+        eps = np.ones(64)
+        eps[17] = bad_value
+        assert tetm.lib.tetm_rz_create(ctypes.byref(ok), ctypes.c_void_p(eps.ctypes.data), None, None,
+                                       ctypes.byref(h)) == tetm.TETM_E_ARG
+        assert tetm.lib.tetm_rz_create(ctypes.byref(ok), None, ctypes.c_void_p(eps.ctypes.data), None,
+                                       ctypes.byref(h)) == tetm.TETM_E_ARG
 
 
 def test_rz_bytes_needed(tetm):
