@@ -159,9 +159,7 @@ int tetm_set_bunch_static(tetm_solver* s, double sigma_z, double charge, int32_t
  * the solver's stream; returns once the launches are queued. */
 int tetm_step(tetm_solver* s, int32_t n);
 
-/* Wait for the solver's stream (synchronizes). TETM_E_TIMEOUT when a bounded
- * wait of the slab kernel gave up (a tensor copy of its material-array
- * instantiation that did not land). */
+/* Wait for the solver's stream (synchronizes). */
 int tetm_sync(tetm_solver* s);
 
 /* Longitudinal wake W(s_m) [V/C], W(s) = -(1/Q) * integral of E_z along the
@@ -395,8 +393,8 @@ typedef struct tetm_batch tetm_batch;
  * 0 launches every step directly. While in the batch a member rejects
  * tetm_step, tetm_set_fields, tetm_set_kernel, tetm_set_tiling and tetm_load
  * (TETM_E_STATE); read-only calls (tetm_wake, tetm_get_fields, tetm_energy,
- * tetm_charge_residual) remain valid after tetm_batch_sync. Destroy the batch
- * before destroying a member. */
+ * tetm_charge_residual) remain valid after tetm_batch_sync. Remove a member
+ * (tetm_batch_remove) or destroy the batch before destroying the member. */
 int tetm_batch_create(tetm_solver* const* solvers, const int64_t* step_limits, int32_t n,
                       int32_t graph_steps, tetm_batch** out);
 

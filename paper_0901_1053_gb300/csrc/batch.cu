@@ -58,7 +58,6 @@ struct tetm_batch {
   bool warmed;                     // one uncaptured launch done (launch set-up outside capture)
   bool failed;                     // a launch failed: no further steps (members resynchronised)
   int* sched;                      // the slab kernel's schedule counters
-  int* err;                        // the slab kernel's bounded-wait error word
   Stage stage[kStages];
   int cur_stage;
   cudaEvent_t order_ev;            // orders the batch's stream against a member's
@@ -163,7 +162,7 @@ cudaError_t launch_one(tetm_batch* b) {
   if constexpr (sizeof(T) == 4) {
     if (b->slab)
       return launch_fused_slab_batch((BatchMember<float>*)b->d_members, b->capacity, work, b->d_wbuf,
-                                     b->wcap, b->err, b->sched, b->nz_max, b->stream);
+                                     b->wcap, b->sched, b->nz_max, b->stream);
   }
   return launch_fused_warp_batch<T>((const BatchMember<T>*)b->d_members, b->capacity, work, b->d_wbuf, b->wcap,
                                     b->tile_y, b->nz_max, b->stream);
@@ -232,7 +231,6 @@ void release(tetm_batch* b) {
     dev_free(b->d_members, b->stream);
     dev_free(b->d_wbuf, b->stream);
     dev_free(b->sched, b->stream);
-    dev_free(b->err, b->stream);
     cudaStreamSynchronize(b->stream);
   }
   for (Stage& s : b->stage) {
@@ -283,15 +281,13 @@ int create_slots(int capacity, size_t esz, int tile_x, int tile_y, int graph_ste
   if (rc == TETM_OK &&
       (dev_alloc(&b->d_members, mbytes, b->stream) != cudaSuccess ||
        dev_alloc((void**)&b->d_wbuf, wbytes, b->stream) != cudaSuccess ||
-       dev_alloc((void**)&b->sched, 2 * sizeof(int), b->stream) != cudaSuccess ||
-       dev_alloc((void**)&b->err, sizeof(int), b->stream) != cudaSuccess))
+       dev_alloc((void**)&b->sched, 2 * sizeof(int), b->stream) != cudaSuccess))
     rc = TETM_E_NOMEM;
   // every slot starts empty (inactive), the list empty, the counters zero
   if (rc == TETM_OK &&
       (cudaMemsetAsync(b->d_members, 0, mbytes, b->stream) != cudaSuccess ||
        cudaMemsetAsync(b->d_wbuf, 0, wbytes, b->stream) != cudaSuccess ||
-       cudaMemsetAsync(b->sched, 0, 2 * sizeof(int), b->stream) != cudaSuccess ||
-       cudaMemsetAsync(b->err, 0, sizeof(int), b->stream) != cudaSuccess))
+       cudaMemsetAsync(b->sched, 0, 2 * sizeof(int), b->stream) != cudaSuccess))
     rc = TETM_E_CUDA;
   if (rc != TETM_OK) {
     cudaGetLastError();
@@ -499,9 +495,7 @@ int tetm_batch_sync(tetm_batch* b) {
   if (!b) return TETM_E_ARG;
   if (cudaStreamSynchronize(b->stream) != cudaSuccess) return TETM_E_CUDA;
   if (harvest(b, b->calls) != TETM_OK) return TETM_E_CUDA;
-  int flag = 0;  // a bounded wait of the slab kernel gave up
-  if (cudaMemcpy(&flag, b->err, sizeof(int), cudaMemcpyDeviceToHost) != cudaSuccess) return TETM_E_CUDA;
-  return flag ? TETM_E_TIMEOUT : TETM_OK;
+  return TETM_OK;
 }
 
 int tetm_batch_info(tetm_batch* b, int32_t* n_members, int32_t* n_active, int32_t* work_items) {

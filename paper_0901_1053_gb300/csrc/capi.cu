@@ -495,19 +495,7 @@ int do_steps(tetm_solver* s, int n) {
           CK(launch_fused_warp_step<T>(a, s->tile_x, s->tile_y, s->stream));
         } else if (slab_shape_ok(s->tile_x, s->tile_y)) {
           if constexpr (sizeof(T) == 4) {
-            if (!s->slab) {  // material arrays: tensor maps of both field sets and the coefficients
-              s->slab = new (std::nothrow) SlabMaps();
-              if (!s->slab) return TETM_E_NOMEM;
-              memset(s->slab, 0, sizeof(SlabMaps));  // one material: no tensor copies
-              void* ez[2] = {s->set[0][kEZ], s->set[1][kEZ]};
-              void* hz[2] = {s->set[0][kHZ], s->set[1][kHZ]};
-              if (!s->uniform && build_slab_maps(s->slab, ez, hz, s->ua, s->L) != 0) {
-                delete s->slab;
-                s->slab = nullptr;
-                return TETM_E_UNSUPPORTED;
-              }
-            }
-            CK(launch_fused_slab_step(a, *s->slab, s->cur, s->err, s->sched, s->stream));
+            CK(launch_fused_slab_step(a, s->sched, s->stream));
           } else {
             return TETM_E_UNSUPPORTED;
           }
@@ -599,10 +587,7 @@ void free_all(tetm_solver* s) {
   dev_free(s->diag.out, st);
   dev_free(s->hist, st);
   dev_free(s->staging, st);
-  dev_free(s->err, st);
   dev_free(s->sched, st);
-  delete s->slab;
-  s->slab = nullptr;
 }
 
 }  // namespace
@@ -695,8 +680,6 @@ int create_impl(const tetm_grid* g, int k_lo, int nz_all, const double* eps_r, c
   if (rc == TETM_OK) rc = cudaMemsetAsync(s->mask, 0, (size_t)s->L.count, s->stream) == cudaSuccess ? TETM_OK : TETM_E_CUDA;
   if (rc == TETM_OK) rc = dalloc(s, (void**)&s->diag.part, sizeof(double) * 2048);
   if (rc == TETM_OK) rc = dalloc(s, (void**)&s->diag.out, sizeof(double) * 8);
-  if (rc == TETM_OK) rc = dalloc(s, (void**)&s->err, sizeof(int));
-  if (rc == TETM_OK) rc = cudaMemsetAsync(s->err, 0, sizeof(int), s->stream) == cudaSuccess ? TETM_OK : TETM_E_CUDA;
   if (rc == TETM_OK) rc = dalloc(s, (void**)&s->sched, 2 * sizeof(int));
   if (rc == TETM_OK) rc = cudaMemsetAsync(s->sched, 0, 2 * sizeof(int), s->stream) == cudaSuccess ? TETM_OK : TETM_E_CUDA;
   s->diag.cap = 2048;
@@ -988,10 +971,8 @@ int tetm_step(tetm_solver* s, int32_t n) {
 
 int tetm_sync(tetm_solver* s) {
   if (!s) return TETM_E_ARG;
-  int flag = 0;
-  CK(cudaMemcpyAsync(&flag, s->err, sizeof(int), cudaMemcpyDeviceToHost, s->stream));
   CK(cudaStreamSynchronize(s->stream));
-  return flag ? TETM_E_TIMEOUT : TETM_OK;
+  return TETM_OK;
 }
 
 int tetm_wake(tetm_solver* s, double* out, int32_t cap, int32_t* n_out, double* s0, double* ds) {

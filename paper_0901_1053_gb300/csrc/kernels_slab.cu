@@ -16,17 +16,15 @@
 //    entry without a field holds zero for ever);
 //  * stores each new component of the quad only when one of its nodes
 //    carries it (the other field set's entry already holds that zero).
-// e_z and h_z (and with material arrays the six per-entry coefficient arrays)
-// are the inputs a node reads at its neighbours; they arrive through a ring
-// of kSD planes in shared memory, filled kSD planes ahead:
-//  * one material: each thread copies its own quad of e_z and h_z into the
-//    slot with a 16-byte asynchronous copy, or writes zeros without a read
-//    where none of the quad's nodes carries that component, so the ring
-//    reads no pipe wall; completion by the thread's copy group, publication
-//    by the last block barrier of the plane before;
-//  * material arrays: one 3D tensor copy (TMA) per array and plane, completion
-//    on an mbarrier per slot (bounded waits: after kSlabPolls polls the CTA
-//    raises the error word, drains the copies in flight and stops).
+// e_z and h_z are the inputs a node reads at its neighbours; they (and with
+// material arrays the six per-entry coefficient arrays, read at the node)
+// arrive through a ring of two planes in shared memory, filled two planes
+// ahead: each thread copies its own quad of every array into the slot with a
+// 16-byte asynchronous copy, or writes zeros without a read where none of
+// the quad's nodes carries that component (an entry without a field, and its
+// coefficient, hold zero), so the ring reads no pipe wall. Completion by the
+// thread's copy group, publication by the last block barrier of the plane
+// before.
 //
 // The intermediates a stage reads one row up or down (hx~, ez', ex~, hz') go
 // through two shared-memory buffers, those one column left or right through
@@ -37,9 +35,6 @@
 // The column of i = 0 sits at 8 in the float32 layout, so the 224-byte rows a
 // tile writes start and end on 32-byte sectors and no two tiles write into
 // the same sector.
-#include <cuda.h>
-#include <cudaTypedefs.h>
-
 #include <algorithm>
 #include <cstring>
 #include <type_traits>
@@ -54,69 +49,31 @@ constexpr int kSX = 64, kSY = 32;   // loaded columns, rows
 constexpr int kOX = 56, kOY = 28;   // owned columns, rows
 constexpr int kQ = kSX / 4;         // column quads per row
 constexpr int kSThreads = kQ * kSY; // 512
-constexpr int kSlabPolls = 1 << 18;
 
 // One material: a two-plane ring of e_z and h_z (one coefficient per
 // component, switched by the activity bytes).
 struct SlabSmemU {
   static constexpr int SD = 2;      // planes in the ring (the next plane lands while this one is worked on)
-  static constexpr unsigned slot_bytes = 2u * kSX * kSY * 4u;
   float ez[SD][kSY * kSX];
   float hz[SD][kSY * kSX];
   float x1[kSY][kSX], x2[kSY][kSX];
-  uint64_t bar[SD];
   int next[2];                      // the CTA's next work item (dynamic schedule)
 };
-// Material arrays: a three-plane ring of e_z, h_z and the six per-entry
-// coefficient arrays (alpha M^-1, 2 alpha M^-1 for e_z and h_z), 208 KB.
+// Material arrays: a two-plane ring of e_z, h_z and the six per-entry
+// coefficient arrays (alpha M^-1, 2 alpha M^-1 for e_z and h_z), 144 KB.
 struct SlabSmemM {
-  static constexpr int SD = 3;
-  static constexpr unsigned slot_bytes = 8u * kSX * kSY * 4u;
+  static constexpr int SD = 2;
   float ez[SD][kSY * kSX];
   float hz[SD][kSY * kSX];
   float co[SD][6][kSY][kSX];
   float x1[kSY][kSX], x2[kSY][kSX];
-  uint64_t bar[SD];
   int next[2];
 };
 template <bool MAT>
 using SlabSmem = typename std::conditional<MAT, SlabSmemM, SlabSmemU>::type;
 
 
-// the six coefficient arrays' tensor maps (material runs)
-struct CoefMaps {
-  CUtensorMap m[6];
-};
-
 __device__ __forceinline__ unsigned su32(const void* p) { return (unsigned)__cvta_generic_to_shared(p); }
-__device__ __forceinline__ void bar_init(uint64_t* b, unsigned count) {
-  asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(su32(b)), "r"(count) : "memory");
-}
-
-__device__ __forceinline__ void bar_expect(uint64_t* b, unsigned bytes) {
-  asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(su32(b)), "r"(bytes) : "memory");
-}
-__device__ __forceinline__ bool bar_try(uint64_t* b, unsigned parity) {
-  unsigned ok;
-  asm volatile(
-      "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n selp.u32 %0, 1, 0, p;\n}"
-      : "=r"(ok)
-      : "r"(su32(b)), "r"(parity)
-      : "memory");
-  return ok != 0;
-}
-__device__ __forceinline__ bool bar_wait(uint64_t* b, unsigned parity) {
-  for (int it = 0; it < kSlabPolls; ++it)
-    if (bar_try(b, parity)) return true;
-  return false;
-}
-// 3D tensor copy of the box at (x, y, z) into shared memory
-__device__ __forceinline__ void tma3(void* dst, const CUtensorMap* map, int x, int y, int z, uint64_t* b) {
-  asm volatile(
-      "cp.async.bulk.tensor.3d.shared::cluster.global.tile.mbarrier::complete_tx::bytes [%0], [%1, {%2, %3, %4}], [%5];"
-      ::"r"(su32(dst)), "l"(reinterpret_cast<uint64_t>(map)), "r"(x), "r"(y), "r"(z), "r"(su32(b))
-      : "memory");
-}
 // loads and stores under a predicate, without a branch (zero where not loaded)
 __device__ __forceinline__ unsigned ld_word_if(const uint8_t* p, bool c) {
   unsigned v;
@@ -174,12 +131,9 @@ __device__ __forceinline__ float right_of(float v0, int q) {
 }
 
 // One (tile, z-chunk) work item of solve a (the ten updates of every plane
-// of the chunk); false when a ring copy did not land (the error word is
-// raised and the copies in flight are drained).
+// of the chunk).
 template <bool MAT>
-__device__ __forceinline__ bool slab_item(const StepArgs<float>& a, const CUtensorMap* tm_ez, const CUtensorMap* tm_hz,
-                                          const CoefMaps* tm_co, int item, SlabSmem<MAT>& S, unsigned& phases,
-                                          int* err) {
+__device__ __forceinline__ void slab_item(const StepArgs<float>& a, int item, SlabSmem<MAT>& S) {
   using Smem = SlabSmem<MAT>;
   constexpr int kSD = Smem::SD;
   const int tid = threadIdx.x, q = tid % kQ, row = tid / kQ;
@@ -189,14 +143,13 @@ __device__ __forceinline__ bool slab_item(const StepArgs<float>& a, const CUtens
   const float uHX = a.co.u[kHX], uHY = a.co.u[kHY], uHZ = a.co.u[kHZ];
   const int ntile = a.tiles_x * a.tiles_y;
   const Q4 zero{{0.f, 0.f, 0.f, 0.f}};
-  bool failed = false;
   const int tile = item % ntile, chunk = item / ntile;
   const int gx0 = (tile % a.tiles_x) * kOX - 4;  // global i of loaded column 0
   const int gy0 = (tile / a.tiles_x) * kOY - 2;  // global j of loaded row 0
   const int k0 = chunk * a.chunk_z, k1 = min(k0 + a.chunk_z, L.nz);
   const int kstart = k0 - 1;
   const int nplanes = k1 - kstart;
-  const int cx = gx0 + L.ox, cy = gy0 + 2;     // tensor coordinates (column, row)
+  const int cx = gx0 + L.ox;                   // layout column of loaded column 0
 
   // this thread's quad; a quad with an active node lies inside its layout
   // row (columns i <= nx + 2 < px - ox), so every predicated access is a
@@ -209,45 +162,31 @@ __device__ __forceinline__ bool slab_item(const StepArgs<float>& a, const CUtens
   auto gidx = [&](int k) { return (long long)(k + 1) * SZ + qoff; };
   auto word = [&](int k) -> unsigned { return ld_word_if(a.co.mask + gidx(k), inq); };
   auto load_if = [&](const float* base, int k, bool p) -> Q4 { return ld4_if(base + gidx(k), p); };
-  // plane k into its slot (one thread): whole 64 x 32 boxes
-  auto issue = [&](int k) {
-    const int s = (k - kstart) % kSD;
-    asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
-    bar_expect(&S.bar[s], Smem::slot_bytes);
-    tma3(&S.ez[s][0], tm_ez, cx, cy, k + 1, &S.bar[s]);
-    tma3(&S.hz[s][0], tm_hz, cx, cy, k + 1, &S.bar[s]);
-    if constexpr (MAT) {
-#pragma unroll
-      for (int c = 0; c < 6; ++c) tma3(&S.co[s][c][0][0], &tm_co->m[c], cx, cy, k + 1, &S.bar[s]);
-    }
-  };
-  // one material: each thread copies the e_z and h_z quad of its own node
-  // row and columns into the slot, only where one of the quad's nodes
-  // carries that component (zeros otherwise: the entry holds zero), so the
-  // ring reads no pipe wall; completion by the thread's copy group and the
-  // block barrier after it
+  // plane k into its slot: each thread copies the quad of its own node row
+  // and columns of e_z, h_z (and of the six coefficient arrays), only where
+  // one of the quad's nodes carries that component (zeros otherwise: the
+  // entry and its coefficient hold zero), so the ring reads no pipe wall;
+  // completion by the thread's copy group and the block barrier after it
   auto issue_q = [&](int k, unsigned mw) {
     const int s = (k - kstart) % kSD;
     const long long g = inq ? gidx(k) : 0;
     cp16_or_zero(&S.ez[s][row * kSX + 4 * q], a.in[kEZ] + g, has(mw, kEZ));
     cp16_or_zero(&S.hz[s][row * kSX + 4 * q], a.in[kHZ] + g, has(mw, kHZ));
+    if constexpr (MAT) {
+#pragma unroll
+      for (int c = 0; c < 6; ++c) cp16_or_zero(&S.co[s][c][row][4 * q], a.co.ua[c] + g, has(mw, c));
+    }
   };
   // activity words of planes kstart .. kstart + 2 (m0 of the plane being
   // worked on, m1, m2 of the next two); z-state and the register prefetch
   // (plane k: hx, hy of k; ex, ey of k+1)
   unsigned m0 = word(kstart), m1 = word(kstart + 1), m2 = word(kstart + 2);
-  if constexpr (MAT) {
-    if (tid == 0)
-      for (int k = kstart; k < kstart + min(kSD, nplanes); ++k) issue(k);
-  } else {
-    issue_q(kstart, m0);
-    cp_commit();
-    if (nplanes > 1) issue_q(kstart + 1, m1);
-    cp_commit();
-    cp_wait<1>();
-    __syncthreads();  // plane kstart's slot is in
-  }
-  int issued = kstart + min(kSD, nplanes) - 1;  // last plane queued (the same in every thread)
+  issue_q(kstart, m0);
+  cp_commit();
+  if (nplanes > 1) issue_q(kstart + 1, m1);
+  cp_commit();
+  cp_wait<1>();
+  __syncthreads();  // plane kstart's slot is in
   Q4 ex0 = load_if(a.in[kEX], kstart, has(m0, kEX)), ey0 = load_if(a.in[kEY], kstart, has(m0, kEY));
   Q4 hxc = load_if(a.in[kHX], kstart, has(m0, kHX)), hyc = load_if(a.in[kHY], kstart, has(m0, kHY));
   Q4 ex1 = load_if(a.in[kEX], kstart + 1, has(m1, kEX)), ey1 = load_if(a.in[kEY], kstart + 1, has(m1, kEY));
@@ -257,11 +196,6 @@ __device__ __forceinline__ bool slab_item(const StepArgs<float>& a, const CUtens
 
   for (int k = kstart; k < k1; ++k) {
     const int s = (k - kstart) % kSD;
-    // every thread waits for the slot itself; the block decides at barrier
-    // (1) (a thread whose wait gave up computes on stale data until then,
-    // nothing is stored before it). One material: the slot is in already.
-    bool ok = true;
-    if constexpr (MAT) ok = bar_wait(&S.bar[s], (phases >> s) & 1u);
     // next plane's register inputs and the activity word three planes on, early
     Q4 hxn_in, hyn_in, exn_in, eyn_in;
     unsigned m3 = 0u;
@@ -318,30 +252,9 @@ __device__ __forceinline__ bool slab_item(const StepArgs<float>& a, const CUtens
       hya.v[e] = hyc.v[e] + cHY[e] * (-dex[e] + (ezx - ez.v[e]));      // U2
     }
     sts4(&S.x1[row][4 * q], hxa);
-    if (!__syncthreads_and(ok)) {  // (1) the slot is read and hx~ is out
-      // a copy did not land: raise the error word, wait (bounded) for the
-      // copies still in flight, stop
-      if (tid == 0) {
-        atomicExch(err, 1);
-        for (int kk = k; kk <= issued; ++kk) {
-          const int ss = (kk - kstart) % kSD;
-          bar_wait(&S.bar[ss], (phases >> ss) & 1u);
-        }
-      }
-      __syncthreads();
-      failed = true;
-      break;
-    }
-    if constexpr (MAT) {
-      phases ^= 1u << s;
-      if (k + kSD < k1) {
-        if (tid == 0) issue(k + kSD);
-        issued = k + kSD;
-      }
-    } else {
-      if (k + kSD < k1) issue_q(k + kSD, m2);
-      cp_commit();
-    }
+    __syncthreads();  // (1) the slot is read and hx~ is out
+    if (k + kSD < k1) issue_q(k + kSD, m2);  // into the freed slot
+    cp_commit();
     // S2: ez' = ez + 2a M^-1 (P_y^T hx~ - P_x^T hy~ - jj_z)
     const Q4 hxaD = row >= 1 ? lds4(&S.x1[row - 1][4 * q]) : zero;
     const float hyaL = left_of(hya.v[3], q);
@@ -410,7 +323,7 @@ __device__ __forceinline__ bool slab_item(const StepArgs<float>& a, const CUtens
       hzn.v[e] = hz.v[e] + cHZ[e] * ((exaU.v[e] - exa.v[e]) - (eyx - eya.v[e]));      // U8
     }
     sts4(&S.x2[row][4 * q], hzn);
-    if constexpr (!MAT) cp_wait<1>();  // this thread's copies of the next plane are in
+    cp_wait<1>();     // this thread's copies of the next plane are in
     __syncthreads();  // (4) (and the next plane's slot is in)
     // S6: ex', ey'
     const Q4 hznD = row >= 1 ? lds4(&S.x2[row - 1][4 * q]) : zero;
@@ -440,27 +353,16 @@ __device__ __forceinline__ bool slab_item(const StepArgs<float>& a, const CUtens
       ey1 = eyn_in;
     }
   }
-  if constexpr (!MAT) cp_wait<0>();
+  cp_wait<0>();
   __syncthreads();  // every thread is done with the ring before the next item refills it
-  return !failed;
 }
 
 template <bool MAT>
-__global__ void __launch_bounds__(kSThreads, 1)
-fused_step_slab(const StepArgs<float> a, const __grid_constant__ CUtensorMap tm_ez,
-                const __grid_constant__ CUtensorMap tm_hz, const __grid_constant__ CoefMaps tm_co, int* err,
-                int* sched) {
+__global__ void __launch_bounds__(kSThreads, 1) fused_step_slab(const StepArgs<float> a, int* sched) {
   using Smem = SlabSmem<MAT>;
-  constexpr int kSD = Smem::SD;
   extern __shared__ __align__(128) unsigned char slab_raw[];
   Smem& S = *reinterpret_cast<Smem*>(slab_raw);
   const int tid = threadIdx.x;
-  if (tid == 0) {
-    for (int s = 0; s < kSD; ++s) bar_init(&S.bar[s], 1u);
-  }
-  asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
-  __syncthreads();
-  unsigned phases = 0;
   const int nitems = a.work ? a.n_work : a.tiles_x * a.tiles_y * a.n_chunks;
 
   // Items in list order: the first per CTA by its index, then (with a
@@ -469,11 +371,10 @@ fused_step_slab(const StepArgs<float> a, const __grid_constant__ CUtensorMap tm_
   // halo rows in L2) and CTAs that drew cheap items (much PEC) take more.
   const int G = gridDim.x;
   int wi = blockIdx.x, par = 0;
-  bool ok = true;
-  while (wi < nitems && ok) {
+  while (wi < nitems) {
     if (tid == 0 && sched) S.next[par] = G + atomicAdd(sched, 1);
     const int item = a.work ? a.work[wi] : wi;
-    ok = slab_item<MAT>(a, &tm_ez, &tm_hz, &tm_co, item, S, phases, err);
+    slab_item<MAT>(a, item, S);
     wi = sched ? S.next[par] : wi + G;
     par ^= 1;
   }
@@ -493,22 +394,20 @@ fused_step_slab(const StepArgs<float> a, const __grid_constant__ CUtensorMap tm_
 // no tensor map is involved).
 __global__ void __launch_bounds__(kSThreads, 1)
 fused_step_slab_batch(const BatchMember<float>* __restrict__ members, const int2* __restrict__ work,
-                      const int* __restrict__ n_work_p, int* err, int* sched) {
+                      const int* __restrict__ n_work_p, int* sched) {
   using Smem = SlabSmem<false>;
   extern __shared__ __align__(128) unsigned char slab_raw[];
   Smem& S = *reinterpret_cast<Smem*>(slab_raw);
   const int tid = threadIdx.x;
-  unsigned phases = 0;
   const int G = gridDim.x;
   const int n_work = *n_work_p;  // written before the launch (stream order)
   int wi = blockIdx.x, par = 0;
-  bool ok = true;
-  while (wi < n_work && ok) {
+  while (wi < n_work) {
     if (tid == 0 && sched) S.next[par] = G + atomicAdd(sched, 1);
     const int2 w = work[wi];
     const BatchMember<float>& mb = members[w.x];
     if (mb.active) {
-      ok = slab_item<false>(mb.a, nullptr, nullptr, nullptr, w.y, S, phases, err);
+      slab_item<false>(mb.a, w.y, S);
     } else {
       // an item of a member past its limit: no work, but the ticket thread 0
       // wrote above must be visible before every thread reads it (slab_item
@@ -527,61 +426,13 @@ fused_step_slab_batch(const BatchMember<float>* __restrict__ members, const int2
   }
 }
 
-// The driver's tensor-map encoder, looked up through the runtime (the library
-// does not link the driver library, so it also loads where no driver is).
-PFN_cuTensorMapEncodeTiled_v12000 encoder() {
-  static PFN_cuTensorMapEncodeTiled_v12000 fn = nullptr;
-  if (!fn) {
-    void* p = nullptr;
-    cudaDriverEntryPointQueryResult q;
-    if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &p, 12000, cudaEnableDefault, &q) ==
-            cudaSuccess &&
-        q == cudaDriverEntryPointSuccess)
-      fn = reinterpret_cast<PFN_cuTensorMapEncodeTiled_v12000>(p);
-  }
-  return fn;
-}
-
-CUresult encode3d(CUtensorMap* map, CUtensorMapDataType type, void* base, const Layout& L, int esz,
-                  unsigned box_x) {
-  PFN_cuTensorMapEncodeTiled_v12000 fn = encoder();
-  if (!fn) return CUDA_ERROR_NOT_FOUND;
-  const cuuint64_t dims[3] = {(cuuint64_t)L.px, (cuuint64_t)(L.ny + 4), (cuuint64_t)(L.nz + 3)};
-  const cuuint64_t strides[2] = {(cuuint64_t)L.px * esz, (cuuint64_t)L.sz * esz};
-  const cuuint32_t box[3] = {box_x, (cuuint32_t)kSY, 1};
-  const cuuint32_t estr[3] = {1, 1, 1};
-  return fn(map, type, 3, base, dims, strides, box, estr, CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE,
-            CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
-}
-
 }  // namespace
 
 bool slab_shape_ok(int tx, int ty) { return tx == kOX && ty == kOY; }
 
-int build_slab_maps(SlabMaps* m, void* const ez[2], void* const hz[2], void* const co[6], const Layout& L) {
-  static_assert(sizeof(CUtensorMap) <= sizeof(m->ez[0]), "tensor map storage");
-  // the tiled copies need 16-byte row strides and 16-byte box starts
-  if ((L.px * 4) % 16 != 0 || L.px % 16 != 0 || (L.ox % 4) != 0) return -1;
-  for (int c = 0; c < 2; ++c) {
-    if (encode3d(reinterpret_cast<CUtensorMap*>(m->ez[c]), CU_TENSOR_MAP_DATA_TYPE_FLOAT32, ez[c], L, 4, kSX) !=
-            CUDA_SUCCESS ||
-        encode3d(reinterpret_cast<CUtensorMap*>(m->hz[c]), CU_TENSOR_MAP_DATA_TYPE_FLOAT32, hz[c], L, 4, kSX) !=
-            CUDA_SUCCESS)
-      return -1;
-  }
-  m->has_co = co != nullptr;
-  if (co)
-    for (int c = 0; c < 6; ++c)
-      if (!co[c] || encode3d(reinterpret_cast<CUtensorMap*>(m->co[c]), CU_TENSOR_MAP_DATA_TYPE_FLOAT32, co[c], L, 4,
-                             kSX) != CUDA_SUCCESS)
-        return -1;
-  return 0;
-}
-
 namespace {
 template <bool MAT>
-cudaError_t launch_slab(const StepArgs<float>& a, const SlabMaps& m, int cur, int* err, int* sched,
-                        cudaStream_t st) {
+cudaError_t launch_slab(const StepArgs<float>& a, int* sched, cudaStream_t st) {
   static int sms = 0;
   const size_t smem = sizeof(SlabSmem<MAT>);
   if (!sms) {
@@ -597,22 +448,13 @@ cudaError_t launch_slab(const StepArgs<float>& a, const SlabMaps& m, int cur, in
   }
   const int items = a.work ? a.n_work : a.tiles_x * a.tiles_y * a.n_chunks;
   if (items <= 0) return cudaSuccess;
-  const CUtensorMap& mez = *reinterpret_cast<const CUtensorMap*>(m.ez[cur]);
-  const CUtensorMap& mhz = *reinterpret_cast<const CUtensorMap*>(m.hz[cur]);
-  CoefMaps mco;
-  if constexpr (MAT) {
-    for (int c = 0; c < 6; ++c) mco.m[c] = *reinterpret_cast<const CUtensorMap*>(m.co[c]);
-  } else {
-    memset(&mco, 0, sizeof(mco));
-  }
-  fused_step_slab<MAT><<<std::min(items, sms), kSThreads, smem, st>>>(a, mez, mhz, mco, err, sched);
+  fused_step_slab<MAT><<<std::min(items, sms), kSThreads, smem, st>>>(a, sched);
   return cudaGetLastError();
 }
 }  // namespace
 
-cudaError_t launch_fused_slab_batch(BatchMember<float>* members, int n_members,
-                                    const int2* work, const int* n_work, int n_bound, int* err, int* sched,
-                                    int nz_max, cudaStream_t st) {
+cudaError_t launch_fused_slab_batch(BatchMember<float>* members, int n_members, const int2* work,
+                                    const int* n_work, int n_bound, int* sched, int nz_max, cudaStream_t st) {
   static int sms = 0;
   const size_t smem = sizeof(SlabSmem<false>);
   if (!sms) {
@@ -627,7 +469,7 @@ cudaError_t launch_fused_slab_batch(BatchMember<float>* members, int n_members,
     }
   }
   if (n_bound > 0) {
-    fused_step_slab_batch<<<std::min(n_bound, sms), kSThreads, smem, st>>>(members, work, n_work, err, sched);
+    fused_step_slab_batch<<<std::min(n_bound, sms), kSThreads, smem, st>>>(members, work, n_work, sched);
     cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess) return e;
   }
@@ -636,11 +478,10 @@ cudaError_t launch_fused_slab_batch(BatchMember<float>* members, int n_members,
   return launch_batch_advance<float>(members, n_members, st);
 }
 
-cudaError_t launch_fused_slab_step(const StepArgs<float>& a, const SlabMaps& m, int cur, int* err, int* sched,
-                                   cudaStream_t st) {
-  // per-entry coefficient arrays (material runs) need their tensor maps
-  if (a.co.ua[0]) return m.has_co ? launch_slab<true>(a, m, cur, err, sched, st) : cudaErrorInvalidValue;
-  return launch_slab<false>(a, m, cur, err, sched, st);
+cudaError_t launch_fused_slab_step(const StepArgs<float>& a, int* sched, cudaStream_t st) {
+  // per-entry coefficient arrays (material runs) stream through the ring too
+  if (a.co.ua[0]) return launch_slab<true>(a, sched, st);
+  return launch_slab<false>(a, sched, st);
 }
 
 }  // namespace tetm

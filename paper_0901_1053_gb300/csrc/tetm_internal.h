@@ -138,29 +138,19 @@ cudaError_t launch_fused_warp_batch(const BatchMember<T>* members, int n_members
 template <typename T>
 cudaError_t launch_batch_advance(BatchMember<T>* members, int n_members, cudaStream_t st);
 
-// ---- block-tiled float32 step with tensor staging (kernels_slab.cu): tile
-// 56 x 28, one CTA of 512 threads per SM ----------------------------------
-struct SlabMaps {  // tensor maps (CUtensorMap) of e_z and h_z of both field sets and
-                  // (material runs) the six coefficient arrays
-  alignas(64) unsigned char ez[2][128];
-  alignas(64) unsigned char hz[2][128];
-  alignas(64) unsigned char co[6][128];
-  bool has_co;
-};
+// ---- block-tiled float32 step with a shared-memory ring (kernels_slab.cu):
+// tile 56 x 28, one CTA of 512 threads per SM ------------------------------
 bool slab_shape_ok(int tile_x, int tile_y);
-// co: the six per-entry coefficient arrays, or nullptr (one material)
-int build_slab_maps(SlabMaps* m, void* const ez[2], void* const hz[2], void* const co[6], const Layout& L);
 // one step of every active member of a float32 batch on the slab kernel
 // (work = (member, item) pairs counted at n_work in device memory, at most
 // n_bound; sched as below), the transverse wakes, then the device-side
 // advance of all n_members slots
-cudaError_t launch_fused_slab_batch(BatchMember<float>* members, int n_members,
-                                    const int2* work, const int* n_work, int n_bound, int* err, int* sched,
-                                    int nz_max, cudaStream_t st);
+cudaError_t launch_fused_slab_batch(BatchMember<float>* members, int n_members, const int2* work,
+                                    const int* n_work, int n_bound, int* sched, int nz_max, cudaStream_t st);
 // sched: two ints of device memory, zero before the first launch, that the
 // kernel's dynamic schedule uses and leaves zero (nullptr: static order)
-cudaError_t launch_fused_slab_step(const StepArgs<float>& a, const SlabMaps& m, int cur, int* err, int* sched,
-                                   cudaStream_t st);
+// (a.co.ua[0] set: the per-entry coefficient arrays of material runs)
+cudaError_t launch_fused_slab_step(const StepArgs<float>& a, int* sched, cudaStream_t st);
 
 // ---- Yee's E/M leapfrog, Eq. (7) (kernels_yee.cu): the step arguments carry
 // dt M^-1 as the per-component constants --------------------------------------
@@ -243,8 +233,6 @@ struct tetm_solver {
   int scheme;     // TETM_SCHEME_*
   int kernel;
   int tile_x, tile_y, chunk_z;
-  tetm::SlabMaps* slab;          // tensor maps of the slab kernel (built on first use)
-  int* err;                      // device error word of the slab kernel's bounded waits
   int* sched;                    // the slab kernel's schedule counters (two ints)
   int tiles_x, tiles_y, n_chunks;
   int* work;
