@@ -1,16 +1,16 @@
-// Block-tiled fused step with tensor staging, float32 (Sec. 4.2, Eq. (23)).
+// Block-tiled fused step, float32 (Sec. 4.2, Eq. (23)).
 //
 // One CTA of 512 threads per SM takes (tile, z chunk) work items in turn. A
 // tile owns 56 x 28 nodes and loads 64 x 32 (4 halo columns and 2 halo rows on
 // each side: the ten updates reach two nodes sideways). Thread t holds the
 // four consecutive columns 4 (t mod 16) .. +3 of row t / 16 (a quad), so its
 // loads and stores are 16-byte vectors, and marches through the chunk plane by
-// plane with the z-state of its quad in registers (old e_x, e_y of the plane,
-// new h_x, h_y of the plane below): no per-row state in shared memory.
+// plane with the z-state of its quad in registers (old e_x, e_y, new h_x, h_y
+// of the planes below): no per-row state in shared memory.
 //
 // Only entries that carry a field move through the per-thread loads and
 // stores. Each thread reads the activity bytes of its quad (one 32-bit word
-// per plane, three planes ahead) and
+// per plane, a few planes ahead) and
 //  * loads h_x, h_y, e_x, e_y of the quad (16-byte loads one plane ahead) only
 //    when one of its four nodes carries that component, else takes zero (an
 //    entry without a field holds zero for ever);
@@ -18,20 +18,30 @@
 //    carries it (the other field set's entry already holds that zero).
 // e_z and h_z are the inputs a node reads at its neighbours; they (and with
 // material arrays the six per-entry coefficient arrays, read at the node)
-// arrive through a ring of two planes in shared memory, filled two planes
-// ahead: each thread copies its own quad of every array into the slot with a
-// 16-byte asynchronous copy, or writes zeros without a read where none of
-// the quad's nodes carries that component (an entry without a field, and its
-// coefficient, hold zero), so the ring reads no pipe wall. Completion by the
-// thread's copy group, publication by the last block barrier of the plane
-// before.
+// arrive through rings of two planes in shared memory: each thread copies its
+// own quad of every array into the slot with a 16-byte asynchronous copy, or
+// writes zeros without a read where none of the quad's nodes carries that
+// component (an entry without a field, and its coefficient, hold zero), so the
+// rings read no pipe wall. Completion by the thread's copy group, publication
+// by a block barrier.
 //
 // The intermediates a stage reads one row up or down (hx~, ez', ex~, hz') go
-// through two shared-memory buffers, those one column left or right through
-// warp shuffles; four block barriers per plane, the first of which also
-// settles the slot waits:
+// through shared-memory buffers, those one column left or right through warp
+// shuffles. Six stages per plane:
 //   S1 hx~, hy~ (U1, U2)  | S2 ez' (U3, + current) | S3 hx', hy' (U4, U5)
 //   S4 ex~, ey~ (U6, U7)  | S5 hz' (U8)            | S6 ex', ey' (U9, U10)
+// With one material they run plane by plane, a block barrier after S1, S2,
+// S4 and S5 (two buffers). With coefficient arrays the sweep is skewed by half
+// a step: iteration i runs S1..S3 of plane i+1 (the TM half reads only old
+// fields) beside S4..S6 of plane i (the TE half reads the new h_x, h_y of
+// planes i and i-1), as pairs A = S1|S4, B = S2|S5, C = S3|S6 with a barrier
+// after A and after B (four buffers: C reads what B wrote, and the next A
+// writes only buffers that other threads last read in B); the copies then
+// have two planes of work to land. (The skew costs the one-material sweep more
+// instructions than its barriers do: its coefficients come from the activity
+// words, and a third plane of e_x, e_y rides in registers.) Per node the
+// arithmetic and its order are the same in both, so the results are the same
+// bits.
 // The column of i = 0 sits at 8 in the float32 layout, so the 224-byte rows a
 // tile writes start and end on 32-byte sectors and no two tiles write into
 // the same sector.
@@ -59,14 +69,14 @@ struct SlabSmemU {
   float x1[kSY][kSX], x2[kSY][kSX];
   int next[2];                      // the CTA's next work item (dynamic schedule)
 };
-// Material arrays: a two-plane ring of e_z, h_z and the six per-entry
-// coefficient arrays (alpha M^-1, 2 alpha M^-1 for e_z and h_z), 144 KB.
+// Material arrays: two-plane rings of e_z and h_z with the six per-entry
+// coefficient arrays (alpha M^-1, 2 alpha M^-1 for e_z and h_z), and the four
+// exchange buffers of the skewed sweep, 160 KB.
 struct SlabSmemM {
-  static constexpr int SD = 2;
-  float ez[SD][kSY * kSX];
-  float hz[SD][kSY * kSX];
-  float co[SD][6][kSY][kSX];
-  float x1[kSY][kSX], x2[kSY][kSX];
+  float ez[2][kSY * kSX];
+  float hz[2][kSY * kSX];
+  float co[2][6][kSY][kSX];
+  float x1[kSY][kSX], x2[kSY][kSX], x3[kSY][kSX], x4[kSY][kSX];  // hx~, ez', ex~, hz'
   int next[2];
 };
 template <bool MAT>
@@ -130,12 +140,11 @@ __device__ __forceinline__ float right_of(float v0, int q) {
   return q + 1 < kQ ? t : 0.f;
 }
 
-// One (tile, z-chunk) work item of solve a (the ten updates of every plane
-// of the chunk).
-template <bool MAT>
-__device__ __forceinline__ void slab_item(const StepArgs<float>& a, int item, SlabSmem<MAT>& S) {
-  using Smem = SlabSmem<MAT>;
-  constexpr int kSD = Smem::SD;
+// One (tile, z-chunk) work item of solve a with one material (the ten
+// updates of every plane of the chunk, plane by plane: four block barriers
+// per plane).
+__device__ __forceinline__ void slab_item(const StepArgs<float>& a, int item, SlabSmemU& S) {
+  constexpr int kSD = SlabSmemU::SD;
   const int tid = threadIdx.x, q = tid % kQ, row = tid / kQ;
   const Layout L = a.L;
   const long long SZ = L.sz, PX = L.px;
@@ -163,49 +172,48 @@ __device__ __forceinline__ void slab_item(const StepArgs<float>& a, int item, Sl
   auto word = [&](int k) -> unsigned { return ld_word_if(a.co.mask + gidx(k), inq); };
   auto load_if = [&](const float* base, int k, bool p) -> Q4 { return ld4_if(base + gidx(k), p); };
   // plane k into its slot: each thread copies the quad of its own node row
-  // and columns of e_z, h_z (and of the six coefficient arrays), only where
-  // one of the quad's nodes carries that component (zeros otherwise: the
-  // entry and its coefficient hold zero), so the ring reads no pipe wall;
-  // completion by the thread's copy group and the block barrier after it
+  // and columns of e_z, h_z, only where one of the quad's nodes carries that
+  // component (zeros otherwise: the entry holds zero), so the ring reads no
+  // pipe wall; completion by the thread's copy group and the block barrier
+  // after it
   auto issue_q = [&](int k, unsigned mw) {
     const int s = (k - kstart) % kSD;
     const long long g = inq ? gidx(k) : 0;
     cp16_or_zero(&S.ez[s][row * kSX + 4 * q], a.in[kEZ] + g, has(mw, kEZ));
     cp16_or_zero(&S.hz[s][row * kSX + 4 * q], a.in[kHZ] + g, has(mw, kHZ));
-    if constexpr (MAT) {
-#pragma unroll
-      for (int c = 0; c < 6; ++c) cp16_or_zero(&S.co[s][c][row][4 * q], a.co.ua[c] + g, has(mw, c));
-    }
   };
-  // activity words of planes kstart .. kstart + 2 (m0 of the plane being
-  // worked on, m1, m2 of the next two); z-state and the register prefetch
-  // (plane k: hx, hy of k; ex, ey of k+1)
-  unsigned m0 = word(kstart), m1 = word(kstart + 1), m2 = word(kstart + 2);
-  issue_q(kstart, m0);
-  cp_commit();
-  if (nplanes > 1) issue_q(kstart + 1, m1);
-  cp_commit();
-  cp_wait<1>();
+  // activity words of planes k .. k + kSD (m[0] of the plane being worked
+  // on; m[kSD] of the plane whose copy is issued next); z-state and the
+  // register prefetch (plane k: hx, hy of k; ex, ey of k+1)
+  unsigned m[kSD + 1];
+#pragma unroll
+  for (int i = 0; i <= kSD; ++i) m[i] = kstart + i <= k1 ? word(kstart + i) : 0u;
+#pragma unroll
+  for (int i = 0; i < kSD; ++i) {
+    if (i < nplanes) issue_q(kstart + i, m[i]);
+    cp_commit();
+  }
+  cp_wait<kSD - 1>();
   __syncthreads();  // plane kstart's slot is in
-  Q4 ex0 = load_if(a.in[kEX], kstart, has(m0, kEX)), ey0 = load_if(a.in[kEY], kstart, has(m0, kEY));
-  Q4 hxc = load_if(a.in[kHX], kstart, has(m0, kHX)), hyc = load_if(a.in[kHY], kstart, has(m0, kHY));
-  Q4 ex1 = load_if(a.in[kEX], kstart + 1, has(m1, kEX)), ey1 = load_if(a.in[kEY], kstart + 1, has(m1, kEY));
+  Q4 ex0 = load_if(a.in[kEX], kstart, has(m[0], kEX)), ey0 = load_if(a.in[kEY], kstart, has(m[0], kEY));
+  Q4 hxc = load_if(a.in[kHX], kstart, has(m[0], kHX)), hyc = load_if(a.in[kHY], kstart, has(m[0], kHY));
+  Q4 ex1 = load_if(a.in[kEX], kstart + 1, has(m[1], kEX)), ey1 = load_if(a.in[kEY], kstart + 1, has(m[1], kEY));
   Q4 hxp = zero, hyp = zero;
   const bool line_row = a.b.on && gj == a.b.j0;
   const bool line_q = line_row && a.b.i0 >= gi && a.b.i0 < gi + 4;  // the quad holds the bunch line node
 
   for (int k = kstart; k < k1; ++k) {
     const int s = (k - kstart) % kSD;
-    // next plane's register inputs and the activity word three planes on, early
+    // next plane's register inputs and the activity word kSD + 1 planes on, early
     Q4 hxn_in, hyn_in, exn_in, eyn_in;
-    unsigned m3 = 0u;
+    unsigned mn = 0u;
     const bool more = k + 1 < k1;
     if (more) {
-      hxn_in = load_if(a.in[kHX], k + 1, has(m1, kHX));
-      hyn_in = load_if(a.in[kHY], k + 1, has(m1, kHY));
-      exn_in = load_if(a.in[kEX], k + 2, has(m2, kEX));
-      eyn_in = load_if(a.in[kEY], k + 2, has(m2, kEY));
-      if (k + 3 <= k1) m3 = word(k + 3);
+      hxn_in = load_if(a.in[kHX], k + 1, has(m[1], kHX));
+      hyn_in = load_if(a.in[kHY], k + 1, has(m[1], kHY));
+      exn_in = load_if(a.in[kEX], k + 2, has(m[2], kEX));
+      eyn_in = load_if(a.in[kEY], k + 2, has(m[2], kEY));
+      if (k + kSD + 1 <= k1) mn = word(k + kSD + 1);
     }
     // slot inputs: e_z, h_z of this quad and its neighbours
     const float* sez = &S.ez[s][0];
@@ -216,31 +224,17 @@ __device__ __forceinline__ void slab_item(const StepArgs<float>& a, int item, Sl
     const Q4 hz = lds4(shz + row * kSX + 4 * q);
     const Q4 hzD = row >= 1 ? lds4(shz + (row - 1) * kSX + 4 * q) : zero;
     const float hzL = q >= 1 ? shz[row * kSX + 4 * q - 1] : 0.f;
+    // one coefficient per component, switched by the activity bytes
     float cHX[4], cHY[4], cEZ[4], cEX[4], cEY[4], cHZ[4], dey[4], dex[4];
-    if constexpr (MAT) {  // per-entry coefficients from the slot
-      const Q4 c0 = lds4(&S.co[s][kEX][row][4 * q]), c1 = lds4(&S.co[s][kEY][row][4 * q]);
-      const Q4 c2 = lds4(&S.co[s][kEZ][row][4 * q]), c3 = lds4(&S.co[s][kHX][row][4 * q]);
-      const Q4 c4 = lds4(&S.co[s][kHY][row][4 * q]), c5 = lds4(&S.co[s][kHZ][row][4 * q]);
 #pragma unroll
-      for (int e = 0; e < 4; ++e) {
-        cEX[e] = c0.v[e];
-        cEY[e] = c1.v[e];
-        cEZ[e] = c2.v[e];
-        cHX[e] = c3.v[e];
-        cHY[e] = c4.v[e];
-        cHZ[e] = c5.v[e];
-      }
-    } else {  // one coefficient per component, switched by the activity bytes
-#pragma unroll
-      for (int e = 0; e < 4; ++e) {
-        const unsigned m = (m0 >> (8 * e)) & 0xFFu;
-        cEX[e] = (m & 1) ? uEX : 0.f;
-        cEY[e] = (m & 2) ? uEY : 0.f;
-        cEZ[e] = (m & 4) ? uEZ : 0.f;
-        cHX[e] = (m & 8) ? uHX : 0.f;
-        cHY[e] = (m & 16) ? uHY : 0.f;
-        cHZ[e] = (m & 32) ? uHZ : 0.f;
-      }
+    for (int e = 0; e < 4; ++e) {
+      const unsigned b = (m[0] >> (8 * e)) & 0xFFu;
+      cEX[e] = (b & 1) ? uEX : 0.f;
+      cEY[e] = (b & 2) ? uEY : 0.f;
+      cEZ[e] = (b & 4) ? uEZ : 0.f;
+      cHX[e] = (b & 8) ? uHX : 0.f;
+      cHY[e] = (b & 16) ? uHY : 0.f;
+      cHZ[e] = (b & 32) ? uHZ : 0.f;
     }
     Q4 hxa, hya;
 #pragma unroll
@@ -253,7 +247,7 @@ __device__ __forceinline__ void slab_item(const StepArgs<float>& a, int item, Sl
     }
     sts4(&S.x1[row][4 * q], hxa);
     __syncthreads();  // (1) the slot is read and hx~ is out
-    if (k + kSD < k1) issue_q(k + kSD, m2);  // into the freed slot
+    if (k + kSD < k1) issue_q(k + kSD, m[kSD]);  // into the freed slot
     cp_commit();
     // S2: ez' = ez + 2a M^-1 (P_y^T hx~ - P_x^T hy~ - jj_z)
     const Q4 hxaD = row >= 1 ? lds4(&S.x1[row - 1][4 * q]) : zero;
@@ -289,9 +283,9 @@ __device__ __forceinline__ void slab_item(const StepArgs<float>& a, int item, Sl
       hyn.v[e] = hya.v[e] + cHY[e] * (-dex[e] + (ezx - ezn.v[e]));     // U5
     }
     const bool st = k >= k0 && own_q;
-    st4_if(a.out[kEZ] + gidx(k), ezn, st && has(m0, kEZ));
-    st4_if(a.out[kHX] + gidx(k), hxn, st && has(m0, kHX));
-    st4_if(a.out[kHY] + gidx(k), hyn, st && has(m0, kHY));
+    st4_if(a.out[kEZ] + gidx(k), ezn, st && has(m[0], kEZ));
+    st4_if(a.out[kHX] + gidx(k), hxn, st && has(m[0], kHX));
+    st4_if(a.out[kHY] + gidx(k), hyn, st && has(m[0], kHY));
     if (st) {
       if (line_q && a.b.i0 < L.nx) {
         const long long mm = (a.n + a.b.kshift) - k - a.b.c0;
@@ -323,7 +317,7 @@ __device__ __forceinline__ void slab_item(const StepArgs<float>& a, int item, Sl
       hzn.v[e] = hz.v[e] + cHZ[e] * ((exaU.v[e] - exa.v[e]) - (eyx - eya.v[e]));      // U8
     }
     sts4(&S.x2[row][4 * q], hzn);
-    cp_wait<1>();     // this thread's copies of the next plane are in
+    cp_wait<kSD - 1>();  // this thread's copies of the next plane are in
     __syncthreads();  // (4) (and the next plane's slot is in)
     // S6: ex', ey'
     const Q4 hznD = row >= 1 ? lds4(&S.x2[row - 1][4 * q]) : zero;
@@ -335,23 +329,285 @@ __device__ __forceinline__ void slab_item(const StepArgs<float>& a, int item, Sl
       exn.v[e] = exa.v[e] + cEX[e] * ((hyp.v[e] - hyn.v[e]) - (hznD.v[e] - hzn.v[e]));   // U9
       eyn.v[e] = eya.v[e] + cEY[e] * (-(hxp.v[e] - hxn.v[e]) + (hzl - hzn.v[e]));       // U10
     }
-    st4_if(a.out[kEX] + gidx(k), exn, st && has(m0, kEX));
-    st4_if(a.out[kEY] + gidx(k), eyn, st && has(m0, kEY));
-    st4_if(a.out[kHZ] + gidx(k), hzn, st && has(m0, kHZ));
+    st4_if(a.out[kEX] + gidx(k), exn, st && has(m[0], kEX));
+    st4_if(a.out[kEY] + gidx(k), eyn, st && has(m[0], kEY));
+    st4_if(a.out[kHZ] + gidx(k), hzn, st && has(m[0], kHZ));
     // carry the z-state, take the prefetched inputs
     hxp = hxn;
     hyp = hyn;
     ex0 = ex1;
     ey0 = ey1;
-    m0 = m1;
-    m1 = m2;
-    m2 = m3;
+#pragma unroll
+    for (int i = 0; i < kSD; ++i) m[i] = m[i + 1];
+    m[kSD] = mn;
     if (more) {
       hxc = hxn_in;
       hyc = hyn_in;
       ex1 = exn_in;
       ey1 = eyn_in;
     }
+  }
+  cp_wait<0>();
+  __syncthreads();  // every thread is done with the ring before the next item refills it
+}
+
+// One (tile, z-chunk) work item of solve a with per-entry coefficient
+// arrays, skewed by half a step: iteration i runs the TM half of plane i+1
+// (U1..U5, which reads only old fields) beside the TE half of plane i
+// (U6..U10, which reads the new h_x, h_y of planes i and i-1), two block
+// barriers per iteration.
+__device__ __forceinline__ void slab_item_mat(const StepArgs<float>& a, int item, SlabSmemM& S) {
+  const int tid = threadIdx.x, q = tid % kQ, row = tid / kQ;
+  const Layout L = a.L;
+  const long long SZ = L.sz, PX = L.px;
+  const int ntile = a.tiles_x * a.tiles_y;
+  const Q4 zero{{0.f, 0.f, 0.f, 0.f}};
+  const int tile = item % ntile, chunk = item / ntile;
+  const int gx0 = (tile % a.tiles_x) * kOX - 4;  // global i of loaded column 0
+  const int gy0 = (tile / a.tiles_x) * kOY - 2;  // global j of loaded row 0
+  const int k0 = chunk * a.chunk_z, k1 = min(k0 + a.chunk_z, L.nz);
+  const int kstart = k0 - 1;                   // the plane below the chunk: its new h_x, h_y feed U6, U7 of k0
+  const int cx = gx0 + L.ox;                   // layout column of loaded column 0
+
+  // this thread's quad; a quad with an active node lies inside its layout
+  // row (columns i <= nx + 2 < px - ox), so every predicated access is a
+  // whole 16-byte vector (a quad across i = nx stores the zeros its entries
+  // past the cells compute: zero input, zero coefficient)
+  const int gi = gx0 + 4 * q, gj = gy0 + row;
+  const bool inq = gj + 2 < L.ny + 4 && cx + 4 * q + 4 <= PX;  // the quad lies inside the arrays
+  const long long qoff = (long long)(gj + 2) * PX + cx + 4 * q;
+  const bool own_q = q >= 1 && q <= kQ - 2 && row >= 2 && row < kSY - 2 && gj < L.ny;
+  auto gidx = [&](int k) { return (long long)(k + 1) * SZ + qoff; };
+  auto word = [&](int k) -> unsigned { return ld_word_if(a.co.mask + gidx(k), inq); };
+  auto load_if = [&](const float* base, int k, bool p) -> Q4 { return ld4_if(base + gidx(k), p); };
+  // e_z of plane k with the coefficient arrays of h_x, h_y, e_z (the TM
+  // half), h_z of plane k with those of e_x, e_y, h_z (the TE half), into
+  // their slots: each thread copies the quads of its own
+  // node row and columns, only where one of the quad's nodes carries that
+  // component (zeros otherwise: the entry and its coefficient hold zero), so
+  // the ring reads no pipe wall; completion by the thread's copy group and
+  // the block barrier after it
+  auto issue_ez = [&](int k, unsigned mw) {
+    const int s = (k - kstart) & 1;
+    const long long g = inq ? gidx(k) : 0;
+    cp16_or_zero(&S.ez[s][row * kSX + 4 * q], a.in[kEZ] + g, has(mw, kEZ));
+    cp16_or_zero(&S.co[s][kHX][row][4 * q], a.co.ua[kHX] + g, has(mw, kHX));
+    cp16_or_zero(&S.co[s][kHY][row][4 * q], a.co.ua[kHY] + g, has(mw, kHY));
+    cp16_or_zero(&S.co[s][kEZ][row][4 * q], a.co.ua[kEZ] + g, has(mw, kEZ));
+  };
+  auto issue_hz = [&](int k, unsigned mw) {
+    const int s = (k - kstart) & 1;
+    const long long g = inq ? gidx(k) : 0;
+    cp16_or_zero(&S.hz[s][row * kSX + 4 * q], a.in[kHZ] + g, has(mw, kHZ));
+    cp16_or_zero(&S.co[s][kEX][row][4 * q], a.co.ua[kEX] + g, has(mw, kEX));
+    cp16_or_zero(&S.co[s][kEY][row][4 * q], a.co.ua[kEY] + g, has(mw, kEY));
+    cp16_or_zero(&S.co[s][kHZ][row][4 * q], a.co.ua[kHZ] + g, has(mw, kHZ));
+  };
+  // Iteration i works on the TM half of plane i+1 and the TE half of plane
+  // i; m[j] is the activity word of plane i + j. The ring holds e_z of
+  // planes i+1, i+2 and h_z of planes i, i+1; after the first barrier the
+  // slots read in A take e_z of i+3 and h_z of i+2 (two planes of work to
+  // land). Registers: old e_x, e_y of planes i, i+1, i+2 (exA, exB, exC),
+  // old h_x, h_y of plane i+1, new h_x, h_y of planes i (hxn) and i-1 (hxp),
+  // and the loads of the next iteration, one iteration ahead.
+  unsigned m[4];
+  m[0] = 0u;  // plane kstart - 1: no TE half there
+#pragma unroll
+  for (int j = 1; j < 4; ++j) m[j] = kstart + j - 1 <= k1 ? word(kstart + j - 1) : 0u;
+  issue_ez(kstart, m[1]);
+  if (kstart + 1 < k1) issue_ez(kstart + 1, m[2]);
+  cp_commit();
+  Q4 exA = zero, eyA = zero;
+  Q4 exB = load_if(a.in[kEX], kstart, has(m[1], kEX)), eyB = load_if(a.in[kEY], kstart, has(m[1], kEY));
+  Q4 exC = load_if(a.in[kEX], kstart + 1, has(m[2], kEX)), eyC = load_if(a.in[kEY], kstart + 1, has(m[2], kEY));
+  Q4 hxc = load_if(a.in[kHX], kstart, has(m[1], kHX)), hyc = load_if(a.in[kHY], kstart, has(m[1], kHY));
+  Q4 hxp = zero, hyp = zero, hxn = zero, hyn = zero;
+  const bool line_row = a.b.on && gj == a.b.j0;
+  const bool line_q = line_row && a.b.i0 >= gi && a.b.i0 < gi + 4;  // the quad holds the bunch line node
+  cp_wait<0>();
+  __syncthreads();  // e_z of planes kstart, kstart + 1 is in
+
+  for (int i = kstart - 1; i < k1; ++i) {
+    const bool tm = i + 1 < k1;  // the TM half of plane p = i + 1 (block-uniform)
+    const bool te = i >= k0;     // the TE half of plane i (block-uniform)
+    const int p = i + 1;
+    const int se = (p - kstart) & 1, sh = (i - kstart) & 1;
+    // the next iteration's register inputs and the activity word four planes on, early
+    Q4 hxn_in = zero, hyn_in = zero, exn_in = zero, eyn_in = zero;
+    unsigned mn = 0u;
+    if (i + 3 <= k1) {
+      hxn_in = load_if(a.in[kHX], i + 2, has(m[2], kHX));
+      hyn_in = load_if(a.in[kHY], i + 2, has(m[2], kHY));
+      exn_in = load_if(a.in[kEX], i + 3, has(m[3], kEX));
+      eyn_in = load_if(a.in[kEY], i + 3, has(m[3], kEY));
+      if (i + 4 <= k1) mn = word(i + 4);
+    }
+    // A warp none of whose quads carries a component in a plane (PEC rows of
+    // a tile at the pipe wall) computes nothing there: every value it would
+    // compute is zero (an entry without a field and its coefficients hold
+    // zero), so it writes zeros where its neighbours read them and keeps to
+    // the barriers and the ring.
+    const bool wtm = __any_sync(0xffffffffu, m[1] != 0u || line_q);
+    const bool wte = __any_sync(0xffffffffu, m[0] != 0u);
+    float cHX[4], cHY[4], cEZ[4], cEX[4], cEY[4], cHZ[4];
+    // ---- A: S1 of plane p (hx~, hy~: U1, U2) | S4 of plane i (ex~, ey~: U6, U7)
+    Q4 ez = zero, hxa = zero, hya = zero;
+    if (tm) {
+      if (wtm) {
+        const float* sez = &S.ez[se][0];
+        ez = lds4(sez + row * kSX + 4 * q);
+        const Q4 ezU = row + 1 < kSY ? lds4(sez + (row + 1) * kSX + 4 * q) : zero;
+        const float ezR = q + 1 < kQ ? sez[row * kSX + 4 * q + 4] : 0.f;
+        const Q4 c0 = lds4(&S.co[se][kHX][row][4 * q]), c1 = lds4(&S.co[se][kHY][row][4 * q]);
+        const Q4 c2 = lds4(&S.co[se][kEZ][row][4 * q]);
+#pragma unroll
+        for (int e = 0; e < 4; ++e) {
+          cHX[e] = c0.v[e];
+          cHY[e] = c1.v[e];
+          cEZ[e] = c2.v[e];
+        }
+#pragma unroll
+        for (int e = 0; e < 4; ++e) {
+          const float dey = eyC.v[e] - eyB.v[e], dex = exC.v[e] - exB.v[e];
+          const float ezx = e < 3 ? ez.v[e + 1] : ezR;
+          hxa.v[e] = hxc.v[e] + cHX[e] * (dey - (ezU.v[e] - ez.v[e]));   // U1
+          hya.v[e] = hyc.v[e] + cHY[e] * (-dex + (ezx - ez.v[e]));      // U2
+        }
+      }
+      sts4(&S.x1[row][4 * q], hxa);
+    }
+    Q4 hz = zero, exa = zero, eya = zero;
+    if (te) {
+      if (wte) {
+        const float* shz = &S.hz[sh][0];
+        hz = lds4(shz + row * kSX + 4 * q);
+        const Q4 hzD = row >= 1 ? lds4(shz + (row - 1) * kSX + 4 * q) : zero;
+        const float hzL = q >= 1 ? shz[row * kSX + 4 * q - 1] : 0.f;
+        const Q4 c0 = lds4(&S.co[sh][kEX][row][4 * q]), c1 = lds4(&S.co[sh][kEY][row][4 * q]);
+        const Q4 c2 = lds4(&S.co[sh][kHZ][row][4 * q]);
+#pragma unroll
+        for (int e = 0; e < 4; ++e) {
+          cEX[e] = c0.v[e];
+          cEY[e] = c1.v[e];
+          cHZ[e] = c2.v[e];
+        }
+#pragma unroll
+        for (int e = 0; e < 4; ++e) {
+          const float hzl = e > 0 ? hz.v[e - 1] : hzL;
+          exa.v[e] = exA.v[e] + cEX[e] * ((hyp.v[e] - hyn.v[e]) - (hzD.v[e] - hz.v[e]));   // U6
+          eya.v[e] = eyA.v[e] + cEY[e] * (-(hxp.v[e] - hxn.v[e]) + (hzl - hz.v[e]));       // U7
+        }
+      }
+      sts4(&S.x3[row][4 * q], exa);
+    }
+    __syncthreads();  // (1) the slots are read; hx~ and ex~ are out
+    if (i + 3 < k1) issue_ez(i + 3, m[3]);  // into the freed slots
+    if (i + 2 < k1) issue_hz(i + 2, m[2]);
+    cp_commit();
+    // ---- B: S2 of plane p (ez': U3 with the bunch current) | S5 of plane i (hz': U8)
+    Q4 ezn = zero;
+    if (tm) {
+      if (wtm) {
+        const Q4 hxaD = row >= 1 ? lds4(&S.x1[row - 1][4 * q]) : zero;
+        const float hyaL = left_of(hya.v[3], q);
+        float cur[4];
+#pragma unroll
+        for (int e = 0; e < 4; ++e) {
+          const float hyl = e > 0 ? hya.v[e - 1] : hyaL;
+          cur[e] = (hxaD.v[e] - hxa.v[e]) - (hyl - hya.v[e]);
+        }
+        if (line_q) {  // the bunch current on its line (one quad of a tile row)
+          const long long dd = (long long)p - (a.n + a.b.kshift) + a.b.c0;
+          if (dd >= -a.b.c0 && dd < a.b.c0) {
+            const float jj = a.b.J[dd + a.b.c0];
+#pragma unroll
+            for (int e = 0; e < 4; ++e)
+              if (gi + e == a.b.i0) cur[e] -= jj;
+          }
+        }
+#pragma unroll
+        for (int e = 0; e < 4; ++e) ezn.v[e] = ez.v[e] + cEZ[e] * cur[e];   // U3
+      }
+      sts4(&S.x2[row][4 * q], ezn);
+    }
+    Q4 hzn = zero;
+    if (te) {
+      if (wte) {
+        const Q4 exaU = row + 1 < kSY ? lds4(&S.x3[row + 1][4 * q]) : zero;
+        const float eyaR = right_of(eya.v[0], q);
+#pragma unroll
+        for (int e = 0; e < 4; ++e) {
+          const float eyx = e < 3 ? eya.v[e + 1] : eyaR;
+          hzn.v[e] = hz.v[e] + cHZ[e] * ((exaU.v[e] - exa.v[e]) - (eyx - eya.v[e]));      // U8
+        }
+      }
+      sts4(&S.x4[row][4 * q], hzn);
+    }
+    cp_wait<1>();     // this thread's copies issued one iteration ago are in
+    __syncthreads();  // (2) ez' and hz' are out (and the slots the next A reads are in)
+    // ---- C: S3 of plane p (hx', hy': U4, U5) | S6 of plane i (ex', ey': U9, U10)
+    // (hx~, ez', ex~, hz' of the thread's own quad come back from the
+    // exchange buffers rather than stay in registers across the barrier)
+    Q4 hxN = zero, hyN = zero;
+    if (tm && wtm) {
+      const Q4 hxa2 = lds4(&S.x1[row][4 * q]);
+      const Q4 ezn2 = lds4(&S.x2[row][4 * q]);
+      const Q4 eznU = row + 1 < kSY ? lds4(&S.x2[row + 1][4 * q]) : zero;
+      const float eznR = right_of(ezn2.v[0], q);
+#pragma unroll
+      for (int e = 0; e < 4; ++e) {
+        const float dey = eyC.v[e] - eyB.v[e], dex = exC.v[e] - exB.v[e];
+        const float ezx = e < 3 ? ezn2.v[e + 1] : eznR;
+        hxN.v[e] = hxa2.v[e] + cHX[e] * (dey - (eznU.v[e] - ezn2.v[e]));  // U4
+        hyN.v[e] = hya.v[e] + cHY[e] * (-dex + (ezx - ezn2.v[e]));      // U5
+      }
+      const bool st = p >= k0 && own_q;
+      st4_if(a.out[kEZ] + gidx(p), ezn2, st && has(m[1], kEZ));
+      st4_if(a.out[kHX] + gidx(p), hxN, st && has(m[1], kHX));
+      st4_if(a.out[kHY] + gidx(p), hyN, st && has(m[1], kHY));
+      if (st && line_q && a.b.i0 < L.nx) {
+        const long long mm = (a.n + a.b.kshift) - p - a.b.c0;
+        if (mm >= a.b.m_min && mm <= a.b.m_max) {
+          const int e = a.b.i0 - gi;  // the quad's entry on the bunch line (no indexed register array)
+          const float v = e == 0 ? ezn2.v[0] : e == 1 ? ezn2.v[1] : e == 2 ? ezn2.v[2] : ezn2.v[3];
+          a.b.W[mm - a.b.m_min] -= (double)v * a.b.inv_q;
+        }
+      }
+    }
+    if (te && wte) {
+      const Q4 exa2 = lds4(&S.x3[row][4 * q]);
+      const Q4 hzn2 = lds4(&S.x4[row][4 * q]);
+      const Q4 hznD = row >= 1 ? lds4(&S.x4[row - 1][4 * q]) : zero;
+      const float hznL = left_of(hzn2.v[3], q);
+      Q4 exn, eyn;
+#pragma unroll
+      for (int e = 0; e < 4; ++e) {
+        const float hzl = e > 0 ? hzn2.v[e - 1] : hznL;
+        exn.v[e] = exa2.v[e] + cEX[e] * ((hyp.v[e] - hyn.v[e]) - (hznD.v[e] - hzn2.v[e]));   // U9
+        eyn.v[e] = eya.v[e] + cEY[e] * (-(hxp.v[e] - hxn.v[e]) + (hzl - hzn2.v[e]));       // U10
+      }
+      const bool st = own_q;
+      st4_if(a.out[kEX] + gidx(i), exn, st && has(m[0], kEX));
+      st4_if(a.out[kEY] + gidx(i), eyn, st && has(m[0], kEY));
+      st4_if(a.out[kHZ] + gidx(i), hzn2, st && has(m[0], kHZ));
+    }
+    // carry the z-state, take the loads made for the next iteration
+    hxp = hxn;
+    hyp = hyn;
+    hxn = hxN;
+    hyn = hyN;
+    exA = exB;
+    eyA = eyB;
+    exB = exC;
+    eyB = eyC;
+    exC = exn_in;
+    eyC = eyn_in;
+    hxc = hxn_in;
+    hyc = hyn_in;
+    m[0] = m[1];
+    m[1] = m[2];
+    m[2] = m[3];
+    m[3] = mn;
   }
   cp_wait<0>();
   __syncthreads();  // every thread is done with the ring before the next item refills it
@@ -374,7 +630,10 @@ __global__ void __launch_bounds__(kSThreads, 1) fused_step_slab(const StepArgs<f
   while (wi < nitems) {
     if (tid == 0 && sched) S.next[par] = G + atomicAdd(sched, 1);
     const int item = a.work ? a.work[wi] : wi;
-    slab_item<MAT>(a, item, S);
+    if constexpr (MAT)
+      slab_item_mat(a, item, S);
+    else
+      slab_item(a, item, S);
     wi = sched ? S.next[par] : wi + G;
     par ^= 1;
   }
@@ -407,7 +666,7 @@ fused_step_slab_batch(const BatchMember<float>* __restrict__ members, const int2
     const int2 w = work[wi];
     const BatchMember<float>& mb = members[w.x];
     if (mb.active) {
-      slab_item<false>(mb.a, w.y, S);
+      slab_item(mb.a, w.y, S);
     } else {
       // an item of a member past its limit: no work, but the ticket thread 0
       // wrote above must be visible before every thread reads it (slab_item
