@@ -104,24 +104,27 @@ template <int N>
 __device__ __forceinline__ void cp_wait() { asm volatile("cp.async.wait_group %0;" ::"n"(N) : "memory"); }
 // the quad's word holds one activity byte per node: component c of any node
 __device__ __forceinline__ bool has(unsigned m, int c) { return (m & (0x01010101u << c)) != 0u; }
+// the same as a word, nonzero where true (a predicate operand for the
+// accesses below, without a conversion from bool)
+__device__ __forceinline__ unsigned hw(unsigned m, int c) { return m & (0x01010101u << c); }
 
 struct Q4 {
   float v[4];
 };
 __device__ __forceinline__ Q4 q4(float4 a) { return Q4{{a.x, a.y, a.z, a.w}}; }
-__device__ __forceinline__ Q4 ld4_if(const float* p, bool c) {
+__device__ __forceinline__ Q4 ld4_if(const float* p, unsigned c) {
   Q4 r;
   asm volatile(
       "{\n .reg .pred q;\n setp.ne.u32 q, %5, 0;\n mov.f32 %0, 0f00000000;\n mov.f32 %1, 0f00000000;\n"
       " mov.f32 %2, 0f00000000;\n mov.f32 %3, 0f00000000;\n"
       " @q ld.global.nc.v4.f32 {%0,%1,%2,%3}, [%4];\n}"
       : "=f"(r.v[0]), "=f"(r.v[1]), "=f"(r.v[2]), "=f"(r.v[3])
-      : "l"(p), "r"((unsigned)c));
+      : "l"(p), "r"(c));
   return r;
 }
-__device__ __forceinline__ void st4_if(float* p, const Q4& v, bool c) {
+__device__ __forceinline__ void st4_if(float* p, const Q4& v, unsigned c) {
   asm volatile("{\n .reg .pred q;\n setp.ne.u32 q, %5, 0;\n @q st.global.v4.f32 [%0], {%1,%2,%3,%4};\n}" ::"l"(p),
-               "f"(v.v[0]), "f"(v.v[1]), "f"(v.v[2]), "f"(v.v[3]), "r"((unsigned)c)
+               "f"(v.v[0]), "f"(v.v[1]), "f"(v.v[2]), "f"(v.v[3]), "r"(c)
                : "memory");
 }
 __device__ __forceinline__ Q4 lds4(const float* p) { return q4(*reinterpret_cast<const float4*>(p)); }
@@ -170,7 +173,7 @@ __device__ __forceinline__ void slab_item(const StepArgs<float>& a, int item, Sl
   const bool own_q = q >= 1 && q <= kQ - 2 && row >= 2 && row < kSY - 2 && gj < L.ny;
   auto gidx = [&](int k) { return (long long)(k + 1) * SZ + qoff; };
   auto word = [&](int k) -> unsigned { return ld_word_if(a.co.mask + gidx(k), inq); };
-  auto load_if = [&](const float* base, int k, bool p) -> Q4 { return ld4_if(base + gidx(k), p); };
+  auto load_if = [&](const float* base, int k, unsigned p) -> Q4 { return ld4_if(base + gidx(k), p); };
   // plane k into its slot: each thread copies the quad of its own node row
   // and columns of e_z, h_z, only where one of the quad's nodes carries that
   // component (zeros otherwise: the entry holds zero), so the ring reads no
@@ -195,9 +198,9 @@ __device__ __forceinline__ void slab_item(const StepArgs<float>& a, int item, Sl
   }
   cp_wait<kSD - 1>();
   __syncthreads();  // plane kstart's slot is in
-  Q4 ex0 = load_if(a.in[kEX], kstart, has(m[0], kEX)), ey0 = load_if(a.in[kEY], kstart, has(m[0], kEY));
-  Q4 hxc = load_if(a.in[kHX], kstart, has(m[0], kHX)), hyc = load_if(a.in[kHY], kstart, has(m[0], kHY));
-  Q4 ex1 = load_if(a.in[kEX], kstart + 1, has(m[1], kEX)), ey1 = load_if(a.in[kEY], kstart + 1, has(m[1], kEY));
+  Q4 ex0 = load_if(a.in[kEX], kstart, hw(m[0], kEX)), ey0 = load_if(a.in[kEY], kstart, hw(m[0], kEY));
+  Q4 hxc = load_if(a.in[kHX], kstart, hw(m[0], kHX)), hyc = load_if(a.in[kHY], kstart, hw(m[0], kHY));
+  Q4 ex1 = load_if(a.in[kEX], kstart + 1, hw(m[1], kEX)), ey1 = load_if(a.in[kEY], kstart + 1, hw(m[1], kEY));
   Q4 hxp = zero, hyp = zero;
   const bool line_row = a.b.on && gj == a.b.j0;
   const bool line_q = line_row && a.b.i0 >= gi && a.b.i0 < gi + 4;  // the quad holds the bunch line node
@@ -209,10 +212,10 @@ __device__ __forceinline__ void slab_item(const StepArgs<float>& a, int item, Sl
     unsigned mn = 0u;
     const bool more = k + 1 < k1;
     if (more) {
-      hxn_in = load_if(a.in[kHX], k + 1, has(m[1], kHX));
-      hyn_in = load_if(a.in[kHY], k + 1, has(m[1], kHY));
-      exn_in = load_if(a.in[kEX], k + 2, has(m[2], kEX));
-      eyn_in = load_if(a.in[kEY], k + 2, has(m[2], kEY));
+      hxn_in = load_if(a.in[kHX], k + 1, hw(m[1], kHX));
+      hyn_in = load_if(a.in[kHY], k + 1, hw(m[1], kHY));
+      exn_in = load_if(a.in[kEX], k + 2, hw(m[2], kEX));
+      eyn_in = load_if(a.in[kEY], k + 2, hw(m[2], kEY));
       if (k + kSD + 1 <= k1) mn = word(k + kSD + 1);
     }
     // slot inputs: e_z, h_z of this quad and its neighbours
@@ -283,9 +286,10 @@ __device__ __forceinline__ void slab_item(const StepArgs<float>& a, int item, Sl
       hyn.v[e] = hya.v[e] + cHY[e] * (-dex[e] + (ezx - ezn.v[e]));     // U5
     }
     const bool st = k >= k0 && own_q;
-    st4_if(a.out[kEZ] + gidx(k), ezn, st && has(m[0], kEZ));
-    st4_if(a.out[kHX] + gidx(k), hxn, st && has(m[0], kHX));
-    st4_if(a.out[kHY] + gidx(k), hyn, st && has(m[0], kHY));
+    const unsigned ms = st ? m[0] : 0u;  // the plane's word where this thread stores
+    st4_if(a.out[kEZ] + gidx(k), ezn, hw(ms, kEZ));
+    st4_if(a.out[kHX] + gidx(k), hxn, hw(ms, kHX));
+    st4_if(a.out[kHY] + gidx(k), hyn, hw(ms, kHY));
     if (st) {
       if (line_q && a.b.i0 < L.nx) {
         const long long mm = (a.n + a.b.kshift) - k - a.b.c0;
@@ -329,9 +333,9 @@ __device__ __forceinline__ void slab_item(const StepArgs<float>& a, int item, Sl
       exn.v[e] = exa.v[e] + cEX[e] * ((hyp.v[e] - hyn.v[e]) - (hznD.v[e] - hzn.v[e]));   // U9
       eyn.v[e] = eya.v[e] + cEY[e] * (-(hxp.v[e] - hxn.v[e]) + (hzl - hzn.v[e]));       // U10
     }
-    st4_if(a.out[kEX] + gidx(k), exn, st && has(m[0], kEX));
-    st4_if(a.out[kEY] + gidx(k), eyn, st && has(m[0], kEY));
-    st4_if(a.out[kHZ] + gidx(k), hzn, st && has(m[0], kHZ));
+    st4_if(a.out[kEX] + gidx(k), exn, hw(ms, kEX));
+    st4_if(a.out[kEY] + gidx(k), eyn, hw(ms, kEY));
+    st4_if(a.out[kHZ] + gidx(k), hzn, hw(ms, kHZ));
     // carry the z-state, take the prefetched inputs
     hxp = hxn;
     hyp = hyn;
@@ -379,7 +383,7 @@ __device__ __forceinline__ void slab_item_mat(const StepArgs<float>& a, int item
   const bool own_q = q >= 1 && q <= kQ - 2 && row >= 2 && row < kSY - 2 && gj < L.ny;
   auto gidx = [&](int k) { return (long long)(k + 1) * SZ + qoff; };
   auto word = [&](int k) -> unsigned { return ld_word_if(a.co.mask + gidx(k), inq); };
-  auto load_if = [&](const float* base, int k, bool p) -> Q4 { return ld4_if(base + gidx(k), p); };
+  auto load_if = [&](const float* base, int k, unsigned p) -> Q4 { return ld4_if(base + gidx(k), p); };
   // e_z of plane k with the coefficient arrays of h_x, h_y, e_z (the TM
   // half), h_z of plane k with those of e_x, e_y, h_z (the TE half), into
   // their slots: each thread copies the quads of its own
@@ -418,9 +422,9 @@ __device__ __forceinline__ void slab_item_mat(const StepArgs<float>& a, int item
   if (kstart + 1 < k1) issue_ez(kstart + 1, m[2]);
   cp_commit();
   Q4 exA = zero, eyA = zero;
-  Q4 exB = load_if(a.in[kEX], kstart, has(m[1], kEX)), eyB = load_if(a.in[kEY], kstart, has(m[1], kEY));
-  Q4 exC = load_if(a.in[kEX], kstart + 1, has(m[2], kEX)), eyC = load_if(a.in[kEY], kstart + 1, has(m[2], kEY));
-  Q4 hxc = load_if(a.in[kHX], kstart, has(m[1], kHX)), hyc = load_if(a.in[kHY], kstart, has(m[1], kHY));
+  Q4 exB = load_if(a.in[kEX], kstart, hw(m[1], kEX)), eyB = load_if(a.in[kEY], kstart, hw(m[1], kEY));
+  Q4 exC = load_if(a.in[kEX], kstart + 1, hw(m[2], kEX)), eyC = load_if(a.in[kEY], kstart + 1, hw(m[2], kEY));
+  Q4 hxc = load_if(a.in[kHX], kstart, hw(m[1], kHX)), hyc = load_if(a.in[kHY], kstart, hw(m[1], kHY));
   Q4 hxp = zero, hyp = zero, hxn = zero, hyn = zero;
   const bool line_row = a.b.on && gj == a.b.j0;
   const bool line_q = line_row && a.b.i0 >= gi && a.b.i0 < gi + 4;  // the quad holds the bunch line node
@@ -436,10 +440,10 @@ __device__ __forceinline__ void slab_item_mat(const StepArgs<float>& a, int item
     Q4 hxn_in = zero, hyn_in = zero, exn_in = zero, eyn_in = zero;
     unsigned mn = 0u;
     if (i + 3 <= k1) {
-      hxn_in = load_if(a.in[kHX], i + 2, has(m[2], kHX));
-      hyn_in = load_if(a.in[kHY], i + 2, has(m[2], kHY));
-      exn_in = load_if(a.in[kEX], i + 3, has(m[3], kEX));
-      eyn_in = load_if(a.in[kEY], i + 3, has(m[3], kEY));
+      hxn_in = load_if(a.in[kHX], i + 2, hw(m[2], kHX));
+      hyn_in = load_if(a.in[kHY], i + 2, hw(m[2], kHY));
+      exn_in = load_if(a.in[kEX], i + 3, hw(m[3], kEX));
+      eyn_in = load_if(a.in[kEY], i + 3, hw(m[3], kEY));
       if (i + 4 <= k1) mn = word(i + 4);
     }
     // A warp none of whose quads carries a component in a plane (PEC rows of
@@ -562,9 +566,10 @@ __device__ __forceinline__ void slab_item_mat(const StepArgs<float>& a, int item
         hyN.v[e] = hya.v[e] + cHY[e] * (-dex + (ezx - ezn2.v[e]));      // U5
       }
       const bool st = p >= k0 && own_q;
-      st4_if(a.out[kEZ] + gidx(p), ezn2, st && has(m[1], kEZ));
-      st4_if(a.out[kHX] + gidx(p), hxN, st && has(m[1], kHX));
-      st4_if(a.out[kHY] + gidx(p), hyN, st && has(m[1], kHY));
+      const unsigned ms = st ? m[1] : 0u;
+      st4_if(a.out[kEZ] + gidx(p), ezn2, hw(ms, kEZ));
+      st4_if(a.out[kHX] + gidx(p), hxN, hw(ms, kHX));
+      st4_if(a.out[kHY] + gidx(p), hyN, hw(ms, kHY));
       if (st && line_q && a.b.i0 < L.nx) {
         const long long mm = (a.n + a.b.kshift) - p - a.b.c0;
         if (mm >= a.b.m_min && mm <= a.b.m_max) {
@@ -586,10 +591,10 @@ __device__ __forceinline__ void slab_item_mat(const StepArgs<float>& a, int item
         exn.v[e] = exa2.v[e] + cEX[e] * ((hyp.v[e] - hyn.v[e]) - (hznD.v[e] - hzn2.v[e]));   // U9
         eyn.v[e] = eya.v[e] + cEY[e] * (-(hxp.v[e] - hxn.v[e]) + (hzl - hzn2.v[e]));       // U10
       }
-      const bool st = own_q;
-      st4_if(a.out[kEX] + gidx(i), exn, st && has(m[0], kEX));
-      st4_if(a.out[kEY] + gidx(i), eyn, st && has(m[0], kEY));
-      st4_if(a.out[kHZ] + gidx(i), hzn2, st && has(m[0], kHZ));
+      const unsigned ms = own_q ? m[0] : 0u;
+      st4_if(a.out[kEX] + gidx(i), exn, hw(ms, kEX));
+      st4_if(a.out[kEY] + gidx(i), eyn, hw(ms, kEY));
+      st4_if(a.out[kHZ] + gidx(i), hzn2, hw(ms, kHZ));
     }
     // carry the z-state, take the loads made for the next iteration
     hxp = hxn;
