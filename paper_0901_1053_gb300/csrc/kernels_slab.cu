@@ -61,13 +61,18 @@ constexpr int kQ = kSX / 4;         // column quads per row
 constexpr int kSThreads = kQ * kSY; // 512
 
 // One material: a two-plane ring of e_z and h_z (one coefficient per
-// component, switched by the activity bytes).
+// component, switched by the activity bytes) and two exchange buffers, laid
+// out in one array with a spare row at the end, so that a read one row or
+// one column past a buffer's edge stays inside it (see slab_item).
 struct SlabSmemU {
-  static constexpr int SD = 2;      // planes in the ring (the next plane lands while this one is worked on)
-  float ez[SD][kSY * kSX];
-  float hz[SD][kSY * kSX];
-  float x1[kSY][kSX], x2[kSY][kSX];
-  int next[2];                      // the CTA's next work item (dynamic schedule)
+  static constexpr int SD = 2;             // planes in the ring (the next plane lands while this one is worked on)
+  static constexpr int kP = kSY * kSX;     // one box plane
+  float f[(2 * SD + 2) * kP + kSX];        // e_z slots, h_z slots, x1, x2, spare row
+  int next[2];                             // the CTA's next work item (dynamic schedule)
+  __device__ __forceinline__ float* ez(int s) { return f + s * kP; }
+  __device__ __forceinline__ float* hz(int s) { return f + (SD + s) * kP; }
+  __device__ __forceinline__ float* x1() { return f + 2 * SD * kP; }
+  __device__ __forceinline__ float* x2() { return f + (2 * SD + 1) * kP; }
 };
 // Material arrays: two-plane rings of e_z and h_z with the six per-entry
 // coefficient arrays (alpha M^-1, 2 alpha M^-1 for e_z and h_z), and the four
@@ -142,10 +147,22 @@ __device__ __forceinline__ float right_of(float v0, int q) {
   const float t = __shfl_down_sync(0xffffffffu, v0, 1);
   return q + 1 < kQ ? t : 0.f;
 }
+// the same without the edge test (the quads at the tile edge take a value of
+// the other half warp's row, which only halo nodes read)
+__device__ __forceinline__ float left_any(float v3) { return __shfl_up_sync(0xffffffffu, v3, 1); }
+__device__ __forceinline__ float right_any(float v0) { return __shfl_down_sync(0xffffffffu, v0, 1); }
 
 // One (tile, z-chunk) work item of solve a with one material (the ten
 // updates of every plane of the chunk, plane by plane: four block barriers
 // per plane).
+//
+// The reads of a neighbour one row or column outside the 64 x 32 box take
+// whatever the neighbouring shared-memory words or lanes hold, without an
+// edge test. Each of the six stages reaches one node sideways, and a value
+// computed from an outside neighbour is wrong only on the box's outermost
+// row or column; through the stages that error reaches at most two rows and
+// two columns in, all of them halo (the tile owns rows 2..29 and columns
+// 4..59 of the box), and halo nodes are never stored.
 __device__ __forceinline__ void slab_item(const StepArgs<float>& a, int item, SlabSmemU& S) {
   constexpr int kSD = SlabSmemU::SD;
   const int tid = threadIdx.x, q = tid % kQ, row = tid / kQ;
@@ -182,8 +199,8 @@ __device__ __forceinline__ void slab_item(const StepArgs<float>& a, int item, Sl
   auto issue_q = [&](int k, unsigned mw) {
     const int s = (k - kstart) % kSD;
     const long long g = inq ? gidx(k) : 0;
-    cp16_or_zero(&S.ez[s][row * kSX + 4 * q], a.in[kEZ] + g, has(mw, kEZ));
-    cp16_or_zero(&S.hz[s][row * kSX + 4 * q], a.in[kHZ] + g, has(mw, kHZ));
+    cp16_or_zero(S.ez(s) + row * kSX + 4 * q, a.in[kEZ] + g, has(mw, kEZ));
+    cp16_or_zero(S.hz(s) + row * kSX + 4 * q, a.in[kHZ] + g, has(mw, kHZ));
   };
   // activity words of planes k .. k + kSD (m[0] of the plane being worked
   // on; m[kSD] of the plane whose copy is issued next); z-state and the
@@ -219,14 +236,16 @@ __device__ __forceinline__ void slab_item(const StepArgs<float>& a, int item, Sl
       if (k + kSD + 1 <= k1) mn = word(k + kSD + 1);
     }
     // slot inputs: e_z, h_z of this quad and its neighbours
-    const float* sez = &S.ez[s][0];
-    const float* shz = &S.hz[s][0];
-    const Q4 ez = lds4(sez + row * kSX + 4 * q);
-    const Q4 ezU = row + 1 < kSY ? lds4(sez + (row + 1) * kSX + 4 * q) : zero;
-    const float ezR = q + 1 < kQ ? sez[row * kSX + 4 * q + 4] : 0.f;
-    const Q4 hz = lds4(shz + row * kSX + 4 * q);
-    const Q4 hzD = row >= 1 ? lds4(shz + (row - 1) * kSX + 4 * q) : zero;
-    const float hzL = q >= 1 ? shz[row * kSX + 4 * q - 1] : 0.f;
+    const float* sez = S.ez(s) + row * kSX + 4 * q;
+    const float* shz = S.hz(s) + row * kSX + 4 * q;
+    const Q4 ez = lds4(sez);
+    const Q4 ezU = lds4(sez + kSX);
+    const float ezR = sez[4];
+    const Q4 hz = lds4(shz);
+    const Q4 hzD = lds4(shz - kSX);
+    const float hzL = shz[-1];
+    float* const x1 = S.x1() + row * kSX + 4 * q;  // this thread's quad in the exchange buffers
+    float* const x2 = S.x2() + row * kSX + 4 * q;
     // one coefficient per component, switched by the activity bytes
     float cHX[4], cHY[4], cEZ[4], cEX[4], cEY[4], cHZ[4], dey[4], dex[4];
 #pragma unroll
@@ -248,13 +267,13 @@ __device__ __forceinline__ void slab_item(const StepArgs<float>& a, int item, Sl
       hxa.v[e] = hxc.v[e] + cHX[e] * (dey[e] - (ezU.v[e] - ez.v[e]));   // U1
       hya.v[e] = hyc.v[e] + cHY[e] * (-dex[e] + (ezx - ez.v[e]));      // U2
     }
-    sts4(&S.x1[row][4 * q], hxa);
+    sts4(x1, hxa);
     __syncthreads();  // (1) the slot is read and hx~ is out
     if (k + kSD < k1) issue_q(k + kSD, m[kSD]);  // into the freed slot
     cp_commit();
     // S2: ez' = ez + 2a M^-1 (P_y^T hx~ - P_x^T hy~ - jj_z)
-    const Q4 hxaD = row >= 1 ? lds4(&S.x1[row - 1][4 * q]) : zero;
-    const float hyaL = left_of(hya.v[3], q);
+    const Q4 hxaD = lds4(x1 - kSX);
+    const float hyaL = left_any(hya.v[3]);
     float cur[4];
 #pragma unroll
     for (int e = 0; e < 4; ++e) {
@@ -273,11 +292,11 @@ __device__ __forceinline__ void slab_item(const StepArgs<float>& a, int item, Sl
     Q4 ezn;
 #pragma unroll
     for (int e = 0; e < 4; ++e) ezn.v[e] = ez.v[e] + cEZ[e] * cur[e];   // U3
-    sts4(&S.x2[row][4 * q], ezn);
+    sts4(x2, ezn);
     __syncthreads();  // (2)
     // S3: hx', hy'
-    const Q4 eznU = row + 1 < kSY ? lds4(&S.x2[row + 1][4 * q]) : zero;
-    const float eznR = right_of(ezn.v[0], q);
+    const Q4 eznU = lds4(x2 + kSX);
+    const float eznR = right_any(ezn.v[0]);
     Q4 hxn, hyn;
 #pragma unroll
     for (int e = 0; e < 4; ++e) {
@@ -309,23 +328,23 @@ __device__ __forceinline__ void slab_item(const StepArgs<float>& a, int item, Sl
       exa.v[e] = ex0.v[e] + cEX[e] * ((hyp.v[e] - hyn.v[e]) - (hzD.v[e] - hz.v[e]));   // U6
       eya.v[e] = ey0.v[e] + cEY[e] * (-(hxp.v[e] - hxn.v[e]) + (hzl - hz.v[e]));       // U7
     }
-    sts4(&S.x1[row][4 * q], exa);
+    sts4(x1, exa);
     __syncthreads();  // (3)
     // S5: hz'
-    const Q4 exaU = row + 1 < kSY ? lds4(&S.x1[row + 1][4 * q]) : zero;
-    const float eyaR = right_of(eya.v[0], q);
+    const Q4 exaU = lds4(x1 + kSX);
+    const float eyaR = right_any(eya.v[0]);
     Q4 hzn;
 #pragma unroll
     for (int e = 0; e < 4; ++e) {
       const float eyx = e < 3 ? eya.v[e + 1] : eyaR;
       hzn.v[e] = hz.v[e] + cHZ[e] * ((exaU.v[e] - exa.v[e]) - (eyx - eya.v[e]));      // U8
     }
-    sts4(&S.x2[row][4 * q], hzn);
+    sts4(x2, hzn);
     cp_wait<kSD - 1>();  // this thread's copies of the next plane are in
     __syncthreads();  // (4) (and the next plane's slot is in)
     // S6: ex', ey'
-    const Q4 hznD = row >= 1 ? lds4(&S.x2[row - 1][4 * q]) : zero;
-    const float hznL = left_of(hzn.v[3], q);
+    const Q4 hznD = lds4(x2 - kSX);
+    const float hznL = left_any(hzn.v[3]);
     Q4 exn, eyn;
 #pragma unroll
     for (int e = 0; e < 4; ++e) {
