@@ -76,13 +76,16 @@ struct SlabSmemU {
 };
 // Material arrays: two-plane rings of e_z and h_z with the six per-entry
 // coefficient arrays (alpha M^-1, 2 alpha M^-1 for e_z and h_z), and the four
-// exchange buffers of the skewed sweep, 160 KB.
+// exchange buffers of the skewed sweep (hx~, ez', ex~, hz'), 160 KB, in one
+// array with a spare row at the end (reads past a buffer's edge stay inside).
 struct SlabSmemM {
-  float ez[2][kSY * kSX];
-  float hz[2][kSY * kSX];
-  float co[2][6][kSY][kSX];
-  float x1[kSY][kSX], x2[kSY][kSX], x3[kSY][kSX], x4[kSY][kSX];  // hx~, ez', ex~, hz'
+  static constexpr int kP = kSY * kSX;
+  float f[22 * kP + kSX];  // e_z slots, h_z slots, 2 x 6 coefficient planes, x1..x4, spare row
   int next[2];
+  __device__ __forceinline__ float* ez(int s) { return f + s * kP; }
+  __device__ __forceinline__ float* hz(int s) { return f + (2 + s) * kP; }
+  __device__ __forceinline__ float* co(int s, int c) { return f + (4 + 6 * s + c) * kP; }
+  __device__ __forceinline__ float* x(int b) { return f + (15 + b) * kP; }  // b = 1..4
 };
 template <bool MAT>
 using SlabSmem = typename std::conditional<MAT, SlabSmemM, SlabSmemU>::type;
@@ -138,17 +141,8 @@ __device__ __forceinline__ void sts4(float* p, const Q4& a) {
 }
 
 // the neighbouring quad's value one column left (x-1) or right (x+1) of this
-// quad, zero at the tile edge (lanes: one row per half warp)
-__device__ __forceinline__ float left_of(float v3, int q) {
-  const float t = __shfl_up_sync(0xffffffffu, v3, 1);
-  return q >= 1 ? t : 0.f;
-}
-__device__ __forceinline__ float right_of(float v0, int q) {
-  const float t = __shfl_down_sync(0xffffffffu, v0, 1);
-  return q + 1 < kQ ? t : 0.f;
-}
-// the same without the edge test (the quads at the tile edge take a value of
-// the other half warp's row, which only halo nodes read)
+// quad (lanes: one row per half warp); at the tile edge a lane takes a value
+// of the other half warp's row, which only halo nodes read
 __device__ __forceinline__ float left_any(float v3) { return __shfl_up_sync(0xffffffffu, v3, 1); }
 __device__ __forceinline__ float right_any(float v0) { return __shfl_down_sync(0xffffffffu, v0, 1); }
 
@@ -378,7 +372,8 @@ __device__ __forceinline__ void slab_item(const StepArgs<float>& a, int item, Sl
 // arrays, skewed by half a step: iteration i runs the TM half of plane i+1
 // (U1..U5, which reads only old fields) beside the TE half of plane i
 // (U6..U10, which reads the new h_x, h_y of planes i and i-1), two block
-// barriers per iteration.
+// barriers per iteration. Neighbour reads past the box edge go without edge
+// tests, as in slab_item (the two-node halo absorbs what they return).
 __device__ __forceinline__ void slab_item_mat(const StepArgs<float>& a, int item, SlabSmemM& S) {
   const int tid = threadIdx.x, q = tid % kQ, row = tid / kQ;
   const Layout L = a.L;
@@ -400,6 +395,11 @@ __device__ __forceinline__ void slab_item_mat(const StepArgs<float>& a, int item
   const bool inq = gj + 2 < L.ny + 4 && cx + 4 * q + 4 <= PX;  // the quad lies inside the arrays
   const long long qoff = (long long)(gj + 2) * PX + cx + 4 * q;
   const bool own_q = q >= 1 && q <= kQ - 2 && row >= 2 && row < kSY - 2 && gj < L.ny;
+  const int qo = row * kSX + 4 * q;  // this thread's quad in a box plane
+  float* const x1 = S.x(1) + qo;     // and in the exchange buffers
+  float* const x2 = S.x(2) + qo;
+  float* const x3 = S.x(3) + qo;
+  float* const x4 = S.x(4) + qo;
   auto gidx = [&](int k) { return (long long)(k + 1) * SZ + qoff; };
   auto word = [&](int k) -> unsigned { return ld_word_if(a.co.mask + gidx(k), inq); };
   auto load_if = [&](const float* base, int k, unsigned p) -> Q4 { return ld4_if(base + gidx(k), p); };
@@ -413,18 +413,20 @@ __device__ __forceinline__ void slab_item_mat(const StepArgs<float>& a, int item
   auto issue_ez = [&](int k, unsigned mw) {
     const int s = (k - kstart) & 1;
     const long long g = inq ? gidx(k) : 0;
-    cp16_or_zero(&S.ez[s][row * kSX + 4 * q], a.in[kEZ] + g, has(mw, kEZ));
-    cp16_or_zero(&S.co[s][kHX][row][4 * q], a.co.ua[kHX] + g, has(mw, kHX));
-    cp16_or_zero(&S.co[s][kHY][row][4 * q], a.co.ua[kHY] + g, has(mw, kHY));
-    cp16_or_zero(&S.co[s][kEZ][row][4 * q], a.co.ua[kEZ] + g, has(mw, kEZ));
+    const int o = row * kSX + 4 * q;
+    cp16_or_zero(S.ez(s) + o, a.in[kEZ] + g, has(mw, kEZ));
+    cp16_or_zero(S.co(s, kHX) + o, a.co.ua[kHX] + g, has(mw, kHX));
+    cp16_or_zero(S.co(s, kHY) + o, a.co.ua[kHY] + g, has(mw, kHY));
+    cp16_or_zero(S.co(s, kEZ) + o, a.co.ua[kEZ] + g, has(mw, kEZ));
   };
   auto issue_hz = [&](int k, unsigned mw) {
     const int s = (k - kstart) & 1;
     const long long g = inq ? gidx(k) : 0;
-    cp16_or_zero(&S.hz[s][row * kSX + 4 * q], a.in[kHZ] + g, has(mw, kHZ));
-    cp16_or_zero(&S.co[s][kEX][row][4 * q], a.co.ua[kEX] + g, has(mw, kEX));
-    cp16_or_zero(&S.co[s][kEY][row][4 * q], a.co.ua[kEY] + g, has(mw, kEY));
-    cp16_or_zero(&S.co[s][kHZ][row][4 * q], a.co.ua[kHZ] + g, has(mw, kHZ));
+    const int o = row * kSX + 4 * q;
+    cp16_or_zero(S.hz(s) + o, a.in[kHZ] + g, has(mw, kHZ));
+    cp16_or_zero(S.co(s, kEX) + o, a.co.ua[kEX] + g, has(mw, kEX));
+    cp16_or_zero(S.co(s, kEY) + o, a.co.ua[kEY] + g, has(mw, kEY));
+    cp16_or_zero(S.co(s, kHZ) + o, a.co.ua[kHZ] + g, has(mw, kHZ));
   };
   // Iteration i works on the TM half of plane i+1 and the TE half of plane
   // i; m[j] is the activity word of plane i + j. The ring holds e_z of
@@ -477,12 +479,12 @@ __device__ __forceinline__ void slab_item_mat(const StepArgs<float>& a, int item
     Q4 ez = zero, hxa = zero, hya = zero;
     if (tm) {
       if (wtm) {
-        const float* sez = &S.ez[se][0];
-        ez = lds4(sez + row * kSX + 4 * q);
-        const Q4 ezU = row + 1 < kSY ? lds4(sez + (row + 1) * kSX + 4 * q) : zero;
-        const float ezR = q + 1 < kQ ? sez[row * kSX + 4 * q + 4] : 0.f;
-        const Q4 c0 = lds4(&S.co[se][kHX][row][4 * q]), c1 = lds4(&S.co[se][kHY][row][4 * q]);
-        const Q4 c2 = lds4(&S.co[se][kEZ][row][4 * q]);
+        const float* sez = S.ez(se) + qo;
+        ez = lds4(sez);
+        const Q4 ezU = lds4(sez + kSX);
+        const float ezR = sez[4];
+        const Q4 c0 = lds4(S.co(se, kHX) + qo), c1 = lds4(S.co(se, kHY) + qo);
+        const Q4 c2 = lds4(S.co(se, kEZ) + qo);
 #pragma unroll
         for (int e = 0; e < 4; ++e) {
           cHX[e] = c0.v[e];
@@ -497,17 +499,17 @@ __device__ __forceinline__ void slab_item_mat(const StepArgs<float>& a, int item
           hya.v[e] = hyc.v[e] + cHY[e] * (-dex + (ezx - ez.v[e]));      // U2
         }
       }
-      sts4(&S.x1[row][4 * q], hxa);
+      sts4(x1, hxa);
     }
     Q4 hz = zero, exa = zero, eya = zero;
     if (te) {
       if (wte) {
-        const float* shz = &S.hz[sh][0];
-        hz = lds4(shz + row * kSX + 4 * q);
-        const Q4 hzD = row >= 1 ? lds4(shz + (row - 1) * kSX + 4 * q) : zero;
-        const float hzL = q >= 1 ? shz[row * kSX + 4 * q - 1] : 0.f;
-        const Q4 c0 = lds4(&S.co[sh][kEX][row][4 * q]), c1 = lds4(&S.co[sh][kEY][row][4 * q]);
-        const Q4 c2 = lds4(&S.co[sh][kHZ][row][4 * q]);
+        const float* shz = S.hz(sh) + qo;
+        hz = lds4(shz);
+        const Q4 hzD = lds4(shz - kSX);
+        const float hzL = shz[-1];
+        const Q4 c0 = lds4(S.co(sh, kEX) + qo), c1 = lds4(S.co(sh, kEY) + qo);
+        const Q4 c2 = lds4(S.co(sh, kHZ) + qo);
 #pragma unroll
         for (int e = 0; e < 4; ++e) {
           cEX[e] = c0.v[e];
@@ -521,7 +523,7 @@ __device__ __forceinline__ void slab_item_mat(const StepArgs<float>& a, int item
           eya.v[e] = eyA.v[e] + cEY[e] * (-(hxp.v[e] - hxn.v[e]) + (hzl - hz.v[e]));       // U7
         }
       }
-      sts4(&S.x3[row][4 * q], exa);
+      sts4(x3, exa);
     }
     __syncthreads();  // (1) the slots are read; hx~ and ex~ are out
     if (i + 3 < k1) issue_ez(i + 3, m[3]);  // into the freed slots
@@ -531,8 +533,8 @@ __device__ __forceinline__ void slab_item_mat(const StepArgs<float>& a, int item
     Q4 ezn = zero;
     if (tm) {
       if (wtm) {
-        const Q4 hxaD = row >= 1 ? lds4(&S.x1[row - 1][4 * q]) : zero;
-        const float hyaL = left_of(hya.v[3], q);
+        const Q4 hxaD = lds4(x1 - kSX);
+        const float hyaL = left_any(hya.v[3]);
         float cur[4];
 #pragma unroll
         for (int e = 0; e < 4; ++e) {
@@ -551,20 +553,20 @@ __device__ __forceinline__ void slab_item_mat(const StepArgs<float>& a, int item
 #pragma unroll
         for (int e = 0; e < 4; ++e) ezn.v[e] = ez.v[e] + cEZ[e] * cur[e];   // U3
       }
-      sts4(&S.x2[row][4 * q], ezn);
+      sts4(x2, ezn);
     }
     Q4 hzn = zero;
     if (te) {
       if (wte) {
-        const Q4 exaU = row + 1 < kSY ? lds4(&S.x3[row + 1][4 * q]) : zero;
-        const float eyaR = right_of(eya.v[0], q);
+        const Q4 exaU = lds4(x3 + kSX);
+        const float eyaR = right_any(eya.v[0]);
 #pragma unroll
         for (int e = 0; e < 4; ++e) {
           const float eyx = e < 3 ? eya.v[e + 1] : eyaR;
           hzn.v[e] = hz.v[e] + cHZ[e] * ((exaU.v[e] - exa.v[e]) - (eyx - eya.v[e]));      // U8
         }
       }
-      sts4(&S.x4[row][4 * q], hzn);
+      sts4(x4, hzn);
     }
     cp_wait<1>();     // this thread's copies issued one iteration ago are in
     __syncthreads();  // (2) ez' and hz' are out (and the slots the next A reads are in)
@@ -573,10 +575,10 @@ __device__ __forceinline__ void slab_item_mat(const StepArgs<float>& a, int item
     // exchange buffers rather than stay in registers across the barrier)
     Q4 hxN = zero, hyN = zero;
     if (tm && wtm) {
-      const Q4 hxa2 = lds4(&S.x1[row][4 * q]);
-      const Q4 ezn2 = lds4(&S.x2[row][4 * q]);
-      const Q4 eznU = row + 1 < kSY ? lds4(&S.x2[row + 1][4 * q]) : zero;
-      const float eznR = right_of(ezn2.v[0], q);
+      const Q4 hxa2 = lds4(x1);
+      const Q4 ezn2 = lds4(x2);
+      const Q4 eznU = lds4(x2 + kSX);
+      const float eznR = right_any(ezn2.v[0]);
 #pragma unroll
       for (int e = 0; e < 4; ++e) {
         const float dey = eyC.v[e] - eyB.v[e], dex = exC.v[e] - exB.v[e];
@@ -599,10 +601,10 @@ __device__ __forceinline__ void slab_item_mat(const StepArgs<float>& a, int item
       }
     }
     if (te && wte) {
-      const Q4 exa2 = lds4(&S.x3[row][4 * q]);
-      const Q4 hzn2 = lds4(&S.x4[row][4 * q]);
-      const Q4 hznD = row >= 1 ? lds4(&S.x4[row - 1][4 * q]) : zero;
-      const float hznL = left_of(hzn2.v[3], q);
+      const Q4 exa2 = lds4(x3);
+      const Q4 hzn2 = lds4(x4);
+      const Q4 hznD = lds4(x4 - kSX);
+      const float hznL = left_any(hzn2.v[3]);
       Q4 exn, eyn;
 #pragma unroll
       for (int e = 0; e < 4; ++e) {
