@@ -36,6 +36,24 @@ __device__ double block_reduce(double v) {
   return v;
 }
 
+// binary32 -> binary64 widening on the integer pipe (IEEE 754: the
+// significand moves up by 29 bits and the exponent is rebiased by
+// 1023 - 127 = 896, or set to all ones for infinities and NaNs, which keep
+// their payload): exact for every normal value, zero, infinity and NaN.
+// Subnormal values (below 2^-126) become zero of the same sign; a field value
+// that small changes a balance term by less than 2^-126 of its normal
+// neighbours. On this part the float64 unit, which the conversion
+// instruction also occupies, is the balances' bottleneck.
+__device__ __forceinline__ double wide(float f) {
+  const unsigned u = __float_as_uint(f), a = u & 0x7FFFFFFFu;
+  const bool normal = a >= 0x00800000u;
+  const unsigned bias = a >= 0x7F800000u ? 0x70000000u : 0x38000000u;
+  const unsigned hi = (u & 0x80000000u) | (normal ? (a >> 3) + bias : 0u);
+  const unsigned lo = normal ? u << 29 : 0u;
+  return __hiloint2double((int)hi, (int)lo);
+}
+__device__ __forceinline__ double wide(double d) { return d; }
+
 struct MinvView {
   const uint8_t* mask;
   double c[6];          // M^-1 constants (uniform material)
@@ -97,16 +115,16 @@ __global__ void energy_items(const T* __restrict__ ex, const T* __restrict__ ey,
       const long long id = L.idx(i, j, k);
       const uint8_t m = mv.mask[id];
       if (m == 0) continue;  // no field object here: every term is zero
-      const double pyez = (double)ez[id + sy] - (double)ez[id];
-      const double pxez = (double)ez[id + sx] - (double)ez[id];
-      const double ptyhz = (double)hz[id - sy] - (double)hz[id];
-      const double ptxhz = (double)hz[id - sx] - (double)hz[id];
-      const double l = (double)hx[id] * ((double)ey[id + sz] - (double)ey[id]) -
-                       (double)hy[id] * ((double)ex[id + sz] - (double)ex[id]);
+      const double pyez = wide(ez[id + sy]) - wide(ez[id]);
+      const double pxez = wide(ez[id + sx]) - wide(ez[id]);
+      const double ptyhz = wide(hz[id - sy]) - wide(hz[id]);
+      const double ptxhz = wide(hz[id - sx]) - wide(hz[id]);
+      const double l = wide(hx[id]) * (wide(ey[id + sz]) - wide(ey[id])) -
+                       wide(hy[id]) * (wide(ex[id + sz]) - wide(ex[id]));
       if (uniform) {
         // inactive entries hold zero fields, so their squares add nothing
         for (int q = 0; q < 6; ++q) {
-          const double v = (double)f[q][id];
+          const double v = wide(f[q][id]);
           sq[q] += v * v;
         }
         if (m & 8) rq[0] += pyez * pyez;
@@ -117,7 +135,7 @@ __global__ void energy_items(const T* __restrict__ ex, const T* __restrict__ ey,
       } else {
         double w = 0.0;
         for (int q = 0; q < 6; ++q) {
-          const double v = (double)f[q][id];
+          const double v = wide(f[q][id]);
           w += 0.5 * v * v * mv.m(q, id);
         }
         const double r = mv(kHX, id) * pyez * pyez + mv(kHY, id) * pxez * pxez +
@@ -148,32 +166,32 @@ __global__ void reduce_pass2(const double* part, int n, double* out) {
 template <typename T>
 __device__ __forceinline__ double dbar(const T* f1, const T* f0, const MinvView& mv, int comp,
                                        long long e) {
-  return 0.5 * ((double)f1[e] + (double)f0[e]) * mv.m(comp, e);
+  return 0.5 * (wide(f1[e]) + wide(f0[e])) * mv.m(comp, e);
 }
 template <typename T>
 __device__ __forceinline__ double dz_tilde(const T* ez, const MinvView& mv, long long e,
                                            long long sx, long long sy, double a2) {
   const double mi = mv(kEZ, e);
   if (mi == 0.0) return 0.0;
-  auto t1 = [&](long long f) { return mv(kHX, f) * ((double)ez[f + sy] - (double)ez[f]); };
-  auto t2 = [&](long long f) { return mv(kHY, f) * ((double)ez[f + sx] - (double)ez[f]); };
+  auto t1 = [&](long long f) { return mv(kHX, f) * (wide(ez[f + sy]) - wide(ez[f])); };
+  auto t2 = [&](long long f) { return mv(kHY, f) * (wide(ez[f + sx]) - wide(ez[f])); };
   const double r = (t1(e - sy) - t1(e)) + (t2(e - sx) - t2(e));
-  return (double)ez[e] * mv.m(kEZ, e) - a2 * r;
+  return wide(ez[e]) * mv.m(kEZ, e) - a2 * r;
 }
 template <typename T>
 __device__ __forceinline__ double bbar(const T* f1, const T* f0, const MinvView& mv, int comp,
                                        long long f) {
-  return 0.5 * ((double)f1[f] + (double)f0[f]) * mv.m(comp, f);
+  return 0.5 * (wide(f1[f]) + wide(f0[f])) * mv.m(comp, f);
 }
 template <typename T>
 __device__ __forceinline__ double bz_tilde(const T* hz, const MinvView& mv, long long f,
                                            long long sx, long long sy, double a2) {
   const double mi = mv(kHZ, f);
   if (mi == 0.0) return 0.0;
-  auto t3 = [&](long long e) { return mv(kEX, e) * ((double)hz[e - sy] - (double)hz[e]); };
-  auto t4 = [&](long long e) { return mv(kEY, e) * ((double)hz[e - sx] - (double)hz[e]); };
+  auto t3 = [&](long long e) { return mv(kEX, e) * (wide(hz[e - sy]) - wide(hz[e])); };
+  auto t4 = [&](long long e) { return mv(kEY, e) * (wide(hz[e - sx]) - wide(hz[e])); };
   const double r = (t3(f + sy) - t3(f)) + (t4(f + sx) - t4(f));
-  return (double)hz[f] * mv.m(kHZ, f) - a2 * r;
+  return wide(hz[f]) * mv.m(kHZ, f) - a2 * r;
 }
 
 struct ChargeFields {
@@ -235,23 +253,6 @@ __global__ void charge_items(ChargeFields cf, MinvView mv, Layout L, WorkView wv
   }
 }
 
-// binary32 -> binary64 widening on the integer pipe (IEEE 754: the
-// significand moves up by 29 bits and the exponent is rebiased by
-// 1023 - 127 = 896, or set to all ones for infinities and NaNs, which keep
-// their payload): exact for every normal value, zero, infinity and NaN.
-// Subnormal values (below 2^-126) become zero of the same sign; a field value
-// that small changes a balance term by less than 2^-126 of its normal
-// neighbours. On this part the float64 unit, which the conversion
-// instruction also occupies, is the balances' bottleneck.
-__device__ __forceinline__ double wide(float f) {
-  const unsigned u = __float_as_uint(f), a = u & 0x7FFFFFFFu;
-  const bool normal = a >= 0x00800000u;
-  const unsigned bias = a >= 0x7F800000u ? 0x70000000u : 0x38000000u;
-  const unsigned hi = (u & 0x80000000u) | (normal ? (a >> 3) + bias : 0u);
-  const unsigned lo = normal ? u << 29 : 0u;
-  return __hiloint2double((int)hi, (int)lo);
-}
-__device__ __forceinline__ double wide(double d) { return d; }
 
 // One material (the vacuum case included): M^-1 and M = 1 / M^-1 per
 // component for the active entries, and the products the balances use.

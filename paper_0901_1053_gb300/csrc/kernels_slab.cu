@@ -80,12 +80,12 @@ struct SlabSmemU {
 // array with a spare row at the end (reads past a buffer's edge stay inside).
 struct SlabSmemM {
   static constexpr int kP = kSY * kSX;
-  float f[22 * kP + kSX];  // e_z slots, h_z slots, 2 x 6 coefficient planes, x1..x4, spare row
+  float f[20 * kP + kSX];  // e_z slots (2), h_z slots (2), 2 x 6 coefficient planes, x1..x4, spare row
   int next[2];
   __device__ __forceinline__ float* ez(int s) { return f + s * kP; }
   __device__ __forceinline__ float* hz(int s) { return f + (2 + s) * kP; }
   __device__ __forceinline__ float* co(int s, int c) { return f + (4 + 6 * s + c) * kP; }
-  __device__ __forceinline__ float* x(int b) { return f + (15 + b) * kP; }  // b = 1..4
+  __device__ __forceinline__ float* x(int b) { return f + (15 + b) * kP; }  // b = 1..4: planes 16..19
 };
 template <bool MAT>
 using SlabSmem = typename std::conditional<MAT, SlabSmemM, SlabSmemU>::type;
