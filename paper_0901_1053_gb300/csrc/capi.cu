@@ -145,6 +145,12 @@ __global__ void scale_coef(const double* minv, double s, long long n, T* out) {
   const long long q = (long long)blockIdx.x * blockDim.x + threadIdx.x;
   if (q < n) out[q] = (T)(s * minv[q]);
 }
+// M = 1/M^-1 per entry (0 where M^-1 is 0: an entry without a field), for the
+// balances, which would otherwise divide at every use
+__global__ void recip_coef(const double* minv, long long n, double* out) {
+  const long long q = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (q < n) out[q] = minv[q] != 0.0 ? 1.0 / minv[q] : 0.0;
+}
 
 // Canonical FIT layout <-> device layout, for planes [k0, k0 + nk).
 template <typename T>
@@ -425,11 +431,12 @@ int queue_balances(tetm_solver* s, double* rec) {
   CK(launch_bunch_charge(s->bunch ? s->q : 0.0, s->bunch ? s->sigma : 1.0, s->g.dz, zc, s->g.nz,
                          s->qline, rec + 4, (double)s->step, rec, s->stream));
   const T *cur[6], *prv[6];
-  const double* ma[6];
+  const double *ma[6], *mr[6];
   for (int c = 0; c < 6; ++c) {
     cur[c] = (const T*)s->set[s->cur][c];
     prv[c] = (const T*)s->set[1 - s->cur][c];
     ma[c] = s->minv_a[c];
+    mr[c] = s->m_a[c];
   }
   const WorkView wv = work_view(s);
   if (s->uniform) {  // one pass for both
@@ -437,8 +444,8 @@ int queue_balances(tetm_solver* s, double* rec) {
                           s->j0, wv, s->diag, rec + 1, rec + 2, rec + 3, s->stream));
     return TETM_OK;
   }
-  CK(launch_energy<T>(cur, s->mask, s->minv_c, ma, s->L, s->alpha, wv, s->diag, rec + 1, s->stream));
-  CK(launch_charge<T>(cur, prv, s->mask, s->minv_c, ma, s->L, s->alpha,
+  CK(launch_energy<T>(cur, s->mask, s->minv_c, ma, mr, s->L, s->alpha, wv, s->diag, rec + 1, s->stream));
+  CK(launch_charge<T>(cur, prv, s->mask, s->minv_c, ma, mr, s->L, s->alpha,
                       s->bunch ? s->qline : nullptr, s->i0, s->j0, wv, s->diag, rec + 2, rec + 3,
                       s->stream));
   return TETM_OK;
@@ -576,6 +583,7 @@ void free_all(tetm_solver* s) {
     for (int c = 0; c < 6; ++c) dev_free(s->set[b][c], st);
   for (int c = 0; c < 6; ++c) {
     dev_free(s->minv_a[c], st);
+    dev_free(s->m_a[c], st);
     dev_free(s->ua[c], st);
   }
   dev_free(s->mask, st);
@@ -744,9 +752,11 @@ int create_impl(const tetm_grid* g, int k_lo, int nz_all, const double* eps_r, c
   if (rc == TETM_OK && !uniform) {
     for (int c = 0; c < 6 && rc == TETM_OK; ++c) {
       rc = dalloc(s, &s->ua[c], (size_t)s->L.count * s->esz);
+      if (rc == TETM_OK) rc = dalloc(s, (void**)&s->m_a[c], sizeof(double) * (size_t)s->L.count);
       if (rc != TETM_OK) break;
       const double sc = (c == kEZ || c == kHZ) ? 2.0 * s->alpha : s->alpha;
       const unsigned nb = (unsigned)((s->L.count + 255) / 256);
+      recip_coef<<<nb, 256, 0, s->stream>>>(s->minv_a[c], s->L.count, s->m_a[c]);
       if (s->esz == 8)
         scale_coef<double><<<nb, 256, 0, s->stream>>>(s->minv_a[c], sc, s->L.count, (double*)s->ua[c]);
       else
@@ -1018,22 +1028,25 @@ int tetm_transverse_wake(tetm_solver* s, double* wx, double* wy, int32_t cap, in
 int tetm_energy(tetm_solver* s, double* w) {
   if (!s || !w) return TETM_E_ARG;
   if (s->scheme != TETM_SCHEME_TETM) return TETM_E_UNSUPPORTED;
-  const double* ma[6];
-  for (int c = 0; c < 6; ++c) ma[c] = s->minv_a[c];
+  const double *ma[6], *mr[6];
+  for (int c = 0; c < 6; ++c) {
+    ma[c] = s->minv_a[c];
+    mr[c] = s->m_a[c];
+  }
   cudaError_t e;
   if (s->esz == 8) {
     const double* f[6];
     for (int c = 0; c < 6; ++c) f[c] = (const double*)s->set[s->cur][c];
     e = s->uniform ? launch_balances<double>(f, nullptr, s->mask, s->minv_c, s->L, s->alpha, nullptr, 0, 0,
                                              work_view(s), s->diag, s->diag.out, nullptr, nullptr, s->stream)
-                   : launch_energy<double>(f, s->mask, s->minv_c, ma, s->L, s->alpha, work_view(s), s->diag,
+                   : launch_energy<double>(f, s->mask, s->minv_c, ma, mr, s->L, s->alpha, work_view(s), s->diag,
                                            s->diag.out, s->stream);
   } else {
     const float* f[6];
     for (int c = 0; c < 6; ++c) f[c] = (const float*)s->set[s->cur][c];
     e = s->uniform ? launch_balances<float>(f, nullptr, s->mask, s->minv_c, s->L, s->alpha, nullptr, 0, 0,
                                             work_view(s), s->diag, s->diag.out, nullptr, nullptr, s->stream)
-                   : launch_energy<float>(f, s->mask, s->minv_c, ma, s->L, s->alpha, work_view(s), s->diag,
+                   : launch_energy<float>(f, s->mask, s->minv_c, ma, mr, s->L, s->alpha, work_view(s), s->diag,
                                           s->diag.out, s->stream);
   }
   CK(e);

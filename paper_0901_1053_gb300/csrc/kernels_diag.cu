@@ -59,16 +59,14 @@ struct MinvView {
   double c[6];          // M^-1 constants (uniform material)
   double r[6];          // their reciprocals M = 1/M^-1
   const double* a[6];   // per-entry M^-1 (material runs) or nullptr
+  const double* ra[6];  // and per-entry M = 1/M^-1 (0 where M^-1 is 0), formed once per solve
   __device__ __forceinline__ double operator()(int comp, long long id) const {
     if (a[comp]) return a[comp][id];
     return ((mask[id] >> comp) & 1) ? c[comp] : 0.0;
   }
   // M = 1/M^-1 of an active entry (0 for inactive ones)
   __device__ __forceinline__ double m(int comp, long long id) const {
-    if (a[comp]) {
-      const double v = a[comp][id];
-      return v != 0.0 ? 1.0 / v : 0.0;
-    }
+    if (ra[comp]) return ra[comp][id];
     return ((mask[id] >> comp) & 1) ? r[comp] : 0.0;
   }
 };
@@ -641,13 +639,15 @@ int balance_threads(const WorkView& wv) {
   return ((area + rounds - 1) / rounds + 31) / 32 * 32;
 }
 
-MinvView make_view(const uint8_t* mask, const double* minv, const double* const minv_a[6]) {
+MinvView make_view(const uint8_t* mask, const double* minv, const double* const minv_a[6],
+                   const double* const m_a[6]) {
   MinvView v;
   v.mask = mask;
   for (int c = 0; c < 6; ++c) {
     v.c[c] = minv ? minv[c] : 0.0;
     v.r[c] = (minv && minv[c] != 0.0) ? 1.0 / minv[c] : 0.0;
     v.a[c] = minv_a ? minv_a[c] : nullptr;
+    v.ra[c] = m_a ? m_a[c] : nullptr;
   }
   return v;
 }
@@ -657,21 +657,22 @@ MinvView make_view(const uint8_t* mask, const double* minv, const double* const 
 
 template <typename T>
 cudaError_t launch_energy(const T* const f[6], const uint8_t* mask, const double* minv,
-                          const double* const minv_a[6], const Layout& L, double alpha,
+                          const double* const minv_a[6], const double* const m_a[6], const Layout& L, double alpha,
                           const WorkView& wv, const DiagScratch& s, double* result,
                           cudaStream_t st) {
   const int nb = wv.n_items;
   if (nb > s.cap) return cudaErrorInvalidValue;
   if (nb == 0) return cudaMemsetAsync(result, 0, sizeof(double), st);
   energy_items<T><<<nb, kBlock, 0, st>>>(f[0], f[1], f[2], f[3], f[4], f[5],
-                                          make_view(mask, minv, minv_a), L, wv, alpha, s.part);
+                                          make_view(mask, minv, minv_a, m_a), L, wv, alpha, s.part);
   reduce_pass2<false><<<1, 1024, 0, st>>>(s.part, nb, result);
   return cudaGetLastError();
 }
 
 template <typename T>
 cudaError_t launch_charge(const T* const cur[6], const T* const prev[6], const uint8_t* mask,
-                          const double* minv, const double* const minv_a[6], const Layout& L,
+                          const double* minv, const double* const minv_a[6], const double* const m_a[6],
+                          const Layout& L,
                           double alpha, const double* qline, int i0, int j0, const WorkView& wv,
                           const DiagScratch& s, double* res_e, double* res_h, cudaStream_t st) {
   const int nb = wv.n_items;
@@ -685,7 +686,7 @@ cudaError_t launch_charge(const T* const cur[6], const T* const prev[6], const u
     cf.cur[c] = cur[c];
     cf.prev[c] = prev[c];
   }
-  charge_items<T><<<nb, kBlock, 0, st>>>(cf, make_view(mask, minv, minv_a), L, wv, alpha, qline,
+  charge_items<T><<<nb, kBlock, 0, st>>>(cf, make_view(mask, minv, minv_a, m_a), L, wv, alpha, qline,
                                           i0, j0, s.part, s.part + nb);
   reduce_pass2<true><<<1, 1024, 0, st>>>(s.part, nb, res_e);
   reduce_pass2<true><<<1, 1024, 0, st>>>(s.part + nb, nb, res_h);
@@ -788,20 +789,20 @@ cudaError_t launch_bunch_charge(double q, double sigma, double dz, double zc, in
 }
 
 template cudaError_t launch_energy<float>(const float* const[6], const uint8_t*, const double*,
-                                          const double* const[6], const Layout&, double,
+                                          const double* const[6], const double* const[6], const Layout&, double,
                                           const WorkView&, const DiagScratch&, double*,
                                           cudaStream_t);
 template cudaError_t launch_energy<double>(const double* const[6], const uint8_t*, const double*,
-                                           const double* const[6], const Layout&, double,
+                                           const double* const[6], const double* const[6], const Layout&, double,
                                            const WorkView&, const DiagScratch&, double*,
                                            cudaStream_t);
 template cudaError_t launch_charge<float>(const float* const[6], const float* const[6],
-                                          const uint8_t*, const double*, const double* const[6],
+                                          const uint8_t*, const double*, const double* const[6], const double* const[6],
                                           const Layout&, double, const double*, int, int,
                                           const WorkView&, const DiagScratch&, double*, double*,
                                           cudaStream_t);
 template cudaError_t launch_charge<double>(const double* const[6], const double* const[6],
-                                           const uint8_t*, const double*, const double* const[6],
+                                           const uint8_t*, const double*, const double* const[6], const double* const[6],
                                            const Layout&, double, const double*, int, int,
                                            const WorkView&, const DiagScratch&, double*, double*,
                                            cudaStream_t);

@@ -184,10 +184,10 @@ struct WorkView {
 };
 
 // Discrete energy W^{n,e} into *result (device); minv[c] constants (mask
-// mode) or minv_a[c] arrays.
+// mode) or minv_a[c] arrays with their reciprocals m_a[c] (0 where minv_a is 0).
 template <typename T>
 cudaError_t launch_energy(const T* const f[6], const uint8_t* mask, const double* minv,
-                          const double* const minv_a[6], const Layout& L, double alpha,
+                          const double* const minv_a[6], const double* const m_a[6], const Layout& L, double alpha,
                           const WorkView& wv, const DiagScratch& s, double* result,
                           cudaStream_t st);
 
@@ -195,7 +195,8 @@ cudaError_t launch_energy(const T* const f[6], const uint8_t* mask, const double
 // *res_h = max|qh|.
 template <typename T>
 cudaError_t launch_charge(const T* const cur[6], const T* const prev[6], const uint8_t* mask,
-                          const double* minv, const double* const minv_a[6], const Layout& L,
+                          const double* minv, const double* const minv_a[6], const double* const m_a[6],
+                          const Layout& L,
                           double alpha, const double* qline, int i0, int j0, const WorkView& wv,
                           const DiagScratch& s, double* res_e, double* res_h, cudaStream_t st);
 
@@ -225,6 +226,7 @@ struct tetm_solver {
   uint8_t* mask;
   double minv_c[6];
   double* minv_a[6];
+  double* m_a[6];  // 1 / minv_a (0 where minv_a is 0), for the balances
   void* ua[6];
   bool uniform;
   bool vacuum;    // no material arrays (eps_r = mu_r = 1)
