@@ -18,7 +18,7 @@ import numpy as np
 
 Shape = Tuple[int, int, int]
 
-CANDIDATES_FP32: List[Shape] = [(56, 28, 32), (56, 28, 16), (56, 28, 64),
+CANDIDATES_FP32: List[Shape] = [(56, 28, 32), (56, 28, 16), (56, 28, 64), (56, 12, 32), (56, 12, 16),
                                 (28, 20, 32), (28, 20, 16), (28, 12, 32), (28, 12, 16),
                                 (28, 28, 32), (28, 8, 32), (28, 4, 32), (32, 8, 64)]
 CANDIDATES_FP64: List[Shape] = [(28, 20, 32), (28, 20, 16), (28, 12, 32), (28, 28, 32),
@@ -100,12 +100,13 @@ class Autotuner:
             s.close()
         return out
 
-    def wave_fitted(self, w, precision: str, tile_ys=(12, 20, 28), max_extra: int = 6):
+    def wave_fitted(self, w, precision: str, tile_ys=(12, 20, 28), max_extra: int = 6, eps_r=None):
         """Shapes (28, ty, cz) whose work-item count fills whole waves of the
         resident warps (16 per SM): for each tile height, the chunk lengths
         around the one that gives one or two full waves; in float32 also slab
-        shapes (56, 28, cz) whose items split evenly over the one CTA per SM
-        (4 to 8 items each)."""
+        shapes whose items split evenly over its CTAs (4 to 8 items each):
+        (56, 28, cz), one CTA per SM, or with the material array eps_r
+        (56, 12, cz), two CTAs per SM."""
         from . import tetm
         try:
             import torch
@@ -113,7 +114,7 @@ class Autotuner:
         except Exception:
             sms = 152
         slots = 16 * sms
-        s = tetm.Solver(w.nx, w.ny, w.nz, w.dx, w.dy, w.dz, w.cdt, precision, pec=w.pec)
+        s = tetm.Solver(w.nx, w.ny, w.nz, w.dx, w.dy, w.dz, w.cdt, precision, eps_r=eps_r, pec=w.pec)
         out = []
         try:
             for ty in tile_ys:
@@ -130,18 +131,19 @@ class Autotuner:
                             best = (eff, c)
                     out.append((28, ty, best[1]))
             if precision == "fp32":
-                s.set_tiling(56, 28, 32)
+                ty, ctas = (28, sms) if eps_r is None else (12, 2 * sms)
+                s.set_tiling(56, ty, 32)
                 items32 = s.info()["work_items"]
                 for rounds in range(4, 9):
-                    cz = max(4, int(round(32 * items32 / (rounds * sms))))
+                    cz = max(4, int(round(32 * items32 / (rounds * ctas))))
                     best = None
                     for c in range(max(4, cz - 4), cz + 5):
-                        s.set_tiling(56, 28, c)
+                        s.set_tiling(56, ty, c)
                         n = s.info()["work_items"]
-                        eff = n / (sms * -(-n // sms))
+                        eff = n / (ctas * -(-n // ctas))
                         if best is None or eff > best[0] + 1e-9:
                             best = (eff, c)
-                    out.append((56, 28, best[1]))
+                    out.append((56, ty, best[1]))
         finally:
             s.close()
         return sorted(set(out))
@@ -150,21 +152,23 @@ class Autotuner:
              candidates: Optional[Sequence[Shape]] = None, materials: bool = False, eps_r=None,
              batch: bool = False) -> Shape:
         """materials: the solve has eps/mu arrays (per-entry coefficients run on
-        the warp-tiled kernel, tile_x = 28, and the float32 slab kernel, 56 x 28);
+        the warp-tiled kernel, tile_x = 28, and the float32 slab kernel, 56 x 12);
         batch: the shape is for a batch of solves (batched launches run the
         warp-tiled kernel, tile_x = 28, and in float32 the slab kernel)."""
         precision = precision or w.precision
         materials = materials or eps_r is not None
-        k = self.key(w, precision) + ("|materials" if materials else "") + ("|batch" if batch else "")
+        k = self.key(w, precision) + ("|materials56x12" if materials else "") + ("|batch" if batch else "")
         if eps_r is not None:
             k += "|" + hashlib.sha1(memoryview(np.ascontiguousarray(eps_r)).tobytes()).hexdigest()[:16]
         if k in self.cache:
             return tuple(self.cache[k])
         cands = list(candidates or (CANDIDATES_FP32 if precision == "fp32" else CANDIDATES_FP64))
         if candidates is None:
-            cands += [c for c in self.wave_fitted(w, precision) if c not in cands]
+            cands += [c for c in self.wave_fitted(w, precision, eps_r=eps_r) if c not in cands]
         if materials:
-            cands = [c for c in cands if c[0] == 28 or (c[0], c[1]) == (56, 28)]
+            cands = [c for c in cands if c[0] == 28 or (c[0], c[1]) == (56, 12)]
+        else:
+            cands = [c for c in cands if (c[0], c[1]) != (56, 12)]
         if batch:
             cands = [c for c in cands if c[0] == 28 or (precision == "fp32" and (c[0], c[1]) == (56, 28))]
         times = self.measure(w, precision, cands, eps_r=eps_r)

@@ -256,7 +256,7 @@ int create_slots(int capacity, size_t esz, int tile_x, int tile_y, int graph_ste
   b->esz = esz;
   b->tile_x = tile_x;
   b->tile_y = tile_y;
-  b->slab = esz == 4 && slab_shape_ok(tile_x, tile_y);
+  b->slab = esz == 4 && slab_shape_ok(tile_x, tile_y, false);
   b->graph_steps = graph_steps;
   int rc = TETM_OK;
   // a blocking stream: work the caller queues on the legacy default stream
@@ -361,7 +361,7 @@ int tetm_batch_create_slots(int32_t capacity, int32_t precision, int32_t tile_x,
   if (capacity < 1 || capacity > (1 << 20) || graph_steps < 0) return TETM_E_ARG;
   if (precision != TETM_FP32 && precision != TETM_FP64) return TETM_E_ARG;
   const size_t esz = precision == TETM_FP64 ? 8 : 4;
-  if (!(esz == 4 && slab_shape_ok(tile_x, tile_y)) && !warp_shape_ok(tile_x, tile_y)) return TETM_E_ARG;
+  if (!(esz == 4 && slab_shape_ok(tile_x, tile_y, false)) && !warp_shape_ok(tile_x, tile_y)) return TETM_E_ARG;
   return create_slots(capacity, esz, tile_x, tile_y, graph_steps, out);
 }
 
@@ -381,7 +381,7 @@ int tetm_batch_create(tetm_solver* const* solvers, const int64_t* step_limits, i
   // float32 members of the slab kernel's tile (the float32 default) run the
   // batched slab kernel; otherwise every member runs the warp-tiled kernel
   // with the first member's tile height
-  const bool slab = esz == 4 && slab_shape_ok(solvers[0]->tile_x, solvers[0]->tile_y);
+  const bool slab = esz == 4 && slab_shape_ok(solvers[0]->tile_x, solvers[0]->tile_y, false);
   const int ty = slab ? solvers[0]->tile_y : ((solvers[0]->tile_x == 28) ? solvers[0]->tile_y : 20);
   const int tx = slab ? solvers[0]->tile_x : 28;
   tetm_batch* b = nullptr;

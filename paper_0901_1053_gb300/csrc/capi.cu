@@ -500,7 +500,7 @@ int do_steps(tetm_solver* s, int n) {
       if (s->n_work > 0) {
         if (warp_shape_ok(s->tile_x, s->tile_y)) {
           CK(launch_fused_warp_step<T>(a, s->tile_x, s->tile_y, s->stream));
-        } else if (slab_shape_ok(s->tile_x, s->tile_y)) {
+        } else if (slab_shape_ok(s->tile_x, s->tile_y, !s->uniform)) {
           if constexpr (sizeof(T) == 4) {
             CK(launch_fused_slab_step(a, s->sched, s->stream));
           } else {
@@ -672,10 +672,10 @@ int create_impl(const tetm_grid* g, int k_lo, int nz_all, const double* eps_r, c
   s->kernel = TETM_KERNEL_FUSED;
   s->uniform = uniform;
   s->vacuum = uniform && eps_u == 1.0 && mu_u == 1.0;
-  // float32: the slab kernel (kernels_slab.cu); float64: the warp-tiled
-  // kernel (kernels_warp.cu)
+  // float32: the slab kernel (kernels_slab.cu; 56 x 12 tiles with
+  // coefficient arrays); float64: the warp-tiled kernel (kernels_warp.cu)
   s->tile_x = s->esz == 4 ? 56 : 28;
-  s->tile_y = s->esz == 4 ? 28 : 20;
+  s->tile_y = s->esz == 4 ? (uniform ? 28 : 12) : 20;
   s->chunk_z = 32;
   int rc = TETM_OK;
   const size_t fbytes = (size_t)s->L.count * s->esz;
@@ -846,7 +846,7 @@ int tetm_set_kernel(tetm_solver* s, int32_t kernel) {
     return TETM_E_UNSUPPORTED;
   if (kernel == TETM_KERNEL_REFERENCE && s->is_slab()) return TETM_E_UNSUPPORTED;  // it updates ghost planes in place
   // (Yee's scheme runs material arrays on the reference updates whatever the kernel)
-  if (kernel == TETM_KERNEL_FUSED && !s->uniform && s->tile_x != 28 && !slab_shape_ok(s->tile_x, s->tile_y) &&
+  if (kernel == TETM_KERNEL_FUSED && !s->uniform && s->tile_x != 28 && !slab_shape_ok(s->tile_x, s->tile_y, true) &&
       s->scheme == TETM_SCHEME_TETM)
     return TETM_E_UNSUPPORTED;
   s->kernel = kernel;
@@ -865,13 +865,16 @@ int tetm_set_tiling(tetm_solver* s, int32_t tile_x, int32_t tile_y, int32_t chun
     s->chunk_z = cz;
     return rebuild_work(s);
   }
-  if ((!fused_shape_ok(tx, ty) && !warp_shape_ok(tx, ty) && !slab_shape_ok(tx, ty)) || cz < 4)
+  const bool slab_u = slab_shape_ok(tx, ty, false), slab_m = slab_shape_ok(tx, ty, true);
+  if ((!fused_shape_ok(tx, ty) && !warp_shape_ok(tx, ty) && !slab_u && !slab_m) || cz < 4)
     return TETM_E_ARG;
-  // per-entry coefficients (general materials) run on the warp-tiled and slab kernels
-  if (!s->uniform && tx != 28 && !slab_shape_ok(tx, ty) && s->kernel == TETM_KERNEL_FUSED)
+  // per-entry coefficients (general materials) run on the warp-tiled kernel
+  // and on the slab kernel's 56 x 12 tiles; one material on its 56 x 28 tiles
+  if (!s->uniform && tx != 28 && !slab_m && s->kernel == TETM_KERNEL_FUSED)
     return TETM_E_UNSUPPORTED;
+  if (s->uniform && slab_m && !slab_u) return TETM_E_UNSUPPORTED;
   // the slab kernel is float32 only
-  if (slab_shape_ok(tx, ty) && s->esz != 4) return TETM_E_UNSUPPORTED;
+  if ((slab_u || slab_m) && s->esz != 4) return TETM_E_UNSUPPORTED;
   if (s->kernel == TETM_KERNEL_TWOSTEP && !fused2_shape_ok(tx, ty)) return TETM_E_UNSUPPORTED;
   if (tx == s->tile_x && ty == s->tile_y && cz == s->chunk_z && s->work) return TETM_OK;
   s->tile_x = tx;
@@ -892,7 +895,7 @@ int tetm_set_scheme(tetm_solver* s, int32_t scheme) {
     yee_shape((int)s->esz, &s->tile_x, &s->tile_y);
   } else {  // the TE/TM scheme's default work shape
     s->tile_x = s->esz == 4 ? 56 : 28;
-    s->tile_y = s->esz == 4 ? 28 : 20;
+    s->tile_y = s->esz == 4 ? (s->uniform ? 28 : 12) : 20;
   }
   s->scheme = scheme;
   return rebuild_work(s);

@@ -59,6 +59,10 @@ constexpr int kSX = 64, kSY = 32;   // loaded columns, rows
 constexpr int kOX = 56, kOY = 28;   // owned columns, rows
 constexpr int kQ = kSX / 4;         // column quads per row
 constexpr int kSThreads = kQ * kSY; // 512
+// with coefficient arrays: a 64 x 16 box (56 x 12 owned), two CTAs of 256
+// threads per SM, whose barriers interleave
+constexpr int kSYM = 16, kOYM = 12;
+constexpr int kMThreads = kQ * kSYM; // 256
 
 // One material: a two-plane ring of e_z and h_z (one coefficient per
 // component, switched by the activity bytes) and two exchange buffers, laid
@@ -79,7 +83,7 @@ struct SlabSmemU {
 // exchange buffers of the skewed sweep (hx~, ez', ex~, hz'), 160 KB, in one
 // array with a spare row at the end (reads past a buffer's edge stay inside).
 struct SlabSmemM {
-  static constexpr int kP = kSY * kSX;
+  static constexpr int kP = kSYM * kSX;
   float f[20 * kP + kSX];  // e_z slots (2), h_z slots (2), 2 x 6 coefficient planes, x1..x4, spare row
   int next[2];
   __device__ __forceinline__ float* ez(int s) { return f + s * kP; }
@@ -382,7 +386,7 @@ __device__ __forceinline__ void slab_item_mat(const StepArgs<float>& a, int item
   const Q4 zero{{0.f, 0.f, 0.f, 0.f}};
   const int tile = item % ntile, chunk = item / ntile;
   const int gx0 = (tile % a.tiles_x) * kOX - 4;  // global i of loaded column 0
-  const int gy0 = (tile / a.tiles_x) * kOY - 2;  // global j of loaded row 0
+  const int gy0 = (tile / a.tiles_x) * kOYM - 2;  // global j of loaded row 0
   const int k0 = chunk * a.chunk_z, k1 = min(k0 + a.chunk_z, L.nz);
   const int kstart = k0 - 1;                   // the plane below the chunk: its new h_x, h_y feed U6, U7 of k0
   const int cx = gx0 + L.ox;                   // layout column of loaded column 0
@@ -394,7 +398,7 @@ __device__ __forceinline__ void slab_item_mat(const StepArgs<float>& a, int item
   const int gi = gx0 + 4 * q, gj = gy0 + row;
   const bool inq = gj + 2 < L.ny + 4 && cx + 4 * q + 4 <= PX;  // the quad lies inside the arrays
   const long long qoff = (long long)(gj + 2) * PX + cx + 4 * q;
-  const bool own_q = q >= 1 && q <= kQ - 2 && row >= 2 && row < kSY - 2 && gj < L.ny;
+  const bool own_q = q >= 1 && q <= kQ - 2 && row >= 2 && row < kSYM - 2 && gj < L.ny;
   const int qo = row * kSX + 4 * q;  // this thread's quad in a box plane
   float* const x1 = S.x(1) + qo;     // and in the exchange buffers
   float* const x2 = S.x(2) + qo;
@@ -640,7 +644,8 @@ __device__ __forceinline__ void slab_item_mat(const StepArgs<float>& a, int item
 }
 
 template <bool MAT>
-__global__ void __launch_bounds__(kSThreads, 1) fused_step_slab(const StepArgs<float> a, int* sched) {
+__global__ void __launch_bounds__(MAT ? kMThreads : kSThreads, MAT ? 2 : 1)
+    fused_step_slab(const StepArgs<float> a, int* sched) {
   using Smem = SlabSmem<MAT>;
   extern __shared__ __align__(128) unsigned char slab_raw[];
   Smem& S = *reinterpret_cast<Smem*>(slab_raw);
@@ -713,7 +718,7 @@ fused_step_slab_batch(const BatchMember<float>* __restrict__ members, const int2
 
 }  // namespace
 
-bool slab_shape_ok(int tx, int ty) { return tx == kOX && ty == kOY; }
+bool slab_shape_ok(int tx, int ty, bool mat) { return tx == kOX && ty == (mat ? kOYM : kOY); }
 
 namespace {
 template <bool MAT>
@@ -733,7 +738,8 @@ cudaError_t launch_slab(const StepArgs<float>& a, int* sched, cudaStream_t st) {
   }
   const int items = a.work ? a.n_work : a.tiles_x * a.tiles_y * a.n_chunks;
   if (items <= 0) return cudaSuccess;
-  fused_step_slab<MAT><<<std::min(items, sms), kSThreads, smem, st>>>(a, sched);
+  constexpr int threads = MAT ? kMThreads : kSThreads, per_sm = MAT ? 2 : 1;
+  fused_step_slab<MAT><<<std::min(items, per_sm * sms), threads, smem, st>>>(a, sched);
   return cudaGetLastError();
 }
 }  // namespace

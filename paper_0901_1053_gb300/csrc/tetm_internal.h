@@ -139,8 +139,9 @@ template <typename T>
 cudaError_t launch_batch_advance(BatchMember<T>* members, int n_members, cudaStream_t st);
 
 // ---- block-tiled float32 step with a shared-memory ring (kernels_slab.cu):
-// tile 56 x 28, one CTA of 512 threads per SM ------------------------------
-bool slab_shape_ok(int tile_x, int tile_y);
+// tile 56 x 28, one CTA of 512 threads per SM; with coefficient arrays (mat)
+// tile 56 x 12, two CTAs of 256 threads per SM ------------------------------
+bool slab_shape_ok(int tile_x, int tile_y, bool mat);
 // one step of every active member of a float32 batch on the slab kernel
 // (work = (member, item) pairs counted at n_work in device memory, at most
 // n_bound; sched as below), the transverse wakes, then the device-side

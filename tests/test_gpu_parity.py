@@ -193,9 +193,20 @@ def test_materials_block_tiles_unsupported(tetm):
     with pytest.raises(tetm.TetmError) as e:
         s.set_tiling(32, 8, 16)
     assert e.value.code == tetm.TETM_E_UNSUPPORTED
+    # the slab kernel's tiles: 56 x 12 with coefficient arrays, 56 x 28 with one material
+    assert (s.info()["tile_x"], s.info()["tile_y"]) == (56, 12)
+    with pytest.raises(tetm.TetmError) as e:
+        s.set_tiling(56, 28, 16)
+    assert e.value.code == tetm.TETM_E_UNSUPPORTED
+    u = tetm.Solver(nx, ny, nz, wl.DXY, wl.DXY, wl.DZ, 0.0, "fp32", pec=pec)
+    assert (u.info()["tile_x"], u.info()["tile_y"]) == (56, 28)
+    with pytest.raises(tetm.TetmError) as e:
+        u.set_tiling(56, 12, 16)
+    assert e.value.code == tetm.TETM_E_UNSUPPORTED
+    u.close()
 
 
-@pytest.mark.parametrize("tiling", [None, (56, 28, 32), (28, 20, 32)])
+@pytest.mark.parametrize("tiling", [None, (56, 12, 32), (28, 20, 32)])
 def test_dielectric_collimator_fp32_wake(tetm, tiling):
     """A collimator with a dielectric liner (eps_r = 3 over the narrow part),
     FP32 fused kernels with coefficient arrays (slab, the default, and
@@ -205,7 +216,7 @@ def test_dielectric_collimator_fp32_wake(tetm, tiling):
     if tiling:
         s.set_tiling(*tiling)
     else:
-        assert (s.info()["tile_x"], s.info()["tile_y"]) == (56, 28)
+        assert (s.info()["tile_x"], s.info()["tile_y"]) == (56, 12)
     s.set_bunch(w.sigma, w.charge, w.i0, w.j0)
     s.step(w.steps)
     o = Oracle(w.nx, w.ny, w.nz, w.dx, w.dy, w.dz, w.cdt, eps_r=eps, pec=w.pec)
@@ -506,7 +517,7 @@ def test_slab_kernel_with_materials_fp32(tetm, dims):
     pec[:, max(0, j0 - 2):j0 + 2, max(0, i0 - 2):i0 + 2] = 0     # a clear bunch line
     steps = nz + 20
     out = {}
-    for tiling in [(56, 28, 32), (28, 20, 32)]:
+    for tiling in [(56, 12, 32), (28, 20, 32)]:
         s = tetm.Solver(nx, ny, nz, wl.DXY, wl.DXY, wl.DZ, 0.0, "fp32", eps_r=eps, mu_r=mu, pec=pec)
         s.set_tiling(*tiling)
         for c, a in init.items():
@@ -521,7 +532,7 @@ def test_slab_kernel_with_materials_fp32(tetm, dims):
         o.set(c, a)
     o.set_bunch(sigma, 1e-9, i0, j0)
     o.step(steps)
-    slab, warp = out[(56, 28, 32)], out[(28, 20, 32)]
+    slab, warp = out[(56, 12, 32)], out[(28, 20, 32)]
     for fam in (("ex", "ey", "ez"), ("hx", "hy", "hz")):
         peak = max(np.max(np.abs(o.get(c))) for c in fam)
         for c in fam:
@@ -539,7 +550,7 @@ def test_slab_kernel_with_materials_chunk_lengths_are_bitwise_identical(tetm):
     ref = None
     for cz in (32, 5, 64):
         s = tetm.Solver(w.nx, w.ny, w.nz, w.dx, w.dy, w.dz, w.cdt, "fp32", eps_r=eps, pec=w.pec)
-        s.set_tiling(56, 28, cz)
+        s.set_tiling(56, 12, cz)
         s.set_bunch(w.sigma, w.charge, w.i0, w.j0)
         s.step(110)
         got = [s.get(c) for c in ("ex", "ey", "ez", "hx", "hy", "hz")] + [s.wake()[0]]
@@ -553,7 +564,7 @@ def test_slab_kernel_with_materials_chunk_lengths_are_bitwise_identical(tetm):
 
 def test_full_size_dielectric_collimator_head_matches_oracle(tetm):
     """256x256x1024 dielectric collimator (per-cell eps array) in the benchmark's
-    launch configuration (slab kernel with coefficient arrays, 56 x 28 x 16): as
+    launch configuration (slab kernel with coefficient arrays, 56 x 12 x 16): as
     for the vacuum collimator, nothing ahead of plane n has moved after n steps,
     so the oracle on the first 80 planes reproduces planes 0..n entry by entry."""
     w, eps = wl.dielectric_collimator(n=256, nz=1024, precision="fp32")
@@ -565,7 +576,7 @@ def test_full_size_dielectric_collimator_head_matches_oracle(tetm):
     assert np.any(eps[:80] != 1.0)
     n = 60
     s = tetm.Solver(w.nx, w.ny, w.nz, w.dx, w.dy, w.dz, w.cdt, "fp32", eps_r=eps, pec=w.pec)
-    s.set_tiling(56, 28, 16)
+    s.set_tiling(56, 12, 16)
     s.set_bunch(w.sigma, w.charge, w.i0, w.j0)
     s.step(n)
     s.sync()
