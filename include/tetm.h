@@ -231,7 +231,7 @@ int tetm_set_stream(tetm_solver* s, void* cuda_stream);
 /* Select the update kernels (TETM_KERNEL_*). With general materials (per-cell
  * eps_r / mu_r that differ) the fused path streams per-entry coefficient
  * arrays and needs the warp-tiled work shape (tile_x = 28) or, in float32,
- * the slab shape 56 x 28 (the defaults); the block-tiled shapes then give
+ * the slab shape 56 x 12 (the defaults); the block-tiled shapes then give
  * TETM_E_UNSUPPORTED. */
 int tetm_set_kernel(tetm_solver* s, int32_t kernel);
 /* TETM_KERNEL_TWOSTEP (temporal blocking of the sweep, Eq. (23) applied twice
@@ -247,10 +247,12 @@ int tetm_set_kernel(tetm_solver* s, int32_t kernel);
 
 /* Fused-kernel work shape: transverse tile tile_x x tile_y and z-chunk
  * length chunk_z >= 4 of one work item. 56 x 28 selects the float32 slab
- * kernel (one CTA of 512 threads per SM; e_z, h_z staged in shared memory
- * by per-thread asynchronous copies of the quads that carry them, or with
- * material arrays by tensor copies of e_z, h_z and the six coefficient
- * arrays; TETM_E_UNSUPPORTED in float64; the float32 default, chunk 32);
+ * kernel for one material (one CTA of 512 threads per SM; e_z, h_z staged in
+ * shared memory by per-thread asynchronous copies of the quads that carry
+ * them), 56 x 12 the slab kernel for material arrays (two CTAs of 256
+ * threads per SM; e_z, h_z and the six coefficient arrays staged the same
+ * way); each gives TETM_E_UNSUPPORTED for the other kind of solve and in
+ * float64; the float32 defaults, chunk 32);
  * tile_x = 28 the warp-tiled kernel (one warp per item, tile_y in {4, 8,
  * 12, 16, 20, 28};
  * the float64 default, 28 x 20 x 32); tile_x = 32 (tile_y in {4, 8, 16}) or
