@@ -5,11 +5,11 @@
 // each side: the ten updates reach two nodes sideways); with coefficient
 // arrays two CTAs of 256 threads per SM do the same on 56 x 12 tiles (64 x 16
 // loaded), one CTA's barriers and copy waits overlapping the other's work.
-// Thread t holds the
-// four consecutive columns 4 (t mod 16) .. +3 of row t / 16 (a quad), so its
-// loads and stores are 16-byte vectors, and marches through the chunk plane by
-// plane with the z-state of its quad in registers (old e_x, e_y, new h_x, h_y
-// of the planes below): no per-row state in shared memory.
+// Thread t holds the four consecutive columns 4 (t mod 16) .. +3 of row
+// t / 16 (a quad), so its loads and stores are 16-byte vectors, and marches
+// through the chunk plane by plane with the z-state of its quad in registers
+// (old e_x, e_y, new h_x, h_y of the planes below): no per-row state in
+// shared memory.
 //
 // Only entries that carry a field move through the per-thread loads and
 // stores. Each thread reads the activity bytes of its quad (one 32-bit word
