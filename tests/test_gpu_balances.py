@@ -105,13 +105,17 @@ def test_periodic_balances_fp64_random_field(tetm, eps):
             assert ok, (n, info)
 
 
-def test_periodic_balances_fp32_fields_against_oracle_on_the_same_state(tetm):
-    """Float32 fields (the benchmark's precision): each record equals the
-    oracle's float64 energy and charges evaluated on the GPU's own float32
-    states (read back exactly), to 1e-12."""
+@pytest.mark.parametrize("eps", [False, True], ids=["vacuum", "materials"])
+def test_periodic_balances_fp32_fields_against_oracle_on_the_same_state(tetm, eps):
+    """Float32 fields (the benchmark's precision), one material or per-cell
+    eps_r: each record equals the oracle's float64 energy and charges
+    evaluated on the GPU's own float32 states (read back exactly), to 1e-12."""
     w = wl.scaled_collimator(40, 48, sigma_cells=3.0, precision="fp32")
-    s = tetm.Solver(w.nx, w.ny, w.nz, w.dx, w.dy, w.dz, w.cdt, "fp32", pec=w.pec)
-    chk = Oracle(w.nx, w.ny, w.nz, w.dx, w.dy, w.dz, w.cdt, pec=w.pec)
+    eps_r = None
+    if eps:
+        eps_r = 1.0 + 2.0 * np.random.default_rng(6).random((w.nz, w.ny, w.nx))
+    s = tetm.Solver(w.nx, w.ny, w.nz, w.dx, w.dy, w.dz, w.cdt, "fp32", eps_r=eps_r, pec=w.pec)
+    chk = Oracle(w.nx, w.ny, w.nz, w.dx, w.dy, w.dz, w.cdt, eps_r=eps_r, pec=w.pec)
     f = random_fields(chk, 43)
     for c in orc.COMPONENTS:
         s.set(c, f[c])
