@@ -151,6 +151,16 @@ __global__ void recip_coef(const double* minv, long long n, double* out) {
   const long long q = (long long)blockIdx.x * blockDim.x + threadIdx.x;
   if (q < n) out[q] = minv[q] != 0.0 ? 1.0 / minv[q] : 0.0;
 }
+// The same (recip) or s M^-1 as a (hi, lo) float32 pair whose sum is the
+// float64 value to 2^-48, for the float32-pair balances
+__global__ void pair_coef(const double* minv, double s, bool recip, long long n, float2* out) {
+  const long long q = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (q >= n) return;
+  const double v = minv[q];
+  const double x = recip ? (v != 0.0 ? 1.0 / v : 0.0) : s * v;
+  const float hi = (float)x;
+  out[q] = make_float2(hi, (float)(x - (double)hi));
+}
 
 // Canonical FIT layout <-> device layout, for planes [k0, k0 + nk).
 template <typename T>
@@ -439,6 +449,14 @@ int queue_balances(tetm_solver* s, double* rec) {
     mr[c] = s->m_a[c];
   }
   const WorkView wv = work_view(s);
+  if constexpr (sizeof(T) == 4) {
+    if (!s->uniform) {  // float32 fields, material arrays: one float32-pair pass
+      CK(launch_balances_mat_f32((const float* const*)cur, (const float* const*)prv, s->mask, s->mp, s->ap, s->L,
+                                 s->alpha, s->bunch ? s->qline : nullptr, s->i0, s->j0, wv, s->diag, rec + 1,
+                                 rec + 2, rec + 3, s->stream));
+      return TETM_OK;
+    }
+  }
   if (s->uniform) {  // one pass for both
     CK(launch_balances<T>(cur, prv, s->mask, s->minv_c, s->L, s->alpha, s->bunch ? s->qline : nullptr, s->i0,
                           s->j0, wv, s->diag, rec + 1, rec + 2, rec + 3, s->stream));
@@ -584,6 +602,8 @@ void free_all(tetm_solver* s) {
   for (int c = 0; c < 6; ++c) {
     dev_free(s->minv_a[c], st);
     dev_free(s->m_a[c], st);
+    dev_free(s->mp[c], st);
+    dev_free(s->ap[c], st);
     dev_free(s->ua[c], st);
   }
   dev_free(s->mask, st);
@@ -752,11 +772,24 @@ int create_impl(const tetm_grid* g, int k_lo, int nz_all, const double* eps_r, c
   if (rc == TETM_OK && !uniform) {
     for (int c = 0; c < 6 && rc == TETM_OK; ++c) {
       rc = dalloc(s, &s->ua[c], (size_t)s->L.count * s->esz);
-      if (rc == TETM_OK) rc = dalloc(s, (void**)&s->m_a[c], sizeof(double) * (size_t)s->L.count);
       if (rc != TETM_OK) break;
       const double sc = (c == kEZ || c == kHZ) ? 2.0 * s->alpha : s->alpha;
       const unsigned nb = (unsigned)((s->L.count + 255) / 256);
-      recip_coef<<<nb, 256, 0, s->stream>>>(s->minv_a[c], s->L.count, s->m_a[c]);
+      // the balances' coefficients: M (and alpha^2 M^-1 of the four
+      // transverse components) as float32 pairs for float32 fields, M in
+      // float64 for float64 fields
+      if (s->esz == 4) {
+        const bool a2 = c == kHX || c == kHY || c == kEX || c == kEY;
+        rc = dalloc(s, (void**)&s->mp[c], sizeof(float2) * (size_t)s->L.count);
+        if (rc == TETM_OK && a2) rc = dalloc(s, (void**)&s->ap[c], sizeof(float2) * (size_t)s->L.count);
+        if (rc != TETM_OK) break;
+        pair_coef<<<nb, 256, 0, s->stream>>>(s->minv_a[c], 0.0, true, s->L.count, s->mp[c]);
+        if (a2) pair_coef<<<nb, 256, 0, s->stream>>>(s->minv_a[c], s->alpha * s->alpha, false, s->L.count, s->ap[c]);
+      } else {
+        rc = dalloc(s, (void**)&s->m_a[c], sizeof(double) * (size_t)s->L.count);
+        if (rc != TETM_OK) break;
+        recip_coef<<<nb, 256, 0, s->stream>>>(s->minv_a[c], s->L.count, s->m_a[c]);
+      }
       if (s->esz == 8)
         scale_coef<double><<<nb, 256, 0, s->stream>>>(s->minv_a[c], sc, s->L.count, (double*)s->ua[c]);
       else
@@ -1049,8 +1082,8 @@ int tetm_energy(tetm_solver* s, double* w) {
     for (int c = 0; c < 6; ++c) f[c] = (const float*)s->set[s->cur][c];
     e = s->uniform ? launch_balances<float>(f, nullptr, s->mask, s->minv_c, s->L, s->alpha, nullptr, 0, 0,
                                             work_view(s), s->diag, s->diag.out, nullptr, nullptr, s->stream)
-                   : launch_energy<float>(f, s->mask, s->minv_c, ma, mr, s->L, s->alpha, work_view(s), s->diag,
-                                          s->diag.out, s->stream);
+                   : launch_balances_mat_f32(f, nullptr, s->mask, s->mp, s->ap, s->L, s->alpha, nullptr, 0, 0,
+                                             work_view(s), s->diag, s->diag.out, nullptr, nullptr, s->stream);
   }
   CK(e);
   CK(cudaMemcpyAsync(w, s->diag.out, sizeof(double), cudaMemcpyDeviceToHost, s->stream));

@@ -605,6 +605,169 @@ balance_items_f32(BalanceFields<float> bf, const uint8_t* __restrict__ mask, Uni
   }
 }
 
+// balance_items_f32 with per-entry coefficients (material arrays): every
+// term of the energy and of Eqs. (35)/(34) is a coefficient of its own entry
+// times a sum of float32 values, so each is formed as the product of the
+// coefficient as a float32 pair (m: M = 1/M^-1 of the six components; a:
+// alpha^2 M^-1 of h_x, h_y, e_x, e_y) and the exact pair of the sum, and the
+// products are summed as pairs. Energy: three pair accumulators (sum M v^2,
+// sum alpha^2 M^-1 d^2 over the four link differences, the cross term),
+// flushed into float64 every kFlush nodes. Charges: the corrected z-fluxes of
+// the edge below and of the face above (previous h_z) are carried up the
+// column as pairs, each charge is summed as one pair and widened once.
+struct MatPairs {
+  const float2* m[6];  // M per component
+  const float2* a[6];  // alpha^2 M^-1 (entries kHX, kHY, kEX, kEY used)
+};
+template <bool CHARGE>
+__global__ void __launch_bounds__(256, 2)
+balance_items_mat_f32(BalanceFields<float> bf, const uint8_t* __restrict__ mask, MatPairs mp, Layout L,
+                      WorkView wv, double alpha, const double* qline, int i0, int j0, double* part_w,
+                      double* part_e, double* part_h) {
+  const float* __restrict__ ex = bf.cur[kEX];
+  const float* __restrict__ ey = bf.cur[kEY];
+  const float* __restrict__ ez = bf.cur[kEZ];
+  const float* __restrict__ hx = bf.cur[kHX];
+  const float* __restrict__ hy = bf.cur[kHY];
+  const float* __restrict__ hz = bf.cur[kHZ];
+  const int item = wv.items ? wv.items[blockIdx.x] : (int)blockIdx.x;
+  const ItemCells ic(wv, L, item);
+  const long long sx = 1, sy = L.px, sz = L.sz;
+  auto M = [&](int c, long long e) { const float2 v = mp.m[c][e]; return F2{v.x, v.y}; };
+  auto A = [&](int c, long long e) { const float2 v = mp.a[c][e]; return F2{v.x, v.y}; };
+  // d^2 of an exact pair d, as a pair (the dropped d.lo^2 is below 2^-48 of it)
+  auto sq2 = [](F2 d) {
+    const F2 p = two_prod(d.hi, d.hi);
+    return F2{p.hi, fmaf(2.f * d.hi, d.lo, p.lo)};
+  };
+  auto neg = [](F2 d) { return F2{-d.hi, -d.lo}; };
+  F2 accW{0.f, 0.f}, accR{0.f, 0.f}, accL{0.f, 0.f};
+  double w = 0.0;
+  int cnt = 0;
+  double me = 0.0, mh = 0.0;
+  auto flush = [&]() {
+    w = fma(0.5, f2_wide(accW), w);
+    w = fma(-0.5, f2_wide(accR), w);
+    w = fma(alpha, f2_wide(accL), w);
+    accW = accR = accL = F2{0.f, 0.f};
+    cnt = 0;
+  };
+  // corrected z-flux of edge e (Eq. (35)): M_ez ez - a2 [(t1(e-sy) - t1(e)) +
+  // (t2(e-sx) - t2(e))], t1(f) = M^-1_hx(f) (ez(f+sy) - ez(f)), t2 likewise
+  // in x; zero on an edge without a field
+  auto dz_at = [&](long long e) {
+    F2 acc{0.f, 0.f};
+    if (!(mask[e] & 4)) return acc;
+    const float z = ez[e];
+    acc_prod(acc, M(kEZ, e), F2{z, 0.f});
+    acc_prod(acc, A(kHX, e - sy), two_sum(ez[e - sy], -z));
+    acc_prod(acc, A(kHX, e), two_sum(ez[e + sy], -z));
+    acc_prod(acc, A(kHY, e - sx), two_sum(ez[e - sx], -z));
+    acc_prod(acc, A(kHY, e), two_sum(ez[e + sx], -z));
+    return acc;
+  };
+  // corrected z-flux of face f of the previous state (Eq. (34)): M_hz hz -
+  // a2 [(t3(f+sy) - t3(f)) + (t4(f+sx) - t4(f))], t3(e) = M^-1_ex(e)
+  // (hz(e-sy) - hz(e)), t4 likewise in x; zero on a face without a field
+  auto bz_at = [&](long long f) {
+    F2 acc{0.f, 0.f};
+    if (!(mask[f] & 32)) return acc;
+    const float* __restrict__ phz = bf.prev[kHZ];
+    const float z = phz[f];
+    acc_prod(acc, M(kHZ, f), F2{z, 0.f});
+    acc_prod(acc, A(kEX, f + sy), two_sum(phz[f + sy], -z));
+    acc_prod(acc, A(kEX, f), two_sum(phz[f - sy], -z));
+    acc_prod(acc, A(kEY, f + sx), two_sum(phz[f + sx], -z));
+    acc_prod(acc, A(kEY, f), two_sum(phz[f - sx], -z));
+    return acc;
+  };
+  for (int c = threadIdx.x; c < ic.tx * ic.ty; c += blockDim.x) {
+    const int i = ic.i0 + c % ic.tx, j = ic.j0 + c / ic.tx;
+    if (i >= L.nx || j >= L.ny) continue;
+    long long n = L.idx(i, j, ic.k0);
+    F2 dz_below{0.f, 0.f}, bz_here{0.f, 0.f};
+    if constexpr (CHARGE) {
+      dz_below = dz_at(n - sz);
+      bz_here = bz_at(n);
+    }
+    for (int k = ic.k0; k < ic.k1; ++k, n += sz) {
+      const unsigned m0 = mask[n];
+      F2 dz_here{0.f, 0.f}, bz_above{0.f, 0.f};
+      if constexpr (CHARGE) {
+        dz_here = dz_at(n);
+        bz_above = bz_at(n + sz);
+      }
+      if (m0 != 0) {  // no field object here: every energy term is zero
+        const float vex = ex[n], vey = ey[n], vez = ez[n], vhx = hx[n], vhy = hy[n], vhz = hz[n];
+        acc_prod(accW, M(kEX, n), two_prod(vex, vex));
+        acc_prod(accW, M(kEY, n), two_prod(vey, vey));
+        acc_prod(accW, M(kEZ, n), two_prod(vez, vez));
+        acc_prod(accW, M(kHX, n), two_prod(vhx, vhx));
+        acc_prod(accW, M(kHY, n), two_prod(vhy, vhy));
+        acc_prod(accW, M(kHZ, n), two_prod(vhz, vhz));
+        acc_prod(accR, A(kHX, n), sq2(two_sum(ez[n + sy], -vez)));
+        acc_prod(accR, A(kHY, n), sq2(two_sum(ez[n + sx], -vez)));
+        acc_prod(accR, A(kEX, n), sq2(two_sum(hz[n - sy], -vhz)));
+        acc_prod(accR, A(kEY, n), sq2(two_sum(hz[n - sx], -vhz)));
+        acc_mul2(accL, vhx, two_sum(ey[n + sz], -vey));
+        acc_mul2(accL, -vhy, two_sum(ex[n + sz], -vex));
+        if (++cnt == kFlush) flush();
+      }
+      if constexpr (CHARGE) {
+        // Eq. (35) at node n: its six incident edges carry a field
+        if ((m0 & 7) == 7 && (mask[n - sx] & 1) && (mask[n - sy] & 2) && (mask[n - sz] & 4)) {
+          const float* __restrict__ pex = bf.prev[kEX];
+          const float* __restrict__ pey = bf.prev[kEY];
+          const F2 Sxl = two_sum(0.5f * ex[n - sx], 0.5f * pex[n - sx]);
+          const F2 Sxn = two_sum(0.5f * ex[n], 0.5f * pex[n]);
+          const F2 Syd = two_sum(0.5f * ey[n - sy], 0.5f * pey[n - sy]);
+          const F2 Syn = two_sum(0.5f * ey[n], 0.5f * pey[n]);
+          F2 qs{0.f, 0.f};
+          acc_prod(qs, M(kEX, n - sx), neg(Sxl));
+          acc_prod(qs, M(kEX, n), Sxn);
+          acc_prod(qs, M(kEY, n - sy), neg(Syd));
+          acc_prod(qs, M(kEY, n), Syn);
+          f2_acc(qs, -dz_below.hi, -dz_below.lo);
+          f2_acc(qs, dz_here.hi, dz_here.lo);
+          double qe = f2_wide(qs);
+          if (qline && i == i0 && j == j0) qe -= qline[k];
+          me = fmax(me, fabs(qe));
+        }
+        // Eq. (34) at the cell whose lower node is n: its six faces carry a field
+        if ((m0 & 56) == 56 && (mask[n + sx] & 8) && (mask[n + sy] & 16) && (mask[n + sz] & 32)) {
+          const float* __restrict__ phx = bf.prev[kHX];
+          const float* __restrict__ phy = bf.prev[kHY];
+          const F2 Bxr = two_sum(0.5f * hx[n + sx], 0.5f * phx[n + sx]);
+          const F2 Bxn = two_sum(0.5f * hx[n], 0.5f * phx[n]);
+          const F2 Byu = two_sum(0.5f * hy[n + sy], 0.5f * phy[n + sy]);
+          const F2 Byn = two_sum(0.5f * hy[n], 0.5f * phy[n]);
+          F2 qs{0.f, 0.f};
+          acc_prod(qs, M(kHX, n + sx), Bxr);
+          acc_prod(qs, M(kHX, n), neg(Bxn));
+          acc_prod(qs, M(kHY, n + sy), Byu);
+          acc_prod(qs, M(kHY, n), neg(Byn));
+          f2_acc(qs, bz_above.hi, bz_above.lo);
+          f2_acc(qs, -bz_here.hi, -bz_here.lo);
+          mh = fmax(mh, fabs(f2_wide(qs)));
+        }
+        dz_below = dz_here;
+        bz_here = bz_above;
+      }
+    }
+  }
+  flush();
+  const double bw = block_reduce<false>(w);
+  if (threadIdx.x == 0) part_w[blockIdx.x] = bw;
+  if constexpr (CHARGE) {
+    const double be = block_reduce<true>(me);
+    const double bh = block_reduce<true>(mh);
+    if (threadIdx.x == 0) {
+      part_e[blockIdx.x] = be;
+      part_h[blockIdx.x] = bh;
+    }
+  }
+}
+
 // The three totals of balance_items: sum of the energy partials, maxima of
 // the two charge partials.
 __global__ void balance_pass2(const double* part_w, const double* part_e, const double* part_h, int n,
@@ -750,6 +913,39 @@ cudaError_t launch_balances(const T* const cur[6], const T* const prev[6], const
   return cudaGetLastError();
   }
 }
+cudaError_t launch_balances_mat_f32(const float* const cur[6], const float* const prev[6], const uint8_t* mask,
+                                   const float2* const m[6], const float2* const a[6], const Layout& L,
+                                   double alpha, const double* qline, int i0, int j0, const WorkView& wv,
+                                   const DiagScratch& s, double* res_w, double* res_e, double* res_h,
+                                   cudaStream_t st) {
+  const int nb = wv.n_items;
+  if (3 * nb > s.cap) return cudaErrorInvalidValue;
+  if (nb == 0) {
+    cudaError_t e = cudaMemsetAsync(res_w, 0, sizeof(double), st);
+    if (e == cudaSuccess && prev) e = cudaMemsetAsync(res_e, 0, sizeof(double), st);
+    if (e == cudaSuccess && prev) e = cudaMemsetAsync(res_h, 0, sizeof(double), st);
+    return e;
+  }
+  BalanceFields<float> bf;
+  MatPairs mp;
+  for (int c = 0; c < 6; ++c) {
+    bf.cur[c] = cur[c];
+    bf.prev[c] = prev ? prev[c] : nullptr;
+    mp.m[c] = m[c];
+    mp.a[c] = a[c];
+  }
+  const int nt = balance_threads(wv);
+  if (prev)
+    balance_items_mat_f32<true><<<nb, nt, 0, st>>>(bf, mask, mp, L, wv, alpha, qline, i0, j0, s.part,
+                                                   s.part + nb, s.part + 2 * nb);
+  else
+    balance_items_mat_f32<false><<<nb, nt, 0, st>>>(bf, mask, mp, L, wv, alpha, nullptr, 0, 0, s.part, nullptr,
+                                                    nullptr);
+  balance_pass2<<<1, 1024, 0, st>>>(s.part, prev ? s.part + nb : nullptr, prev ? s.part + 2 * nb : nullptr, nb,
+                                    res_w, res_e, res_h);
+  return cudaGetLastError();
+}
+
 template cudaError_t launch_balances<float>(const float* const[6], const float* const[6], const uint8_t*,
                                             const double*, const Layout&, double, const double*, int, int,
                                             const WorkView&, const DiagScratch&, double*, double*, double*,

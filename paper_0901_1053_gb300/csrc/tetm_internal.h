@@ -210,6 +210,16 @@ cudaError_t launch_balances(const T* const cur[6], const T* const prev[6], const
                             int j0, const WorkView& wv, const DiagScratch& s, double* res_w, double* res_e,
                             double* res_h, cudaStream_t st);
 
+// Float32 fields with material arrays: the energy into *res_w and, when prev
+// is not null, the charge residuals into *res_e, *res_h, in one pass of
+// float32-pair arithmetic; m[c]: M = 1/M^-1 per entry, a[c]: alpha^2 M^-1 per
+// entry (c = kHX, kHY, kEX, kEY), both as (hi, lo) float32 pairs.
+cudaError_t launch_balances_mat_f32(const float* const cur[6], const float* const prev[6], const uint8_t* mask,
+                                   const float2* const m[6], const float2* const a[6], const Layout& L,
+                                   double alpha, const double* qline, int i0, int j0, const WorkView& wv,
+                                   const DiagScratch& s, double* res_w, double* res_e, double* res_h,
+                                   cudaStream_t st);
+
 // Truncated Gaussian bunch charge in the dual cell of each node k = 0..nz of
 // the bunch line at bunch-centre position zc; *qmax = max |ql[k]|; *tag = tag.
 cudaError_t launch_bunch_charge(double q, double sigma, double dz, double zc, int nz, double* ql,
@@ -227,7 +237,9 @@ struct tetm_solver {
   uint8_t* mask;
   double minv_c[6];
   double* minv_a[6];
-  double* m_a[6];  // 1 / minv_a (0 where minv_a is 0), for the balances
+  double* m_a[6];  // float64 fields: 1 / minv_a (0 where minv_a is 0), for the balances
+  float2* mp[6];   // float32 fields: the same as (hi, lo) float32 pairs
+  float2* ap[6];   // float32 fields: alpha^2 minv_a as pairs (kHX, kHY, kEX, kEY)
   void* ua[6];
   bool uniform;
   bool vacuum;    // no material arrays (eps_r = mu_r = 1)
