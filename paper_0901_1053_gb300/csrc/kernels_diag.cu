@@ -67,6 +67,10 @@ struct MinvView {
   // M = 1/M^-1 of an active entry (0 for inactive ones)
   __device__ __forceinline__ double m(int comp, long long id) const {
     if (ra[comp]) return ra[comp][id];
+    if (a[comp]) {  // per-entry M^-1 without its reciprocals
+      const double v = a[comp][id];
+      return v != 0.0 ? 1.0 / v : 0.0;
+    }
     return ((mask[id] >> comp) & 1) ? r[comp] : 0.0;
   }
 };
