@@ -462,10 +462,12 @@ int queue_balances(tetm_solver* s, double* rec) {
                           s->j0, wv, s->diag, rec + 1, rec + 2, rec + 3, s->stream));
     return TETM_OK;
   }
-  CK(launch_energy<T>(cur, s->mask, s->minv_c, ma, mr, s->L, s->alpha, wv, s->diag, rec + 1, s->stream));
-  CK(launch_charge<T>(cur, prv, s->mask, s->minv_c, ma, mr, s->L, s->alpha,
-                      s->bunch ? s->qline : nullptr, s->i0, s->j0, wv, s->diag, rec + 2, rec + 3,
-                      s->stream));
+  if constexpr (sizeof(T) == 8) {  // float64 fields, material arrays: two float64 passes
+    CK(launch_energy<T>(cur, s->mask, s->minv_c, ma, mr, s->L, s->alpha, wv, s->diag, rec + 1, s->stream));
+    CK(launch_charge<T>(cur, prv, s->mask, s->minv_c, ma, mr, s->L, s->alpha,
+                        s->bunch ? s->qline : nullptr, s->i0, s->j0, wv, s->diag, rec + 2, rec + 3,
+                        s->stream));
+  }
   return TETM_OK;
 }
 

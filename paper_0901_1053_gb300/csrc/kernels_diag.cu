@@ -92,10 +92,11 @@ struct ItemCells {
 };
 
 // Energy of Sec. 4.4, W = 1/2 <Q^e y, y> with Q^e = [[I - a^2 R_0, a L],
-// [a L^T, I - a^2 R_1]], in integral variables: the share of node index
-// (i,j,k) is 1/2 sum_c M_c f_c^2 - a^2/2 (M_mux^-1 (P_y ez)^2 +
-// M_muy^-1 (P_x ez)^2 + M_epsx^-1 (P_y^T hz)^2 + M_epsy^-1 (P_x^T hz)^2)
-// + a (hx P_z ey - hy P_z ex). One partial per work item.
+// [a L^T, I - a^2 R_1]], in integral variables, for float64 fields with
+// per-entry material matrices: the share of node index (i,j,k) is
+// 1/2 sum_c M_c f_c^2 - a^2/2 (M_mux^-1 (P_y ez)^2 + M_muy^-1 (P_x ez)^2 +
+// M_epsx^-1 (P_y^T hz)^2 + M_epsy^-1 (P_x^T hz)^2) + a (hx P_z ey - hy P_z ex).
+// One partial per work item.
 template <typename T>
 __global__ void energy_items(const T* __restrict__ ex, const T* __restrict__ ey,
                              const T* __restrict__ ez, const T* __restrict__ hx,
@@ -105,11 +106,7 @@ __global__ void energy_items(const T* __restrict__ ex, const T* __restrict__ ey,
   const ItemCells ic(wv, L, item);
   const long long sx = 1, sy = L.px, sz = L.sz;
   const T* f[6] = {ex, ey, ez, hx, hy, hz};
-  const bool uniform = mv.a[0] == nullptr;
-  // uniform material: per-component sums of squares, scaled once at the end
-  double sq[6] = {0, 0, 0, 0, 0, 0};
-  double rq[4] = {0, 0, 0, 0};  // (P_y ez)^2 on hx faces, (P_x ez)^2 on hy faces, (P_y^T hz)^2 on ex, (P_x^T hz)^2 on ey
-  double acc = 0.0;             // cross terms (and everything, for material arrays)
+  double acc = 0.0;
   for (int c = threadIdx.x; c < ic.tx * ic.ty; c += blockDim.x) {
     const int i = ic.i0 + c % ic.tx, j = ic.j0 + c / ic.tx;
     if (i >= L.nx || j >= L.ny) continue;
@@ -123,33 +120,15 @@ __global__ void energy_items(const T* __restrict__ ex, const T* __restrict__ ey,
       const double ptxhz = wide(hz[id - sx]) - wide(hz[id]);
       const double l = wide(hx[id]) * (wide(ey[id + sz]) - wide(ey[id])) -
                        wide(hy[id]) * (wide(ex[id + sz]) - wide(ex[id]));
-      if (uniform) {
-        // inactive entries hold zero fields, so their squares add nothing
-        for (int q = 0; q < 6; ++q) {
-          const double v = wide(f[q][id]);
-          sq[q] += v * v;
-        }
-        if (m & 8) rq[0] += pyez * pyez;
-        if (m & 16) rq[1] += pxez * pxez;
-        if (m & 1) rq[2] += ptyhz * ptyhz;
-        if (m & 2) rq[3] += ptxhz * ptxhz;
-        acc += alpha * l;
-      } else {
-        double w = 0.0;
-        for (int q = 0; q < 6; ++q) {
-          const double v = wide(f[q][id]);
-          w += 0.5 * v * v * mv.m(q, id);
-        }
-        const double r = mv(kHX, id) * pyez * pyez + mv(kHY, id) * pxez * pxez +
-                         mv(kEX, id) * ptyhz * ptyhz + mv(kEY, id) * ptxhz * ptxhz;
-        acc += w - 0.5 * alpha * alpha * r + alpha * l;
+      double w = 0.0;
+      for (int q = 0; q < 6; ++q) {
+        const double v = wide(f[q][id]);
+        w += 0.5 * v * v * mv.m(q, id);
       }
+      const double r = mv(kHX, id) * pyez * pyez + mv(kHY, id) * pxez * pxez +
+                       mv(kEX, id) * ptyhz * ptyhz + mv(kEY, id) * ptxhz * ptxhz;
+      acc += w - 0.5 * alpha * alpha * r + alpha * l;
     }
-  }
-  if (uniform) {
-    for (int q = 0; q < 6; ++q) acc += 0.5 * mv.r[q] * sq[q];
-    acc -= 0.5 * alpha * alpha *
-           (mv.c[kHX] * rq[0] + mv.c[kHY] * rq[1] + mv.c[kEX] * rq[2] + mv.c[kEY] * rq[3]);
   }
   const double b = block_reduce<false>(acc);
   if (threadIdx.x == 0) part[blockIdx.x] = b;
@@ -988,19 +967,10 @@ cudaError_t launch_bunch_charge(double q, double sigma, double dz, double zc, in
   return cudaGetLastError();
 }
 
-template cudaError_t launch_energy<float>(const float* const[6], const uint8_t*, const double*,
-                                          const double* const[6], const double* const[6], const Layout&, double,
-                                          const WorkView&, const DiagScratch&, double*,
-                                          cudaStream_t);
 template cudaError_t launch_energy<double>(const double* const[6], const uint8_t*, const double*,
                                            const double* const[6], const double* const[6], const Layout&, double,
                                            const WorkView&, const DiagScratch&, double*,
                                            cudaStream_t);
-template cudaError_t launch_charge<float>(const float* const[6], const float* const[6],
-                                          const uint8_t*, const double*, const double* const[6], const double* const[6],
-                                          const Layout&, double, const double*, int, int,
-                                          const WorkView&, const DiagScratch&, double*, double*,
-                                          cudaStream_t);
 template cudaError_t launch_charge<double>(const double* const[6], const double* const[6],
                                            const uint8_t*, const double*, const double* const[6], const double* const[6],
                                            const Layout&, double, const double*, int, int,

@@ -184,16 +184,18 @@ struct WorkView {
   int tile_x, tile_y, chunk_z, tiles_x, tiles_y;
 };
 
-// Discrete energy W^{n,e} into *result (device); minv[c] constants (mask
-// mode) or minv_a[c] arrays with their reciprocals m_a[c] (0 where minv_a is 0).
+// Float64 fields with material arrays: the discrete energy W^{n,e} into
+// *result (device) from the minv_a[c] arrays and their reciprocals m_a[c]
+// (0 where minv_a is 0). Instantiated for double.
 template <typename T>
 cudaError_t launch_energy(const T* const f[6], const uint8_t* mask, const double* minv,
                           const double* const minv_a[6], const double* const m_a[6], const Layout& L, double alpha,
                           const WorkView& wv, const DiagScratch& s, double* result,
                           cudaStream_t st);
 
-// Charge residuals of the last step into device slots: *res_e = max|qe - qbunch|,
-// *res_h = max|qh|.
+// Float64 fields with material arrays: the charge residuals of the last step
+// into device slots, *res_e = max|qe - qbunch|, *res_h = max|qh|. Instantiated
+// for double.
 template <typename T>
 cudaError_t launch_charge(const T* const cur[6], const T* const prev[6], const uint8_t* mask,
                           const double* minv, const double* const minv_a[6], const double* const m_a[6],
